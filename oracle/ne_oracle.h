@@ -1,0 +1,136 @@
+/*
+ * ne_oracle.h -- plain, slow, FP64 CPU oracle of the nonequilibrium free-energy
+ * method of Freitas, Asta & de Koning (Frenkel-Ladd and reversible-scaling
+ * switching of an EAM crystal under Langevin dynamics).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library exists to check the CUDA path.  Only
+ * the test-suite, the package smoke check and the CPU-baseline leg of the
+ * benchmark may load it.  It shares no code, header, constant or table
+ * generator with the CUDA library; the two are written independently from the
+ * paper and meet only through seeded inputs.
+ *
+ * Units: metal (Angstrom, eV, ps, atomic mass unit, Kelvin).
+ * All arrays are caller-owned host memory.  Positions are AoS [n][3].
+ * Functions return 0 on success, a negative ORA_E* code on error.
+ */
+#ifndef NE_ORACLE_H
+#define NE_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORA_OK = 0, ORA_EINVAL = -1, ORA_ERANGE = -4, ORA_ENAN = -6 };
+enum { ORA_BCC = 0, ORA_FCC = 1 };
+enum { ORA_PATH_FL = 0, ORA_PATH_RS = 1 };
+enum { ORA_H0_EAM = 0, ORA_H0_HARMONIC = 1 };
+/* Philox stream ids (4th counter word, low bits). */
+enum { ORA_STREAM_FL = 0, ORA_STREAM_INITV = 1, ORA_STREAM_RS = 2,
+       ORA_STREAM_MSD = 3, ORA_STREAM_STEP = 4 };
+
+/* Analytic Fe-like EAM: Johnson-type exponential pair and density,
+ * Finnis-Sinclair embedding F = -B sqrt(rho), quintic taper r_s..r_c. */
+typedef struct {
+    double A, alpha, beta, B, r_e, r_s, r_c, rho_max;
+    int n_knots;
+} ora_eam;
+
+/* One Langevin switching trajectory. */
+typedef struct {
+    double dt;        /* ps */
+    double T;         /* K */
+    double damp;      /* ps, gamma = 1/damp */
+    double mass;      /* eV ps^2 / A^2 */
+    double k_spring;  /* Einstein spring, eV/A^2 */
+    int lambda_fn;    /* FL: 1 linear, 2 polynomial */
+    int path;         /* ORA_PATH_FL / ORA_PATH_RS */
+    long t_eq, t_s;   /* steps */
+    double lambda_f;  /* RS end point */
+    uint64_t seed;
+    uint32_t replica;
+    int fix_cm;       /* 1: centre of mass held fixed (noise and force means removed) */
+    int h0;           /* ORA_H0_EAM, or ORA_H0_HARMONIC (springs k_h0 to the sites) */
+    double k_h0;
+} ora_md;
+
+/* constants */
+double ora_kB(void);
+double ora_hbar(void);
+double ora_amu(void);          /* 1 u in eV ps^2/A^2 */
+
+/* crystal: sites r0 [n][3], box lengths; returns n via n_out. */
+int ora_create_crystal(int lattice, double a, int nx, int ny, int nz,
+                       double* x0, double box[3], int* n_out);
+
+/* analytic functions and tables */
+void ora_eam_analytic(const ora_eam* p, int which /*0 phi,1 f,2 F*/, double x,
+                      double* y, double* dy);
+void ora_eam_theta(const ora_eam* p, double* theta /* [3][n_knots][2] */);
+int ora_hermite(const double* th /* [n][2] */, int n, double xmax, double x,
+                double* y, double* dy);
+
+/* neighbour pairs (half list i<j) within rcut, minimum image */
+int ora_pairs_brute(const double* x, int n, const double box[3], double rcut,
+                    int* pi, int* pj, int max_pairs, int* n_pairs);
+int ora_pairs_cells(const double* x, int n, const double box[3], double rcut,
+                    int* pi, int* pj, int max_pairs, int* n_pairs);
+
+/* EAM energy, forces and per-atom density from knot parameters theta. */
+int ora_eam_energy_forces(const ora_eam* p, const double* theta, const double* x,
+                          int n, const double box[3], double* f, double* E,
+                          double* rho);
+/* dE/dtheta [3][n_knots][2] (same layout as theta). */
+int ora_eam_grad_theta(const ora_eam* p, const double* theta, const double* x,
+                       int n, const double box[3], double* grad);
+
+void ora_spring(const double* x, const double* x0, int n, double k, double* f,
+                double* E);
+
+double ora_lambda_fl(int fn, double tau);
+double ora_lambda_rs(double lambda_f, double tau);
+
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void ora_normals(uint64_t seed, uint32_t replica, uint32_t stream, uint32_t atom,
+                 uint64_t step, double z[3]);
+
+int ora_init_velocities(const ora_md* md, int n, double* v);
+
+/* FL schedule: t_eq at 0, switch 0->1, t_eq at 1, switch 1->0.
+ * RS schedule: t_eq at 1, switch 1->lambda_f, t_eq at lambda_f, switch back.
+ * Wcum_f / Wcum_b (nullable): cumulative work after each switch step, t_s+1.
+ * trace (nullable): every trace_stride steps, 8 doubles
+ *   (step, lambda, dH/dlambda, U0, U_E, T_internal, W_f, W_b). */
+int ora_switch_run(const ora_eam* p, const double* theta, const ora_md* md,
+                   double* x, double* v, const double* x0, int n,
+                   const double box[3], double* W_f, double* W_b,
+                   double* Wcum_f, double* Wcum_b, double* trace,
+                   int trace_stride, int n_trace_max);
+
+/* Plain Langevin steps at fixed lambda (FL blend), n_steps, noise stream STEP,
+ * starting at global step step0. */
+int ora_langevin_steps(const ora_eam* p, const double* theta, const ora_md* md,
+                       double lambda, double* x, double* v, const double* x0,
+                       int n, const double box[3], long step0, long n_steps);
+
+/* Spring-constant fit from the mean-squared displacement. */
+int ora_msd_fit(const ora_eam* p, const double* theta, const ora_md* md, double* x,
+                double* v, const double* x0, int n, const double box[3],
+                long n_eq, long n_samples, int stride, double* msd_out,
+                double* k_out);
+
+/* Free-energy assembly (host, FP64). */
+double ora_einstein_F(int n, double T, double mass, double k);
+double ora_cm_correction(int n, double V, double T, double mass, double k);
+int ora_free_energy(int n, double V, double T, double mass, double k,
+                    const double* W_f, const double* W_b, int n_seeds,
+                    double* F_per_atom, double* stderr_per_atom,
+                    double* Ediss_per_atom);
+int ora_rs_free_energy(int n, double T0, double F0_T0, double lambda_f, long t_s,
+                       const double* Wcum_f, const double* Wcum_b, int n_seeds,
+                       const double* T_grid, int n_T, double* F_per_atom);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
