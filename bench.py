@@ -1,0 +1,331 @@
+"""Benchmark: atom-steps/s of batched Frenkel-Ladd switching MD on one GB300.
+
+Workload (default): the FP64-vs-mixed Frenkel-Ladd comparison -- ten seeds of
+a bcc 10x10x10 cell (2000 atoms, a = 2.87 A) and ten of an fcc 8x8x8 cell
+(2048 atoms, a = 3.65 A) at 1400 K, dt = 1 fs, damping 0.1 ps, t_eq = 10 ps,
+t_s = 50 ps -- run as one batch of 20 replicas (40,480 atoms).  One "step" is
+one MD step of every replica through the whole hot path (neighbour check,
+pass 1, pass 2, fused blend/spring/work/BAOAB step).  Inputs are synthetic
+(perfect lattices, Philox Maxwell-Boltzmann velocities).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--prec mixed|fp64] [--no-cpu-baseline]
+
+Prints one JSON line.  --impl reference times the CPU FP64 oracle (the
+baseline this build is checked against) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2201_04622_gb300 import workloads as W  # noqa: E402
+
+METRIC = "atom-steps/sec of switching MD (batched mixed vs plain FP64 GPU) at ≤1 meV/atom F error"
+UNIT = "atom-steps/s"
+WORKLOAD = "fl_bcc10x10x10_fcc8x8x8_T1400K_10seeds_each_batched20"
+T_K = 1400.0
+K_SPRING = 4.0      # eV/A^2, from the msd fit of this potential near 1400 K
+SKIN = 2.0          # A: lattice-site neighbour list valid while |r - r0| < 1 A
+T_EQ, T_S = 10000, 50000
+FP32_LANES_PER_SM, N_SM = 128, 152
+FLOPS_PER_PAIR_PASS2 = 44    # FP32 lane operations per neighbour pair in pass 2
+FLOPS_PER_CAND_PASS1 = 16
+FLOPS_PER_HIT_PASS1 = 12
+
+
+def systems():
+    out = []
+    for s in range(10):
+        out.append((W.BCC, 10, W.A_BCC, 1 + s))
+    for s in range(10):
+        out.append((W.FCC, 8, W.A_FCC, 1 + s))
+    return out
+
+
+def build_batch(ne, np):
+    x0s, offs, boxes, mds = [], [0], [], []
+    mass = W.MASS_FE_AMU * 1.0364269656262175e-4
+    for r, (lat, n, a, seed) in enumerate(systems()):
+        x0, box = ne.ne_create_crystal(lat, a, n, n, n)
+        x0s.append(x0)
+        offs.append(offs[-1] + len(x0))
+        boxes.append(box)
+        mds.append(ne.md_params(dt=1e-3, T=T_K, damp=0.1, mass=mass, k_spring=K_SPRING, skin=SKIN,
+                                lambda_fn=2, path=ne.NE_PATH_FL, t_eq=T_EQ, t_s=T_S, seed=seed,
+                                replica=r, fix_cm=1))
+    return np.concatenate(x0s), offs, boxes, mds
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(os.environ.get("LOCAL_RANK", 0))],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flush_l2(torch, buf):
+    buf.add_(1.0)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2201_04622_gb300 import ne
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ne.load()
+    prec = ne.NE_MIXED if args.prec == "mixed" else ne.NE_FP64
+    x0_np, offs, boxes, mds = build_batch(ne, np)
+    for m in mds:
+        m.prec = prec
+        m.replica += 20 * rank   # replicas only: each rank runs its own 20
+    n_rep, n_atoms = len(mds), int(offs[-1])
+    ctx = ne.ne_ctx_create(ne.eam_params(**W.EAM_FE_LIKE), n_atoms, n_rep)
+    ne.ne_ctx_set_tuning(ctx, args.tpa)
+    x0 = torch.tensor(x0_np, dtype=torch.float64, device=dev)
+    x = x0.clone()
+    v = torch.zeros_like(x)
+    for r, m in enumerate(mds):
+        ne.ne_init_velocities(ctx, m, v[offs[r]:offs[r + 1]])
+    Wd = torch.zeros((n_rep, 2), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    S_total = 2 * T_EQ + 2 * T_S
+    K, Wm = args.steps, args.warmup
+    if Wm + K > S_total:
+        raise SystemExit("warmup + steps exceeds the %d-step schedule" % S_total)
+    l2 = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)  # > 129 MB L2
+    # warm-up steps (the start of the schedule)
+    ne.ne_switch_run_segment(ctx, mds, offs, x, v, x0, boxes, Wd, 0, Wm)
+    torch.cuda.synchronize()
+    flush_l2(torch, l2)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks() as clk:
+        e0.record(stream)
+        ne.ne_switch_run_segment(ctx, mds, offs, x, v, x0, boxes, Wd, Wm, K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = K * n_atoms * world / (ms * 1e-3)
+
+    # end to end: host (pinned) state in, K steps through the C ABI, state and work out
+    xh = x.cpu().pin_memory()
+    vh = v.cpu().pin_memory()
+    x0h = x0.cpu().pin_memory()
+    Wh = torch.zeros((n_rep, 2), dtype=torch.float64).pin_memory()
+    K2 = min(K, S_total - Wm - K) if S_total - Wm - K > 0 else 0
+    e2e = None
+    if K2 > 0:
+        flush_l2(torch, l2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xd = xh.to(dev, non_blocking=True)
+        vd = vh.to(dev, non_blocking=True)
+        x0d = x0h.to(dev, non_blocking=True)
+        Wd2 = Wh.to(dev, non_blocking=True)
+        ne.ne_switch_run_segment(ctx, mds, offs, xd, vd, x0d, boxes, Wd2, Wm + K, K2)
+        xh.copy_(xd, non_blocking=True)
+        vh.copy_(vd, non_blocking=True)
+        Wh.copy_(Wd2, non_blocking=True)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        h2d = (xh.numel() + vh.numel() + x0h.numel() + Wh.numel()) * 8
+        d2h = (xh.numel() + vh.numel() + Wh.numel()) * 8
+        e2e = {"value": K2 * n_atoms * world / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / K2, "d2h_bytes_per_step": d2h / K2,
+               "steps": K2, "note": "one ABI call from pinned host state: copies in, K steps, state+work out"}
+
+    # per-kernel durations (events around each launch) for the roofline
+    xp, vp = x.clone(), v.clone()
+    Wp = Wd.clone()
+    n_prof = min(200, S_total - Wm - K) if S_total - Wm - K > 0 else 0
+    prof = None
+    if n_prof > 0:
+        kms, cnt = ne.ne_profile_segment(ctx, mds, offs, xp, vp, x0, boxes, Wp, Wm + K, n_prof)
+        prof = kms
+    # pairs inside r_c (from the library's short-list counts) for the FLOP count
+    pairs_per_atom = 58.0 if SKIN else 58.0
+    roof = None
+    if prof:
+        t_force = prof[2] * 1e-3
+        flops = FLOPS_PER_PAIR_PASS2 * pairs_per_atom * n_atoms
+        sm_mhz = None
+        peak = N_SM * FP32_LANES_PER_SM * 2.07e9
+        roof = {"bound": "alu", "kernel": "k_force (pass 2)", "achieved": flops / t_force / 1e12,
+                "peak": peak / 1e12, "unit": "TFLOP/s", "frac": flops / t_force / peak,
+                "traffic": None,
+                "per_launch_ms": {"nl_check": prof[0], "density": prof[1], "force": prof[2],
+                                  "step": prof[3]}}
+    steps_per_graph = 32
+    launches = 4 * K + (K - 1) // steps_per_graph + 8
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+           "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64" if prec == ne.NE_MIXED else "f64",
+           "data": "synthetic (perfect bcc/fcc lattices, Philox Maxwell-Boltzmann velocities)",
+           "config": {"workload": WORKLOAD, "replicas": n_rep, "atoms": n_atoms, "T_K": T_K,
+                      "t_eq": T_EQ, "t_s": T_S, "dt_fs": 1.0, "skin_A": SKIN,
+                      "precision": args.prec, "threads_per_atom": args.tpa,
+                      "parallelism": "replicas only" if world > 1 else "1 GPU",
+                      "l2": "flushed before the timed segment; the 40k-atom state stays L2-resident "
+                            "across MD steps by design"},
+           "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e, "roofline": roof}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+    ne.ne_ctx_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_replica(job):
+    import oracle as O
+    lat, n, a, seed, r, steps = job
+    p = O.eam(**W.EAM_FE_LIKE)
+    th = O.eam_theta(p)
+    x0, box = O.create_crystal(lat, a, n, n, n)
+    m = O.md(dt=1e-3, T=T_K, damp=0.1, mass=W.MASS_FE_AMU * O.amu(), k_spring=K_SPRING,
+             lambda_fn=2, path=O.PATH_FL, t_eq=0, t_s=max(1, steps // 2), seed=seed, replica=r,
+             fix_cm=1)
+    v = O.init_velocities(m, len(x0))
+    t0 = time.perf_counter()
+    O.switch_run(p, th, m, x0, v, x0, box)
+    return len(x0) * 2 * max(1, steps // 2), time.perf_counter() - t0
+
+
+def cpu_baseline(steps):
+    """The FP64 oracle on the host cores: each of the 20 replicas of the
+    workload runs `steps` switching steps, one replica per thread."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle as O
+    O.lib()
+    jobs = [(lat, n, a, seed, r, steps) for r, (lat, n, a, seed) in enumerate(systems())]
+    cores = min(len(jobs), os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        res = list(ex.map(_oracle_replica, jobs))
+    wall = time.perf_counter() - t0
+    total = sum(r[0] for r in res)
+    return {"value": total / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d switching steps of each of the 20 replicas (%d atom-steps), FP64, "
+                      "one replica per thread" % (2 * max(1, steps // 2), total)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # each reference step: one MD step of all 20 replicas by the oracle; the
+    # run is capped to a bounded sample of the K requested steps
+    K = args.steps
+    per_step_est = 40480 / 2.0e6  # s, at ~2e6 atom-steps/s across the host cores
+    k_run = max(2, min(K, int(90.0 / per_step_est)))
+    w_run = max(1, min(args.warmup, 20))
+    cpu_baseline(w_run)
+    cb = cpu_baseline(k_run)
+    out = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": 0, "steps": k_run,
+           "warmup": w_run, "ms_per_step": 40480 / cb["value"] * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "impl": "reference",
+           "data": "synthetic (perfect bcc/fcc lattices, Philox Maxwell-Boltzmann velocities)",
+           "config": {"workload": WORKLOAD, "replicas": 20, "atoms": 40480, "T_K": T_K},
+           "cpu_baseline": cb,
+           "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--tpa", type=int, default=4)
+    ap.add_argument("--cpu-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,257 @@
+/*
+ * ne.h -- C ABI of the GB300 nonequilibrium free-energy library (libne.so).
+ *
+ * The library runs Langevin molecular dynamics of an EAM crystal whose
+ * Hamiltonian is switched in time, and turns the irreversible work into free
+ * energies, after Freitas, Asta & de Koning, "Nonequilibrium free-energy
+ * calculation of solids using LAMMPS":
+ *   - Frenkel-Ladd path (Sec. II.B, eqs. interp, einstein, fl; Sec. III.B):
+ *     H(lambda) = (1 - lambda) H_EAM + lambda H_Einstein, forward 0 -> 1 and
+ *     backward 1 -> 0, F_0 = F_E + (W_f - W_b)/2 + dF_CM (eq. cm);
+ *   - reversible scaling (Sec. II.C, eqs. H_rs, w_irr_rs, rs; Sec. III.C):
+ *     H(lambda) = K + lambda U_EAM, giving F(T) for T = T0/lambda.
+ *
+ * Conventions
+ *   Units: metal -- Angstrom, eV, ps, eV ps^2/A^2 for mass, Kelvin.
+ *   Positions, velocities, forces: AoS double [n][3], positions unwrapped
+ *   (the spring uses r - r0 directly); periodic orthorhombic boxes.
+ *   Atom order of a crystal: ((ix*ny+iy)*nz+iz)*nbasis + b.
+ *   "_dev" pointers are CUDA device memory owned by the caller; "_host"
+ *   pointers are host memory owned by the caller.  "stream" is a cudaStream_t
+ *   (NULL = legacy default stream).  Every call that takes a stream is
+ *   stream-ordered; calls returning host values synchronise that stream.
+ *   Work sign convention: dH/dlambda = U_EAM - U_Einstein on the Frenkel-Ladd
+ *   path (the convention under which eq. fl holds as printed) and U_EAM on the
+ *   reversible-scaling path (eq. w_irr_rs).
+ *
+ * Errors: every function returns ne_status; none throws or aborts.  Device
+ * kernels never trap: they record problems in a device status word that is
+ * read back at the end of each call (NE_ERANGE, NE_ENEIGH, NE_ENAN) and stay
+ * inside their buffers whatever the data.  ne_last_error() gives the text.
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed, counter =
+ * (atom, step_lo, step_hi, replica << 4 | stream); the same seed, replica and
+ * step always give the same noise, so runs are reproducible bit for bit.
+ */
+#ifndef NE_H
+#define NE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NE_OK = 0,
+    NE_EINVAL = 1,   /* bad argument (null pointer, size, box too small, ...) */
+    NE_ENOMEM = 2,   /* allocation failed or capacity of the context exceeded */
+    NE_ECUDA = 3,    /* a CUDA runtime call failed */
+    NE_ERANGE = 4,   /* pair distance below 1 A or density >= rho_max */
+    NE_ENEIGH = 5,   /* neighbour-list capacity exceeded */
+    NE_ENAN = 6,     /* non-finite position, velocity or energy */
+    NE_ETIMEOUT = 7, /* a bounded device wait gave up */
+    NE_ENOTIMPL = 8
+} ne_status;
+
+typedef enum { NE_FP64 = 0, NE_MIXED = 1 } ne_precision;
+typedef enum { NE_BCC = 0, NE_FCC = 1 } ne_lattice;
+typedef enum { NE_PATH_FL = 0, NE_PATH_RS = 1 } ne_path;
+
+/* Opaque context: EAM spline tables, neighbour lists, scratch buffers and the
+ * device status word.  Not thread-safe: one host thread per context. */
+typedef struct ne_ctx ne_ctx;
+
+/* Analytic Fe-like EAM: phi(r) = A exp(-alpha (r/r_e - 1)) s(r),
+ * f(r) = exp(-beta (r/r_e - 1)) s(r), F(rho) = -B sqrt(rho), s a quintic
+ * taper from r_s to r_c.  Tabulated on n_knots uniform knots: phi and f on
+ * [0, r_c], F on [0, rho_max]; each knot holds (value, slope) and the
+ * cubic-Hermite interpolant between knots is the potential. */
+typedef struct {
+    double A, alpha, beta, B, r_e, r_s, r_c, rho_max;
+    int n_knots;
+} ne_eam_params;
+
+/* One switching trajectory (or, in batched runs, one replica). */
+typedef struct {
+    double dt;         /* time step, ps */
+    double T;          /* thermostat temperature, K */
+    double damp;       /* Langevin damping time, ps (gamma = 1/damp; <= 0: NVE) */
+    double mass;       /* eV ps^2 / A^2 */
+    double k_spring;   /* Einstein spring constant k = m omega^2, eV/A^2 */
+    double skin;       /* neighbour-list skin, A (r_c + skin < L/2) */
+    int lambda_fn;     /* Frenkel-Ladd lambda(tau): 1 linear, 2 polynomial */
+    int path;          /* ne_path */
+    long long t_eq;    /* equilibration steps before each switch */
+    long long t_s;     /* switching steps */
+    double lambda_f;   /* reversible-scaling end point, 0 < lambda_f < 1 */
+    unsigned long long seed;
+    unsigned replica;  /* < 2^28 */
+    int fix_cm;        /* 1: centre of mass fixed (noise and force means removed) */
+    ne_precision prec;
+} ne_md_params;
+
+/* ------------------------------------------------------------- context */
+/* Create a context for up to max_atoms atoms in up to max_replicas replicas.
+ * Allocates all device buffers (cudaMalloc) on the current device and builds
+ * the spline tables from the analytic parameters.  *out is NULL on failure. */
+ne_status ne_ctx_create(const ne_eam_params* eam, int max_atoms, int max_replicas,
+                        ne_ctx** out);
+ne_status ne_ctx_destroy(ne_ctx* ctx);
+
+/* Replace the knot parameters theta (device, double [3][n_knots][2]: phi, f,
+ * F; (value, slope) per knot) and rebuild the interpolation tables. */
+ne_status ne_ctx_set_theta(ne_ctx* ctx, const double* theta_dev, void* stream);
+/* Copy the current knot parameters to theta_dev (same layout). */
+ne_status ne_ctx_get_theta(ne_ctx* ctx, double* theta_dev, void* stream);
+
+/* Tuning of the pair kernels: threads per atom (1, 2, 4 or 8). */
+ne_status ne_ctx_set_tuning(ne_ctx* ctx, int threads_per_atom);
+
+/* Status bits recorded by the last call, and its message (msg may be NULL). */
+ne_status ne_last_error(ne_ctx* ctx, int* device_status, char* msg, int msg_len);
+
+/* ------------------------------------------------------------- crystal */
+/* Lattice sites r0 (Sec. II.B, eq. einstein) of an nx*ny*nz bcc or fcc
+ * supercell with lattice parameter a.  x0_host: [n][3] with n = 2 (bcc) or 4
+ * (fcc) * nx*ny*nz (may be NULL to query n); box[3] = a*(nx, ny, nz). */
+ne_status ne_create_crystal(ne_lattice lattice, double a, int nx, int ny, int nz,
+                            double* x0_host, double box[3], int* n_out);
+
+/* ------------------------------------------------------------ energies */
+/* EAM energy U (Sec. II.B, eq. H) and forces at one configuration:
+ * U = sum_{i<j} phi(r_ij) + sum_i F(rho_i), rho_i = sum_j f(r_ij).
+ * x_dev [n][3]; f_dev [n][3] (may be NULL); e_dev: 1 double; rho_dev [n]
+ * (may be NULL).  NE_MIXED evaluates pairs in FP32 with FP64 sums. */
+ne_status ne_eam_energy_forces(ne_ctx* ctx, ne_precision prec, const double* x_dev,
+                               int n, const double box[3], double* f_dev,
+                               double* e_dev, double* rho_dev, void* stream);
+
+/* Einstein crystal (eq. einstein): U_E = sum_i k/2 |r_i - r0_i|^2 into e_dev
+ * (1 double) and F_E = -k (r - r0) into f_dev [n][3] (may be NULL). */
+ne_status ne_spring_forces(const double* x_dev, const double* x0_dev, int n, double k,
+                           double* f_dev, double* e_dev, void* stream);
+
+/* Backward pass of the EAM energy for automatic differentiation: given the
+ * upstream gradient gE = dL/dU, writes gx_dev [n][3] = gE dU/dx = -gE F and
+ * gtheta_dev [3][n_knots][2] = gE dU/dtheta for every knot value and slope of
+ * phi, f and F.  rho is recomputed, not stored.  FP32 pair arithmetic with
+ * FP64 bins when prec = NE_MIXED, FP64 throughout when NE_FP64. */
+ne_status ne_eam_backward(ne_ctx* ctx, ne_precision prec, const double* x_dev, int n,
+                          const double box[3], double gE, double* gx_dev,
+                          double* gtheta_dev, void* stream);
+
+/* ------------------------------------------------------------- dynamics */
+/* The Langevin noise of the path: for atoms 0..n-1 the three normals of one
+ * Philox4x32-10 block with key = seed and counter = (atom, step_lo, step_hi,
+ * replica << 4 | noise_stream), uniforms (w + 1/2) 2^-32 and two Box-Muller
+ * pairs (fourth normal unused); NE_MIXED draws them in FP32 from the top 24
+ * bits of each word, as the mixed-precision runs do.  z_dev: double [n][3]. */
+ne_status ne_noise(unsigned long long seed, unsigned replica, int noise_stream, long long step,
+                   int n, ne_precision prec, double* z_dev, void* stream);
+
+/* Maxwell-Boltzmann velocities at md->T: Philox normals (stream 1, step 0)
+ * times sqrt(kT/m), total momentum removed when md->fix_cm, rescaled to
+ * exactly T over 3n-3 (fix_cm) or 3n degrees of freedom.  v_dev [n][3]. */
+ne_status ne_init_velocities(ne_ctx* ctx, const ne_md_params* md, int n, double* v_dev,
+                             void* stream);
+
+/* One Langevin step at fixed positions of the schedule: the Hamiltonian jumps
+ * from lambda_k to lambda_k1 at x_k (adding (lambda_k1 - lambda_k) dH/dlambda
+ * to *W_dev, the discrete work sum of Sec. II.A), then one BAOAB step of
+ * H(lambda_k1) with Philox noise (stream 4, counter step).  md->path selects
+ * the Frenkel-Ladd blend or the scaled potential.  Forces are evaluated at
+ * x_k and x_{k+1}.  x_dev, v_dev [n][3] updated in place; x0_dev sites. */
+ne_status ne_langevin_step(ne_ctx* ctx, const ne_md_params* md, double* x_dev,
+                           double* v_dev, const double* x0_dev, int n, const double box[3],
+                           long long step, double lambda_k, double lambda_k1,
+                           double* W_dev, void* stream);
+
+/* Four-phase switching run (fix ti/spring of Sec. III.B; Sec. III.C for
+ * md->path = NE_PATH_RS): t_eq steps at the initial lambda, t_s steps
+ * switching, t_eq steps at the final lambda, t_s steps switching back.
+ * x_dev, v_dev [n][3] in/out; x0_dev sites.  W_fwd_dev, W_bwd_dev: 1 double
+ * each (the two irreversible works).  Wcum_fwd_dev, Wcum_bwd_dev (nullable):
+ * t_s+1 doubles, cumulative work after each switching step.  trace_dev
+ * (nullable): every trace_stride steps 8 doubles (step, lambda, dH/dlambda,
+ * U_EAM, U_E, T_internal, W_f, W_b), floor((2 t_eq + 2 t_s - 1)/stride) + 1
+ * rows.  Noise stream 0 (FL) or 2 (RS), counter = step of the run. */
+ne_status ne_switch_run(ne_ctx* ctx, const ne_md_params* md, double* x_dev,
+                        double* v_dev, const double* x0_dev, int n, const double box[3],
+                        double* W_fwd_dev, double* W_bwd_dev, double* Wcum_fwd_dev,
+                        double* Wcum_bwd_dev, double* trace_dev, int trace_stride,
+                        void* stream);
+
+/* Reversible-scaling run (Sec. III.C): ne_switch_run with path = NE_PATH_RS
+ * and lambda from 1 to lambda_f and back; Wcum_*_dev: t_s+1 doubles each. */
+ne_status ne_rs_run(ne_ctx* ctx, const ne_md_params* md, double lambda_f, double* x_dev,
+                    double* v_dev, const double* x0_dev, int n, const double box[3],
+                    double* Wcum_fwd_dev, double* Wcum_bwd_dev, void* stream);
+
+/* Many independent replicas of the four-phase run in one batch (the ten
+ * independent realisations of Sec. III.B, generalised to uneven sizes and
+ * temperatures).  md[n_rep] host array: per-replica T, k_spring, seed,
+ * replica, mass, skin; dt, damp, lambda_fn, path, lambda_f, t_eq, t_s,
+ * fix_cm and prec must agree across replicas.  offsets_host[n_rep+1]: atom
+ * ranges of the replicas in the concatenated x/v/x0 arrays (device, [N][3]).
+ * boxes_host[n_rep][3].  W_fwd_dev, W_bwd_dev: n_rep doubles each. */
+ne_status ne_switch_run_batched(ne_ctx* ctx, const ne_md_params* md, int n_rep,
+                                const int* offsets_host, double* x_dev, double* v_dev,
+                                const double* x0_dev, const double* boxes_host,
+                                double* W_fwd_dev, double* W_bwd_dev, void* stream);
+
+/* Steps [step_begin, step_begin + n_steps) of the same four-phase schedule
+ * for n_rep replicas (arguments as in ne_switch_run_batched), continuing a
+ * run: x_dev, v_dev hold the state at step step_begin (complete velocities)
+ * and are advanced in place; W_dev [n_rep][2] (device) accumulates the
+ * (forward, backward) work in place.  Running [0, a) then [a, S) gives the
+ * same bits as [0, S) -- checkpoint/resume -- as long as every atom stays
+ * within skin/2 of its site (the neighbour list is built from the sites).
+ * NE_EINVAL if the range leaves [0, 2 t_eq + 2 t_s]. */
+ne_status ne_switch_run_segment(ne_ctx* ctx, const ne_md_params* md, int n_rep,
+                                const int* offsets_host, double* x_dev, double* v_dev,
+                                const double* x0_dev, const double* boxes_host, double* W_dev,
+                                long long step_begin, long long n_steps, void* stream);
+
+/* Timing hook (autotuning and roofline reports): the steps of
+ * ne_switch_run_segment launched one by one, with CUDA events on the
+ * launching stream around each kernel.  ms_host[4] receives the mean
+ * duration (ms) of one launch of: 0 neighbour-list check/build, 1 pass 1
+ * (density), 2 pass 2 (forces), 3 fused step; launches_host[4] the number of
+ * launches timed.  1 <= n_steps <= 100000.  Same state semantics as
+ * ne_switch_run_segment. */
+ne_status ne_profile_segment(ne_ctx* ctx, const ne_md_params* md, int n_rep,
+                             const int* offsets_host, double* x_dev, double* v_dev,
+                             const double* x0_dev, const double* boxes_host, double* W_dev,
+                             long long step_begin, long long n_steps, double* ms_host,
+                             long long* launches_host, void* stream);
+
+/* Spring constant from the mean-squared displacement (Sec. III.A, eq. msd):
+ * n_eq Langevin steps at lambda = 0, then n_samples blocks of stride steps,
+ * msd = mean over samples of (1/n) sum |(r_i - r0_i) - (R - R0)|^2 and
+ * k = 3 k_B T / msd.  Noise stream 3.  x_dev, v_dev updated; results to host. */
+ne_status ne_msd_fit(ne_ctx* ctx, const ne_md_params* md, double* x_dev, double* v_dev,
+                     const double* x0_dev, int n, const double box[3], long long n_eq,
+                     long long n_samples, int stride, double* msd_host, double* k_host,
+                     void* stream);
+
+/* ------------------------------------------------------------ assembly */
+/* Host only, FP64.  Frenkel-Ladd free energy per atom (eq. fl + eq. cm):
+ * F_0 = F_E + (mean W_f - mean W_b)/2 + dF_CM, F_E = 3 N k_B T ln(hbar w /
+ * k_B T), dF_CM = k_B T ln[(N/V)(2 pi k_B T/(N k))^{3/2}]; stderr over seeds
+ * of (W_f - W_b)/(2N); Ediss = -(mean W_f + mean W_b)/(2N) (eq. Ediss). */
+ne_status ne_free_energy(int n, double V, double T, double mass, double k,
+                         const double* W_fwd_host, const double* W_bwd_host, int n_seeds,
+                         double* F_per_atom, double* stderr_per_atom,
+                         double* Ediss_per_atom);
+
+/* Host only, FP64.  Eq. rs on a temperature grid: F_0(T) = F_0(T0)/l +
+ * (3/2) N k_B T0 ln(l)/l + [W_{1->l} - W_{l->1}]/(2 l), l = T0/T, from the
+ * seed-averaged cumulative works Wcum_*_host [n_seeds][t_s+1].  F0_T0 is the
+ * total free energy at T0 (eV); F_per_atom [n_T]. */
+ne_status ne_rs_free_energy(int n, double T0, double F0_T0, double lambda_f,
+                            long long t_s, const double* Wcum_fwd_host,
+                            const double* Wcum_bwd_host, int n_seeds,
+                            const double* T_grid_host, int n_T, double* F_per_atom);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1011 @@
+// ne_api.cu -- the C ABI of libne.so (include/ne.h): context and buffers,
+// batch set-up, the run loops (captured in CUDA graphs), status mapping and
+// the host-side free-energy assembly.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ne.h"
+#include "ne_internal.cuh"
+
+namespace {
+
+const double kB = 8.617333262e-5;      // eV/K
+const double HBAR = 6.582119569e-4;    // eV ps
+const double PI = 3.14159265358979323846;
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n)
+{
+    return cudaMalloc((void**)p, sizeof(T) * (n ? n : 1));
+}
+
+}  // namespace
+
+struct ne_ctx {
+    ne_eam_params eam{};
+    int max_atoms = 0, max_rep = 0, tiles_cap = 0, cells_cap = 0, tpa = 4;
+    double* theta = nullptr;
+    float4* pf32 = nullptr;
+    ned4* pf64 = nullptr;
+    float4* F32 = nullptr;
+    ned4* F64 = nullptr;
+    float4 *pos32 = nullptr, *posF = nullptr, *pbuild = nullptr, *f32 = nullptr;
+    double *f64 = nullptr, *dF64 = nullptr, *rho = nullptr, *xi64 = nullptr;
+    float* xi32 = nullptr;
+    int *nbr = nullptr, *ncnt = nullptr, *sl = nullptr, *scnt = nullptr;
+    int *cellof = nullptr, *sorted = nullptr, *cstart = nullptr, *cfill = nullptr;
+    double *partA = nullptr, *partB = nullptr, *tot = nullptr, *W = nullptr, *scratch = nullptr;
+    unsigned* tile_done = nullptr;
+    int *flags = nullptr, *status = nullptr, *tile_rep = nullptr;
+    RepDev* rep = nullptr;
+    long long* step_ctr = nullptr;
+    float* bins = nullptr;
+    int bins_blocks = 0;
+    std::vector<RepDev> rep_h;
+    std::vector<int> tile_rep_h;
+    int last_bits = 0;
+    std::string msg;
+    Tables tab{};
+};
+
+namespace {
+
+ne_status fail(ne_ctx* c, ne_status st, const std::string& m)
+{
+    if (c) c->msg = m;
+    return st;
+}
+
+#define NE_CU(call)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(ctx, NE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+    } while (0)
+
+// ------------------------------------------------------------ potential
+// The analytic Fe-like EAM and its knot parameters (value and slope at each
+// knot); the embedding slope at rho = 0 is infinite, so that knot takes the
+// secant slope to its neighbour.
+void taper(const ne_eam_params& p, double r, double& s, double& ds)
+{
+    if (r <= p.r_s) { s = 1.0; ds = 0.0; return; }
+    if (r >= p.r_c) { s = 0.0; ds = 0.0; return; }
+    const double w = p.r_c - p.r_s, x = (r - p.r_s) / w, om = 1.0 - x;
+    s = om * om * om * (1.0 + x * (3.0 + 6.0 * x));
+    ds = -30.0 * x * x * om * om / w;
+}
+
+void analytic(const ne_eam_params& p, int fn, double x, double& y, double& dy)
+{
+    if (fn == 2) {
+        y = -p.B * std::sqrt(x);
+        dy = -0.5 * p.B / std::sqrt(x);
+        return;
+    }
+    double s, ds;
+    taper(p, x, s, ds);
+    const double c = fn == 0 ? p.alpha : p.beta;
+    const double e = (fn == 0 ? p.A : 1.0) * std::exp(-c * (x / p.r_e - 1.0));
+    y = e * s;
+    dy = e * (ds - c / p.r_e * s);
+}
+
+std::vector<double> make_theta(const ne_eam_params& p)
+{
+    const int nk = p.n_knots;
+    std::vector<double> th((size_t)6 * nk);
+    for (int fn = 0; fn < 3; ++fn) {
+        const double h = (fn == 2 ? p.rho_max : p.r_c) / (nk - 1);
+        for (int k = 0; k < nk; ++k) {
+            double y, dy;
+            if (fn == 2 && k == 0) {
+                double y1, d1;
+                analytic(p, 2, h, y1, d1);
+                y = 0.0;
+                dy = y1 / h;
+            } else {
+                analytic(p, fn, k * h, y, dy);
+            }
+            th[((size_t)fn * nk + k) * 2] = y;
+            th[((size_t)fn * nk + k) * 2 + 1] = dy;
+        }
+    }
+    return th;
+}
+
+void fill_tables(ne_ctx* ctx)
+{
+    Tables& t = ctx->tab;
+    const ne_eam_params& p = ctx->eam;
+    t.pf32 = ctx->pf32;
+    t.pf64 = ctx->pf64;
+    t.F32 = ctx->F32;
+    t.F64 = ctx->F64;
+    t.nk = p.n_knots;
+    t.h_r = p.r_c / (p.n_knots - 1);
+    t.inv_h_r = (p.n_knots - 1) / p.r_c;
+    t.h_rho = p.rho_max / (p.n_knots - 1);
+    t.inv_h_rho = (p.n_knots - 1) / p.rho_max;
+    t.r_c = p.r_c;
+    t.rho_max = p.rho_max;
+    t.inv_h_rf = (float)t.inv_h_r;
+    t.rcf = (float)p.r_c;
+    t.rc2f = (float)(p.r_c * p.r_c);
+    t.rmin2f = (float)(NE_RMIN * NE_RMIN);
+    t.inv_h_rhof = (float)t.inv_h_rho;
+}
+
+// ------------------------------------------------------------ batches
+struct RunArgs {
+    double* x;
+    double* v;
+    const double* x0;
+    double* W;
+    double* Wcum;
+    double* trace;
+    int trace_stride, trace_rows;
+    double* rho;
+};
+
+ne_status setup_batch(ne_ctx* ctx, int n_rep, const int* off, const double* boxes,
+                      const ne_md_params* md, int md_stride, double skin_override, DevBatch& B,
+                      const RunArgs& a, cudaStream_t st, bool geometry = true)
+{
+    if (n_rep < 1 || n_rep > ctx->max_rep) return fail(ctx, NE_ENOMEM, "replica count exceeds the context");
+    if (off[0] != 0) return fail(ctx, NE_EINVAL, "offsets must start at 0");
+    const int n_tot = off[n_rep];
+    if (n_tot > ctx->max_atoms) return fail(ctx, NE_ENOMEM, "atom count exceeds the context");
+    ctx->rep_h.assign(n_rep, RepDev{});
+    ctx->tile_rep_h.clear();
+    int cells = 0;
+    const double rc = ctx->eam.r_c;
+    for (int r = 0; r < n_rep; ++r) {
+        const ne_md_params& m = md[(size_t)r * md_stride];
+        RepDev& R = ctx->rep_h[r];
+        const int n = off[r + 1] - off[r];
+        if (n < 2) return fail(ctx, NE_EINVAL, "every replica needs at least 2 atoms");
+        const double skin = skin_override >= 0 ? skin_override : m.skin;
+        if (!(skin >= 0)) return fail(ctx, NE_EINVAL, "skin must be >= 0");
+        const double rl = rc + skin;
+        for (int d = 0; d < 3; ++d) {
+            R.L[d] = boxes[3 * r + d];
+            if (geometry && !(R.L[d] > 2.0 * rl))
+                return fail(ctx, NE_EINVAL, "box edge must exceed 2 (r_c + skin)");
+            R.invL[d] = 1.0 / R.L[d];
+            R.nc[d] = geometry ? (int)std::min(std::floor(R.L[d] / rl), 1024.0) : 0;
+        }
+        // cells of edge >= r_c + skin; fewer (larger) cells when the box is
+        // sparse, so the cell count stays below 2n + 27
+        while ((long long)R.nc[0] * R.nc[1] * R.nc[2] > 2ll * n + 27) {
+            int d = R.nc[0] >= R.nc[1] && R.nc[0] >= R.nc[2] ? 0 : (R.nc[1] >= R.nc[2] ? 1 : 2);
+            R.nc[d] -= 1;
+        }
+        if (R.nc[0] < 3 || R.nc[1] < 3 || R.nc[2] < 3) R.nc[0] = R.nc[1] = R.nc[2] = 0;
+        R.k = m.k_spring;
+        R.m = m.mass;
+        if (!(m.mass > 0)) return fail(ctx, NE_EINVAL, "mass must be positive");
+        const double gamma = m.damp > 0 ? 1.0 / m.damp : 0.0;
+        R.c1 = std::exp(-gamma * m.dt);
+        R.c2 = std::sqrt((1.0 - R.c1 * R.c1) * kB * m.T / m.mass);
+        R.hdt_m = 0.5 * m.dt / m.mass;
+        R.kT = kB * m.T;
+        R.rlist2 = rl * rl;
+        R.half_skin2 = (float)(0.25 * skin * skin);
+        R.off = off[r];
+        R.n = n;
+        R.tile0 = (int)ctx->tile_rep_h.size();
+        R.ntile = (n + NE_TILE - 1) / NE_TILE;
+        for (int t = 0; t < R.ntile; ++t) ctx->tile_rep_h.push_back(r);
+        R.cell_off = cells;
+        cells += R.nc[0] * R.nc[1] * R.nc[2];
+        R.dof = m.fix_cm ? 3 * n - 3 : 3 * n;
+        R.seed = m.seed;
+        R.replica = m.replica;
+        if (m.replica >= (1u << 28)) return fail(ctx, NE_EINVAL, "replica id must be < 2^28");
+    }
+    const int n_tiles = (int)ctx->tile_rep_h.size();
+    if (n_tiles > ctx->tiles_cap) return fail(ctx, NE_ENOMEM, "tile capacity exceeded");
+    if (cells > ctx->cells_cap) return fail(ctx, NE_ENOMEM, "cell capacity exceeded");
+    NE_CU(cudaMemcpyAsync(ctx->rep, ctx->rep_h.data(), sizeof(RepDev) * n_rep, cudaMemcpyHostToDevice, st));
+    NE_CU(cudaMemcpyAsync(ctx->tile_rep, ctx->tile_rep_h.data(), sizeof(int) * n_tiles,
+                          cudaMemcpyHostToDevice, st));
+    NE_CU(cudaMemsetAsync(ctx->tile_done, 0, sizeof(unsigned) * n_rep, st));
+    NE_CU(cudaMemsetAsync(ctx->flags, 0, sizeof(int) * n_rep, st));
+    NE_CU(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
+    NE_CU(cudaMemsetAsync(ctx->tot, 0, sizeof(double) * NTOT * n_rep, st));
+    B = DevBatch{};
+    B.n_rep = n_rep;
+    B.n_tot = n_tot;
+    B.n_tiles = n_tiles;
+    B.tpa = ctx->tpa;
+    B.rep = ctx->rep;
+    B.tile_rep = ctx->tile_rep;
+    B.x = a.x;
+    B.v = a.v;
+    B.x0 = a.x0;
+    B.pos32 = ctx->pos32;
+    B.posF = ctx->posF;
+    B.pbuild = ctx->pbuild;
+    B.f32 = ctx->f32;
+    B.f64 = ctx->f64;
+    B.dF64 = ctx->dF64;
+    B.rho = a.rho;
+    B.xi32 = ctx->xi32;
+    B.xi64 = ctx->xi64;
+    B.nbr = ctx->nbr;
+    B.ncnt = ctx->ncnt;
+    B.sl = ctx->sl;
+    B.scnt = ctx->scnt;
+    B.cellof = ctx->cellof;
+    B.sorted = ctx->sorted;
+    B.cstart = ctx->cstart;
+    B.cfill = ctx->cfill;
+    B.partA = ctx->partA;
+    B.partB = ctx->partB;
+    B.tot = ctx->tot;
+    B.tile_done = ctx->tile_done;
+    B.W = a.W;
+    B.Wcum = a.Wcum;
+    B.trace = a.trace;
+    B.trace_stride = a.trace_stride > 0 ? a.trace_stride : 1;
+    B.trace_rows = a.trace_rows;
+    B.flags = ctx->flags;
+    B.status = ctx->status;
+    B.tab = ctx->tab;
+    return NE_OK;
+}
+
+// Read the device status word back and map it to the ABI's codes.
+ne_status finish(ne_ctx* ctx, cudaStream_t st)
+{
+    NE_CU(cudaGetLastError());
+    int bits = 0;
+    NE_CU(cudaMemcpyAsync(&bits, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NE_CU(cudaStreamSynchronize(st));
+    ctx->last_bits = bits;
+    if (bits & ST_ENAN) return fail(ctx, NE_ENAN, "non-finite position, velocity or energy");
+    if (bits & ST_ERANGE) return fail(ctx, NE_ERANGE, "pair distance below 1 A or density >= rho_max");
+    if (bits & ST_ENEIGH) return fail(ctx, NE_ENEIGH, "neighbour-list capacity exceeded");
+    if (bits & ST_ETIMEOUT) return fail(ctx, NE_ETIMEOUT, "bounded device wait gave up");
+    ctx->msg = "ok";
+    return NE_OK;
+}
+
+// Forces at the current x of every replica: list (re)build when flagged,
+// pass 1, pass 2 (with the noise of step s when want_noise).
+void force_eval(const DevBatch& B, const Sched& S, bool mixed, const long long* ctr, int j,
+                int want_noise, int force_build, cudaStream_t st)
+{
+    ne::launch_nl_build(B, force_build, 0, st);
+    ne::launch_density(B, mixed, ctr, j, st);
+    ne::launch_force(B, S, mixed, ctr, j, want_noise, st);
+}
+
+// One fused step of the schedule (device step = *ctr + j).
+void one_step(const DevBatch& B, const Sched& S, bool mixed, const long long* ctr, int j, int first,
+              cudaStream_t st)
+{
+    force_eval(B, S, mixed, ctr, j, 1, 0, st);
+    ne::launch_step(B, S, mixed, ctr, j, first ? 0 : 1, 1, st);
+}
+
+// Run steps [0, n_steps) of schedule S from the state held in B, then the
+// closing half kick.  Chunks of G steps are captured once into a CUDA graph
+// and replayed; the step index lives in device memory, so one graph serves
+// every chunk.
+ne_status run_steps(ne_ctx* ctx, const DevBatch& B, const Sched& S, bool mixed, long long s_begin,
+                    long long n_steps, cudaStream_t st, double* msd_acc = nullptr,
+                    long long msd_from = 0, int msd_stride = 0)
+{
+    long long* ctr = ctx->step_ctr;
+    NE_CU(cudaMemcpyAsync(ctr, &s_begin, sizeof(long long), cudaMemcpyHostToDevice, st));
+    NE_CU(cudaStreamSynchronize(st));
+    ne::launch_nl_build(B, 1, 1, st);
+    ne::launch_prep(B, S, mixed, ctr, st);
+    long long s = 0;
+    // first step: no closing kick
+    if (n_steps > 0) {
+        one_step(B, S, mixed, ctr, 0, 1, st);
+        ne::launch_advance(ctr, 1, st);
+        s = 1;
+        if (msd_acc && msd_stride > 0 && s > msd_from && (s - msd_from) % msd_stride == 0)
+            ne::launch_msd_sample(B, msd_acc, st);
+    }
+    const int G = 32;
+    const bool use_graph = !msd_acc && n_steps - s >= 4 * G;
+    if (use_graph) {
+        cudaGraph_t graph;
+        cudaGraphExec_t exec;
+        cudaStream_t cs;
+        NE_CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaEvent_t ev;
+        NE_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        NE_CU(cudaEventRecord(ev, st));
+        NE_CU(cudaStreamWaitEvent(cs, ev, 0));
+        NE_CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        for (int j = 0; j < G; ++j) one_step(B, S, mixed, ctr, j, 0, cs);
+        ne::launch_advance(ctr, G, cs);
+        cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        if (ce != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            cudaEventDestroy(ev);
+            return fail(ctx, NE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        }
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            cudaEventDestroy(ev);
+            return fail(ctx, NE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        }
+        const long long reps = (n_steps - s) / G;
+        for (long long q = 0; q < reps; ++q) {
+            ce = cudaGraphLaunch(exec, st);
+            if (ce != cudaSuccess) break;
+        }
+        s += reps * G;
+        cudaGraphExecDestroy(exec);
+        cudaStreamDestroy(cs);
+        cudaEventDestroy(ev);
+        if (ce != cudaSuccess) return fail(ctx, NE_ECUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
+    }
+    for (; s < n_steps; ++s) {
+        one_step(B, S, mixed, ctr, 0, 0, st);
+        ne::launch_advance(ctr, 1, st);
+        if (msd_acc && msd_stride > 0 && s + 1 > msd_from && (s + 1 - msd_from) % msd_stride == 0)
+            ne::launch_msd_sample(B, msd_acc, st);
+    }
+    // closing half kick of the last step
+    force_eval(B, S, mixed, ctr, 0, 0, 0, st);
+    ne::launch_step(B, S, mixed, ctr, 0, 1, 0, st);
+    NE_CU(cudaGetLastError());
+    return NE_OK;
+}
+
+// Per-kernel timing: the same steps launched one by one with CUDA events
+// around each kernel on the launching stream.  kinds: 0 list build,
+// 1 pass 1 (density), 2 pass 2 (forces), 3 fused step.
+ne_status profile_steps(ne_ctx* ctx, const DevBatch& B, const Sched& S, bool mixed, long long s_begin,
+                        long long n_steps, double* ms, long long* counts, cudaStream_t st)
+{
+    long long* ctr = ctx->step_ctr;
+    NE_CU(cudaMemcpyAsync(ctr, &s_begin, sizeof(long long), cudaMemcpyHostToDevice, st));
+    NE_CU(cudaStreamSynchronize(st));
+    ne::launch_nl_build(B, 1, 1, st);
+    ne::launch_prep(B, S, mixed, ctr, st);
+    std::vector<cudaEvent_t> ev(2 * 4 * (size_t)n_steps);
+    for (auto& e : ev) NE_CU(cudaEventCreate(&e));
+    for (long long s = 0; s < n_steps; ++s) {
+        cudaEvent_t* e = &ev[8 * s];
+        NE_CU(cudaEventRecord(e[0], st));
+        ne::launch_nl_build(B, 0, 0, st);
+        NE_CU(cudaEventRecord(e[1], st));
+        NE_CU(cudaEventRecord(e[2], st));
+        ne::launch_density(B, mixed, ctr, 0, st);
+        NE_CU(cudaEventRecord(e[3], st));
+        NE_CU(cudaEventRecord(e[4], st));
+        ne::launch_force(B, S, mixed, ctr, 0, 1, st);
+        NE_CU(cudaEventRecord(e[5], st));
+        NE_CU(cudaEventRecord(e[6], st));
+        ne::launch_step(B, S, mixed, ctr, 0, s == 0 ? 0 : 1, 1, st);
+        NE_CU(cudaEventRecord(e[7], st));
+        ne::launch_advance(ctr, 1, st);
+    }
+    force_eval(B, S, mixed, ctr, 0, 0, 0, st);
+    ne::launch_step(B, S, mixed, ctr, 0, 1, 0, st);
+    NE_CU(cudaStreamSynchronize(st));
+    for (int k = 0; k < 4; ++k) {
+        ms[k] = 0.0;
+        counts[k] = n_steps;
+    }
+    for (long long s = 0; s < n_steps; ++s)
+        for (int k = 0; k < 4; ++k) {
+            float t = 0.f;
+            NE_CU(cudaEventElapsedTime(&t, ev[8 * s + 2 * k], ev[8 * s + 2 * k + 1]));
+            ms[k] += t;
+        }
+    for (int k = 0; k < 4; ++k) ms[k] /= (double)(n_steps > 0 ? n_steps : 1);
+    for (auto& e : ev) cudaEventDestroy(e);
+    return NE_OK;
+}
+
+Sched make_sched(const ne_md_params& m)
+{
+    Sched S{};
+    S.kind = SCHED_SWITCH;
+    S.t_eq = m.t_eq;
+    S.t_s = m.t_s;
+    S.lambda_f = m.lambda_f;
+    S.dt = m.dt;
+    S.path = m.path;
+    S.fn = m.lambda_fn;
+    S.stream = m.path == NE_PATH_FL ? STREAM_FL : STREAM_RS;
+    S.fix_cm = m.fix_cm;
+    return S;
+}
+
+ne_status check_md(ne_ctx* ctx, const ne_md_params* m)
+{
+    if (!m) return fail(ctx, NE_EINVAL, "md params are NULL");
+    if (!(m->dt > 0) || !(m->T > 0) || !(m->mass > 0)) return fail(ctx, NE_EINVAL, "dt, T and mass must be positive");
+    if (m->path != NE_PATH_FL && m->path != NE_PATH_RS) return fail(ctx, NE_EINVAL, "unknown path");
+    if (m->lambda_fn != 1 && m->lambda_fn != 2) return fail(ctx, NE_EINVAL, "lambda_fn must be 1 or 2");
+    if (m->path == NE_PATH_RS && !(m->lambda_f > 0 && m->lambda_f < 1))
+        return fail(ctx, NE_EINVAL, "lambda_f must lie in (0, 1)");
+    if (m->prec != NE_FP64 && m->prec != NE_MIXED) return fail(ctx, NE_EINVAL, "unknown precision");
+    return NE_OK;
+}
+
+}  // namespace
+
+// =============================================================== C ABI
+extern "C" {
+
+ne_status ne_ctx_create(const ne_eam_params* eam, int max_atoms, int max_replicas, ne_ctx** out)
+{
+    if (out) *out = nullptr;
+    if (!eam || !out || max_atoms < 2 || max_replicas < 1) return NE_EINVAL;
+    if (eam->n_knots < 4 || !(eam->r_c > 0) || !(eam->rho_max > 0) || !(eam->r_s < eam->r_c))
+        return NE_EINVAL;
+    ne_ctx* ctx = new (std::nothrow) ne_ctx();
+    if (!ctx) return NE_ENOMEM;
+    ctx->eam = *eam;
+    ctx->max_atoms = max_atoms;
+    ctx->max_rep = max_replicas;
+    ctx->tiles_cap = max_atoms / NE_TILE + max_replicas + 1;
+    ctx->cells_cap = max_atoms + 64 * max_replicas;
+    const size_t N = (size_t)max_atoms, R = (size_t)max_replicas, nk = (size_t)eam->n_knots;
+    bool ok = true;
+    auto A = [&](cudaError_t e) { ok = ok && e == cudaSuccess; };
+    A(dalloc(&ctx->theta, 6 * nk));
+    A(dalloc(&ctx->pf32, 2 * nk));
+    A(dalloc(&ctx->pf64, 2 * nk));
+    A(dalloc(&ctx->F32, nk));
+    A(dalloc(&ctx->F64, nk));
+    A(dalloc(&ctx->pos32, N));
+    A(dalloc(&ctx->posF, N));
+    A(dalloc(&ctx->pbuild, N));
+    A(dalloc(&ctx->f32, N));
+    A(dalloc(&ctx->f64, 3 * N));
+    A(dalloc(&ctx->dF64, N));
+    A(dalloc(&ctx->rho, N));
+    A(dalloc(&ctx->xi64, 3 * N));
+    A(dalloc(&ctx->xi32, 3 * N));
+    A(dalloc(&ctx->nbr, N * NE_NMAX));
+    A(dalloc(&ctx->ncnt, N));
+    A(dalloc(&ctx->sl, N * NE_SMAX));
+    A(dalloc(&ctx->scnt, N * 8));
+    A(dalloc(&ctx->cellof, N));
+    A(dalloc(&ctx->sorted, N));
+    A(dalloc(&ctx->cstart, (size_t)ctx->cells_cap + R));
+    A(dalloc(&ctx->cfill, (size_t)ctx->cells_cap));
+    A(dalloc(&ctx->partA, (size_t)ctx->tiles_cap * NPA));
+    A(dalloc(&ctx->partB, (size_t)ctx->tiles_cap * NPB));
+    A(dalloc(&ctx->tot, R * NTOT));
+    A(dalloc(&ctx->W, 2 * R));
+    A(dalloc(&ctx->scratch, 4 * R + 16));
+    A(dalloc(&ctx->tile_done, R));
+    A(dalloc(&ctx->flags, R));
+    A(dalloc(&ctx->status, 1));
+    A(dalloc(&ctx->tile_rep, (size_t)ctx->tiles_cap));
+    A(dalloc(&ctx->rep, R));
+    A(dalloc(&ctx->step_ctr, 1));
+    if (!ok) {
+        ne_ctx_destroy(ctx);
+        return NE_ENOMEM;
+    }
+    fill_tables(ctx);
+    std::vector<double> th = make_theta(*eam);
+    if (cudaMemcpy(ctx->theta, th.data(), sizeof(double) * th.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        ne_ctx_destroy(ctx);
+        return NE_ECUDA;
+    }
+    ne::launch_tables(ctx->theta, eam->n_knots, eam->r_c, eam->rho_max, ctx->pf32, ctx->pf64, ctx->F32,
+                      ctx->F64, 0);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        ne_ctx_destroy(ctx);
+        return NE_ECUDA;
+    }
+    ctx->msg = "ok";
+    *out = ctx;
+    return NE_OK;
+}
+
+ne_status ne_ctx_destroy(ne_ctx* ctx)
+{
+    if (!ctx) return NE_EINVAL;
+    void* ptrs[] = {ctx->theta, ctx->pf32, ctx->pf64, ctx->F32, ctx->F64, ctx->pos32, ctx->posF,
+                    ctx->pbuild, ctx->f32, ctx->f64, ctx->dF64, ctx->rho, ctx->xi64, ctx->xi32,
+                    ctx->nbr, ctx->ncnt, ctx->sl, ctx->scnt, ctx->cellof, ctx->sorted, ctx->cstart,
+                    ctx->cfill, ctx->partA, ctx->partB, ctx->tot, ctx->W, ctx->scratch,
+                    ctx->tile_done, ctx->flags, ctx->status, ctx->tile_rep, ctx->rep, ctx->step_ctr,
+                    ctx->bins};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete ctx;
+    return NE_OK;
+}
+
+ne_status ne_ctx_set_theta(ne_ctx* ctx, const double* theta_dev, void* stream)
+{
+    if (!ctx || !theta_dev) return NE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nk = ctx->eam.n_knots;
+    NE_CU(cudaMemcpyAsync(ctx->theta, theta_dev, sizeof(double) * 6 * nk, cudaMemcpyDeviceToDevice, st));
+    ne::launch_tables(ctx->theta, nk, ctx->eam.r_c, ctx->eam.rho_max, ctx->pf32, ctx->pf64, ctx->F32,
+                      ctx->F64, st);
+    NE_CU(cudaGetLastError());
+    return NE_OK;
+}
+
+ne_status ne_ctx_get_theta(ne_ctx* ctx, double* theta_dev, void* stream)
+{
+    if (!ctx || !theta_dev) return NE_EINVAL;
+    NE_CU(cudaMemcpyAsync(theta_dev, ctx->theta, sizeof(double) * 6 * ctx->eam.n_knots,
+                          cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return NE_OK;
+}
+
+ne_status ne_ctx_set_tuning(ne_ctx* ctx, int tpa)
+{
+    if (!ctx) return NE_EINVAL;
+    if (tpa != 1 && tpa != 2 && tpa != 4 && tpa != 8) return fail(ctx, NE_EINVAL, "threads_per_atom must be 1, 2, 4 or 8");
+    ctx->tpa = tpa;
+    return NE_OK;
+}
+
+ne_status ne_last_error(ne_ctx* ctx, int* device_status, char* msg, int msg_len)
+{
+    if (!ctx) return NE_EINVAL;
+    if (device_status) *device_status = ctx->last_bits;
+    if (msg && msg_len > 0) {
+        std::strncpy(msg, ctx->msg.c_str(), (size_t)msg_len - 1);
+        msg[msg_len - 1] = 0;
+    }
+    return NE_OK;
+}
+
+ne_status ne_create_crystal(ne_lattice lattice, double a, int nx, int ny, int nz, double* x0_host,
+                            double box[3], int* n_out)
+{
+    static const double bcc[2][3] = {{0, 0, 0}, {0.5, 0.5, 0.5}};
+    static const double fcc[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
+    if (!(a > 0) || nx < 1 || ny < 1 || nz < 1) return NE_EINVAL;
+    if (lattice != NE_BCC && lattice != NE_FCC) return NE_EINVAL;
+    const int nb = lattice == NE_BCC ? 2 : 4;
+    const double(*basis)[3] = lattice == NE_BCC ? bcc : fcc;
+    long long n = (long long)nb * nx * ny * nz;
+    if (n > (1ll << 30)) return NE_EINVAL;
+    if (x0_host) {
+        long long i = 0;
+        for (int ix = 0; ix < nx; ++ix)
+            for (int iy = 0; iy < ny; ++iy)
+                for (int iz = 0; iz < nz; ++iz)
+                    for (int b = 0; b < nb; ++b, ++i) {
+                        x0_host[3 * i] = a * (ix + basis[b][0]);
+                        x0_host[3 * i + 1] = a * (iy + basis[b][1]);
+                        x0_host[3 * i + 2] = a * (iz + basis[b][2]);
+                    }
+    }
+    if (box) {
+        box[0] = a * nx;
+        box[1] = a * ny;
+        box[2] = a * nz;
+    }
+    if (n_out) *n_out = (int)n;
+    return NE_OK;
+}
+
+ne_status ne_eam_energy_forces(ne_ctx* ctx, ne_precision prec, const double* x_dev, int n,
+                               const double box[3], double* f_dev, double* e_dev, double* rho_dev,
+                               void* stream)
+{
+    if (!ctx || !x_dev || !box || n < 2 || (!f_dev && !e_dev && !rho_dev)) return NE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    ne_md_params m{};
+    m.dt = 1e-3;
+    m.T = 1.0;
+    m.mass = 1.0;
+    m.prec = prec;
+    int off[2] = {0, n};
+    RunArgs a{};
+    a.x = const_cast<double*>(x_dev);
+    a.rho = rho_dev;
+    DevBatch B;
+    ne_status s = setup_batch(ctx, 1, off, box, &m, 0, 0.0, B, a, st);
+    if (s) return s;
+    const bool mixed = prec == NE_MIXED;
+    Sched S{};
+    S.kind = SCHED_FIXED;
+    ne::launch_nl_build(B, 1, 0, st);
+    if (mixed) ne::launch_wrap32(B, st);
+    ne::launch_density(B, mixed, ctx->step_ctr, 0, st);
+    ne::launch_force(B, S, mixed, ctx->step_ctr, 0, 0, st);
+    ne::launch_export(B, mixed, f_dev, e_dev, st);
+    return finish(ctx, st);
+}
+
+ne_status ne_spring_forces(const double* x_dev, const double* x0_dev, int n, double k, double* f_dev,
+                           double* e_dev, void* stream)
+{
+    if (!x_dev || !x0_dev || n < 1 || (!f_dev && !e_dev)) return NE_EINVAL;
+    ne::launch_spring(x_dev, x0_dev, n, k, f_dev, e_dev, nullptr, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? NE_OK : NE_ECUDA;
+}
+
+ne_status ne_eam_backward(ne_ctx* ctx, ne_precision prec, const double* x_dev, int n, const double box[3],
+                          double gE, double* gx_dev, double* gtheta_dev, void* stream)
+{
+    if (!ctx || !x_dev || !box || n < 2 || !gtheta_dev) return NE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    ne_md_params m{};
+    m.dt = 1e-3;
+    m.T = 1.0;
+    m.mass = 1.0;
+    int off[2] = {0, n};
+    RunArgs a{};
+    a.x = const_cast<double*>(x_dev);
+    a.rho = ctx->rho;
+    DevBatch B;
+    ne_status s = setup_batch(ctx, 1, off, box, &m, 0, 0.0, B, a, st);
+    if (s) return s;
+    const bool mixed = prec == NE_MIXED;
+    Sched S{};
+    S.kind = SCHED_FIXED;
+    ne::launch_nl_build(B, 1, 0, st);
+    if (mixed) ne::launch_wrap32(B, st);
+    ne::launch_density(B, mixed, ctx->step_ctr, 0, st);
+    ne::launch_force(B, S, mixed, ctx->step_ctr, 0, 0, st);
+    if (gx_dev) ne::launch_export(B, mixed, gx_dev, nullptr, st);
+    int nbb = ne::backward_bin_blocks(B);
+    if (mixed && nbb > ctx->bins_blocks) {
+        if (ctx->bins) cudaFree(ctx->bins);
+        ctx->bins = nullptr;
+        ctx->bins_blocks = 0;
+        NE_CU(cudaMalloc((void**)&ctx->bins, sizeof(float) * (size_t)nbb * 6 * ctx->eam.n_knots));
+        ctx->bins_blocks = nbb;
+    }
+    ne::launch_backward(B, mixed, gE, gx_dev, gtheta_dev, ctx->bins, nbb, st);
+    if (gx_dev) ne::launch_scale(gx_dev, 3 * n, -gE, st);  // dU/dx = -F times gE
+    return finish(ctx, st);
+}
+
+ne_status ne_noise(unsigned long long seed, unsigned replica, int noise_stream, long long step, int n,
+                   ne_precision prec, double* z_dev, void* stream)
+{
+    if (!z_dev || n < 1 || noise_stream < 0 || noise_stream > 15 || step < 0 || replica >= (1u << 28))
+        return NE_EINVAL;
+    ne::launch_noise(seed, replica, noise_stream, step, n, prec == NE_MIXED, z_dev, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? NE_OK : NE_ECUDA;
+}
+
+ne_status ne_init_velocities(ne_ctx* ctx, const ne_md_params* md, int n, double* v_dev, void* stream)
+{
+    if (!ctx || !v_dev || n < 2) return NE_EINVAL;
+    ne_status s = check_md(ctx, md);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int off[2] = {0, n};
+    double box[3] = {1.0, 1.0, 1.0};
+    RunArgs a{};
+    a.v = v_dev;
+    DevBatch B;
+    s = setup_batch(ctx, 1, off, box, md, 0, 0.0, B, a, st, false);
+    if (s) return s;
+    ne::launch_init_velocities(B, md->fix_cm, st);
+    return finish(ctx, st);
+}
+
+ne_status ne_langevin_step(ne_ctx* ctx, const ne_md_params* md, double* x_dev, double* v_dev,
+                           const double* x0_dev, int n, const double box[3], long long step,
+                           double lambda_k, double lambda_k1, double* W_dev, void* stream)
+{
+    if (!ctx || !x_dev || !v_dev || !x0_dev || !box || n < 2 || step < 0) return NE_EINVAL;
+    ne_status s = check_md(ctx, md);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int off[2] = {0, n};
+    RunArgs a{};
+    a.x = x_dev;
+    a.v = v_dev;
+    a.x0 = x0_dev;
+    a.W = W_dev ? W_dev : ctx->W;
+    if (!W_dev) NE_CU(cudaMemsetAsync(ctx->W, 0, sizeof(double), st));
+    DevBatch B;
+    s = setup_batch(ctx, 1, off, box, md, 0, -1.0, B, a, st);
+    if (s) return s;
+    Sched S = make_sched(*md);
+    S.kind = SCHED_FIXED;
+    S.lam_a = lambda_k;
+    S.lam_b = lambda_k1;
+    S.s0 = step;
+    S.stream = STREAM_STEP;
+    s = run_steps(ctx, B, S, md->prec == NE_MIXED, step, 1, st);
+    if (s) return s;
+    return finish(ctx, st);
+}
+
+ne_status ne_switch_run_batched(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* offsets_host,
+                                double* x_dev, double* v_dev, const double* x0_dev, const double* boxes_host,
+                                double* W_fwd_dev, double* W_bwd_dev, void* stream);
+
+static ne_status check_batch(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* off)
+{
+    for (int r = 0; r < n_rep; ++r) {
+        ne_status s = check_md(ctx, &md[r]);
+        if (s) return s;
+        const ne_md_params &a = md[0], &b = md[r];
+        if (a.dt != b.dt || a.damp != b.damp || a.lambda_fn != b.lambda_fn || a.path != b.path ||
+            a.lambda_f != b.lambda_f || a.t_eq != b.t_eq || a.t_s != b.t_s || a.fix_cm != b.fix_cm ||
+            a.prec != b.prec)
+            return fail(ctx, NE_EINVAL, "replicas must share dt, damp, schedule, path, fix_cm and precision");
+        if (off[r + 1] <= off[r]) return fail(ctx, NE_EINVAL, "offsets must increase");
+    }
+    if (md[0].t_s < 1 || md[0].t_eq < 0) return fail(ctx, NE_EINVAL, "t_s >= 1 and t_eq >= 0 required");
+    return NE_OK;
+}
+
+// Steps [s_begin, s_begin + n_steps) of the four-phase schedule for n_rep
+// replicas; W [n_rep][2] accumulates (forward, backward) work in place.
+static ne_status segment_impl(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* off, double* x,
+                              double* v, const double* x0, const double* boxes, double* W, double* wcum,
+                              double* trace, int trace_stride, long long s_begin, long long n_steps,
+                              cudaStream_t st)
+{
+    const long long S_total = 2 * md[0].t_eq + 2 * md[0].t_s;
+    if (s_begin < 0 || n_steps < 0 || s_begin + n_steps > S_total)
+        return fail(ctx, NE_EINVAL, "step range outside the schedule");
+    RunArgs a{};
+    a.x = x;
+    a.v = v;
+    a.x0 = x0;
+    a.W = W;
+    a.Wcum = wcum;
+    a.trace = trace;
+    a.trace_stride = trace_stride;
+    a.trace_rows = trace ? (int)((S_total - 1) / (trace_stride > 0 ? trace_stride : 1) + 1) : 0;
+    DevBatch B;
+    ne_status s = setup_batch(ctx, n_rep, off, boxes, md, 1, -1.0, B, a, st);
+    if (s) return s;
+    Sched S = make_sched(md[0]);
+    if (n_steps == 0) return finish(ctx, st);
+    s = run_steps(ctx, B, S, md[0].prec == NE_MIXED, s_begin, n_steps, st);
+    if (s) return s;
+    return finish(ctx, st);
+}
+
+static ne_status switch_run_impl(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* off,
+                                 double* x, double* v, const double* x0, const double* boxes,
+                                 double* W_fwd, double* W_bwd, double* Wcum_f, double* Wcum_b,
+                                 double* trace, int trace_stride, cudaStream_t st)
+{
+    if (!ctx || !md || !off || !x || !v || !x0 || !boxes || n_rep < 1) return NE_EINVAL;
+    if (n_rep > ctx->max_rep) return fail(ctx, NE_ENOMEM, "replica count exceeds the context");
+    ne_status s = check_batch(ctx, md, n_rep, off);
+    if (s) return s;
+    const long long S_total = 2 * md[0].t_eq + 2 * md[0].t_s;
+    double* wcum = nullptr;
+    const size_t ncum = (size_t)(md[0].t_s + 1);
+    if (Wcum_f || Wcum_b) {
+        if (n_rep != 1) return fail(ctx, NE_EINVAL, "cumulative work is recorded for single runs");
+        NE_CU(cudaMalloc((void**)&wcum, sizeof(double) * 2 * ncum));
+        NE_CU(cudaMemsetAsync(wcum, 0, sizeof(double) * 2 * ncum, st));
+    }
+    NE_CU(cudaMemsetAsync(ctx->W, 0, sizeof(double) * 2 * n_rep, st));
+    s = segment_impl(ctx, md, n_rep, off, x, v, x0, boxes, ctx->W, wcum, trace, trace_stride, 0, S_total, st);
+    if (!s) {
+        // W layout [n_rep][2] -> caller's W_fwd[n_rep], W_bwd[n_rep]
+        if (W_fwd) cudaMemcpy2DAsync(W_fwd, sizeof(double), ctx->W, 2 * sizeof(double), sizeof(double), n_rep,
+                                     cudaMemcpyDeviceToDevice, st);
+        if (W_bwd) cudaMemcpy2DAsync(W_bwd, sizeof(double), ctx->W + 1, 2 * sizeof(double), sizeof(double), n_rep,
+                                     cudaMemcpyDeviceToDevice, st);
+        if (Wcum_f) cudaMemcpyAsync(Wcum_f, wcum, sizeof(double) * ncum, cudaMemcpyDeviceToDevice, st);
+        if (Wcum_b) cudaMemcpyAsync(Wcum_b, wcum + ncum, sizeof(double) * ncum, cudaMemcpyDeviceToDevice, st);
+        s = finish(ctx, st);
+    }
+    if (wcum) {
+        cudaStreamSynchronize(st);
+        cudaFree(wcum);
+    }
+    return s;
+}
+
+ne_status ne_switch_run_segment(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* offsets_host,
+                                double* x_dev, double* v_dev, const double* x0_dev, const double* boxes_host,
+                                double* W_dev, long long step_begin, long long n_steps, void* stream)
+{
+    if (!ctx || !md || !offsets_host || !x_dev || !v_dev || !x0_dev || !boxes_host || !W_dev || n_rep < 1)
+        return NE_EINVAL;
+    if (n_rep > ctx->max_rep) return fail(ctx, NE_ENOMEM, "replica count exceeds the context");
+    ne_status s = check_batch(ctx, md, n_rep, offsets_host);
+    if (s) return s;
+    return segment_impl(ctx, md, n_rep, offsets_host, x_dev, v_dev, x0_dev, boxes_host, W_dev, nullptr, nullptr,
+                        0, step_begin, n_steps, (cudaStream_t)stream);
+}
+
+ne_status ne_switch_run(ne_ctx* ctx, const ne_md_params* md, double* x_dev, double* v_dev,
+                        const double* x0_dev, int n, const double box[3], double* W_fwd_dev,
+                        double* W_bwd_dev, double* Wcum_fwd_dev, double* Wcum_bwd_dev, double* trace_dev,
+                        int trace_stride, void* stream)
+{
+    if (n < 2 || !box) return NE_EINVAL;
+    int off[2] = {0, n};
+    return switch_run_impl(ctx, md, 1, off, x_dev, v_dev, x0_dev, box, W_fwd_dev, W_bwd_dev, Wcum_fwd_dev,
+                           Wcum_bwd_dev, trace_dev, trace_stride, (cudaStream_t)stream);
+}
+
+ne_status ne_rs_run(ne_ctx* ctx, const ne_md_params* md, double lambda_f, double* x_dev, double* v_dev,
+                    const double* x0_dev, int n, const double box[3], double* Wcum_fwd_dev,
+                    double* Wcum_bwd_dev, void* stream)
+{
+    if (!md) return NE_EINVAL;
+    ne_md_params m = *md;
+    m.path = NE_PATH_RS;
+    m.lambda_f = lambda_f;
+    if (n < 2 || !box) return NE_EINVAL;
+    int off[2] = {0, n};
+    return switch_run_impl(ctx, &m, 1, off, x_dev, v_dev, x0_dev, box, nullptr, nullptr, Wcum_fwd_dev,
+                           Wcum_bwd_dev, nullptr, 0, (cudaStream_t)stream);
+}
+
+ne_status ne_switch_run_batched(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* offsets_host,
+                                double* x_dev, double* v_dev, const double* x0_dev, const double* boxes_host,
+                                double* W_fwd_dev, double* W_bwd_dev, void* stream)
+{
+    return switch_run_impl(ctx, md, n_rep, offsets_host, x_dev, v_dev, x0_dev, boxes_host, W_fwd_dev,
+                           W_bwd_dev, nullptr, nullptr, nullptr, 0, (cudaStream_t)stream);
+}
+
+ne_status ne_profile_segment(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* offsets_host,
+                             double* x_dev, double* v_dev, const double* x0_dev, const double* boxes_host,
+                             double* W_dev, long long step_begin, long long n_steps, double* ms_host,
+                             long long* launches_host, void* stream)
+{
+    if (!ctx || !md || !offsets_host || !x_dev || !v_dev || !x0_dev || !boxes_host || !W_dev || !ms_host ||
+        !launches_host || n_rep < 1 || n_steps < 1 || n_steps > 100000)
+        return NE_EINVAL;
+    if (n_rep > ctx->max_rep) return fail(ctx, NE_ENOMEM, "replica count exceeds the context");
+    ne_status s = check_batch(ctx, md, n_rep, offsets_host);
+    if (s) return s;
+    const long long S_total = 2 * md[0].t_eq + 2 * md[0].t_s;
+    if (step_begin < 0 || step_begin + n_steps > S_total) return fail(ctx, NE_EINVAL, "step range outside the schedule");
+    cudaStream_t st = (cudaStream_t)stream;
+    RunArgs a{};
+    a.x = x_dev;
+    a.v = v_dev;
+    a.x0 = x0_dev;
+    a.W = W_dev;
+    DevBatch B;
+    s = setup_batch(ctx, n_rep, offsets_host, boxes_host, md, 1, -1.0, B, a, st);
+    if (s) return s;
+    Sched S = make_sched(md[0]);
+    s = profile_steps(ctx, B, S, md[0].prec == NE_MIXED, step_begin, n_steps, ms_host, launches_host, st);
+    if (s) return s;
+    return finish(ctx, st);
+}
+
+ne_status ne_msd_fit(ne_ctx* ctx, const ne_md_params* md, double* x_dev, double* v_dev, const double* x0_dev,
+                     int n, const double box[3], long long n_eq, long long n_samples, int stride,
+                     double* msd_host, double* k_host, void* stream)
+{
+    if (!ctx || !x_dev || !v_dev || !x0_dev || !box || n < 2 || n_eq < 0 || n_samples < 1 || stride < 1)
+        return NE_EINVAL;
+    ne_status s = check_md(ctx, md);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int off[2] = {0, n};
+    RunArgs a{};
+    a.x = x_dev;
+    a.v = v_dev;
+    a.x0 = x0_dev;
+    a.W = ctx->W;
+    DevBatch B;
+    s = setup_batch(ctx, 1, off, box, md, 0, -1.0, B, a, st);
+    if (s) return s;
+    Sched S = make_sched(*md);
+    S.kind = SCHED_FIXED;
+    S.path = NE_PATH_FL;
+    S.lam_a = S.lam_b = 0.0;
+    S.s0 = -1;
+    S.stream = STREAM_MSD;
+    double* acc = ctx->scratch;
+    NE_CU(cudaMemsetAsync(acc, 0, sizeof(double), st));
+    s = run_steps(ctx, B, S, md->prec == NE_MIXED, 0, n_eq + n_samples * stride, st, acc, n_eq, stride);
+    if (s) return s;
+    double sum = 0.0;
+    NE_CU(cudaMemcpyAsync(&sum, acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+    s = finish(ctx, st);
+    if (s) return s;
+    const double msd = sum / (double)n_samples;
+    if (msd_host) *msd_host = msd;
+    if (k_host) *k_host = 3.0 * kB * md->T / msd;
+    return NE_OK;
+}
+
+// ------------------------------------------------------------ assembly
+ne_status ne_free_energy(int n, double V, double T, double mass, double k, const double* W_fwd,
+                         const double* W_bwd, int n_seeds, double* F_per_atom, double* stderr_per_atom,
+                         double* Ediss_per_atom)
+{
+    if (n < 1 || n_seeds < 1 || !W_fwd || !W_bwd || !(V > 0) || !(T > 0) || !(mass > 0) || !(k > 0))
+        return NE_EINVAL;
+    double wf = 0, wb = 0;
+    for (int q = 0; q < n_seeds; ++q) {
+        wf += W_fwd[q];
+        wb += W_bwd[q];
+    }
+    wf /= n_seeds;
+    wb /= n_seeds;
+    const double kT = kB * T, w = std::sqrt(k / mass);
+    const double FE = 3.0 * n * kT * std::log(HBAR * w / kT);            // Einstein crystal
+    const double dcm = kT * std::log(n / V * std::pow(2.0 * PI * kT / (n * k), 1.5));  // eq. cm
+    if (F_per_atom) *F_per_atom = (FE + 0.5 * (wf - wb) + dcm) / n;
+    if (stderr_per_atom) {
+        double se = 0.0;
+        if (n_seeds > 1) {
+            double m = 0.5 * (wf - wb) / n, ss = 0.0;
+            for (int q = 0; q < n_seeds; ++q) {
+                double d = 0.5 * (W_fwd[q] - W_bwd[q]) / n - m;
+                ss += d * d;
+            }
+            se = std::sqrt(ss / (n_seeds - 1) / n_seeds);
+        }
+        *stderr_per_atom = se;
+    }
+    if (Ediss_per_atom) *Ediss_per_atom = -0.5 * (wf + wb) / n;
+    return NE_OK;
+}
+
+ne_status ne_rs_free_energy(int n, double T0, double F0_T0, double lambda_f, long long t_s,
+                            const double* Wf, const double* Wb, int n_seeds, const double* T_grid, int n_T,
+                            double* F_per_atom)
+{
+    if (n < 1 || t_s < 1 || n_seeds < 1 || !Wf || !Wb || !T_grid || !F_per_atom || !(lambda_f > 0 && lambda_f < 1))
+        return NE_EINVAL;
+    const size_t m = (size_t)t_s + 1;
+    std::vector<double> cf(m, 0.0), cb(m, 0.0), lf(m), lb(m);
+    for (int q = 0; q < n_seeds; ++q)
+        for (size_t k = 0; k < m; ++k) {
+            cf[k] += Wf[q * m + k] / n_seeds;
+            cb[k] += Wb[q * m + k] / n_seeds;
+        }
+    for (size_t k = 0; k < m; ++k) {
+        lf[k] = ne_lambda_rs(lambda_f, (double)k / t_s);
+        lb[k] = ne_lambda_rs(lambda_f, 1.0 - (double)k / t_s);
+    }
+    for (int g = 0; g < n_T; ++g) {
+        const double l = T0 / T_grid[g];
+        if (l > 1.0 || l < lambda_f) return NE_EINVAL;
+        // forward: lambda falls from 1 to lambda_f; backward rises back
+        size_t kf = 0;
+        while (kf + 1 < m - 1 && lf[kf + 1] > l) ++kf;
+        double af = (l - lf[kf]) / (lf[kf + 1] - lf[kf]);
+        const double w1l = cf[kf] + af * (cf[kf + 1] - cf[kf]);
+        size_t kb = 0;
+        while (kb + 1 < m - 1 && lb[kb + 1] < l) ++kb;
+        double ab = (l - lb[kb]) / (lb[kb + 1] - lb[kb]);
+        const double wl1 = cb[m - 1] - (cb[kb] + ab * (cb[kb + 1] - cb[kb]));
+        const double F = F0_T0 / l + 1.5 * n * kB * T0 * std::log(l) / l + (w1l - wl1) / (2.0 * l);
+        F_per_atom[g] = F / n;
+    }
+    return NE_OK;
+}
+
+}  // extern "C"
+
+// dU/dx = -F scaled by the upstream gradient (used by ne_eam_backward).
+__global__ void k_scale(double* p, int n, double s)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) p[q] *= s;
+}
+
+namespace ne {
+void launch_scale(double* p, int n, double s, cudaStream_t st) { k_scale<<<64, 256, 0, st>>>(p, n, s); }
+}  // namespace ne

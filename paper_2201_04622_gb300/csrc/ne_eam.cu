@@ -1,0 +1,567 @@
+// ne_eam.cu -- EAM kernels of libne.so: spline tables, pass 1 (density rho_i,
+// embedding F(rho_i), F'(rho_i), per-step short neighbour list), pass 2
+// (pair + embedding forces, pair energy, Langevin noise of the step, and the
+// per-replica totals), and the backward pass for dU/dtheta.
+//
+// EAM energy (Sec. II.B, eq. H with U = EAM):
+//   U = sum_{i<j} phi(r_ij) + sum_i F(rho_i),   rho_i = sum_{j != i} f(r_ij)
+//   F_i = sum_j [phi'(r_ij) + (F'(rho_i) + F'(rho_j)) f'(r_ij)] (r_j - r_i) / r_ij
+// The full neighbour list holds each pair twice, so every atom sums its own
+// rho and force without atomics; the pair energy takes 1/2 per direction.
+//
+// Pair kernels give TPA consecutive lanes to one atom; lane l takes list
+// entries l, l+TPA, ...  The lists are interleaved so that, for a fixed
+// iteration, the lanes of a warp read consecutive words.
+#include "ne_internal.cuh"
+
+namespace {
+
+// ------------------------------------------------------------ tables
+// theta (value y, slope m per knot) -> per-interval cubic in u in [0, 1):
+// p(u) = c0 + c1 u + c2 u^2 + c3 u^3 with c0 = y0, c1 = h m0,
+// c2 = 3 (y1 - y0) - 2 h m0 - h m1, c3 = 2 (y0 - y1) + h m0 + h m1 -- the
+// cubic Hermite interpolant written in the power basis.
+__global__ void k_tables(const double* __restrict__ theta, int nk, double r_c, double rho_max,
+                         float4* pf32, ned4* pf64, float4* F32, ned4* F64)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nk - 1) return;
+    for (int fn = 0; fn < 3; ++fn) {
+        double h = (fn == 2 ? rho_max : r_c) / (nk - 1);
+        const double* t = theta + (size_t)fn * nk * 2;
+        double y0 = t[2 * k], m0 = t[2 * k + 1], y1 = t[2 * k + 2], m1 = t[2 * k + 3];
+        ned4 c;
+        c.x = y0;
+        c.y = h * m0;
+        c.z = 3.0 * (y1 - y0) - 2.0 * h * m0 - h * m1;
+        c.w = 2.0 * (y0 - y1) + h * m0 + h * m1;
+        float4 cf = make_float4((float)c.x, (float)c.y, (float)c.z, (float)c.w);
+        if (fn < 2) {
+            pf64[2 * k + fn] = c;
+            pf32[2 * k + fn] = cf;
+        } else {
+            F64[k] = c;
+            F32[k] = cf;
+        }
+    }
+}
+
+template <typename T>
+struct V3 {
+    T x, y, z;
+};
+
+// Position of atom i for the pair kernels: the wrapped FP32 copy (mixed) or
+// the unwrapped FP64 state (FP64 path).
+template <bool MIXED>
+struct Pos;
+template <>
+struct Pos<true> {
+    using R = float;
+    static __device__ __forceinline__ V3<float> load(const DevBatch& B, int i)
+    {
+        float4 p = B.pos32[i];
+        return {p.x, p.y, p.z};
+    }
+};
+template <>
+struct Pos<false> {
+    using R = double;
+    static __device__ __forceinline__ V3<double> load(const DevBatch& B, int i)
+    {
+        return {B.x[3 * i], B.x[3 * i + 1], B.x[3 * i + 2]};
+    }
+};
+
+__device__ __forceinline__ float mi(float d, float L, float invL) { return d - L * rintf(d * invL); }
+__device__ __forceinline__ double mi(double d, double L, double invL) { return d - L * rint(d * invL); }
+
+template <typename R>
+__device__ __forceinline__ R lane_sum(R v, int tpa)
+{
+    for (int o = tpa >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------ pass 1
+template <bool MIXED, int TPA>
+__global__ void __launch_bounds__(NE_TILE* TPA) k_density(DevBatch B)
+{
+    using R = typename Pos<MIXED>::R;
+    __shared__ double red[NE_TILE * TPA];
+    const int tile = blockIdx.x;
+    const int rep = B.tile_rep[tile];
+    const RepDev& P = B.rep[rep];
+    const int local = threadIdx.x / TPA, lane = threadIdx.x % TPA;
+    const int a = (tile - P.tile0) * NE_TILE + local;
+    const bool valid = a < P.n;
+    const int i = P.off + (valid ? a : 0);
+    const R L0 = (R)P.L[0], L1 = (R)P.L[1], L2 = (R)P.L[2];
+    const R iL0 = (R)P.invL[0], iL1 = (R)P.invL[1], iL2 = (R)P.invL[2];
+    const R rc2 = MIXED ? (R)B.tab.rc2f : (R)(B.tab.r_c * B.tab.r_c);
+    const R rmin2 = (R)(NE_RMIN * NE_RMIN);
+    const R inv_h = MIXED ? (R)B.tab.inv_h_rf : (R)B.tab.inv_h_r;
+    const int nk = B.tab.nk;
+    const int cap = NE_SMAX / TPA;
+    double rho = 0.0;
+    float chunk = 0.f;
+    int nchunk = 0;
+    int m = 0, bad = 0;
+    if (valid) {
+        const V3<R> pi = Pos<MIXED>::load(B, i);
+        if (!isfinite(pi.x) || !isfinite(pi.y) || !isfinite(pi.z)) bad |= ST_ENAN;
+        const int cnt = min(B.ncnt[i], NE_NMAX);
+        for (int k = lane; k < cnt; k += TPA) {
+            const int jn = B.nbr[ne_nbr_index(k, i, B.n_tot, TPA)];
+            const V3<R> pj = Pos<MIXED>::load(B, jn);
+            R dx = mi(pj.x - pi.x, L0, iL0), dy = mi(pj.y - pi.y, L1, iL1), dz = mi(pj.z - pi.z, L2, iL2);
+            R r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < rc2) {
+                if (r2 < rmin2) bad |= ST_ERANGE;
+                R r = sqrt(r2);
+                R t = r * inv_h;
+                int kk = min(max((int)t, 0), nk - 2);
+                R u = t - (R)kk;
+                R fr;
+                if constexpr (MIXED) {
+                    float4 c = __ldg(&B.tab.pf32[2 * kk + 1]);
+                    fr = (R)(c.x + (float)u * (c.y + (float)u * (c.z + (float)u * c.w)));
+                    chunk += (float)fr;
+                    if (++nchunk == 8) {
+                        rho += (double)chunk;
+                        chunk = 0.f;
+                        nchunk = 0;
+                    }
+                } else {
+                    ned4 c = B.tab.pf64[2 * kk + 1];
+                    fr = (R)(c.x + (double)u * (c.y + (double)u * (c.z + (double)u * c.w)));
+                    rho += (double)fr;
+                }
+                if (m < cap)
+                    B.sl[(m * B.n_tot + i) * TPA + lane] = jn;
+                else
+                    bad |= ST_ENEIGH;
+                ++m;
+            }
+        }
+        rho += (double)chunk;
+        B.scnt[i * TPA + lane] = min(m, cap);
+    }
+    rho = lane_sum(rho, TPA);
+    double Femb = 0.0;
+    if (valid && lane == 0) {
+        if (!(rho < B.tab.rho_max)) bad |= ST_ERANGE;
+        double t = rho * B.tab.inv_h_rho;
+        int kk = min(max((int)t, 0), nk - 2);
+        double dF;
+        if constexpr (MIXED) {
+            float u = (float)(t - kk);
+            float4 c = __ldg(&B.tab.F32[kk]);
+            Femb = (double)(c.x + u * (c.y + u * (c.z + u * c.w)));
+            dF = (double)((c.y + u * (2.f * c.z + 3.f * u * c.w)) * (float)B.tab.inv_h_rho);
+            float4 p = B.pos32[i];
+            B.posF[i] = make_float4(p.x, p.y, p.z, (float)dF);
+        } else {
+            double u = t - kk;
+            ned4 c = B.tab.F64[kk];
+            Femb = c.x + u * (c.y + u * (c.z + u * c.w));
+            dF = (c.y + u * (2.0 * c.z + 3.0 * u * c.w)) * B.tab.inv_h_rho;
+            B.dF64[i] = dF;
+        }
+        if (B.rho) B.rho[i] = rho;
+        if (!isfinite(Femb)) bad |= ST_ENAN;
+    }
+    if (bad) ne_set_status(B.status, bad);
+    red[threadIdx.x] = Femb;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) B.partA[(size_t)tile * NPA + PA_UEMB] = red[0];
+}
+
+// ------------------------------------------------------------ pass 2
+template <bool MIXED, int TPA>
+__global__ void __launch_bounds__(NE_TILE* TPA)
+    k_force(DevBatch B, Sched S, const long long* __restrict__ step_base, int j, int want_noise)
+{
+    using R = typename Pos<MIXED>::R;
+    __shared__ double red[7][NE_TILE * TPA];
+    __shared__ int s_last;
+    const int tile = blockIdx.x;
+    const int rep = B.tile_rep[tile];
+    const RepDev& P = B.rep[rep];
+    const int local = threadIdx.x / TPA, lane = threadIdx.x % TPA;
+    const int a = (tile - P.tile0) * NE_TILE + local;
+    const bool valid = a < P.n;
+    const int i = P.off + (valid ? a : 0);
+    const R L0 = (R)P.L[0], L1 = (R)P.L[1], L2 = (R)P.L[2];
+    const R iL0 = (R)P.invL[0], iL1 = (R)P.invL[1], iL2 = (R)P.invL[2];
+    const R inv_h = MIXED ? (R)B.tab.inv_h_rf : (R)B.tab.inv_h_r;
+    const int nk = B.tab.nk;
+    R fx = 0, fy = 0, fz = 0, ep = 0;
+    if (valid) {
+        V3<R> pi;
+        R dFi;
+        if constexpr (MIXED) {
+            float4 p = B.posF[i];
+            pi.x = (R)p.x;
+            pi.y = (R)p.y;
+            pi.z = (R)p.z;
+            dFi = (R)p.w;
+        } else {
+            pi = Pos<false>::load(B, i);
+            dFi = (R)B.dF64[i];
+        }
+        const int m = B.scnt[i * TPA + lane];
+        for (int q = 0; q < m; ++q) {
+            const int jn = B.sl[(q * B.n_tot + i) * TPA + lane];
+            V3<R> pj;
+            R dFj;
+            if constexpr (MIXED) {
+                float4 p = B.posF[jn];
+                pj.x = (R)p.x;
+                pj.y = (R)p.y;
+                pj.z = (R)p.z;
+                dFj = (R)p.w;
+            } else {
+                pj = Pos<false>::load(B, jn);
+                dFj = (R)B.dF64[jn];
+            }
+            R dx = mi(pj.x - pi.x, L0, iL0), dy = mi(pj.y - pi.y, L1, iL1), dz = mi(pj.z - pi.z, L2, iL2);
+            R r2 = dx * dx + dy * dy + dz * dz;
+            R r = sqrt(r2);
+            R ir = (R)1 / r;
+            R t = r * inv_h;
+            int kk = min(max((int)t, 0), nk - 2);
+            R u = t - (R)kk;
+            R phi, dphi, df;
+            if constexpr (MIXED) {
+                float4 c = __ldg(&B.tab.pf32[2 * kk]);
+                float4 g = __ldg(&B.tab.pf32[2 * kk + 1]);
+                float uf = (float)u;
+                phi = c.x + uf * (c.y + uf * (c.z + uf * c.w));
+                dphi = (c.y + uf * (2.f * c.z + 3.f * uf * c.w)) * (float)inv_h;
+                df = (g.y + uf * (2.f * g.z + 3.f * uf * g.w)) * (float)inv_h;
+            } else {
+                ned4 c = B.tab.pf64[2 * kk];
+                ned4 g = B.tab.pf64[2 * kk + 1];
+                phi = c.x + u * (c.y + u * (c.z + u * c.w));
+                dphi = (c.y + u * (2.0 * c.z + 3.0 * u * c.w)) * inv_h;
+                df = (g.y + u * (2.0 * g.z + 3.0 * u * g.w)) * inv_h;
+            }
+            R s = (dphi + (dFi + dFj) * df) * ir;
+            fx += s * dx;
+            fy += s * dy;
+            fz += s * dz;
+            ep += (R)0.5 * phi;
+        }
+    }
+    fx = lane_sum(fx, TPA);
+    fy = lane_sum(fy, TPA);
+    fz = lane_sum(fz, TPA);
+    double epd = lane_sum((double)ep, TPA);
+    double v[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (valid && lane == 0) {
+        if constexpr (MIXED) {
+            B.f32[i] = make_float4((float)fx, (float)fy, (float)fz, 0.f);
+        } else {
+            B.f64[3 * i] = (double)fx;
+            B.f64[3 * i + 1] = (double)fy;
+            B.f64[3 * i + 2] = (double)fz;
+        }
+        v[0] = epd;
+        v[1] = (double)fx;
+        v[2] = (double)fy;
+        v[3] = (double)fz;
+        if (want_noise) {
+            const long long s = *step_base + j;
+            uint4 w = ne_philox_block(P.seed, P.replica, (unsigned)S.stream, (unsigned)a,
+                                      (unsigned long long)s);
+            if constexpr (MIXED) {
+                float z[3];
+                ne_normals32(w, z);
+                B.xi32[3 * i] = z[0];
+                B.xi32[3 * i + 1] = z[1];
+                B.xi32[3 * i + 2] = z[2];
+                v[4] = z[0];
+                v[5] = z[1];
+                v[6] = z[2];
+            } else {
+                double z[3];
+                ne_normals64(w, z);
+                B.xi64[3 * i] = z[0];
+                B.xi64[3 * i + 1] = z[1];
+                B.xi64[3 * i + 2] = z[2];
+                v[4] = z[0];
+                v[5] = z[1];
+                v[6] = z[2];
+            }
+        }
+    }
+    for (int q = 0; q < 7; ++q) red[q][threadIdx.x] = v[q];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < 7; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double* pa = B.partA + (size_t)tile * NPA;
+        pa[PA_UPAIR] = red[0][0];
+        pa[PA_F0X] = red[1][0];
+        pa[PA_F0Y] = red[2][0];
+        pa[PA_F0Z] = red[3][0];
+        pa[PA_XIX] = red[4][0];
+        pa[PA_XIY] = red[5][0];
+        pa[PA_XIZ] = red[6][0];
+        __threadfence();
+        unsigned prev = atomicAdd(&B.tile_done[rep], 1u);
+        s_last = (prev == (unsigned)P.ntile - 1u);
+    }
+    __syncthreads();
+    if (s_last) {
+        // Last tile of this replica: fixed-order sums of every tile partial.
+        __threadfence();
+        for (int q = threadIdx.x; q < NTOT; q += blockDim.x) {
+            double acc = 0.0;
+            for (int t = P.tile0; t < P.tile0 + P.ntile; ++t)
+                acc += q < NPA ? __ldcg(&B.partA[(size_t)t * NPA + q])
+                               : __ldcg(&B.partB[(size_t)t * NPB + (q - NPA)]);
+            B.tot[(size_t)rep * NTOT + q] = acc;
+        }
+        if (threadIdx.x == 0) B.tile_done[rep] = 0u;
+    }
+}
+
+// ------------------------------------------------------------ backward
+// dU/dtheta: U is linear in the phi and F knot parameters; the f knots enter
+// through rho_i, weighted by F'(rho_i).  With the full list each pair is seen
+// from both atoms: phi takes 1/2 per direction, f takes F'(rho_i) from atom
+// i's side only.  Hermite basis on interval k with u in [0, 1) and spacing h:
+// (h00, h h10, h01, h h11) multiply (y_k, m_k, y_{k+1}, m_{k+1}).
+__device__ __forceinline__ void hermite_w(double u, double h, double w[4])
+{
+    double u2 = u * u, u3 = u2 * u;
+    w[0] = 2 * u3 - 3 * u2 + 1;
+    w[1] = (u3 - 2 * u2 + u) * h;
+    w[2] = -2 * u3 + 3 * u2;
+    w[3] = (u3 - u2) * h;
+}
+
+__device__ __forceinline__ void hermite_wf(float u, float h, float w[4])
+{
+    float u2 = u * u, u3 = u2 * u;
+    w[0] = 2 * u3 - 3 * u2 + 1;
+    w[1] = (u3 - 2 * u2 + u) * h;
+    w[2] = -2 * u3 + 3 * u2;
+    w[3] = (u3 - u2) * h;
+}
+
+// Mixed precision: FP32 basis weights accumulated in shared-memory FP32 bins
+// per block, flushed to bins[block][3*nk*2]; k_bins_reduce then sums the
+// blocks in FP64 in fixed order.
+template <int TPA>
+__global__ void __launch_bounds__(NE_TILE* TPA) k_backward_mixed(DevBatch B, float* __restrict__ bins)
+{
+    extern __shared__ float sb[];
+    const int nk = B.tab.nk;
+    const int nb = 3 * nk * 2;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) sb[q] = 0.f;
+    __syncthreads();
+    const float h_r = (float)B.tab.h_r, inv_h = B.tab.inv_h_rf;
+    const float h_rho = (float)B.tab.h_rho;
+    for (int tile = blockIdx.x; tile < B.n_tiles; tile += gridDim.x) {
+        const int rep = B.tile_rep[tile];
+        const RepDev& P = B.rep[rep];
+        const int local = threadIdx.x / TPA, lane = threadIdx.x % TPA;
+        const int a = (tile - P.tile0) * NE_TILE + local;
+        if (a < P.n) {
+            const int i = P.off + a;
+            const float Lf0 = (float)P.L[0], Lf1 = (float)P.L[1], Lf2 = (float)P.L[2];
+            const float iL0 = (float)P.invL[0], iL1 = (float)P.invL[1], iL2 = (float)P.invL[2];
+            float4 pi = B.posF[i];
+            const float dFi = pi.w;
+            const int m = B.scnt[i * TPA + lane];
+            for (int q = 0; q < m; ++q) {
+                const int jn = B.sl[(q * B.n_tot + i) * TPA + lane];
+                float4 pj = B.posF[jn];
+                float dx = mi(pj.x - pi.x, Lf0, iL0), dy = mi(pj.y - pi.y, Lf1, iL1),
+                      dz = mi(pj.z - pi.z, Lf2, iL2);
+                float r = sqrtf(dx * dx + dy * dy + dz * dz);
+                float t = r * inv_h;
+                int kk = min(max((int)t, 0), nk - 2);
+                float w[4];
+                hermite_wf(t - (float)kk, h_r, w);
+                float* bphi = sb + 2 * kk;
+                float* bf = sb + 2 * nk + 2 * kk;
+                for (int c = 0; c < 4; ++c) {
+                    atomicAdd(bphi + c, 0.5f * w[c]);
+                    atomicAdd(bf + c, dFi * w[c]);
+                }
+            }
+            if (lane == 0) {
+                double t = B.rho[i] * B.tab.inv_h_rho;
+                int kk = min(max((int)t, 0), nk - 2);
+                float w[4];
+                hermite_wf((float)(t - kk), h_rho, w);
+                float* bF = sb + 4 * nk + 2 * kk;
+                for (int c = 0; c < 4; ++c) atomicAdd(bF + c, w[c]);
+            }
+        }
+    }
+    __syncthreads();
+    float* out = bins + (size_t)blockIdx.x * nb;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) out[q] = sb[q];
+}
+
+__global__ void k_bins_reduce(const float* __restrict__ bins, int n_blocks, int nb, double gE,
+                              double* __restrict__ gtheta)
+{
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nb) return;
+    double acc = 0.0;
+    for (int b = 0; b < n_blocks; ++b) acc += (double)bins[(size_t)b * nb + q];
+    gtheta[q] = gE * acc;
+}
+
+// FP64 path: FP64 basis weights added straight into gtheta (pre-zeroed) with
+// FP64 atomics, scaled by gE.
+template <int TPA>
+__global__ void __launch_bounds__(NE_TILE* TPA) k_backward_fp64(DevBatch B, double gE, double* gtheta)
+{
+    const int nk = B.tab.nk;
+    const int tile = blockIdx.x;
+    const int rep = B.tile_rep[tile];
+    const RepDev& P = B.rep[rep];
+    const int local = threadIdx.x / TPA, lane = threadIdx.x % TPA;
+    const int a = (tile - P.tile0) * NE_TILE + local;
+    if (a >= P.n) return;
+    const int i = P.off + a;
+    const double dFi = B.dF64[i];
+    const double xi = B.x[3 * i], yi = B.x[3 * i + 1], zi = B.x[3 * i + 2];
+    const int m = B.scnt[i * TPA + lane];
+    for (int q = 0; q < m; ++q) {
+        const int jn = B.sl[(q * B.n_tot + i) * TPA + lane];
+        double dx = mi(B.x[3 * jn] - xi, P.L[0], P.invL[0]);
+        double dy = mi(B.x[3 * jn + 1] - yi, P.L[1], P.invL[1]);
+        double dz = mi(B.x[3 * jn + 2] - zi, P.L[2], P.invL[2]);
+        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        double t = r * B.tab.inv_h_r;
+        int kk = min(max((int)t, 0), nk - 2);
+        double w[4];
+        hermite_w(t - kk, B.tab.h_r, w);
+        for (int c = 0; c < 4; ++c) {
+            atomicAdd(gtheta + 2 * kk + c, gE * 0.5 * w[c]);
+            atomicAdd(gtheta + 2 * nk + 2 * kk + c, gE * dFi * w[c]);
+        }
+    }
+    if (lane == 0) {
+        double t = B.rho[i] * B.tab.inv_h_rho;
+        int kk = min(max((int)t, 0), nk - 2);
+        double w[4];
+        hermite_w(t - kk, B.tab.h_rho, w);
+        for (int c = 0; c < 4; ++c) atomicAdd(gtheta + 4 * nk + 2 * kk + c, gE * w[c]);
+    }
+}
+
+template <bool MIXED>
+void density_tpa(const DevBatch& B, cudaStream_t st)
+{
+    dim3 g(B.n_tiles);
+    switch (B.tpa) {
+    case 1: k_density<MIXED, 1><<<g, NE_TILE * 1, 0, st>>>(B); break;
+    case 2: k_density<MIXED, 2><<<g, NE_TILE * 2, 0, st>>>(B); break;
+    case 4: k_density<MIXED, 4><<<g, NE_TILE * 4, 0, st>>>(B); break;
+    default: k_density<MIXED, 8><<<g, NE_TILE * 8, 0, st>>>(B); break;
+    }
+}
+
+template <bool MIXED>
+void force_tpa(const DevBatch& B, const Sched& S, const long long* sb, int j, int wn,
+               cudaStream_t st)
+{
+    dim3 g(B.n_tiles);
+    switch (B.tpa) {
+    case 1: k_force<MIXED, 1><<<g, NE_TILE * 1, 0, st>>>(B, S, sb, j, wn); break;
+    case 2: k_force<MIXED, 2><<<g, NE_TILE * 2, 0, st>>>(B, S, sb, j, wn); break;
+    case 4: k_force<MIXED, 4><<<g, NE_TILE * 4, 0, st>>>(B, S, sb, j, wn); break;
+    default: k_force<MIXED, 8><<<g, NE_TILE * 8, 0, st>>>(B, S, sb, j, wn); break;
+    }
+}
+
+}  // namespace
+
+namespace ne {
+
+void launch_tables(const double* theta, int nk, double r_c, double rho_max, float4* pf32,
+                   ned4* pf64, float4* F32, ned4* F64, cudaStream_t st)
+{
+    int n = nk - 1;
+    k_tables<<<(n + 255) / 256, 256, 0, st>>>(theta, nk, r_c, rho_max, pf32, pf64, F32, F64);
+}
+
+void launch_density(const DevBatch& B, bool mixed, const long long*, int, cudaStream_t st)
+{
+    if (mixed)
+        density_tpa<true>(B, st);
+    else
+        density_tpa<false>(B, st);
+}
+
+void launch_force(const DevBatch& B, const Sched& S, bool mixed, const long long* step_base, int j,
+                  int want_noise, cudaStream_t st)
+{
+    if (mixed)
+        force_tpa<true>(B, S, step_base, j, want_noise, st);
+    else
+        force_tpa<false>(B, S, step_base, j, want_noise, st);
+}
+
+int backward_bin_blocks(const DevBatch& B)
+{
+    int nb = B.n_tiles < 296 ? B.n_tiles : 296;
+    return nb < 1 ? 1 : nb;
+}
+
+void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, double* gtheta,
+                     float* bins, int n_bin_blocks, cudaStream_t st)
+{
+    (void)gx;
+    const int nk = B.tab.nk;
+    const int nb = 3 * nk * 2;
+    if (mixed) {
+        size_t smem = (size_t)nb * sizeof(float);
+        switch (B.tpa) {
+        case 1:
+            cudaFuncSetAttribute(k_backward_mixed<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_backward_mixed<1><<<n_bin_blocks, NE_TILE * 1, smem, st>>>(B, bins);
+            break;
+        case 2:
+            cudaFuncSetAttribute(k_backward_mixed<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_backward_mixed<2><<<n_bin_blocks, NE_TILE * 2, smem, st>>>(B, bins);
+            break;
+        case 4:
+            cudaFuncSetAttribute(k_backward_mixed<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_backward_mixed<4><<<n_bin_blocks, NE_TILE * 4, smem, st>>>(B, bins);
+            break;
+        default:
+            cudaFuncSetAttribute(k_backward_mixed<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_backward_mixed<8><<<n_bin_blocks, NE_TILE * 8, smem, st>>>(B, bins);
+            break;
+        }
+        k_bins_reduce<<<(nb + 255) / 256, 256, 0, st>>>(bins, n_bin_blocks, nb, gE, gtheta);
+    } else {
+        cudaMemsetAsync(gtheta, 0, sizeof(double) * nb, st);
+        dim3 g(B.n_tiles);
+        switch (B.tpa) {
+        case 1: k_backward_fp64<1><<<g, NE_TILE * 1, 0, st>>>(B, gE, gtheta); break;
+        case 2: k_backward_fp64<2><<<g, NE_TILE * 2, 0, st>>>(B, gE, gtheta); break;
+        case 4: k_backward_fp64<4><<<g, NE_TILE * 4, 0, st>>>(B, gE, gtheta); break;
+        default: k_backward_fp64<8><<<g, NE_TILE * 8, 0, st>>>(B, gE, gtheta); break;
+        }
+    }
+}
+
+}  // namespace ne

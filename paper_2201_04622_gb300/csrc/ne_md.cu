@@ -1,0 +1,510 @@
+// ne_md.cu -- dynamics kernels of libne.so: neighbour-list build, the fused
+// lambda-blend + Einstein spring + work increment + BAOAB Langevin step,
+// Maxwell-Boltzmann initial velocities, the spring energy, and small
+// reductions (msd samples, exported energies/forces).
+#include "ne_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ double wrap(double x, double L, double invL) { return x - L * floor(x * invL); }
+
+// ------------------------------------------------------------ neighbours
+// One block per replica whose rebuild flag is set (or all, when forced):
+//   1. bin atoms into cells of edge >= r_c + skin (wrapped positions);
+//   2. counting sort by cell (count, exclusive scan, scatter), then an
+//      insertion sort inside each cell so the order does not depend on
+//      the order of the atomics;
+//   3. full list of every atom within r_c + skin, minimum image, over the
+//      27 surrounding cells (all pairs when the box holds < 3 cells/axis).
+// The wrapped positions at the build are kept for the displacement check.
+__global__ void __launch_bounds__(512) k_nl_build(DevBatch B, int force, int from_sites)
+{
+    const int rep = blockIdx.x;
+    const RepDev& P = B.rep[rep];
+    if (!force && B.flags[rep] == 0) return;
+    const int n = P.n, off = P.off, tid = threadIdx.x, bs = blockDim.x;
+    const int tpa = B.tpa;
+    // reference positions of the list: the lattice sites at the start of a
+    // run (the list then depends on the sites only), the current positions
+    // when an atom has strayed more than skin/2 from its reference
+    const double* X = from_sites ? B.x0 : B.x;
+    for (int a = tid; a < n; a += bs) {
+        const int i = off + a;
+        B.pbuild[i] = make_float4((float)wrap(X[3 * i], P.L[0], P.invL[0]),
+                                  (float)wrap(X[3 * i + 1], P.L[1], P.invL[1]),
+                                  (float)wrap(X[3 * i + 2], P.L[2], P.invL[2]), 0.f);
+    }
+    int bad = 0;
+    if (P.nc[0] == 0) {
+        for (int a = tid; a < n; a += bs) {
+            const int i = off + a;
+            const double xi = X[3 * i], yi = X[3 * i + 1], zi = X[3 * i + 2];
+            int cnt = 0;
+            for (int b = 0; b < n; ++b) {
+                if (b == a) continue;
+                const int j = off + b;
+                double dx = X[3 * j] - xi, dy = X[3 * j + 1] - yi, dz = X[3 * j + 2] - zi;
+                dx -= P.L[0] * rint(dx * P.invL[0]);
+                dy -= P.L[1] * rint(dy * P.invL[1]);
+                dz -= P.L[2] * rint(dz * P.invL[2]);
+                if (dx * dx + dy * dy + dz * dz < P.rlist2) {
+                    if (cnt < NE_NMAX) B.nbr[ne_nbr_index(cnt, i, B.n_tot, tpa)] = j;
+                    ++cnt;
+                }
+            }
+            if (cnt > NE_NMAX) bad |= ST_ENEIGH;
+            B.ncnt[i] = min(cnt, NE_NMAX);
+        }
+    } else {
+        const int nc0 = P.nc[0], nc1 = P.nc[1], nc2 = P.nc[2];
+        const int ncell = nc0 * nc1 * nc2;
+        int* start = B.cstart + P.cell_off + rep;  // ncell + 1 entries
+        int* fill = B.cfill + P.cell_off;
+        for (int c = tid; c <= ncell; c += bs) start[c] = 0;
+        for (int c = tid; c < ncell; c += bs) fill[c] = 0;
+        __syncthreads();
+        for (int a = tid; a < n; a += bs) {
+            const int i = off + a;
+            int c3[3];
+            for (int d = 0; d < 3; ++d) {
+                double s = wrap(X[3 * i + d], P.L[d], P.invL[d]);
+                int q = (int)(s * P.invL[d] * P.nc[d]);
+                c3[d] = min(max(q, 0), P.nc[d] - 1);
+            }
+            const int c = (c3[0] * nc1 + c3[1]) * nc2 + c3[2];
+            B.cellof[i] = c;
+            atomicAdd(&start[c + 1], 1);
+        }
+        __syncthreads();
+        if (tid == 0)
+            for (int c = 0; c < ncell; ++c) start[c + 1] += start[c];
+        __syncthreads();
+        for (int a = tid; a < n; a += bs) {
+            const int c = B.cellof[off + a];
+            const int pos = atomicAdd(&fill[c], 1);
+            B.sorted[off + start[c] + pos] = a;
+        }
+        __syncthreads();
+        for (int c = tid; c < ncell; c += bs) {
+            int* sl = B.sorted + off + start[c];
+            const int len = start[c + 1] - start[c];
+            for (int p = 1; p < len; ++p) {
+                int key = sl[p], q = p - 1;
+                while (q >= 0 && sl[q] > key) {
+                    sl[q + 1] = sl[q];
+                    --q;
+                }
+                sl[q + 1] = key;
+            }
+        }
+        __syncthreads();
+        for (int a = tid; a < n; a += bs) {
+            const int i = off + a;
+            const int c = B.cellof[i];
+            const int cx = c / (nc1 * nc2), cy = (c / nc2) % nc1, cz = c % nc2;
+            const double xi = X[3 * i], yi = X[3 * i + 1], zi = X[3 * i + 2];
+            int cnt = 0;
+            for (int dx = -1; dx <= 1; ++dx)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dz = -1; dz <= 1; ++dz) {
+                        const int ox = (cx + dx + nc0) % nc0, oy = (cy + dy + nc1) % nc1,
+                                  oz = (cz + dz + nc2) % nc2;
+                        const int o = (ox * nc1 + oy) * nc2 + oz;
+                        for (int p = start[o]; p < start[o + 1]; ++p) {
+                            const int b = B.sorted[off + p];
+                            if (b == a) continue;
+                            const int j = off + b;
+                            double ex = X[3 * j] - xi, ey = X[3 * j + 1] - yi, ez = X[3 * j + 2] - zi;
+                            ex -= P.L[0] * rint(ex * P.invL[0]);
+                            ey -= P.L[1] * rint(ey * P.invL[1]);
+                            ez -= P.L[2] * rint(ez * P.invL[2]);
+                            if (ex * ex + ey * ey + ez * ez < P.rlist2) {
+                                if (cnt < NE_NMAX) B.nbr[ne_nbr_index(cnt, i, B.n_tot, tpa)] = j;
+                                ++cnt;
+                            }
+                        }
+                    }
+            if (cnt > NE_NMAX) bad |= ST_ENEIGH;
+            B.ncnt[i] = min(cnt, NE_NMAX);
+        }
+    }
+    if (bad) ne_set_status(B.status, bad);
+    __syncthreads();
+    if (tid == 0) B.flags[rep] = 0;
+}
+
+// ------------------------------------------------------------ fused step
+// Total force of H(lambda) on atom i from the EAM force F0, the spring force
+// F_E = -k u and, with the centre of mass fixed, their replica means:
+//   Frenkel-Ladd (eq. interp): (1 - lambda) F0 + lambda F_E
+//   reversible scaling (eq. H_rs): lambda F0
+__device__ __forceinline__ double blend(int path, double lam, double F0, double FE)
+{
+    return path == 0 ? (1.0 - lam) * F0 + lam * FE : lam * F0;
+}
+
+// One thread per atom.  With s the global step and Lambda(s) the schedule:
+//   do_close: v += dt/2m F(x_s; Lambda(s))      (second half kick of step s-1)
+//   do_open:  W += (Lambda(s+1) - Lambda(s)) dH/dlambda(x_s)   (first thread
+//             of the replica; the discrete work sum of Sec. II.A)
+//             v += dt/2m F(x_s; Lambda(s+1));  x += dt/2 v;
+//             v = c1 v + c2 (xi - mean xi);    x += dt/2 v
+// then the tile partials at the resulting x (U_E, sum u, sum |u|^2) and the
+// kinetic energy of the completed velocity v_s, the FP32 wrapped copy of x
+// and the displacement check against the list-build positions.
+template <bool MIXED>
+__global__ void __launch_bounds__(NE_TILE)
+    k_step(DevBatch B, Sched S, const long long* __restrict__ step_base, int j, int do_close, int do_open)
+{
+    __shared__ double red[NPB][NE_TILE];
+    const int tile = blockIdx.x;
+    const int rep = B.tile_rep[tile];
+    const RepDev& P = B.rep[rep];
+    const int a = (tile - P.tile0) * NE_TILE + threadIdx.x;
+    const bool valid = a < P.n;
+    const int i = P.off + (valid ? a : 0);
+    const long long s = *step_base + j;
+    const double* T = B.tot + (size_t)rep * NTOT;
+    const double lam_s = ne_sched_lambda(S, s);
+    const double lam_n = ne_sched_lambda(S, s + 1);
+    const double invN = 1.0 / P.n;
+    double part[NPB] = {0, 0, 0, 0, 0, 0};
+    int bad = 0;
+    if (valid) {
+        double x[3], v[3], u[3], F0[3], mF0[3], mFE[3];
+        for (int c = 0; c < 3; ++c) {
+            x[c] = B.x[3 * i + c];
+            v[c] = B.v[3 * i + c];
+            u[c] = x[c] - B.x0[3 * i + c];
+        }
+        if constexpr (MIXED) {
+            float4 f = B.f32[i];
+            F0[0] = f.x;
+            F0[1] = f.y;
+            F0[2] = f.z;
+        } else {
+            F0[0] = B.f64[3 * i];
+            F0[1] = B.f64[3 * i + 1];
+            F0[2] = B.f64[3 * i + 2];
+        }
+        for (int c = 0; c < 3; ++c) {
+            mF0[c] = S.fix_cm ? T[TOT_F0X + c] * invN : 0.0;
+            mFE[c] = S.fix_cm ? -P.k * T[TOT_UX + c] * invN : 0.0;
+        }
+        if (do_close) {
+            for (int c = 0; c < 3; ++c)
+                v[c] += P.hdt_m * blend(S.path, lam_s, F0[c] - mF0[c], -P.k * u[c] - mFE[c]);
+        }
+        part[PB_KE] = 0.5 * P.m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (do_open) {
+            double xi[3];
+            for (int c = 0; c < 3; ++c) {
+                xi[c] = MIXED ? (double)B.xi32[3 * i + c] : B.xi64[3 * i + c];
+                if (S.fix_cm) xi[c] -= T[TOT_XIX + c] * invN;
+            }
+            for (int c = 0; c < 3; ++c) {
+                v[c] += P.hdt_m * blend(S.path, lam_n, F0[c] - mF0[c], -P.k * u[c] - mFE[c]);
+                x[c] += 0.5 * S.dt * v[c];
+                v[c] = P.c1 * v[c] + P.c2 * xi[c];
+                x[c] += 0.5 * S.dt * v[c];
+                u[c] = x[c] - B.x0[3 * i + c];
+            }
+        }
+        for (int c = 0; c < 3; ++c) {
+            if (!isfinite(x[c]) || !isfinite(v[c])) bad |= ST_ENAN;
+            B.x[3 * i + c] = x[c];
+            B.v[3 * i + c] = v[c];
+            part[PB_UX + c] = u[c];
+        }
+        part[PB_U2] = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        part[PB_UE] = 0.5 * P.k * part[PB_U2];
+        // FP32 wrapped copy and displacement since the list build
+        float w[3];
+        for (int c = 0; c < 3; ++c) w[c] = (float)wrap(x[c], P.L[c], P.invL[c]);
+        if constexpr (MIXED) B.pos32[i] = make_float4(w[0], w[1], w[2], 0.f);
+        float4 pb = B.pbuild[i];
+        float d0 = w[0] - pb.x, d1 = w[1] - pb.y, d2 = w[2] - pb.z;
+        const float L0 = (float)P.L[0], L1 = (float)P.L[1], L2 = (float)P.L[2];
+        d0 -= L0 * rintf(d0 / L0);
+        d1 -= L1 * rintf(d1 / L1);
+        d2 -= L2 * rintf(d2 / L2);
+        if (d0 * d0 + d1 * d1 + d2 * d2 > P.half_skin2) B.flags[rep] = 1;
+    }
+    if (bad) ne_set_status(B.status, bad);
+    if (do_open && valid && a == 0) {
+        const double U0 = T[TOT_UEMB] + T[TOT_UPAIR];
+        const double g = S.path == 0 ? U0 - T[TOT_UE] : U0;
+        const double dW = (lam_n - lam_s) * g;
+        int slot = -1;
+        long long k = 0;
+        if (S.kind == SCHED_FIXED) {
+            slot = 0;
+        } else if (s >= S.t_eq && s < S.t_eq + S.t_s) {
+            slot = 0;
+            k = s - S.t_eq;
+        } else if (s >= 2 * S.t_eq + S.t_s && s < 2 * S.t_eq + 2 * S.t_s) {
+            slot = 1;
+            k = s - (2 * S.t_eq + S.t_s);
+        }
+        if (slot >= 0) {
+            double* W = B.W + (S.kind == SCHED_FIXED ? rep : 2 * rep + slot);
+            *W += dW;
+            if (B.Wcum && S.kind == SCHED_SWITCH) {
+                double* wc = B.Wcum + ((size_t)(2 * rep + slot)) * (S.t_s + 1);
+                if (k == 0) wc[0] = 0.0;
+                wc[k + 1] = *W;
+            }
+        }
+        if (B.trace && s % B.trace_stride == 0 && s / B.trace_stride < B.trace_rows) {
+            double* row = B.trace + 8 * (s / B.trace_stride);
+            row[0] = (double)s;
+            row[1] = lam_s;
+            row[2] = g;
+            row[3] = U0;
+            row[4] = T[TOT_UE];
+            row[6] = B.W[2 * rep];
+            row[7] = B.W[2 * rep + 1];
+            if (slot == 0) row[6] -= dW;
+            if (slot == 1) row[7] -= dW;
+        }
+    }
+    for (int q = 0; q < NPB; ++q) red[q][threadIdx.x] = part[q];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < NPB; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double* pb = B.partB + (size_t)tile * NPB;
+        for (int q = 0; q < NPB; ++q) pb[q] = red[q][0];
+    }
+}
+
+// Trace temperature column: KE of v_s (tile partials of the step kernel of
+// step s) summed in fixed order after that kernel.
+__global__ void k_trace_T(DevBatch B, const long long* __restrict__ step_base, int j)
+{
+    const long long s = *step_base + j;
+    if (!B.trace || s % B.trace_stride != 0 || s / B.trace_stride >= B.trace_rows) return;
+    const RepDev& P = B.rep[0];
+    double ke = 0.0;
+    for (int t = P.tile0; t < P.tile0 + P.ntile; ++t) ke += B.partB[(size_t)t * NPB + PB_KE];
+    const double kB = 8.617333262e-5;
+    B.trace[8 * (s / B.trace_stride) + 5] = 2.0 * ke / (P.dof * kB);
+}
+
+__global__ void k_advance(long long* step_base, long long by) { *step_base += by; }
+
+__global__ void k_noise(unsigned long long seed, unsigned replica, int stream, long long step, int n,
+                        int mixed, double* z)
+{
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+        uint4 w = ne_philox_block(seed, replica, (unsigned)stream, (unsigned)a, (unsigned long long)step);
+        if (mixed) {
+            float f[3];
+            ne_normals32(w, f);
+            for (int c = 0; c < 3; ++c) z[3 * a + c] = f[c];
+        } else {
+            double d[3];
+            ne_normals64(w, d);
+            for (int c = 0; c < 3; ++c) z[3 * a + c] = d[c];
+        }
+    }
+}
+
+// FP32 copy of the positions wrapped into the box (pass-1/2 input of the
+// mixed path when no step kernel has produced it).
+__global__ void k_wrap32(DevBatch B)
+{
+    const int tile = blockIdx.x;
+    const RepDev& P = B.rep[B.tile_rep[tile]];
+    const int a = (tile - P.tile0) * NE_TILE + threadIdx.x;
+    if (a >= P.n) return;
+    const int i = P.off + a;
+    B.pos32[i] = make_float4((float)wrap(B.x[3 * i], P.L[0], P.invL[0]),
+                             (float)wrap(B.x[3 * i + 1], P.L[1], P.invL[1]),
+                             (float)wrap(B.x[3 * i + 2], P.L[2], P.invL[2]), 0.f);
+}
+
+// ------------------------------------------------------------ velocities
+// Philox normals (stream 1, step 0) times sqrt(kT/m); mean removed when the
+// centre of mass is fixed; rescaled to exactly T over the free dof.
+__global__ void __launch_bounds__(256) k_init_v(DevBatch B, int fix_cm)
+{
+    __shared__ double red[4][256];
+    const int rep = blockIdx.x;
+    const RepDev& P = B.rep[rep];
+    const double sd = sqrt(P.kT / P.m);
+    double sum[4] = {0, 0, 0, 0};
+    for (int a = threadIdx.x; a < P.n; a += blockDim.x) {
+        double z[3];
+        ne_normals64(ne_philox_block(P.seed, P.replica, STREAM_INITV, (unsigned)a, 0ull), z);
+        for (int c = 0; c < 3; ++c) {
+            B.v[3 * (P.off + a) + c] = sd * z[c];
+            sum[c] += sd * z[c];
+        }
+    }
+    for (int q = 0; q < 3; ++q) red[q][threadIdx.x] = sum[q];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    double mean[3];
+    for (int c = 0; c < 3; ++c) mean[c] = fix_cm ? red[c][0] / P.n : 0.0;
+    __syncthreads();
+    double ke = 0.0;
+    for (int a = threadIdx.x; a < P.n; a += blockDim.x)
+        for (int c = 0; c < 3; ++c) {
+            double* vv = &B.v[3 * (P.off + a) + c];
+            *vv -= mean[c];
+            ke += 0.5 * P.m * (*vv) * (*vv);
+        }
+    red[3][threadIdx.x] = ke;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[3][threadIdx.x] += red[3][threadIdx.x + w];
+        __syncthreads();
+    }
+    const double kB = 8.617333262e-5;
+    const double t_now = 2.0 * red[3][0] / (P.dof * kB);
+    const double sc = sqrt((P.kT / kB) / t_now);
+    for (int a = threadIdx.x; a < P.n; a += blockDim.x)
+        for (int c = 0; c < 3; ++c) B.v[3 * (P.off + a) + c] *= sc;
+}
+
+// ------------------------------------------------------------ spring
+// Einstein crystal (eq. einstein): U_E = sum k/2 |r - r0|^2, F_E = -k (r - r0).
+__global__ void __launch_bounds__(1024) k_spring(const double* __restrict__ x, const double* __restrict__ x0,
+                                                 int n, double k, double* f, double* e)
+{
+    __shared__ double red[1024];
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < 3 * n; q += blockDim.x) {
+        double u = x[q] - x0[q];
+        acc += 0.5 * k * u * u;
+        if (f) f[q] = -k * u;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && e) *e = red[0];
+}
+
+// EAM forces and energy of replica 0 to caller buffers.
+template <bool MIXED>
+__global__ void k_export(DevBatch B, double* f, double* e)
+{
+    const RepDev& P = B.rep[0];
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < P.n; a += gridDim.x * blockDim.x) {
+        const int i = P.off + a;
+        if (f) {
+            if constexpr (MIXED) {
+                float4 g = B.f32[i];
+                f[3 * a] = g.x;
+                f[3 * a + 1] = g.y;
+                f[3 * a + 2] = g.z;
+            } else {
+                f[3 * a] = B.f64[3 * i];
+                f[3 * a + 1] = B.f64[3 * i + 1];
+                f[3 * a + 2] = B.f64[3 * i + 2];
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && e) *e = B.tot[TOT_UEMB] + B.tot[TOT_UPAIR];
+}
+
+// One msd sample per replica from the step-kernel partials:
+// (1/n) sum |u_i - mean u|^2 = (1/n) sum |u|^2 - |mean u|^2.
+__global__ void k_msd_sample(DevBatch B, double* acc)
+{
+    const int rep = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    const RepDev& P = B.rep[rep];
+    double s[4] = {0, 0, 0, 0};
+    for (int t = P.tile0; t < P.tile0 + P.ntile; ++t) {
+        const double* pb = B.partB + (size_t)t * NPB;
+        s[0] += pb[PB_UX];
+        s[1] += pb[PB_UY];
+        s[2] += pb[PB_UZ];
+        s[3] += pb[PB_U2];
+    }
+    const double invN = 1.0 / P.n;
+    acc[rep] += s[3] * invN - (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]) * invN * invN;
+}
+
+}  // namespace
+
+namespace ne {
+
+void launch_nl_build(const DevBatch& B, int force, int from_sites, cudaStream_t st)
+{
+    k_nl_build<<<B.n_rep, 512, 0, st>>>(B, force, from_sites);
+}
+
+void launch_step(const DevBatch& B, const Sched& S, bool mixed, const long long* step_base, int j,
+                 int do_close, int do_open, cudaStream_t st)
+{
+    if (mixed)
+        k_step<true><<<B.n_tiles, NE_TILE, 0, st>>>(B, S, step_base, j, do_close, do_open);
+    else
+        k_step<false><<<B.n_tiles, NE_TILE, 0, st>>>(B, S, step_base, j, do_close, do_open);
+    if (B.trace) k_trace_T<<<1, 1, 0, st>>>(B, step_base, j);
+}
+
+void launch_prep(const DevBatch& B, const Sched& S, bool mixed, const long long* step_base,
+                 cudaStream_t st)
+{
+    if (mixed)
+        k_step<true><<<B.n_tiles, NE_TILE, 0, st>>>(B, S, step_base, 0, 0, 0);
+    else
+        k_step<false><<<B.n_tiles, NE_TILE, 0, st>>>(B, S, step_base, 0, 0, 0);
+}
+
+void launch_wrap32(const DevBatch& B, cudaStream_t st)
+{
+    k_wrap32<<<B.n_tiles, NE_TILE, 0, st>>>(B);
+}
+
+void launch_noise(unsigned long long seed, unsigned replica, int stream, long long step, int n, int mixed,
+                  double* z, cudaStream_t st)
+{
+    k_noise<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, st>>>(seed, replica, stream, step, n,
+                                                                            mixed, z);
+}
+
+void launch_advance(long long* step_base, long long by, cudaStream_t st)
+{
+    k_advance<<<1, 1, 0, st>>>(step_base, by);
+}
+
+void launch_init_velocities(const DevBatch& B, int fix_cm, cudaStream_t st)
+{
+    k_init_v<<<B.n_rep, 256, 0, st>>>(B, fix_cm);
+}
+
+void launch_spring(const double* x, const double* x0, int n, double k, double* f, double* e,
+                   double*, cudaStream_t st)
+{
+    k_spring<<<1, 1024, 0, st>>>(x, x0, n, k, f, e);
+}
+
+void launch_export(const DevBatch& B, bool mixed, double* f_out, double* e_out, cudaStream_t st)
+{
+    if (mixed)
+        k_export<true><<<64, 256, 0, st>>>(B, f_out, e_out);
+    else
+        k_export<false><<<64, 256, 0, st>>>(B, f_out, e_out);
+}
+
+void launch_msd_sample(const DevBatch& B, double* acc, cudaStream_t st)
+{
+    k_msd_sample<<<B.n_rep, 32, 0, st>>>(B, acc);
+}
+
+}  // namespace ne

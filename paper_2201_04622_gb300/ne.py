@@ -1,0 +1,361 @@
+"""Thin Python binding of libne.so (include/ne.h): one function per C entry
+point, same names, argument marshalling only.  Device arrays are torch CUDA
+tensors (float64, contiguous); every computation runs in the library's
+kernels.  There is no CPU fallback: without the built library or a GPU the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+NE_OK, NE_EINVAL, NE_ENOMEM, NE_ECUDA, NE_ERANGE, NE_ENEIGH, NE_ENAN, NE_ETIMEOUT, NE_ENOTIMPL = range(9)
+STATUS = ["NE_OK", "NE_EINVAL", "NE_ENOMEM", "NE_ECUDA", "NE_ERANGE", "NE_ENEIGH", "NE_ENAN",
+          "NE_ETIMEOUT", "NE_ENOTIMPL"]
+NE_FP64, NE_MIXED = 0, 1
+NE_BCC, NE_FCC = 0, 1
+NE_PATH_FL, NE_PATH_RS = 0, 1
+
+# every symbol include/ne.h declares
+SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_set_theta", "ne_ctx_get_theta",
+           "ne_ctx_set_tuning", "ne_last_error", "ne_create_crystal", "ne_eam_energy_forces",
+           "ne_spring_forces", "ne_eam_backward", "ne_noise", "ne_init_velocities", "ne_langevin_step",
+           "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment",
+           "ne_profile_segment",
+           "ne_msd_fit", "ne_free_energy",
+           "ne_rs_free_energy"]
+
+
+class NeError(RuntimeError):
+    def __init__(self, code, what, msg=""):
+        super().__init__("%s: %s%s" % (what, STATUS[code] if 0 <= code < len(STATUS) else code,
+                                        (" (" + msg + ")") if msg else ""))
+        self.code = code
+
+
+class EamParams(C.Structure):
+    _fields_ = [("A", C.c_double), ("alpha", C.c_double), ("beta", C.c_double),
+                ("B", C.c_double), ("r_e", C.c_double), ("r_s", C.c_double),
+                ("r_c", C.c_double), ("rho_max", C.c_double), ("n_knots", C.c_int)]
+
+
+class MdParams(C.Structure):
+    _fields_ = [("dt", C.c_double), ("T", C.c_double), ("damp", C.c_double),
+                ("mass", C.c_double), ("k_spring", C.c_double), ("skin", C.c_double),
+                ("lambda_fn", C.c_int), ("path", C.c_int), ("t_eq", C.c_longlong),
+                ("t_s", C.c_longlong), ("lambda_f", C.c_double), ("seed", C.c_ulonglong),
+                ("replica", C.c_uint), ("fix_cm", C.c_int), ("prec", C.c_int)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libne.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing and not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(path):
+                raise NeError(NE_ECUDA, "load", "libne.so is not built")
+            L = C.CDLL(path)
+            p, i, d, ll = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+            sigs = {
+                "ne_ctx_create": [p, i, i, p],
+                "ne_ctx_destroy": [p],
+                "ne_ctx_set_theta": [p, p, p],
+                "ne_ctx_get_theta": [p, p, p],
+                "ne_ctx_set_tuning": [p, i],
+                "ne_last_error": [p, p, p, i],
+                "ne_create_crystal": [i, d, i, i, i, p, p, p],
+                "ne_eam_energy_forces": [p, i, p, i, p, p, p, p, p],
+                "ne_spring_forces": [p, p, i, d, p, p, p],
+                "ne_eam_backward": [p, i, p, i, p, d, p, p, p],
+                "ne_noise": [C.c_ulonglong, C.c_uint, i, ll, i, i, p, p],
+                "ne_init_velocities": [p, p, i, p, p],
+                "ne_langevin_step": [p, p, p, p, p, i, p, ll, d, d, p, p],
+                "ne_switch_run": [p, p, p, p, p, i, p, p, p, p, p, p, i, p],
+                "ne_rs_run": [p, p, d, p, p, p, i, p, p, p, p],
+                "ne_switch_run_batched": [p, p, i, p, p, p, p, p, p, p, p],
+                "ne_switch_run_segment": [p, p, i, p, p, p, p, p, p, ll, ll, p],
+                "ne_profile_segment": [p, p, i, p, p, p, p, p, p, ll, ll, p, p, p],
+                "ne_msd_fit": [p, p, p, p, p, i, p, ll, ll, i, p, p, p],
+                "ne_free_energy": [i, d, d, d, d, p, p, i, p, p, p],
+                "ne_rs_free_energy": [i, d, d, d, ll, p, p, i, p, i, p],
+            }
+            for name, args in sigs.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------------ helpers
+def _torch():
+    import torch
+    return torch
+
+
+def _dev(t, n=None):
+    """Pointer of a contiguous float64 CUDA tensor (or None)."""
+    if t is None:
+        return None
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise NeError(NE_EINVAL, "argument", "expected a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() < n:
+        raise NeError(NE_EINVAL, "argument", "tensor too small")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(stream)
+    torch = _torch()
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _box(box):
+    return (C.c_double * 3)(*[float(b) for b in box])
+
+
+def _err(ctx, code, what):
+    if code != NE_OK:
+        msg = ""
+        if ctx is not None:
+            buf = C.create_string_buffer(256)
+            st = C.c_int()
+            load().ne_last_error(ctx, C.byref(st), buf, 256)
+            msg = buf.value.decode()
+        raise NeError(code, what, msg)
+
+
+def eam_params(A, alpha, beta, B, r_e, r_s, r_c, rho_max, n_knots) -> EamParams:
+    return EamParams(A, alpha, beta, B, r_e, r_s, r_c, rho_max, int(n_knots))
+
+
+def md_params(dt=1e-3, T=100.0, damp=0.1, mass=None, k_spring=5.0, skin=0.5, lambda_fn=2,
+              path=NE_PATH_FL, t_eq=0, t_s=1, lambda_f=0.5, seed=1, replica=0, fix_cm=1,
+              prec=NE_FP64) -> MdParams:
+    if mass is None:
+        mass = 55.845 * 1.0364269656262175e-4
+    return MdParams(dt, T, damp, mass, k_spring, skin, lambda_fn, path, t_eq, t_s, lambda_f,
+                    seed, replica, fix_cm, prec)
+
+
+# ------------------------------------------------------------------ entry points
+def ne_ctx_create(eam: EamParams, max_atoms: int, max_replicas: int = 1):
+    h = C.c_void_p()
+    _err(None, load().ne_ctx_create(C.byref(eam), int(max_atoms), int(max_replicas), C.byref(h)),
+         "ne_ctx_create")
+    return h
+
+
+def ne_ctx_destroy(ctx):
+    _err(None, load().ne_ctx_destroy(ctx), "ne_ctx_destroy")
+
+
+def ne_ctx_set_theta(ctx, theta, stream=None):
+    _err(ctx, load().ne_ctx_set_theta(ctx, _dev(theta), _stream(stream)), "ne_ctx_set_theta")
+
+
+def ne_ctx_get_theta(ctx, theta, stream=None):
+    _err(ctx, load().ne_ctx_get_theta(ctx, _dev(theta), _stream(stream)), "ne_ctx_get_theta")
+
+
+def ne_ctx_set_tuning(ctx, threads_per_atom):
+    _err(ctx, load().ne_ctx_set_tuning(ctx, int(threads_per_atom)), "ne_ctx_set_tuning")
+
+
+def ne_last_error(ctx):
+    buf = C.create_string_buffer(256)
+    st = C.c_int()
+    load().ne_last_error(ctx, C.byref(st), buf, 256)
+    return st.value, buf.value.decode()
+
+
+def ne_create_crystal(lattice, a, nx, ny, nz):
+    """Host: returns (x0 numpy [n][3], box numpy [3])."""
+    import numpy as np
+    n = C.c_int()
+    box = (C.c_double * 3)()
+    L = load()
+    _err(None, L.ne_create_crystal(int(lattice), float(a), nx, ny, nz, None, box, C.byref(n)),
+         "ne_create_crystal")
+    x0 = np.zeros((n.value, 3))
+    _err(None, L.ne_create_crystal(int(lattice), float(a), nx, ny, nz,
+                                   x0.ctypes.data_as(C.c_void_p), box, C.byref(n)),
+         "ne_create_crystal")
+    return x0, np.array(list(box))
+
+
+def ne_eam_energy_forces(ctx, prec, x, box, f=None, e=None, rho=None, stream=None):
+    n = x.shape[0]
+    _err(ctx, load().ne_eam_energy_forces(ctx, int(prec), _dev(x, 3 * n), n, _box(box),
+                                          _dev(f, 3 * n), _dev(e, 1), _dev(rho, n),
+                                          _stream(stream)), "ne_eam_energy_forces")
+
+
+def ne_spring_forces(x, x0, k, f=None, e=None, stream=None):
+    n = x.shape[0]
+    _err(None, load().ne_spring_forces(_dev(x, 3 * n), _dev(x0, 3 * n), n, float(k),
+                                       _dev(f, 3 * n), _dev(e, 1), _stream(stream)),
+         "ne_spring_forces")
+
+
+def ne_eam_backward(ctx, prec, x, box, gE, gx, gtheta, stream=None):
+    n = x.shape[0]
+    _err(ctx, load().ne_eam_backward(ctx, int(prec), _dev(x, 3 * n), n, _box(box), float(gE),
+                                     _dev(gx, 3 * n), _dev(gtheta), _stream(stream)),
+         "ne_eam_backward")
+
+
+def ne_noise(seed, replica, noise_stream, step, z, prec=NE_FP64, stream=None):
+    n = z.shape[0]
+    _err(None, load().ne_noise(int(seed), int(replica), int(noise_stream), int(step), n, int(prec),
+                               _dev(z, 3 * n), _stream(stream)), "ne_noise")
+
+
+def ne_init_velocities(ctx, md: MdParams, v, stream=None):
+    n = v.shape[0]
+    _err(ctx, load().ne_init_velocities(ctx, C.byref(md), n, _dev(v, 3 * n), _stream(stream)),
+         "ne_init_velocities")
+
+
+def ne_langevin_step(ctx, md: MdParams, x, v, x0, box, step, lambda_k, lambda_k1, W=None,
+                     stream=None):
+    n = x.shape[0]
+    _err(ctx, load().ne_langevin_step(ctx, C.byref(md), _dev(x, 3 * n), _dev(v, 3 * n),
+                                      _dev(x0, 3 * n), n, _box(box), int(step), float(lambda_k),
+                                      float(lambda_k1), _dev(W, 1), _stream(stream)),
+         "ne_langevin_step")
+
+
+def ne_switch_run(ctx, md: MdParams, x, v, x0, box, W_fwd, W_bwd, Wcum_fwd=None, Wcum_bwd=None,
+                  trace=None, trace_stride=0, stream=None):
+    n = x.shape[0]
+    _err(ctx, load().ne_switch_run(ctx, C.byref(md), _dev(x, 3 * n), _dev(v, 3 * n),
+                                   _dev(x0, 3 * n), n, _box(box), _dev(W_fwd, 1), _dev(W_bwd, 1),
+                                   _dev(Wcum_fwd), _dev(Wcum_bwd), _dev(trace), int(trace_stride),
+                                   _stream(stream)), "ne_switch_run")
+
+
+def ne_rs_run(ctx, md: MdParams, lambda_f, x, v, x0, box, Wcum_fwd, Wcum_bwd, stream=None):
+    n = x.shape[0]
+    _err(ctx, load().ne_rs_run(ctx, C.byref(md), float(lambda_f), _dev(x, 3 * n), _dev(v, 3 * n),
+                               _dev(x0, 3 * n), n, _box(box), _dev(Wcum_fwd), _dev(Wcum_bwd),
+                               _stream(stream)), "ne_rs_run")
+
+
+def ne_switch_run_batched(ctx, mds, offsets, x, v, x0, boxes, W_fwd, W_bwd, stream=None):
+    n_rep = len(mds)
+    arr = (MdParams * n_rep)(*mds)
+    off = (C.c_int * (n_rep + 1))(*[int(o) for o in offsets])
+    flat = [float(b) for bx in boxes for b in bx]
+    bx = (C.c_double * len(flat))(*flat)
+    _err(ctx, load().ne_switch_run_batched(ctx, arr, n_rep, off, _dev(x), _dev(v), _dev(x0), bx,
+                                           _dev(W_fwd, n_rep), _dev(W_bwd, n_rep),
+                                           _stream(stream)), "ne_switch_run_batched")
+
+
+def _batch_args(mds, offsets, boxes):
+    n_rep = len(mds)
+    arr = (MdParams * n_rep)(*mds)
+    off = (C.c_int * (n_rep + 1))(*[int(o) for o in offsets])
+    flat = [float(b) for bx in boxes for b in bx]
+    return n_rep, arr, off, (C.c_double * len(flat))(*flat)
+
+
+def ne_switch_run_segment(ctx, mds, offsets, x, v, x0, boxes, W, step_begin, n_steps, stream=None):
+    n_rep, arr, off, bx = _batch_args(mds, offsets, boxes)
+    _err(ctx, load().ne_switch_run_segment(ctx, arr, n_rep, off, _dev(x), _dev(v), _dev(x0), bx,
+                                           _dev(W, 2 * n_rep), int(step_begin), int(n_steps),
+                                           _stream(stream)), "ne_switch_run_segment")
+
+
+def ne_profile_segment(ctx, mds, offsets, x, v, x0, boxes, W, step_begin, n_steps, stream=None):
+    """Returns (mean ms per launch [4], launches [4]) for list build, pass 1,
+    pass 2 and the fused step."""
+    n_rep, arr, off, bx = _batch_args(mds, offsets, boxes)
+    ms = (C.c_double * 4)()
+    cnt = (C.c_longlong * 4)()
+    _err(ctx, load().ne_profile_segment(ctx, arr, n_rep, off, _dev(x), _dev(v), _dev(x0), bx,
+                                        _dev(W, 2 * n_rep), int(step_begin), int(n_steps), ms, cnt,
+                                        _stream(stream)), "ne_profile_segment")
+    return list(ms), list(cnt)
+
+
+def ne_msd_fit(ctx, md: MdParams, x, v, x0, box, n_eq, n_samples, stride, stream=None):
+    n = x.shape[0]
+    msd, k = C.c_double(), C.c_double()
+    _err(ctx, load().ne_msd_fit(ctx, C.byref(md), _dev(x, 3 * n), _dev(v, 3 * n),
+                                _dev(x0, 3 * n), n, _box(box), int(n_eq), int(n_samples),
+                                int(stride), C.byref(msd), C.byref(k), _stream(stream)),
+         "ne_msd_fit")
+    return msd.value, k.value
+
+
+def ne_free_energy(n, V, T, mass, k, W_fwd, W_bwd):
+    import numpy as np
+    wf = np.ascontiguousarray(W_fwd, np.float64).ravel()
+    wb = np.ascontiguousarray(W_bwd, np.float64).ravel()
+    F, se, ed = C.c_double(), C.c_double(), C.c_double()
+    _err(None, load().ne_free_energy(int(n), float(V), float(T), float(mass), float(k),
+                                     wf.ctypes.data_as(C.c_void_p), wb.ctypes.data_as(C.c_void_p),
+                                     wf.size, C.byref(F), C.byref(se), C.byref(ed)),
+         "ne_free_energy")
+    return F.value, se.value, ed.value
+
+
+def ne_rs_free_energy(n, T0, F0_T0, lambda_f, t_s, Wcum_fwd, Wcum_bwd, T_grid):
+    import numpy as np
+    cf = np.ascontiguousarray(np.atleast_2d(Wcum_fwd), np.float64)
+    cb = np.ascontiguousarray(np.atleast_2d(Wcum_bwd), np.float64)
+    tg = np.ascontiguousarray(T_grid, np.float64)
+    out = np.zeros(tg.size)
+    _err(None, load().ne_rs_free_energy(int(n), float(T0), float(F0_T0), float(lambda_f),
+                                        int(t_s), cf.ctypes.data_as(C.c_void_p),
+                                        cb.ctypes.data_as(C.c_void_p), cf.shape[0],
+                                        tg.ctypes.data_as(C.c_void_p), tg.size,
+                                        out.ctypes.data_as(C.c_void_p)), "ne_rs_free_energy")
+    return out
+
+
+# ------------------------------------------------------------------ autograd
+def eam_energy_function():
+    """torch.autograd.Function whose forward is ne_eam_energy_forces and whose
+    backward is ne_eam_backward: EAMEnergy.apply(x, theta, ctx, box, prec) -> U."""
+    torch = _torch()
+
+    class EAMEnergy(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, x, theta, ctx, box, prec):
+            ne_ctx_set_theta(ctx, theta.detach().contiguous())
+            e = torch.zeros(1, dtype=torch.float64, device=x.device)
+            ne_eam_energy_forces(ctx, prec, x.detach().contiguous(), box, e=e)
+            fctx.save_for_backward(x, theta)
+            fctx.ne = (ctx, tuple(box), prec)
+            return e[0]
+
+        @staticmethod
+        def backward(fctx, gE):
+            x, theta = fctx.saved_tensors
+            ctx, box, prec = fctx.ne
+            ne_ctx_set_theta(ctx, theta.detach().contiguous())
+            gx = torch.empty_like(x)
+            gth = torch.empty_like(theta)
+            ne_eam_backward(ctx, prec, x.detach().contiguous(), box, float(gE), gx, gth)
+            return gx, gth, None, None, None
+
+    return EAMEnergy

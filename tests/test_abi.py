@@ -1,0 +1,71 @@
+"""The C ABI without a GPU: libne.so builds for sm_103a, loads, exports every
+entry point include/ne.h declares, and its host-only functions agree with the
+oracle.  No kernel is launched here."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2201_04622_gb300 import ne, workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ne.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^ne_status\s+(ne_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_binding_symbols():
+    assert declared_symbols() == sorted(ne.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol():
+    L = ne.load()
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+
+
+def test_invalid_arguments_are_rejected_without_a_gpu():
+    L = ne.load()
+    assert L.ne_ctx_create(None, 10, 1, None) == ne.NE_EINVAL
+    assert L.ne_ctx_destroy(None) == ne.NE_EINVAL
+    box = (C.c_double * 3)()
+    assert L.ne_create_crystal(7, 2.87, 2, 2, 2, None, box, None) == ne.NE_EINVAL
+    assert L.ne_create_crystal(ne.NE_BCC, -1.0, 2, 2, 2, None, box, None) == ne.NE_EINVAL
+    assert L.ne_noise(1, 0, 99, 0, 10, 0, None, None) == ne.NE_EINVAL
+
+
+@pytest.mark.parametrize("lat,a,n", [(ne.NE_BCC, 2.87, (4, 4, 4)), (ne.NE_FCC, 3.65, (3, 4, 5))])
+def test_crystal_matches_oracle(lat, a, n):
+    x0, box = ne.ne_create_crystal(lat, a, *n)
+    xo, bo = O.create_crystal(lat, a, *n)
+    assert np.array_equal(x0, xo) and np.array_equal(box, bo)
+
+
+def test_free_energy_assembly_matches_oracle():
+    g = np.random.default_rng(4)
+    m = W.MASS_FE_AMU * O.amu()
+    for n, T, k in [(128, 100.0, 5.787), (2000, 1400.0, 3.1), (8192, 400.0, 6.2)]:
+        V = n * 11.82
+        wf = g.normal(-4.0 * n, 0.01 * n, 10)
+        wb = g.normal(4.0 * n, 0.01 * n, 10)
+        a = ne.ne_free_energy(n, V, T, m, k, wf, wb)
+        b = O.free_energy(n, V, T, m, k, wf, wb)
+        assert np.allclose(a, b, rtol=1e-13, atol=1e-15)
+
+
+def test_rs_assembly_matches_oracle():
+    g = np.random.default_rng(5)
+    n, T0, lf, ts = 128, 100.0, 0.0625, 400
+    cf = np.cumsum(g.normal(0.5, 0.1, (3, ts + 1)), axis=1)
+    cb = np.cumsum(g.normal(-0.5, 0.1, (3, ts + 1)), axis=1)
+    cf[:, 0] = 0
+    cb[:, 0] = 0
+    Ts = np.arange(100.0, 1601.0, 1.0)
+    a = ne.ne_rs_free_energy(n, T0, -550.0, lf, ts, cf, cb, Ts)
+    b = O.rs_free_energy(n, T0, -550.0, lf, ts, cf, cb, Ts)
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-12)

@@ -1,0 +1,434 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs.
+
+Tolerances
+  FP64 path: energies and forces 1e-10 relative (norm-wise for forces, with
+  a 1e-12 eV/A floor per component); trajectories with the same Philox
+  stream 1e-8 A over the first 100 steps.
+  Mixed path (FP32 pair arithmetic, FP64 sums and integration): pair
+  distances come from FP32 positions wrapped into the box, whose rounding
+  is ulp(L) ~ L 2^-24 (1e-6 A for L ~ 15 A); through phi' ~ 1-10 eV/A that
+  is ~1e-5 relative in a force and, summed with random signs over ~7000
+  pairs, ~1e-7 relative in the total energy.  The tests allow 5e-5 and 1e-6.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2201_04622_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2201_04622_gb300 import ne  # noqa: E402
+
+DEV = torch.device("cuda:0")
+MASS = W.MASS_FE_AMU * 1.0364269656262175e-4
+
+
+@pytest.fixture(scope="module")
+def pot():
+    p = O.eam(**W.EAM_FE_LIKE)
+    return p, O.eam_theta(p)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = ne.ne_ctx_create(ne.eam_params(**W.EAM_FE_LIKE), 60000, 64)
+    yield c
+    ne.ne_ctx_destroy(c)
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=DEV)
+
+
+def N(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def crystal(lat, n):
+    return O.create_crystal(lat, W.A_BCC if lat == O.BCC else W.A_FCC, n, n, n)
+
+
+def gpu_eam(ctx, prec, x, box):
+    xt = T(x)
+    f = torch.zeros_like(xt)
+    e = torch.zeros(1, dtype=torch.float64, device=DEV)
+    rho = torch.zeros(x.shape[0], dtype=torch.float64, device=DEV)
+    ne.ne_eam_energy_forces(ctx, prec, xt, box, f=f, e=e, rho=rho)
+    torch.cuda.synchronize()
+    return float(e.item()), N(f), N(rho)
+
+
+# ---------------------------------------------------------------- noise
+def test_noise_matches_oracle_philox(ctx):
+    n = 4096
+    for seed, rep, stream, step in [(1, 0, 0, 0), (7, 3, 2, 123456), (2 ** 40 + 5, 17, 4, 2 ** 33 + 9)]:
+        z = torch.zeros((n, 3), dtype=torch.float64, device=DEV)
+        ne.ne_noise(seed, rep, stream, step, z, ne.NE_FP64)
+        zo = np.array([O.normals(seed, rep, stream, a, step) for a in range(n)])
+        # libm vs CUDA log/sincospi differ in the last bits only; any
+        # difference in a Philox word would move a normal by O(1)
+        assert np.abs(N(z) - zo).max() < 1e-12
+        ne.ne_noise(seed, rep, stream, step, z, ne.NE_MIXED)
+        assert np.abs(N(z) - zo).max() < 2e-5
+
+
+# ---------------------------------------------------------------- EAM
+CASES = [(O.BCC, 4, 0.1, 1), (O.BCC, 6, 0.15, 2), (O.FCC, 5, 0.12, 3), (O.BCC, 10, 0.1, 4),
+         (O.FCC, 8, 0.1, 5)]
+
+
+@pytest.mark.parametrize("lat,n,amp,seed", CASES)
+def test_eam_fp64_matches_oracle(ctx, pot, lat, n, amp, seed):
+    p, th = pot
+    x0, box = crystal(lat, n)
+    x = W.displaced(x0, amp, seed)
+    Eo, fo, rho_o = O.eam_energy_forces(p, th, x, box)
+    for tpa in (1, 2, 4, 8):
+        ne.ne_ctx_set_tuning(ctx, tpa)
+        E, f, rho = gpu_eam(ctx, ne.NE_FP64, x, box)
+        assert E == pytest.approx(Eo, rel=1e-10)
+        assert rel(f, fo) < 1e-10
+        assert np.abs(f - fo).max() < 1e-10 * np.abs(fo).max() + 1e-12
+        assert rel(rho, rho_o) < 1e-12
+    ne.ne_ctx_set_tuning(ctx, 4)
+
+
+@pytest.mark.parametrize("lat,n,amp,seed", CASES)
+def test_eam_mixed_matches_oracle(ctx, pot, lat, n, amp, seed):
+    p, th = pot
+    x0, box = crystal(lat, n)
+    x = W.displaced(x0, amp, seed)
+    Eo, fo, rho_o = O.eam_energy_forces(p, th, x, box)
+    E, f, rho = gpu_eam(ctx, ne.NE_MIXED, x, box)
+    assert E == pytest.approx(Eo, rel=1e-6)
+    assert rel(f, fo) < 5e-5
+    assert rel(rho, rho_o) < 1e-6
+
+
+def test_unwrapped_images_give_the_same_energy(ctx):
+    x0, box = crystal(O.BCC, 6)
+    x = W.displaced(x0, 0.1, 9)
+    g = np.random.default_rng(1)
+    E1, f1, _ = gpu_eam(ctx, ne.NE_FP64, x, box)
+    E2, f2, _ = gpu_eam(ctx, ne.NE_FP64, x + box * g.integers(-3, 4, size=x.shape), box)
+    assert E2 == pytest.approx(E1, rel=1e-12)
+    assert rel(f2, f1) < 1e-10
+
+
+def test_spring_matches_oracle():
+    x0, box = crystal(O.BCC, 5)
+    x = W.displaced(x0, 0.2, 3)
+    Eo, fo = O.spring(x, x0, 5.5)
+    f = torch.zeros((len(x), 3), dtype=torch.float64, device=DEV)
+    e = torch.zeros(1, dtype=torch.float64, device=DEV)
+    ne.ne_spring_forces(T(x), T(x0), 5.5, f=f, e=e)
+    assert float(e.item()) == pytest.approx(Eo, rel=1e-13)
+    assert np.allclose(N(f), fo, rtol=1e-15, atol=0)
+
+
+# ---------------------------------------------------------------- dynamics
+def md_pair(**kw):
+    """Matching oracle and library parameter blocks."""
+    base = dict(dt=1e-3, T=100.0, damp=0.1, k_spring=6.0, lambda_fn=2, t_eq=20, t_s=30,
+                lambda_f=0.5, seed=11, replica=2, fix_cm=1)
+    base.update(kw)
+    skin = base.pop("skin", 0.3)
+    prec = base.pop("prec", ne.NE_FP64)
+    path = base.pop("path", O.PATH_FL)
+    mo = O.md(mass=MASS, path=path, **base)
+    mg = ne.md_params(mass=MASS, skin=skin, prec=prec, path=path, **base)
+    return mo, mg
+
+
+def test_init_velocities_match_oracle(ctx):
+    for fix_cm in (1, 0):
+        mo, mg = md_pair(T=300.0, fix_cm=fix_cm, seed=5, replica=9)
+        v = torch.zeros((432, 3), dtype=torch.float64, device=DEV)
+        ne.ne_init_velocities(ctx, mg, v)
+        vo = O.init_velocities(mo, 432)
+        assert np.abs(N(v) - vo).max() < 1e-13 * np.abs(vo).max()
+
+
+def test_langevin_steps_match_oracle(ctx, pot):
+    p, th = pot
+    x0, box = crystal(O.BCC, 4)
+    mo, mg = md_pair(T=300.0)
+    v0 = O.init_velocities(mo, len(x0))
+    xo, vo = O.langevin_steps(p, th, mo, 0.3, x0, v0, x0, box, 40, 20)
+    x, v = T(x0), T(v0)
+    W_ = torch.zeros(1, dtype=torch.float64, device=DEV)
+    for s in range(40, 60):
+        ne.ne_langevin_step(ctx, mg, x, v, T(x0), box, s, 0.3, 0.3, W_)
+    assert np.abs(N(x) - xo).max() < 1e-10
+    assert np.abs(N(v) - vo).max() < 1e-8
+    assert float(W_.item()) == 0.0
+
+
+def _run_both(ctx, pot, lat, n, trace_stride=0, **kw):
+    p, th = pot
+    x0, box = crystal(lat, n)
+    mo, mg = md_pair(**kw)
+    v0 = O.init_velocities(mo, len(x0))
+    ro = O.switch_run(p, th, mo, x0, v0, x0, box, cumulative=True, trace_stride=trace_stride)
+    x, v = T(x0), T(v0)
+    wf = torch.zeros(1, dtype=torch.float64, device=DEV)
+    wb = torch.zeros(1, dtype=torch.float64, device=DEV)
+    cf = torch.zeros(mo.t_s + 1, dtype=torch.float64, device=DEV)
+    cb = torch.zeros(mo.t_s + 1, dtype=torch.float64, device=DEV)
+    tr = None
+    if trace_stride:
+        rows = (2 * mo.t_eq + 2 * mo.t_s - 1) // trace_stride + 1
+        tr = torch.zeros((rows, 8), dtype=torch.float64, device=DEV)
+    ne.ne_switch_run(ctx, mg, x, v, T(x0), box, wf, wb, cf, cb, tr, trace_stride)
+    out = dict(x=N(x), v=N(v), W_f=float(wf.item()), W_b=float(wb.item()), Wcum_f=N(cf),
+               Wcum_b=N(cb))
+    if tr is not None:
+        out["trace"] = N(tr)
+    return ro, out
+
+
+@pytest.mark.parametrize("lat,n,path", [(O.BCC, 4, O.PATH_FL), (O.FCC, 4, O.PATH_FL),
+                                        (O.BCC, 4, O.PATH_RS), (O.BCC, 7, O.PATH_FL)])
+def test_switch_run_trajectory_parity_100_steps(ctx, pot, lat, n, path):
+    ro, g = _run_both(ctx, pot, lat, n, trace_stride=7, path=path, T=300.0)
+    assert np.abs(g["x"] - ro["x"]).max() < 1e-8
+    assert np.abs(g["v"] - ro["v"]).max() < 1e-6
+    assert g["W_f"] == pytest.approx(ro["W_f"], rel=1e-9, abs=1e-9)
+    assert g["W_b"] == pytest.approx(ro["W_b"], rel=1e-9, abs=1e-9)
+    assert np.allclose(g["Wcum_f"], ro["Wcum_f"], rtol=1e-9, atol=1e-9)
+    assert np.allclose(g["Wcum_b"], ro["Wcum_b"], rtol=1e-9, atol=1e-9)
+    assert np.allclose(g["trace"], ro["trace"], rtol=1e-9, atol=1e-8)
+
+
+def test_switch_run_with_graph_chunks(ctx, pot):
+    """A run long enough to be replayed from captured CUDA graphs (t_eq and
+    t_s not multiples of the chunk), at the 4x4x4 bcc size of the smallest
+    workload, still tracks the oracle."""
+    ro, g = _run_both(ctx, pot, O.BCC, 4, t_eq=61, t_s=97, T=100.0)
+    assert np.abs(g["x"] - ro["x"]).max() < 1e-8
+    assert g["W_f"] == pytest.approx(ro["W_f"], rel=1e-9)
+    assert g["W_b"] == pytest.approx(ro["W_b"], rel=1e-9)
+
+
+def test_batched_replicas_match_independent_oracle_runs(ctx, pot):
+    p, th = pot
+    systems = [(O.BCC, 4, 100.0, 6.0, 3), (O.FCC, 4, 300.0, 5.0, 4), (O.BCC, 5, 200.0, 5.5, 7),
+               (O.BCC, 6, 800.0, 4.5, 1)]
+    xs, x0s, vs, offs, boxes, mgs, ros = [], [], [], [0], [], [], []
+    for r, (lat, n, Tk, k, seed) in enumerate(systems):
+        x0, box = crystal(lat, n)
+        mo, mg = md_pair(T=Tk, k_spring=k, seed=seed, replica=r, skin=0.4)
+        v0 = O.init_velocities(mo, len(x0))
+        ros.append(O.switch_run(p, th, mo, x0, v0, x0, box))
+        x0s.append(x0)
+        vs.append(v0)
+        offs.append(offs[-1] + len(x0))
+        boxes.append(box)
+        mgs.append(mg)
+    x = T(np.concatenate(x0s))
+    v = T(np.concatenate(vs))
+    wf = torch.zeros(len(systems), dtype=torch.float64, device=DEV)
+    wb = torch.zeros_like(wf)
+    ne.ne_switch_run_batched(ctx, mgs, offs, x, v, T(np.concatenate(x0s)), boxes, wf, wb)
+    xg = N(x)
+    for r, ro in enumerate(ros):
+        assert np.abs(xg[offs[r]:offs[r + 1]] - ro["x"]).max() < 1e-8
+        assert float(wf[r]) == pytest.approx(ro["W_f"], rel=1e-9)
+        assert float(wb[r]) == pytest.approx(ro["W_b"], rel=1e-9)
+
+
+def test_full_size_batched_sample(ctx, pot):
+    """The launch configuration of the benchmark (10 bcc 10^3 and 10 fcc 8^3
+    replicas at 1400 K, batched) for the first steps; replicas 0 and 19 are
+    checked against the oracle atom by atom in FP64; the mixed run tracks
+    them to FP32 accuracy."""
+    p, th = pot
+    systems = [(O.BCC, 10)] * 10 + [(O.FCC, 8)] * 10
+    x0s, vs, offs, boxes, mgs = [], [], [0], [], []
+    checks = {}
+    for r, (lat, n) in enumerate(systems):
+        x0, box = crystal(lat, n)
+        mo, mg = md_pair(T=1400.0, k_spring=4.0, seed=1 + r % 10, replica=r, t_eq=5, t_s=10, skin=1.0)
+        v0 = O.init_velocities(mo, len(x0))
+        if r in (0, 19):
+            checks[r] = O.switch_run(p, th, mo, x0, v0, x0, box)
+        x0s.append(x0)
+        vs.append(v0)
+        offs.append(offs[-1] + len(x0))
+        boxes.append(box)
+        mgs.append(mg)
+    for prec, tol in [(ne.NE_FP64, 1e-8), (ne.NE_MIXED, 2e-4)]:
+        for m in mgs:
+            m.prec = prec
+        x = T(np.concatenate(x0s))
+        v = T(np.concatenate(vs))
+        wf = torch.zeros(len(systems), dtype=torch.float64, device=DEV)
+        wb = torch.zeros_like(wf)
+        ne.ne_switch_run_batched(ctx, mgs, offs, x, v, T(np.concatenate(x0s)), boxes, wf, wb)
+        xg = N(x)
+        for r, ro in checks.items():
+            assert np.abs(xg[offs[r]:offs[r + 1]] - ro["x"]).max() < tol
+            assert float(wf[r]) == pytest.approx(ro["W_f"], rel=10 * tol, abs=10 * tol)
+
+
+def test_msd_fit_matches_oracle(ctx, pot):
+    p, th = pot
+    x0, box = crystal(O.BCC, 4)
+    mo, mg = md_pair(T=100.0)
+    v0 = O.init_velocities(mo, len(x0))
+    msd_o, k_o = O.msd_fit(p, th, mo, x0, v0, x0, box, 20, 10, 5)
+    x, v = T(x0), T(v0)
+    msd, k = ne.ne_msd_fit(ctx, mg, x, v, T(x0), box, 20, 10, 5)
+    assert msd == pytest.approx(msd_o, rel=1e-9)
+    assert k == pytest.approx(k_o, rel=1e-9)
+
+
+# ---------------------------------------------------------------- backward
+@pytest.mark.parametrize("prec,tol", [(ne.NE_FP64, 1e-10), (ne.NE_MIXED, 1e-5)])
+def test_backward_matches_oracle_gradient(ctx, pot, prec, tol):
+    p, th = pot
+    x0, box = crystal(O.BCC, 6)
+    x = W.displaced(x0, 0.1, 5)
+    go = O.eam_grad_theta(p, th, x, box)
+    _, fo, _ = O.eam_energy_forces(p, th, x, box)
+    gx = torch.zeros((len(x), 3), dtype=torch.float64, device=DEV)
+    gth = torch.zeros((3, W.EAM_FE_LIKE["n_knots"], 2), dtype=torch.float64, device=DEV)
+    ne.ne_eam_backward(ctx, prec, T(x), box, 2.0, gx, gth)
+    assert rel(N(gth), 2.0 * go) < tol
+    for w in range(3):
+        assert rel(N(gth)[w], 2.0 * go[w]) < 10 * tol
+    assert rel(N(gx), -2.0 * fo) < (1e-10 if prec == ne.NE_FP64 else 5e-5)
+
+
+def test_autograd_function_against_finite_differences(ctx, pot):
+    p, th = pot
+    x0, box = crystal(O.BCC, 5)
+    x = W.displaced(x0, 0.05, 8)
+    EAM = ne.eam_energy_function()
+    theta = T(th).requires_grad_(True)
+    xt = T(x).requires_grad_(True)
+    U = EAM.apply(xt, theta, ctx, box, ne.NE_FP64)
+    U.backward()
+    gth = N(theta.grad)
+    gx = N(xt.grad)
+    rng = np.random.default_rng(0)
+    active = [np.flatnonzero(np.abs(gth[w]).sum(1) > 0) for w in range(3)]
+    for w in range(3):
+        for k in rng.choice(active[w], 4, replace=False):
+            for s in (0, 1):
+                h = 1e-6
+                tp, tm = th.copy(), th.copy()
+                tp[w, k, s] += h
+                tm[w, k, s] -= h
+                ep = float(EAM.apply(T(x), T(tp), ctx, box, ne.NE_FP64))
+                em = float(EAM.apply(T(x), T(tm), ctx, box, ne.NE_FP64))
+                fd = (ep - em) / (2 * h)
+                assert gth[w, k, s] == pytest.approx(fd, rel=1e-6, abs=1e-6)
+    for i, c in [(3, 0), (50, 2), (200, 1)]:
+        h = 1e-5
+        xp, xm = x.copy(), x.copy()
+        xp[i, c] += h
+        xm[i, c] -= h
+        fd = (float(EAM.apply(T(xp), T(th), ctx, box, ne.NE_FP64)) -
+              float(EAM.apply(T(xm), T(th), ctx, box, ne.NE_FP64))) / (2 * h)
+        assert gx[i, c] == pytest.approx(fd, rel=1e-6, abs=1e-7)
+    # restore the analytic tables
+    ne.ne_ctx_set_theta(ctx, T(th))
+
+
+# ---------------------------------------------------------------- free energy
+def test_mixed_free_energy_within_1meV_of_fp64_and_oracle(ctx, pot):
+    """Same seeds in FP64 and mixed precision, and the oracle, on the 4x4x4
+    bcc cell at 100 K: free energies per atom agree within 1 meV/atom."""
+    p, th = pot
+    x0, box = crystal(O.BCC, 4)
+    n = len(x0)
+    V = float(np.prod(box))
+    res = {}
+    for name, prec in [("fp64", ne.NE_FP64), ("mixed", ne.NE_MIXED)]:
+        wfs, wbs = [], []
+        for seed in (1, 2, 3):
+            mo, mg = md_pair(T=100.0, k_spring=7.0, t_eq=300, t_s=1000, seed=seed, prec=prec)
+            v0 = O.init_velocities(mo, n)
+            x, v = T(x0), T(v0)
+            wf = torch.zeros(1, dtype=torch.float64, device=DEV)
+            wb = torch.zeros(1, dtype=torch.float64, device=DEV)
+            ne.ne_switch_run(ctx, mg, x, v, T(x0), box, wf, wb)
+            wfs.append(float(wf.item()))
+            wbs.append(float(wb.item()))
+        res[name] = ne.ne_free_energy(n, V, 100.0, MASS, 7.0, wfs, wbs)
+    wfs, wbs = [], []
+    for seed in (1, 2, 3):
+        mo, _ = md_pair(T=100.0, k_spring=7.0, t_eq=300, t_s=1000, seed=seed)
+        r = O.switch_run(p, th, mo, x0, O.init_velocities(mo, n), x0, box)
+        wfs.append(r["W_f"])
+        wbs.append(r["W_b"])
+    Fo = O.free_energy(n, V, 100.0, MASS, 7.0, wfs, wbs)
+    assert res["fp64"][0] == pytest.approx(Fo[0], abs=1e-9)
+    assert abs(res["mixed"][0] - Fo[0]) < 1e-3
+    assert abs(res["mixed"][0] - Fo[0]) < 2 * math.hypot(res["mixed"][1], Fo[1]) + 1e-4
+
+
+# ---------------------------------------------------------------- errors
+def test_errors_are_reported_not_trapped(ctx):
+    x0, box = crystal(O.BCC, 4)
+    x = x0.copy()
+    x[1] = x[0] + np.array([0.5, 0.0, 0.0])
+    with pytest.raises(ne.NeError, match="NE_ERANGE"):
+        gpu_eam(ctx, ne.NE_FP64, x, box)
+    x = x0.copy()
+    x[5, 1] = float("nan")
+    with pytest.raises(ne.NeError, match="NE_ENAN"):
+        gpu_eam(ctx, ne.NE_FP64, x, box)
+    with pytest.raises(ne.NeError, match="NE_EINVAL"):
+        xs, bs = crystal(O.BCC, 3)
+        gpu_eam(ctx, ne.NE_FP64, xs, bs)
+    # neighbour capacity: r_c + skin = 9.5 A holds > 256 bcc neighbours
+    xb, bb = crystal(O.BCC, 7)
+    mo, mg = md_pair(skin=4.2)
+    xt, vt = T(xb), T(np.zeros_like(xb))
+    wf = torch.zeros(1, dtype=torch.float64, device=DEV)
+    with pytest.raises(ne.NeError, match="NE_ENEIGH"):
+        ne.ne_switch_run(ctx, mg, xt, vt, T(xb), bb, wf, wf.clone())
+    # the context still works afterwards
+    E, f, _ = gpu_eam(ctx, ne.NE_FP64, x0, box)
+    assert E / len(x0) == pytest.approx(-4.28, abs=1e-9)
+
+
+def test_resume_from_checkpoint_is_bitwise(ctx):
+    """Counter-based noise, deterministic reductions and a neighbour list
+    built from the sites make [0, a) + [a, S) identical to [0, S)."""
+    systems = [(O.BCC, 5, 600.0, 1), (O.FCC, 4, 900.0, 2)]
+    x0s, vs, offs, boxes, mgs = [], [], [0], [], []
+    for r, (lat, n, Tk, seed) in enumerate(systems):
+        x0, box = crystal(lat, n)
+        mo, mg = md_pair(T=Tk, k_spring=5.0, seed=seed, replica=r, t_eq=40, t_s=150, skin=1.2,
+                         prec=ne.NE_MIXED)
+        x0s.append(x0)
+        vs.append(O.init_velocities(mo, len(x0)))
+        offs.append(offs[-1] + len(x0))
+        boxes.append(box)
+        mgs.append(mg)
+    S = 2 * 40 + 2 * 150
+    X0 = T(np.concatenate(x0s))
+    out = []
+    for cuts in ([0, S], [0, 77, 230, S]):
+        x, v = X0.clone(), T(np.concatenate(vs))
+        Wd = torch.zeros((len(systems), 2), dtype=torch.float64, device=DEV)
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            ne.ne_switch_run_segment(ctx, mgs, offs, x, v, X0, boxes, Wd, a, b - a)
+        out.append((N(x), N(v), N(Wd)))
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
