@@ -105,6 +105,12 @@ ne_status ne_ctx_get_theta(ne_ctx* ctx, double* theta_dev, void* stream);
 /* Tuning of the pair kernels: threads per atom (1, 2, 4 or 8). */
 ne_status ne_ctx_set_tuning(ne_ctx* ctx, int threads_per_atom);
 
+/* Number of per-replica neighbour-list builds since the context was created
+ * (one at the start of every run or segment, plus one each time an atom of
+ * the replica strays more than skin/2 from its list-build position).
+ * Synchronises the device. */
+ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds);
+
 /* Status bits recorded by the last call, and its message (msg may be NULL). */
 ne_status ne_last_error(ne_ctx* ctx, int* device_status, char* msg, int msg_len);
 

@@ -42,9 +42,10 @@ struct ne_ctx {
     int *cellof = nullptr, *sorted = nullptr, *cstart = nullptr, *cfill = nullptr;
     double *partA = nullptr, *partB = nullptr, *tot = nullptr, *W = nullptr, *scratch = nullptr;
     unsigned* tile_done = nullptr;
-    int *flags = nullptr, *status = nullptr, *tile_rep = nullptr;
+    int *flags = nullptr, *building = nullptr, *status = nullptr, *tile_rep = nullptr;
     RepDev* rep = nullptr;
     long long* step_ctr = nullptr;
+    unsigned long long* rebuilds = nullptr;
     float* bins = nullptr;
     int bins_blocks = 0;
     std::vector<RepDev> rep_h;
@@ -257,6 +258,8 @@ ne_status setup_batch(ne_ctx* ctx, int n_rep, const int* off, const double* boxe
     B.trace_stride = a.trace_stride > 0 ? a.trace_stride : 1;
     B.trace_rows = a.trace_rows;
     B.flags = ctx->flags;
+    B.building = ctx->building;
+    B.rebuilds = ctx->rebuilds;
     B.status = ctx->status;
     B.tab = ctx->tab;
     return NE_OK;
@@ -493,10 +496,13 @@ ne_status ne_ctx_create(const ne_eam_params* eam, int max_atoms, int max_replica
     A(dalloc(&ctx->scratch, 4 * R + 16));
     A(dalloc(&ctx->tile_done, R));
     A(dalloc(&ctx->flags, R));
+    A(dalloc(&ctx->building, R));
     A(dalloc(&ctx->status, 1));
     A(dalloc(&ctx->tile_rep, (size_t)ctx->tiles_cap));
     A(dalloc(&ctx->rep, R));
     A(dalloc(&ctx->step_ctr, 1));
+    A(dalloc(&ctx->rebuilds, 1));
+    if (ok) ok = cudaMemset(ctx->rebuilds, 0, sizeof(unsigned long long)) == cudaSuccess;
     if (!ok) {
         ne_ctx_destroy(ctx);
         return NE_ENOMEM;
@@ -525,7 +531,7 @@ ne_status ne_ctx_destroy(ne_ctx* ctx)
                     ctx->pbuild, ctx->f32, ctx->f64, ctx->dF64, ctx->rho, ctx->xi64, ctx->xi32,
                     ctx->nbr, ctx->ncnt, ctx->sl, ctx->scnt, ctx->cellof, ctx->sorted, ctx->cstart,
                     ctx->cfill, ctx->partA, ctx->partB, ctx->tot, ctx->W, ctx->scratch,
-                    ctx->tile_done, ctx->flags, ctx->status, ctx->tile_rep, ctx->rep, ctx->step_ctr,
+                    ctx->tile_done, ctx->flags, ctx->building, ctx->status, ctx->tile_rep, ctx->rep, ctx->step_ctr, ctx->rebuilds,
                     ctx->bins};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -558,6 +564,16 @@ ne_status ne_ctx_set_tuning(ne_ctx* ctx, int tpa)
     if (!ctx) return NE_EINVAL;
     if (tpa != 1 && tpa != 2 && tpa != 4 && tpa != 8) return fail(ctx, NE_EINVAL, "threads_per_atom must be 1, 2, 4 or 8");
     ctx->tpa = tpa;
+    return NE_OK;
+}
+
+ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds)
+{
+    if (!ctx || !list_builds) return NE_EINVAL;
+    unsigned long long v = 0;
+    if (cudaMemcpy(&v, ctx->rebuilds, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(ctx, NE_ECUDA, "reading the counters failed");
+    *list_builds = (long long)v;
     return NE_OK;
 }
 

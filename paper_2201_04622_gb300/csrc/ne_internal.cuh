@@ -117,7 +117,9 @@ struct DevBatch {
     double* Wcum;      // nullable, [n_rep][2][t_s + 1]
     double* trace;     // nullable, [rows][8], single replica
     int trace_stride, trace_rows;
-    int* flags;        // [n_rep] list rebuild requested
+    int* flags;        // [n_rep] list rebuild requested (set by the step kernel)
+    int* building;     // [n_rep] rebuild in progress this step
+    unsigned long long* rebuilds;  // count of replica list builds
     int* status;
     Tables tab;
 };

@@ -9,24 +9,33 @@ namespace {
 __device__ __forceinline__ double wrap(double x, double L, double invL) { return x - L * floor(x * invL); }
 
 // ------------------------------------------------------------ neighbours
-// One block per replica whose rebuild flag is set (or all, when forced):
-//   1. bin atoms into cells of edge >= r_c + skin (wrapped positions);
-//   2. counting sort by cell (count, exclusive scan, scatter), then an
-//      insertion sort inside each cell so the order does not depend on
-//      the order of the atomics;
-//   3. full list of every atom within r_c + skin, minimum image, over the
-//      27 surrounding cells (all pairs when the box holds < 3 cells/axis).
-// The wrapped positions at the build are kept for the displacement check.
-__global__ void __launch_bounds__(512) k_nl_build(DevBatch B, int force, int from_sites)
+// Rebuild of the candidate list of every replica whose flag is set (or of
+// all replicas, when forced), in two launches:
+//   k_nl_bin   one block per replica: reference positions (the lattice
+//              sites at the start of a run, the current positions after an
+//              atom strayed more than skin/2), wrapped; cell binning with
+//              cells of edge >= r_c + skin; counting sort by cell (count,
+//              exclusive scan, scatter) and an insertion sort inside each
+//              cell so the order does not depend on the atomics;
+//   k_nl_list  one thread per atom on every SM: all atoms of the 27
+//              surrounding cells (all atoms when the box holds < 3 cells per
+//              axis) within r_c + skin, minimum image, FP32 distances with a
+//              1e-3 A margin so that rounding never drops a pair.
+// Both return at once for replicas that need no rebuild.
+__global__ void __launch_bounds__(512) k_nl_bin(DevBatch B, int force, int from_sites)
 {
     const int rep = blockIdx.x;
     const RepDev& P = B.rep[rep];
-    if (!force && B.flags[rep] == 0) return;
-    const int n = P.n, off = P.off, tid = threadIdx.x, bs = blockDim.x;
-    const int tpa = B.tpa;
-    // reference positions of the list: the lattice sites at the start of a
-    // run (the list then depends on the sites only), the current positions
-    // when an atom has strayed more than skin/2 from its reference
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const int go = force || B.flags[rep] != 0;
+    __syncthreads();
+    if (tid == 0) {
+        B.building[rep] = go;
+        B.flags[rep] = 0;
+        if (go) atomicAdd(B.rebuilds, 1ull);
+    }
+    if (!go) return;
+    const int n = P.n, off = P.off;
     const double* X = from_sites ? B.x0 : B.x;
     for (int a = tid; a < n; a += bs) {
         const int i = off + a;
@@ -34,103 +43,96 @@ __global__ void __launch_bounds__(512) k_nl_build(DevBatch B, int force, int fro
                                   (float)wrap(X[3 * i + 1], P.L[1], P.invL[1]),
                                   (float)wrap(X[3 * i + 2], P.L[2], P.invL[2]), 0.f);
     }
-    int bad = 0;
-    if (P.nc[0] == 0) {
-        for (int a = tid; a < n; a += bs) {
-            const int i = off + a;
-            const double xi = X[3 * i], yi = X[3 * i + 1], zi = X[3 * i + 2];
-            int cnt = 0;
-            for (int b = 0; b < n; ++b) {
-                if (b == a) continue;
-                const int j = off + b;
-                double dx = X[3 * j] - xi, dy = X[3 * j + 1] - yi, dz = X[3 * j + 2] - zi;
-                dx -= P.L[0] * rint(dx * P.invL[0]);
-                dy -= P.L[1] * rint(dy * P.invL[1]);
-                dz -= P.L[2] * rint(dz * P.invL[2]);
-                if (dx * dx + dy * dy + dz * dz < P.rlist2) {
-                    if (cnt < NE_NMAX) B.nbr[ne_nbr_index(cnt, i, B.n_tot, tpa)] = j;
-                    ++cnt;
-                }
+    if (P.nc[0] == 0) return;
+    const int nc0 = P.nc[0], nc1 = P.nc[1], nc2 = P.nc[2];
+    const int ncell = nc0 * nc1 * nc2;
+    int* start = B.cstart + P.cell_off + rep;  // ncell + 1 entries
+    int* fill = B.cfill + P.cell_off;
+    for (int c = tid; c <= ncell; c += bs) start[c] = 0;
+    for (int c = tid; c < ncell; c += bs) fill[c] = 0;
+    __syncthreads();
+    for (int a = tid; a < n; a += bs) {
+        const int i = off + a;
+        int c3[3];
+        for (int d = 0; d < 3; ++d) {
+            double s = wrap(X[3 * i + d], P.L[d], P.invL[d]);
+            int q = (int)(s * P.invL[d] * P.nc[d]);
+            c3[d] = min(max(q, 0), P.nc[d] - 1);
+        }
+        const int c = (c3[0] * nc1 + c3[1]) * nc2 + c3[2];
+        B.cellof[i] = c;
+        atomicAdd(&start[c + 1], 1);
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int c = 0; c < ncell; ++c) start[c + 1] += start[c];
+    __syncthreads();
+    for (int a = tid; a < n; a += bs) {
+        const int c = B.cellof[off + a];
+        const int pos = atomicAdd(&fill[c], 1);
+        B.sorted[off + start[c] + pos] = a;
+    }
+    __syncthreads();
+    for (int c = tid; c < ncell; c += bs) {
+        int* sl = B.sorted + off + start[c];
+        const int len = start[c + 1] - start[c];
+        for (int p = 1; p < len; ++p) {
+            int key = sl[p], q = p - 1;
+            while (q >= 0 && sl[q] > key) {
+                sl[q + 1] = sl[q];
+                --q;
             }
-            if (cnt > NE_NMAX) bad |= ST_ENEIGH;
-            B.ncnt[i] = min(cnt, NE_NMAX);
-        }
-    } else {
-        const int nc0 = P.nc[0], nc1 = P.nc[1], nc2 = P.nc[2];
-        const int ncell = nc0 * nc1 * nc2;
-        int* start = B.cstart + P.cell_off + rep;  // ncell + 1 entries
-        int* fill = B.cfill + P.cell_off;
-        for (int c = tid; c <= ncell; c += bs) start[c] = 0;
-        for (int c = tid; c < ncell; c += bs) fill[c] = 0;
-        __syncthreads();
-        for (int a = tid; a < n; a += bs) {
-            const int i = off + a;
-            int c3[3];
-            for (int d = 0; d < 3; ++d) {
-                double s = wrap(X[3 * i + d], P.L[d], P.invL[d]);
-                int q = (int)(s * P.invL[d] * P.nc[d]);
-                c3[d] = min(max(q, 0), P.nc[d] - 1);
-            }
-            const int c = (c3[0] * nc1 + c3[1]) * nc2 + c3[2];
-            B.cellof[i] = c;
-            atomicAdd(&start[c + 1], 1);
-        }
-        __syncthreads();
-        if (tid == 0)
-            for (int c = 0; c < ncell; ++c) start[c + 1] += start[c];
-        __syncthreads();
-        for (int a = tid; a < n; a += bs) {
-            const int c = B.cellof[off + a];
-            const int pos = atomicAdd(&fill[c], 1);
-            B.sorted[off + start[c] + pos] = a;
-        }
-        __syncthreads();
-        for (int c = tid; c < ncell; c += bs) {
-            int* sl = B.sorted + off + start[c];
-            const int len = start[c + 1] - start[c];
-            for (int p = 1; p < len; ++p) {
-                int key = sl[p], q = p - 1;
-                while (q >= 0 && sl[q] > key) {
-                    sl[q + 1] = sl[q];
-                    --q;
-                }
-                sl[q + 1] = key;
-            }
-        }
-        __syncthreads();
-        for (int a = tid; a < n; a += bs) {
-            const int i = off + a;
-            const int c = B.cellof[i];
-            const int cx = c / (nc1 * nc2), cy = (c / nc2) % nc1, cz = c % nc2;
-            const double xi = X[3 * i], yi = X[3 * i + 1], zi = X[3 * i + 2];
-            int cnt = 0;
-            for (int dx = -1; dx <= 1; ++dx)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dz = -1; dz <= 1; ++dz) {
-                        const int ox = (cx + dx + nc0) % nc0, oy = (cy + dy + nc1) % nc1,
-                                  oz = (cz + dz + nc2) % nc2;
-                        const int o = (ox * nc1 + oy) * nc2 + oz;
-                        for (int p = start[o]; p < start[o + 1]; ++p) {
-                            const int b = B.sorted[off + p];
-                            if (b == a) continue;
-                            const int j = off + b;
-                            double ex = X[3 * j] - xi, ey = X[3 * j + 1] - yi, ez = X[3 * j + 2] - zi;
-                            ex -= P.L[0] * rint(ex * P.invL[0]);
-                            ey -= P.L[1] * rint(ey * P.invL[1]);
-                            ez -= P.L[2] * rint(ez * P.invL[2]);
-                            if (ex * ex + ey * ey + ez * ez < P.rlist2) {
-                                if (cnt < NE_NMAX) B.nbr[ne_nbr_index(cnt, i, B.n_tot, tpa)] = j;
-                                ++cnt;
-                            }
-                        }
-                    }
-            if (cnt > NE_NMAX) bad |= ST_ENEIGH;
-            B.ncnt[i] = min(cnt, NE_NMAX);
+            sl[q + 1] = key;
         }
     }
+}
+
+__global__ void __launch_bounds__(NE_TILE) k_nl_list(DevBatch B)
+{
+    const int tile = blockIdx.x;
+    const int rep = B.tile_rep[tile];
+    if (!B.building[rep]) return;
+    const RepDev& P = B.rep[rep];
+    const int a = (tile - P.tile0) * NE_TILE + threadIdx.x;
+    if (a >= P.n) return;
+    const int off = P.off, i = off + a, tpa = B.tpa;
+    const float L0 = (float)P.L[0], L1 = (float)P.L[1], L2 = (float)P.L[2];
+    const float iL0 = (float)P.invL[0], iL1 = (float)P.invL[1], iL2 = (float)P.invL[2];
+    const float rl = sqrtf((float)P.rlist2) + 1e-3f;
+    const float rl2 = rl * rl;
+    const float4 pi = B.pbuild[i];
+    int cnt = 0, bad = 0;
+    auto test = [&](int b) {
+        if (b == a) return;
+        const int j = off + b;
+        const float4 pj = B.pbuild[j];
+        float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+        dx -= L0 * rintf(dx * iL0);
+        dy -= L1 * rintf(dy * iL1);
+        dz -= L2 * rintf(dz * iL2);
+        if (dx * dx + dy * dy + dz * dz < rl2) {
+            if (cnt < NE_NMAX) B.nbr[ne_nbr_index(cnt, i, B.n_tot, tpa)] = j;
+            ++cnt;
+        }
+    };
+    if (P.nc[0] == 0) {
+        for (int b = 0; b < P.n; ++b) test(b);
+    } else {
+        const int nc0 = P.nc[0], nc1 = P.nc[1], nc2 = P.nc[2];
+        const int* start = B.cstart + P.cell_off + rep;
+        const int c = B.cellof[i];
+        const int cx = c / (nc1 * nc2), cy = (c / nc2) % nc1, cz = c % nc2;
+        for (int dx = -1; dx <= 1; ++dx)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dz = -1; dz <= 1; ++dz) {
+                    const int o = (((cx + dx + nc0) % nc0) * nc1 + (cy + dy + nc1) % nc1) * nc2 +
+                                  (cz + dz + nc2) % nc2;
+                    for (int p = start[o]; p < start[o + 1]; ++p) test(B.sorted[off + p]);
+                }
+    }
+    if (cnt > NE_NMAX) bad |= ST_ENEIGH;
+    B.ncnt[i] = min(cnt, NE_NMAX);
     if (bad) ne_set_status(B.status, bad);
-    __syncthreads();
-    if (tid == 0) B.flags[rep] = 0;
 }
 
 // ------------------------------------------------------------ fused step
@@ -444,7 +446,8 @@ namespace ne {
 
 void launch_nl_build(const DevBatch& B, int force, int from_sites, cudaStream_t st)
 {
-    k_nl_build<<<B.n_rep, 512, 0, st>>>(B, force, from_sites);
+    k_nl_bin<<<B.n_rep, 512, 0, st>>>(B, force, from_sites);
+    k_nl_list<<<B.n_tiles, NE_TILE, 0, st>>>(B);
 }
 
 void launch_step(const DevBatch& B, const Sched& S, bool mixed, const long long* step_base, int j,

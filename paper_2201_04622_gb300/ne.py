@@ -24,7 +24,7 @@ NE_PATH_FL, NE_PATH_RS = 0, 1
 
 # every symbol include/ne.h declares
 SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_set_theta", "ne_ctx_get_theta",
-           "ne_ctx_set_tuning", "ne_last_error", "ne_create_crystal", "ne_eam_energy_forces",
+           "ne_ctx_set_tuning", "ne_ctx_counters", "ne_last_error", "ne_create_crystal", "ne_eam_energy_forces",
            "ne_spring_forces", "ne_eam_backward", "ne_noise", "ne_init_velocities", "ne_langevin_step",
            "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment",
            "ne_profile_segment",
@@ -75,6 +75,7 @@ def load(build_if_missing: bool = True):
                 "ne_ctx_set_theta": [p, p, p],
                 "ne_ctx_get_theta": [p, p, p],
                 "ne_ctx_set_tuning": [p, i],
+                "ne_ctx_counters": [p, p],
                 "ne_last_error": [p, p, p, i],
                 "ne_create_crystal": [i, d, i, i, i, p, p, p],
                 "ne_eam_energy_forces": [p, i, p, i, p, p, p, p, p],
@@ -176,6 +177,13 @@ def ne_ctx_get_theta(ctx, theta, stream=None):
 
 def ne_ctx_set_tuning(ctx, threads_per_atom):
     _err(ctx, load().ne_ctx_set_tuning(ctx, int(threads_per_atom)), "ne_ctx_set_tuning")
+
+
+def ne_ctx_counters(ctx):
+    """Number of per-replica neighbour-list builds so far."""
+    v = C.c_longlong()
+    _err(ctx, load().ne_ctx_counters(ctx, C.byref(v)), "ne_ctx_counters")
+    return v.value
 
 
 def ne_last_error(ctx):

@@ -80,8 +80,18 @@ def test_noise_matches_oracle_philox(ctx):
         # libm vs CUDA log/sincospi differ in the last bits only; any
         # difference in a Philox word would move a normal by O(1)
         assert np.abs(N(z) - zo).max() < 1e-12
+        # the FP32 draw keeps the top 24 bits of each Philox word of the
+        # oracle; Box-Muller of those uniforms (numpy FP64) is the reference
         ne.ne_noise(seed, rep, stream, step, z, ne.NE_MIXED)
-        assert np.abs(N(z) - zo).max() < 2e-5
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        w = np.array([O.philox([a, step & 0xFFFFFFFF, step >> 32, (rep << 4) | stream], key)
+                      for a in range(n)], dtype=np.float64)
+        u = (np.floor(w / 256.0) + 0.5) * 2.0 ** -24
+        r0, r1 = np.sqrt(-2 * np.log(u[:, 0])), np.sqrt(-2 * np.log(u[:, 2]))
+        z24 = np.stack([r0 * np.cos(2 * np.pi * u[:, 1]), r0 * np.sin(2 * np.pi * u[:, 1]),
+                        r1 * np.cos(2 * np.pi * u[:, 3])], axis=1)
+        assert np.abs(N(z) - z24).max() < 4e-6 * (1 + np.abs(z24).max())
+        assert np.abs(N(z) - zo).max() < 1e-3
 
 
 # ---------------------------------------------------------------- EAM
@@ -296,7 +306,12 @@ def test_msd_fit_matches_oracle(ctx, pot):
 
 
 # ---------------------------------------------------------------- backward
-@pytest.mark.parametrize("prec,tol", [(ne.NE_FP64, 1e-10), (ne.NE_MIXED, 1e-5)])
+# Mixed precision: the knot weights depend on u = r/h - k; an FP32 pair
+# distance carries ~2^-24 r ~ 3e-7 A of rounding against h = r_c/4999 ~
+# 1.06e-3 A, so u moves by ~3e-4 and each pair's weight is split between
+# neighbouring knots with that error; summed over pairs that is ~1e-4 of the
+# gradient norm.  FP64: 1e-10.
+@pytest.mark.parametrize("prec,tol", [(ne.NE_FP64, 1e-10), (ne.NE_MIXED, 1e-3)])
 def test_backward_matches_oracle_gradient(ctx, pot, prec, tol):
     p, th = pot
     x0, box = crystal(O.BCC, 6)
@@ -308,7 +323,7 @@ def test_backward_matches_oracle_gradient(ctx, pot, prec, tol):
     ne.ne_eam_backward(ctx, prec, T(x), box, 2.0, gx, gth)
     assert rel(N(gth), 2.0 * go) < tol
     for w in range(3):
-        assert rel(N(gth)[w], 2.0 * go[w]) < 10 * tol
+        assert rel(N(gth)[w], 2.0 * go[w]) < 3 * tol
     assert rel(N(gx), -2.0 * fo) < (1e-10 if prec == ne.NE_FP64 else 5e-5)
 
 
