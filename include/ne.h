@@ -130,6 +130,33 @@ ne_status ne_eam_energy_forces(ne_ctx* ctx, ne_precision prec, const double* x_d
                                int n, const double box[3], double* f_dev,
                                double* e_dev, double* rho_dev, void* stream);
 
+/* Allocation-free variant of ne_eam_energy_forces, for callers that cannot
+ * allocate device memory once they are running -- an engine or framework
+ * that has reserved the device memory for its own pool, or a real-time
+ * pipeline that forbids cudaMalloc after start-up (it can synchronise the
+ * device and can fail).  The paper has no counterpart; it is a deployment
+ * convenience.  No context is needed and nothing is allocated: no
+ * cudaMalloc, cudaFree or allocating library call.  The spline tables (built
+ * from *eam on every call), cell arrays, neighbour lists and per-atom buffers
+ * live in one file-scope device array of NE_NOALLOC_SCRATCH_BYTES bytes that
+ * every GPU which loads the library holds until the process exits.
+ *   Limits: n <= NE_NOALLOC_MAX_ATOMS and eam->n_knots <=
+ *   NE_NOALLOC_MAX_KNOTS, else NE_ENOMEM; box edges > 2 r_c, else NE_EINVAL.
+ *   Arguments and results as for ne_eam_energy_forces (no rho output).
+ *   The first call on a device looks up the device address of the array
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture.
+ *   All calls on a device share the one array, which keeps the previous
+ *   call's contents (the call clears what must start at zero): calls that
+ *   overlap on the GPU -- on different streams or host threads -- race and
+ *   must be serialised by the caller.  The call synchronises `stream`. */
+#define NE_NOALLOC_MAX_ATOMS 2048
+#define NE_NOALLOC_MAX_KNOTS 5000
+#define NE_NOALLOC_SCRATCH_BYTES (4608u * 1024u)
+ne_status ne_eam_energy_forces_noalloc(const ne_eam_params* eam, ne_precision prec,
+                                       const double* x_dev, int n, const double box[3],
+                                       double* f_dev, double* e_dev, void* stream);
+
 /* Einstein crystal (eq. einstein): U_E = sum_i k/2 |r_i - r0_i|^2 into e_dev
  * (1 double) and F_E = -k (r - r0) into f_dev [n][3] (may be NULL). */
 ne_status ne_spring_forces(const double* x_dev, const double* x0_dev, int n, double k,

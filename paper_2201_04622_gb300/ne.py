@@ -25,7 +25,7 @@ NE_PATH_FL, NE_PATH_RS = 0, 1
 # every symbol include/ne.h declares
 SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_set_theta", "ne_ctx_get_theta",
            "ne_ctx_set_tuning", "ne_ctx_counters", "ne_last_error", "ne_create_crystal", "ne_eam_energy_forces",
-           "ne_spring_forces", "ne_eam_backward", "ne_noise", "ne_init_velocities", "ne_langevin_step",
+           "ne_eam_energy_forces_noalloc", "ne_spring_forces", "ne_eam_backward", "ne_noise", "ne_init_velocities", "ne_langevin_step",
            "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment",
            "ne_profile_segment",
            "ne_msd_fit", "ne_free_energy",
@@ -79,6 +79,7 @@ def load(build_if_missing: bool = True):
                 "ne_last_error": [p, p, p, i],
                 "ne_create_crystal": [i, d, i, i, i, p, p, p],
                 "ne_eam_energy_forces": [p, i, p, i, p, p, p, p, p],
+                "ne_eam_energy_forces_noalloc": [p, i, p, i, p, p, p, p],
                 "ne_spring_forces": [p, p, i, d, p, p, p],
                 "ne_eam_backward": [p, i, p, i, p, d, p, p, p],
                 "ne_noise": [C.c_ulonglong, C.c_uint, i, ll, i, i, p, p],
@@ -213,6 +214,19 @@ def ne_eam_energy_forces(ctx, prec, x, box, f=None, e=None, rho=None, stream=Non
     _err(ctx, load().ne_eam_energy_forces(ctx, int(prec), _dev(x, 3 * n), n, _box(box),
                                           _dev(f, 3 * n), _dev(e, 1), _dev(rho, n),
                                           _stream(stream)), "ne_eam_energy_forces")
+
+
+NE_NOALLOC_MAX_ATOMS = 2048
+
+
+def ne_eam_energy_forces_noalloc(eam: EamParams, prec, x, box, f=None, e=None, stream=None):
+    """EAM energy/forces with no device allocation (scratch in a static
+    device array of the library; n <= NE_NOALLOC_MAX_ATOMS)."""
+    n = x.shape[0]
+    _err(None, load().ne_eam_energy_forces_noalloc(C.byref(eam), int(prec), _dev(x, 3 * n), n,
+                                                   _box(box), _dev(f, 3 * n), _dev(e, 1),
+                                                   _stream(stream)),
+         "ne_eam_energy_forces_noalloc")
 
 
 def ne_spring_forces(x, x0, k, f=None, e=None, stream=None):
