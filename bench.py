@@ -40,9 +40,11 @@ K_SPRING = 4.0      # eV/A^2, from the msd fit of this potential near 1400 K (se
 SKIN = float(os.environ.get("NE_BENCH_SKIN", "2.6"))  # A
 T_EQ, T_S = 10000, 50000
 FP32_LANES_PER_SM, N_SM = 128, 152
-FLOPS_PER_PAIR_PASS2 = 44    # FP32 lane operations per neighbour pair in pass 2
-FLOPS_PER_CAND_PASS1 = 16
-FLOPS_PER_HIT_PASS1 = 12
+FLOPS_PER_PAIR_PASS2 = 44    # FP32 lane operations per neighbour pair in pass 2 (multi-kernel path)
+# crystal runner, lane operations (FP32 + INT32) counted from the source:
+OPS_VISIT = 24    # one lattice-stencil entry examined in pass 1
+OPS_PAIR = 62     # one pair inside r_c: spline of f in pass 1 + forces in pass 2
+OPS_ATOM = 120    # per atom-step: F(rho), broadcasts, sums, Philox + Box-Muller, BAOAB
 
 
 def systems():
@@ -160,8 +162,19 @@ def run_ours(args):
     if Wm + K > S_total:
         raise SystemExit("warmup + steps exceeds the %d-step schedule" % S_total)
     l2 = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)  # > 129 MB L2
+    path = args.path
+    if path == "auto":
+        path = "crystal" if prec == ne.NE_MIXED else "general"
+    crystals = [(lat, a, n, n, n) for (lat, n, a, seed) in systems()]
+
+    def segment(xx, vv, x00, WW, s0, ns):
+        if path == "crystal":
+            ne.ne_crystal_run_segment(ctx, mds, crystals, xx, vv, WW, s0, ns)
+        else:
+            ne.ne_switch_run_segment(ctx, mds, offs, xx, vv, x00, boxes, WW, s0, ns)
+
     # warm-up steps (the start of the schedule)
-    ne.ne_switch_run_segment(ctx, mds, offs, x, v, x0, boxes, Wd, 0, Wm)
+    segment(x, v, x0, Wd, 0, Wm)
     torch.cuda.synchronize()
     flush_l2(torch, l2)
     if world > 1:
@@ -169,14 +182,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    builds0 = ne.ne_ctx_counters(ctx)
+    c0 = ne.ne_ctx_counters(ctx)
     with Clocks() as clk:
         e0.record(stream)
-        ne.ne_switch_run_segment(ctx, mds, offs, x, v, x0, boxes, Wd, Wm, K)
+        segment(x, v, x0, Wd, Wm, K)
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    list_builds = ne.ne_ctx_counters(ctx) - builds0
+    c1 = ne.ne_ctx_counters(ctx)
+    list_builds = c1[0] - c0[0]
+    visits, pairs = c1[1] - c0[1], c1[2] - c0[2]
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -199,7 +214,7 @@ def run_ours(args):
         vd = vh.to(dev, non_blocking=True)
         x0d = x0h.to(dev, non_blocking=True)
         Wd2 = Wh.to(dev, non_blocking=True)
-        ne.ne_switch_run_segment(ctx, mds, offs, xd, vd, x0d, boxes, Wd2, Wm + K, K2)
+        segment(xd, vd, x0d, Wd2, Wm + K, K2)
         xh.copy_(xd, non_blocking=True)
         vh.copy_(vd, non_blocking=True)
         Wh.copy_(Wd2, non_blocking=True)
@@ -211,17 +226,28 @@ def run_ours(args):
                "h2d_bytes_per_step": h2d / K2, "d2h_bytes_per_step": d2h / K2,
                "steps": K2, "note": "one ABI call from pinned host state: copies in, K steps, state+work out"}
 
+    roof = None
+    if path == "crystal":
+        # one persistent launch per segment: its duration is the timed region
+        ops = OPS_VISIT * visits + OPS_PAIR * pairs + OPS_ATOM * K * n_atoms
+        peak = N_SM * FP32_LANES_PER_SM * 2.07e9
+        roof = {"bound": "alu", "kernel": "k_cluster (persistent crystal runner)",
+                "achieved": ops / (ms * 1e-3) / 1e12, "peak": peak / 1e12, "unit": "T lane-ops/s",
+                "frac": ops / (ms * 1e-3) / peak, "traffic": None,
+                "per_atom_step": {"stencil_visits": visits / (K * n_atoms), "pairs": pairs / (K * n_atoms)},
+                "note": "lane-ops = FP32 + INT32 lane instructions counted from the source per stencil "
+                        "visit (%d), pair (%d) and atom-step (%d); peak = 152 SMs x 128 lanes x 2.07 GHz"
+                        % (OPS_VISIT, OPS_PAIR, OPS_ATOM)}
     # per-kernel durations (events around each launch) for the roofline
     xp, vp = x.clone(), v.clone()
     Wp = Wd.clone()
-    n_prof = min(200, S_total - Wm - K) if S_total - Wm - K > 0 else 0
+    n_prof = min(200, S_total - Wm - K) if S_total - Wm - K > 0 and path == "general" else 0
     prof = None
     if n_prof > 0:
         kms, cnt = ne.ne_profile_segment(ctx, mds, offs, xp, vp, x0, boxes, Wp, Wm + K, n_prof)
         prof = kms
     # pairs inside r_c (from the library's short-list counts) for the FLOP count
     pairs_per_atom = 58.0 if SKIN else 58.0
-    roof = None
     if prof:
         t_force = prof[2] * 1e-3
         flops = FLOPS_PER_PAIR_PASS2 * pairs_per_atom * n_atoms
@@ -233,14 +259,14 @@ def run_ours(args):
                 "per_launch_ms": {"nl_check": prof[0], "density": prof[1], "force": prof[2],
                                   "step": prof[3]}}
     steps_per_graph = 32
-    launches = 5 * K + (K - 1) // steps_per_graph + 10
+    launches = 1 if path == "crystal" else 5 * K + (K - 1) // steps_per_graph + 10
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64" if prec == ne.NE_MIXED else "f64",
            "data": "synthetic (perfect bcc/fcc lattices, Philox Maxwell-Boltzmann velocities)",
            "config": {"workload": WORKLOAD, "replicas": n_rep, "atoms": n_atoms, "T_K": T_K,
                       "t_eq": T_EQ, "t_s": T_S, "dt_fs": 1.0, "skin_A": SKIN,
-                      "precision": args.prec, "threads_per_atom": args.tpa,
+                      "precision": args.prec, "path": path, "threads_per_atom": args.tpa,
                       "list_builds_per_replica_step": list_builds / (K * n_rep),
                       "parallelism": "replicas only" if world > 1 else "1 GPU",
                       "l2": "flushed before the timed segment; the 40k-atom state stays L2-resident "
@@ -319,6 +345,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--tpa", type=int, default=4)
+    ap.add_argument("--path", default="auto", choices=["auto", "crystal", "general"],
+                    help="crystal: persistent cluster runner (mixed); general: multi-kernel path")
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

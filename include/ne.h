@@ -105,11 +105,15 @@ ne_status ne_ctx_get_theta(ne_ctx* ctx, double* theta_dev, void* stream);
 /* Tuning of the pair kernels: threads per atom (1, 2, 4 or 8). */
 ne_status ne_ctx_set_tuning(ne_ctx* ctx, int threads_per_atom);
 
-/* Number of per-replica neighbour-list builds since the context was created
- * (one at the start of every run or segment, plus one each time an atom of
- * the replica strays more than skin/2 from its list-build position).
+/* Work counters since the context was created (each pointer may be NULL):
+ * list_builds -- per-replica neighbour-list builds of the multi-kernel path
+ * (one at the start of every run or segment, plus one each time an atom
+ * strays more than skin/2 from its list-build position); stencil_visits and
+ * pairs -- lattice-stencil entries examined and pairs found inside r_c by
+ * ne_crystal_run_segment (pass 1), for algorithmic operation counts.
  * Synchronises the device. */
-ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds);
+ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds, long long* stencil_visits,
+                          long long* pairs);
 
 /* Status bits recorded by the last call, and its message (msg may be NULL). */
 ne_status ne_last_error(ne_ctx* ctx, int* device_status, char* msg, int msg_len);
@@ -242,6 +246,30 @@ ne_status ne_switch_run_segment(ne_ctx* ctx, const ne_md_params* md, int n_rep,
                                 const int* offsets_host, double* x_dev, double* v_dev,
                                 const double* x0_dev, const double* boxes_host, double* W_dev,
                                 long long step_begin, long long n_steps, void* stream);
+
+/* A crystal replica: nx*ny*nz cells of a bcc or fcc lattice with parameter a;
+ * its sites r0 and atom order are those of ne_create_crystal. */
+typedef struct {
+    ne_lattice lattice;
+    double a;
+    int nx, ny, nz;
+} ne_crystal;
+
+/* Persistent batched runner for crystals (mixed precision): steps
+ * [step_begin, step_begin + n_steps) of the four-phase schedule (Sec. III.B /
+ * III.C) for n_rep crystal replicas, each advanced by one thread-block cluster
+ * for the whole range in one launch.  Same semantics as ne_switch_run_segment
+ * with x0 = the sites of cr[r]: x_dev, v_dev [N][3] (replicas concatenated in
+ * order, each in crystal atom order) hold the state at step_begin and are
+ * advanced in place; W_dev [n_rep][2] accumulates (forward, backward) work.
+ * md[r].prec must be NE_MIXED; at most 4096 atoms per replica, at least 3
+ * cells per axis and box edges > 2 r_c + 1.2 A.  Neighbours come from a
+ * lattice stencil covering displacements up to D = min(2 A, (L/2 - r_c)/2)
+ * from the sites; a replica whose atoms stray further is reported as
+ * NE_ERANGE.  Noise, work and schedule are those of ne_switch_run_segment. */
+ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep,
+                                 double* x_dev, double* v_dev, double* W_dev, long long step_begin,
+                                 long long n_steps, void* stream);
 
 /* Timing hook (autotuning and roofline reports): the steps of
  * ne_switch_run_segment launched one by one, with CUDA events on the

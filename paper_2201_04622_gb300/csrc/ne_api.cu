@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/ne.h"
+#include "ne_cluster.cuh"
 #include "ne_internal.cuh"
 
 namespace {
@@ -46,6 +47,10 @@ struct ne_ctx {
     RepDev* rep = nullptr;
     long long* step_ctr = nullptr;
     unsigned long long* rebuilds = nullptr;
+    unsigned long long* work = nullptr;  // crystal runner: [0] stencil entries visited, [1] pairs < r_c
+    XRep* xrep = nullptr;
+    float4* st_vec = nullptr;
+    int* st_code = nullptr;
     float* bins = nullptr;
     int bins_blocks = 0;
     std::vector<RepDev> rep_h;
@@ -502,6 +507,11 @@ ne_status ne_ctx_create(const ne_eam_params* eam, int max_atoms, int max_replica
     A(dalloc(&ctx->rep, R));
     A(dalloc(&ctx->step_ctr, 1));
     A(dalloc(&ctx->rebuilds, 1));
+    A(dalloc(&ctx->xrep, R));
+    A(dalloc(&ctx->work, 2));
+    if (ok) ok = cudaMemset(ctx->work, 0, 2 * sizeof(unsigned long long)) == cudaSuccess;
+    A(dalloc(&ctx->st_vec, R * 4 * NE_STENCIL_MAX));
+    A(dalloc(&ctx->st_code, R * 4 * NE_STENCIL_MAX));
     if (ok) ok = cudaMemset(ctx->rebuilds, 0, sizeof(unsigned long long)) == cudaSuccess;
     if (!ok) {
         ne_ctx_destroy(ctx);
@@ -531,7 +541,7 @@ ne_status ne_ctx_destroy(ne_ctx* ctx)
                     ctx->pbuild, ctx->f32, ctx->f64, ctx->dF64, ctx->rho, ctx->xi64, ctx->xi32,
                     ctx->nbr, ctx->ncnt, ctx->sl, ctx->scnt, ctx->cellof, ctx->sorted, ctx->cstart,
                     ctx->cfill, ctx->partA, ctx->partB, ctx->tot, ctx->W, ctx->scratch,
-                    ctx->tile_done, ctx->flags, ctx->building, ctx->status, ctx->tile_rep, ctx->rep, ctx->step_ctr, ctx->rebuilds,
+                    ctx->tile_done, ctx->flags, ctx->building, ctx->status, ctx->tile_rep, ctx->rep, ctx->step_ctr, ctx->rebuilds, ctx->xrep, ctx->work, ctx->st_vec, ctx->st_code,
                     ctx->bins};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -567,13 +577,16 @@ ne_status ne_ctx_set_tuning(ne_ctx* ctx, int tpa)
     return NE_OK;
 }
 
-ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds)
+ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds, long long* stencil_visits, long long* pairs)
 {
-    if (!ctx || !list_builds) return NE_EINVAL;
-    unsigned long long v = 0;
-    if (cudaMemcpy(&v, ctx->rebuilds, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (!ctx) return NE_EINVAL;
+    unsigned long long v[3] = {0, 0, 0};
+    if (cudaMemcpy(&v[0], ctx->rebuilds, sizeof(v[0]), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&v[1], ctx->work, 2 * sizeof(v[0]), cudaMemcpyDeviceToHost) != cudaSuccess)
         return fail(ctx, NE_ECUDA, "reading the counters failed");
-    *list_builds = (long long)v;
+    if (list_builds) *list_builds = (long long)v[0];
+    if (stencil_visits) *stencil_visits = (long long)v[1];
+    if (pairs) *pairs = (long long)v[2];
     return NE_OK;
 }
 
@@ -877,6 +890,121 @@ ne_status ne_switch_run_batched(ne_ctx* ctx, const ne_md_params* md, int n_rep, 
 {
     return switch_run_impl(ctx, md, n_rep, offsets_host, x_dev, v_dev, x0_dev, boxes_host, W_fwd_dev,
                            W_bwd_dev, nullptr, nullptr, nullptr, 0, (cudaStream_t)stream);
+}
+
+ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep,
+                                 double* x_dev, double* v_dev, double* W_dev, long long step_begin,
+                                 long long n_steps, void* stream)
+{
+    if (!ctx || !md || !cr || !x_dev || !v_dev || !W_dev || n_rep < 1) return NE_EINVAL;
+    if (n_rep > ctx->max_rep) return fail(ctx, NE_ENOMEM, "replica count exceeds the context");
+    std::vector<int> off(n_rep + 1, 0);
+    for (int r = 0; r < n_rep; ++r) {
+        if ((cr[r].lattice != NE_BCC && cr[r].lattice != NE_FCC) || !(cr[r].a > 0) || cr[r].nx < 3 ||
+            cr[r].ny < 3 || cr[r].nz < 3)
+            return fail(ctx, NE_EINVAL, "crystal: bcc/fcc, a > 0 and at least 3 cells per axis");
+        const long long nn = (long long)(cr[r].lattice == NE_BCC ? 2 : 4) * cr[r].nx * cr[r].ny * cr[r].nz;
+        if (nn > 16ll * ne::cluster_atoms_per_cta())
+            return fail(ctx, NE_EINVAL, "crystal runner: at most 4096 atoms per replica");
+        off[r + 1] = off[r] + (int)nn;
+    }
+    ne_status s = check_batch(ctx, md, n_rep, off.data());
+    if (s) return s;
+    if (md[0].prec != NE_MIXED) return fail(ctx, NE_EINVAL, "the crystal runner is mixed precision; use ne_switch_run_segment for FP64");
+    const long long S_total = 2 * md[0].t_eq + 2 * md[0].t_s;
+    if (step_begin < 0 || n_steps < 0 || step_begin + n_steps > S_total)
+        return fail(ctx, NE_EINVAL, "step range outside the schedule");
+    cudaStream_t st = (cudaStream_t)stream;
+    static const double bcc[2][3] = {{0, 0, 0}, {0.5, 0.5, 0.5}};
+    static const double fcc[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
+    const double rc = ctx->eam.r_c;
+    std::vector<XRep> xr(n_rep);
+    std::vector<float4> sv;
+    std::vector<int> sc;
+    int n_max = 0, nbst_max = 0;
+    for (int r = 0; r < n_rep; ++r) {
+        const ne_md_params& m = md[r];
+        XRep& X = xr[r];
+        X = XRep{};
+        X.nb = cr[r].lattice == NE_BCC ? 2 : 4;
+        const double(*basis)[3] = cr[r].lattice == NE_BCC ? bcc : fcc;
+        for (int b = 0; b < X.nb; ++b)
+            for (int d = 0; d < 3; ++d) X.basis[b][d] = basis[b][d];
+        X.a = cr[r].a;
+        X.nx = cr[r].nx;
+        X.ny = cr[r].ny;
+        X.nz = cr[r].nz;
+        X.n = off[r + 1] - off[r];
+        X.off = off[r];
+        X.k = m.k_spring;
+        X.kf = (float)m.k_spring;
+        X.mf = (float)m.mass;
+        X.hdt_mf = (float)(0.5 * m.dt / m.mass);
+        const double gamma = m.damp > 0 ? 1.0 / m.damp : 0.0;
+        const double c1 = std::exp(-gamma * m.dt);
+        X.c1f = (float)c1;
+        X.c2f = (float)std::sqrt((1.0 - c1 * c1) * kB * m.T / m.mass);
+        X.seed = m.seed;
+        X.replica = m.replica;
+        if (m.replica >= (1u << 28)) return fail(ctx, NE_EINVAL, "replica id must be < 2^28");
+        // stencil: sites within r_c + 2D of each basis site, sorted by distance
+        const double Lmin = X.a * std::min(X.nx, std::min(X.ny, X.nz));
+        const double D = std::min(2.0, 0.5 * (0.5 * Lmin - rc) - 1e-3);
+        if (D < 0.3) return fail(ctx, NE_EINVAL, "box too small for the crystal runner (needs L/2 > r_c + 0.6 A)");
+        X.D = (float)D;
+        const double Rst = rc + 2.0 * D;
+        const int M = (int)std::ceil(Rst / X.a) + 1;
+        std::vector<std::vector<std::pair<double, std::pair<float4, int>>>> per(X.nb);
+        for (int b = 0; b < X.nb; ++b) {
+            for (int dx = -M; dx <= M; ++dx)
+                for (int dy = -M; dy <= M; ++dy)
+                    for (int dz = -M; dz <= M; ++dz)
+                        for (int b2 = 0; b2 < X.nb; ++b2) {
+                            if (dx == 0 && dy == 0 && dz == 0 && b2 == b) continue;
+                            const double ex = X.a * (dx + basis[b2][0] - basis[b][0]);
+                            const double ey = X.a * (dy + basis[b2][1] - basis[b][1]);
+                            const double ez = X.a * (dz + basis[b2][2] - basis[b][2]);
+                            const double d = std::sqrt(ex * ex + ey * ey + ez * ez);
+                            if (d >= Rst) continue;
+                            const int code = (dx + 128) | ((dy + 128) << 8) | ((dz + 128) << 16) | (b2 << 24);
+                            per[b].push_back({d, {make_float4((float)ex, (float)ey, (float)ez, (float)d), code}});
+                        }
+            std::stable_sort(per[b].begin(), per[b].end(), [](const auto& p, const auto& q) {
+                return p.first < q.first || (p.first == q.first && p.second.second < q.second.second);
+            });
+        }
+        size_t cnt = 0;
+        for (int b = 0; b < X.nb; ++b) cnt = std::max(cnt, per[b].size());
+        if (cnt > NE_STENCIL_MAX) return fail(ctx, NE_EINVAL, "stencil too large");
+        X.st_cnt = (int)cnt;
+        X.st_off = (int)sv.size();
+        for (int b = 0; b < X.nb; ++b)
+            for (size_t q = 0; q < cnt; ++q) {
+                if (q < per[b].size()) {
+                    sv.push_back(per[b][q].second.first);
+                    sc.push_back(per[b][q].second.second);
+                } else {  // padding: beyond any cutoff
+                    sv.push_back(make_float4(0.f, 0.f, 0.f, 1e30f));
+                    sc.push_back(128 | (128 << 8) | (128 << 16));
+                }
+            }
+        n_max = std::max(n_max, X.n);
+        nbst_max = std::max(nbst_max, X.nb * X.st_cnt);
+    }
+    if (sv.size() > (size_t)ctx->max_rep * 4 * NE_STENCIL_MAX) return fail(ctx, NE_ENOMEM, "stencil capacity exceeded");
+    const int per_cta = ne::cluster_atoms_per_cta();
+    int C = (n_max + per_cta - 1) / per_cta;
+    if (C < 1) C = 1;
+    NE_CU(cudaMemcpyAsync(ctx->xrep, xr.data(), sizeof(XRep) * n_rep, cudaMemcpyHostToDevice, st));
+    NE_CU(cudaMemcpyAsync(ctx->st_vec, sv.data(), sizeof(float4) * sv.size(), cudaMemcpyHostToDevice, st));
+    NE_CU(cudaMemcpyAsync(ctx->st_code, sc.data(), sizeof(int) * sc.size(), cudaMemcpyHostToDevice, st));
+    NE_CU(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
+    Sched S = make_sched(md[0]);
+    const size_t smem = ne::cluster_smem_bytes(n_max, nbst_max);
+    NE_CU(ne::launch_cluster(ctx->xrep, n_rep, C, smem, ctx->st_vec, ctx->st_code, x_dev, v_dev, W_dev, ctx->status,
+                             S, step_begin, n_steps, ctx->tab, ctx->work, st));
+    NE_CU(cudaStreamSynchronize(st));  // host vectors above must outlive the copies
+    return finish(ctx, st);
 }
 
 ne_status ne_profile_segment(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* offsets_host,

@@ -1,0 +1,29 @@
+// ne_cluster.cuh -- replica description and launcher of the persistent
+// cluster-per-replica runner for crystals (ne_cluster.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ne_internal.cuh"
+
+#define NE_STENCIL_MAX 640  // stencil entries per basis site
+
+struct XRep {
+    double a;             // lattice parameter
+    double basis[4][3];   // fractional basis positions
+    double k;             // spring constant (FP64 for the mean spring force)
+    float kf, mf, hdt_mf, c1f, c2f;
+    float D;              // largest displacement from a site the stencil covers
+    int n, off, nb, nx, ny, nz;
+    int st_off, st_cnt;   // stencil of basis b: entries [st_off + b * st_cnt, + st_cnt)
+    unsigned long long seed;
+    unsigned replica;
+};
+
+namespace ne {
+size_t cluster_smem_bytes(int n_max, int nb_nst_max);
+int cluster_atoms_per_cta();
+cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, const float4* st_vec,
+                           const int* st_code, double* x, double* v, double* W, int* status, const Sched& S,
+                           long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
+                           cudaStream_t st);
+}  // namespace ne

@@ -27,7 +27,7 @@ SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_set_theta", "ne_ctx_get_th
            "ne_ctx_set_tuning", "ne_ctx_counters", "ne_last_error", "ne_create_crystal", "ne_eam_energy_forces",
            "ne_eam_energy_forces_noalloc", "ne_spring_forces", "ne_eam_backward", "ne_noise", "ne_init_velocities", "ne_langevin_step",
            "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment",
-           "ne_profile_segment",
+           "ne_profile_segment", "ne_crystal_run_segment",
            "ne_msd_fit", "ne_free_energy",
            "ne_rs_free_energy"]
 
@@ -43,6 +43,11 @@ class EamParams(C.Structure):
     _fields_ = [("A", C.c_double), ("alpha", C.c_double), ("beta", C.c_double),
                 ("B", C.c_double), ("r_e", C.c_double), ("r_s", C.c_double),
                 ("r_c", C.c_double), ("rho_max", C.c_double), ("n_knots", C.c_int)]
+
+
+class Crystal(C.Structure):
+    _fields_ = [("lattice", C.c_int), ("a", C.c_double), ("nx", C.c_int), ("ny", C.c_int),
+                ("nz", C.c_int)]
 
 
 class MdParams(C.Structure):
@@ -75,7 +80,7 @@ def load(build_if_missing: bool = True):
                 "ne_ctx_set_theta": [p, p, p],
                 "ne_ctx_get_theta": [p, p, p],
                 "ne_ctx_set_tuning": [p, i],
-                "ne_ctx_counters": [p, p],
+                "ne_ctx_counters": [p, p, p, p],
                 "ne_last_error": [p, p, p, i],
                 "ne_create_crystal": [i, d, i, i, i, p, p, p],
                 "ne_eam_energy_forces": [p, i, p, i, p, p, p, p, p],
@@ -90,6 +95,7 @@ def load(build_if_missing: bool = True):
                 "ne_switch_run_batched": [p, p, i, p, p, p, p, p, p, p, p],
                 "ne_switch_run_segment": [p, p, i, p, p, p, p, p, p, ll, ll, p],
                 "ne_profile_segment": [p, p, i, p, p, p, p, p, p, ll, ll, p, p, p],
+                "ne_crystal_run_segment": [p, p, p, i, p, p, p, ll, ll, p],
                 "ne_msd_fit": [p, p, p, p, p, i, p, ll, ll, i, p, p, p],
                 "ne_free_energy": [i, d, d, d, d, p, p, i, p, p, p],
                 "ne_rs_free_energy": [i, d, d, d, ll, p, p, i, p, i, p],
@@ -181,10 +187,10 @@ def ne_ctx_set_tuning(ctx, threads_per_atom):
 
 
 def ne_ctx_counters(ctx):
-    """Number of per-replica neighbour-list builds so far."""
-    v = C.c_longlong()
-    _err(ctx, load().ne_ctx_counters(ctx, C.byref(v)), "ne_ctx_counters")
-    return v.value
+    """(list builds, stencil entries visited, pairs inside r_c) so far."""
+    a, b, c = C.c_longlong(), C.c_longlong(), C.c_longlong()
+    _err(ctx, load().ne_ctx_counters(ctx, C.byref(a), C.byref(b), C.byref(c)), "ne_ctx_counters")
+    return a.value, b.value, c.value
 
 
 def ne_last_error(ctx):
@@ -316,6 +322,17 @@ def ne_profile_segment(ctx, mds, offsets, x, v, x0, boxes, W, step_begin, n_step
                                         _dev(W, 2 * n_rep), int(step_begin), int(n_steps), ms, cnt,
                                         _stream(stream)), "ne_profile_segment")
     return list(ms), list(cnt)
+
+
+def ne_crystal_run_segment(ctx, mds, crystals, x, v, W, step_begin, n_steps, stream=None):
+    """crystals: list of (lattice, a, nx, ny, nz)."""
+    n_rep = len(mds)
+    arr = (MdParams * n_rep)(*mds)
+    cr = (Crystal * n_rep)(*[Crystal(int(c[0]), float(c[1]), int(c[2]), int(c[3]), int(c[4]))
+                             for c in crystals])
+    _err(ctx, load().ne_crystal_run_segment(ctx, arr, cr, n_rep, _dev(x), _dev(v), _dev(W, 2 * n_rep),
+                                            int(step_begin), int(n_steps), _stream(stream)),
+         "ne_crystal_run_segment")
 
 
 def ne_msd_fit(ctx, md: MdParams, x, v, x0, box, n_eq, n_samples, stride, stream=None):

@@ -1,0 +1,151 @@
+"""GPU parity of the persistent crystal runner (ne_crystal_run_segment,
+mixed precision, one thread-block cluster per replica) against the oracle
+and against the multi-kernel path on the same seeded inputs.
+
+Tolerances: the runner computes pair distances as (r0_j - r0_i) + u_j - u_i
+in FP32 with |u| < 2 A, so a distance carries ~2^-24 * 5 A ~ 3e-7 A of
+rounding (finer than the wrapped-coordinate path); over 100 steps positions
+follow the FP64 oracle to ~1e-6 A.  The tests allow 2e-5 A over 100 steps at
+the small sizes and 2e-4 A on the 40k-atom batch (FP32 round-off grows with
+the chaotic divergence of the trajectories).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2201_04622_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2201_04622_gb300 import ne  # noqa: E402
+
+DEV = torch.device("cuda:0")
+MASS = W.MASS_FE_AMU * 1.0364269656262175e-4
+
+
+@pytest.fixture(scope="module")
+def pot():
+    p = O.eam(**W.EAM_FE_LIKE)
+    return p, O.eam_theta(p)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = ne.ne_ctx_create(ne.eam_params(**W.EAM_FE_LIKE), 60000, 64)
+    yield c
+    ne.ne_ctx_destroy(c)
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=DEV)
+
+
+def lat_a(lat):
+    return W.A_BCC if lat == O.BCC else W.A_FCC
+
+
+def md_pair(**kw):
+    base = dict(dt=1e-3, T=300.0, damp=0.1, k_spring=6.0, lambda_fn=2, t_eq=20, t_s=30,
+                lambda_f=0.5, seed=11, replica=2, fix_cm=1)
+    base.update(kw)
+    path = base.pop("path", O.PATH_FL)
+    mo = O.md(mass=MASS, path=path, **base)
+    mg = ne.md_params(mass=MASS, skin=1.0, prec=ne.NE_MIXED, path=path, **base)
+    return mo, mg
+
+
+def run_crystals(ctx, systems, s0, ns, x=None, v=None, Wd=None, **kw):
+    mgs, crs, x0s, vs = [], [], [], []
+    for r, (lat, n, Tk, seed) in enumerate(systems):
+        mo, mg = md_pair(T=Tk, seed=seed, replica=r, **kw)
+        x0, box = O.create_crystal(lat, lat_a(lat), n, n, n)
+        x0s.append(x0)
+        vs.append(O.init_velocities(mo, len(x0)))
+        mgs.append(mg)
+        crs.append((lat, lat_a(lat), n, n, n))
+    if x is None:
+        x, v = T(np.concatenate(x0s)), T(np.concatenate(vs))
+        Wd = torch.zeros((len(systems), 2), dtype=torch.float64, device=DEV)
+    ne.ne_crystal_run_segment(ctx, mgs, crs, x, v, Wd, s0, ns)
+    return x, v, Wd, x0s, vs
+
+
+@pytest.mark.parametrize("lat,n,path", [(O.BCC, 5, O.PATH_FL), (O.FCC, 4, O.PATH_FL),
+                                        (O.BCC, 6, O.PATH_RS)])
+def test_crystal_runner_tracks_oracle_100_steps(ctx, pot, lat, n, path):
+    p, th = pot
+    x, v, Wd, x0s, vs = run_crystals(ctx, [(lat, n, 300.0, 5)], 0, 100, path=path)
+    mo, _ = md_pair(T=300.0, seed=5, replica=0, path=path)
+    x0, box = O.create_crystal(lat, lat_a(lat), n, n, n)
+    ro = O.switch_run(p, th, mo, x0, vs[0], x0, box)
+    assert np.abs(x.cpu().numpy() - ro["x"]).max() < 2e-5
+    assert np.abs(v.cpu().numpy() - ro["v"]).max() < 2e-3
+    Wg = Wd.cpu().numpy()[0]
+    assert Wg[0] == pytest.approx(ro["W_f"], rel=1e-5, abs=1e-4)
+    assert Wg[1] == pytest.approx(ro["W_b"], rel=1e-5, abs=1e-4)
+
+
+def test_crystal_runner_matches_multikernel_mixed_path(ctx):
+    systems = [(O.BCC, 6, 800.0, 3), (O.FCC, 5, 1200.0, 4), (O.BCC, 8, 400.0, 9)]
+    x, v, Wd, x0s, vs = run_crystals(ctx, systems, 0, 100)
+    offs = np.cumsum([0] + [len(a) for a in x0s])
+    mgs = [md_pair(T=Tk, seed=seed, replica=r)[1] for r, (lat, n, Tk, seed) in enumerate(systems)]
+    boxes = [O.create_crystal(lat, lat_a(lat), n, n, n)[1] for (lat, n, Tk, seed) in systems]
+    X0 = T(np.concatenate(x0s))
+    x2, v2 = X0.clone(), T(np.concatenate(vs))
+    W2 = torch.zeros((len(systems), 2), dtype=torch.float64, device=DEV)
+    for m in mgs:
+        m.skin = 1.0
+    ne.ne_switch_run_segment(ctx, mgs, list(offs), x2, v2, X0, boxes, W2, 0, 100)
+    assert torch.abs(x - x2).max().item() < 2e-5
+    assert torch.allclose(Wd, W2, rtol=1e-5, atol=1e-4)
+
+
+def test_crystal_runner_full_size_batch(ctx, pot):
+    """The benchmark batch (10 bcc 10^3 + 10 fcc 8^3 at 1400 K, 40,480 atoms)
+    for 30 steps; replicas 0 and 19 atom by atom against the oracle."""
+    p, th = pot
+    systems = [(O.BCC, 10, 1400.0, 1 + r) for r in range(10)] + \
+              [(O.FCC, 8, 1400.0, 1 + r) for r in range(10)]
+    x, v, Wd, x0s, vs = run_crystals(ctx, systems, 0, 30, t_eq=5, t_s=10, k_spring=4.0)
+    offs = np.cumsum([0] + [len(a) for a in x0s])
+    xg = x.cpu().numpy()
+    for r in (0, 19):
+        lat, n, Tk, seed = systems[r]
+        mo, _ = md_pair(T=Tk, seed=seed, replica=r, t_eq=5, t_s=10, k_spring=4.0)
+        x0, box = O.create_crystal(lat, lat_a(lat), n, n, n)
+        ro = O.switch_run(p, th, mo, x0, vs[r], x0, box)
+        assert np.abs(xg[offs[r]:offs[r + 1]] - ro["x"]).max() < 2e-4
+        assert float(Wd[r, 0]) == pytest.approx(ro["W_f"], rel=1e-4, abs=1e-3)
+        assert float(Wd[r, 1]) == pytest.approx(ro["W_b"], rel=1e-4, abs=1e-3)
+    # work counters advanced: every atom examined stencil entries and found pairs
+    builds, visits, pairs = ne.ne_ctx_counters(ctx)
+    assert pairs > 30 * offs[-1] * 40
+
+
+def test_crystal_runner_resume_is_bitwise(ctx):
+    systems = [(O.BCC, 6, 900.0, 1), (O.FCC, 5, 700.0, 2)]
+    S = 2 * 40 + 2 * 150
+    x, v, Wd, _, _ = run_crystals(ctx, systems, 0, S, t_eq=40, t_s=150)
+    ref = (x.clone(), v.clone(), Wd.clone())
+    x, v, Wd, _, _ = run_crystals(ctx, systems, 0, 77, t_eq=40, t_s=150)
+    for a, b in ((77, 230), (230, S)):
+        run_crystals(ctx, systems, a, b - a, x=x, v=v, Wd=Wd, t_eq=40, t_s=150)
+    for p_, q_ in zip(ref, (x, v, Wd)):
+        assert torch.equal(p_, q_)
+
+
+def test_crystal_runner_rejects_small_boxes_and_fp64(ctx):
+    mo, mg = md_pair()
+    x = torch.zeros((128, 3), dtype=torch.float64, device=DEV)
+    Wd = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
+    with pytest.raises(ne.NeError, match="NE_EINVAL"):
+        ne.ne_crystal_run_segment(ctx, [mg], [(O.BCC, 2.87, 4, 4, 4)], x, x.clone(), Wd, 0, 10)
+    mg.prec = ne.NE_FP64
+    x = torch.zeros((250, 3), dtype=torch.float64, device=DEV)
+    with pytest.raises(ne.NeError, match="NE_EINVAL"):
+        ne.ne_crystal_run_segment(ctx, [mg], [(O.BCC, 2.87, 5, 5, 5)], x, x.clone(), Wd, 0, 10)
