@@ -49,6 +49,8 @@ struct ne_ctx {
     unsigned long long* rebuilds = nullptr;
     unsigned long long* work = nullptr;  // crystal runner: [0] stencil entries visited, [1] pairs < r_c
     XRep* xrep = nullptr;
+    double* lam_tab = nullptr;  // lambda of each step of a crystal-runner segment
+    long long lam_cap = 0;
     float4* st_vec = nullptr;
     int* st_code = nullptr;
     float* bins = nullptr;
@@ -541,7 +543,7 @@ ne_status ne_ctx_destroy(ne_ctx* ctx)
                     ctx->pbuild, ctx->f32, ctx->f64, ctx->dF64, ctx->rho, ctx->xi64, ctx->xi32,
                     ctx->nbr, ctx->ncnt, ctx->sl, ctx->scnt, ctx->cellof, ctx->sorted, ctx->cstart,
                     ctx->cfill, ctx->partA, ctx->partB, ctx->tot, ctx->W, ctx->scratch,
-                    ctx->tile_done, ctx->flags, ctx->building, ctx->status, ctx->tile_rep, ctx->rep, ctx->step_ctr, ctx->rebuilds, ctx->xrep, ctx->work, ctx->st_vec, ctx->st_code,
+                    ctx->tile_done, ctx->flags, ctx->building, ctx->status, ctx->tile_rep, ctx->rep, ctx->step_ctr, ctx->rebuilds, ctx->xrep, ctx->work, ctx->st_vec, ctx->st_code, ctx->lam_tab,
                     ctx->bins};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -905,7 +907,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
             return fail(ctx, NE_EINVAL, "crystal: bcc/fcc, a > 0 and at least 3 cells per axis");
         const long long nn = (long long)(cr[r].lattice == NE_BCC ? 2 : 4) * cr[r].nx * cr[r].ny * cr[r].nz;
         if (nn > 16ll * ne::cluster_atoms_per_cta())
-            return fail(ctx, NE_EINVAL, "crystal runner: at most 4096 atoms per replica");
+            return fail(ctx, NE_EINVAL, "crystal runner: at most 16 x 320 atoms per replica");
         off[r + 1] = off[r] + (int)nn;
     }
     ne_status s = check_batch(ctx, md, n_rep, off.data());
@@ -921,7 +923,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
     std::vector<XRep> xr(n_rep);
     std::vector<float4> sv;
     std::vector<int> sc;
-    int n_max = 0, nbst_max = 0;
+    int n_max = 0, nbst_max = 0, lut_max = 0;
     for (int r = 0; r < n_rep; ++r) {
         const ne_md_params& m = md[r];
         XRep& X = xr[r];
@@ -966,7 +968,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
                             const double ez = X.a * (dz + basis[b2][2] - basis[b][2]);
                             const double d = std::sqrt(ex * ex + ey * ey + ez * ez);
                             if (d >= Rst) continue;
-                            const int code = (dx + 128) | ((dy + 128) << 8) | ((dz + 128) << 16) | (b2 << 24);
+                            const int code = (dx + M) | ((dy + M) << 8) | ((dz + M) << 16) | (b2 << 24);
                             per[b].push_back({d, {make_float4((float)ex, (float)ey, (float)ez, (float)d), code}});
                         }
             std::stable_sort(per[b].begin(), per[b].end(), [](const auto& p, const auto& q) {
@@ -977,6 +979,8 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         for (int b = 0; b < X.nb; ++b) cnt = std::max(cnt, per[b].size());
         if (cnt > NE_STENCIL_MAX) return fail(ctx, NE_EINVAL, "stencil too large");
         X.st_cnt = (int)cnt;
+        X.st_margin = M;
+        lut_max = std::max(lut_max, X.nx + X.ny + X.nz + 6 * M);
         X.st_off = (int)sv.size();
         for (int b = 0; b < X.nb; ++b)
             for (size_t q = 0; q < cnt; ++q) {
@@ -985,7 +989,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
                     sc.push_back(per[b][q].second.second);
                 } else {  // padding: beyond any cutoff
                     sv.push_back(make_float4(0.f, 0.f, 0.f, 1e30f));
-                    sc.push_back(128 | (128 << 8) | (128 << 16));
+                    sc.push_back(M | (M << 8) | (M << 16));
                 }
             }
         n_max = std::max(n_max, X.n);
@@ -1000,9 +1004,30 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
     NE_CU(cudaMemcpyAsync(ctx->st_code, sc.data(), sizeof(int) * sc.size(), cudaMemcpyHostToDevice, st));
     NE_CU(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
     Sched S = make_sched(md[0]);
-    const size_t smem = ne::cluster_smem_bytes(n_max, nbst_max);
+    // shared memory: replica state, stencil, lists and sums, then as many r
+    // intervals of the (phi, f) tables, counted down from r_c, as still fit
+    int dev = 0, smem_max = 0;
+    NE_CU(cudaGetDevice(&dev));
+    NE_CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t base = (ne::cluster_smem_bytes(n_max, nbst_max, lut_max) + 15) & ~(size_t)15;
+    if (base > (size_t)smem_max) return fail(ctx, NE_EINVAL, "replica too large for the crystal runner");
+    const int nk = ctx->eam.n_knots;
+    const long long fit = ((long long)smem_max - (long long)base) / (2 * (long long)sizeof(float4));
+    const int n_int = (int)std::min<long long>(nk - 1, fit);
+    const int k_lo = nk - 1 - n_int;
+    const size_t smem = base + (size_t)n_int * 2 * sizeof(float4);
+    if (n_steps + 2 > ctx->lam_cap) {
+        if (ctx->lam_tab) {
+            NE_CU(cudaStreamSynchronize(st));
+            cudaFree(ctx->lam_tab);
+            ctx->lam_tab = nullptr;
+            ctx->lam_cap = 0;
+        }
+        NE_CU(cudaMalloc((void**)&ctx->lam_tab, sizeof(double) * (size_t)(n_steps + 2)));
+        ctx->lam_cap = n_steps + 2;
+    }
     NE_CU(ne::launch_cluster(ctx->xrep, n_rep, C, smem, ctx->st_vec, ctx->st_code, x_dev, v_dev, W_dev, ctx->status,
-                             S, step_begin, n_steps, ctx->tab, ctx->work, st));
+                             S, step_begin, n_steps, ctx->tab, ctx->work, k_lo, ctx->lam_tab, st));
     NE_CU(cudaStreamSynchronize(st));  // host vectors above must outlive the copies
     return finish(ctx, st);
 }

@@ -29,6 +29,7 @@
 // FP32; positions x (registers, FP64), rho accumulation (FP32 chunks of 8 into
 // FP64), the work W and all replica sums in FP64 (CTA sums as FP32
 // double-float pairs, summed across the cluster in FP64).
+#include <algorithm>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -39,15 +40,17 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int THREADS = 512;
+constexpr int THREADS = 640;
 constexpr int TPA = 2;
-constexpr int SLOTS = THREADS / TPA;  // atoms per CTA
-constexpr int SLMAX = 96;             // short-list entries per atom
+constexpr int SLOTS = THREADS / TPA;  // atoms per CTA (one CTA per SM)
+constexpr int SLMAX = 80;             // short-list entries per atom
 constexpr int NWARP = THREADS / 32;
 
 // partial sums
 enum { A_UEMB = 0, A_UPAIR, A_FX, A_FY, A_FZ, A_XX, A_XY, A_XZ, NA_ };
 enum { B_UE = 0, B_UX, B_UY, B_UZ, B_U2, B_KE, B_UMAX, NB_ };
+// values per warp in the reduction scratch: the larger of the two reductions
+constexpr int NRED = (int)NA_ > (int)NB_ ? (int)NA_ : (int)NB_;
 
 struct dfl {
     float hi, lo;
@@ -76,66 +79,44 @@ __device__ __forceinline__ void warp_df_sum(dfl (&v)[NV])
         }
 }
 
-// CTA sum of NV double-float values -> doubles (thread 0 returns them in out).
-template <int NV>
-__device__ void cta_sum(dfl (&v)[NV], float* s_red, double* out)
+// CTA sums of NV double-float values (and, when HASMAX, the maximum of mx),
+// written into slot `rank` of the slot arrays of every CTA of the cluster:
+// sums to dst[rank * NV + q] (FP64), the maximum to mslot[rank] (FP32).  The
+// warps' partials are combined in double-float (FP32 arithmetic) and
+// converted to FP64 once.  One __syncthreads; the caller separates two uses
+// of s_red by a cluster barrier.
+template <int NV, bool HASMAX>
+__device__ __forceinline__ void cta_sum_bcast(cg::cluster_group& cluster, dfl (&v)[NV], float mx, float* s_red,
+                                              double* dst, float* mslot, int rank, int C)
 {
     warp_df_sum<NV>(v);
+    if (HASMAX)
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0)
+    constexpr int NS = NV + (HASMAX ? 1 : 0);
+    static_assert(NS <= NRED, "reduction scratch too small");
+    if (l == 0) {
         for (int q = 0; q < NV; ++q) {
-            s_red[(w * NV + q) * 2] = v[q].hi;
-            s_red[(w * NV + q) * 2 + 1] = v[q].lo;
+            s_red[(w * NRED + q) * 2] = v[q].hi;
+            s_red[(w * NRED + q) * 2 + 1] = v[q].lo;
         }
+        if (HASMAX) s_red[(w * NRED + NV) * 2] = mx;
+    }
     __syncthreads();
-    if (threadIdx.x == 0)
-        for (int q = 0; q < NV; ++q) {
-            double acc = 0.0;
+    if (threadIdx.x < NS) {
+        const int q = threadIdx.x;
+        if (q < NV) {
+            dfl acc = {0.f, 0.f};
             for (int ww = 0; ww < NWARP; ++ww)
-                acc += (double)s_red[(ww * NV + q) * 2] + (double)s_red[(ww * NV + q) * 2 + 1];
-            out[q] = acc;
+                acc = df_add(acc, {s_red[(ww * NRED + q) * 2], s_red[(ww * NRED + q) * 2 + 1]});
+            const double d = (double)acc.hi + (double)acc.lo;
+            for (int r = 0; r < C; ++r) cluster.map_shared_rank(dst, r)[rank * NV + q] = d;
+        } else {
+            float m = 0.f;
+            for (int ww = 0; ww < NWARP; ++ww) m = fmaxf(m, s_red[(ww * NRED + q) * 2]);
+            for (int r = 0; r < C; ++r) cluster.map_shared_rank(mslot, r)[rank] = m;
         }
-    __syncthreads();
-}
-
-__device__ __forceinline__ float cta_max(float v, float* s_red)
-{
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) s_red[w] = v;
-    __syncthreads();
-    float m = 0.f;
-    for (int ww = 0; ww < NWARP; ++ww) m = fmaxf(m, s_red[ww]);
-    __syncthreads();
-    return m;
-}
-
-struct Site {
-    int ix, iy, iz, b;
-};
-
-__device__ __forceinline__ Site site_of(const XRep& R, int a)
-{
-    Site s;
-    s.b = a % R.nb;
-    int c = a / R.nb;
-    s.iz = c % R.nz;
-    c /= R.nz;
-    s.iy = c % R.ny;
-    s.ix = c / R.ny;
-    return s;
-}
-
-__device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-
-// Atom index of stencil entry `code` seen from site s.
-__device__ __forceinline__ int neighbour(const XRep& R, const Site& s, int code)
-{
-    const int dx = (code & 255) - 128, dy = ((code >> 8) & 255) - 128, dz = ((code >> 16) & 255) - 128;
-    const int b2 = (code >> 24) & 255;
-    const int jx = wrapi(s.ix + dx, R.nx), jy = wrapi(s.iy + dy, R.ny), jz = wrapi(s.iz + dz, R.nz);
-    return ((jx * R.ny + jy) * R.nz + jz) * R.nb + b2;
+    }
 }
 
 __device__ __forceinline__ float blendf(int path, float lam, float F0, float FE)
@@ -143,191 +124,237 @@ __device__ __forceinline__ float blendf(int path, float lam, float F0, float FE)
     return path == 0 ? (1.f - lam) * F0 + lam * FE : lam * F0;
 }
 
-__global__ void __launch_bounds__(THREADS, 2)
+// Lambda(s) of the schedule for s = s_begin .. s_begin + count - 1, once per
+// run segment (FP64; read by the persistent kernel instead of evaluated).
+__global__ void k_lambda_table(Sched S, long long s_begin, long long count, double* out)
+{
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+         q += (long long)gridDim.x * blockDim.x)
+        out[q] = ne_sched_lambda(S, s_begin + q);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
     k_cluster(const XRep* __restrict__ reps, const float4* __restrict__ st_vec, const int* __restrict__ st_code,
               double* __restrict__ xg, double* __restrict__ vg, double* __restrict__ Wg, int* status, Sched S,
-              long long s_begin, long long n_steps, Tables tab, unsigned long long* work)
+              long long s_begin, long long n_steps, Tables tab, unsigned long long* work, int k_lo,
+              const double* __restrict__ lam_tab)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
     const int rep = blockIdx.x / C;
-    const XRep& R = reps[rep];
-    const int n = R.n;
-    const int nst = R.st_cnt;
+    const int n = reps[rep].n, nb = reps[rep].nb, nx = reps[rep].nx, ny = reps[rep].ny, nz = reps[rep].nz;
+    const int nst = reps[rep].st_cnt, M = reps[rep].st_margin;
     const int A_c = (n + C - 1) / C;
 
     // ---- shared memory
     float4* s_u = (float4*)smem;                                  // [n] (u, F')
-    float4* s_sv = s_u + n;                                       // [nb * nst]
-    int* s_sc = (int*)(s_sv + R.nb * nst);                        // [nb * nst]
-    unsigned short* s_sl = (unsigned short*)(s_sc + R.nb * nst);  // [SLOTS][SLMAX]
+    float4* s_sv = s_u + n;                                       // [nb * nst] (r0_j - r0_i, |.|)
+    int* s_sc = (int*)(s_sv + nb * nst);                          // [nb * nst] packed offsets
+    int* s_lx = s_sc + nb * nst;                                  // [nx + 2M] wrapped x-cell * ny nz nb
+    int* s_ly = s_lx + nx + 2 * M;                                // [ny + 2M]
+    int* s_lz = s_ly + ny + 2 * M;                                // [nz + 2M]
+    unsigned short* s_sl = (unsigned short*)(s_lz + nz + 2 * M);  // [SLOTS][SLMAX]
     double* s_slotA = (double*)(((size_t)(s_sl + SLOTS * SLMAX) + 15) & ~(size_t)15);  // [16][NA_]
-    double* s_slotB = s_slotA + 16 * NA_;                         // [2][16][NB_]
-    double* s_tot = s_slotB + 2 * 16 * NB_;                       // [NA_ + NB_]
-    double* s_cta = s_tot + NA_ + NB_;                            // [8]
-    float* s_red = (float*)(s_cta + 8);                           // [NWARP][8][2]
-    float* s_misc = s_red + NWARP * 16;                           // [4]
+    double* s_slotB = s_slotA + 16 * NA_;                         // [2][16][NB_ - 1]
+    double* s_tot = s_slotB + 2 * 16 * (NB_ - 1);                 // [NA_ + NB_ - 1] (+1 spare)
+    double* s_lam = s_tot + NA_ + NB_;                            // [2] lambda(s), lambda(s+1)
+    double* s_r0 = s_lam + 2;                                     // [SLOTS][3] sites of the owned atoms
+    float4* s_f = (float4*)(((size_t)(s_r0 + SLOTS * 3) + 15) & ~(size_t)15);  // [SLOTS] force, pair energy
+    float2* s_rho = (float2*)(s_f + SLOTS);                       // [SLOTS] rho as double-float
+    float* s_slotM = (float*)(s_rho + SLOTS);                     // [2][16] max |u| per CTA
+    float* s_red = s_slotM + 32;                                  // [NWARP][NRED][2]
+    float* s_misc = s_red + NWARP * NRED * 2;                     // [4]
+    float4* s_tab = (float4*)(((size_t)(s_misc + 4) + 15) & ~(size_t)15);  // [nk-1-k_lo][2] (phi, f)
 
-    for (int q = threadIdx.x; q < R.nb * nst; q += THREADS) {
-        s_sv[q] = st_vec[R.st_off + q];
-        s_sc[q] = st_code[R.st_off + q];
+    for (int q = threadIdx.x; q < nb * nst; q += THREADS) {
+        s_sv[q] = st_vec[reps[rep].st_off + q];
+        s_sc[q] = st_code[reps[rep].st_off + q];
     }
+    const int n_int = tab.nk - 1 - k_lo;  // intervals of the r grid held in shared memory
+    for (int q = threadIdx.x; q < 2 * n_int; q += THREADS) s_tab[q] = tab.pf32[2 * k_lo + q];
+    for (int q = threadIdx.x; q < nx + 2 * M; q += THREADS) s_lx[q] = (((q - M) % nx + nx) % nx) * ny * nz * nb;
+    for (int q = threadIdx.x; q < ny + 2 * M; q += THREADS) s_ly[q] = (((q - M) % ny + ny) % ny) * nz * nb;
+    for (int q = threadIdx.x; q < nz + 2 * M; q += THREADS) s_lz[q] = (((q - M) % nz + nz) % nz) * nb;
 
+    // pair phases: TPA consecutive threads per atom slot
     const int slot = threadIdx.x / TPA, lane = threadIdx.x % TPA;
     const int a = rank * A_c + slot;
     const bool valid = slot < A_c && a < n;
-    const bool owner = valid && lane == 0;
     const int ai = valid ? a : 0;
-    const Site site = site_of(R, ai);
-    const int stb = site.b * nst;
+    int sx, sy, sz, stb;
+    {
+        const int b = ai % nb;
+        int c = ai / nb;
+        sz = c % nz;
+        c /= nz;
+        sy = c % ny;
+        sx = c / ny;
+        stb = b * nst;
+    }
+    // atom phases (density epilogue, noise, BAOAB): one thread per atom
+    const int ta = rank * A_c + threadIdx.x;
+    const bool own = threadIdx.x < A_c && ta < n;
+    const size_t gi = (size_t)(reps[rep].off + (own ? ta : 0)) * 3;
     cluster.sync();  // every CTA of the cluster has started: distributed shared memory is usable
 
-    // ---- state of the owned atom: x FP64 (registers), v FP32
-    double x[3] = {0, 0, 0}, r0[3];
+    // ---- state of the owned atom: position x in FP64 (registers), velocity
+    // in FP32; its site r0 in shared memory
+    double xr[3] = {0, 0, 0};
     float v[3] = {0, 0, 0}, u[3] = {0, 0, 0};
-    r0[0] = R.a * (site.ix + R.basis[site.b][0]);
-    r0[1] = R.a * (site.iy + R.basis[site.b][1]);
-    r0[2] = R.a * (site.iz + R.basis[site.b][2]);
-    const size_t gi = (size_t)(R.off + ai) * 3;
     int bad = 0;
-    if (owner) {
-        for (int c = 0; c < 3; ++c) {
-            x[c] = xg[gi + c];
-            v[c] = (float)vg[gi + c];
-            u[c] = (float)(x[c] - r0[c]);
-        }
-        const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
-        for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[a] = uv;
-    }
-    // partials for the first step
     {
         dfl pb[NB_ - 1] = {};
-        float umax = 0.f;
-        if (owner) {
+        float um = 0.f;
+        if (own) {
+            const int b = ta % nb;
+            int c = ta / nb;
+            const int iz = c % nz;
+            c /= nz;
+            const int iy = c % ny, ix = c / ny;
+            const double ra = reps[rep].a;
+            s_r0[threadIdx.x * 3] = ra * (ix + reps[rep].basis[b][0]);
+            s_r0[threadIdx.x * 3 + 1] = ra * (iy + reps[rep].basis[b][1]);
+            s_r0[threadIdx.x * 3 + 2] = ra * (iz + reps[rep].basis[b][2]);
+            for (int q = 0; q < 3; ++q) {
+                xr[q] = xg[gi + q];
+                v[q] = (float)vg[gi + q];
+                u[q] = (float)(xr[q] - s_r0[threadIdx.x * 3 + q]);
+            }
+            const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
+            for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[ta] = uv;
             const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            pb[B_UE] = {0.5f * R.kf * u2, 0.f};
+            pb[B_UE] = {0.5f * reps[rep].kf * u2, 0.f};
             pb[B_UX] = {u[0], 0.f};
             pb[B_UY] = {u[1], 0.f};
             pb[B_UZ] = {u[2], 0.f};
             pb[B_U2] = {u2, 0.f};
-            pb[B_KE] = {0.5f * R.mf * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), 0.f};
-            umax = sqrtf(u2);
+            pb[B_KE] = {0.5f * reps[rep].mf * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), 0.f};
+            um = sqrtf(u2);
         }
-        cta_sum<NB_ - 1>(pb, s_red, s_cta);
-        umax = cta_max(umax, s_red);
-        if (threadIdx.x == 0) {
-            double* dst = cluster.map_shared_rank(s_slotB, 0) + ((s_begin & 1) * 16 + rank) * NB_;
-            for (int q = 0; q < NB_ - 1; ++q) dst[q] = s_cta[q];
-            dst[B_UMAX] = umax;
-        }
+        cta_sum_bcast<NB_ - 1, true>(cluster, pb, um, s_red, s_slotB + (s_begin & 1) * 16 * (NB_ - 1),
+                                     s_slotM + (s_begin & 1) * 16, rank, C);
     }
 
-    unsigned long long n_cand = 0, n_pair = 0;  // work counters (stencil entries visited, pairs < r_c)
+    unsigned n_cand = 0, n_pair = 0;  // work counters (stencil entries visited, pairs < r_c)
     const float rc = (float)tab.r_c, rc2 = tab.rc2f, rmin2 = tab.rmin2f, inv_h = tab.inv_h_rf;
     const int nk = tab.nk;
     const float dt = (float)S.dt;
-    float F0[3] = {0, 0, 0}, xi[3] = {0, 0, 0};
 
+#pragma unroll 1
     for (long long it = 0; it <= n_steps; ++it) {
         const long long s = s_begin + it;
         const bool fin = it == n_steps;
-        cluster.sync();  // u of step s visible everywhere
+        cluster.sync();  // u and partial sums of step s visible everywhere
         if (threadIdx.x == 0) {
-            const double* sb = cluster.map_shared_rank(s_slotB, 0) + (s & 1) * 16 * NB_;
-            double um = 0.0;
-            for (int r = 0; r < C; ++r) um = fmax(um, sb[r * NB_ + B_UMAX]);
-            s_misc[0] = (float)um;
-            if (um > (double)R.D) ne_set_status(status, ST_ERANGE);
+            const float* sm = s_slotM + (s & 1) * 16;
+            float um = 0.f;
+            for (int r = 0; r < C; ++r) um = fmaxf(um, sm[r]);
+            s_misc[0] = um;
+            if (um > reps[rep].D) ne_set_status(status, ST_ERANGE);
+            s_lam[0] = lam_tab[it];
+            s_lam[1] = lam_tab[it + 1];
         }
         __syncthreads();
         const float umax = s_misc[0];
 
-        // ---------------- pass 1: density, F(rho), F'(rho), short list
+        // ---------------- pass 1: density and short list (pair threads)
         const float4 ui = s_u[ai];
-        float emb = 0.f;
         int m = 0;
         {
             const float cut = rc + sqrtf(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + umax;
-            double rho = 0.0;
-            float chunk = 0.f;
-            int nchunk = 0;
-            if (valid) {
-                for (int k = lane; k < nst; k += TPA) {
-                    const float4 e = s_sv[stb + k];
-                    if (e.w >= cut) break;
-                    const int j = neighbour(R, site, s_sc[stb + k]);
-                    const float4 uj = s_u[j];
-                    const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    ++n_cand;
-                    if (r2 < rc2) {
-                        ++n_pair;
-                        if (r2 < rmin2) bad |= ST_ERANGE;
-                        const float r = sqrtf(r2);
-                        const float t = r * inv_h;
-                        const int kk = min(max((int)t, 0), nk - 2);
-                        const float w = t - (float)kk;
-                        const float4 c = __ldg(&tab.pf32[2 * kk + 1]);
-                        chunk += c.x + w * (c.y + w * (c.z + w * c.w));
-                        if (++nchunk == 8) {
-                            rho += (double)chunk;
-                            chunk = 0.f;
-                            nchunk = 0;
-                        }
-                        if (m < SLMAX / TPA)
-                            s_sl[slot * SLMAX + m * TPA + lane] = (unsigned short)k;
-                        else
-                            bad |= ST_ENEIGH;
-                        ++m;
-                    }
-                }
-                m = min(m, SLMAX / TPA);
+            int lo = 0, hi = nst;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_sv[stb + mid].w < cut) lo = mid + 1;
+                else hi = mid;
             }
-            rho += (double)chunk;
-            for (int o = TPA >> 1; o > 0; o >>= 1) rho += __shfl_xor_sync(0xffffffffu, rho, o);
-            if (owner) {
-                if (!(rho < tab.rho_max)) bad |= ST_ERANGE;
-                const double t = rho * tab.inv_h_rho;
-                const int kk = min(max((int)t, 0), nk - 2);
-                const float w = (float)(t - kk);
-                const float4 c = __ldg(&tab.F32[kk]);
-                emb = c.x + w * (c.y + w * (c.z + w * c.w));
-                const float dF = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * tab.inv_h_rhof;
-                for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[a].w = dF;
-                if (!isfinite(emb)) bad |= ST_ENAN;
-            }
-        }
-        cluster.sync();  // F' visible everywhere
-
-        // ---------------- pass 2: forces, pair energy, noise
-        {
-            float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
-            if (valid) {
-                const float dFi = s_u[ai].w;
-                for (int q = 0; q < m; ++q) {
-                    const int k = s_sl[slot * SLMAX + q * TPA + lane];
-                    const float4 e = s_sv[stb + k];
-                    const int j = neighbour(R, site, s_sc[stb + k]);
-                    const float4 uj = s_u[j];
-                    const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
-                    const float r = sqrtf(dx * dx + dy * dy + dz * dz);
-                    const float ir = 1.f / r;
+            const int K = valid ? lo : 0;
+            dfl rho = {0.f, 0.f};
+#pragma unroll 2
+            for (int k = lane; k < K; k += TPA) {
+                const int code = s_sc[stb + k];
+                const int j = s_lx[sx + (code & 255)] + s_ly[sy + ((code >> 8) & 255)] +
+                              s_lz[sz + ((code >> 16) & 255)] + (code >> 24);
+                const float4 uj = s_u[j];
+                const float4 e = s_sv[stb + k];
+                const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < rc2) {
+                    if (r2 < rmin2) bad |= ST_ERANGE;
+                    const float r = sqrtf(r2);
                     const float t = r * inv_h;
                     const int kk = min(max((int)t, 0), nk - 2);
                     const float w = t - (float)kk;
-                    const float4 c = __ldg(&tab.pf32[2 * kk]);
-                    const float4 g = __ldg(&tab.pf32[2 * kk + 1]);
-                    const float phi = c.x + w * (c.y + w * (c.z + w * c.w));
-                    const float dphi = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * inv_h;
-                    const float df = (g.y + w * (2.f * g.z + 3.f * w * g.w)) * inv_h;
-                    const float sc = (dphi + (dFi + uj.w) * df) * ir;
-                    fx += sc * dx;
-                    fy += sc * dy;
-                    fz += sc * dz;
-                    ep += 0.5f * phi;
+                    const float4 c = kk >= k_lo ? s_tab[2 * (kk - k_lo) + 1] : __ldg(&tab.pf32[2 * kk + 1]);
+                    rho = df_add(rho, {c.x + w * (c.y + w * (c.z + w * c.w)), 0.f});
+                    if (m < SLMAX / TPA)
+                        s_sl[slot * SLMAX + m * TPA + lane] = (unsigned short)k;
+                    else
+                        bad |= ST_ENEIGH;
+                    ++m;
                 }
+            }
+            n_cand += (K > lane) ? (unsigned)((K - lane + TPA - 1) / TPA) : 0u;
+            m = min(m, SLMAX / TPA);
+            n_pair += (unsigned)m;
+            for (int o = TPA >> 1; o > 0; o >>= 1)
+                rho = df_add(rho, {__shfl_xor_sync(0xffffffffu, rho.hi, o), __shfl_xor_sync(0xffffffffu, rho.lo, o)});
+            if (valid && lane == 0) s_rho[slot] = make_float2(rho.hi, rho.lo);
+        }
+        __syncthreads();
+        // embedding of the owned atom: rho to FP64 once, F(rho), F'(rho)
+        float emb = 0.f;
+        if (own) {
+            const float2 rr = s_rho[threadIdx.x];
+            const double rho = (double)rr.x + (double)rr.y;
+            if (!(rho < tab.rho_max)) bad |= ST_ERANGE;
+            const double t = rho * tab.inv_h_rho;
+            const int kk = min(max((int)t, 0), nk - 2);
+            const float w = (float)(t - kk);
+            const float4 c = __ldg(&tab.F32[kk]);
+            emb = c.x + w * (c.y + w * (c.z + w * c.w));
+            const float dF = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * tab.inv_h_rhof;
+            for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[ta].w = dF;
+            if (!isfinite(emb)) bad |= ST_ENAN;
+        }
+        cluster.sync();  // F' visible everywhere
+
+        // ---------------- pass 2: forces and pair energy (pair threads)
+        {
+            float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
+            const float dFi = s_u[ai].w;
+#pragma unroll 2
+            for (int q = 0; q < m; ++q) {
+                const int k = s_sl[slot * SLMAX + q * TPA + lane];
+                const int code = s_sc[stb + k];
+                const int j = s_lx[sx + (code & 255)] + s_ly[sy + ((code >> 8) & 255)] +
+                              s_lz[sz + ((code >> 16) & 255)] + (code >> 24);
+                const float4 uj = s_u[j];
+                const float4 e = s_sv[stb + k];
+                const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
+                const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+                const float ir = 1.f / r;
+                const float t = r * inv_h;
+                const int kk = min(max((int)t, 0), nk - 2);
+                const float w = t - (float)kk;
+                float4 c, g;
+                if (kk >= k_lo) {
+                    c = s_tab[2 * (kk - k_lo)];
+                    g = s_tab[2 * (kk - k_lo) + 1];
+                } else {
+                    c = __ldg(&tab.pf32[2 * kk]);
+                    g = __ldg(&tab.pf32[2 * kk + 1]);
+                }
+                const float phi = c.x + w * (c.y + w * (c.z + w * c.w));
+                const float dphi = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * inv_h;
+                const float df = (g.y + w * (2.f * g.z + 3.f * w * g.w)) * inv_h;
+                const float sc = (dphi + (dFi + uj.w) * df) * ir;
+                fx += sc * dx;
+                fy += sc * dy;
+                fz += sc * dz;
+                ep += 0.5f * phi;
             }
             for (int o = TPA >> 1; o > 0; o >>= 1) {
                 fx += __shfl_xor_sync(0xffffffffu, fx, o);
@@ -335,48 +362,49 @@ __global__ void __launch_bounds__(THREADS, 2)
                 fz += __shfl_xor_sync(0xffffffffu, fz, o);
                 ep += __shfl_xor_sync(0xffffffffu, ep, o);
             }
+            if (valid && lane == 0) s_f[slot] = make_float4(fx, fy, fz, ep);
+        }
+        __syncthreads();
+        // noise of the owned atom and the CTA partial sums of step s
+        float F0[3] = {0.f, 0.f, 0.f}, xi[3] = {0.f, 0.f, 0.f};
+        {
             dfl pa[NA_] = {};
-            if (owner) {
-                F0[0] = fx;
-                F0[1] = fy;
-                F0[2] = fz;
-                if (!fin) {
-                    ne_normals32(ne_philox_block(R.seed, R.replica, (unsigned)S.stream, (unsigned)a,
-                                                 (unsigned long long)s),
+            if (own) {
+                const float4 f = s_f[threadIdx.x];
+                F0[0] = f.x;
+                F0[1] = f.y;
+                F0[2] = f.z;
+                if (!fin)
+                    ne_normals32(ne_philox_block(reps[rep].seed, reps[rep].replica, (unsigned)S.stream,
+                                                 (unsigned)ta, (unsigned long long)s),
                                  xi);
-                }
                 pa[A_UEMB] = {emb, 0.f};
-                pa[A_UPAIR] = {ep, 0.f};
-                pa[A_FX] = {fx, 0.f};
-                pa[A_FY] = {fy, 0.f};
-                pa[A_FZ] = {fz, 0.f};
+                pa[A_UPAIR] = {f.w, 0.f};
+                pa[A_FX] = {f.x, 0.f};
+                pa[A_FY] = {f.y, 0.f};
+                pa[A_FZ] = {f.z, 0.f};
                 pa[A_XX] = {xi[0], 0.f};
                 pa[A_XY] = {xi[1], 0.f};
                 pa[A_XZ] = {xi[2], 0.f};
             }
-            cta_sum<NA_>(pa, s_red, s_cta);
-            if (threadIdx.x == 0) {
-                double* dst = cluster.map_shared_rank(s_slotA, 0) + rank * NA_;
-                for (int q = 0; q < NA_; ++q) dst[q] = s_cta[q];
-            }
+            cta_sum_bcast<NA_, false>(cluster, pa, 0.f, s_red, s_slotA, nullptr, rank, C);
         }
-        cluster.sync();  // partial sums of step s complete
+        cluster.sync();  // partial sums of step s complete in every CTA
 
         // ---------------- replica totals (fixed order over the cluster's CTAs)
         if (threadIdx.x < NA_ + NB_ - 1) {
             const int q = threadIdx.x;
             double acc = 0.0;
             if (q < NA_) {
-                const double* sa = cluster.map_shared_rank(s_slotA, 0);
-                for (int r = 0; r < C; ++r) acc += sa[r * NA_ + q];
+                for (int r = 0; r < C; ++r) acc += s_slotA[r * NA_ + q];
             } else {
-                const double* sb = cluster.map_shared_rank(s_slotB, 0) + (s & 1) * 16 * NB_;
-                for (int r = 0; r < C; ++r) acc += sb[r * NB_ + (q - NA_)];
+                const double* sb = s_slotB + (s & 1) * 16 * (NB_ - 1);
+                for (int r = 0; r < C; ++r) acc += sb[r * (NB_ - 1) + (q - NA_)];
             }
             s_tot[q] = acc;
         }
         __syncthreads();
-        const double lam_s = ne_sched_lambda(S, s), lam_n = ne_sched_lambda(S, s + 1);
+        const double lam_s = s_lam[0], lam_n = s_lam[1];
         if (!fin && rank == 0 && threadIdx.x == 0) {
             const double U0 = s_tot[A_UEMB] + s_tot[A_UPAIR];
             const double g = S.path == 0 ? U0 - s_tot[NA_ + B_UE] : U0;
@@ -390,54 +418,48 @@ __global__ void __launch_bounds__(THREADS, 2)
         {
             dfl pb[NB_ - 1] = {};
             float un = 0.f;
-            if (owner) {
+            if (own) {
+                const float kf = reps[rep].kf, hdt = reps[rep].hdt_mf, c1 = reps[rep].c1f, c2 = reps[rep].c2f;
                 const float invN = 1.f / (float)n;
                 float mF0[3], mFE[3], mxi[3];
                 for (int c = 0; c < 3; ++c) {
-                    mF0[c] = S.fix_cm ? (float)(s_tot[A_FX + c] * invN) : 0.f;
-                    mFE[c] = S.fix_cm ? (float)(-R.k * s_tot[NA_ + B_UX + c] * invN) : 0.f;
-                    mxi[c] = S.fix_cm ? (float)(s_tot[A_XX + c] * invN) : 0.f;
+                    mF0[c] = S.fix_cm ? (float)s_tot[A_FX + c] * invN : 0.f;
+                    mFE[c] = S.fix_cm ? -kf * (float)s_tot[NA_ + B_UX + c] * invN : 0.f;
+                    mxi[c] = S.fix_cm ? (float)s_tot[A_XX + c] * invN : 0.f;
                 }
                 const float ls = (float)lam_s, ln = (float)lam_n;
                 if (it > 0)
-                    for (int c = 0; c < 3; ++c)
-                        v[c] += R.hdt_mf * blendf(S.path, ls, F0[c] - mF0[c], -R.kf * u[c] - mFE[c]);
+                    for (int c = 0; c < 3; ++c) v[c] += hdt * blendf(S.path, ls, F0[c] - mF0[c], -kf * u[c] - mFE[c]);
                 if (!fin) {
                     for (int c = 0; c < 3; ++c) {
-                        v[c] += R.hdt_mf * blendf(S.path, ln, F0[c] - mF0[c], -R.kf * u[c] - mFE[c]);
+                        v[c] += hdt * blendf(S.path, ln, F0[c] - mF0[c], -kf * u[c] - mFE[c]);
                         const float v1 = v[c];
-                        v[c] = R.c1f * v[c] + R.c2f * (xi[c] - mxi[c]);
-                        x[c] += (double)(0.5f * dt * (v1 + v[c]));
-                        u[c] = (float)(x[c] - r0[c]);
+                        v[c] = c1 * v[c] + c2 * (xi[c] - mxi[c]);
+                        xr[c] += (double)(0.5f * dt * (v1 + v[c]));
+                        u[c] = (float)(xr[c] - s_r0[threadIdx.x * 3 + c]);
                     }
                     const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
-                    for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[a] = uv;
+                    for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[ta] = uv;
                 }
                 const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-                pb[B_UE] = {0.5f * R.kf * u2, 0.f};
+                pb[B_UE] = {0.5f * kf * u2, 0.f};
                 pb[B_UX] = {u[0], 0.f};
                 pb[B_UY] = {u[1], 0.f};
                 pb[B_UZ] = {u[2], 0.f};
                 pb[B_U2] = {u2, 0.f};
-                pb[B_KE] = {0.5f * R.mf * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), 0.f};
+                pb[B_KE] = {0.5f * reps[rep].mf * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), 0.f};
                 un = sqrtf(u2);
                 for (int c = 0; c < 3; ++c)
-                    if (!isfinite(x[c]) || !isfinite(v[c])) bad |= ST_ENAN;
+                    if (!isfinite(xr[c]) || !isfinite(v[c])) bad |= ST_ENAN;
             }
-            if (!fin) {
-                cta_sum<NB_ - 1>(pb, s_red, s_cta);
-                un = cta_max(un, s_red);
-                if (threadIdx.x == 0) {
-                    double* dst = cluster.map_shared_rank(s_slotB, 0) + (((s + 1) & 1) * 16 + rank) * NB_;
-                    for (int q = 0; q < NB_ - 1; ++q) dst[q] = s_cta[q];
-                    dst[B_UMAX] = un;
-                }
-            }
+            if (!fin)
+                cta_sum_bcast<NB_ - 1, true>(cluster, pb, un, s_red, s_slotB + ((s + 1) & 1) * 16 * (NB_ - 1),
+                                             s_slotM + ((s + 1) & 1) * 16, rank, C);
         }
     }
-    if (owner)
+    if (own)
         for (int c = 0; c < 3; ++c) {
-            xg[gi + c] = x[c];
+            xg[gi + c] = xr[c];
             vg[gi + c] = (double)v[c];
         }
     if (bad) ne_set_status(status, bad);
@@ -447,8 +469,8 @@ __global__ void __launch_bounds__(THREADS, 2)
             n_pair += __shfl_xor_sync(0xffffffffu, n_pair, o);
         }
         if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&work[0], n_cand);
-            atomicAdd(&work[1], n_pair);
+            atomicAdd(&work[0], (unsigned long long)n_cand);
+            atomicAdd(&work[1], (unsigned long long)n_pair);
         }
     }
     cluster.sync();  // no CTA leaves while others may still touch its shared memory
@@ -458,13 +480,16 @@ __global__ void __launch_bounds__(THREADS, 2)
 
 namespace ne {
 
-size_t cluster_smem_bytes(int n_max, int nb_nst_max)
+// Bytes of everything but the spline tables; the tables take what is left.
+size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
 {
     size_t b = sizeof(float4) * (size_t)n_max + (sizeof(float4) + sizeof(int)) * (size_t)nb_nst_max +
-               sizeof(unsigned short) * SLOTS * SLMAX;
+               sizeof(int) * (size_t)lut_max + sizeof(unsigned short) * SLOTS * SLMAX;
     b = (b + 15) & ~(size_t)15;
-    b += sizeof(double) * (16 * NA_ + 2 * 16 * NB_ + NA_ + NB_ + 8) + sizeof(float) * (NWARP * 16 + 4);
-    return b;
+    b += sizeof(double) * (16 * NA_ + 2 * 16 * (NB_ - 1) + NA_ + NB_ + 2 + SLOTS * 3);
+    b += 16;  // alignment of s_f
+    b += sizeof(float4) * SLOTS + sizeof(float2) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2 + 4);
+    return ((b + 15) & ~(size_t)15) + 16;  // + alignment of s_tab
 }
 
 int cluster_atoms_per_cta() { return SLOTS; }
@@ -472,8 +497,10 @@ int cluster_atoms_per_cta() { return SLOTS; }
 cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, const float4* st_vec,
                            const int* st_code, double* x, double* v, double* W, int* status, const Sched& S,
                            long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
-                           cudaStream_t st)
+                           int k_lo, double* lam_tab, cudaStream_t st)
 {
+    k_lambda_table<<<(int)std::min<long long>((n_steps + 2 + 255) / 256, 1024), 256, 0, st>>>(S, s_begin, n_steps + 2,
+                                                                                            lam_tab);
     cudaError_t e = cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (C > 8) {
@@ -493,7 +520,7 @@ cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, cons
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_cluster, reps, st_vec, st_code, x, v, W, status, S, s_begin, n_steps, tab,
-                              work);
+                              work, k_lo, (const double*)lam_tab);
 }
 
 }  // namespace ne

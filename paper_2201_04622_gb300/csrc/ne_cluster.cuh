@@ -15,15 +15,16 @@ struct XRep {
     float D;              // largest displacement from a site the stencil covers
     int n, off, nb, nx, ny, nz;
     int st_off, st_cnt;   // stencil of basis b: entries [st_off + b * st_cnt, + st_cnt)
+    int st_margin;        // M: cell offsets of the stencil lie in [-M, M]
     unsigned long long seed;
     unsigned replica;
 };
 
 namespace ne {
-size_t cluster_smem_bytes(int n_max, int nb_nst_max);
+size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max);
 int cluster_atoms_per_cta();
 cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, const float4* st_vec,
                            const int* st_code, double* x, double* v, double* W, int* status, const Sched& S,
                            long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
-                           cudaStream_t st);
+                           int k_lo, double* lam_tab, cudaStream_t st);
 }  // namespace ne
