@@ -36,7 +36,7 @@ METRIC = "atom-steps/sec of switching MD (batched mixed vs plain FP64 GPU) at â‰
 UNIT = "atom-steps/s"
 WORKLOAD = "fl_bcc10x10x10_fcc8x8x8_T1400K_10seeds_each_batched20"
 T_K = 1400.0
-K_SPRING = 4.0      # eV/A^2, from the msd fit of this potential near 1400 K
+K_SPRING = {W.BCC: W.K_BCC_1400, W.FCC: W.K_FCC_1400}  # eV/A^2, msd fits at 1400 K
 SKIN = float(os.environ.get("NE_BENCH_SKIN", "2.6"))  # A
 T_EQ, T_S = 10000, 50000
 FP32_LANES_PER_SM, N_SM = 128, 152
@@ -64,7 +64,7 @@ def build_batch(ne, np):
         x0s.append(x0)
         offs.append(offs[-1] + len(x0))
         boxes.append(box)
-        mds.append(ne.md_params(dt=1e-3, T=T_K, damp=0.1, mass=mass, k_spring=K_SPRING, skin=SKIN,
+        mds.append(ne.md_params(dt=1e-3, T=T_K, damp=0.1, mass=mass, k_spring=K_SPRING[lat], skin=SKIN,
                                 lambda_fn=2, path=ne.NE_PATH_FL, t_eq=T_EQ, t_s=T_S, seed=seed,
                                 replica=r, fix_cm=1))
     return np.concatenate(x0s), offs, boxes, mds
@@ -287,7 +287,7 @@ def _oracle_replica(job):
     p = O.eam(**W.EAM_FE_LIKE)
     th = O.eam_theta(p)
     x0, box = O.create_crystal(lat, a, n, n, n)
-    m = O.md(dt=1e-3, T=T_K, damp=0.1, mass=W.MASS_FE_AMU * O.amu(), k_spring=K_SPRING,
+    m = O.md(dt=1e-3, T=T_K, damp=0.1, mass=W.MASS_FE_AMU * O.amu(), k_spring=K_SPRING[lat],
              lambda_fn=2, path=O.PATH_FL, t_eq=0, t_s=max(1, steps // 2), seed=seed, replica=r,
              fix_cm=1)
     v = O.init_velocities(m, len(x0))

@@ -44,7 +44,8 @@ typedef enum {
     NE_EINVAL = 1,   /* bad argument (null pointer, size, box too small, ...) */
     NE_ENOMEM = 2,   /* allocation failed or capacity of the context exceeded */
     NE_ECUDA = 3,    /* a CUDA runtime call failed */
-    NE_ERANGE = 4,   /* pair distance below 1 A or density >= rho_max */
+    NE_ERANGE = 4,   /* pair distance below 0.2 A, density >= rho_max, or (crystal
+                        runner) an atom beyond the displacement its stencil covers */
     NE_ENEIGH = 5,   /* neighbour-list capacity exceeded */
     NE_ENAN = 6,     /* non-finite position, velocity or energy */
     NE_ETIMEOUT = 7, /* a bounded device wait gave up */

@@ -28,7 +28,11 @@ static const double AMU_KG = 1.66053906660e-27;
 static const double EV_J = 1.602176634e-19;
 /* 1 eV ps^2 / A^2 expressed in kg: 1 eV * (1e-12 s)^2 / (1e-10 m)^2. */
 static const double EV_PS2_PER_A2_KG = 1.602176634e-19 * 1.0e-4;
-static const double R_MIN = 1.0; /* A: shorter pair distances are an error */
+/* A: shorter pair distances are an error.  Near lambda = 1 of the
+ * Frenkel-Ladd path the crystal is a set of independent Einstein oscillators
+ * (Sec. II.B, eq. einstein) whose atoms may overlap, and the tables cover
+ * [0, r_c]; only near-coincident atoms are rejected. */
+static const double R_MIN = 0.2;
 
 double ora_kB(void) { return KB_EV_PER_K; }
 double ora_hbar(void) { return HBAR_EV_PS; }

@@ -281,7 +281,7 @@ ne_status finish(ne_ctx* ctx, cudaStream_t st)
     NE_CU(cudaStreamSynchronize(st));
     ctx->last_bits = bits;
     if (bits & ST_ENAN) return fail(ctx, NE_ENAN, "non-finite position, velocity or energy");
-    if (bits & ST_ERANGE) return fail(ctx, NE_ERANGE, "pair distance below 1 A or density >= rho_max");
+    if (bits & ST_ERANGE) return fail(ctx, NE_ERANGE, "pair distance below 0.2 A, density >= rho_max, or an atom beyond the crystal runner's stencil range");
     if (bits & ST_ENEIGH) return fail(ctx, NE_ENEIGH, "neighbour-list capacity exceeded");
     if (bits & ST_ETIMEOUT) return fail(ctx, NE_ETIMEOUT, "bounded device wait gave up");
     ctx->msg = "ok";

@@ -29,7 +29,7 @@ struct __align__(32) ned4 {
 #define NE_TILE 64
 #define NE_NMAX 256   // candidate neighbours per atom (r < r_c + skin)
 #define NE_SMAX 128   // neighbours per atom inside r_c
-#define NE_RMIN 1.0   // A: shorter pair distances are reported as NE_ERANGE
+#define NE_RMIN 0.2   // A: shorter pair distances are reported as NE_ERANGE (atoms may overlap at lambda -> 1)
 
 // device status bits
 enum { ST_ERANGE = 1, ST_ENEIGH = 2, ST_ENAN = 4, ST_ETIMEOUT = 8, ST_EINVAL = 16 };

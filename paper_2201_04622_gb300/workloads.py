@@ -15,8 +15,12 @@ import numpy as np
 
 # Fe-like analytic EAM (builder-chosen parameters; tabulated on 5000 knots).
 EAM_FE_LIKE = dict(A=0.3743608608532552, alpha=8.0, beta=4.0, B=1.7094801525746224,
-                   r_e=2.4855, r_s=4.6, r_c=5.3, rho_max=30.0, n_knots=5000)
+                   r_e=2.4855, r_s=4.6, r_c=5.3, rho_max=100.0, n_knots=5000)
 MASS_FE_AMU = 55.845
+# Spring constants k = 3 k_B T / <msd> (eq. msd) of this potential at 1400 K,
+# fitted with the library on bcc 10^3 and fcc 8^3 (2 ps + 5 ps, every 10 steps).
+K_BCC_1400 = 2.38
+K_FCC_1400 = 2.68
 A_BCC = 2.87
 A_FCC = 3.65
 BCC, FCC = 0, 1

@@ -128,7 +128,7 @@ def test_tables_interpolate_analytic_potential(pot):
     p, th = pot
     for which, xmax, xs in [(0, 5.3, np.linspace(1.5, 5.29, 50)),
                             (1, 5.3, np.linspace(1.5, 5.29, 50)),
-                            (2, 30.0, np.linspace(2.0, 29.0, 50))]:
+                            (2, W.EAM_FE_LIKE["rho_max"], np.linspace(2.0, 29.0, 50))]:
         for x in xs:
             ya, _ = O.eam_analytic(p, which, x)
             yt, _ = O.hermite(th[which], xmax, x)
@@ -206,7 +206,7 @@ def test_eam_range_errors(pot):
     p, th = pot
     x0, box = O.create_crystal(O.BCC, 2.87, 4, 4, 4)
     x = x0.copy()
-    x[1] = x[0] + np.array([0.5, 0.0, 0.0])
+    x[1] = x[0] + np.array([0.1, 0.0, 0.0])
     with pytest.raises(O.OracleError, match="ERANGE"):
         O.eam_energy_forces(p, th, x, box)
     x0, box = O.create_crystal(O.BCC, 2.87, 3, 3, 3)  # r_c >= L/2
