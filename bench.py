@@ -34,7 +34,6 @@ from paper_2201_04622_gb300 import workloads as W  # noqa: E402
 
 METRIC = "atom-steps/sec of switching MD (batched mixed vs plain FP64 GPU) at ≤1 meV/atom F error"
 UNIT = "atom-steps/s"
-WORKLOAD = "fl_bcc10x10x10_fcc8x8x8_T1400K_10seeds_each_batched20"
 T_K = 1400.0
 K_SPRING = {W.BCC: W.K_BCC_1400, W.FCC: W.K_FCC_1400}  # eV/A^2, msd fits at 1400 K
 SKIN = float(os.environ.get("NE_BENCH_SKIN", "2.6"))  # A
@@ -47,24 +46,37 @@ OPS_PAIR = 62     # one pair inside r_c: spline of f in pass 1 + forces in pass 
 OPS_ATOM = 120    # per atom-step: F(rho), broadcasts, sums, Philox + Box-Muller, BAOAB
 
 
+WORKLOADS = {
+    "fl2": "fl_bcc10x10x10_fcc8x8x8_T1400K_10seeds_each_batched20",
+    "batched256": "fl_256_uneven_replicas_bcc6-12_fcc5-10_T300-1600K",
+}
+ARGS = None
+
+
 def systems():
+    """(lattice, n, a, seed, T) per replica of the workload."""
     out = []
+    if ARGS is not None and ARGS.workload == "batched256":
+        for r in W.batched_replicas(256, seed=1):
+            a = W.A_BCC if r["lattice"] == W.BCC else W.A_FCC
+            out.append((r["lattice"], r["n"], a, 1, r["T"]))
+        return out
     for s in range(10):
-        out.append((W.BCC, 10, W.A_BCC, 1 + s))
+        out.append((W.BCC, 10, W.A_BCC, 1 + s, T_K))
     for s in range(10):
-        out.append((W.FCC, 8, W.A_FCC, 1 + s))
+        out.append((W.FCC, 8, W.A_FCC, 1 + s, T_K))
     return out
 
 
 def build_batch(ne, np):
     x0s, offs, boxes, mds = [], [0], [], []
     mass = W.MASS_FE_AMU * 1.0364269656262175e-4
-    for r, (lat, n, a, seed) in enumerate(systems()):
+    for r, (lat, n, a, seed, Tk) in enumerate(systems()):
         x0, box = ne.ne_create_crystal(lat, a, n, n, n)
         x0s.append(x0)
         offs.append(offs[-1] + len(x0))
         boxes.append(box)
-        mds.append(ne.md_params(dt=1e-3, T=T_K, damp=0.1, mass=mass, k_spring=K_SPRING[lat], skin=SKIN,
+        mds.append(ne.md_params(dt=1e-3, T=Tk, damp=0.1, mass=mass, k_spring=K_SPRING[lat], skin=SKIN,
                                 lambda_fn=2, path=ne.NE_PATH_FL, t_eq=T_EQ, t_s=T_S, seed=seed,
                                 replica=r, fix_cm=1))
     return np.concatenate(x0s), offs, boxes, mds
@@ -165,7 +177,7 @@ def run_ours(args):
     path = args.path
     if path == "auto":
         path = "crystal" if prec == ne.NE_MIXED else "general"
-    crystals = [(lat, a, n, n, n) for (lat, n, a, seed) in systems()]
+    crystals = [(lat, a, n, n, n) for (lat, n, a, seed, Tk) in systems()]
 
     def segment(xx, vv, x00, WW, s0, ns):
         if path == "crystal":
@@ -264,7 +276,8 @@ def run_ours(args):
            "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64" if prec == ne.NE_MIXED else "f64",
            "data": "synthetic (perfect bcc/fcc lattices, Philox Maxwell-Boltzmann velocities)",
-           "config": {"workload": WORKLOAD, "replicas": n_rep, "atoms": n_atoms, "T_K": T_K,
+           "config": {"workload": WORKLOADS[args.workload], "replicas": n_rep, "atoms": n_atoms,
+                      "T_K": T_K if args.workload == "fl2" else "300-1600",
                       "t_eq": T_EQ, "t_s": T_S, "dt_fs": 1.0, "skin_A": SKIN,
                       "precision": args.prec, "path": path, "threads_per_atom": args.tpa,
                       "list_builds_per_replica_step": list_builds / (K * n_rep),
@@ -283,11 +296,11 @@ def run_ours(args):
 
 def _oracle_replica(job):
     import oracle as O
-    lat, n, a, seed, r, steps = job
+    lat, n, a, seed, r, steps, Tk = job
     p = O.eam(**W.EAM_FE_LIKE)
     th = O.eam_theta(p)
     x0, box = O.create_crystal(lat, a, n, n, n)
-    m = O.md(dt=1e-3, T=T_K, damp=0.1, mass=W.MASS_FE_AMU * O.amu(), k_spring=K_SPRING[lat],
+    m = O.md(dt=1e-3, T=Tk, damp=0.1, mass=W.MASS_FE_AMU * O.amu(), k_spring=K_SPRING[lat],
              lambda_fn=2, path=O.PATH_FL, t_eq=0, t_s=max(1, steps // 2), seed=seed, replica=r,
              fix_cm=1)
     v = O.init_velocities(m, len(x0))
@@ -302,7 +315,7 @@ def cpu_baseline(steps):
     from concurrent.futures import ThreadPoolExecutor
     import oracle as O
     O.lib()
-    jobs = [(lat, n, a, seed, r, steps) for r, (lat, n, a, seed) in enumerate(systems())]
+    jobs = [(lat, n, a, seed, r, steps, Tk) for r, (lat, n, a, seed, Tk) in enumerate(systems())]
     cores = min(len(jobs), os.cpu_count() or 1)
     t0 = time.perf_counter()
     with ThreadPoolExecutor(cores) as ex:
@@ -318,19 +331,21 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # each reference step: one MD step of all 20 replicas by the oracle; the
-    # run is capped to a bounded sample of the K requested steps
+    # each reference step: one MD step of every replica of the workload by the
+    # oracle (one replica per host thread); the run is a bounded sample of the
+    # K requested steps
+    n_atoms = sum((2 if lat == W.BCC else 4) * n ** 3 for (lat, n, a, seed, Tk) in systems())
     K = args.steps
-    per_step_est = 40480 / 2.0e6  # s, at ~2e6 atom-steps/s across the host cores
+    per_step_est = n_atoms / 2.0e6  # s, at ~2e6 atom-steps/s across the host cores
     k_run = max(2, min(K, int(90.0 / per_step_est)))
     w_run = max(1, min(args.warmup, 20))
     cpu_baseline(w_run)
     cb = cpu_baseline(k_run)
     out = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": 0, "steps": k_run,
-           "warmup": w_run, "ms_per_step": 40480 / cb["value"] * 1e3, "higher_is_better": True,
+           "warmup": w_run, "ms_per_step": n_atoms / cb["value"] * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "impl": "reference",
            "data": "synthetic (perfect bcc/fcc lattices, Philox Maxwell-Boltzmann velocities)",
-           "config": {"workload": WORKLOAD, "replicas": 20, "atoms": 40480, "T_K": T_K},
+           "config": {"workload": WORKLOADS[args.workload], "replicas": len(systems()), "atoms": n_atoms},
            "cpu_baseline": cb,
            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
@@ -349,7 +364,10 @@ def main():
                     help="crystal: persistent cluster runner (mixed); general: multi-kernel path")
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="fl2", choices=sorted(WORKLOADS))
     args = ap.parse_args()
+    global ARGS
+    ARGS = args
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":

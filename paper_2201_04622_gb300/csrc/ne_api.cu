@@ -51,6 +51,8 @@ struct ne_ctx {
     XRep* xrep = nullptr;
     double* lam_tab = nullptr;  // lambda of each step of a crystal-runner segment
     long long lam_cap = 0;
+    cudaStream_t gst[16] = {};  // crystal runner: one stream per replica size class
+    cudaEvent_t gev[17] = {};
     float4* st_vec = nullptr;
     int* st_code = nullptr;
     float* bins = nullptr;
@@ -547,6 +549,10 @@ ne_status ne_ctx_destroy(ne_ctx* ctx)
                     ctx->bins};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (int g = 0; g < 16; ++g)
+        if (ctx->gst[g]) cudaStreamDestroy(ctx->gst[g]);
+    for (int g = 0; g < 17; ++g)
+        if (ctx->gev[g]) cudaEventDestroy(ctx->gev[g]);
     delete ctx;
     return NE_OK;
 }
@@ -924,6 +930,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
     std::vector<float4> sv;
     std::vector<int> sc;
     int n_max = 0, nbst_max = 0, lut_max = 0;
+    (void)n_max;
     for (int r = 0; r < n_rep; ++r) {
         const ne_md_params& m = md[r];
         XRep& X = xr[r];
@@ -996,26 +1003,25 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         nbst_max = std::max(nbst_max, X.nb * X.st_cnt);
     }
     if (sv.size() > (size_t)ctx->max_rep * 4 * NE_STENCIL_MAX) return fail(ctx, NE_ENOMEM, "stencil capacity exceeded");
+    // Replicas grouped by cluster size C = ceil(n / atoms per CTA), each group
+    // one launch on its own stream, largest replicas first.
     const int per_cta = ne::cluster_atoms_per_cta();
-    int C = (n_max + per_cta - 1) / per_cta;
-    if (C < 1) C = 1;
-    NE_CU(cudaMemcpyAsync(ctx->xrep, xr.data(), sizeof(XRep) * n_rep, cudaMemcpyHostToDevice, st));
+    std::vector<int> order(n_rep);
+    for (int r = 0; r < n_rep; ++r) order[r] = r;
+    auto csize = [&](int r) { return std::max(1, (xr[r].n + per_cta - 1) / per_cta); };
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
+        return csize(p) > csize(q) || (csize(p) == csize(q) && xr[p].n > xr[q].n);
+    });
+    std::vector<XRep> xs(n_rep);
+    for (int q = 0; q < n_rep; ++q) {
+        xs[q] = xr[order[q]];
+        xs[q].widx = order[q];
+    }
+    NE_CU(cudaMemcpyAsync(ctx->xrep, xs.data(), sizeof(XRep) * n_rep, cudaMemcpyHostToDevice, st));
     NE_CU(cudaMemcpyAsync(ctx->st_vec, sv.data(), sizeof(float4) * sv.size(), cudaMemcpyHostToDevice, st));
     NE_CU(cudaMemcpyAsync(ctx->st_code, sc.data(), sizeof(int) * sc.size(), cudaMemcpyHostToDevice, st));
     NE_CU(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
     Sched S = make_sched(md[0]);
-    // shared memory: replica state, stencil, lists and sums, then as many r
-    // intervals of the (phi, f) tables, counted down from r_c, as still fit
-    int dev = 0, smem_max = 0;
-    NE_CU(cudaGetDevice(&dev));
-    NE_CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const size_t base = (ne::cluster_smem_bytes(n_max, nbst_max, lut_max) + 15) & ~(size_t)15;
-    if (base > (size_t)smem_max) return fail(ctx, NE_EINVAL, "replica too large for the crystal runner");
-    const int nk = ctx->eam.n_knots;
-    const long long fit = ((long long)smem_max - (long long)base) / (2 * (long long)sizeof(float4));
-    const int n_int = (int)std::min<long long>(nk - 1, fit);
-    const int k_lo = nk - 1 - n_int;
-    const size_t smem = base + (size_t)n_int * 2 * sizeof(float4);
     if (n_steps + 2 > ctx->lam_cap) {
         if (ctx->lam_tab) {
             NE_CU(cudaStreamSynchronize(st));
@@ -1026,8 +1032,54 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         NE_CU(cudaMalloc((void**)&ctx->lam_tab, sizeof(double) * (size_t)(n_steps + 2)));
         ctx->lam_cap = n_steps + 2;
     }
-    NE_CU(ne::launch_cluster(ctx->xrep, n_rep, C, smem, ctx->st_vec, ctx->st_code, x_dev, v_dev, W_dev, ctx->status,
-                             S, step_begin, n_steps, ctx->tab, ctx->work, k_lo, ctx->lam_tab, st));
+    NE_CU(ne::launch_lambda_table(S, step_begin, n_steps + 2, ctx->lam_tab, st));
+    int dev = 0, smem_max = 0;
+    NE_CU(cudaGetDevice(&dev));
+    NE_CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int nk = ctx->eam.n_knots;
+    // groups
+    std::vector<std::pair<int, int>> groups;  // [begin, end) in xs
+    for (int q = 0; q < n_rep;) {
+        int e = q;
+        while (e < n_rep && csize(order[e]) == csize(order[q])) ++e;
+        groups.push_back({q, e});
+        q = e;
+    }
+    if (groups.size() > 16) return fail(ctx, NE_EINVAL, "crystal runner: at most 16 size classes per call");
+    const bool multi = groups.size() > 1;
+    if (multi) {
+        if (!ctx->gev[0]) {
+            for (int g = 0; g < 17; ++g) NE_CU(cudaEventCreateWithFlags(&ctx->gev[g], cudaEventDisableTiming));
+            for (int g = 0; g < 16; ++g) NE_CU(cudaStreamCreateWithFlags(&ctx->gst[g], cudaStreamNonBlocking));
+        }
+        NE_CU(cudaEventRecord(ctx->gev[16], st));
+    }
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const int b = groups[g].first, e = groups[g].second;
+        int gn = 0, gnb = 0, glut = 0;
+        for (int q = b; q < e; ++q) {
+            gn = std::max(gn, xs[q].n);
+            gnb = std::max(gnb, xs[q].nb * xs[q].st_cnt);
+            glut = std::max(glut, xs[q].nx + xs[q].ny + xs[q].nz + 6 * xs[q].st_margin);
+        }
+        // shared memory: replica state, stencil, lists and sums, then as many
+        // r intervals of the (phi, f) tables, counted down from r_c, as fit
+        const size_t base = (ne::cluster_smem_bytes(gn, gnb, glut) + 15) & ~(size_t)15;
+        if (base > (size_t)smem_max) return fail(ctx, NE_EINVAL, "replica too large for the crystal runner");
+        const long long fit = ((long long)smem_max - (long long)base) / (2 * (long long)sizeof(float4));
+        const int n_int = (int)std::min<long long>(nk - 1, fit);
+        const int k_lo = nk - 1 - n_int;
+        const size_t smem = base + (size_t)n_int * 2 * sizeof(float4);
+        cudaStream_t gs = multi ? ctx->gst[g] : st;
+        if (multi) NE_CU(cudaStreamWaitEvent(gs, ctx->gev[16], 0));
+        NE_CU(ne::launch_cluster(ctx->xrep + b, e - b, csize(order[b]), smem, ctx->st_vec, ctx->st_code, x_dev, v_dev,
+                                 W_dev, ctx->status, S, step_begin, n_steps, ctx->tab, ctx->work, k_lo, ctx->lam_tab,
+                                 gs));
+        if (multi) {
+            NE_CU(cudaEventRecord(ctx->gev[g], gs));
+            NE_CU(cudaStreamWaitEvent(st, ctx->gev[g], 0));
+        }
+    }
     NE_CU(cudaStreamSynchronize(st));  // host vectors above must outlive the copies
     return finish(ctx, st);
 }

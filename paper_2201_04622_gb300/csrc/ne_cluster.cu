@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             int wslot = -1;
             if (s >= S.t_eq && s < S.t_eq + S.t_s) wslot = 0;
             else if (s >= 2 * S.t_eq + S.t_s && s < 2 * S.t_eq + 2 * S.t_s) wslot = 1;
-            if (wslot >= 0) Wg[2 * rep + wslot] += (lam_n - lam_s) * g;
+            if (wslot >= 0) Wg[2 * reps[rep].widx + wslot] += (lam_n - lam_s) * g;
         }
 
         // ---------------- fused step of the owned atom
@@ -494,13 +494,17 @@ size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
 
 int cluster_atoms_per_cta() { return SLOTS; }
 
+cudaError_t launch_lambda_table(const Sched& S, long long s_begin, long long count, double* out, cudaStream_t st)
+{
+    k_lambda_table<<<(int)std::min<long long>((count + 255) / 256, 1024), 256, 0, st>>>(S, s_begin, count, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, const float4* st_vec,
                            const int* st_code, double* x, double* v, double* W, int* status, const Sched& S,
                            long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
                            int k_lo, double* lam_tab, cudaStream_t st)
 {
-    k_lambda_table<<<(int)std::min<long long>((n_steps + 2 + 255) / 256, 1024), 256, 0, st>>>(S, s_begin, n_steps + 2,
-                                                                                            lam_tab);
     cudaError_t e = cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (C > 8) {

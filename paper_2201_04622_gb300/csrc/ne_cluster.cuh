@@ -18,11 +18,13 @@ struct XRep {
     int st_margin;        // M: cell offsets of the stencil lie in [-M, M]
     unsigned long long seed;
     unsigned replica;
+    int widx;             // index of the replica in the caller's arrays (work W)
 };
 
 namespace ne {
 size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max);
 int cluster_atoms_per_cta();
+cudaError_t launch_lambda_table(const Sched& S, long long s_begin, long long count, double* out, cudaStream_t st);
 cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, const float4* st_vec,
                            const int* st_code, double* x, double* v, double* W, int* status, const Sched& S,
                            long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,

@@ -149,3 +149,23 @@ def test_crystal_runner_rejects_small_boxes_and_fp64(ctx):
     x = torch.zeros((250, 3), dtype=torch.float64, device=DEV)
     with pytest.raises(ne.NeError, match="NE_EINVAL"):
         ne.ne_crystal_run_segment(ctx, [mg], [(O.BCC, 2.87, 5, 5, 5)], x, x.clone(), Wd, 0, 10)
+
+
+def test_uneven_batch_size_classes_match_multikernel_path(ctx):
+    """Replicas of 432 to 4000 atoms (cluster sizes 2 to 13 CTAs, launched per
+    size class on separate streams) against the multi-kernel mixed path."""
+    systems = [(O.BCC, 6, 1500.0, 1), (O.FCC, 10, 600.0, 2), (O.BCC, 9, 1100.0, 3), (O.FCC, 5, 300.0, 4),
+               (O.BCC, 12, 900.0, 5), (O.FCC, 7, 1300.0, 6), (O.BCC, 6, 400.0, 7)]
+    x, v, Wd, x0s, vs = run_crystals(ctx, systems, 0, 60, t_eq=10, t_s=25, k_spring=3.0)
+    offs = np.cumsum([0] + [len(a) for a in x0s])
+    mgs = [md_pair(T=Tk, seed=seed, replica=r, t_eq=10, t_s=25, k_spring=3.0)[1]
+           for r, (lat, n, Tk, seed) in enumerate(systems)]
+    boxes = [O.create_crystal(lat, lat_a(lat), n, n, n)[1] for (lat, n, Tk, seed) in systems]
+    X0 = T(np.concatenate(x0s))
+    x2, v2 = X0.clone(), T(np.concatenate(vs))
+    W2 = torch.zeros((len(systems), 2), dtype=torch.float64, device=DEV)
+    for m in mgs:
+        m.skin = 1.5
+    ne.ne_switch_run_segment(ctx, mgs, list(offs), x2, v2, X0, boxes, W2, 0, 60)
+    assert torch.abs(x - x2).max().item() < 2e-5
+    assert torch.allclose(Wd, W2, rtol=1e-5, atol=1e-4)
