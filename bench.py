@@ -185,6 +185,12 @@ def run_ours(args):
         else:
             ne.ne_switch_run_segment(ctx, mds, offs, xx, vv, x00, boxes, WW, s0, ns)
 
+    tuned = None
+    if path == "general" and args.autotune:
+        from paper_2201_04622_gb300 import autotune
+        best, table = autotune.tune(ctx, mds, offs, x, v, x0, boxes, Wd, 0, 60,
+                                    skins=[1.0, 1.8, 2.6])
+        tuned = {"best": {k: best[k] for k in ("tpa", "skin", "ms_per_step")}, "candidates": len(table)}
     # warm-up steps (the start of the schedule)
     segment(x, v, x0, Wd, 0, Wm)
     torch.cuda.synchronize()
@@ -272,6 +278,28 @@ def run_ours(args):
                                   "step": prof[3]}}
     steps_per_graph = 32
     launches = 1 if path == "crystal" else 5 * K + (K - 1) // steps_per_graph + 10
+    # the plain FP64 GPU path on the same batch (the comparison the metric names)
+    fp64 = None
+    if prec == ne.NE_MIXED and not args.no_fp64:
+        K64 = min(K, 2000, S_total - 1)
+        m64 = [ne.md_params(dt=m.dt, T=m.T, damp=m.damp, mass=m.mass, k_spring=m.k_spring, skin=SKIN,
+                            lambda_fn=m.lambda_fn, path=m.path, t_eq=m.t_eq, t_s=m.t_s, seed=m.seed,
+                            replica=m.replica, fix_cm=m.fix_cm, prec=ne.NE_FP64) for m in mds]
+        x64, v64 = x0.clone(), v.clone()
+        W64 = torch.zeros_like(Wd)
+        ne.ne_switch_run_segment(ctx, m64, offs, x64, v64, x0, boxes, W64, 0, 50)
+        flush_l2(torch, l2)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        ne.ne_switch_run_segment(ctx, m64, offs, x64, v64, x0, boxes, W64, 50, K64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        v64val = K64 * n_atoms * world / (ms64 * 1e-3)
+        fp64 = {"value": v64val, "unit": UNIT, "ms_per_step": ms64 / K64, "steps": K64,
+                "path": "multi-kernel, FP64 throughout", "speedup_of_mixed": value / v64val}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64" if prec == ne.NE_MIXED else "f64",
@@ -280,11 +308,13 @@ def run_ours(args):
                       "T_K": T_K if args.workload == "fl2" else "300-1600",
                       "t_eq": T_EQ, "t_s": T_S, "dt_fs": 1.0, "skin_A": SKIN,
                       "precision": args.prec, "path": path, "threads_per_atom": args.tpa,
+                      "autotune": tuned,
                       "list_builds_per_replica_step": list_builds / (K * n_rep),
                       "parallelism": "replicas only" if world > 1 else "1 GPU",
                       "l2": "flushed before the timed segment; the 40k-atom state stays L2-resident "
                             "across MD steps by design"},
-           "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e, "roofline": roof}
+           "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e, "roofline": roof,
+           "fp64_gpu": fp64}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_steps)
     ne.ne_ctx_destroy(ctx)
@@ -364,6 +394,9 @@ def main():
                     help="crystal: persistent cluster runner (mixed); general: multi-kernel path")
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
+    ap.add_argument("--autotune", action="store_true",
+                    help="multi-kernel path: pick threads per atom and skin by timing the batch")
     ap.add_argument("--workload", default="fl2", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     global ARGS

@@ -447,3 +447,26 @@ def test_resume_from_checkpoint_is_bitwise(ctx):
         out.append((N(x), N(v), N(Wd)))
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+
+
+def test_autotuner_picks_a_valid_configuration_and_restores_state(ctx):
+    from paper_2201_04622_gb300 import autotune
+    systems = [(O.BCC, 8, 900.0, 1), (O.FCC, 7, 900.0, 2)]
+    x0s, vs, offs, boxes, mgs = [], [], [0], [], []
+    for r, (lat, n, Tk, seed) in enumerate(systems):
+        x0, box = crystal(lat, n)
+        mo, mg = md_pair(T=Tk, seed=seed, replica=r, prec=ne.NE_MIXED, t_eq=50, t_s=100)
+        x0s.append(x0)
+        vs.append(O.init_velocities(mo, len(x0)))
+        offs.append(offs[-1] + len(x0))
+        boxes.append(box)
+        mgs.append(mg)
+    x, v = T(np.concatenate(x0s)), T(np.concatenate(vs))
+    X0 = T(np.concatenate(x0s))
+    Wd = torch.zeros((2, 2), dtype=torch.float64, device=DEV)
+    x_in = x.clone()
+    best, table = autotune.tune(ctx, mgs, offs, x, v, X0, boxes, Wd, 0, 20, skins=[0.6, 1.2])
+    assert torch.equal(x, x_in)
+    assert best["tpa"] in (1, 2, 4, 8) and best["skin"] in (0.6, 1.2) and len(table) == 8
+    assert all(t["ms_per_step"] > 0 for t in table)
+    ne.ne_ctx_set_tuning(ctx, 4)
