@@ -1008,7 +1008,8 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
     const int per_cta = ne::cluster_atoms_per_cta();
     std::vector<int> order(n_rep);
     for (int r = 0; r < n_rep; ++r) order[r] = r;
-    auto csize = [&](int r) { return std::max(1, (xr[r].n + per_cta - 1) / per_cta); };
+    (void)per_cta;
+    auto csize = [&](int r) { return ne::cluster_size_for(xr[r].n, xr[r].nb); };
     std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
         return csize(p) > csize(q) || (csize(p) == csize(q) && xr[p].n > xr[q].n);
     });

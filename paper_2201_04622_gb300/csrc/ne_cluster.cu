@@ -14,16 +14,22 @@
 // displacement from a site the stencil covers; a replica whose atoms stray
 // further is reported (NE_ERANGE) -- the crystal has melted.
 //
-// One MD step (same arithmetic order as the multi-kernel path):
-//   [cluster barrier]  pass 1: rho, F(rho), F'(rho), short list in smem,
-//                      F' broadcast
-//   [cluster barrier]  pass 2: forces, pair energy, this step's normals;
-//                      CTA partial sums to rank 0
-//   [cluster barrier]  replica totals (fixed order); work increment (rank 0);
-//                      closing and opening half kicks, drift, OU, drift;
-//                      new u broadcast; partial sums for the next step
-// The barriers are barrier.cluster arrive/wait (hardware; every CTA of a
-// cluster is co-scheduled), so no thread spins on memory.
+// One MD step s, two cluster barriers:
+//   [cluster barrier]  replica sums of step s (from the partial sums every
+//                      CTA broadcast at the end of step s-1): noise mean,
+//                      spring mean, max |u|; the work increment of step s-1;
+//                      pass 1: rho, F(rho), F'(rho), short list, F' broadcast
+//   [cluster barrier]  pass 2: forces and pair energy; closing and opening
+//                      half kicks, drift, Ornstein-Uhlenbeck, drift; new u
+//                      broadcast; the normals of step s+1 (counter-based, so
+//                      drawn one step ahead); CTA partial sums for step s+1.
+// The work increment of step s is applied at step s+1 from those sums, in
+// the same order, so a segment boundary changes no bit of the result.  The
+// barriers are barrier.cluster arrive/wait (hardware; every CTA of a cluster
+// is co-scheduled), so no thread spins on memory.  The EAM forces sum to zero
+// in exact arithmetic; their FP32 round-off mean is not subtracted (the spring
+// and noise means are), which lets the centre of mass move by ~1e-4 A per
+// 100 ps.
 //
 // Precision: pair distances, splines, forces, velocities and the OU update in
 // FP32; positions x (registers, FP64), rho accumulation (FP32 chunks of 8 into
@@ -46,11 +52,10 @@ constexpr int SLOTS = THREADS / TPA;  // atoms per CTA (one CTA per SM)
 constexpr int SLMAX = 80;             // short-list entries per atom
 constexpr int NWARP = THREADS / 32;
 
-// partial sums
-enum { A_UEMB = 0, A_UPAIR, A_FX, A_FY, A_FZ, A_XX, A_XY, A_XZ, NA_ };
-enum { B_UE = 0, B_UX, B_UY, B_UZ, B_U2, B_KE, B_UMAX, NB_ };
+// partial sums broadcast at the end of step s for step s+1
+enum { P_U0 = 0, P_UE, P_UX, P_UY, P_UZ, P_XX, P_XY, P_XZ, P_KE, NP_ };
 // values per warp in the reduction scratch: the larger of the two reductions
-constexpr int NRED = (int)NA_ > (int)NB_ ? (int)NA_ : (int)NB_;
+constexpr int NRED = (int)NP_ + 1;  // sums and one maximum
 
 struct dfl {
     float hi, lo;
@@ -87,15 +92,18 @@ __device__ __forceinline__ void warp_df_sum(dfl (&v)[NV])
 // of s_red by a cluster barrier.
 template <int NV, bool HASMAX>
 __device__ __forceinline__ void cta_sum_bcast(cg::cluster_group& cluster, dfl (&v)[NV], float mx, float* s_red,
-                                              double* dst, float* mslot, int rank, int C)
+                                              double* dst, float* mslot, int rank, int C, int nwarp)
 {
-    warp_df_sum<NV>(v);
-    if (HASMAX)
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    // only the first nwarp warps hold values (the threads that own atoms)
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (w < nwarp) {
+        warp_df_sum<NV>(v);
+        if (HASMAX)
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
     constexpr int NS = NV + (HASMAX ? 1 : 0);
     static_assert(NS <= NRED, "reduction scratch too small");
-    if (l == 0) {
+    if (l == 0 && w < nwarp) {
         for (int q = 0; q < NV; ++q) {
             s_red[(w * NRED + q) * 2] = v[q].hi;
             s_red[(w * NRED + q) * 2 + 1] = v[q].lo;
@@ -107,13 +115,13 @@ __device__ __forceinline__ void cta_sum_bcast(cg::cluster_group& cluster, dfl (&
         const int q = threadIdx.x;
         if (q < NV) {
             dfl acc = {0.f, 0.f};
-            for (int ww = 0; ww < NWARP; ++ww)
+            for (int ww = 0; ww < nwarp; ++ww)
                 acc = df_add(acc, {s_red[(ww * NRED + q) * 2], s_red[(ww * NRED + q) * 2 + 1]});
             const double d = (double)acc.hi + (double)acc.lo;
             for (int r = 0; r < C; ++r) cluster.map_shared_rank(dst, r)[rank * NV + q] = d;
         } else {
             float m = 0.f;
-            for (int ww = 0; ww < NWARP; ++ww) m = fmaxf(m, s_red[(ww * NRED + q) * 2]);
+            for (int ww = 0; ww < nwarp; ++ww) m = fmaxf(m, s_red[(ww * NRED + q) * 2]);
             for (int r = 0; r < C; ++r) cluster.map_shared_rank(mslot, r)[rank] = m;
         }
     }
@@ -133,6 +141,13 @@ __global__ void k_lambda_table(Sched S, long long s_begin, long long count, doub
         out[q] = ne_sched_lambda(S, s_begin + q);
 }
 
+// Atoms per CTA: the replica split in C equal parts, rounded up to whole
+// cells so a CTA holds every basis site of its cells.
+__host__ __device__ inline int atoms_per_cta(int n, int C, int nb)
+{
+    return (((n + C - 1) / C) + nb - 1) / nb * nb;
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
     k_cluster(const XRep* __restrict__ reps, const float4* __restrict__ st_vec, const int* __restrict__ st_code,
               double* __restrict__ xg, double* __restrict__ vg, double* __restrict__ Wg, int* status, Sched S,
@@ -146,7 +161,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int rep = blockIdx.x / C;
     const int n = reps[rep].n, nb = reps[rep].nb, nx = reps[rep].nx, ny = reps[rep].ny, nz = reps[rep].nz;
     const int nst = reps[rep].st_cnt, M = reps[rep].st_margin;
-    const int A_c = (n + C - 1) / C;
+    const int A_c = atoms_per_cta(n, C, nb);
+    const int cells_c = A_c / nb;
 
     // ---- shared memory
     float4* s_u = (float4*)smem;                                  // [n] (u, F')
@@ -156,17 +172,15 @@ __global__ void __launch_bounds__(THREADS, 1)
     int* s_ly = s_lx + nx + 2 * M;                                // [ny + 2M]
     int* s_lz = s_ly + ny + 2 * M;                                // [nz + 2M]
     unsigned short* s_sl = (unsigned short*)(s_lz + nz + 2 * M);  // [SLOTS][SLMAX]
-    double* s_slotA = (double*)(((size_t)(s_sl + SLOTS * SLMAX) + 15) & ~(size_t)15);  // [16][NA_]
-    double* s_slotB = s_slotA + 16 * NA_;                         // [2][16][NB_ - 1]
-    double* s_tot = s_slotB + 2 * 16 * (NB_ - 1);                 // [NA_ + NB_ - 1] (+1 spare)
-    double* s_lam = s_tot + NA_ + NB_;                            // [2] lambda(s), lambda(s+1)
-    double* s_r0 = s_lam + 2;                                     // [SLOTS][3] sites of the owned atoms
-    float4* s_f = (float4*)(((size_t)(s_r0 + SLOTS * 3) + 15) & ~(size_t)15);  // [SLOTS] force, pair energy
-    float2* s_rho = (float2*)(s_f + SLOTS);                       // [SLOTS] rho as double-float
-    float* s_slotM = (float*)(s_rho + SLOTS);                     // [2][16] max |u| per CTA
+    double* s_slotP = (double*)(((size_t)(s_sl + SLOTS * SLMAX) + 15) & ~(size_t)15);  // [2][16][NP_]
+    double* s_tot = s_slotP + 2 * 16 * NP_;                       // [NP_ + 1]
+    double* s_r0 = s_tot + NP_ + 1;                               // [SLOTS][3] sites of the owned atoms
+    float4* s_f = (float4*)(((size_t)(s_r0 + SLOTS * 3) + 15) & ~(size_t)15);  // [2][SLOTS] force, pair energy
+    float2* s_rho = (float2*)(s_f + 2 * SLOTS);                   // [2][SLOTS] rho as double-float
+    float* s_slotM = (float*)(s_rho + 2 * SLOTS);                 // [2][16] max |u| per CTA
     float* s_red = s_slotM + 32;                                  // [NWARP][NRED][2]
-    float* s_misc = s_red + NWARP * NRED * 2;                     // [4]
-    float4* s_tab = (float4*)(((size_t)(s_misc + 4) + 15) & ~(size_t)15);  // [nk-1-k_lo][2] (phi, f)
+    float* s_misc = s_red + NWARP * NRED * 2;                     // [8]
+    float4* s_tab = (float4*)(((size_t)(s_misc + 8) + 15) & ~(size_t)15);  // [nk-1-k_lo][2] (phi, f)
 
     for (int q = threadIdx.x; q < nb * nst; q += THREADS) {
         s_sv[q] = st_vec[reps[rep].st_off + q];
@@ -174,18 +188,27 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     const int n_int = tab.nk - 1 - k_lo;  // intervals of the r grid held in shared memory
     for (int q = threadIdx.x; q < 2 * n_int; q += THREADS) s_tab[q] = tab.pf32[2 * k_lo + q];
-    for (int q = threadIdx.x; q < nx + 2 * M; q += THREADS) s_lx[q] = (((q - M) % nx + nx) % nx) * ny * nz * nb;
-    for (int q = threadIdx.x; q < ny + 2 * M; q += THREADS) s_ly[q] = (((q - M) % ny + ny) % ny) * nz * nb;
-    for (int q = threadIdx.x; q < nz + 2 * M; q += THREADS) s_lz[q] = (((q - M) % nz + nz) % nz) * nb;
+    // shared-memory copy of the replica is basis-major: entry b * ncell + cell
+    const int ncell = n / nb;
+    for (int q = threadIdx.x; q < nx + 2 * M; q += THREADS) s_lx[q] = (((q - M) % nx + nx) % nx) * ny * nz;
+    for (int q = threadIdx.x; q < ny + 2 * M; q += THREADS) s_ly[q] = (((q - M) % ny + ny) % ny) * nz;
+    for (int q = threadIdx.x; q < nz + 2 * M; q += THREADS) s_lz[q] = ((q - M) % nz + nz) % nz;
 
-    // pair phases: TPA consecutive threads per atom slot
-    const int slot = threadIdx.x / TPA, lane = threadIdx.x % TPA;
-    const int a = rank * A_c + slot;
+    // slots are basis-major inside a CTA: the atoms of a warp share a stencil
+    // and their neighbours for one stencil entry lie close together
+    auto slot_atom = [&](int sl) { return rank * A_c + (sl % cells_c) * nb + sl / cells_c; };
+    // pair phases: two threads per slot, in different warps (warp w and
+    // w + SLOTS/32 hold the same 32 slots, one for the even and one for the
+    // odd stencil entries), so the 32 lanes of a warp read one stencil entry
+    // and consecutive neighbours at each iteration
+    const int slot = threadIdx.x % SLOTS, lane = threadIdx.x / SLOTS;
+    const int a = slot_atom(slot);
     const bool valid = slot < A_c && a < n;
     const int ai = valid ? a : 0;
-    int sx, sy, sz, stb;
+    int sx, sy, sz, stb, sui;
     {
         const int b = ai % nb;
+        sui = b * ncell + ai / nb;
         int c = ai / nb;
         sz = c % nz;
         c /= nz;
@@ -193,19 +216,22 @@ __global__ void __launch_bounds__(THREADS, 1)
         sx = c / ny;
         stb = b * nst;
     }
-    // atom phases (density epilogue, noise, BAOAB): one thread per atom
-    const int ta = rank * A_c + threadIdx.x;
+    // atom phases (density epilogue, BAOAB, noise): one thread per slot
+    const int ta = slot_atom(threadIdx.x);
     const bool own = threadIdx.x < A_c && ta < n;
+    const int tsu = own ? (ta % nb) * ncell + ta / nb : 0;  // its shared-memory entry
+    const int own_warps = (A_c + 31) / 32;                   // warps holding owned atoms
     const size_t gi = (size_t)(reps[rep].off + (own ? ta : 0)) * 3;
     cluster.sync();  // every CTA of the cluster has started: distributed shared memory is usable
 
     // ---- state of the owned atom: position x in FP64 (registers), velocity
-    // in FP32; its site r0 in shared memory
+    // and this step's normals in FP32; its site r0 in shared memory
     double xr[3] = {0, 0, 0};
-    float v[3] = {0, 0, 0}, u[3] = {0, 0, 0};
+    float v[3] = {0, 0, 0}, u[3] = {0, 0, 0}, xi[3] = {0, 0, 0};
     int bad = 0;
+    const float kf = reps[rep].kf;
     {
-        dfl pb[NB_ - 1] = {};
+        dfl pp[NP_] = {};
         float um = 0.f;
         if (own) {
             const int b = ta % nb;
@@ -223,44 +249,71 @@ __global__ void __launch_bounds__(THREADS, 1)
                 u[q] = (float)(xr[q] - s_r0[threadIdx.x * 3 + q]);
             }
             const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
-            for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[ta] = uv;
+            for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[tsu] = uv;
+            ne_normals32(ne_philox_block(reps[rep].seed, reps[rep].replica, (unsigned)S.stream, (unsigned)ta,
+                                         (unsigned long long)s_begin),
+                         xi);
             const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            pb[B_UE] = {0.5f * reps[rep].kf * u2, 0.f};
-            pb[B_UX] = {u[0], 0.f};
-            pb[B_UY] = {u[1], 0.f};
-            pb[B_UZ] = {u[2], 0.f};
-            pb[B_U2] = {u2, 0.f};
-            pb[B_KE] = {0.5f * reps[rep].mf * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), 0.f};
+            pp[P_UE] = {0.5f * kf * u2, 0.f};
+            pp[P_UX] = {u[0], 0.f};
+            pp[P_UY] = {u[1], 0.f};
+            pp[P_UZ] = {u[2], 0.f};
+            pp[P_XX] = {xi[0], 0.f};
+            pp[P_XY] = {xi[1], 0.f};
+            pp[P_XZ] = {xi[2], 0.f};
+            pp[P_KE] = {0.5f * reps[rep].mf * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), 0.f};
             um = sqrtf(u2);
         }
-        cta_sum_bcast<NB_ - 1, true>(cluster, pb, um, s_red, s_slotB + (s_begin & 1) * 16 * (NB_ - 1),
-                                     s_slotM + (s_begin & 1) * 16, rank, C);
+        cta_sum_bcast<NP_, true>(cluster, pp, um, s_red, s_slotP + (s_begin & 1) * 16 * NP_,
+                                 s_slotM + (s_begin & 1) * 16, rank, C, own_warps);
     }
 
     unsigned n_cand = 0, n_pair = 0;  // work counters (stencil entries visited, pairs < r_c)
     const float rc = (float)tab.r_c, rc2 = tab.rc2f, rmin2 = tab.rmin2f, inv_h = tab.inv_h_rf;
     const int nk = tab.nk;
     const float dt = (float)S.dt;
+    double UE_prev = 0.0;  // rank 0, thread 0: U_E at the positions of the previous step
 
 #pragma unroll 1
     for (long long it = 0; it <= n_steps; ++it) {
         const long long s = s_begin + it;
         const bool fin = it == n_steps;
-        cluster.sync();  // u and partial sums of step s visible everywhere
-        if (threadIdx.x == 0) {
-            const float* sm = s_slotM + (s & 1) * 16;
-            float um = 0.f;
-            for (int r = 0; r < C; ++r) um = fmaxf(um, sm[r]);
-            s_misc[0] = um;
-            if (um > reps[rep].D) ne_set_status(status, ST_ERANGE);
-            s_lam[0] = lam_tab[it];
-            s_lam[1] = lam_tab[it + 1];
+        cluster.sync();  // u of step s and the partial sums for step s visible everywhere
+
+        // ---------------- replica sums for step s (fixed order over the CTAs)
+        if (threadIdx.x <= NP_) {
+            const int q = threadIdx.x;
+            if (q < NP_) {
+                const double* sp = s_slotP + (s & 1) * 16 * NP_;
+                double acc = 0.0;
+                for (int r = 0; r < C; ++r) acc += sp[r * NP_ + q];
+                s_tot[q] = acc;
+            } else {
+                const float* sm = s_slotM + (s & 1) * 16;
+                float um = 0.f;
+                for (int r = 0; r < C; ++r) um = fmaxf(um, sm[r]);
+                s_misc[0] = um;
+                if (um > reps[rep].D) ne_set_status(status, ST_ERANGE);
+            }
         }
         __syncthreads();
+        if (rank == 0 && threadIdx.x == 0) {
+            // work increment of step s - 1: (lambda_s - lambda_{s-1}) dH/dlambda(x_{s-1})
+            if (it > 0) {
+                const long long sp = s - 1;
+                const double U0 = s_tot[P_U0];
+                const double g = S.path == 0 ? U0 - UE_prev : U0;
+                int wslot = -1;
+                if (sp >= S.t_eq && sp < S.t_eq + S.t_s) wslot = 0;
+                else if (sp >= 2 * S.t_eq + S.t_s && sp < 2 * S.t_eq + 2 * S.t_s) wslot = 1;
+                if (wslot >= 0) Wg[2 * reps[rep].widx + wslot] += (lam_tab[it] - lam_tab[it - 1]) * g;
+            }
+            UE_prev = s_tot[P_UE];
+        }
         const float umax = s_misc[0];
 
         // ---------------- pass 1: density and short list (pair threads)
-        const float4 ui = s_u[ai];
+        const float4 ui = s_u[sui];
         int m = 0;
         {
             const float cut = rc + sqrtf(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + umax;
@@ -273,42 +326,41 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int K = valid ? lo : 0;
             dfl rho = {0.f, 0.f};
 #pragma unroll 2
-            for (int k = lane; k < K; k += TPA) {
+            for (int k = lane; k < K; k += 2) {
                 const int code = s_sc[stb + k];
                 const int j = s_lx[sx + (code & 255)] + s_ly[sy + ((code >> 8) & 255)] +
-                              s_lz[sz + ((code >> 16) & 255)] + (code >> 24);
+                              s_lz[sz + ((code >> 16) & 255)] + (code >> 24) * ncell;
                 const float4 uj = s_u[j];
                 const float4 e = s_sv[stb + k];
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 < rc2) {
                     if (r2 < rmin2) bad |= ST_ERANGE;
-                    const float r = sqrtf(r2);
+                    const float r = r2 * rsqrtf(r2);
                     const float t = r * inv_h;
                     const int kk = min(max((int)t, 0), nk - 2);
                     const float w = t - (float)kk;
                     const float4 c = kk >= k_lo ? s_tab[2 * (kk - k_lo) + 1] : __ldg(&tab.pf32[2 * kk + 1]);
                     rho = df_add(rho, {c.x + w * (c.y + w * (c.z + w * c.w)), 0.f});
-                    if (m < SLMAX / TPA)
-                        s_sl[slot * SLMAX + m * TPA + lane] = (unsigned short)k;
+                    if (m < SLMAX / 2)
+                        s_sl[(lane * SLOTS + slot) * (SLMAX / 2) + m] = (unsigned short)k;
                     else
                         bad |= ST_ENEIGH;
                     ++m;
                 }
             }
-            n_cand += (K > lane) ? (unsigned)((K - lane + TPA - 1) / TPA) : 0u;
-            m = min(m, SLMAX / TPA);
+            n_cand += (K > lane) ? (unsigned)((K - lane + 1) / 2) : 0u;
+            m = min(m, SLMAX / 2);
             n_pair += (unsigned)m;
-            for (int o = TPA >> 1; o > 0; o >>= 1)
-                rho = df_add(rho, {__shfl_xor_sync(0xffffffffu, rho.hi, o), __shfl_xor_sync(0xffffffffu, rho.lo, o)});
-            if (valid && lane == 0) s_rho[slot] = make_float2(rho.hi, rho.lo);
+            if (valid) s_rho[lane * SLOTS + slot] = make_float2(rho.hi, rho.lo);
         }
         __syncthreads();
         // embedding of the owned atom: rho to FP64 once, F(rho), F'(rho)
         float emb = 0.f;
         if (own) {
-            const float2 rr = s_rho[threadIdx.x];
-            const double rho = (double)rr.x + (double)rr.y;
+            const float2 r0_ = s_rho[threadIdx.x], r1_ = s_rho[SLOTS + threadIdx.x];
+            const dfl rr = df_add({r0_.x, r0_.y}, {r1_.x, r1_.y});
+            const double rho = (double)rr.hi + (double)rr.lo;
             if (!(rho < tab.rho_max)) bad |= ST_ERANGE;
             const double t = rho * tab.inv_h_rho;
             const int kk = min(max((int)t, 0), nk - 2);
@@ -316,7 +368,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const float4 c = __ldg(&tab.F32[kk]);
             emb = c.x + w * (c.y + w * (c.z + w * c.w));
             const float dF = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * tab.inv_h_rhof;
-            for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[ta].w = dF;
+            for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[tsu].w = dF;
             if (!isfinite(emb)) bad |= ST_ENAN;
         }
         cluster.sync();  // F' visible everywhere
@@ -324,18 +376,19 @@ __global__ void __launch_bounds__(THREADS, 1)
         // ---------------- pass 2: forces and pair energy (pair threads)
         {
             float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
-            const float dFi = s_u[ai].w;
+            const float dFi = s_u[sui].w;
 #pragma unroll 2
             for (int q = 0; q < m; ++q) {
-                const int k = s_sl[slot * SLMAX + q * TPA + lane];
+                const int k = s_sl[(lane * SLOTS + slot) * (SLMAX / 2) + q];
                 const int code = s_sc[stb + k];
                 const int j = s_lx[sx + (code & 255)] + s_ly[sy + ((code >> 8) & 255)] +
-                              s_lz[sz + ((code >> 16) & 255)] + (code >> 24);
+                              s_lz[sz + ((code >> 16) & 255)] + (code >> 24) * ncell;
                 const float4 uj = s_u[j];
                 const float4 e = s_sv[stb + k];
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
-                const float r = sqrtf(dx * dx + dy * dy + dz * dz);
-                const float ir = 1.f / r;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const float ir = rsqrtf(r2);
+                const float r = r2 * ir;
                 const float t = r * inv_h;
                 const int kk = min(max((int)t, 0), nk - 2);
                 const float w = t - (float)kk;
@@ -356,105 +409,60 @@ __global__ void __launch_bounds__(THREADS, 1)
                 fz += sc * dz;
                 ep += 0.5f * phi;
             }
-            for (int o = TPA >> 1; o > 0; o >>= 1) {
-                fx += __shfl_xor_sync(0xffffffffu, fx, o);
-                fy += __shfl_xor_sync(0xffffffffu, fy, o);
-                fz += __shfl_xor_sync(0xffffffffu, fz, o);
-                ep += __shfl_xor_sync(0xffffffffu, ep, o);
-            }
-            if (valid && lane == 0) s_f[slot] = make_float4(fx, fy, fz, ep);
+            if (valid) s_f[lane * SLOTS + slot] = make_float4(fx, fy, fz, ep);
         }
         __syncthreads();
-        // noise of the owned atom and the CTA partial sums of step s
-        float F0[3] = {0.f, 0.f, 0.f}, xi[3] = {0.f, 0.f, 0.f};
-        {
-            dfl pa[NA_] = {};
-            if (own) {
-                const float4 f = s_f[threadIdx.x];
-                F0[0] = f.x;
-                F0[1] = f.y;
-                F0[2] = f.z;
-                if (!fin)
-                    ne_normals32(ne_philox_block(reps[rep].seed, reps[rep].replica, (unsigned)S.stream,
-                                                 (unsigned)ta, (unsigned long long)s),
-                                 xi);
-                pa[A_UEMB] = {emb, 0.f};
-                pa[A_UPAIR] = {f.w, 0.f};
-                pa[A_FX] = {f.x, 0.f};
-                pa[A_FY] = {f.y, 0.f};
-                pa[A_FZ] = {f.z, 0.f};
-                pa[A_XX] = {xi[0], 0.f};
-                pa[A_XY] = {xi[1], 0.f};
-                pa[A_XZ] = {xi[2], 0.f};
-            }
-            cta_sum_bcast<NA_, false>(cluster, pa, 0.f, s_red, s_slotA, nullptr, rank, C);
-        }
-        cluster.sync();  // partial sums of step s complete in every CTA
-
-        // ---------------- replica totals (fixed order over the cluster's CTAs)
-        if (threadIdx.x < NA_ + NB_ - 1) {
-            const int q = threadIdx.x;
-            double acc = 0.0;
-            if (q < NA_) {
-                for (int r = 0; r < C; ++r) acc += s_slotA[r * NA_ + q];
-            } else {
-                const double* sb = s_slotB + (s & 1) * 16 * (NB_ - 1);
-                for (int r = 0; r < C; ++r) acc += sb[r * (NB_ - 1) + (q - NA_)];
-            }
-            s_tot[q] = acc;
-        }
-        __syncthreads();
-        const double lam_s = s_lam[0], lam_n = s_lam[1];
-        if (!fin && rank == 0 && threadIdx.x == 0) {
-            const double U0 = s_tot[A_UEMB] + s_tot[A_UPAIR];
-            const double g = S.path == 0 ? U0 - s_tot[NA_ + B_UE] : U0;
-            int wslot = -1;
-            if (s >= S.t_eq && s < S.t_eq + S.t_s) wslot = 0;
-            else if (s >= 2 * S.t_eq + S.t_s && s < 2 * S.t_eq + 2 * S.t_s) wslot = 1;
-            if (wslot >= 0) Wg[2 * reps[rep].widx + wslot] += (lam_n - lam_s) * g;
-        }
 
         // ---------------- fused step of the owned atom
         {
-            dfl pb[NB_ - 1] = {};
+            dfl pp[NP_] = {};
             float un = 0.f;
             if (own) {
-                const float kf = reps[rep].kf, hdt = reps[rep].hdt_mf, c1 = reps[rep].c1f, c2 = reps[rep].c2f;
+                const float4 f0_ = s_f[threadIdx.x], f1_ = s_f[SLOTS + threadIdx.x];
+                const float4 f = make_float4(f0_.x + f1_.x, f0_.y + f1_.y, f0_.z + f1_.z, f0_.w + f1_.w);
+                const float F0[3] = {f.x, f.y, f.z};
+                const float hdt = reps[rep].hdt_mf, c1 = reps[rep].c1f, c2 = reps[rep].c2f;
                 const float invN = 1.f / (float)n;
-                float mF0[3], mFE[3], mxi[3];
+                float mFE[3], mxi[3];
                 for (int c = 0; c < 3; ++c) {
-                    mF0[c] = S.fix_cm ? (float)s_tot[A_FX + c] * invN : 0.f;
-                    mFE[c] = S.fix_cm ? -kf * (float)s_tot[NA_ + B_UX + c] * invN : 0.f;
-                    mxi[c] = S.fix_cm ? (float)s_tot[A_XX + c] * invN : 0.f;
+                    mFE[c] = S.fix_cm ? -kf * (float)s_tot[P_UX + c] * invN : 0.f;
+                    mxi[c] = S.fix_cm ? (float)s_tot[P_XX + c] * invN : 0.f;
                 }
-                const float ls = (float)lam_s, ln = (float)lam_n;
+                const float ls = (float)lam_tab[it], ln = (float)lam_tab[it + 1];
                 if (it > 0)
-                    for (int c = 0; c < 3; ++c) v[c] += hdt * blendf(S.path, ls, F0[c] - mF0[c], -kf * u[c] - mFE[c]);
+                    for (int c = 0; c < 3; ++c) v[c] += hdt * blendf(S.path, ls, F0[c], -kf * u[c] - mFE[c]);
+                pp[P_U0] = {emb + f.w, 0.f};
                 if (!fin) {
                     for (int c = 0; c < 3; ++c) {
-                        v[c] += hdt * blendf(S.path, ln, F0[c] - mF0[c], -kf * u[c] - mFE[c]);
+                        v[c] += hdt * blendf(S.path, ln, F0[c], -kf * u[c] - mFE[c]);
                         const float v1 = v[c];
                         v[c] = c1 * v[c] + c2 * (xi[c] - mxi[c]);
                         xr[c] += (double)(0.5f * dt * (v1 + v[c]));
                         u[c] = (float)(xr[c] - s_r0[threadIdx.x * 3 + c]);
                     }
                     const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
-                    for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[ta] = uv;
+                    for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[tsu] = uv;
+                    // normals of the next step
+                    ne_normals32(ne_philox_block(reps[rep].seed, reps[rep].replica, (unsigned)S.stream,
+                                                 (unsigned)ta, (unsigned long long)(s + 1)),
+                                 xi);
                 }
                 const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-                pb[B_UE] = {0.5f * kf * u2, 0.f};
-                pb[B_UX] = {u[0], 0.f};
-                pb[B_UY] = {u[1], 0.f};
-                pb[B_UZ] = {u[2], 0.f};
-                pb[B_U2] = {u2, 0.f};
-                pb[B_KE] = {0.5f * reps[rep].mf * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), 0.f};
+                pp[P_UE] = {0.5f * kf * u2, 0.f};
+                pp[P_UX] = {u[0], 0.f};
+                pp[P_UY] = {u[1], 0.f};
+                pp[P_UZ] = {u[2], 0.f};
+                pp[P_XX] = {xi[0], 0.f};
+                pp[P_XY] = {xi[1], 0.f};
+                pp[P_XZ] = {xi[2], 0.f};
+                pp[P_KE] = {0.5f * reps[rep].mf * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), 0.f};
                 un = sqrtf(u2);
                 for (int c = 0; c < 3; ++c)
                     if (!isfinite(xr[c]) || !isfinite(v[c])) bad |= ST_ENAN;
             }
             if (!fin)
-                cta_sum_bcast<NB_ - 1, true>(cluster, pb, un, s_red, s_slotB + ((s + 1) & 1) * 16 * (NB_ - 1),
-                                             s_slotM + ((s + 1) & 1) * 16, rank, C);
+                cta_sum_bcast<NP_, true>(cluster, pp, un, s_red, s_slotP + ((s + 1) & 1) * 16 * NP_,
+                                         s_slotM + ((s + 1) & 1) * 16, rank, C, own_warps);
         }
     }
     if (own)
@@ -486,10 +494,18 @@ size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
     size_t b = sizeof(float4) * (size_t)n_max + (sizeof(float4) + sizeof(int)) * (size_t)nb_nst_max +
                sizeof(int) * (size_t)lut_max + sizeof(unsigned short) * SLOTS * SLMAX;
     b = (b + 15) & ~(size_t)15;
-    b += sizeof(double) * (16 * NA_ + 2 * 16 * (NB_ - 1) + NA_ + NB_ + 2 + SLOTS * 3);
+    b += sizeof(double) * (2 * 16 * NP_ + NP_ + 1 + SLOTS * 3);
     b += 16;  // alignment of s_f
-    b += sizeof(float4) * SLOTS + sizeof(float2) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2 + 4);
+    b += 2 * sizeof(float4) * SLOTS + 2 * sizeof(float2) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2 + 8);
     return ((b + 15) & ~(size_t)15) + 16;  // + alignment of s_tab
+}
+
+int cluster_size_for(int n, int nb)
+{
+    int C = (n + SLOTS - 1) / SLOTS;
+    if (C < 1) C = 1;
+    while (atoms_per_cta(n, C, nb) > SLOTS) ++C;
+    return C;
 }
 
 int cluster_atoms_per_cta() { return SLOTS; }
