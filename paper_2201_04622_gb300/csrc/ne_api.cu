@@ -912,8 +912,8 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
             cr[r].ny < 3 || cr[r].nz < 3)
             return fail(ctx, NE_EINVAL, "crystal: bcc/fcc, a > 0 and at least 3 cells per axis");
         const long long nn = (long long)(cr[r].lattice == NE_BCC ? 2 : 4) * cr[r].nx * cr[r].ny * cr[r].nz;
-        if (nn > 16ll * ne::cluster_atoms_per_cta())
-            return fail(ctx, NE_EINVAL, "crystal runner: at most 16 x 320 atoms per replica");
+        if (nn > 4096)
+            return fail(ctx, NE_EINVAL, "crystal runner: at most 4096 atoms per replica");
         off[r + 1] = off[r] + (int)nn;
     }
     ne_status s = check_batch(ctx, md, n_rep, off.data());

@@ -2,7 +2,7 @@
 // one thread-block cluster per replica runs a whole step range of the
 // four-phase switching schedule in one launch.
 //
-// Per replica, the cluster's C CTAs each own up to 256 atoms.  Every CTA
+// Per replica, the cluster's C CTAs each own up to 384 atoms.  Every CTA
 // keeps, in shared memory, the displacements from the lattice sites
 // u_j = x_j - r0_j (FP32) and F'(rho_j) of all atoms of the replica; each CTA
 // broadcasts its atoms' values to the other CTAs through distributed shared
@@ -46,7 +46,7 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int THREADS = 640;
+constexpr int THREADS = 768;  // 24 warps: six per SMSP, 80 registers a thread
 constexpr int TPA = 2;
 constexpr int SLOTS = THREADS / TPA;  // atoms per CTA (one CTA per SM)
 constexpr int SLMAX = 80;             // short-list entries per atom
