@@ -106,6 +106,16 @@ ne_status ne_ctx_get_theta(ne_ctx* ctx, double* theta_dev, void* stream);
 /* Tuning of the pair kernels: threads per atom (1, 2, 4 or 8). */
 ne_status ne_ctx_set_tuning(ne_ctx* ctx, int threads_per_atom);
 
+/* CTAs per thread-block cluster of ne_crystal_run_segment (a scheduling
+ * choice; the paper has no counterpart).  0 (the default): chosen per call --
+ * the smallest C whose CTAs hold each replica, or, when that C is the same
+ * for every replica, the C that runs the batch fastest given how many such
+ * clusters the device holds at once.  1..16: every replica uses C CTAs
+ * (NE_EINVAL at run time if that is too few for a replica).  The CTA sums of
+ * a replica depend on C, so results agree across C to rounding only; a fixed
+ * C makes a replica's bits independent of the rest of its batch. */
+ne_status ne_ctx_set_cluster_size(ne_ctx* ctx, int ctas);
+
 /* Work counters since the context was created (each pointer may be NULL):
  * list_builds -- per-replica neighbour-list builds of the multi-kernel path
  * (one at the start of every run or segment, plus one each time an atom

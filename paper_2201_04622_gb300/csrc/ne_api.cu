@@ -31,6 +31,7 @@ cudaError_t dalloc(T** p, size_t n)
 struct ne_ctx {
     ne_eam_params eam{};
     int max_atoms = 0, max_rep = 0, tiles_cap = 0, cells_cap = 0, tpa = 4;
+    int cluster_c = 0;  // crystal runner: CTAs per cluster (0: chosen per batch)
     double* theta = nullptr;
     float4* pf32 = nullptr;
     ned4* pf64 = nullptr;
@@ -585,6 +586,14 @@ ne_status ne_ctx_set_tuning(ne_ctx* ctx, int tpa)
     return NE_OK;
 }
 
+ne_status ne_ctx_set_cluster_size(ne_ctx* ctx, int ctas)
+{
+    if (!ctx) return NE_EINVAL;
+    if (ctas < 0 || ctas > 16) return fail(ctx, NE_EINVAL, "cluster size must be 0 (automatic) or 1..16");
+    ctx->cluster_c = ctas;
+    return NE_OK;
+}
+
 ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds, long long* stencil_visits, long long* pairs)
 {
     if (!ctx) return NE_EINVAL;
@@ -1003,13 +1012,73 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         nbst_max = std::max(nbst_max, X.nb * X.st_cnt);
     }
     if (sv.size() > (size_t)ctx->max_rep * 4 * NE_STENCIL_MAX) return fail(ctx, NE_ENOMEM, "stencil capacity exceeded");
-    // Replicas grouped by cluster size C = ceil(n / atoms per CTA), each group
-    // one launch on its own stream, largest replicas first.
-    const int per_cta = ne::cluster_atoms_per_cta();
+    int dev = 0, smem_max = 0;
+    NE_CU(cudaGetDevice(&dev));
+    NE_CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int nk = ctx->eam.n_knots;
+    // shared memory of a launch over replicas rs: replica state, stencil,
+    // lists and sums, then as many r intervals of the (phi, f) tables,
+    // counted down from r_c, as fit (k_lo: first interval held)
+    auto launch_smem = [&](const std::vector<int>& rs, size_t& smem, int& k_lo) -> bool {
+        int gn = 0, gnb = 0, glut = 0;
+        for (int r : rs) {
+            gn = std::max(gn, xr[r].n);
+            gnb = std::max(gnb, xr[r].nb * xr[r].st_cnt);
+            glut = std::max(glut, xr[r].nx + xr[r].ny + xr[r].nz + 6 * xr[r].st_margin);
+        }
+        const size_t base = (ne::cluster_smem_bytes(gn, gnb, glut) + 15) & ~(size_t)15;
+        if (base > (size_t)smem_max) return false;
+        const long long fit = ((long long)smem_max - (long long)base) / (2 * (long long)sizeof(float4));
+        const int n_int = (int)std::min<long long>(nk - 1, fit);
+        k_lo = nk - 1 - n_int;
+        smem = base + (size_t)n_int * 2 * sizeof(float4);
+        return true;
+    };
+    // Cluster size per replica: the smallest C whose CTAs hold it, unless the
+    // caller fixed C (ne_ctx_set_cluster_size).  When every replica needs the
+    // same smallest C, a larger C is taken if the device then runs the batch
+    // in fewer waves or with fewer atoms per CTA: clusters must fit inside one
+    // GPC, so the number of co-resident clusters (cudaOccupancyMaxActiveClusters)
+    // is not 152 / C.  The estimate is waves x (atoms per CTA + 96), the
+    // constant being the per-step cost that does not scale with the atoms.
+    std::vector<int> csel(n_rep);
+    bool uniform = true;
+    for (int r = 0; r < n_rep; ++r) {
+        csel[r] = ne::cluster_size_for(xr[r].n, xr[r].nb);
+        uniform = uniform && csel[r] == csel[0];
+    }
+    if (ctx->cluster_c > 0) {
+        for (int r = 0; r < n_rep; ++r) {
+            if (ctx->cluster_c < csel[r])
+                return fail(ctx, NE_EINVAL, "crystal runner: the fixed cluster size is too small for a replica");
+            csel[r] = ctx->cluster_c;
+        }
+    } else if (uniform) {
+        std::vector<int> all(n_rep);
+        for (int r = 0; r < n_rep; ++r) all[r] = r;
+        size_t smem = 0;
+        int k_lo = 0;
+        if (!launch_smem(all, smem, k_lo)) return fail(ctx, NE_EINVAL, "replica too large for the crystal runner");
+        int best = csel[0];
+        double best_t = -1.0;
+        for (int C = csel[0]; C <= 16; ++C) {
+            const int act = ne::cluster_max_active(C, smem);
+            if (act < 1) continue;
+            int A = 0;
+            for (int r = 0; r < n_rep; ++r) A = std::max(A, ne::cluster_atoms_for(xr[r].n, C, xr[r].nb));
+            const double t = (double)((n_rep + act - 1) / act) * (A + 96);
+            if (best_t < 0.0 || t < 0.97 * best_t) {
+                best = C;
+                best_t = t;
+            }
+        }
+        for (int r = 0; r < n_rep; ++r) csel[r] = best;
+    }
+    // Replicas grouped by cluster size, each group one launch on its own
+    // stream, largest replicas first.
     std::vector<int> order(n_rep);
     for (int r = 0; r < n_rep; ++r) order[r] = r;
-    (void)per_cta;
-    auto csize = [&](int r) { return ne::cluster_size_for(xr[r].n, xr[r].nb); };
+    auto csize = [&](int r) { return csel[r]; };
     std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
         return csize(p) > csize(q) || (csize(p) == csize(q) && xr[p].n > xr[q].n);
     });
@@ -1034,10 +1103,6 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         ctx->lam_cap = n_steps + 2;
     }
     NE_CU(ne::launch_lambda_table(S, step_begin, n_steps + 2, ctx->lam_tab, st));
-    int dev = 0, smem_max = 0;
-    NE_CU(cudaGetDevice(&dev));
-    NE_CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const int nk = ctx->eam.n_knots;
     // groups
     std::vector<std::pair<int, int>> groups;  // [begin, end) in xs
     for (int q = 0; q < n_rep;) {
@@ -1057,20 +1122,11 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
     }
     for (size_t g = 0; g < groups.size(); ++g) {
         const int b = groups[g].first, e = groups[g].second;
-        int gn = 0, gnb = 0, glut = 0;
-        for (int q = b; q < e; ++q) {
-            gn = std::max(gn, xs[q].n);
-            gnb = std::max(gnb, xs[q].nb * xs[q].st_cnt);
-            glut = std::max(glut, xs[q].nx + xs[q].ny + xs[q].nz + 6 * xs[q].st_margin);
-        }
-        // shared memory: replica state, stencil, lists and sums, then as many
-        // r intervals of the (phi, f) tables, counted down from r_c, as fit
-        const size_t base = (ne::cluster_smem_bytes(gn, gnb, glut) + 15) & ~(size_t)15;
-        if (base > (size_t)smem_max) return fail(ctx, NE_EINVAL, "replica too large for the crystal runner");
-        const long long fit = ((long long)smem_max - (long long)base) / (2 * (long long)sizeof(float4));
-        const int n_int = (int)std::min<long long>(nk - 1, fit);
-        const int k_lo = nk - 1 - n_int;
-        const size_t smem = base + (size_t)n_int * 2 * sizeof(float4);
+        std::vector<int> rs;
+        for (int q = b; q < e; ++q) rs.push_back(order[q]);
+        size_t smem = 0;
+        int k_lo = 0;
+        if (!launch_smem(rs, smem, k_lo)) return fail(ctx, NE_EINVAL, "replica too large for the crystal runner");
         cudaStream_t gs = multi ? ctx->gst[g] : st;
         if (multi) NE_CU(cudaStreamWaitEvent(gs, ctx->gev[16], 0));
         NE_CU(ne::launch_cluster(ctx->xrep + b, e - b, csize(order[b]), smem, ctx->st_vec, ctx->st_code, x_dev, v_dev,

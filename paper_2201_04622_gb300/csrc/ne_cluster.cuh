@@ -24,7 +24,9 @@ struct XRep {
 namespace ne {
 size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max);
 int cluster_atoms_per_cta();
-int cluster_size_for(int n, int nb);  // CTAs per cluster for an n-atom replica
+int cluster_size_for(int n, int nb);           // smallest CTAs per cluster for an n-atom replica
+int cluster_atoms_for(int n, int C, int nb);    // atoms per CTA of an n-atom replica on C CTAs
+int cluster_max_active(int C, size_t smem);     // co-resident clusters of C CTAs (0 if none or on error)
 cudaError_t launch_lambda_table(const Sched& S, long long s_begin, long long count, double* out, cudaStream_t st);
 cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, const float4* st_vec,
                            const int* st_code, double* x, double* v, double* W, int* status, const Sched& S,

@@ -24,8 +24,9 @@ NE_PATH_FL, NE_PATH_RS = 0, 1
 
 # every symbol include/ne.h declares
 SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_set_theta", "ne_ctx_get_theta",
-           "ne_ctx_set_tuning", "ne_ctx_counters", "ne_last_error", "ne_create_crystal", "ne_eam_energy_forces",
-           "ne_eam_energy_forces_noalloc", "ne_spring_forces", "ne_eam_backward", "ne_noise", "ne_init_velocities", "ne_langevin_step",
+           "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_counters", "ne_last_error",
+           "ne_create_crystal", "ne_eam_energy_forces", "ne_eam_energy_forces_noalloc", "ne_spring_forces",
+           "ne_eam_backward", "ne_noise", "ne_init_velocities", "ne_langevin_step",
            "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment",
            "ne_profile_segment", "ne_crystal_run_segment",
            "ne_msd_fit", "ne_free_energy",
@@ -80,6 +81,7 @@ def load(build_if_missing: bool = True):
                 "ne_ctx_set_theta": [p, p, p],
                 "ne_ctx_get_theta": [p, p, p],
                 "ne_ctx_set_tuning": [p, i],
+                "ne_ctx_set_cluster_size": [p, i],
                 "ne_ctx_counters": [p, p, p, p],
                 "ne_last_error": [p, p, p, i],
                 "ne_create_crystal": [i, d, i, i, i, p, p, p],
@@ -184,6 +186,11 @@ def ne_ctx_get_theta(ctx, theta, stream=None):
 
 def ne_ctx_set_tuning(ctx, threads_per_atom):
     _err(ctx, load().ne_ctx_set_tuning(ctx, int(threads_per_atom)), "ne_ctx_set_tuning")
+
+
+def ne_ctx_set_cluster_size(ctx, ctas):
+    """CTAs per cluster of the crystal runner (0: chosen per batch)."""
+    _err(ctx, load().ne_ctx_set_cluster_size(ctx, int(ctas)), "ne_ctx_set_cluster_size")
 
 
 def ne_ctx_counters(ctx):

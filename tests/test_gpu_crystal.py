@@ -169,3 +169,26 @@ def test_uneven_batch_size_classes_match_multikernel_path(ctx):
     ne.ne_switch_run_segment(ctx, mgs, list(offs), x2, v2, X0, boxes, W2, 0, 60)
     assert torch.abs(x - x2).max().item() < 2e-5
     assert torch.allclose(Wd, W2, rtol=1e-5, atol=1e-4)
+
+
+def test_cluster_size_changes_rounding_only(ctx):
+    """The same batch on clusters of 3 (the fewest CTAs that hold 1024
+    atoms), 5 and 16 CTAs and on the size chosen from the device's cluster
+    occupancy: the CTA sums regroup, nothing else changes."""
+    systems = [(O.BCC, 8, 1000.0, 3), (O.BCC, 8, 1000.0, 4)]
+    out = []
+    try:
+        for C in (0, 3, 5, 16):
+            ne.ne_ctx_set_cluster_size(ctx, C)
+            x, v, Wd, _, _ = run_crystals(ctx, systems, 0, 100)
+            out.append((x, Wd))
+        ne.ne_ctx_set_cluster_size(ctx, 2)
+        with pytest.raises(ne.NeError, match="NE_EINVAL"):
+            run_crystals(ctx, systems, 0, 10)
+    finally:
+        ne.ne_ctx_set_cluster_size(ctx, 0)
+    for x, Wd in out[1:]:
+        assert torch.abs(x - out[0][0]).max().item() < 2e-5
+        assert torch.allclose(Wd, out[0][1], rtol=1e-5, atol=1e-4)
+    with pytest.raises(ne.NeError, match="NE_EINVAL"):
+        ne.ne_ctx_set_cluster_size(ctx, 17)
