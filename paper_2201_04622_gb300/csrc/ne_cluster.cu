@@ -49,7 +49,9 @@ namespace {
 constexpr int THREADS = 768;  // 24 warps: six per SMSP, 80 registers a thread
 constexpr int TPA = 2;
 constexpr int SLOTS = THREADS / TPA;  // atoms per CTA (one CTA per SM)
-constexpr int SLMAX = 80;             // short-list entries per atom
+constexpr int SLMAX = 80;             // short-list entries per atom (SLMAX / TPA per thread)
+constexpr int SLQ = SLMAX / TPA;
+static_assert(NE_STENCIL_MAX / TPA <= 256, "short-list entries are bytes");
 constexpr int NWARP = THREADS / 32;
 
 // partial sums broadcast at the end of step s for step s+1
@@ -171,7 +173,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     int* s_lx = s_sc + nb * nst;                                  // [nx + 2M] wrapped x-cell * ny nz nb
     int* s_ly = s_lx + nx + 2 * M;                                // [ny + 2M]
     int* s_lz = s_ly + ny + 2 * M;                                // [nz + 2M]
-    unsigned short* s_sl = (unsigned short*)(s_lz + nz + 2 * M);  // [SLOTS][SLMAX]
+    // short list: entry q of thread (slot, lane) at [q][lane][slot], holding
+    // k / TPA of its stencil entry k (k = TPA * entry + lane)
+    unsigned char* s_sl = (unsigned char*)(s_lz + nz + 2 * M);  // [SLQ][TPA][SLOTS]
     double* s_slotP = (double*)(((size_t)(s_sl + SLOTS * SLMAX) + 15) & ~(size_t)15);  // [2][16][NP_]
     double* s_tot = s_slotP + 2 * 16 * NP_;                       // [NP_ + 1]
     double* s_r0 = s_tot + NP_ + 1;                               // [SLOTS][3] sites of the owned atoms
@@ -342,15 +346,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const float w = t - (float)kk;
                     const float4 c = kk >= k_lo ? s_tab[2 * (kk - k_lo) + 1] : __ldg(&tab.pf32[2 * kk + 1]);
                     rho = df_add(rho, {c.x + w * (c.y + w * (c.z + w * c.w)), 0.f});
-                    if (m < SLMAX / 2)
-                        s_sl[(lane * SLOTS + slot) * (SLMAX / 2) + m] = (unsigned short)k;
+                    if (m < SLQ)
+                        s_sl[(m * TPA + lane) * SLOTS + slot] = (unsigned char)(k / TPA);
                     else
                         bad |= ST_ENEIGH;
                     ++m;
                 }
             }
             n_cand += (K > lane) ? (unsigned)((K - lane + 1) / 2) : 0u;
-            m = min(m, SLMAX / 2);
+            m = min(m, SLQ);
             n_pair += (unsigned)m;
             if (valid) s_rho[lane * SLOTS + slot] = make_float2(rho.hi, rho.lo);
         }
@@ -379,7 +383,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const float dFi = s_u[sui].w;
 #pragma unroll 2
             for (int q = 0; q < m; ++q) {
-                const int k = s_sl[(lane * SLOTS + slot) * (SLMAX / 2) + q];
+                const int k = TPA * s_sl[(q * TPA + lane) * SLOTS + slot] + lane;
                 const int code = s_sc[stb + k];
                 const int j = s_lx[sx + (code & 255)] + s_ly[sy + ((code >> 8) & 255)] +
                               s_lz[sz + ((code >> 16) & 255)] + (code >> 24) * ncell;
@@ -492,7 +496,7 @@ namespace ne {
 size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
 {
     size_t b = sizeof(float4) * (size_t)n_max + (sizeof(float4) + sizeof(int)) * (size_t)nb_nst_max +
-               sizeof(int) * (size_t)lut_max + sizeof(unsigned short) * SLOTS * SLMAX;
+               sizeof(int) * (size_t)lut_max + sizeof(unsigned char) * SLOTS * SLMAX;
     b = (b + 15) & ~(size_t)15;
     b += sizeof(double) * (2 * 16 * NP_ + NP_ + 1 + SLOTS * 3);
     b += 16;  // alignment of s_f
