@@ -55,7 +55,7 @@ struct ne_ctx {
     cudaStream_t gst[16] = {};  // crystal runner: one stream per replica size class
     cudaEvent_t gev[17] = {};
     float4* st_vec = nullptr;
-    int* st_code = nullptr;
+    float* st_dist = nullptr;
     float* bins = nullptr;
     int bins_blocks = 0;
     std::vector<RepDev> rep_h;
@@ -516,7 +516,7 @@ ne_status ne_ctx_create(const ne_eam_params* eam, int max_atoms, int max_replica
     A(dalloc(&ctx->work, 2));
     if (ok) ok = cudaMemset(ctx->work, 0, 2 * sizeof(unsigned long long)) == cudaSuccess;
     A(dalloc(&ctx->st_vec, R * 4 * NE_STENCIL_MAX));
-    A(dalloc(&ctx->st_code, R * 4 * NE_STENCIL_MAX));
+    A(dalloc(&ctx->st_dist, R * 4 * NE_STENCIL_MAX));
     if (ok) ok = cudaMemset(ctx->rebuilds, 0, sizeof(unsigned long long)) == cudaSuccess;
     if (!ok) {
         ne_ctx_destroy(ctx);
@@ -546,7 +546,7 @@ ne_status ne_ctx_destroy(ne_ctx* ctx)
                     ctx->pbuild, ctx->f32, ctx->f64, ctx->dF64, ctx->rho, ctx->xi64, ctx->xi32,
                     ctx->nbr, ctx->ncnt, ctx->sl, ctx->scnt, ctx->cellof, ctx->sorted, ctx->cstart,
                     ctx->cfill, ctx->partA, ctx->partB, ctx->tot, ctx->W, ctx->scratch,
-                    ctx->tile_done, ctx->flags, ctx->building, ctx->status, ctx->tile_rep, ctx->rep, ctx->step_ctr, ctx->rebuilds, ctx->xrep, ctx->work, ctx->st_vec, ctx->st_code, ctx->lam_tab,
+                    ctx->tile_done, ctx->flags, ctx->building, ctx->status, ctx->tile_rep, ctx->rep, ctx->step_ctr, ctx->rebuilds, ctx->xrep, ctx->work, ctx->st_vec, ctx->st_dist, ctx->lam_tab,
                     ctx->bins};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -909,6 +909,15 @@ ne_status ne_switch_run_batched(ne_ctx* ctx, const ne_md_params* md, int n_rep, 
                            W_bwd_dev, nullptr, nullptr, nullptr, 0, (cudaStream_t)stream);
 }
 
+// the packed neighbour code of a stencil entry, carried in the .w of its
+// lattice vector as the float with the same bits
+static float code_bits(int code)
+{
+    float f;
+    std::memcpy(&f, &code, sizeof f);
+    return f;
+}
+
 ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep,
                                  double* x_dev, double* v_dev, double* W_dev, long long step_begin,
                                  long long n_steps, void* stream)
@@ -936,8 +945,8 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
     static const double fcc[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
     const double rc = ctx->eam.r_c;
     std::vector<XRep> xr(n_rep);
-    std::vector<float4> sv;
-    std::vector<int> sc;
+    std::vector<float4> sv;  // (lattice vector, neighbour code as float bits)
+    std::vector<float> sd;   // |lattice vector|
     int n_max = 0, nbst_max = 0, lut_max = 0;
     (void)n_max;
     for (int r = 0; r < n_rep; ++r) {
@@ -985,7 +994,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
                             const double d = std::sqrt(ex * ex + ey * ey + ez * ez);
                             if (d >= Rst) continue;
                             const int code = (dx + M) | ((dy + M) << 8) | ((dz + M) << 16) | (b2 << 24);
-                            per[b].push_back({d, {make_float4((float)ex, (float)ey, (float)ez, (float)d), code}});
+                            per[b].push_back({d, {make_float4((float)ex, (float)ey, (float)ez, code_bits(code)), code}});
                         }
             std::stable_sort(per[b].begin(), per[b].end(), [](const auto& p, const auto& q) {
                 return p.first < q.first || (p.first == q.first && p.second.second < q.second.second);
@@ -1002,10 +1011,10 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
             for (size_t q = 0; q < cnt; ++q) {
                 if (q < per[b].size()) {
                     sv.push_back(per[b][q].second.first);
-                    sc.push_back(per[b][q].second.second);
+                    sd.push_back((float)per[b][q].first);
                 } else {  // padding: beyond any cutoff
-                    sv.push_back(make_float4(0.f, 0.f, 0.f, 1e30f));
-                    sc.push_back(M | (M << 8) | (M << 16));
+                    sv.push_back(make_float4(0.f, 0.f, 0.f, code_bits(M | (M << 8) | (M << 16))));
+                    sd.push_back(1e30f);
                 }
             }
         n_max = std::max(n_max, X.n);
@@ -1089,7 +1098,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
     }
     NE_CU(cudaMemcpyAsync(ctx->xrep, xs.data(), sizeof(XRep) * n_rep, cudaMemcpyHostToDevice, st));
     NE_CU(cudaMemcpyAsync(ctx->st_vec, sv.data(), sizeof(float4) * sv.size(), cudaMemcpyHostToDevice, st));
-    NE_CU(cudaMemcpyAsync(ctx->st_code, sc.data(), sizeof(int) * sc.size(), cudaMemcpyHostToDevice, st));
+    NE_CU(cudaMemcpyAsync(ctx->st_dist, sd.data(), sizeof(float) * sd.size(), cudaMemcpyHostToDevice, st));
     NE_CU(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
     Sched S = make_sched(md[0]);
     if (n_steps + 2 > ctx->lam_cap) {
@@ -1129,7 +1138,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         if (!launch_smem(rs, smem, k_lo)) return fail(ctx, NE_EINVAL, "replica too large for the crystal runner");
         cudaStream_t gs = multi ? ctx->gst[g] : st;
         if (multi) NE_CU(cudaStreamWaitEvent(gs, ctx->gev[16], 0));
-        NE_CU(ne::launch_cluster(ctx->xrep + b, e - b, csize(order[b]), smem, ctx->st_vec, ctx->st_code, x_dev, v_dev,
+        NE_CU(ne::launch_cluster(ctx->xrep + b, e - b, csize(order[b]), smem, ctx->st_vec, ctx->st_dist, x_dev, v_dev,
                                  W_dev, ctx->status, S, step_begin, n_steps, ctx->tab, ctx->work, k_lo, ctx->lam_tab,
                                  gs));
         if (multi) {

@@ -18,8 +18,10 @@
 //   [cluster barrier]  replica sums of step s (from the partial sums every
 //                      CTA broadcast at the end of step s-1): noise mean,
 //                      spring mean, max |u|; the work increment of step s-1;
-//                      pass 1: rho, F(rho), F'(rho), short list, F' broadcast
-//   [cluster barrier]  pass 2: forces and pair energy; closing and opening
+//                      pass 1: rho, the pair forces phi'(r) and energy phi(r),
+//                      short list; F(rho), F'(rho), F' broadcast
+//   [cluster barrier]  pass 2: the embedding forces (F'_i + F'_j) f'(r) over
+//                      the short list; closing and opening
 //                      half kicks, drift, Ornstein-Uhlenbeck, drift; new u
 //                      broadcast; the normals of step s+1 (counter-based, so
 //                      drawn one step ahead); CTA partial sums for step s+1.
@@ -151,7 +153,7 @@ __host__ __device__ inline int atoms_per_cta(int n, int C, int nb)
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
-    k_cluster(const XRep* __restrict__ reps, const float4* __restrict__ st_vec, const int* __restrict__ st_code,
+    k_cluster(const XRep* __restrict__ reps, const float4* __restrict__ st_vec, const float* __restrict__ st_dist,
               double* __restrict__ xg, double* __restrict__ vg, double* __restrict__ Wg, int* status, Sched S,
               long long s_begin, long long n_steps, Tables tab, unsigned long long* work, int k_lo,
               const double* __restrict__ lam_tab)
@@ -168,9 +170,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     // ---- shared memory
     float4* s_u = (float4*)smem;                                  // [n] (u, F')
-    float4* s_sv = s_u + n;                                       // [nb * nst] (r0_j - r0_i, |.|)
-    int* s_sc = (int*)(s_sv + nb * nst);                          // [nb * nst] packed offsets
-    int* s_lx = s_sc + nb * nst;                                  // [nx + 2M] wrapped x-cell * ny nz nb
+    float4* s_sv = s_u + n;                                       // [nb * nst] (r0_j - r0_i, code bits)
+    float* s_sd = (float*)(s_sv + nb * nst);                      // [nb * nst] |r0_j - r0_i|
+    int* s_lx = (int*)(s_sd + nb * nst);                          // [nx + 2M] wrapped x-cell * ny nz
     int* s_ly = s_lx + nx + 2 * M;                                // [ny + 2M]
     int* s_lz = s_ly + ny + 2 * M;                                // [nz + 2M]
     // short list: entry q of thread (slot, lane) at [q][lane][slot], holding
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     for (int q = threadIdx.x; q < nb * nst; q += THREADS) {
         s_sv[q] = st_vec[reps[rep].st_off + q];
-        s_sc[q] = st_code[reps[rep].st_off + q];
+        s_sd[q] = st_dist[reps[rep].st_off + q];
     }
     const int n_int = tab.nk - 1 - k_lo;  // intervals of the r grid held in shared memory
     for (int q = threadIdx.x; q < 2 * n_int; q += THREADS) s_tab[q] = tab.pf32[2 * k_lo + q];
@@ -316,36 +318,52 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         const float umax = s_misc[0];
 
-        // ---------------- pass 1: density and short list (pair threads)
+        // ---------------- pass 1: density, pair forces and energy, short list
+        // (pair threads); the F'(rho) terms of the forces follow in pass 2
         const float4 ui = s_u[sui];
         int m = 0;
+        float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
         {
             const float cut = rc + sqrtf(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + umax;
             int lo = 0, hi = nst;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (s_sv[stb + mid].w < cut) lo = mid + 1;
+                if (s_sd[stb + mid] < cut) lo = mid + 1;
                 else hi = mid;
             }
             const int K = valid ? lo : 0;
             dfl rho = {0.f, 0.f};
 #pragma unroll 2
             for (int k = lane; k < K; k += 2) {
-                const int code = s_sc[stb + k];
+                const float4 e = s_sv[stb + k];
+                const int code = __float_as_int(e.w);
                 const int j = s_lx[sx + (code & 255)] + s_ly[sy + ((code >> 8) & 255)] +
                               s_lz[sz + ((code >> 16) & 255)] + (code >> 24) * ncell;
                 const float4 uj = s_u[j];
-                const float4 e = s_sv[stb + k];
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 < rc2) {
                     if (r2 < rmin2) bad |= ST_ERANGE;
-                    const float r = r2 * rsqrtf(r2);
+                    const float ir = rsqrtf(r2);
+                    const float r = r2 * ir;
                     const float t = r * inv_h;
                     const int kk = min(max((int)t, 0), nk - 2);
                     const float w = t - (float)kk;
-                    const float4 c = kk >= k_lo ? s_tab[2 * (kk - k_lo) + 1] : __ldg(&tab.pf32[2 * kk + 1]);
-                    rho = df_add(rho, {c.x + w * (c.y + w * (c.z + w * c.w)), 0.f});
+                    float4 c, g;
+                    if (kk >= k_lo) {
+                        c = s_tab[2 * (kk - k_lo)];
+                        g = s_tab[2 * (kk - k_lo) + 1];
+                    } else {
+                        c = __ldg(&tab.pf32[2 * kk]);
+                        g = __ldg(&tab.pf32[2 * kk + 1]);
+                    }
+                    rho = df_add(rho, {g.x + w * (g.y + w * (g.z + w * g.w)), 0.f});
+                    const float phi = c.x + w * (c.y + w * (c.z + w * c.w));
+                    const float sc = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * inv_h * ir;
+                    fx += sc * dx;
+                    fy += sc * dy;
+                    fz += sc * dz;
+                    ep += 0.5f * phi;
                     if (m < SLQ)
                         s_sl[(m * TPA + lane) * SLOTS + slot] = (unsigned char)(k / TPA);
                     else
@@ -377,18 +395,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         cluster.sync();  // F' visible everywhere
 
-        // ---------------- pass 2: forces and pair energy (pair threads)
+        // ---------------- pass 2: embedding forces (F'_i + F'_j) f'(r) over
+        // the short list (pair threads)
         {
-            float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
             const float dFi = s_u[sui].w;
 #pragma unroll 2
             for (int q = 0; q < m; ++q) {
                 const int k = TPA * s_sl[(q * TPA + lane) * SLOTS + slot] + lane;
-                const int code = s_sc[stb + k];
+                const float4 e = s_sv[stb + k];
+                const int code = __float_as_int(e.w);
                 const int j = s_lx[sx + (code & 255)] + s_ly[sy + ((code >> 8) & 255)] +
                               s_lz[sz + ((code >> 16) & 255)] + (code >> 24) * ncell;
                 const float4 uj = s_u[j];
-                const float4 e = s_sv[stb + k];
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 const float ir = rsqrtf(r2);
@@ -396,22 +414,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const float t = r * inv_h;
                 const int kk = min(max((int)t, 0), nk - 2);
                 const float w = t - (float)kk;
-                float4 c, g;
-                if (kk >= k_lo) {
-                    c = s_tab[2 * (kk - k_lo)];
-                    g = s_tab[2 * (kk - k_lo) + 1];
-                } else {
-                    c = __ldg(&tab.pf32[2 * kk]);
-                    g = __ldg(&tab.pf32[2 * kk + 1]);
-                }
-                const float phi = c.x + w * (c.y + w * (c.z + w * c.w));
-                const float dphi = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * inv_h;
-                const float df = (g.y + w * (2.f * g.z + 3.f * w * g.w)) * inv_h;
-                const float sc = (dphi + (dFi + uj.w) * df) * ir;
+                const float4 g = kk >= k_lo ? s_tab[2 * (kk - k_lo) + 1] : __ldg(&tab.pf32[2 * kk + 1]);
+                const float sc = (dFi + uj.w) * (g.y + w * (2.f * g.z + 3.f * w * g.w)) * inv_h * ir;
                 fx += sc * dx;
                 fy += sc * dy;
                 fz += sc * dz;
-                ep += 0.5f * phi;
             }
             if (valid) s_f[lane * SLOTS + slot] = make_float4(fx, fy, fz, ep);
         }
@@ -495,7 +502,7 @@ namespace ne {
 // Bytes of everything but the spline tables; the tables take what is left.
 size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
 {
-    size_t b = sizeof(float4) * (size_t)n_max + (sizeof(float4) + sizeof(int)) * (size_t)nb_nst_max +
+    size_t b = sizeof(float4) * (size_t)n_max + (sizeof(float4) + sizeof(float)) * (size_t)nb_nst_max +
                sizeof(int) * (size_t)lut_max + sizeof(unsigned char) * SLOTS * SLMAX;
     b = (b + 15) & ~(size_t)15;
     b += sizeof(double) * (2 * 16 * NP_ + NP_ + 1 + SLOTS * 3);
@@ -547,7 +554,7 @@ cudaError_t launch_lambda_table(const Sched& S, long long s_begin, long long cou
 }
 
 cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, const float4* st_vec,
-                           const int* st_code, double* x, double* v, double* W, int* status, const Sched& S,
+                           const float* st_dist, double* x, double* v, double* W, int* status, const Sched& S,
                            long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
                            int k_lo, double* lam_tab, cudaStream_t st)
 {
@@ -569,7 +576,7 @@ cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, cons
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_cluster, reps, st_vec, st_code, x, v, W, status, S, s_begin, n_steps, tab,
+    return cudaLaunchKernelEx(&cfg, k_cluster, reps, st_vec, st_dist, x, v, W, status, S, s_begin, n_steps, tab,
                               work, k_lo, (const double*)lam_tab);
 }
 
