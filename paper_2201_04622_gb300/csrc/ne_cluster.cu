@@ -186,14 +186,18 @@ __global__ void __launch_bounds__(THREADS, 1)
     float* s_slotM = (float*)(s_rho + 2 * SLOTS);                 // [2][16] max |u| per CTA
     float* s_red = s_slotM + 32;                                  // [NWARP][NRED][2]
     float* s_misc = s_red + NWARP * NRED * 2;                     // [8]
-    float4* s_tab = (float4*)(((size_t)(s_misc + 8) + 15) & ~(size_t)15);  // [nk-1-k_lo][2] (phi, f)
+    // spline intervals [k_lo, nk - 1) of phi, then of f: separate arrays, so
+    // consecutive intervals fall in consecutive 16-byte bank groups
+    float4* s_tabP = (float4*)(((size_t)(s_misc + 8) + 15) & ~(size_t)15);  // [nk-1-k_lo]
 
     for (int q = threadIdx.x; q < nb * nst; q += THREADS) {
         s_sv[q] = st_vec[reps[rep].st_off + q];
         s_sd[q] = st_dist[reps[rep].st_off + q];
     }
     const int n_int = tab.nk - 1 - k_lo;  // intervals of the r grid held in shared memory
-    for (int q = threadIdx.x; q < 2 * n_int; q += THREADS) s_tab[q] = tab.pf32[2 * k_lo + q];
+    float4* s_tabF = s_tabP + n_int;                                           // [nk-1-k_lo]
+    for (int q = threadIdx.x; q < 2 * n_int; q += THREADS)
+        ((q & 1) ? s_tabF : s_tabP)[q >> 1] = tab.pf32[2 * k_lo + q];
     // shared-memory copy of the replica is basis-major: entry b * ncell + cell
     const int ncell = n / nb;
     for (int q = threadIdx.x; q < nx + 2 * M; q += THREADS) s_lx[q] = (((q - M) % nx + nx) % nx) * ny * nz;
@@ -351,8 +355,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const float w = t - (float)kk;
                     float4 c, g;
                     if (kk >= k_lo) {
-                        c = s_tab[2 * (kk - k_lo)];
-                        g = s_tab[2 * (kk - k_lo) + 1];
+                        c = s_tabP[kk - k_lo];
+                        g = s_tabF[kk - k_lo];
                     } else {
                         c = __ldg(&tab.pf32[2 * kk]);
                         g = __ldg(&tab.pf32[2 * kk + 1]);
@@ -414,7 +418,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const float t = r * inv_h;
                 const int kk = min(max((int)t, 0), nk - 2);
                 const float w = t - (float)kk;
-                const float4 g = kk >= k_lo ? s_tab[2 * (kk - k_lo) + 1] : __ldg(&tab.pf32[2 * kk + 1]);
+                const float4 g = kk >= k_lo ? s_tabF[kk - k_lo] : __ldg(&tab.pf32[2 * kk + 1]);
                 const float sc = (dFi + uj.w) * (g.y + w * (2.f * g.z + 3.f * w * g.w)) * inv_h * ir;
                 fx += sc * dx;
                 fy += sc * dy;
@@ -508,7 +512,7 @@ size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
     b += sizeof(double) * (2 * 16 * NP_ + NP_ + 1 + SLOTS * 3);
     b += 16;  // alignment of s_f
     b += 2 * sizeof(float4) * SLOTS + 2 * sizeof(float2) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2 + 8);
-    return ((b + 15) & ~(size_t)15) + 16;  // + alignment of s_tab
+    return ((b + 15) & ~(size_t)15) + 16;  // + alignment of the tables
 }
 
 int cluster_size_for(int n, int nb)
