@@ -56,8 +56,11 @@ constexpr int SLQ = SLMAX / TPA;
 static_assert(NE_STENCIL_MAX / TPA <= 256, "short-list entries are bytes");
 constexpr int NWARP = THREADS / 32;
 
-// partial sums broadcast at the end of step s for step s+1
-enum { P_U0 = 0, P_UE, P_UX, P_UY, P_UZ, P_XX, P_XY, P_XZ, P_KE, NP_ };
+// partial sums broadcast at the end of step s for step s+1: the energies
+// (double-float within a CTA), then sum u and sum xi for the mean removal (FP32
+// within a CTA); all in FP64 across the cluster
+enum { P_U0 = 0, P_UE, P_UX, P_UY, P_UZ, P_XX, P_XY, P_XZ, NP_ };
+constexpr int ND_ = 2, NF_ = NP_ - ND_;
 // values per warp in the reduction scratch: the larger of the two reductions
 constexpr int NRED = (int)NP_ + 1;  // sums and one maximum
 
@@ -88,40 +91,52 @@ __device__ __forceinline__ void warp_df_sum(dfl (&v)[NV])
         }
 }
 
-// CTA sums of NV double-float values (and, when HASMAX, the maximum of mx),
+// CTA sums of ND double-float and NF FP32 values and the maximum of mx,
 // written into slot `rank` of the slot arrays of every CTA of the cluster:
-// sums to dst[rank * NV + q] (FP64), the maximum to mslot[rank] (FP32).  The
-// warps' partials are combined in double-float (FP32 arithmetic) and
-// converted to FP64 once.  One __syncthreads; the caller separates two uses
-// of s_red by a cluster barrier.
-template <int NV, bool HASMAX>
-__device__ __forceinline__ void cta_sum_bcast(cg::cluster_group& cluster, dfl (&v)[NV], float mx, float* s_red,
-                                              double* dst, float* mslot, int rank, int C, int nwarp)
+// sums to dst[rank * (ND + NF) + q] (FP64), the maximum to mslot[rank]
+// (FP32).  The warps' partials are combined in fixed order, the double-float
+// ones in double-float (FP32 arithmetic), and converted to FP64 once.  One
+// __syncthreads; the caller separates two uses of s_red by a cluster barrier.
+template <int ND, int NF>
+__device__ __forceinline__ void cta_sum_bcast(cg::cluster_group& cluster, dfl (&vd)[ND], float (&vf)[NF], float mx,
+                                              float* s_red, double* dst, float* mslot, int rank, int C, int nwarp)
 {
+    constexpr int NV = ND + NF;
+    static_assert(NV + 1 <= NRED, "reduction scratch too small");
     // only the first nwarp warps hold values (the threads that own atoms)
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (w < nwarp) {
-        warp_df_sum<NV>(v);
-        if (HASMAX)
-            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    constexpr int NS = NV + (HASMAX ? 1 : 0);
-    static_assert(NS <= NRED, "reduction scratch too small");
-    if (l == 0 && w < nwarp) {
-        for (int q = 0; q < NV; ++q) {
-            s_red[(w * NRED + q) * 2] = v[q].hi;
-            s_red[(w * NRED + q) * 2 + 1] = v[q].lo;
+        warp_df_sum<ND>(vd);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) vf[q] += __shfl_xor_sync(0xffffffffu, vf[q], o);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         }
-        if (HASMAX) s_red[(w * NRED + NV) * 2] = mx;
+        if (l == 0) {
+            for (int q = 0; q < ND; ++q) {
+                s_red[(w * NRED + q) * 2] = vd[q].hi;
+                s_red[(w * NRED + q) * 2 + 1] = vd[q].lo;
+            }
+            for (int q = 0; q < NF; ++q) s_red[(w * NRED + ND + q) * 2] = vf[q];
+            s_red[(w * NRED + NV) * 2] = mx;
+        }
     }
     __syncthreads();
-    if (threadIdx.x < NS) {
+    if (threadIdx.x <= NV) {
         const int q = threadIdx.x;
         if (q < NV) {
-            dfl acc = {0.f, 0.f};
-            for (int ww = 0; ww < nwarp; ++ww)
-                acc = df_add(acc, {s_red[(ww * NRED + q) * 2], s_red[(ww * NRED + q) * 2 + 1]});
-            const double d = (double)acc.hi + (double)acc.lo;
+            double d;
+            if (q < ND) {
+                dfl acc = {0.f, 0.f};
+                for (int ww = 0; ww < nwarp; ++ww)
+                    acc = df_add(acc, {s_red[(ww * NRED + q) * 2], s_red[(ww * NRED + q) * 2 + 1]});
+                d = (double)acc.hi + (double)acc.lo;
+            } else {
+                float acc = 0.f;
+                for (int ww = 0; ww < nwarp; ++ww) acc += s_red[(ww * NRED + q) * 2];
+                d = (double)acc;
+            }
             for (int r = 0; r < C; ++r) cluster.map_shared_rank(dst, r)[rank * NV + q] = d;
         } else {
             float m = 0.f;
@@ -241,7 +256,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     int bad = 0;
     const float kf = reps[rep].kf;
     {
-        dfl pp[NP_] = {};
+        dfl pd[ND_] = {};
+        float pf[NF_] = {};
         float um = 0.f;
         if (own) {
             const int b = ta % nb;
@@ -264,24 +280,23 @@ __global__ void __launch_bounds__(THREADS, 1)
                                          (unsigned long long)s_begin),
                          xi);
             const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            pp[P_UE] = {0.5f * kf * u2, 0.f};
-            pp[P_UX] = {u[0], 0.f};
-            pp[P_UY] = {u[1], 0.f};
-            pp[P_UZ] = {u[2], 0.f};
-            pp[P_XX] = {xi[0], 0.f};
-            pp[P_XY] = {xi[1], 0.f};
-            pp[P_XZ] = {xi[2], 0.f};
-            pp[P_KE] = {0.5f * reps[rep].mf * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), 0.f};
+            pd[P_UE] = {0.5f * kf * u2, 0.f};
+            for (int c = 0; c < 3; ++c) {
+                pf[P_UX - ND_ + c] = u[c];
+                pf[P_XX - ND_ + c] = xi[c];
+            }
             um = sqrtf(u2);
         }
-        cta_sum_bcast<NP_, true>(cluster, pp, um, s_red, s_slotP + (s_begin & 1) * 16 * NP_,
-                                 s_slotM + (s_begin & 1) * 16, rank, C, own_warps);
+        cta_sum_bcast<ND_, NF_>(cluster, pd, pf, um, s_red, s_slotP + (s_begin & 1) * 16 * NP_,
+                                s_slotM + (s_begin & 1) * 16, rank, C, own_warps);
     }
 
     unsigned n_cand = 0, n_pair = 0;  // work counters (stencil entries visited, pairs < r_c)
     const float rc = (float)tab.r_c, rc2 = tab.rc2f, rmin2 = tab.rmin2f, inv_h = tab.inv_h_rf;
     const int nk = tab.nk;
     const float dt = (float)S.dt;
+    const float rho_maxf = (float)tab.rho_max;
+    const float ihr_hi = (float)tab.inv_h_rho, ihr_lo = (float)(tab.inv_h_rho - (double)ihr_hi);
     double UE_prev = 0.0;  // rank 0, thread 0: U_E at the positions of the previous step
 
 #pragma unroll 1
@@ -386,11 +401,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (own) {
             const float2 r0_ = s_rho[threadIdx.x], r1_ = s_rho[SLOTS + threadIdx.x];
             const dfl rr = df_add({r0_.x, r0_.y}, {r1_.x, r1_.y});
-            const double rho = (double)rr.hi + (double)rr.lo;
-            if (!(rho < tab.rho_max)) bad |= ST_ERANGE;
-            const double t = rho * tab.inv_h_rho;
-            const int kk = min(max((int)t, 0), nk - 2);
-            const float w = (float)(t - kk);
+            if (!(rr.hi < rho_maxf)) bad |= ST_ERANGE;
+            // offset in the interval from the double-float rho: the product
+            // with the high part of 1/h exact inside the FMA, the low parts added
+            const int kk = min(max((int)(rr.hi * ihr_hi), 0), nk - 2);
+            const float w = fmaf(rr.hi, ihr_hi, -(float)kk) + (rr.hi * ihr_lo + rr.lo * ihr_hi);
             const float4 c = __ldg(&tab.F32[kk]);
             emb = c.x + w * (c.y + w * (c.z + w * c.w));
             const float dF = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * tab.inv_h_rhof;
@@ -430,7 +445,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 
         // ---------------- fused step of the owned atom
         {
-            dfl pp[NP_] = {};
+            dfl pd[ND_] = {};
+            float pf[NF_] = {};
             float un = 0.f;
             if (own) {
                 const float4 f0_ = s_f[threadIdx.x], f1_ = s_f[SLOTS + threadIdx.x];
@@ -446,7 +462,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const float ls = (float)lam_tab[it], ln = (float)lam_tab[it + 1];
                 if (it > 0)
                     for (int c = 0; c < 3; ++c) v[c] += hdt * blendf(S.path, ls, F0[c], -kf * u[c] - mFE[c]);
-                pp[P_U0] = {emb + f.w, 0.f};
+                pd[P_U0] = {emb + f.w, 0.f};
                 if (!fin) {
                     for (int c = 0; c < 3; ++c) {
                         v[c] += hdt * blendf(S.path, ln, F0[c], -kf * u[c] - mFE[c]);
@@ -463,21 +479,18 @@ __global__ void __launch_bounds__(THREADS, 1)
                                  xi);
                 }
                 const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-                pp[P_UE] = {0.5f * kf * u2, 0.f};
-                pp[P_UX] = {u[0], 0.f};
-                pp[P_UY] = {u[1], 0.f};
-                pp[P_UZ] = {u[2], 0.f};
-                pp[P_XX] = {xi[0], 0.f};
-                pp[P_XY] = {xi[1], 0.f};
-                pp[P_XZ] = {xi[2], 0.f};
-                pp[P_KE] = {0.5f * reps[rep].mf * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), 0.f};
+                pd[P_UE] = {0.5f * kf * u2, 0.f};
+                for (int c = 0; c < 3; ++c) {
+                    pf[P_UX - ND_ + c] = u[c];
+                    pf[P_XX - ND_ + c] = xi[c];
+                }
                 un = sqrtf(u2);
                 for (int c = 0; c < 3; ++c)
                     if (!isfinite(xr[c]) || !isfinite(v[c])) bad |= ST_ENAN;
             }
             if (!fin)
-                cta_sum_bcast<NP_, true>(cluster, pp, un, s_red, s_slotP + ((s + 1) & 1) * 16 * NP_,
-                                         s_slotM + ((s + 1) & 1) * 16, rank, C, own_warps);
+                cta_sum_bcast<ND_, NF_>(cluster, pd, pf, un, s_red, s_slotP + ((s + 1) & 1) * 16 * NP_,
+                                        s_slotM + ((s + 1) & 1) * 16, rank, C, own_warps);
         }
     }
     if (own)
