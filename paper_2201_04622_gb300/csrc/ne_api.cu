@@ -981,6 +981,13 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         X.D = (float)D;
         const double Rst = rc + 2.0 * D;
         const int M = (int)std::ceil(Rst / X.a) + 1;
+        // neighbour code of a stencil entry (dx, dy, dz, b2): bits 0-9 the
+        // offset (dx + M) * (ny + 2M) + dy + M into the xy table of wrapped
+        // cells, bits 10-14 dz + M, bits 15-31 b2 * (cells per replica), the
+        // start of basis site b2 in the basis-major copy of the replica
+        const int LY = X.ny + 2 * M, ncell = X.nx * X.ny * X.nz;
+        if (2 * M * LY + 2 * M >= 1024 || 2 * M >= 32 || (X.nb - 1) * ncell >= (1 << 16))
+            return fail(ctx, NE_EINVAL, "crystal runner: box shape outside the stencil code range");
         std::vector<std::vector<std::pair<double, std::pair<float4, int>>>> per(X.nb);
         for (int b = 0; b < X.nb; ++b) {
             for (int dx = -M; dx <= M; ++dx)
@@ -993,7 +1000,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
                             const double ez = X.a * (dz + basis[b2][2] - basis[b][2]);
                             const double d = std::sqrt(ex * ex + ey * ey + ez * ez);
                             if (d >= Rst) continue;
-                            const int code = (dx + M) | ((dy + M) << 8) | ((dz + M) << 16) | (b2 << 24);
+                            const int code = ((dx + M) * LY + dy + M) | ((dz + M) << 10) | ((b2 * ncell) << 15);
                             per[b].push_back({d, {make_float4((float)ex, (float)ey, (float)ez, code_bits(code)), code}});
                         }
             std::stable_sort(per[b].begin(), per[b].end(), [](const auto& p, const auto& q) {
@@ -1005,7 +1012,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         if (cnt > NE_STENCIL_MAX) return fail(ctx, NE_EINVAL, "stencil too large");
         X.st_cnt = (int)cnt;
         X.st_margin = M;
-        lut_max = std::max(lut_max, X.nx + X.ny + X.nz + 6 * M);
+        lut_max = std::max(lut_max, (X.nx + 2 * M) * LY + X.nz + 2 * M);
         X.st_off = (int)sv.size();
         for (int b = 0; b < X.nb; ++b)
             for (size_t q = 0; q < cnt; ++q) {
@@ -1013,7 +1020,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
                     sv.push_back(per[b][q].second.first);
                     sd.push_back((float)per[b][q].first);
                 } else {  // padding: beyond any cutoff
-                    sv.push_back(make_float4(0.f, 0.f, 0.f, code_bits(M | (M << 8) | (M << 16))));
+                    sv.push_back(make_float4(0.f, 0.f, 0.f, code_bits((M * LY + M) | (M << 10))));
                     sd.push_back(1e30f);
                 }
             }
@@ -1033,7 +1040,8 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         for (int r : rs) {
             gn = std::max(gn, xr[r].n);
             gnb = std::max(gnb, xr[r].nb * xr[r].st_cnt);
-            glut = std::max(glut, xr[r].nx + xr[r].ny + xr[r].nz + 6 * xr[r].st_margin);
+            const int Mr = xr[r].st_margin;
+            glut = std::max(glut, (xr[r].nx + 2 * Mr) * (xr[r].ny + 2 * Mr) + xr[r].nz + 2 * Mr);
         }
         const size_t base = (ne::cluster_smem_bytes(gn, gnb, glut) + 15) & ~(size_t)15;
         if (base > (size_t)smem_max) return false;

@@ -187,9 +187,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     float4* s_u = (float4*)smem;                                  // [n] (u, F')
     float4* s_sv = s_u + n;                                       // [nb * nst] (r0_j - r0_i, code bits)
     float* s_sd = (float*)(s_sv + nb * nst);                      // [nb * nst] |r0_j - r0_i|
-    int* s_lx = (int*)(s_sd + nb * nst);                          // [nx + 2M] wrapped x-cell * ny nz
-    int* s_ly = s_lx + nx + 2 * M;                                // [ny + 2M]
-    int* s_lz = s_ly + ny + 2 * M;                                // [nz + 2M]
+    // wrapped cell offsets: s_lxy[X * LY + Y] = ((X - M) mod nx * ny + (Y - M) mod ny) * nz,
+    // s_lz[Z] = (Z - M) mod nz, for X, Y, Z = cell index + stencil offset + M
+    const int LY = ny + 2 * M;
+    int* s_lxy = (int*)(s_sd + nb * nst);                         // [(nx + 2M) * LY]
+    int* s_lz = s_lxy + (nx + 2 * M) * LY;                        // [nz + 2M]
     // short list: entry q of thread (slot, lane) at [q][lane][slot], holding
     // k / TPA of its stencil entry k (k = TPA * entry + lane)
     unsigned char* s_sl = (unsigned char*)(s_lz + nz + 2 * M);  // [SLQ][TPA][SLOTS]
@@ -215,8 +217,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         ((q & 1) ? s_tabF : s_tabP)[q >> 1] = tab.pf32[2 * k_lo + q];
     // shared-memory copy of the replica is basis-major: entry b * ncell + cell
     const int ncell = n / nb;
-    for (int q = threadIdx.x; q < nx + 2 * M; q += THREADS) s_lx[q] = (((q - M) % nx + nx) % nx) * ny * nz;
-    for (int q = threadIdx.x; q < ny + 2 * M; q += THREADS) s_ly[q] = (((q - M) % ny + ny) % ny) * nz;
+    for (int q = threadIdx.x; q < (nx + 2 * M) * LY; q += THREADS)
+        s_lxy[q] = ((((q / LY - M) % nx + nx) % nx) * ny + ((q % LY - M) % ny + ny) % ny) * nz;
     for (int q = threadIdx.x; q < nz + 2 * M; q += THREADS) s_lz[q] = ((q - M) % nz + nz) % nz;
 
     // slots are basis-major inside a CTA: the atoms of a warp share a stencil
@@ -230,15 +232,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int a = slot_atom(slot);
     const bool valid = slot < A_c && a < n;
     const int ai = valid ? a : 0;
-    int sx, sy, sz, stb, sui;
+    int sxy, sz, stb, sui;
     {
         const int b = ai % nb;
         sui = b * ncell + ai / nb;
         int c = ai / nb;
         sz = c % nz;
         c /= nz;
-        sy = c % ny;
-        sx = c / ny;
+        sxy = (c / ny) * LY + c % ny;
         stb = b * nst;
     }
     // atom phases (density epilogue, BAOAB, noise): one thread per slot
@@ -356,8 +357,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int k = lane; k < K; k += 2) {
                 const float4 e = s_sv[stb + k];
                 const int code = __float_as_int(e.w);
-                const int j = s_lx[sx + (code & 255)] + s_ly[sy + ((code >> 8) & 255)] +
-                              s_lz[sz + ((code >> 16) & 255)] + (code >> 24) * ncell;
+                const int j = s_lxy[sxy + (code & 1023)] + s_lz[sz + ((code >> 10) & 31)] +
+                              (int)((unsigned)code >> 15);
                 const float4 uj = s_u[j];
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
@@ -423,8 +424,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int k = TPA * s_sl[(q * TPA + lane) * SLOTS + slot] + lane;
                 const float4 e = s_sv[stb + k];
                 const int code = __float_as_int(e.w);
-                const int j = s_lx[sx + (code & 255)] + s_ly[sy + ((code >> 8) & 255)] +
-                              s_lz[sz + ((code >> 16) & 255)] + (code >> 24) * ncell;
+                const int j = s_lxy[sxy + (code & 1023)] + s_lz[sz + ((code >> 10) & 31)] +
+                              (int)((unsigned)code >> 15);
                 const float4 uj = s_u[j];
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
