@@ -33,10 +33,10 @@
 // and noise means are), which lets the centre of mass move by ~1e-4 A per
 // 100 ps.
 //
-// Precision: pair distances, splines, forces, velocities and the OU update in
-// FP32; positions x (registers, FP64), rho accumulation (FP32 chunks of 8 into
-// FP64), the work W and all replica sums in FP64 (CTA sums as FP32
-// double-float pairs, summed across the cluster in FP64).
+// Precision: pair distances, splines, rho, forces, velocities and the OU
+// update in FP32; positions x (registers) and the work W in FP64; the replica
+// energies as double-float pairs within a CTA and FP64 across the cluster,
+// the sums for the mean removal in FP32 within a CTA and FP64 across it.
 #include <algorithm>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     double* s_tot = s_slotP + 2 * 16 * NP_;                       // [NP_ + 1]
     double* s_r0 = s_tot + NP_ + 1;                               // [SLOTS][3] sites of the owned atoms
     float4* s_f = (float4*)(((size_t)(s_r0 + SLOTS * 3) + 15) & ~(size_t)15);  // [2][SLOTS] force, pair energy
-    float2* s_rho = (float2*)(s_f + 2 * SLOTS);                   // [2][SLOTS] rho as double-float
+    float* s_rho = (float*)(s_f + 2 * SLOTS);                     // [2][SLOTS] rho per pair lane
     float* s_slotM = (float*)(s_rho + 2 * SLOTS);                 // [2][16] max |u| per CTA
     float* s_red = s_slotM + 32;                                  // [NWARP][NRED][2]
     float* s_misc = s_red + NWARP * NRED * 2;                     // [8]
@@ -352,7 +352,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                 else hi = mid;
             }
             const int K = valid ? lo : 0;
-            dfl rho = {0.f, 0.f};
+            // rho in FP32: F(rho) is evaluated in FP32, which the sum's
+            // rounding (~1e-7 relative) does not reach
+            float rho = 0.f;
 #pragma unroll 2
             for (int k = lane; k < K; k += 2) {
                 const float4 e = s_sv[stb + k];
@@ -365,9 +367,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (r2 < rc2) {
                     if (r2 < rmin2) bad |= ST_ERANGE;
                     const float ir = rsqrtf(r2);
-                    const float r = r2 * ir;
-                    const float t = r * inv_h;
-                    const int kk = min(max((int)t, 0), nk - 2);
+                    const float t = r2 * ir * inv_h;  // r / h >= 0
+                    const int kk = min((int)t, nk - 2);
                     const float w = t - (float)kk;
                     float4 c, g;
                     if (kk >= k_lo) {
@@ -377,36 +378,41 @@ __global__ void __launch_bounds__(THREADS, 1)
                         c = __ldg(&tab.pf32[2 * kk]);
                         g = __ldg(&tab.pf32[2 * kk + 1]);
                     }
-                    rho = df_add(rho, {g.x + w * (g.y + w * (g.z + w * g.w)), 0.f});
-                    const float phi = c.x + w * (c.y + w * (c.z + w * c.w));
-                    const float sc = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * inv_h * ir;
+                    rho += g.x + w * (g.y + w * (g.z + w * g.w));
+                    // phi and dphi/dw together (Horner with derivative)
+                    float pv = fmaf(c.w, w, c.z), pd = c.w;
+                    pd = fmaf(pd, w, pv);
+                    pv = fmaf(pv, w, c.y);
+                    pd = fmaf(pd, w, pv);
+                    pv = fmaf(pv, w, c.x);
+                    const float sc = pd * (inv_h * ir);
                     fx += sc * dx;
                     fy += sc * dy;
                     fz += sc * dz;
-                    ep += 0.5f * phi;
-                    if (m < SLQ)
-                        s_sl[(m * TPA + lane) * SLOTS + slot] = (unsigned char)(k / TPA);
-                    else
-                        bad |= ST_ENEIGH;
+                    ep += pv;
+                    // entries past the capacity overwrite the last one; the
+                    // overflow is reported after the loop
+                    s_sl[(min(m, SLQ - 1) * TPA + lane) * SLOTS + slot] = (unsigned char)(k / TPA);
                     ++m;
                 }
             }
             n_cand += (K > lane) ? (unsigned)((K - lane + 1) / 2) : 0u;
+            if (m > SLQ) bad |= ST_ENEIGH;
             m = min(m, SLQ);
             n_pair += (unsigned)m;
-            if (valid) s_rho[lane * SLOTS + slot] = make_float2(rho.hi, rho.lo);
+            ep *= 0.5f;  // each pair energy is shared by the two atoms
+            if (valid) s_rho[lane * SLOTS + slot] = rho;
         }
         __syncthreads();
-        // embedding of the owned atom: rho to FP64 once, F(rho), F'(rho)
+        // embedding of the owned atom: F(rho), F'(rho)
         float emb = 0.f;
         if (own) {
-            const float2 r0_ = s_rho[threadIdx.x], r1_ = s_rho[SLOTS + threadIdx.x];
-            const dfl rr = df_add({r0_.x, r0_.y}, {r1_.x, r1_.y});
-            if (!(rr.hi < rho_maxf)) bad |= ST_ERANGE;
-            // offset in the interval from the double-float rho: the product
-            // with the high part of 1/h exact inside the FMA, the low parts added
-            const int kk = min(max((int)(rr.hi * ihr_hi), 0), nk - 2);
-            const float w = fmaf(rr.hi, ihr_hi, -(float)kk) + (rr.hi * ihr_lo + rr.lo * ihr_hi);
+            const float rho = s_rho[threadIdx.x] + s_rho[SLOTS + threadIdx.x];
+            if (!(rho < rho_maxf)) bad |= ST_ERANGE;
+            // offset in the interval: the product with the high part of 1/h
+            // is exact inside the FMA, the low part is added
+            const int kk = min(max((int)(rho * ihr_hi), 0), nk - 2);
+            const float w = fmaf(rho, ihr_hi, -(float)kk) + rho * ihr_lo;
             const float4 c = __ldg(&tab.F32[kk]);
             emb = c.x + w * (c.y + w * (c.z + w * c.w));
             const float dF = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * tab.inv_h_rhof;
@@ -430,12 +436,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 const float ir = rsqrtf(r2);
-                const float r = r2 * ir;
-                const float t = r * inv_h;
-                const int kk = min(max((int)t, 0), nk - 2);
+                const float t = r2 * ir * inv_h;
+                const int kk = min((int)t, nk - 2);
                 const float w = t - (float)kk;
                 const float4 g = kk >= k_lo ? s_tabF[kk - k_lo] : __ldg(&tab.pf32[2 * kk + 1]);
-                const float sc = (dFi + uj.w) * (g.y + w * (2.f * g.z + 3.f * w * g.w)) * inv_h * ir;
+                const float sc = (dFi + uj.w) * (g.y + w * (2.f * g.z + 3.f * w * g.w)) * (inv_h * ir);
                 fx += sc * dx;
                 fy += sc * dy;
                 fz += sc * dz;
@@ -525,7 +530,7 @@ size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
     b = (b + 15) & ~(size_t)15;
     b += sizeof(double) * (2 * 16 * NP_ + NP_ + 1 + SLOTS * 3);
     b += 16;  // alignment of s_f
-    b += 2 * sizeof(float4) * SLOTS + 2 * sizeof(float2) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2 + 8);
+    b += 2 * sizeof(float4) * SLOTS + 2 * sizeof(float) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2 + 8);
     return ((b + 15) & ~(size_t)15) + 16;  // + alignment of the tables
 }
 
