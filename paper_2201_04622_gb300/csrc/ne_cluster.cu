@@ -54,6 +54,9 @@ constexpr int SLOTS = THREADS / TPA;  // atoms per CTA (one CTA per SM)
 constexpr int SLMAX = 80;             // short-list entries per atom (SLMAX / TPA per thread)
 constexpr int SLQ = SLMAX / TPA;
 static_assert(NE_STENCIL_MAX / TPA <= 256, "short-list entries are bytes");
+// stencil scan bounds: entries of basis b with |r0_j - r0_i| < r_c + c for
+// c = q * 2D / (NKT - 1), q = 0 .. NKT - 1 (the last: the whole stencil)
+constexpr int NKT = 256;
 constexpr int NWARP = THREADS / 32;
 
 // partial sums broadcast at the end of step s for step s+1: the energies
@@ -192,9 +195,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int LY = ny + 2 * M;
     int* s_lxy = (int*)(s_sd + nb * nst);                         // [(nx + 2M) * LY]
     int* s_lz = s_lxy + (nx + 2 * M) * LY;                        // [nz + 2M]
+    unsigned short* s_K = (unsigned short*)(s_lz + nz + 2 * M);  // [4][NKT] scan bounds
     // short list: entry q of thread (slot, lane) at [q][lane][slot], holding
     // k / TPA of its stencil entry k (k = TPA * entry + lane)
-    unsigned char* s_sl = (unsigned char*)(s_lz + nz + 2 * M);  // [SLQ][TPA][SLOTS]
+    unsigned char* s_sl = (unsigned char*)(s_K + 4 * NKT);      // [SLQ][TPA][SLOTS]
     double* s_slotP = (double*)(((size_t)(s_sl + SLOTS * SLMAX) + 15) & ~(size_t)15);  // [2][16][NP_]
     double* s_tot = s_slotP + 2 * 16 * NP_;                       // [NP_ + 1]
     double* s_r0 = s_tot + NP_ + 1;                               // [SLOTS][3] sites of the owned atoms
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int a = slot_atom(slot);
     const bool valid = slot < A_c && a < n;
     const int ai = valid ? a : 0;
-    int sxy, sz, stb, sui;
+    int sxy, sz, stb, skb, sui;
     {
         const int b = ai % nb;
         sui = b * ncell + ai / nb;
@@ -241,6 +245,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         c /= nz;
         sxy = (c / ny) * LY + c % ny;
         stb = b * nst;
+        skb = b * NKT;
     }
     // atom phases (density epilogue, BAOAB, noise): one thread per slot
     const int ta = slot_atom(threadIdx.x);
@@ -249,6 +254,23 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int own_warps = (A_c + 31) / 32;                   // warps holding owned atoms
     const size_t gi = (size_t)(reps[rep].off + (own ? ta : 0)) * 3;
     cluster.sync();  // every CTA of the cluster has started: distributed shared memory is usable
+    const float Dr = reps[rep].D;
+    for (int q = threadIdx.x; q < nb * NKT; q += THREADS) {
+        const int b = q / NKT, iq = q % NKT;
+        int cnt = nst;
+        if (iq < NKT - 1) {
+            const float cq = (float)tab.r_c + (float)iq * (2.f * Dr / (float)(NKT - 1));
+            int lo = 0, hi = nst;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_sd[b * nst + mid] < cq) lo = mid + 1;
+                else hi = mid;
+            }
+            cnt = lo;
+        }
+        s_K[q] = (unsigned short)cnt;
+    }
+    const float inv_dK = (float)(NKT - 1) / (2.f * Dr);
 
     // ---- state of the owned atom: position x in FP64 (registers), velocity
     // and this step's normals in FP32; its site r0 in shared memory
@@ -293,7 +315,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 
     unsigned n_cand = 0, n_pair = 0;  // work counters (stencil entries visited, pairs < r_c)
-    const float rc = (float)tab.r_c, rc2 = tab.rc2f, rmin2 = tab.rmin2f, inv_h = tab.inv_h_rf;
+    const float rc2 = tab.rc2f, rmin2 = tab.rmin2f, inv_h = tab.inv_h_rf;
     const int nk = tab.nk;
     const float dt = (float)S.dt;
     const float rho_maxf = (float)tab.rho_max;
@@ -344,14 +366,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         int m = 0;
         float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
         {
-            const float cut = rc + sqrtf(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + umax;
-            int lo = 0, hi = nst;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s_sd[stb + mid] < cut) lo = mid + 1;
-                else hi = mid;
-            }
-            const int K = valid ? lo : 0;
+            // every entry with |r0_j - r0_i| < r_c + |u_i| + max |u| (two
+            // bins of margin against rounding of the bin index)
+            const float c = sqrtf(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + umax;
+            const int K = valid ? (int)s_K[skb + min(NKT - 1, (int)(c * inv_dK) + 2)] : 0;
             // rho in FP32: F(rho) is evaluated in FP32, which the sum's
             // rounding (~1e-7 relative) does not reach
             float rho = 0.f;
@@ -526,7 +544,7 @@ namespace ne {
 size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
 {
     size_t b = sizeof(float4) * (size_t)n_max + (sizeof(float4) + sizeof(float)) * (size_t)nb_nst_max +
-               sizeof(int) * (size_t)lut_max + sizeof(unsigned char) * SLOTS * SLMAX;
+               sizeof(int) * (size_t)lut_max + sizeof(unsigned short) * 4 * NKT + sizeof(unsigned char) * SLOTS * SLMAX;
     b = (b + 15) & ~(size_t)15;
     b += sizeof(double) * (2 * 16 * NP_ + NP_ + 1 + SLOTS * 3);
     b += 16;  // alignment of s_f
