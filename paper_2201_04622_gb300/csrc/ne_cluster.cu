@@ -34,9 +34,10 @@
 // 100 ps.
 //
 // Precision: pair distances, splines, rho, forces, velocities and the OU
-// update in FP32; positions x (registers) and the work W in FP64; the replica
-// energies as double-float pairs within a CTA and FP64 across the cluster,
-// the sums for the mean removal in FP32 within a CTA and FP64 across it.
+// update in FP32; positions in fixed point (2^-32 A, registers); the work W
+// in FP64; the replica energies as double-float pairs within a CTA and FP64
+// across the cluster, the sums for the mean removal in FP32 within a CTA and
+// FP64 across it.
 #include <algorithm>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -149,6 +150,20 @@ __device__ __forceinline__ void cta_sum_bcast(cg::cluster_group& cluster, dfl (&
     }
 }
 
+// Positions of owned atoms in fixed point, X = x * 2^32 (int64): the drift
+// of a step (FP32) is added as an exact integer, the displacement from the
+// site is converted to FP32 with integer and FP32 instructions only (no FP64,
+// which runs at 1/64 of the FP32 rate here), and a position written out as
+// X * 2^-32 in FP64 reads back to the same X, so segments resume bit for bit.
+constexpr double XSCALE = 4294967296.0;  // 2^32 per Angstrom
+
+// d * 2^-32 rounded once to FP32 (exact split into 2^16 parts; |d| < 2^40)
+__device__ __forceinline__ float fix_to_float(long long d)
+{
+    const int hi = (int)(d >> 16), lo = (int)(d & 0xffff);
+    return fmaf((float)hi, 1.52587890625e-05f, (float)lo * 2.3283064365386963e-10f);
+}
+
 __device__ __forceinline__ float blendf(int path, float lam, float F0, float FE)
 {
     return path == 0 ? (1.f - lam) * F0 + lam * FE : lam * F0;
@@ -201,7 +216,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     unsigned char* s_sl = (unsigned char*)(s_K + 4 * NKT);      // [SLQ][TPA][SLOTS]
     double* s_slotP = (double*)(((size_t)(s_sl + SLOTS * SLMAX) + 15) & ~(size_t)15);  // [2][16][NP_]
     double* s_tot = s_slotP + 2 * 16 * NP_;                       // [NP_ + 1]
-    double* s_r0 = s_tot + NP_ + 1;                               // [SLOTS][3] sites of the owned atoms
+    long long* s_r0 = (long long*)(s_tot + NP_ + 1);              // [SLOTS][3] sites of the owned atoms * 2^32
     float4* s_f = (float4*)(((size_t)(s_r0 + SLOTS * 3) + 15) & ~(size_t)15);  // [2][SLOTS] force, pair energy
     float* s_rho = (float*)(s_f + 2 * SLOTS);                     // [2][SLOTS] rho per pair lane
     float* s_slotM = (float*)(s_rho + 2 * SLOTS);                 // [2][16] max |u| per CTA
@@ -272,9 +287,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     const float inv_dK = (float)(NKT - 1) / (2.f * Dr);
 
-    // ---- state of the owned atom: position x in FP64 (registers), velocity
-    // and this step's normals in FP32; its site r0 in shared memory
-    double xr[3] = {0, 0, 0};
+    // ---- state of the owned atom: position in fixed point (registers),
+    // velocity and this step's normals in FP32; its site in shared memory
+    long long xr[3] = {0, 0, 0};
     float v[3] = {0, 0, 0}, u[3] = {0, 0, 0}, xi[3] = {0, 0, 0};
     int bad = 0;
     const float kf = reps[rep].kf;
@@ -289,13 +304,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             c /= nz;
             const int iy = c % ny, ix = c / ny;
             const double ra = reps[rep].a;
-            s_r0[threadIdx.x * 3] = ra * (ix + reps[rep].basis[b][0]);
-            s_r0[threadIdx.x * 3 + 1] = ra * (iy + reps[rep].basis[b][1]);
-            s_r0[threadIdx.x * 3 + 2] = ra * (iz + reps[rep].basis[b][2]);
+            s_r0[threadIdx.x * 3] = __double2ll_rn(ra * (ix + reps[rep].basis[b][0]) * XSCALE);
+            s_r0[threadIdx.x * 3 + 1] = __double2ll_rn(ra * (iy + reps[rep].basis[b][1]) * XSCALE);
+            s_r0[threadIdx.x * 3 + 2] = __double2ll_rn(ra * (iz + reps[rep].basis[b][2]) * XSCALE);
             for (int q = 0; q < 3; ++q) {
-                xr[q] = xg[gi + q];
+                xr[q] = __double2ll_rn(xg[gi + q] * XSCALE);
                 v[q] = (float)vg[gi + q];
-                u[q] = (float)(xr[q] - s_r0[threadIdx.x * 3 + q]);
+                u[q] = fix_to_float(xr[q] - s_r0[threadIdx.x * 3 + q]);
             }
             const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
             for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[tsu] = uv;
@@ -492,8 +507,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                         v[c] += hdt * blendf(S.path, ln, F0[c], -kf * u[c] - mFE[c]);
                         const float v1 = v[c];
                         v[c] = c1 * v[c] + c2 * (xi[c] - mxi[c]);
-                        xr[c] += (double)(0.5f * dt * (v1 + v[c]));
-                        u[c] = (float)(xr[c] - s_r0[threadIdx.x * 3 + c]);
+                        const float dlt = 0.5f * dt * (v1 + v[c]);
+                        if (!(fabsf(dlt) < 0.25f)) bad |= ST_ERANGE;  // > 250 A/ps at 1 fs, or NaN
+                        xr[c] += (long long)__float2int_rn(dlt * 4294967296.f);
+                        u[c] = fix_to_float(xr[c] - s_r0[threadIdx.x * 3 + c]);
                     }
                     const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
                     for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[tsu] = uv;
@@ -510,7 +527,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 un = sqrtf(u2);
                 for (int c = 0; c < 3; ++c)
-                    if (!isfinite(xr[c]) || !isfinite(v[c])) bad |= ST_ENAN;
+                    if (!isfinite(v[c])) bad |= ST_ENAN;
             }
             if (!fin)
                 cta_sum_bcast<ND_, NF_>(cluster, pd, pf, un, s_red, s_slotP + ((s + 1) & 1) * 16 * NP_,
@@ -519,7 +536,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     if (own)
         for (int c = 0; c < 3; ++c) {
-            xg[gi + c] = xr[c];
+            xg[gi + c] = (double)xr[c] / XSCALE;
             vg[gi + c] = (double)v[c];
         }
     if (bad) ne_set_status(status, bad);
