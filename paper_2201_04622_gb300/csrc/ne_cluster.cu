@@ -141,11 +141,13 @@ __device__ __forceinline__ void cta_sum_bcast(cg::cluster_group& cluster, dfl (&
                 for (int ww = 0; ww < nwarp; ++ww) acc += s_red[(ww * NRED + q) * 2];
                 d = (double)acc;
             }
-            for (int r = 0; r < C; ++r) cluster.map_shared_rank(dst, r)[rank * NV + q] = d;
+            dst[rank * NV + q] = d;
+            for (int r = 1; r < C; ++r) cluster.map_shared_rank(dst, (rank + r) % C)[rank * NV + q] = d;
         } else {
             float m = 0.f;
             for (int ww = 0; ww < nwarp; ++ww) m = fmaxf(m, s_red[(ww * NRED + q) * 2]);
-            for (int r = 0; r < C; ++r) cluster.map_shared_rank(mslot, r)[rank] = m;
+            mslot[rank] = m;
+            for (int r = 1; r < C; ++r) cluster.map_shared_rank(mslot, (rank + r) % C)[rank] = m;
         }
     }
 }
@@ -313,7 +315,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 u[q] = fix_to_float(xr[q] - s_r0[threadIdx.x * 3 + q]);
             }
             const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
-            for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[tsu] = uv;
+            s_u[tsu] = uv;
+            for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, (rank + r) % C)[tsu] = uv;
             ne_normals32(ne_philox_block(reps[rep].seed, reps[rep].replica, (unsigned)S.stream, (unsigned)ta,
                                          (unsigned long long)s_begin),
                          xi);
@@ -449,7 +452,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             const float4 c = __ldg(&tab.F32[kk]);
             emb = c.x + w * (c.y + w * (c.z + w * c.w));
             const float dF = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * tab.inv_h_rhof;
-            for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[tsu].w = dF;
+            s_u[tsu].w = dF;
+            for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, (rank + r) % C)[tsu].w = dF;
             if (!isfinite(emb)) bad |= ST_ENAN;
         }
         cluster.sync();  // F' visible everywhere
@@ -513,7 +517,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                         u[c] = fix_to_float(xr[c] - s_r0[threadIdx.x * 3 + c]);
                     }
                     const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
-                    for (int r = 0; r < C; ++r) cluster.map_shared_rank(s_u, r)[tsu] = uv;
+                    s_u[tsu] = uv;
+                    for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, (rank + r) % C)[tsu] = uv;
                     // normals of the next step
                     ne_normals32(ne_philox_block(reps[rep].seed, reps[rep].replica, (unsigned)S.stream,
                                                  (unsigned)ta, (unsigned long long)(s + 1)),
