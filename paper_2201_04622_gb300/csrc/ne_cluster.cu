@@ -204,8 +204,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int cells_c = A_c / nb;
 
     // ---- shared memory
-    float4* s_u = (float4*)smem;                                  // [n] (u, F')
-    float4* s_sv = s_u + n;                                       // [nb * nst] (r0_j - r0_i, code bits)
+    // the replica's (u, F') in two buffers by step parity: step s reads
+    // buffer s & 1 while a CTA that is ahead writes u of step s + 1 into the
+    // other one, so no barrier is needed between the two
+    float4* s_u = (float4*)smem;                                  // [2][n] (u, F')
+    float4* s_sv = s_u + 2 * n;                                   // [nb * nst] (r0_j - r0_i, code bits)
     float* s_sd = (float*)(s_sv + nb * nst);                      // [nb * nst] |r0_j - r0_i|
     // wrapped cell offsets: s_lxy[X * LY + Y] = ((X - M) mod nx * ny + (Y - M) mod ny) * nz,
     // s_lz[Z] = (Z - M) mod nz, for X, Y, Z = cell index + stencil offset + M
@@ -218,10 +221,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     unsigned char* s_sl = (unsigned char*)(s_K + 4 * NKT);      // [SLQ][TPA][SLOTS]
     double* s_slotP = (double*)(((size_t)(s_sl + SLOTS * SLMAX) + 15) & ~(size_t)15);  // [2][16][NP_]
     double* s_tot = s_slotP + 2 * 16 * NP_;                       // [NP_ + 1]
-    long long* s_r0 = (long long*)(s_tot + NP_ + 1);              // [SLOTS][3] sites of the owned atoms * 2^32
-    float4* s_f = (float4*)(((size_t)(s_r0 + SLOTS * 3) + 15) & ~(size_t)15);  // [2][SLOTS] force, pair energy
-    float* s_rho = (float*)(s_f + 2 * SLOTS);                     // [2][SLOTS] rho per pair lane
-    float* s_slotM = (float*)(s_rho + 2 * SLOTS);                 // [2][16] max |u| per CTA
+    // partial force, pair energy and rho of the second pair lane of each slot
+    // (the first lane is the owning thread and keeps its part in registers)
+    float4* s_f = (float4*)(((size_t)(s_tot + NP_ + 1) + 15) & ~(size_t)15);  // [SLOTS]
+    float* s_rho = (float*)(s_f + SLOTS);                         // [SLOTS]
+    float* s_slotM = (float*)(s_rho + SLOTS);                     // [2][16] max |u| per CTA
     float* s_red = s_slotM + 32;                                  // [NWARP][NRED][2]
     float* s_misc = s_red + NWARP * NRED * 2;                     // [8]
     // spline intervals [k_lo, nk - 1) of phi, then of f: separate arrays, so
@@ -269,6 +273,15 @@ __global__ void __launch_bounds__(THREADS, 1)
     const bool own = threadIdx.x < A_c && ta < n;
     const int tsu = own ? (ta % nb) * ncell + ta / nb : 0;  // its shared-memory entry
     const int own_warps = (A_c + 31) / 32;                   // warps holding owned atoms
+    // site of the owned atom, component q, in fixed point
+    auto site_fix = [&](int q) -> long long {
+        const int b = ta % nb;
+        int c = ta / nb;
+        const int iz = c % nz;
+        c /= nz;
+        const int ic = q == 0 ? c / ny : (q == 1 ? c % ny : iz);
+        return __double2ll_rn(reps[rep].a * (ic + reps[rep].basis[b][q]) * XSCALE);
+    };
     const size_t gi = (size_t)(reps[rep].off + (own ? ta : 0)) * 3;
     cluster.sync();  // every CTA of the cluster has started: distributed shared memory is usable
     const float Dr = reps[rep].D;
@@ -289,8 +302,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     const float inv_dK = (float)(NKT - 1) / (2.f * Dr);
 
-    // ---- state of the owned atom: position in fixed point (registers),
-    // velocity and this step's normals in FP32; its site in shared memory
+    // ---- state of the owned atom: displacement from its site in fixed point
+    // (x * 2^32 - site * 2^32, registers), velocity and this step's normals
+    // in FP32
     long long xr[3] = {0, 0, 0};
     float v[3] = {0, 0, 0}, u[3] = {0, 0, 0}, xi[3] = {0, 0, 0};
     int bad = 0;
@@ -300,23 +314,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         float pf[NF_] = {};
         float um = 0.f;
         if (own) {
-            const int b = ta % nb;
-            int c = ta / nb;
-            const int iz = c % nz;
-            c /= nz;
-            const int iy = c % ny, ix = c / ny;
-            const double ra = reps[rep].a;
-            s_r0[threadIdx.x * 3] = __double2ll_rn(ra * (ix + reps[rep].basis[b][0]) * XSCALE);
-            s_r0[threadIdx.x * 3 + 1] = __double2ll_rn(ra * (iy + reps[rep].basis[b][1]) * XSCALE);
-            s_r0[threadIdx.x * 3 + 2] = __double2ll_rn(ra * (iz + reps[rep].basis[b][2]) * XSCALE);
             for (int q = 0; q < 3; ++q) {
-                xr[q] = __double2ll_rn(xg[gi + q] * XSCALE);
+                xr[q] = __double2ll_rn(xg[gi + q] * XSCALE) - site_fix(q);
                 v[q] = (float)vg[gi + q];
-                u[q] = fix_to_float(xr[q] - s_r0[threadIdx.x * 3 + q]);
+                u[q] = fix_to_float(xr[q]);
             }
             const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
-            s_u[tsu] = uv;
-            for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, (rank + r) % C)[tsu] = uv;
+            float4* s_u0 = s_u + (s_begin & 1) * n;
+            s_u0[tsu] = uv;
+            for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u0, (rank + r) % C)[tsu] = uv;
             ne_normals32(ne_philox_block(reps[rep].seed, reps[rep].replica, (unsigned)S.stream, (unsigned)ta,
                                          (unsigned long long)s_begin),
                          xi);
@@ -344,6 +350,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (long long it = 0; it <= n_steps; ++it) {
         const long long s = s_begin + it;
         const bool fin = it == n_steps;
+        float4* const s_uc = s_u + (s & 1) * n;        // (u, F') of step s
+        float4* const s_un = s_u + ((s + 1) & 1) * n;  // u of step s + 1
         cluster.sync();  // u of step s and the partial sums for step s visible everywhere
 
         // ---------------- replica sums for step s (fixed order over the CTAs)
@@ -380,9 +388,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 
         // ---------------- pass 1: density, pair forces and energy, short list
         // (pair threads); the F'(rho) terms of the forces follow in pass 2
-        const float4 ui = s_u[sui];
+        const float4 ui = s_uc[sui];
         int m = 0;
-        float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
+        float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f, rho = 0.f;
         {
             // every entry with |r0_j - r0_i| < r_c + |u_i| + max |u| (two
             // bins of margin against rounding of the bin index)
@@ -390,14 +398,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int K = valid ? (int)s_K[skb + min(NKT - 1, (int)(c * inv_dK) + 2)] : 0;
             // rho in FP32: F(rho) is evaluated in FP32, which the sum's
             // rounding (~1e-7 relative) does not reach
-            float rho = 0.f;
 #pragma unroll 2
             for (int k = lane; k < K; k += 2) {
                 const float4 e = s_sv[stb + k];
                 const int code = __float_as_int(e.w);
                 const int j = s_lxy[sxy + (code & 1023)] + s_lz[sz + ((code >> 10) & 31)] +
                               (int)((unsigned)code >> 15);
-                const float4 uj = s_u[j];
+                const float4 uj = s_uc[j];
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 < rc2) {
@@ -437,13 +444,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             m = min(m, SLQ);
             n_pair += (unsigned)m;
             ep *= 0.5f;  // each pair energy is shared by the two atoms
-            if (valid) s_rho[lane * SLOTS + slot] = rho;
+            if (valid && lane == 1) s_rho[slot] = rho;
         }
         __syncthreads();
         // embedding of the owned atom: F(rho), F'(rho)
         float emb = 0.f;
         if (own) {
-            const float rho = s_rho[threadIdx.x] + s_rho[SLOTS + threadIdx.x];
+            rho += s_rho[threadIdx.x];  // owner = pair lane 0 of its slot
             if (!(rho < rho_maxf)) bad |= ST_ERANGE;
             // offset in the interval: the product with the high part of 1/h
             // is exact inside the FMA, the low part is added
@@ -452,8 +459,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             const float4 c = __ldg(&tab.F32[kk]);
             emb = c.x + w * (c.y + w * (c.z + w * c.w));
             const float dF = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * tab.inv_h_rhof;
-            s_u[tsu].w = dF;
-            for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, (rank + r) % C)[tsu].w = dF;
+            s_uc[tsu].w = dF;
+            for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_uc, (rank + r) % C)[tsu].w = dF;
             if (!isfinite(emb)) bad |= ST_ENAN;
         }
         cluster.sync();  // F' visible everywhere
@@ -461,7 +468,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         // ---------------- pass 2: embedding forces (F'_i + F'_j) f'(r) over
         // the short list (pair threads)
         {
-            const float dFi = s_u[sui].w;
+            const float dFi = s_uc[sui].w;
 #pragma unroll 2
             for (int q = 0; q < m; ++q) {
                 const int k = TPA * s_sl[(q * TPA + lane) * SLOTS + slot] + lane;
@@ -469,7 +476,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int code = __float_as_int(e.w);
                 const int j = s_lxy[sxy + (code & 1023)] + s_lz[sz + ((code >> 10) & 31)] +
                               (int)((unsigned)code >> 15);
-                const float4 uj = s_u[j];
+                const float4 uj = s_uc[j];
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 const float ir = rsqrtf(r2);
@@ -482,7 +489,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 fy += sc * dy;
                 fz += sc * dz;
             }
-            if (valid) s_f[lane * SLOTS + slot] = make_float4(fx, fy, fz, ep);
+            if (valid && lane == 1) s_f[slot] = make_float4(fx, fy, fz, ep);
         }
         __syncthreads();
 
@@ -492,8 +499,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             float pf[NF_] = {};
             float un = 0.f;
             if (own) {
-                const float4 f0_ = s_f[threadIdx.x], f1_ = s_f[SLOTS + threadIdx.x];
-                const float4 f = make_float4(f0_.x + f1_.x, f0_.y + f1_.y, f0_.z + f1_.z, f0_.w + f1_.w);
+                const float4 f1_ = s_f[threadIdx.x];
+                const float4 f = make_float4(fx + f1_.x, fy + f1_.y, fz + f1_.z, ep + f1_.w);
                 const float F0[3] = {f.x, f.y, f.z};
                 const float hdt = reps[rep].hdt_mf, c1 = reps[rep].c1f, c2 = reps[rep].c2f;
                 const float invN = 1.f / (float)n;
@@ -514,11 +521,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                         const float dlt = 0.5f * dt * (v1 + v[c]);
                         if (!(fabsf(dlt) < 0.25f)) bad |= ST_ERANGE;  // > 250 A/ps at 1 fs, or NaN
                         xr[c] += (long long)__float2int_rn(dlt * 4294967296.f);
-                        u[c] = fix_to_float(xr[c] - s_r0[threadIdx.x * 3 + c]);
+                        u[c] = fix_to_float(xr[c]);
                     }
                     const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
-                    s_u[tsu] = uv;
-                    for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, (rank + r) % C)[tsu] = uv;
+                    s_un[tsu] = uv;
+                    for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_un, (rank + r) % C)[tsu] = uv;
                     // normals of the next step
                     ne_normals32(ne_philox_block(reps[rep].seed, reps[rep].replica, (unsigned)S.stream,
                                                  (unsigned)ta, (unsigned long long)(s + 1)),
@@ -541,7 +548,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     if (own)
         for (int c = 0; c < 3; ++c) {
-            xg[gi + c] = (double)xr[c] / XSCALE;
+            xg[gi + c] = (double)(xr[c] + site_fix(c)) / XSCALE;
             vg[gi + c] = (double)v[c];
         }
     if (bad) ne_set_status(status, bad);
@@ -565,12 +572,12 @@ namespace ne {
 // Bytes of everything but the spline tables; the tables take what is left.
 size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
 {
-    size_t b = sizeof(float4) * (size_t)n_max + (sizeof(float4) + sizeof(float)) * (size_t)nb_nst_max +
+    size_t b = 2 * sizeof(float4) * (size_t)n_max + (sizeof(float4) + sizeof(float)) * (size_t)nb_nst_max +
                sizeof(int) * (size_t)lut_max + sizeof(unsigned short) * 4 * NKT + sizeof(unsigned char) * SLOTS * SLMAX;
     b = (b + 15) & ~(size_t)15;
-    b += sizeof(double) * (2 * 16 * NP_ + NP_ + 1 + SLOTS * 3);
+    b += sizeof(double) * (2 * 16 * NP_ + NP_ + 1);
     b += 16;  // alignment of s_f
-    b += 2 * sizeof(float4) * SLOTS + 2 * sizeof(float) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2 + 8);
+    b += sizeof(float4) * SLOTS + sizeof(float) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2 + 8);
     return ((b + 15) & ~(size_t)15) + 16;  // + alignment of the tables
 }
 
