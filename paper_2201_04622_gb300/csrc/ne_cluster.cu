@@ -14,17 +14,19 @@
 // displacement from a site the stencil covers; a replica whose atoms stray
 // further is reported (NE_ERANGE) -- the crystal has melted.
 //
-// One MD step s, two cluster barriers:
+// One MD step s:
 //   [cluster barrier]  replica sums of step s (from the partial sums every
 //                      CTA broadcast at the end of step s-1): noise mean,
 //                      spring mean, max |u|; the work increment of step s-1;
 //                      pass 1: rho, the pair forces phi'(r) and energy phi(r),
 //                      short list; F(rho), F'(rho), F' broadcast
 //   [cluster barrier]  pass 2: the embedding forces (F'_i + F'_j) f'(r) over
-//                      the short list; closing and opening
-//                      half kicks, drift, Ornstein-Uhlenbeck, drift; new u
-//                      broadcast; the normals of step s+1 (counter-based, so
-//                      drawn one step ahead); CTA partial sums for step s+1.
+//                      the short list
+//   [arrive]           closing and opening half kicks, drift,
+//                      Ornstein-Uhlenbeck, drift; the normals of step s+1
+//                      (counter-based, so drawn one step ahead)
+//   [wait]             new u broadcast (no CTA still reads u of step s);
+//                      CTA partial sums for step s+1.
 // The work increment of step s is applied at step s+1 from those sums, in
 // the same order, so a segment boundary changes no bit of the result.  The
 // barriers are barrier.cluster arrive/wait (hardware; every CTA of a cluster
@@ -204,11 +206,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int cells_c = A_c / nb;
 
     // ---- shared memory
-    // the replica's (u, F') in two buffers by step parity: step s reads
-    // buffer s & 1 while a CTA that is ahead writes u of step s + 1 into the
-    // other one, so no barrier is needed between the two
-    float4* s_u = (float4*)smem;                                  // [2][n] (u, F')
-    float4* s_sv = s_u + 2 * n;                                   // [nb * nst] (r0_j - r0_i, code bits)
+    float4* s_u = (float4*)smem;                                  // [n] (u, F')
+    float4* s_sv = s_u + n;                                       // [nb * nst] (r0_j - r0_i, code bits)
     float* s_sd = (float*)(s_sv + nb * nst);                      // [nb * nst] |r0_j - r0_i|
     // wrapped cell offsets: s_lxy[X * LY + Y] = ((X - M) mod nx * ny + (Y - M) mod ny) * nz,
     // s_lz[Z] = (Z - M) mod nz, for X, Y, Z = cell index + stencil offset + M
@@ -320,9 +319,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 u[q] = fix_to_float(xr[q]);
             }
             const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
-            float4* s_u0 = s_u + (s_begin & 1) * n;
-            s_u0[tsu] = uv;
-            for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u0, (rank + r) % C)[tsu] = uv;
+            s_u[tsu] = uv;
+            for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, (rank + r) % C)[tsu] = uv;
             ne_normals32(ne_philox_block(reps[rep].seed, reps[rep].replica, (unsigned)S.stream, (unsigned)ta,
                                          (unsigned long long)s_begin),
                          xi);
@@ -350,8 +348,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (long long it = 0; it <= n_steps; ++it) {
         const long long s = s_begin + it;
         const bool fin = it == n_steps;
-        float4* const s_uc = s_u + (s & 1) * n;        // (u, F') of step s
-        float4* const s_un = s_u + ((s + 1) & 1) * n;  // u of step s + 1
         cluster.sync();  // u of step s and the partial sums for step s visible everywhere
 
         // ---------------- replica sums for step s (fixed order over the CTAs)
@@ -388,7 +384,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
         // ---------------- pass 1: density, pair forces and energy, short list
         // (pair threads); the F'(rho) terms of the forces follow in pass 2
-        const float4 ui = s_uc[sui];
+        const float4 ui = s_u[sui];
         int m = 0;
         float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f, rho = 0.f;
         {
@@ -404,7 +400,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int code = __float_as_int(e.w);
                 const int j = s_lxy[sxy + (code & 1023)] + s_lz[sz + ((code >> 10) & 31)] +
                               (int)((unsigned)code >> 15);
-                const float4 uj = s_uc[j];
+                const float4 uj = s_u[j];
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 < rc2) {
@@ -459,8 +455,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             const float4 c = __ldg(&tab.F32[kk]);
             emb = c.x + w * (c.y + w * (c.z + w * c.w));
             const float dF = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * tab.inv_h_rhof;
-            s_uc[tsu].w = dF;
-            for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_uc, (rank + r) % C)[tsu].w = dF;
+            s_u[tsu].w = dF;
+            for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, (rank + r) % C)[tsu].w = dF;
             if (!isfinite(emb)) bad |= ST_ENAN;
         }
         cluster.sync();  // F' visible everywhere
@@ -468,7 +464,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         // ---------------- pass 2: embedding forces (F'_i + F'_j) f'(r) over
         // the short list (pair threads)
         {
-            const float dFi = s_uc[sui].w;
+            const float dFi = s_u[sui].w;
 #pragma unroll 2
             for (int q = 0; q < m; ++q) {
                 const int k = TPA * s_sl[(q * TPA + lane) * SLOTS + slot] + lane;
@@ -476,7 +472,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int code = __float_as_int(e.w);
                 const int j = s_lxy[sxy + (code & 1023)] + s_lz[sz + ((code >> 10) & 31)] +
                               (int)((unsigned)code >> 15);
-                const float4 uj = s_uc[j];
+                const float4 uj = s_u[j];
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 const float ir = rsqrtf(r2);
@@ -494,6 +490,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncthreads();
 
         // ---------------- fused step of the owned atom
+        // This CTA has finished reading u and F' of step s: arrive on the
+        // cluster barrier now, integrate, and wait only before writing u of
+        // step s + 1 into the other CTAs, which by then have all finished
+        // reading step s too (the integration hides the barrier's latency).
+        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
         {
             dfl pd[ND_] = {};
             float pf[NF_] = {};
@@ -523,13 +524,18 @@ __global__ void __launch_bounds__(THREADS, 1)
                         xr[c] += (long long)__float2int_rn(dlt * 4294967296.f);
                         u[c] = fix_to_float(xr[c]);
                     }
-                    const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
-                    s_un[tsu] = uv;
-                    for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_un, (rank + r) % C)[tsu] = uv;
                     // normals of the next step
                     ne_normals32(ne_philox_block(reps[rep].seed, reps[rep].replica, (unsigned)S.stream,
                                                  (unsigned)ta, (unsigned long long)(s + 1)),
                                  xi);
+                }
+            }
+            asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+            if (own) {
+                if (!fin) {
+                    const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
+                    s_u[tsu] = uv;
+                    for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, (rank + r) % C)[tsu] = uv;
                 }
                 const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
                 pd[P_UE] = {0.5f * kf * u2, 0.f};
@@ -572,7 +578,7 @@ namespace ne {
 // Bytes of everything but the spline tables; the tables take what is left.
 size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
 {
-    size_t b = 2 * sizeof(float4) * (size_t)n_max + (sizeof(float4) + sizeof(float)) * (size_t)nb_nst_max +
+    size_t b = sizeof(float4) * (size_t)n_max + (sizeof(float4) + sizeof(float)) * (size_t)nb_nst_max +
                sizeof(int) * (size_t)lut_max + sizeof(unsigned short) * 4 * NKT + sizeof(unsigned char) * SLOTS * SLMAX;
     b = (b + 15) & ~(size_t)15;
     b += sizeof(double) * (2 * 16 * NP_ + NP_ + 1);
