@@ -35,11 +35,11 @@
 // and noise means are), which lets the centre of mass move by ~1e-4 A per
 // 100 ps.
 //
-// Precision: pair distances, splines, rho, forces, velocities and the OU
-// update in FP32; positions in fixed point (2^-32 A, registers); the work W
-// in FP64; the replica energies as double-float pairs within a CTA and FP64
-// across the cluster, the sums for the mean removal in FP32 within a CTA and
-// FP64 across it.
+// Precision: pair distances, splines, forces, velocities and the OU update
+// in FP32; rho as a double-float; positions in fixed point (2^-32 A,
+// registers); the work W in FP64; the replica energies as double-float pairs
+// within a CTA and FP64 across the cluster, the sums for the mean removal in
+// FP32 within a CTA and FP64 across it.
 #include <algorithm>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     // partial force, pair energy and rho of the second pair lane of each slot
     // (the first lane is the owning thread and keeps its part in registers)
     float4* s_f = (float4*)(((size_t)(s_tot + NP_ + 1) + 15) & ~(size_t)15);  // [SLOTS]
-    float* s_rho = (float*)(s_f + SLOTS);                         // [SLOTS]
+    float2* s_rho = (float2*)(s_f + SLOTS);                       // [SLOTS] double-float
     float* s_slotM = (float*)(s_rho + SLOTS);                     // [2][16] max |u| per CTA
     float* s_red = s_slotM + 32;                                  // [NWARP][NRED][2]
     float* s_misc = s_red + NWARP * NRED * 2;                     // [8]
@@ -386,14 +386,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         // (pair threads); the F'(rho) terms of the forces follow in pass 2
         const float4 ui = s_u[sui];
         int m = 0;
-        float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f, rho = 0.f;
+        float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
+        dfl rho = {0.f, 0.f};
         {
             // every entry with |r0_j - r0_i| < r_c + |u_i| + max |u| (two
             // bins of margin against rounding of the bin index)
             const float c = sqrtf(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + umax;
             const int K = valid ? (int)s_K[skb + min(NKT - 1, (int)(c * inv_dK) + 2)] : 0;
-            // rho in FP32: F(rho) is evaluated in FP32, which the sum's
-            // rounding (~1e-7 relative) does not reach
+            // rho accumulated as a double-float (FP64-class precision from
+            // FP32 arithmetic)
 #pragma unroll 2
             for (int k = lane; k < K; k += 2) {
                 const float4 e = s_sv[stb + k];
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         c = __ldg(&tab.pf32[2 * kk]);
                         g = __ldg(&tab.pf32[2 * kk + 1]);
                     }
-                    rho += g.x + w * (g.y + w * (g.z + w * g.w));
+                    rho = df_add(rho, {g.x + w * (g.y + w * (g.z + w * g.w)), 0.f});
                     // phi and dphi/dw together (Horner with derivative)
                     float pv = fmaf(c.w, w, c.z), pd = c.w;
                     pd = fmaf(pd, w, pv);
@@ -440,18 +441,19 @@ __global__ void __launch_bounds__(THREADS, 1)
             m = min(m, SLQ);
             n_pair += (unsigned)m;
             ep *= 0.5f;  // each pair energy is shared by the two atoms
-            if (valid && lane == 1) s_rho[slot] = rho;
+            if (valid && lane == 1) s_rho[slot] = make_float2(rho.hi, rho.lo);
         }
         __syncthreads();
         // embedding of the owned atom: F(rho), F'(rho)
         float emb = 0.f;
         if (own) {
-            rho += s_rho[threadIdx.x];  // owner = pair lane 0 of its slot
-            if (!(rho < rho_maxf)) bad |= ST_ERANGE;
-            // offset in the interval: the product with the high part of 1/h
-            // is exact inside the FMA, the low part is added
-            const int kk = min(max((int)(rho * ihr_hi), 0), nk - 2);
-            const float w = fmaf(rho, ihr_hi, -(float)kk) + rho * ihr_lo;
+            const float2 r1_ = s_rho[threadIdx.x];  // owner = pair lane 0 of its slot
+            const dfl rr = df_add(rho, {r1_.x, r1_.y});
+            if (!(rr.hi < rho_maxf)) bad |= ST_ERANGE;
+            // offset in the interval from the double-float rho: the product
+            // with the high part of 1/h exact inside the FMA, the low parts added
+            const int kk = min(max((int)(rr.hi * ihr_hi), 0), nk - 2);
+            const float w = fmaf(rr.hi, ihr_hi, -(float)kk) + (rr.hi * ihr_lo + rr.lo * ihr_hi);
             const float4 c = __ldg(&tab.F32[kk]);
             emb = c.x + w * (c.y + w * (c.z + w * c.w));
             const float dF = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * tab.inv_h_rhof;
@@ -583,7 +585,7 @@ size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
     b = (b + 15) & ~(size_t)15;
     b += sizeof(double) * (2 * 16 * NP_ + NP_ + 1);
     b += 16;  // alignment of s_f
-    b += sizeof(float4) * SLOTS + sizeof(float) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2 + 8);
+    b += sizeof(float4) * SLOTS + sizeof(float2) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2 + 8);
     return ((b + 15) & ~(size_t)15) + 16;  // + alignment of the tables
 }
 
