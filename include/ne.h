@@ -145,6 +145,17 @@ ne_status ne_eam_energy_forces(ne_ctx* ctx, ne_precision prec, const double* x_d
                                int n, const double box[3], double* f_dev,
                                double* e_dev, double* rho_dev, void* stream);
 
+/* Configurational virial of the EAM at one configuration, for the pressure
+ * that fixes the lattice parameter (Sec. III.A: the crystal is brought to
+ * zero pressure before switching):
+ *   W = sum_{i<j} r_ij . F_ij = -sum_{i<j} r_ij [phi'(r_ij) + (F'(rho_i) +
+ *       F'(rho_j)) f'(r_ij)] = -dU/d(eps) under x -> (1+eps) x, box -> (1+eps) box,
+ * so that P = (N_dof k_B T + W) / (3 V) at temperature T.  Always FP64.
+ * x_dev [n][3] (device, unwrapped positions); w_dev: 1 double (device).
+ * NE_ERANGE as ne_eam_energy_forces. */
+ne_status ne_eam_virial(ne_ctx* ctx, const double* x_dev, int n, const double box[3], double* w_dev,
+                        void* stream);
+
 /* Allocation-free variant of ne_eam_energy_forces, for callers that cannot
  * allocate device memory once they are running -- an engine or framework
  * that has reserved the device memory for its own pool, or a real-time
@@ -305,6 +316,17 @@ ne_status ne_msd_fit(ne_ctx* ctx, const ne_md_params* md, double* x_dev, double*
                      void* stream);
 
 /* ------------------------------------------------------------ assembly */
+/* Host only, FP64.  Jarzynski's equality (eq. jarz, Sec. II.A): the
+ * free-energy difference from the exponential average of the work done on
+ * the system over independent realisations started in equilibrium,
+ *   dF = -k_B T ln[(1/n) sum_s exp(-W_s / k_B T)],
+ * evaluated with the smallest W factored out (no overflow).  W_host
+ * [n_seeds] in eV (work done on the system: for this library's switching
+ * works, W = -W_fwd or -W_bwd); *dF_out in eV.  Exact in the limit of many
+ * realisations, biased upward by roughly the dissipation when few are
+ * available (Sec. II.A). */
+ne_status ne_jarzynski(double T, const double* W_host, int n_seeds, double* dF_out);
+
 /* Host only, FP64.  Frenkel-Ladd free energy per atom (eq. fl + eq. cm):
  * F_0 = F_E + (mean W_f - mean W_b)/2 + dF_CM, F_E = 3 N k_B T ln(hbar w /
  * k_B T), dF_CM = k_B T ln[(N/V)(2 pi k_B T/(N k))^{3/2}]; stderr over seeds

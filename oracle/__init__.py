@@ -225,6 +225,15 @@ def eam_energy_forces(p: EAM, theta, x, box):
     return E.value, f, rho
 
 
+def eam_virial(p: EAM, theta, x, box):
+    """W = sum_{i<j} r_ij . F_ij = -sum_{i<j} r dU/dr (Sec. III.A zero pressure)."""
+    theta, x, box = _f64(theta), _f64(x), _f64(box)
+    W = C.c_double()
+    _check(lib().ora_eam_virial(C.byref(p), _ptr(theta), _ptr(x), x.shape[0], _ptr(box), C.byref(W)),
+           "eam_virial")
+    return W.value
+
+
 def eam_grad_theta(p: EAM, theta, x, box):
     theta, x, box = _f64(theta), _f64(x), _f64(box)
     g = np.zeros_like(theta)
@@ -321,6 +330,14 @@ def einstein_F(n, T, mass, k):
 
 def cm_correction(n, V, T, mass, k):
     return lib().ora_cm_correction(n, V, T, mass, k)
+
+
+def jarzynski(T, W):
+    """-kT ln mean exp(-W/kT) (eq. jarz)."""
+    W = _f64(W).ravel()
+    f = lib().ora_jarzynski
+    f.restype = C.c_double
+    return f(C.c_double(T), _ptr(W), W.size)
 
 
 def free_energy(n, V, T, mass, k, W_f, W_b):

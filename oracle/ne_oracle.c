@@ -336,6 +336,42 @@ int ora_eam_energy_forces(const ora_eam* p, const double* theta, const double* x
 /* dU/dtheta for every knot value and slope of phi, f and F.  U is linear in
  * the phi and F knots; the f knots enter through rho, weighted by
  * F'(rho_i) + F'(rho_j) for each pair. */
+/* Virial: the r dU/dr of every pair inside r_c, with dU/dr = phi'(r) +
+ * (F'(rho_i) + F'(rho_j)) f'(r); W = -sum over pairs. */
+int ora_eam_virial(const ora_eam* p, const double* theta, const double* x, int n,
+                   const double box[3], double* W)
+{
+    int nk = p->n_knots;
+    const double* th_phi = theta;
+    const double* th_f = theta + 2 * nk;
+    const double* th_F = theta + 4 * nk;
+    double* rho = calloc(n > 0 ? n : 1, sizeof(double));
+    double E;
+    int st = ora_eam_energy_forces(p, theta, x, n, box, NULL, &E, rho);
+    if (st) { free(rho); return st; }
+    int *pi, *pj, np;
+    st = pair_list(x, n, box, p->r_c, &pi, &pj, &np);
+    if (st) { free(rho); return st; }
+    double w = 0.0;
+    for (int q = 0; q < np; q++) {
+        int i = pi[q], j = pj[q];
+        double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
+        min_image(box, d);
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double fr, dfr, ph, dph, Fi, dFi, Fj, dFj;
+        ora_hermite(th_f, nk, p->r_c, r, &fr, &dfr);
+        ora_hermite(th_phi, nk, p->r_c, r, &ph, &dph);
+        ora_hermite(th_F, nk, p->rho_max, rho[i], &Fi, &dFi);
+        ora_hermite(th_F, nk, p->rho_max, rho[j], &Fj, &dFj);
+        w -= r * (dph + (dFi + dFj) * dfr);
+    }
+    free(pi);
+    free(pj);
+    free(rho);
+    *W = w;
+    return ORA_OK;
+}
+
 int ora_eam_grad_theta(const ora_eam* p, const double* theta, const double* x,
                        int n, const double box[3], double* grad)
 {
@@ -765,6 +801,19 @@ double ora_cm_correction(int n, double V, double T, double mass, double k)
 /* Eq. fl plus eq. cm: F_0 = F_E + (mean W_f - mean W_b)/2 + dF_CM, per atom;
  * the error bar is the standard error over seeds of (W_f - W_b)/(2N); the
  * dissipation (eq. Ediss) is -(mean W_f + mean W_b)/2 in this sign convention. */
+/* Eq. jarz: dF = -kT ln[(1/n) sum exp(x_s)], x_s = -W_s/kT, written as
+ * -kT [x_max + ln sum exp(x_s - x_max) - ln n]. */
+double ora_jarzynski(double T, const double* W, int n)
+{
+    double kT = ora_kB() * T;
+    double xmax = -W[0] / kT;
+    for (int s = 1; s < n; s++)
+        if (-W[s] / kT > xmax) xmax = -W[s] / kT;
+    double sum = 0.0;
+    for (int s = 0; s < n; s++) sum += exp(-W[s] / kT - xmax);
+    return -kT * (xmax + log(sum) - log((double)n));
+}
+
 int ora_free_energy(int n, double V, double T, double mass, double k,
                     const double* W_f, const double* W_b, int n_seeds,
                     double* F_per_atom, double* stderr_per_atom,

@@ -81,6 +81,10 @@ int ora_eam_energy_forces(const ora_eam* p, const double* theta, const double* x
                           int n, const double box[3], double* f, double* E,
                           double* rho);
 /* dE/dtheta [3][n_knots][2] (same layout as theta). */
+/* Configurational virial W = sum_{i<j} r_ij . F_ij = -sum_{i<j} r dU/dr
+ * (Sec. III.A zero-pressure condition; P = (N_dof k_B T + W) / (3V)). */
+int ora_eam_virial(const ora_eam* p, const double* theta, const double* x, int n,
+                   const double box[3], double* W);
 int ora_eam_grad_theta(const ora_eam* p, const double* theta, const double* x,
                        int n, const double box[3], double* grad);
 
@@ -122,6 +126,9 @@ int ora_msd_fit(const ora_eam* p, const double* theta, const ora_md* md, double*
 /* Free-energy assembly (host, FP64). */
 double ora_einstein_F(int n, double T, double mass, double k);
 double ora_cm_correction(int n, double V, double T, double mass, double k);
+/* Eq. jarz (Sec. II.A): exp(-dF/kT) = mean exp(-W/kT) over realisations,
+ * W the work done on the system. */
+double ora_jarzynski(double T, const double* W, int n);
 int ora_free_energy(int n, double V, double T, double mass, double k,
                     const double* W_f, const double* W_b, int n_seeds,
                     double* F_per_atom, double* stderr_per_atom,

@@ -678,6 +678,28 @@ ne_status ne_eam_energy_forces(ne_ctx* ctx, ne_precision prec, const double* x_d
     return finish(ctx, st);
 }
 
+ne_status ne_eam_virial(ne_ctx* ctx, const double* x_dev, int n, const double box[3], double* w_dev,
+                        void* stream)
+{
+    if (!ctx || !x_dev || !box || n < 2 || !w_dev) return NE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    ne_md_params m{};
+    m.dt = 1e-3;
+    m.T = 1.0;
+    m.mass = 1.0;
+    m.prec = NE_FP64;
+    int off[2] = {0, n};
+    RunArgs a{};
+    a.x = const_cast<double*>(x_dev);
+    DevBatch B;
+    ne_status s = setup_batch(ctx, 1, off, box, &m, 0, 0.0, B, a, st);
+    if (s) return s;
+    ne::launch_nl_build(B, 1, 0, st);
+    ne::launch_density(B, false, ctx->step_ctr, 0, st);
+    ne::launch_virial(B, w_dev, st);
+    return finish(ctx, st);
+}
+
 ne_status ne_spring_forces(const double* x_dev, const double* x0_dev, int n, double k, double* f_dev,
                            double* e_dev, void* stream)
 {
@@ -1255,6 +1277,18 @@ ne_status ne_free_energy(int n, double V, double T, double mass, double k, const
         *stderr_per_atom = se;
     }
     if (Ediss_per_atom) *Ediss_per_atom = -0.5 * (wf + wb) / n;
+    return NE_OK;
+}
+
+ne_status ne_jarzynski(double T, const double* W_host, int n_seeds, double* dF_out)
+{
+    if (!W_host || n_seeds < 1 || !(T > 0) || !dF_out) return NE_EINVAL;
+    const double kT = kB * T;
+    double wmin = W_host[0];
+    for (int q = 1; q < n_seeds; ++q) wmin = std::min(wmin, W_host[q]);
+    double acc = 0.0;  // every term exp(-(W - W_min)/kT) <= 1
+    for (int q = 0; q < n_seeds; ++q) acc += std::exp(-(W_host[q] - wmin) / kT);
+    *dF_out = wmin - kT * std::log(acc / n_seeds);
     return NE_OK;
 }
 

@@ -466,6 +466,62 @@ __global__ void __launch_bounds__(NE_TILE* TPA) k_backward_fp64(DevBatch B, doub
     }
 }
 
+// Configurational virial for the pressure (Sec. III.A: the lattice
+// parameter at zero pressure): W = sum_{i<j} r_ij . F_ij = -sum_{i<j} r dU/dr
+// with dU/dr = phi'(r) + (F'_i + F'_j) f'(r), in FP64 after an FP64 density
+// pass.  Each pair is seen from both atoms, so every visit adds half.  Tile
+// partials in fixed order; P = (N_dof k_B T + W) / (3 V).
+template <int TPA>
+__global__ void __launch_bounds__(NE_TILE* TPA) k_virial(DevBatch B)
+{
+    __shared__ double red[NE_TILE * TPA];
+    const int nk = B.tab.nk;
+    const int tile = blockIdx.x;
+    const RepDev& P = B.rep[B.tile_rep[tile]];
+    const int local = threadIdx.x / TPA, lane = threadIdx.x % TPA;
+    const int a = (tile - P.tile0) * NE_TILE + local;
+    double w = 0.0;
+    if (a < P.n) {
+        const int i = P.off + a;
+        const V3<double> pi = Pos<false>::load(B, i);
+        const double dFi = B.dF64[i];
+        const int m = B.scnt[i * TPA + lane];
+        for (int q = 0; q < m; ++q) {
+            const int jn = B.sl[(q * B.n_tot + i) * TPA + lane];
+            const V3<double> pj = Pos<false>::load(B, jn);
+            const double dx = mi(pj.x - pi.x, P.L[0], P.invL[0]);
+            const double dy = mi(pj.y - pi.y, P.L[1], P.invL[1]);
+            const double dz = mi(pj.z - pi.z, P.L[2], P.invL[2]);
+            const double r = sqrt(dx * dx + dy * dy + dz * dz);
+            const double t = r * B.tab.inv_h_r;
+            const int kk = min(max((int)t, 0), nk - 2);
+            const double u = t - kk;
+            const ned4 c = B.tab.pf64[2 * kk];
+            const ned4 g = B.tab.pf64[2 * kk + 1];
+            const double dphi = (c.y + u * (2.0 * c.z + 3.0 * u * c.w)) * B.tab.inv_h_r;
+            const double df = (g.y + u * (2.0 * g.z + 3.0 * u * g.w)) * B.tab.inv_h_r;
+            w -= 0.5 * (dphi + (dFi + B.dF64[jn]) * df) * r;
+        }
+    }
+    red[threadIdx.x] = w;
+    __syncthreads();
+    for (int h = NE_TILE * TPA / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) B.partA[tile] = red[0];
+}
+
+// Sum of n tile partials in tile order (one thread: deterministic).
+__global__ void k_sum_tiles(const double* part, int n, double* out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double acc = 0.0;
+        for (int t = 0; t < n; ++t) acc += part[t];
+        *out = acc;
+    }
+}
+
 template <bool MIXED>
 void density_tpa(const DevBatch& B, cudaStream_t st)
 {
@@ -523,6 +579,18 @@ int backward_bin_blocks(const DevBatch& B)
 {
     int nb = B.n_tiles < 296 ? B.n_tiles : 296;
     return nb < 1 ? 1 : nb;
+}
+
+void launch_virial(const DevBatch& B, double* out, cudaStream_t st)
+{
+    dim3 g(B.n_tiles);
+    switch (B.tpa) {
+    case 1: k_virial<1><<<g, NE_TILE * 1, 0, st>>>(B); break;
+    case 2: k_virial<2><<<g, NE_TILE * 2, 0, st>>>(B); break;
+    case 4: k_virial<4><<<g, NE_TILE * 4, 0, st>>>(B); break;
+    default: k_virial<8><<<g, NE_TILE * 8, 0, st>>>(B); break;
+    }
+    k_sum_tiles<<<1, 32, 0, st>>>(B.partA, B.n_tiles, out);
 }
 
 void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, double* gtheta,

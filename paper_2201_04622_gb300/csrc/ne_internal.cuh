@@ -275,4 +275,5 @@ void launch_msd_sample(const DevBatch& B, double* acc, cudaStream_t st);
 void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, double* gtheta,
                      float* bins, int n_bin_blocks, cudaStream_t st);
 int backward_bin_blocks(const DevBatch& B);
+void launch_virial(const DevBatch& B, double* out, cudaStream_t st);
 }  // namespace ne

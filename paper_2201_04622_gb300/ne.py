@@ -25,11 +25,12 @@ NE_PATH_FL, NE_PATH_RS = 0, 1
 # every symbol include/ne.h declares
 SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_set_theta", "ne_ctx_get_theta",
            "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_counters", "ne_last_error",
-           "ne_create_crystal", "ne_eam_energy_forces", "ne_eam_energy_forces_noalloc", "ne_spring_forces",
+           "ne_create_crystal", "ne_eam_energy_forces", "ne_eam_virial", "ne_eam_energy_forces_noalloc",
+           "ne_spring_forces",
            "ne_eam_backward", "ne_noise", "ne_init_velocities", "ne_langevin_step",
            "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment",
            "ne_profile_segment", "ne_crystal_run_segment",
-           "ne_msd_fit", "ne_free_energy",
+           "ne_msd_fit", "ne_free_energy", "ne_jarzynski",
            "ne_rs_free_energy"]
 
 
@@ -86,6 +87,7 @@ def load(build_if_missing: bool = True):
                 "ne_last_error": [p, p, p, i],
                 "ne_create_crystal": [i, d, i, i, i, p, p, p],
                 "ne_eam_energy_forces": [p, i, p, i, p, p, p, p, p],
+                "ne_eam_virial": [p, p, i, p, p, p],
                 "ne_eam_energy_forces_noalloc": [p, i, p, i, p, p, p, p],
                 "ne_spring_forces": [p, p, i, d, p, p, p],
                 "ne_eam_backward": [p, i, p, i, p, d, p, p, p],
@@ -100,6 +102,7 @@ def load(build_if_missing: bool = True):
                 "ne_crystal_run_segment": [p, p, p, i, p, p, p, ll, ll, p],
                 "ne_msd_fit": [p, p, p, p, p, i, p, ll, ll, i, p, p, p],
                 "ne_free_energy": [i, d, d, d, d, p, p, i, p, p, p],
+                "ne_jarzynski": [d, p, i, p],
                 "ne_rs_free_energy": [i, d, d, d, ll, p, p, i, p, i, p],
             }
             for name, args in sigs.items():
@@ -227,6 +230,13 @@ def ne_eam_energy_forces(ctx, prec, x, box, f=None, e=None, rho=None, stream=Non
     _err(ctx, load().ne_eam_energy_forces(ctx, int(prec), _dev(x, 3 * n), n, _box(box),
                                           _dev(f, 3 * n), _dev(e, 1), _dev(rho, n),
                                           _stream(stream)), "ne_eam_energy_forces")
+
+
+def ne_eam_virial(ctx, x, box, w, stream=None):
+    """Configurational virial W = -dU/d(eps) (FP64) into the 1-element device tensor w."""
+    n = x.shape[0]
+    _err(ctx, load().ne_eam_virial(ctx, _dev(x, 3 * n), n, _box(box), _dev(w, 1), _stream(stream)),
+         "ne_eam_virial")
 
 
 NE_NOALLOC_MAX_ATOMS = 2048
@@ -362,6 +372,15 @@ def ne_free_energy(n, V, T, mass, k, W_fwd, W_bwd):
                                      wf.size, C.byref(F), C.byref(se), C.byref(ed)),
          "ne_free_energy")
     return F.value, se.value, ed.value
+
+
+def ne_jarzynski(T, W):
+    """-k_B T ln mean exp(-W / k_B T) (eq. jarz); W: works done on the system (eV)."""
+    import numpy as np
+    w = np.ascontiguousarray(W, np.float64).ravel()
+    out = C.c_double()
+    _err(None, load().ne_jarzynski(float(T), w.ctypes.data_as(C.c_void_p), w.size, C.byref(out)), "ne_jarzynski")
+    return out.value
 
 
 def ne_rs_free_energy(n, T0, F0_T0, lambda_f, t_s, Wcum_fwd, Wcum_bwd, T_grid):

@@ -9,6 +9,8 @@ import numpy as np
 from . import ne
 
 AMU = 1.0364269656262175e-4  # eV ps^2 / A^2
+KB = 8.617333262e-5  # eV / K
+EV_PER_A3_IN_GPA = 160.21766339999999
 
 
 def crystal_sites(lattice, a, n):
@@ -68,3 +70,87 @@ def free_energy(lattice, a, n, T, mass, k, W_f, W_b):
     """(F per atom, standard error, dissipation per atom) from eq. fl + eq. cm."""
     x0, box = crystal_sites(lattice, a, n)
     return ne.ne_free_energy(len(x0), float(np.prod(box)), T, mass, k, W_f, W_b)
+
+
+def pressure(ctx, lattice, a, n, T, mass, n_eq=2000, n_samples=50, stride=20, prec=ne.NE_MIXED, seed=1,
+             skin=1.0, device="cuda"):
+    """Pressure of an n^3 crystal at lattice parameter a and temperature T
+    (NVT Langevin at lambda = 0 of the FL schedule): P = (N_dof k_B T + <W>) / (3V),
+    W the configurational virial (ne_eam_virial) sampled every `stride` steps
+    after n_eq steps.  Returns (P, standard error) in eV/A^3."""
+    import torch
+    x0_np, box = crystal_sites(lattice, a, n)
+    nat = len(x0_np)
+    t_eq = n_eq + n_samples * stride
+    md = ne.md_params(T=T, mass=mass, skin=skin, prec=prec, t_eq=t_eq, t_s=1, seed=seed, replica=0, fix_cm=1)
+    x0 = torch.tensor(x0_np, dtype=torch.float64, device=device)
+    x, v = x0.clone(), torch.zeros_like(x0)
+    ne.ne_init_velocities(ctx, md, v)
+    Wd = torch.zeros((1, 2), dtype=torch.float64, device=device)
+    w = torch.zeros(1, dtype=torch.float64, device=device)
+    ne.ne_switch_run_segment(ctx, [md], [0, nat], x, v, x0, [box], Wd, 0, n_eq)
+    ws, s0 = [], n_eq
+    for _ in range(n_samples):
+        ne.ne_switch_run_segment(ctx, [md], [0, nat], x, v, x0, [box], Wd, s0, stride)
+        s0 += stride
+        ne.ne_eam_virial(ctx, x, box, w)
+        ws.append(float(w.item()))
+    V = float(np.prod(box))
+    ws = np.asarray(ws)
+    P = ((3 * nat - 3) * KB * T + ws.mean()) / (3 * V)
+    err = ws.std(ddof=1) / np.sqrt(len(ws)) / (3 * V) if len(ws) > 1 else float("nan")
+    return P, err
+
+
+def lattice_parameter(ctx, lattice, n, T, mass, a_grid, **kw):
+    """Zero-pressure lattice parameter at T (Sec. III.A: the crystal is set to
+    P = 0 before switching): P(a) on a_grid, a straight line through the
+    points, its root.  Returns (a0, [(a, P, err)])."""
+    pts = [(a,) + tuple(pressure(ctx, lattice, a, n, T, mass, **kw)) for a in a_grid]
+    A = np.array([[1.0, a] for a, _, _ in pts])
+    c = np.linalg.lstsq(A, np.array([P for _, P, _ in pts]), rcond=None)[0]
+    return -c[0] / c[1], pts
+
+
+def fl_free_energies(lattice, a, n, T, mass, k, W_f, W_b):
+    """Free energy per atom from one set of FL works: the two-sided estimate
+    (eq. fl + eq. cm) with its standard error and dissipation, and the
+    one-sided Jarzynski estimates (eq. jarz) from the forward works (the
+    system goes EAM -> Einstein, work done on it -W_f) and from the backward
+    works (Einstein -> EAM, work -W_b)."""
+    x0, box = crystal_sites(lattice, a, n)
+    nat, V = len(x0), float(np.prod(box))
+    F, se, ed = ne.ne_free_energy(nat, V, T, mass, k, W_f, W_b)
+    F_ref = ne.ne_free_energy(nat, V, T, mass, k, [0.0], [0.0])[0]  # F_E + dF_CM per atom
+    return {"F": F, "stderr": se, "Ediss": ed,
+            "F_jarzynski_fwd": F_ref - ne.ne_jarzynski(T, -np.asarray(W_f, np.float64)) / nat,
+            "F_jarzynski_bwd": F_ref + ne.ne_jarzynski(T, -np.asarray(W_b, np.float64)) / nat}
+
+
+def fl_convergence(ctx, lattice, a, n, T, mass, k, t_s_list, seeds, t_eq, **kw):
+    """The FL free energy and dissipation against the switching time
+    (the convergence study of Sec. III.B): for each t_s (steps), one forward
+    and backward run per seed.  Returns one row per t_s."""
+    rows = []
+    for ts in t_s_list:
+        Wf, Wb, _ = fl_batch(ctx, [(lattice, a, n)] * len(seeds), T, [k] * len(seeds), list(seeds), t_eq, ts,
+                             mass, **kw)
+        rows.append(dict(t_s=ts, **fl_free_energies(lattice, a, n, T, mass, k, Wf, Wb)))
+    return rows
+
+
+def size_scaling(ctx, lattice, a, sizes, T, mass, k, seeds, t_eq, t_s, **kw):
+    """F(N) for n^3 cells (the finite-size study of Sec. III.D), all sizes and
+    seeds in one batch, and a straight-line fit in 1/N: returns the rows and
+    (F at 1/N -> 0, slope)."""
+    crystals = [(lattice, a, m) for m in sizes for _ in seeds]
+    Wf, Wb, _ = fl_batch(ctx, crystals, T, [k] * len(crystals), list(seeds) * len(sizes), t_eq, t_s, mass, **kw)
+    rows, ns = [], len(seeds)
+    for q, m in enumerate(sizes):
+        x0, _ = crystal_sites(lattice, a, m)
+        r = fl_free_energies(lattice, a, m, T, mass, k, Wf[q * ns:(q + 1) * ns], Wb[q * ns:(q + 1) * ns])
+        rows.append(dict(n=m, atoms=len(x0), **r))
+    inv = np.array([1.0 / r["atoms"] for r in rows])
+    Fs = np.array([r["F"] for r in rows])
+    slope, F_inf = np.polyfit(inv, Fs, 1)
+    return rows, (F_inf, slope)

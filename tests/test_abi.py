@@ -69,3 +69,12 @@ def test_rs_assembly_matches_oracle():
     a = ne.ne_rs_free_energy(n, T0, -550.0, lf, ts, cf, cb, Ts)
     b = O.rs_free_energy(n, T0, -550.0, lf, ts, cf, cb, Ts)
     assert np.allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+def test_jarzynski_matches_oracle():
+    g = np.random.default_rng(6)
+    for T, n in [(100.0, 1), (1400.0, 10), (400.0, 257)]:
+        w = g.normal(-8000.0, 0.5, n)
+        assert ne.ne_jarzynski(T, w) == pytest.approx(O.jarzynski(T, w), rel=1e-13, abs=1e-10)
+    with pytest.raises(ne.NeError):
+        ne.ne_jarzynski(-1.0, [1.0])

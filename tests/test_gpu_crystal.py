@@ -192,3 +192,26 @@ def test_cluster_size_changes_rounding_only(ctx):
         assert torch.allclose(Wd, out[0][1], rtol=1e-5, atol=1e-4)
     with pytest.raises(ne.NeError, match="NE_EINVAL"):
         ne.ne_ctx_set_cluster_size(ctx, 17)
+
+
+def test_free_energy_estimators_and_convergence_workflow(ctx):
+    """Two-sided FL estimate and the one-sided Jarzynski estimates from the
+    same works agree to within the dissipation; dissipation falls with the
+    switching time (Sec. III.B)."""
+    from paper_2201_04622_gb300 import workflow as WF
+    rows = WF.fl_convergence(ctx, O.BCC, W.A_BCC, 5, 800.0, MASS, 2.8, [500, 2000], [1, 2, 3, 4], 300,
+                             runner="crystal")
+    for r in rows:
+        tol = 3 * abs(r["Ediss"]) + 6 * r["stderr"] + 1e-4
+        assert abs(r["F_jarzynski_fwd"] - r["F"]) < tol
+        assert abs(r["F_jarzynski_bwd"] - r["F"]) < tol
+    assert rows[1]["Ediss"] < rows[0]["Ediss"]
+    assert abs(rows[1]["F"] - rows[0]["F"]) < 5 * (rows[0]["stderr"] + rows[1]["stderr"]) + 2 * rows[0]["Ediss"]
+
+
+def test_size_scaling_workflow(ctx):
+    from paper_2201_04622_gb300 import workflow as WF
+    rows, (F_inf, slope) = WF.size_scaling(ctx, O.BCC, W.A_BCC, [5, 6], 800.0, MASS, 2.8, [1, 2], 200, 500,
+                                           runner="crystal")
+    assert [r["atoms"] for r in rows] == [250, 432]
+    assert all(np.isfinite([r["F"] for r in rows])) and np.isfinite(F_inf)

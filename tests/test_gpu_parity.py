@@ -127,6 +127,17 @@ def test_eam_mixed_matches_oracle(ctx, pot, lat, n, amp, seed):
     assert rel(rho, rho_o) < 1e-6
 
 
+@pytest.mark.parametrize("lat,n,amp,seed", CASES)
+def test_virial_matches_oracle(ctx, pot, lat, n, amp, seed):
+    p, th = pot
+    x0, box = crystal(lat, n)
+    x = W.displaced(x0, amp, seed)
+    Wo = O.eam_virial(p, th, x, box)
+    w = torch.zeros(1, dtype=torch.float64, device=DEV)
+    ne.ne_eam_virial(ctx, T(x), box, w)
+    assert float(w.item()) == pytest.approx(Wo, rel=1e-10, abs=1e-9)
+
+
 def test_unwrapped_images_give_the_same_energy(ctx):
     x0, box = crystal(O.BCC, 6)
     x = W.displaced(x0, 0.1, 9)
@@ -492,3 +503,21 @@ def test_backward_at_full_size(ctx, pot, lat, n):
             assert rel(N(gx), -fo) < ftol
     finally:
         ne.ne_ctx_destroy(big)
+
+
+def test_zero_pressure_lattice_parameter(ctx):
+    """Near T = 0 the fitted lattice parameter is the potential's static
+    zero-pressure value, 2.87 A (to the thermal expansion of a few kelvin);
+    at 1400 K the crystal expands, by ~4 % with this strongly anharmonic
+    potential (the oracle gives P = +4.3 GPa at a = 2.93 A and -0.7 GPa at
+    2.99 A for bcc 5^3 at 1400 K); the grid brackets the root."""
+    from paper_2201_04622_gb300 import workflow as WF
+    mass = MASS
+    a0, pts = WF.lattice_parameter(ctx, O.BCC, 6, 5.0, mass, [2.86, 2.87, 2.88], n_eq=400, n_samples=10,
+                                   stride=20)
+    assert a0 == pytest.approx(2.87, abs=1.5e-3)
+    assert all(e < 1e-5 for _, _, e in pts)
+    a1, pts = WF.lattice_parameter(ctx, O.BCC, 6, 1400.0, mass, [2.95, 2.985, 3.02], n_eq=1000, n_samples=20,
+                                   stride=20)
+    assert pts[0][1] > 0 > pts[-1][1]
+    assert 2.95 < a1 < 3.02

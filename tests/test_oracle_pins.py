@@ -238,6 +238,36 @@ def test_eam_grad_theta_central_differences(pot):
 
 
 # --------------------------------------------------------------- schedules
+@pytest.mark.parametrize("lat,a,n,amp,seed", [(O.BCC, 2.80, 5, 0.10, 2), (O.BCC, 2.95, 5, 0.20, 3),
+                                                (O.FCC, 3.65, 4, 0.15, 4)])
+def test_virial_is_minus_the_scaling_derivative_of_the_energy(pot, lat, a, n, amp, seed):
+    """W = sum_{i<j} r_ij . F_ij (the configurational virial behind the
+    zero-pressure lattice parameter of Sec. III.A) equals -dU/d(eps) when
+    positions and box are scaled by (1 + eps): U depends on the coordinates
+    only through the pair distances, each of which scales by (1 + eps)."""
+    p, th = pot
+    x0, box = O.create_crystal(lat, a, n, n, n)
+    x = W.displaced(x0, amp, seed)
+    w = O.eam_virial(p, th, x, box)
+    eps = 1e-6
+    Ep = O.eam_energy_forces(p, th, x * (1 + eps), np.asarray(box) * (1 + eps))[0]
+    Em = O.eam_energy_forces(p, th, x * (1 - eps), np.asarray(box) * (1 - eps))[0]
+    assert w == pytest.approx(-(Ep - Em) / (2 * eps), rel=1e-6, abs=1e-5)
+
+
+def test_virial_sign_and_zero_pressure_lattice(pot):
+    """The analytic potential's A and B were fixed so that the perfect bcc
+    crystal at a = 2.87 A is at zero static pressure: W vanishes there,
+    is positive under compression and negative under tension."""
+    p, th = pot
+    ws = {}
+    for a in (2.84, 2.87, 2.90):
+        x0, box = O.create_crystal(O.BCC, a, 6, 6, 6)
+        ws[a] = O.eam_virial(p, th, x0, box) / len(x0)
+    assert abs(ws[2.87]) < 1e-8
+    assert ws[2.84] > 1e-3 and ws[2.90] < -1e-3
+
+
 def test_fl_lambda_function2_pins():
     coef = GOLDEN["fl_function2_coefficients"]["value"]
     for t in [Fraction(0), Fraction(1, 4), Fraction(1, 2), Fraction(3, 4), Fraction(1)]:
@@ -528,3 +558,21 @@ def test_forward_backward_cancels_dissipation(pot):
     assert abs(out[300][0] - out[3000][0]) < 4 * se + 2e-5
     assert out[300][2] > out[3000][2] > -1e-5
     assert out[300][2] > 3 * out[3000][2]
+
+
+def test_jarzynski_estimator_pins():
+    """Eq. jarz on work samples with known exponential averages: a Gaussian
+    work distribution N(mu, s^2) gives exactly dF = mu - s^2 / (2 k_B T)
+    (sampled here by 200,001 equally spaced normal quantiles); one sample or
+    equal samples give W itself; Jensen's inequality bounds dF by mean W."""
+    T = 1400.0
+    kT = O.kB() * T
+    mu, s = -3.7, 0.2
+    z = scipy.stats.norm.ppf((np.arange(200001) + 0.5) / 200001)
+    dF = O.jarzynski(T, mu + s * z)
+    assert dF == pytest.approx(mu - s * s / (2 * kT), abs=2e-3 * s * s / (2 * kT))
+    assert O.jarzynski(T, [2.5]) == pytest.approx(2.5, rel=1e-15)
+    assert O.jarzynski(T, [1e4] * 7) == pytest.approx(1e4, rel=1e-15)
+    w = np.random.default_rng(3).normal(50.0, 1.0, 40)
+    assert O.jarzynski(T, w) <= w.mean()
+    assert O.jarzynski(T, w) >= w.min()
