@@ -140,7 +140,7 @@ def fl_convergence(ctx, lattice, a, n, T, mass, k, t_s_list, seeds, t_eq, **kw):
 
 
 def size_scaling(ctx, lattice, a, sizes, T, mass, k, seeds, t_eq, t_s, **kw):
-    """F(N) for n^3 cells (the finite-size study of Sec. III.D), all sizes and
+    """F(N) for n^3 cells (the finite-size study of Sec. IV.A), all sizes and
     seeds in one batch, and a straight-line fit in 1/N: returns the rows and
     (F at 1/N -> 0, slope)."""
     crystals = [(lattice, a, m) for m in sizes for _ in seeds]
