@@ -39,7 +39,7 @@ _LIB = os.path.join(_LIB_DIR, "libne_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BCC, FCC = 0, 1
+BCC, FCC, HCP = 0, 1, 2
 PATH_FL, PATH_RS = 0, 1
 H0_EAM, H0_HARMONIC = 0, 1
 STREAM_FL, STREAM_INITV, STREAM_RS, STREAM_MSD, STREAM_STEP = 0, 1, 2, 3, 4
@@ -161,13 +161,19 @@ def md(dt=1e-3, T=100.0, damp=0.1, mass=None, k_spring=5.0, lambda_fn=2, path=PA
               seed, replica, fix_cm, h0, k_h0)
 
 
-def create_crystal(lattice, a, nx, ny, nz):
+def create_crystal(lattice, a, nx, ny, nz, c_over_a=None):
+    """Sites and box; hcp uses the orthohexagonal cell (a, sqrt(3) a, c) with
+    c = c_over_a * a (default ideal, sqrt(8/3))."""
     n = (2 if lattice == BCC else 4) * nx * ny * nz
     x0 = np.zeros((n, 3))
     box = np.zeros(3)
     nout = C.c_int()
-    _check(lib().ora_create_crystal(lattice, a, nx, ny, nz, _ptr(x0), _ptr(box),
-                                    C.byref(nout)), "create_crystal")
+    if c_over_a is None:
+        st = lib().ora_create_crystal(lattice, a, nx, ny, nz, _ptr(x0), _ptr(box), C.byref(nout))
+    else:
+        st = lib().ora_create_crystal_ca(lattice, C.c_double(a), C.c_double(c_over_a), nx, ny, nz, _ptr(x0),
+                                         _ptr(box), C.byref(nout))
+    _check(st, "create_crystal")
     return x0, box
 
 

@@ -41,16 +41,28 @@ double ora_amu(void) { (void)EV_J; return AMU_KG / EV_PS2_PER_A2_KG; }
 /* ------------------------------------------------------------------ crystal */
 /* Lattice sites r0 of a bcc or fcc supercell (the Einstein-crystal anchor
  * points of Sec. II.B, eq. einstein).  Atom order: ((ix*ny+iy)*nz+iz)*nb+b. */
-int ora_create_crystal(int lattice, double a, int nx, int ny, int nz,
-                       double* x0, double box[3], int* n_out)
+/* Orthorhombic supercells of cubic bcc and fcc cells (edge a) and of the
+ * orthohexagonal hcp cell (edges a, sqrt(3) a, c) with its four atoms:
+ * A layer at (0,0,0), (1/2,1/2,0); B layer above the triangle centres at
+ * (0,1/3,1/2), (1/2,5/6,1/2) (fractions of the cell edges). */
+int ora_create_crystal_ca(int lattice, double a, double c_over_a, int nx, int ny, int nz,
+                          double* x0, double box[3], int* n_out)
 {
     static const double bcc[2][3] = {{0, 0, 0}, {0.5, 0.5, 0.5}};
     static const double fcc[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
+    static const double hcp[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0, 1.0 / 3.0, 0.5}, {0.5, 5.0 / 6.0, 0.5}};
     const double(*basis)[3];
     int nb;
+    double cell[3] = {a, a, a};
     if (lattice == ORA_BCC) { basis = bcc; nb = 2; }
     else if (lattice == ORA_FCC) { basis = fcc; nb = 4; }
-    else return ORA_EINVAL;
+    else if (lattice == ORA_HCP) {
+        if (!(c_over_a > 0)) return ORA_EINVAL;
+        basis = hcp;
+        nb = 4;
+        cell[1] = sqrt(3.0) * a;
+        cell[2] = c_over_a * a;
+    } else return ORA_EINVAL;
     if (nx < 1 || ny < 1 || nz < 1 || !(a > 0)) return ORA_EINVAL;
     int i = 0;
     for (int ix = 0; ix < nx; ix++)
@@ -58,15 +70,21 @@ int ora_create_crystal(int lattice, double a, int nx, int ny, int nz,
             for (int iz = 0; iz < nz; iz++)
                 for (int b = 0; b < nb; b++) {
                     if (x0) {
-                        x0[3 * i + 0] = a * (ix + basis[b][0]);
-                        x0[3 * i + 1] = a * (iy + basis[b][1]);
-                        x0[3 * i + 2] = a * (iz + basis[b][2]);
+                        x0[3 * i + 0] = cell[0] * (ix + basis[b][0]);
+                        x0[3 * i + 1] = cell[1] * (iy + basis[b][1]);
+                        x0[3 * i + 2] = cell[2] * (iz + basis[b][2]);
                     }
                     i++;
                 }
-    if (box) { box[0] = a * nx; box[1] = a * ny; box[2] = a * nz; }
+    if (box) { box[0] = cell[0] * nx; box[1] = cell[1] * ny; box[2] = cell[2] * nz; }
     if (n_out) *n_out = i;
     return ORA_OK;
+}
+
+int ora_create_crystal(int lattice, double a, int nx, int ny, int nz,
+                       double* x0, double box[3], int* n_out)
+{
+    return ora_create_crystal_ca(lattice, a, sqrt(8.0 / 3.0), nx, ny, nz, x0, box, n_out);
 }
 
 /* ------------------------------------------------------------ analytic EAM */

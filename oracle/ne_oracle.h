@@ -22,7 +22,7 @@ extern "C" {
 #endif
 
 enum { ORA_OK = 0, ORA_EINVAL = -1, ORA_ERANGE = -4, ORA_ENAN = -6 };
-enum { ORA_BCC = 0, ORA_FCC = 1 };
+enum { ORA_BCC = 0, ORA_FCC = 1, ORA_HCP = 2 };
 enum { ORA_PATH_FL = 0, ORA_PATH_RS = 1 };
 enum { ORA_H0_EAM = 0, ORA_H0_HARMONIC = 1 };
 /* Philox stream ids (4th counter word, low bits). */
@@ -62,6 +62,10 @@ double ora_amu(void);          /* 1 u in eV ps^2/A^2 */
 /* crystal: sites r0 [n][3], box lengths; returns n via n_out. */
 int ora_create_crystal(int lattice, double a, int nx, int ny, int nz,
                        double* x0, double box[3], int* n_out);
+/* Same with the axial ratio of hcp given: c = c_over_a * a (ignored for
+ * bcc and fcc); ora_create_crystal uses the ideal sqrt(8/3). */
+int ora_create_crystal_ca(int lattice, double a, double c_over_a, int nx, int ny, int nz,
+                          double* x0, double box[3], int* n_out);
 
 /* analytic functions and tables */
 void ora_eam_analytic(const ora_eam* p, int which /*0 phi,1 f,2 F*/, double x,

@@ -61,6 +61,31 @@ def test_crystal_sites_and_shells(lat, a, nb, shells):
     assert np.allclose(x0[nb * ((1 * 4 + 2) * 4 + 3)], a * np.array([1, 2, 3]))
 
 
+def test_hcp_sites_and_shells():
+    """The orthohexagonal hcp cell: with the ideal axial ratio every site has
+    the textbook coordination shells (12 at a, 6 at sqrt(2) a, 2 at
+    sqrt(8/3) a, 18 at sqrt(3) a, 12 at sqrt(11/3) a, 6 at 2a); with c/a = 1.6
+    the twelve nearest split into 6 in-plane at a and 6 at sqrt(a^2/3 + c^2/4)."""
+    a = 2.58
+    x0, box = O.create_crystal(O.HCP, a, 6, 3, 3)
+    assert x0.shape == (4 * 54, 3)
+    assert np.allclose(box, [6 * a, 3 * math.sqrt(3) * a, 3 * math.sqrt(8 / 3) * a])
+    d = x0[None] - x0[:, None]
+    d -= box * np.rint(d / box)
+    r = np.sqrt((d ** 2).sum(-1))
+    shells = [(1.0, 12), (math.sqrt(2), 6), (math.sqrt(8 / 3), 2), (math.sqrt(3), 18), (math.sqrt(11 / 3), 12),
+              (2.0, 6)]
+    for i in (0, 1, 2, 3, 101):
+        for dist, count in shells:
+            assert np.sum(np.abs(r[i] - dist * a) < 1e-9) == count
+    x1, b1 = O.create_crystal(O.HCP, a, 6, 3, 3, c_over_a=1.6)
+    d = x1[None] - x1[:, None]
+    d -= b1 * np.rint(d / b1)
+    r1 = np.sqrt((d ** 2).sum(-1))[2]
+    assert np.sum(np.abs(r1 - a) < 1e-9) == 6
+    assert np.sum(np.abs(r1 - a * math.sqrt(1 / 3 + 1.6 ** 2 / 4)) < 1e-9) == 6
+
+
 # --------------------------------------------------------- analytic EAM
 def _phi_f_numpy(r, which):
     q = W.EAM_FE_LIKE
