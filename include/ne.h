@@ -53,7 +53,7 @@ typedef enum {
 } ne_status;
 
 typedef enum { NE_FP64 = 0, NE_MIXED = 1 } ne_precision;
-typedef enum { NE_BCC = 0, NE_FCC = 1 } ne_lattice;
+typedef enum { NE_BCC = 0, NE_FCC = 1, NE_HCP = 2 } ne_lattice;
 typedef enum { NE_PATH_FL = 0, NE_PATH_RS = 1 } ne_path;
 
 /* Opaque context: EAM spline tables, neighbour lists, scratch buffers and the
@@ -130,11 +130,20 @@ ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds, long long* stenci
 ne_status ne_last_error(ne_ctx* ctx, int* device_status, char* msg, int msg_len);
 
 /* ------------------------------------------------------------- crystal */
-/* Lattice sites r0 (Sec. II.B, eq. einstein) of an nx*ny*nz bcc or fcc
+/* Lattice sites r0 (Sec. II.B, eq. einstein) of an nx*ny*nz bcc, fcc or hcp
  * supercell with lattice parameter a.  x0_host: [n][3] with n = 2 (bcc) or 4
- * (fcc) * nx*ny*nz (may be NULL to query n); box[3] = a*(nx, ny, nz). */
+ * (fcc, hcp) * nx*ny*nz (may be NULL to query n); box[3] = a*(nx, ny, nz)
+ * for bcc and fcc (hcp: see ne_create_crystal_ca).  Atom order
+ * ((ix*ny+iy)*nz+iz)*nb+b. */
 ne_status ne_create_crystal(ne_lattice lattice, double a, int nx, int ny, int nz,
                             double* x0_host, double box[3], int* n_out);
+/* Same with the hcp axial ratio given (c = c_over_a * a, > 0; ignored for
+ * bcc and fcc).  hcp uses the orthohexagonal cell with edges (a, sqrt(3) a,
+ * c) and four atoms at fractions (0,0,0), (1/2,1/2,0), (0,1/3,1/2),
+ * (1/2,5/6,1/2); box = (nx a, ny sqrt(3) a, nz c).  ne_create_crystal uses
+ * the ideal sqrt(8/3) for hcp. */
+ne_status ne_create_crystal_ca(ne_lattice lattice, double a, double c_over_a, int nx, int ny, int nz,
+                               double* x0_host, double box[3], int* n_out);
 
 /* ------------------------------------------------------------ energies */
 /* EAM energy U (Sec. II.B, eq. H) and forces at one configuration:
@@ -275,6 +284,7 @@ typedef struct {
     ne_lattice lattice;
     double a;
     int nx, ny, nz;
+    double c_over_a;  /* hcp only: c / a; 0 = ideal sqrt(8/3) */
 } ne_crystal;
 
 /* Persistent batched runner for crystals (mixed precision): steps

@@ -618,15 +618,41 @@ ne_status ne_last_error(ne_ctx* ctx, int* device_status, char* msg, int msg_len)
     return NE_OK;
 }
 
-ne_status ne_create_crystal(ne_lattice lattice, double a, int nx, int ny, int nz, double* x0_host,
-                            double box[3], int* n_out)
+// Cell edges and basis (fractions of the edges) of a lattice; hcp is the
+// orthohexagonal cell (a, sqrt(3) a, c).
+static bool lattice_cell(ne_lattice lattice, double a, double c_over_a, double cell[3], int* nb,
+                         const double (**basis)[3])
 {
     static const double bcc[2][3] = {{0, 0, 0}, {0.5, 0.5, 0.5}};
     static const double fcc[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
+    static const double hcp[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0, 1.0 / 3.0, 0.5}, {0.5, 5.0 / 6.0, 0.5}};
+    cell[0] = cell[1] = cell[2] = a;
+    if (lattice == NE_BCC) {
+        *nb = 2;
+        *basis = bcc;
+    } else if (lattice == NE_FCC) {
+        *nb = 4;
+        *basis = fcc;
+    } else if (lattice == NE_HCP) {
+        if (!(c_over_a > 0)) return false;
+        *nb = 4;
+        *basis = hcp;
+        cell[1] = std::sqrt(3.0) * a;
+        cell[2] = c_over_a * a;
+    } else {
+        return false;
+    }
+    return true;
+}
+
+ne_status ne_create_crystal_ca(ne_lattice lattice, double a, double c_over_a, int nx, int ny, int nz,
+                               double* x0_host, double box[3], int* n_out)
+{
     if (!(a > 0) || nx < 1 || ny < 1 || nz < 1) return NE_EINVAL;
-    if (lattice != NE_BCC && lattice != NE_FCC) return NE_EINVAL;
-    const int nb = lattice == NE_BCC ? 2 : 4;
-    const double(*basis)[3] = lattice == NE_BCC ? bcc : fcc;
+    double cell[3];
+    int nb;
+    const double(*basis)[3];
+    if (!lattice_cell(lattice, a, lattice == NE_HCP ? c_over_a : 1.0, cell, &nb, &basis)) return NE_EINVAL;
     long long n = (long long)nb * nx * ny * nz;
     if (n > (1ll << 30)) return NE_EINVAL;
     if (x0_host) {
@@ -635,18 +661,24 @@ ne_status ne_create_crystal(ne_lattice lattice, double a, int nx, int ny, int nz
             for (int iy = 0; iy < ny; ++iy)
                 for (int iz = 0; iz < nz; ++iz)
                     for (int b = 0; b < nb; ++b, ++i) {
-                        x0_host[3 * i] = a * (ix + basis[b][0]);
-                        x0_host[3 * i + 1] = a * (iy + basis[b][1]);
-                        x0_host[3 * i + 2] = a * (iz + basis[b][2]);
+                        x0_host[3 * i] = cell[0] * (ix + basis[b][0]);
+                        x0_host[3 * i + 1] = cell[1] * (iy + basis[b][1]);
+                        x0_host[3 * i + 2] = cell[2] * (iz + basis[b][2]);
                     }
     }
     if (box) {
-        box[0] = a * nx;
-        box[1] = a * ny;
-        box[2] = a * nz;
+        box[0] = cell[0] * nx;
+        box[1] = cell[1] * ny;
+        box[2] = cell[2] * nz;
     }
     if (n_out) *n_out = (int)n;
     return NE_OK;
+}
+
+ne_status ne_create_crystal(ne_lattice lattice, double a, int nx, int ny, int nz, double* x0_host,
+                            double box[3], int* n_out)
+{
+    return ne_create_crystal_ca(lattice, a, std::sqrt(8.0 / 3.0), nx, ny, nz, x0_host, box, n_out);
 }
 
 ne_status ne_eam_energy_forces(ne_ctx* ctx, ne_precision prec, const double* x_dev, int n,
@@ -948,10 +980,14 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
     if (n_rep > ctx->max_rep) return fail(ctx, NE_ENOMEM, "replica count exceeds the context");
     std::vector<int> off(n_rep + 1, 0);
     for (int r = 0; r < n_rep; ++r) {
-        if ((cr[r].lattice != NE_BCC && cr[r].lattice != NE_FCC) || !(cr[r].a > 0) || cr[r].nx < 3 ||
-            cr[r].ny < 3 || cr[r].nz < 3)
-            return fail(ctx, NE_EINVAL, "crystal: bcc/fcc, a > 0 and at least 3 cells per axis");
-        const long long nn = (long long)(cr[r].lattice == NE_BCC ? 2 : 4) * cr[r].nx * cr[r].ny * cr[r].nz;
+        double cell[3];
+        int nb;
+        const double(*basis)[3];
+        const double ca = cr[r].c_over_a > 0 ? cr[r].c_over_a : std::sqrt(8.0 / 3.0);
+        if (!lattice_cell(cr[r].lattice, cr[r].a, ca, cell, &nb, &basis) || !(cr[r].a > 0) || cr[r].nx < 3 ||
+            cr[r].ny < 3 || cr[r].nz < 3 || cr[r].c_over_a < 0)
+            return fail(ctx, NE_EINVAL, "crystal: bcc/fcc/hcp, a > 0, c/a >= 0 and at least 3 cells per axis");
+        const long long nn = (long long)nb * cr[r].nx * cr[r].ny * cr[r].nz;
         if (nn > 4096)
             return fail(ctx, NE_EINVAL, "crystal runner: at most 4096 atoms per replica");
         off[r + 1] = off[r] + (int)nn;
@@ -963,8 +999,6 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
     if (step_begin < 0 || n_steps < 0 || step_begin + n_steps > S_total)
         return fail(ctx, NE_EINVAL, "step range outside the schedule");
     cudaStream_t st = (cudaStream_t)stream;
-    static const double bcc[2][3] = {{0, 0, 0}, {0.5, 0.5, 0.5}};
-    static const double fcc[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
     const double rc = ctx->eam.r_c;
     std::vector<XRep> xr(n_rep);
     std::vector<float4> sv;  // (lattice vector, neighbour code as float bits)
@@ -975,11 +1009,11 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         const ne_md_params& m = md[r];
         XRep& X = xr[r];
         X = XRep{};
-        X.nb = cr[r].lattice == NE_BCC ? 2 : 4;
-        const double(*basis)[3] = cr[r].lattice == NE_BCC ? bcc : fcc;
+        const double(*basis)[3];
+        lattice_cell(cr[r].lattice, cr[r].a, cr[r].c_over_a > 0 ? cr[r].c_over_a : std::sqrt(8.0 / 3.0), X.cell,
+                     &X.nb, &basis);
         for (int b = 0; b < X.nb; ++b)
             for (int d = 0; d < 3; ++d) X.basis[b][d] = basis[b][d];
-        X.a = cr[r].a;
         X.nx = cr[r].nx;
         X.ny = cr[r].ny;
         X.nz = cr[r].nz;
@@ -997,12 +1031,12 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         X.replica = m.replica;
         if (m.replica >= (1u << 28)) return fail(ctx, NE_EINVAL, "replica id must be < 2^28");
         // stencil: sites within r_c + 2D of each basis site, sorted by distance
-        const double Lmin = X.a * std::min(X.nx, std::min(X.ny, X.nz));
+        const double Lmin = std::min(X.cell[0] * X.nx, std::min(X.cell[1] * X.ny, X.cell[2] * X.nz));
         const double D = std::min(2.0, 0.5 * (0.5 * Lmin - rc) - 1e-3);
         if (D < 0.3) return fail(ctx, NE_EINVAL, "box too small for the crystal runner (needs L/2 > r_c + 0.6 A)");
         X.D = (float)D;
         const double Rst = rc + 2.0 * D;
-        const int M = (int)std::ceil(Rst / X.a) + 1;
+        const int M = (int)std::ceil(Rst / std::min(X.cell[0], std::min(X.cell[1], X.cell[2]))) + 1;
         // neighbour code of a stencil entry (dx, dy, dz, b2): bits 0-9 the
         // offset (dx + M) * (ny + 2M) + dy + M into the xy table of wrapped
         // cells, bits 10-14 dz + M, bits 15-31 b2 * (cells per replica), the
@@ -1017,9 +1051,9 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
                     for (int dz = -M; dz <= M; ++dz)
                         for (int b2 = 0; b2 < X.nb; ++b2) {
                             if (dx == 0 && dy == 0 && dz == 0 && b2 == b) continue;
-                            const double ex = X.a * (dx + basis[b2][0] - basis[b][0]);
-                            const double ey = X.a * (dy + basis[b2][1] - basis[b][1]);
-                            const double ez = X.a * (dz + basis[b2][2] - basis[b][2]);
+                            const double ex = X.cell[0] * (dx + basis[b2][0] - basis[b][0]);
+                            const double ey = X.cell[1] * (dy + basis[b2][1] - basis[b][1]);
+                            const double ez = X.cell[2] * (dz + basis[b2][2] - basis[b][2]);
                             const double d = std::sqrt(ex * ex + ey * ey + ez * ez);
                             if (d >= Rst) continue;
                             const int code = ((dx + M) * LY + dy + M) | ((dz + M) << 10) | ((b2 * ncell) << 15);

@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int iz = c % nz;
         c /= nz;
         const int ic = q == 0 ? c / ny : (q == 1 ? c % ny : iz);
-        return __double2ll_rn(reps[rep].a * (ic + reps[rep].basis[b][q]) * XSCALE);
+        return __double2ll_rn(reps[rep].cell[q] * (ic + reps[rep].basis[b][q]) * XSCALE);
     };
     const size_t gi = (size_t)(reps[rep].off + (own ? ta : 0)) * 3;
     cluster.sync();  // every CTA of the cluster has started: distributed shared memory is usable

@@ -8,8 +8,8 @@
 #define NE_STENCIL_MAX 512  // stencil entries per basis site (short lists store entry / 2 in a byte)
 
 struct XRep {
-    double a;             // lattice parameter
-    double basis[4][3];   // fractional basis positions
+    double cell[3];       // cell edges (a, a, a; hcp: a, sqrt(3) a, c)
+    double basis[4][3];   // basis positions as fractions of the cell edges
     double k;             // spring constant (FP64 for the mean spring force)
     float kf, mf, hdt_mf, c1f, c2f;
     float D;              // largest displacement from a site the stencil covers

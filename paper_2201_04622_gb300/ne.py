@@ -19,13 +19,13 @@ NE_OK, NE_EINVAL, NE_ENOMEM, NE_ECUDA, NE_ERANGE, NE_ENEIGH, NE_ENAN, NE_ETIMEOU
 STATUS = ["NE_OK", "NE_EINVAL", "NE_ENOMEM", "NE_ECUDA", "NE_ERANGE", "NE_ENEIGH", "NE_ENAN",
           "NE_ETIMEOUT", "NE_ENOTIMPL"]
 NE_FP64, NE_MIXED = 0, 1
-NE_BCC, NE_FCC = 0, 1
+NE_BCC, NE_FCC, NE_HCP = 0, 1, 2
 NE_PATH_FL, NE_PATH_RS = 0, 1
 
 # every symbol include/ne.h declares
 SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_set_theta", "ne_ctx_get_theta",
            "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_counters", "ne_last_error",
-           "ne_create_crystal", "ne_eam_energy_forces", "ne_eam_virial", "ne_eam_energy_forces_noalloc",
+           "ne_create_crystal", "ne_create_crystal_ca", "ne_eam_energy_forces", "ne_eam_virial", "ne_eam_energy_forces_noalloc",
            "ne_spring_forces",
            "ne_eam_backward", "ne_noise", "ne_init_velocities", "ne_langevin_step",
            "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment",
@@ -49,7 +49,7 @@ class EamParams(C.Structure):
 
 class Crystal(C.Structure):
     _fields_ = [("lattice", C.c_int), ("a", C.c_double), ("nx", C.c_int), ("ny", C.c_int),
-                ("nz", C.c_int)]
+                ("nz", C.c_int), ("c_over_a", C.c_double)]
 
 
 class MdParams(C.Structure):
@@ -86,6 +86,7 @@ def load(build_if_missing: bool = True):
                 "ne_ctx_counters": [p, p, p, p],
                 "ne_last_error": [p, p, p, i],
                 "ne_create_crystal": [i, d, i, i, i, p, p, p],
+                "ne_create_crystal_ca": [i, d, d, i, i, i, p, p, p],
                 "ne_eam_energy_forces": [p, i, p, i, p, p, p, p, p],
                 "ne_eam_virial": [p, p, i, p, p, p],
                 "ne_eam_energy_forces_noalloc": [p, i, p, i, p, p, p, p],
@@ -210,18 +211,22 @@ def ne_last_error(ctx):
     return st.value, buf.value.decode()
 
 
-def ne_create_crystal(lattice, a, nx, ny, nz):
-    """Host: returns (x0 numpy [n][3], box numpy [3])."""
+def ne_create_crystal(lattice, a, nx, ny, nz, c_over_a=None):
+    """Host: returns (x0 numpy [n][3], box numpy [3]); hcp with c = c_over_a * a
+    (ne_create_crystal_ca) or the ideal axial ratio."""
     import numpy as np
     n = C.c_int()
     box = (C.c_double * 3)()
     L = load()
-    _err(None, L.ne_create_crystal(int(lattice), float(a), nx, ny, nz, None, box, C.byref(n)),
-         "ne_create_crystal")
+    if c_over_a is None:
+        def call(ptr):
+            return L.ne_create_crystal(int(lattice), float(a), nx, ny, nz, ptr, box, C.byref(n))
+    else:
+        def call(ptr):
+            return L.ne_create_crystal_ca(int(lattice), float(a), float(c_over_a), nx, ny, nz, ptr, box, C.byref(n))
+    _err(None, call(None), "ne_create_crystal")
     x0 = np.zeros((n.value, 3))
-    _err(None, L.ne_create_crystal(int(lattice), float(a), nx, ny, nz,
-                                   x0.ctypes.data_as(C.c_void_p), box, C.byref(n)),
-         "ne_create_crystal")
+    _err(None, call(x0.ctypes.data_as(C.c_void_p)), "ne_create_crystal")
     return x0, np.array(list(box))
 
 
@@ -342,11 +347,11 @@ def ne_profile_segment(ctx, mds, offsets, x, v, x0, boxes, W, step_begin, n_step
 
 
 def ne_crystal_run_segment(ctx, mds, crystals, x, v, W, step_begin, n_steps, stream=None):
-    """crystals: list of (lattice, a, nx, ny, nz)."""
+    """crystals: list of (lattice, a, nx, ny, nz[, c_over_a])."""
     n_rep = len(mds)
     arr = (MdParams * n_rep)(*mds)
-    cr = (Crystal * n_rep)(*[Crystal(int(c[0]), float(c[1]), int(c[2]), int(c[3]), int(c[4]))
-                             for c in crystals])
+    cr = (Crystal * n_rep)(*[Crystal(int(c[0]), float(c[1]), int(c[2]), int(c[3]), int(c[4]),
+                                     float(c[5]) if len(c) > 5 else 0.0) for c in crystals])
     _err(ctx, load().ne_crystal_run_segment(ctx, arr, cr, n_rep, _dev(x), _dev(v), _dev(W, 2 * n_rep),
                                             int(step_begin), int(n_steps), _stream(stream)),
          "ne_crystal_run_segment")

@@ -23,7 +23,8 @@ K_BCC_1400 = 2.38
 K_FCC_1400 = 2.68
 A_BCC = 2.87
 A_FCC = 3.65
-BCC, FCC = 0, 1
+A_HCP = 2.581  # ideal hcp with the fcc nearest-neighbour distance, A_FCC / sqrt(2)
+BCC, FCC, HCP = 0, 1, 2
 
 
 def eam_params(**over):

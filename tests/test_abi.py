@@ -39,11 +39,12 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert L.ne_noise(1, 0, 99, 0, 10, 0, None, None) == ne.NE_EINVAL
 
 
-@pytest.mark.parametrize("lat,a,n", [(ne.NE_BCC, 2.87, (4, 4, 4)), (ne.NE_FCC, 3.65, (3, 4, 5))])
-def test_crystal_matches_oracle(lat, a, n):
-    x0, box = ne.ne_create_crystal(lat, a, *n)
-    xo, bo = O.create_crystal(lat, a, *n)
-    assert np.array_equal(x0, xo) and np.array_equal(box, bo)
+@pytest.mark.parametrize("lat,a,n,ca", [(ne.NE_BCC, 2.87, (4, 4, 4), None), (ne.NE_FCC, 3.65, (3, 4, 5), None),
+                                       (ne.NE_HCP, 2.58, (4, 3, 3), None), (ne.NE_HCP, 2.58, (3, 3, 4), 1.6)])
+def test_crystal_matches_oracle(lat, a, n, ca):
+    x0, box = ne.ne_create_crystal(lat, a, *n, c_over_a=ca)
+    xo, bo = O.create_crystal(lat, a, *n, c_over_a=ca)
+    assert np.allclose(x0, xo, rtol=0, atol=1e-13) and np.allclose(box, bo, rtol=0, atol=1e-13)
 
 
 def test_free_energy_assembly_matches_oracle():

@@ -45,7 +45,7 @@ def T(a):
 
 
 def lat_a(lat):
-    return W.A_BCC if lat == O.BCC else W.A_FCC
+    return {O.BCC: W.A_BCC, O.FCC: W.A_FCC, O.HCP: W.A_HCP}[lat]
 
 
 def md_pair(**kw):
@@ -75,7 +75,7 @@ def run_crystals(ctx, systems, s0, ns, x=None, v=None, Wd=None, **kw):
 
 
 @pytest.mark.parametrize("lat,n,path", [(O.BCC, 5, O.PATH_FL), (O.FCC, 4, O.PATH_FL),
-                                        (O.BCC, 6, O.PATH_RS)])
+                                        (O.BCC, 6, O.PATH_RS), (O.HCP, 5, O.PATH_FL)])
 def test_crystal_runner_tracks_oracle_100_steps(ctx, pot, lat, n, path):
     p, th = pot
     x, v, Wd, x0s, vs = run_crystals(ctx, [(lat, n, 300.0, 5)], 0, 100, path=path)
@@ -152,10 +152,11 @@ def test_crystal_runner_rejects_small_boxes_and_fp64(ctx):
 
 
 def test_uneven_batch_size_classes_match_multikernel_path(ctx):
-    """Replicas of 432 to 4000 atoms (cluster sizes 2 to 13 CTAs, launched per
-    size class on separate streams) against the multi-kernel mixed path."""
+    """Replicas of 432 to 4000 atoms (bcc, fcc and hcp; cluster sizes 2 to 11
+    CTAs, launched per size class on separate streams) against the
+    multi-kernel mixed path."""
     systems = [(O.BCC, 6, 1500.0, 1), (O.FCC, 10, 600.0, 2), (O.BCC, 9, 1100.0, 3), (O.FCC, 5, 300.0, 4),
-               (O.BCC, 12, 900.0, 5), (O.FCC, 7, 1300.0, 6), (O.BCC, 6, 400.0, 7)]
+               (O.BCC, 12, 900.0, 5), (O.FCC, 7, 1300.0, 6), (O.BCC, 6, 400.0, 7), (O.HCP, 6, 1000.0, 8)]
     x, v, Wd, x0s, vs = run_crystals(ctx, systems, 0, 60, t_eq=10, t_s=25, k_spring=3.0)
     offs = np.cumsum([0] + [len(a) for a in x0s])
     mgs = [md_pair(T=Tk, seed=seed, replica=r, t_eq=10, t_s=25, k_spring=3.0)[1]

@@ -138,6 +138,24 @@ def test_virial_matches_oracle(ctx, pot, lat, n, amp, seed):
     assert float(w.item()) == pytest.approx(Wo, rel=1e-10, abs=1e-9)
 
 
+@pytest.mark.parametrize("dims,ca,amp,seed", [((5, 3, 3), None, 0.12, 6), ((5, 3, 4), 1.58, 0.1, 7)])
+def test_hcp_energy_forces_virial_match_oracle(ctx, pot, dims, ca, amp, seed):
+    """hcp (orthohexagonal cell, ideal or given c/a): a non-cubic box."""
+    p, th = pot
+    x0, box = O.create_crystal(O.HCP, W.A_HCP, *dims, c_over_a=ca)
+    x = W.displaced(x0, amp, seed)
+    Eo, fo, rho_o = O.eam_energy_forces(p, th, x, box)
+    E, f, rho = gpu_eam(ctx, ne.NE_FP64, x, box)
+    assert E == pytest.approx(Eo, rel=1e-10)
+    assert rel(f, fo) < 1e-10
+    E, f, rho = gpu_eam(ctx, ne.NE_MIXED, x, box)
+    assert E == pytest.approx(Eo, rel=1e-6)
+    assert rel(f, fo) < 5e-5
+    w = torch.zeros(1, dtype=torch.float64, device=DEV)
+    ne.ne_eam_virial(ctx, T(x), box, w)
+    assert float(w.item()) == pytest.approx(O.eam_virial(p, th, x, box), rel=1e-10, abs=1e-9)
+
+
 def test_unwrapped_images_give_the_same_energy(ctx):
     x0, box = crystal(O.BCC, 6)
     x = W.displaced(x0, 0.1, 9)
