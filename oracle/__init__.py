@@ -62,7 +62,8 @@ class MD(C.Structure):
                 ("lambda_fn", C.c_int), ("path", C.c_int),
                 ("t_eq", C.c_long), ("t_s", C.c_long), ("lambda_f", C.c_double),
                 ("seed", C.c_uint64), ("replica", C.c_uint32),
-                ("fix_cm", C.c_int), ("h0", C.c_int), ("k_h0", C.c_double)]
+                ("fix_cm", C.c_int), ("h0", C.c_int), ("k_h0", C.c_double),
+                ("npt", C.c_int), ("P0", C.c_double), ("beta_T", C.c_double), ("tau_p", C.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -154,11 +155,13 @@ def eam(A, alpha, beta, B, r_e, r_s, r_c, rho_max, n_knots) -> EAM:
 
 def md(dt=1e-3, T=100.0, damp=0.1, mass=None, k_spring=5.0, lambda_fn=2, path=PATH_FL,
        t_eq=0, t_s=1, lambda_f=0.5, seed=1, replica=0, fix_cm=1, h0=H0_EAM,
-       k_h0=0.0) -> MD:
+       k_h0=0.0, npt=0, P0=0.0, beta_T=0.0, tau_p=0.0) -> MD:
+    """npt = 1: isotropic barostat at pressure P0 (eV/A^3) with coupling
+    compressibility beta_T (A^3/eV) and time tau_p (ps); RS path only."""
     if mass is None:
         mass = 55.845 * amu()
     return MD(dt, T, damp, mass, k_spring, lambda_fn, path, t_eq, t_s, lambda_f,
-              seed, replica, fix_cm, h0, k_h0)
+              seed, replica, fix_cm, h0, k_h0, npt, P0, beta_T, tau_p)
 
 
 def create_crystal(lattice, a, nx, ny, nz, c_over_a=None):
@@ -288,7 +291,8 @@ def switch_run(p: EAM, theta, m: MD, x, v, x0, box, cumulative=False, trace_stri
     """Run the four-phase schedule in place on copies of x, v.
 
     Returns dict with W_f, W_b, x, v and optionally Wcum_f/Wcum_b, trace."""
-    theta, x0, box = _f64(theta), _f64(x0), _f64(box)
+    theta, x0 = _f64(theta), _f64(x0)
+    box = _f64(box).copy()  # the barostat updates it
     x, v = _f64(x).copy(), _f64(v).copy()
     n = x.shape[0]
     wf, wb = C.c_double(), C.c_double()
@@ -303,7 +307,7 @@ def switch_run(p: EAM, theta, m: MD, x, v, x0, box, cumulative=False, trace_stri
                                 _ptr(x0), n, _ptr(box), C.byref(wf), C.byref(wb),
                                 _ptr(cf), _ptr(cb), _ptr(tr), trace_stride, ntr),
            "switch_run")
-    out = dict(W_f=wf.value, W_b=wb.value, x=x, v=v)
+    out = dict(W_f=wf.value, W_b=wb.value, x=x, v=v, box=box)
     if cumulative:
         out.update(Wcum_f=cf, Wcum_b=cb)
     if tr is not None:

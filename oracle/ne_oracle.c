@@ -574,9 +574,9 @@ int ora_init_velocities(const ora_md* md, int n, double* v)
     return ORA_OK;
 }
 
-/* Potential terms at one configuration. */
+/* Potential terms at one configuration (Wv: virial of U0, with the barostat). */
 typedef struct {
-    double U0, UE;
+    double U0, UE, Wv;
     double* F0;
     double* FE;
 } terms;
@@ -585,11 +585,16 @@ static int eval_terms(const ora_eam* p, const double* theta, const ora_md* md,
                       const double* x, const double* x0, int n, const double box[3],
                       terms* t)
 {
+    t->Wv = 0.0;
     if (md->h0 == ORA_H0_HARMONIC) {
-        ora_spring(x, x0, n, md->k_h0, t->F0, &t->U0);
+        ora_spring(x, x0, n, md->k_h0, t->F0, &t->U0);  /* with the barostat: k_h0 = 0, an ideal gas */
     } else {
         int st = ora_eam_energy_forces(p, theta, x, n, box, t->F0, &t->U0, NULL);
         if (st) return st;
+        if (md->npt) {
+            st = ora_eam_virial(p, theta, x, n, box, &t->Wv);
+            if (st) return st;
+        }
     }
     ora_spring(x, x0, n, md->k_spring, t->FE, &t->UE);
     return ORA_OK;
@@ -626,11 +631,24 @@ static double dH_dlambda(const ora_md* md, const terms* t)
  *   2. half kick with F(x_s; lambda_b);  3. half drift;
  *   4. Ornstein-Uhlenbeck velocity update (Langevin thermostat, damping
  *      1/gamma), noise mean removed when the centre of mass is fixed;
- *   5. half drift;  6. forces at x_{s+1};  7. half kick with F(x_{s+1}; lambda_b).
- * t holds the terms at x_s on entry and at x_{s+1} on return. */
+ *   5. half drift;  5b. with the barostat, the volume update below;
+ *   6. forces at x_{s+1};  7. half kick with F(x_{s+1}; lambda_b).
+ * t holds the terms at x_s on entry and at x_{s+1} on return.
+ *
+ * Barostat (md->npt, RS path): the positions at fixed velocities are one
+ * configuration of a system whose scaled coordinates x/V^(1/3) and volume
+ * V = e^eps sample p(eps) ~ V^(N'+1) exp(-(lambda U + P0 V)/kT) (N' = dof/3
+ * independent positions).  eps takes one Euler-Maruyama step of the
+ * overdamped Langevin equation with that stationary density and mobility
+ * D = kT m_p / V, m_p = beta_T / tau_p (isotropic stochastic cell rescaling
+ * at fixed momenta).  Its Ito drift D d(ln p)/d eps + dD/d eps is
+ *   d eps = m_p [(dof kT + lambda W)/(3V) - P0] dt + sqrt(2 kT m_p dt / V) eta,
+ * W the virial of U at x_s (the Jacobian's kT/V cancels against dD/d eps);
+ * positions and box are scaled by e^(d eps / 3) about the origin, eta
+ * drawn from the barostat stream. */
 static int md_step(const ora_eam* p, const double* theta, const ora_md* md,
                    uint32_t stream, long s, double lam_a, double lam_b, double* x,
-                   double* v, const double* x0, int n, const double box[3], terms* t,
+                   double* v, const double* x0, int n, double box[3], terms* t,
                    double* F, double* xi, double* dW)
 {
     double m = md->mass, dt = md->dt;
@@ -656,6 +674,16 @@ static int md_step(const ora_eam* p, const double* theta, const ora_md* md,
     }
     for (int i = 0; i < 3 * n; i++) v[i] = c1 * v[i] + c2 * xi[i];
     for (int i = 0; i < 3 * n; i++) x[i] += 0.5 * dt * v[i];
+    if (md->npt) {
+        double kT = KB_EV_PER_K * md->T, V = box[0] * box[1] * box[2];
+        double mp = md->beta_T / md->tau_p, z[3];
+        ora_normals(md->seed, md->replica, ORA_STREAM_BARO, 0, (uint64_t)s, z);
+        double drive = (dof(md, n) * kT + lam_b * t->Wv) / (3.0 * V) - md->P0;
+        double deps = mp * drive * dt + sqrt(2.0 * kT * mp * dt / V) * z[0];
+        double mu = exp(deps / 3.0);
+        for (int i = 0; i < 3 * n; i++) x[i] *= mu;
+        for (int c = 0; c < 3; c++) box[c] *= mu;
+    }
     int st = eval_terms(p, theta, md, x, x0, n, box, t);
     if (st) return st;
     blend_force(md, t, n, lam_b, F);
@@ -691,12 +719,15 @@ static void ws_free(workspace* w)
  * lambda, switch back.  W_f and W_b are the two irreversible works. */
 int ora_switch_run(const ora_eam* p, const double* theta, const ora_md* md,
                    double* x, double* v, const double* x0, int n,
-                   const double box[3], double* W_f, double* W_b,
+                   double box[3], double* W_f, double* W_b,
                    double* Wcum_f, double* Wcum_b, double* trace,
                    int trace_stride, int n_trace_max)
 {
     if (n < 2 || md->t_s < 1 || md->t_eq < 0) return ORA_EINVAL;
     if (md->path == ORA_PATH_RS && !(md->lambda_f > 0 && md->lambda_f < 1)) return ORA_EINVAL;
+    if (md->npt && (md->path != ORA_PATH_RS || !(md->beta_T > 0) || !(md->tau_p > 0) || md->P0 < 0 ||
+                    (md->h0 == ORA_H0_HARMONIC && md->k_h0 != 0.0)))
+        return ORA_EINVAL;  /* the Einstein crystal has no pressure (Sec. III.A) */
     workspace w;
     ws_alloc(&w, n);
     uint32_t stream = md->path == ORA_PATH_FL ? ORA_STREAM_FL : ORA_STREAM_RS;
@@ -739,14 +770,15 @@ int ora_langevin_steps(const ora_eam* p, const double* theta, const ora_md* md,
                        double lambda, double* x, double* v, const double* x0,
                        int n, const double box[3], long step0, long n_steps)
 {
-    if (n < 2) return ORA_EINVAL;
+    if (n < 2 || md->npt) return ORA_EINVAL;  /* fixed box */
+    double bx[3] = {box[0], box[1], box[2]};
     workspace w;
     ws_alloc(&w, n);
-    int st = eval_terms(p, theta, md, x, x0, n, box, &w.t);
+    int st = eval_terms(p, theta, md, x, x0, n, bx, &w.t);
     for (long s = 0; s < n_steps && !st; s++) {
         double dW;
         st = md_step(p, theta, md, ORA_STREAM_STEP, step0 + s, lambda, lambda, x, v, x0,
-                     n, box, &w.t, w.F, w.xi, &dW);
+                     n, bx, &w.t, w.F, w.xi, &dW);
     }
     ws_free(&w);
     return st;
@@ -761,6 +793,8 @@ int ora_msd_fit(const ora_eam* p, const double* theta, const ora_md* md, double*
     if (n < 2 || n_samples < 1 || stride < 1) return ORA_EINVAL;
     ora_md m0 = *md;
     m0.path = ORA_PATH_FL;
+    m0.npt = 0;
+    double bx[3] = {box[0], box[1], box[2]};
     workspace w;
     ws_alloc(&w, n);
     int st = eval_terms(p, theta, &m0, x, x0, n, box, &w.t);
@@ -768,13 +802,13 @@ int ora_msd_fit(const ora_eam* p, const double* theta, const ora_md* md, double*
     long s = 0;
     for (; s < n_eq && !st; s++) {
         double dW;
-        st = md_step(p, theta, &m0, ORA_STREAM_MSD, s, 0.0, 0.0, x, v, x0, n, box, &w.t,
+        st = md_step(p, theta, &m0, ORA_STREAM_MSD, s, 0.0, 0.0, x, v, x0, n, bx, &w.t,
                      w.F, w.xi, &dW);
     }
     for (long q = 0; q < n_samples && !st; q++) {
         for (int r = 0; r < stride && !st; r++, s++) {
             double dW;
-            st = md_step(p, theta, &m0, ORA_STREAM_MSD, s, 0.0, 0.0, x, v, x0, n, box,
+            st = md_step(p, theta, &m0, ORA_STREAM_MSD, s, 0.0, 0.0, x, v, x0, n, bx,
                          &w.t, w.F, w.xi, &dW);
         }
         double R[3] = {0, 0, 0}, R0[3] = {0, 0, 0};

@@ -27,7 +27,7 @@ enum { ORA_PATH_FL = 0, ORA_PATH_RS = 1 };
 enum { ORA_H0_EAM = 0, ORA_H0_HARMONIC = 1 };
 /* Philox stream ids (4th counter word, low bits). */
 enum { ORA_STREAM_FL = 0, ORA_STREAM_INITV = 1, ORA_STREAM_RS = 2,
-       ORA_STREAM_MSD = 3, ORA_STREAM_STEP = 4 };
+       ORA_STREAM_MSD = 3, ORA_STREAM_STEP = 4, ORA_STREAM_BARO = 5 };
 
 /* Analytic Fe-like EAM: Johnson-type exponential pair and density,
  * Finnis-Sinclair embedding F = -B sqrt(rho), quintic taper r_s..r_c. */
@@ -52,6 +52,11 @@ typedef struct {
     int fix_cm;       /* 1: centre of mass held fixed (noise and force means removed) */
     int h0;           /* ORA_H0_EAM, or ORA_H0_HARMONIC (springs k_h0 to the sites) */
     double k_h0;
+    /* isotropic barostat (reversible-scaling path only, Sec. III.C): 0 off */
+    int npt;
+    double P0;        /* target pressure, eV/A^3 */
+    double beta_T;    /* compressibility of the coupling, A^3/eV */
+    double tau_p;     /* relaxation time of the coupling, ps */
 } ora_md;
 
 /* constants */
@@ -108,10 +113,12 @@ int ora_init_velocities(const ora_md* md, int n, double* v);
  * RS schedule: t_eq at 1, switch 1->lambda_f, t_eq at lambda_f, switch back.
  * Wcum_f / Wcum_b (nullable): cumulative work after each switch step, t_s+1.
  * trace (nullable): every trace_stride steps, 8 doubles
- *   (step, lambda, dH/dlambda, U0, U_E, T_internal, W_f, W_b). */
+ *   (step, lambda, dH/dlambda, U0, U_E, T_internal, W_f, W_b).
+ * With md->npt (RS path only) the box follows the isotropic barostat and
+ * box[] returns the final box. */
 int ora_switch_run(const ora_eam* p, const double* theta, const ora_md* md,
                    double* x, double* v, const double* x0, int n,
-                   const double box[3], double* W_f, double* W_b,
+                   double box[3], double* W_f, double* W_b,
                    double* Wcum_f, double* Wcum_b, double* trace,
                    int trace_stride, int n_trace_max);
 

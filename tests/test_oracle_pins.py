@@ -601,3 +601,49 @@ def test_jarzynski_estimator_pins():
     w = np.random.default_rng(3).normal(50.0, 1.0, 40)
     assert O.jarzynski(T, w) <= w.mean()
     assert O.jarzynski(T, w) >= w.min()
+
+
+def test_barostat_samples_the_ideal_gas_volume_distribution():
+    """Isothermal-isobaric ideal gas (U = 0) with the centre of mass fixed:
+    the N - 1 free positions give p(V) ~ V^(N-1) exp(-P0 V / kT), a Gamma
+    distribution with mean N kT / P0 and variance N (kT / P0)^2.  The final
+    volumes of independent runs (each many barostat relaxation times long)
+    sample it; a wrong Jacobian term would shift the mean by 1/N = 12.5 %."""
+    n, T = 8, 300.0
+    kT = O.kB() * T
+    P0 = 2.585e-5
+    V0 = n * kT / P0
+    L = V0 ** (1 / 3)
+    g = np.random.default_rng(8)
+    x0 = g.uniform(0, L, (n, 3))
+    box = np.array([L, L, L])
+    p, th = O.eam(**W.EAM_FE_LIKE), None
+    th = np.zeros(3 * 2 * W.EAM_FE_LIKE["n_knots"])
+
+    def one(seed):
+        m = O.md(T=T, mass=mass(), path=O.PATH_RS, lambda_f=0.5, t_eq=1500, t_s=1, seed=seed,
+                 h0=O.H0_HARMONIC, k_h0=0.0, npt=1, P0=P0, beta_T=1.0 / P0, tau_p=0.5)
+        v = O.init_velocities(m, n)
+        r = O.switch_run(p, th, m, x0, v, x0, box)
+        return float(np.prod(r["box"]))
+
+    with ThreadPoolExecutor(8) as ex:
+        Vs = np.array(list(ex.map(one, range(1, 801))))
+    se = Vs.std(ddof=1) / np.sqrt(len(Vs))
+    assert abs(Vs.mean() - V0) < max(4 * se, 0.02 * V0)
+    assert abs(Vs.mean() - V0) < 0.06 * V0
+    assert Vs.var(ddof=1) == pytest.approx(n * (kT / P0) ** 2, rel=0.3)
+
+
+def test_barostat_relaxes_a_cold_crystal_to_zero_pressure(pot):
+    """At 20 K and P0 = 0, bcc started under tension (a = 2.90 A) contracts to
+    the potential's static zero-pressure lattice parameter, 2.87 A (thermal
+    expansion at 20 K is ~1e-3 A)."""
+    p, th = pot
+    x0, box = O.create_crystal(O.BCC, 2.90, 4, 4, 4)
+    m = O.md(T=20.0, mass=mass(), path=O.PATH_RS, lambda_f=0.9, t_eq=2000, t_s=1, seed=3,
+             npt=1, P0=0.0, beta_T=1.2, tau_p=0.2)
+    v = O.init_velocities(m, len(x0))
+    r = O.switch_run(p, th, m, x0, v, x0, box)
+    assert r["box"][0] / 4 == pytest.approx(2.8705, abs=2.5e-3)
+    assert np.allclose(r["box"], r["box"][0])
