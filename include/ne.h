@@ -87,6 +87,20 @@ typedef struct {
     unsigned replica;  /* < 2^28 */
     int fix_cm;        /* 1: centre of mass fixed (noise and force means removed) */
     ne_precision prec;
+    /* Isotropic barostat (Sec. III.C: reversible scaling at P = 0), RS path
+     * of the multi-kernel runs only; 0 = fixed box.  Each step, after the
+     * second drift, ln V takes one step of the overdamped Langevin equation
+     * whose stationary density is V^(N'+1) exp(-(lambda U + P0 V)/k_B T)
+     * (N' = dof/3) at fixed scaled coordinates:
+     *   d ln V = m [(dof k_B T + lambda W)/(3V) - P0] dt + sqrt(2 k_B T m dt / V) eta,
+     * m = beta_T / tau_p, W the virial of U at the step's start, eta from
+     * Philox stream 5; positions and box scale by exp(d ln V / 3) about the
+     * origin.  The final boxes are read back with ne_ctx_boxes (pass them
+     * to the next segment).  With P0 = 0, eq. rs gives G(T) at zero pressure. */
+    int npt;
+    double P0;         /* eV / A^3, >= 0 */
+    double beta_T;     /* coupling compressibility, A^3 / eV, > 0 */
+    double tau_p;      /* coupling time, ps, > 0 */
 } ne_md_params;
 
 /* ------------------------------------------------------------- context */
@@ -115,6 +129,12 @@ ne_status ne_ctx_set_tuning(ne_ctx* ctx, int threads_per_atom);
  * a replica depend on C, so results agree across C to rounding only; a fixed
  * C makes a replica's bits independent of the rest of its batch. */
 ne_status ne_ctx_set_cluster_size(ne_ctx* ctx, int ctas);
+
+/* Boxes [n_rep][3] (host) at the end of the last multi-kernel run or
+ * segment of this context, in the order of its replicas: with the barostat
+ * (ne_md_params.npt) the volumes it reached, else the boxes passed in.
+ * NE_EINVAL if n_rep differs from that run's replica count. */
+ne_status ne_ctx_boxes(ne_ctx* ctx, int n_rep, double* boxes_host);
 
 /* Work counters since the context was created (each pointer may be NULL):
  * list_builds -- per-replica neighbour-list builds of the multi-kernel path

@@ -32,6 +32,7 @@ struct ne_ctx {
     ne_eam_params eam{};
     int max_atoms = 0, max_rep = 0, tiles_cap = 0, cells_cap = 0, tpa = 4;
     int cluster_c = 0;  // crystal runner: CTAs per cluster (0: chosen per batch)
+    int last_nrep = 0;  // replicas of the last multi-kernel run (ne_ctx_boxes)
     double* theta = nullptr;
     float4* pf32 = nullptr;
     ned4* pf64 = nullptr;
@@ -175,7 +176,7 @@ ne_status setup_batch(ne_ctx* ctx, int n_rep, const int* off, const double* boxe
     if (n_tot > ctx->max_atoms) return fail(ctx, NE_ENOMEM, "atom count exceeds the context");
     ctx->rep_h.assign(n_rep, RepDev{});
     ctx->tile_rep_h.clear();
-    int cells = 0;
+    int cells = 0, npt_any = 0;
     const double rc = ctx->eam.r_c;
     for (int r = 0; r < n_rep; ++r) {
         const ne_md_params& m = md[(size_t)r * md_stride];
@@ -185,12 +186,15 @@ ne_status setup_batch(ne_ctx* ctx, int n_rep, const int* off, const double* boxe
         const double skin = skin_override >= 0 ? skin_override : m.skin;
         if (!(skin >= 0)) return fail(ctx, NE_EINVAL, "skin must be >= 0");
         const double rl = rc + skin;
+        // with the barostat the cells keep an edge >= r_c + skin down to a
+        // 10 % linear contraction of the box (further is reported as NE_ERANGE)
+        const double shrink = m.npt ? 0.9 : 1.0;
         for (int d = 0; d < 3; ++d) {
             R.L[d] = boxes[3 * r + d];
             if (geometry && !(R.L[d] > 2.0 * rl))
                 return fail(ctx, NE_EINVAL, "box edge must exceed 2 (r_c + skin)");
             R.invL[d] = 1.0 / R.L[d];
-            R.nc[d] = geometry ? (int)std::min(std::floor(R.L[d] / rl), 1024.0) : 0;
+            R.nc[d] = geometry ? (int)std::min(std::floor(shrink * R.L[d] / rl), 1024.0) : 0;
         }
         // cells of edge >= r_c + skin; fewer (larger) cells when the box is
         // sparse, so the cell count stays below 2n + 27
@@ -220,7 +224,12 @@ ne_status setup_batch(ne_ctx* ctx, int n_rep, const int* off, const double* boxe
         R.seed = m.seed;
         R.replica = m.replica;
         if (m.replica >= (1u << 28)) return fail(ctx, NE_EINVAL, "replica id must be < 2^28");
+        R.npt = m.npt;
+        R.P0 = m.P0;
+        R.mp = m.npt ? m.beta_T / m.tau_p : 0.0;
+        npt_any |= m.npt;
     }
+    ctx->last_nrep = n_rep;
     const int n_tiles = (int)ctx->tile_rep_h.size();
     if (n_tiles > ctx->tiles_cap) return fail(ctx, NE_ENOMEM, "tile capacity exceeded");
     if (cells > ctx->cells_cap) return fail(ctx, NE_ENOMEM, "cell capacity exceeded");
@@ -272,6 +281,7 @@ ne_status setup_batch(ne_ctx* ctx, int n_rep, const int* off, const double* boxe
     B.rebuilds = ctx->rebuilds;
     B.status = ctx->status;
     B.tab = ctx->tab;
+    B.npt_any = npt_any;
     return NE_OK;
 }
 
@@ -307,6 +317,7 @@ void one_step(const DevBatch& B, const Sched& S, bool mixed, const long long* ct
 {
     force_eval(B, S, mixed, ctr, j, 1, 0, st);
     ne::launch_step(B, S, mixed, ctr, j, first ? 0 : 1, 1, st);
+    if (B.npt_any) ne::launch_npt_box(B, S, ctr, j, st);
 }
 
 // Run steps [0, n_steps) of schedule S from the state held in B, then the
@@ -320,7 +331,9 @@ ne_status run_steps(ne_ctx* ctx, const DevBatch& B, const Sched& S, bool mixed, 
     long long* ctr = ctx->step_ctr;
     NE_CU(cudaMemcpyAsync(ctr, &s_begin, sizeof(long long), cudaMemcpyHostToDevice, st));
     NE_CU(cudaStreamSynchronize(st));
-    ne::launch_nl_build(B, 1, 1, st);
+    // list from the lattice sites (from the positions when a barostat may
+    // have changed the box since the sites were made)
+    ne::launch_nl_build(B, 1, B.npt_any ? 0 : 1, st);
     ne::launch_prep(B, S, mixed, ctr, st);
     long long s = 0;
     // first step: no closing kick
@@ -453,6 +466,11 @@ ne_status check_md(ne_ctx* ctx, const ne_md_params* m)
     if (m->path == NE_PATH_RS && !(m->lambda_f > 0 && m->lambda_f < 1))
         return fail(ctx, NE_EINVAL, "lambda_f must lie in (0, 1)");
     if (m->prec != NE_FP64 && m->prec != NE_MIXED) return fail(ctx, NE_EINVAL, "unknown precision");
+    if (m->npt != 0 && m->npt != 1) return fail(ctx, NE_EINVAL, "npt must be 0 or 1");
+    if (m->npt && m->path != NE_PATH_RS)
+        return fail(ctx, NE_EINVAL, "the barostat runs on the reversible-scaling path (the Einstein crystal has no pressure)");
+    if (m->npt && (!(m->beta_T > 0) || !(m->tau_p > 0) || !(m->P0 >= 0)))
+        return fail(ctx, NE_EINVAL, "barostat: beta_T > 0, tau_p > 0 and P0 >= 0 required");
     return NE_OK;
 }
 
@@ -591,6 +609,18 @@ ne_status ne_ctx_set_cluster_size(ne_ctx* ctx, int ctas)
     if (!ctx) return NE_EINVAL;
     if (ctas < 0 || ctas > 16) return fail(ctx, NE_EINVAL, "cluster size must be 0 (automatic) or 1..16");
     ctx->cluster_c = ctas;
+    return NE_OK;
+}
+
+ne_status ne_ctx_boxes(ne_ctx* ctx, int n_rep, double* boxes_host)
+{
+    if (!ctx || !boxes_host || n_rep < 1) return NE_EINVAL;
+    if (n_rep != ctx->last_nrep) return fail(ctx, NE_EINVAL, "replica count differs from the last run");
+    std::vector<RepDev> r(n_rep);
+    if (cudaMemcpy(r.data(), ctx->rep, sizeof(RepDev) * n_rep, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(ctx, NE_ECUDA, "reading the boxes failed");
+    for (int q = 0; q < n_rep; ++q)
+        for (int d = 0; d < 3; ++d) boxes_host[3 * q + d] = r[q].L[d];
     return NE_OK;
 }
 
@@ -810,6 +840,7 @@ ne_status ne_langevin_step(ne_ctx* ctx, const ne_md_params* md, double* x_dev, d
     if (!ctx || !x_dev || !v_dev || !x0_dev || !box || n < 2 || step < 0) return NE_EINVAL;
     ne_status s = check_md(ctx, md);
     if (s) return s;
+    if (md->npt) return fail(ctx, NE_EINVAL, "the barostat runs in the switching runs (ne_switch_run_segment, ne_rs_run)");
     cudaStream_t st = (cudaStream_t)stream;
     int off[2] = {0, n};
     RunArgs a{};
@@ -995,6 +1026,8 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
     ne_status s = check_batch(ctx, md, n_rep, off.data());
     if (s) return s;
     if (md[0].prec != NE_MIXED) return fail(ctx, NE_EINVAL, "the crystal runner is mixed precision; use ne_switch_run_segment for FP64");
+    for (int r = 0; r < n_rep; ++r)
+        if (md[r].npt) return fail(ctx, NE_EINVAL, "the crystal runner keeps the box fixed; use ne_switch_run_segment for the barostat");
     const long long S_total = 2 * md[0].t_eq + 2 * md[0].t_s;
     if (step_begin < 0 || n_steps < 0 || step_begin + n_steps > S_total)
         return fail(ctx, NE_EINVAL, "step range outside the schedule");
@@ -1250,6 +1283,7 @@ ne_status ne_msd_fit(ne_ctx* ctx, const ne_md_params* md, double* x_dev, double*
         return NE_EINVAL;
     ne_status s = check_md(ctx, md);
     if (s) return s;
+    if (md->npt) return fail(ctx, NE_EINVAL, "the barostat runs in the switching runs (ne_switch_run_segment, ne_rs_run)");
     cudaStream_t st = (cudaStream_t)stream;
     int off[2] = {0, n};
     RunArgs a{};

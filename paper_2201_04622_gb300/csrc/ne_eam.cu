@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
     k_force(DevBatch B, Sched S, const long long* __restrict__ step_base, int j, int want_noise)
 {
     using R = typename Pos<MIXED>::R;
-    __shared__ double red[7][NE_TILE * TPA];
+    __shared__ double red[8][NE_TILE * TPA];
     __shared__ int s_last;
     const int tile = blockIdx.x;
     const int rep = B.tile_rep[tile];
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
     const R iL0 = (R)P.invL[0], iL1 = (R)P.invL[1], iL2 = (R)P.invL[2];
     const R inv_h = MIXED ? (R)B.tab.inv_h_rf : (R)B.tab.inv_h_r;
     const int nk = B.tab.nk;
-    R fx = 0, fy = 0, fz = 0, ep = 0;
+    R fx = 0, fy = 0, fz = 0, ep = 0, vir = 0;  // vir: -(1/2) sum_j r dU/dr (the pair's half)
     if (valid) {
         V3<R> pi;
         R dFi;
@@ -256,13 +256,15 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
             fy += s * dy;
             fz += s * dz;
             ep += (R)0.5 * phi;
+            vir -= (R)0.5 * s * r2;
         }
     }
     fx = lane_sum(fx, TPA);
     fy = lane_sum(fy, TPA);
     fz = lane_sum(fz, TPA);
     double epd = lane_sum((double)ep, TPA);
-    double v[7] = {0, 0, 0, 0, 0, 0, 0};
+    double vird = lane_sum((double)vir, TPA);
+    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (valid && lane == 0) {
         if constexpr (MIXED) {
             B.f32[i] = make_float4((float)fx, (float)fy, (float)fz, 0.f);
@@ -272,6 +274,7 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
             B.f64[3 * i + 2] = (double)fz;
         }
         v[0] = epd;
+        v[7] = vird;
         v[1] = (double)fx;
         v[2] = (double)fy;
         v[3] = (double)fz;
@@ -300,11 +303,11 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
             }
         }
     }
-    for (int q = 0; q < 7; ++q) red[q][threadIdx.x] = v[q];
+    for (int q = 0; q < 8; ++q) red[q][threadIdx.x] = v[q];
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w)
-            for (int q = 0; q < 7; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+            for (int q = 0; q < 8; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -316,6 +319,7 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
         pa[PA_XIX] = red[4][0];
         pa[PA_XIY] = red[5][0];
         pa[PA_XIZ] = red[6][0];
+        pa[PA_VIR] = red[7][0];
         __threadfence();
         unsigned prev = atomicAdd(&B.tile_done[rep], 1u);
         s_last = (prev == (unsigned)P.ntile - 1u);

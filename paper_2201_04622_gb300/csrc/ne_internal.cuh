@@ -35,15 +35,16 @@ struct __align__(32) ned4 {
 enum { ST_ERANGE = 1, ST_ENEIGH = 2, ST_ENAN = 4, ST_ETIMEOUT = 8, ST_EINVAL = 16 };
 
 // Philox stream ids (low 4 bits of the 4th counter word)
-enum { STREAM_FL = 0, STREAM_INITV = 1, STREAM_RS = 2, STREAM_MSD = 3, STREAM_STEP = 4 };
+enum { STREAM_FL = 0, STREAM_INITV = 1, STREAM_RS = 2, STREAM_MSD = 3, STREAM_STEP = 4, STREAM_BARO = 5 };
 
 // tile partials of pass 1 / pass 2 (at x_k)
-enum { PA_UEMB = 0, PA_UPAIR, PA_F0X, PA_F0Y, PA_F0Z, PA_XIX, PA_XIY, PA_XIZ, NPA };
+enum { PA_UEMB = 0, PA_UPAIR, PA_F0X, PA_F0Y, PA_F0Z, PA_XIX, PA_XIY, PA_XIZ, PA_VIR, NPA };
 // tile partials of the step kernel (at x_{k+1}; KE of the completed velocity)
 enum { PB_UE = 0, PB_UX, PB_UY, PB_UZ, PB_U2, PB_KE, NPB };
 // per-replica totals
-enum { TOT_UEMB = 0, TOT_UPAIR, TOT_F0X, TOT_F0Y, TOT_F0Z, TOT_XIX, TOT_XIY, TOT_XIZ,
+enum { TOT_UEMB = 0, TOT_UPAIR, TOT_F0X, TOT_F0Y, TOT_F0Z, TOT_XIX, TOT_XIY, TOT_XIZ, TOT_VIR,
        TOT_UE, TOT_UX, TOT_UY, TOT_UZ, TOT_U2, TOT_KE, NTOT };
+static_assert(TOT_VIR == PA_VIR && TOT_UE == NPA, "totals: pass-2 partials first, then the step's");
 
 struct RepDev {
     double L[3], invL[3];
@@ -60,6 +61,8 @@ struct RepDev {
     int dof;
     unsigned long long seed;
     unsigned replica;
+    int npt;         // isotropic barostat on (RS path)
+    double P0, mp;   // target pressure, mobility beta_T / tau_p
 };
 
 // Schedule of a run, shared by the replicas of one launch.
@@ -122,6 +125,7 @@ struct DevBatch {
     unsigned long long* rebuilds;  // count of replica list builds
     int* status;
     Tables tab;
+    int npt_any;       // some replica has the barostat on
 };
 
 // ------------------------------------------------------------------ lambda
@@ -276,4 +280,5 @@ void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, doubl
                      float* bins, int n_bin_blocks, cudaStream_t st);
 int backward_bin_blocks(const DevBatch& B);
 void launch_virial(const DevBatch& B, double* out, cudaStream_t st);
+void launch_npt_box(const DevBatch& B, const Sched& S, const long long* step_base, int j, cudaStream_t st);
 }  // namespace ne

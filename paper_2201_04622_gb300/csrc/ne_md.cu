@@ -154,6 +154,27 @@ __device__ __forceinline__ double blend(int path, double lam, double F0, double 
 // then the tile partials at the resulting x (U_E, sum u, sum |u|^2) and the
 // kinetic energy of the completed velocity v_s, the FP32 wrapped copy of x
 // and the displacement check against the list-build positions.
+//
+// With the barostat (RepDev.npt), after the second drift ln V takes one
+// Euler-Maruyama step of the overdamped Langevin equation whose stationary
+// density is V^(N'+1) exp(-(lambda U + P0 V)/kT) at fixed scaled
+// coordinates (N' = dof / 3; the Ito drift includes the derivative of the
+// mobility kT m / V, which cancels the Jacobian's kT / V):
+//   d ln V = m [(dof kT + lambda W)/(3V) - P0] dt + sqrt(2 kT m dt / V) eta,
+// W the virial at x_s (replica totals of pass 2 of this step), eta the first
+// normal of Philox stream 5 at (atom 0, step s).  Every block computes the
+// same factor; positions scale about the origin here, the box in k_npt_box
+// after this kernel.
+__device__ inline double npt_scale(const RepDev& P, const double* T, double lam, long long s, double dt)
+{
+    const double V = P.L[0] * P.L[1] * P.L[2];
+    double z[3];
+    ne_normals64(ne_philox_block(P.seed, P.replica, (unsigned)STREAM_BARO, 0u, (unsigned long long)s), z);
+    const double drive = (P.dof * P.kT + lam * T[TOT_VIR]) / (3.0 * V) - P.P0;
+    const double deps = P.mp * drive * dt + sqrt(2.0 * P.kT * P.mp * dt / V) * z[0];
+    return exp(deps / 3.0);
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(NE_TILE)
     k_step(DevBatch B, Sched S, const long long* __restrict__ step_base, int j, int do_close, int do_open)
@@ -174,6 +195,7 @@ __global__ void __launch_bounds__(NE_TILE)
     int bad = 0;
     if (valid) {
         double x[3], v[3], u[3], F0[3], mF0[3], mFE[3];
+        double Lb[3] = {P.L[0], P.L[1], P.L[2]};  // box after this step (the barostat scales it)
         for (int c = 0; c < 3; ++c) {
             x[c] = B.x[3 * i + c];
             v[c] = B.v[3 * i + c];
@@ -209,8 +231,15 @@ __global__ void __launch_bounds__(NE_TILE)
                 x[c] += 0.5 * S.dt * v[c];
                 v[c] = P.c1 * v[c] + P.c2 * xi[c];
                 x[c] += 0.5 * S.dt * v[c];
-                u[c] = x[c] - B.x0[3 * i + c];
             }
+            if (P.npt) {
+                const double mu = npt_scale(P, T, lam_n, s, S.dt);
+                for (int c = 0; c < 3; ++c) {
+                    x[c] *= mu;
+                    Lb[c] = mu * P.L[c];
+                }
+            }
+            for (int c = 0; c < 3; ++c) u[c] = x[c] - B.x0[3 * i + c];
         }
         for (int c = 0; c < 3; ++c) {
             if (!isfinite(x[c]) || !isfinite(v[c])) bad |= ST_ENAN;
@@ -222,11 +251,11 @@ __global__ void __launch_bounds__(NE_TILE)
         part[PB_UE] = 0.5 * P.k * part[PB_U2];
         // FP32 wrapped copy and displacement since the list build
         float w[3];
-        for (int c = 0; c < 3; ++c) w[c] = (float)wrap(x[c], P.L[c], P.invL[c]);
+        for (int c = 0; c < 3; ++c) w[c] = (float)wrap(x[c], Lb[c], 1.0 / Lb[c]);
         if constexpr (MIXED) B.pos32[i] = make_float4(w[0], w[1], w[2], 0.f);
         float4 pb = B.pbuild[i];
         float d0 = w[0] - pb.x, d1 = w[1] - pb.y, d2 = w[2] - pb.z;
-        const float L0 = (float)P.L[0], L1 = (float)P.L[1], L2 = (float)P.L[2];
+        const float L0 = (float)Lb[0], L1 = (float)Lb[1], L2 = (float)Lb[2];
         d0 -= L0 * rintf(d0 / L0);
         d1 -= L1 * rintf(d1 / L1);
         d2 -= L2 * rintf(d2 / L2);
@@ -297,6 +326,32 @@ __global__ void k_trace_T(DevBatch B, const long long* __restrict__ step_base, i
 }
 
 __global__ void k_advance(long long* step_base, long long by) { *step_base += by; }
+
+// Box of every barostatted replica after the step kernel of step s (same
+// scale factor as that kernel).  A box whose cells became shorter than
+// r_c + skin, or whose edge fell below 2 (r_c + skin), is reported
+// (NE_ERANGE) and left unchanged.
+__global__ void k_npt_box(DevBatch B, Sched S, const long long* __restrict__ step_base, int j)
+{
+    const int rep = blockIdx.x;
+    if (rep >= B.n_rep || threadIdx.x != 0) return;
+    RepDev& P = const_cast<RepDev*>(B.rep)[rep];
+    if (!P.npt) return;
+    const long long s = *step_base + j;
+    const double mu = npt_scale(P, B.tot + (size_t)rep * NTOT, ne_sched_lambda(S, s + 1), s, S.dt);
+    const double rl = sqrt(P.rlist2);
+    for (int c = 0; c < 3; ++c) {
+        const double L = mu * P.L[c];
+        if (!(L > 2.0 * rl) || (P.nc[c] > 0 && !(L / P.nc[c] >= rl))) {
+            ne_set_status(B.status, ST_ERANGE);
+            return;
+        }
+    }
+    for (int c = 0; c < 3; ++c) {
+        P.L[c] *= mu;
+        P.invL[c] = 1.0 / P.L[c];
+    }
+}
 
 __global__ void k_noise(unsigned long long seed, unsigned replica, int stream, long long step, int n,
                         int mixed, double* z)
@@ -467,6 +522,11 @@ void launch_prep(const DevBatch& B, const Sched& S, bool mixed, const long long*
         k_step<true><<<B.n_tiles, NE_TILE, 0, st>>>(B, S, step_base, 0, 0, 0);
     else
         k_step<false><<<B.n_tiles, NE_TILE, 0, st>>>(B, S, step_base, 0, 0, 0);
+}
+
+void launch_npt_box(const DevBatch& B, const Sched& S, const long long* step_base, int j, cudaStream_t st)
+{
+    k_npt_box<<<B.n_rep, 32, 0, st>>>(B, S, step_base, j);
 }
 
 void launch_wrap32(const DevBatch& B, cudaStream_t st)

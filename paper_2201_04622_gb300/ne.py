@@ -24,7 +24,7 @@ NE_PATH_FL, NE_PATH_RS = 0, 1
 
 # every symbol include/ne.h declares
 SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_set_theta", "ne_ctx_get_theta",
-           "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_counters", "ne_last_error",
+           "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_boxes", "ne_ctx_counters", "ne_last_error",
            "ne_create_crystal", "ne_create_crystal_ca", "ne_eam_energy_forces", "ne_eam_virial", "ne_eam_energy_forces_noalloc",
            "ne_spring_forces",
            "ne_eam_backward", "ne_noise", "ne_init_velocities", "ne_langevin_step",
@@ -57,7 +57,8 @@ class MdParams(C.Structure):
                 ("mass", C.c_double), ("k_spring", C.c_double), ("skin", C.c_double),
                 ("lambda_fn", C.c_int), ("path", C.c_int), ("t_eq", C.c_longlong),
                 ("t_s", C.c_longlong), ("lambda_f", C.c_double), ("seed", C.c_ulonglong),
-                ("replica", C.c_uint), ("fix_cm", C.c_int), ("prec", C.c_int)]
+                ("replica", C.c_uint), ("fix_cm", C.c_int), ("prec", C.c_int),
+                ("npt", C.c_int), ("P0", C.c_double), ("beta_T", C.c_double), ("tau_p", C.c_double)]
 
 
 def lib_path() -> str:
@@ -83,6 +84,7 @@ def load(build_if_missing: bool = True):
                 "ne_ctx_get_theta": [p, p, p],
                 "ne_ctx_set_tuning": [p, i],
                 "ne_ctx_set_cluster_size": [p, i],
+                "ne_ctx_boxes": [p, i, p],
                 "ne_ctx_counters": [p, p, p, p],
                 "ne_last_error": [p, p, p, i],
                 "ne_create_crystal": [i, d, i, i, i, p, p, p],
@@ -161,11 +163,13 @@ def eam_params(A, alpha, beta, B, r_e, r_s, r_c, rho_max, n_knots) -> EamParams:
 
 def md_params(dt=1e-3, T=100.0, damp=0.1, mass=None, k_spring=5.0, skin=0.5, lambda_fn=2,
               path=NE_PATH_FL, t_eq=0, t_s=1, lambda_f=0.5, seed=1, replica=0, fix_cm=1,
-              prec=NE_FP64) -> MdParams:
+              prec=NE_FP64, npt=0, P0=0.0, beta_T=0.0, tau_p=0.0) -> MdParams:
+    """npt = 1: isotropic barostat at P0 (eV/A^3), coupling compressibility
+    beta_T (A^3/eV) and time tau_p (ps); reversible-scaling path only."""
     if mass is None:
         mass = 55.845 * 1.0364269656262175e-4
     return MdParams(dt, T, damp, mass, k_spring, skin, lambda_fn, path, t_eq, t_s, lambda_f,
-                    seed, replica, fix_cm, prec)
+                    seed, replica, fix_cm, prec, npt, P0, beta_T, tau_p)
 
 
 # ------------------------------------------------------------------ entry points
@@ -190,6 +194,14 @@ def ne_ctx_get_theta(ctx, theta, stream=None):
 
 def ne_ctx_set_tuning(ctx, threads_per_atom):
     _err(ctx, load().ne_ctx_set_tuning(ctx, int(threads_per_atom)), "ne_ctx_set_tuning")
+
+
+def ne_ctx_boxes(ctx, n_rep):
+    """Boxes [n_rep][3] at the end of the last multi-kernel run (the barostat's)."""
+    import numpy as np
+    out = np.zeros((n_rep, 3))
+    _err(ctx, load().ne_ctx_boxes(ctx, int(n_rep), out.ctypes.data_as(C.c_void_p)), "ne_ctx_boxes")
+    return out
 
 
 def ne_ctx_set_cluster_size(ctx, ctas):

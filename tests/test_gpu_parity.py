@@ -251,6 +251,65 @@ def test_switch_run_trajectory_parity_100_steps(ctx, pot, lat, n, path):
     assert np.allclose(g["trace"], ro["trace"], rtol=1e-9, atol=1e-8)
 
 
+NPT = dict(path=O.PATH_RS, T=300.0, t_eq=30, t_s=35, lambda_f=0.5, npt=1, P0=0.0, beta_T=1.2, tau_p=0.05)
+
+
+@pytest.mark.parametrize("prec,tx,tb,tw", [(ne.NE_FP64, 1e-8, 1e-12, 1e-9), (ne.NE_MIXED, 2e-5, 1e-6, 1e-5)])
+def test_rs_barostat_trajectory_matches_oracle(ctx, pot, prec, tx, tb, tw):
+    """Reversible scaling with the isotropic barostat at P = 0 (Sec. III.C):
+    bcc started under tension (a = 2.90 A) contracts while lambda goes
+    1 -> 0.5 and back; positions, works and the box follow the oracle,
+    including the barostat's Philox noise."""
+    p, th = pot
+    x0, box = O.create_crystal(O.BCC, 2.90, 5, 5, 5)
+    mo, mg = md_pair(prec=prec, **NPT)
+    v0 = O.init_velocities(mo, len(x0))
+    ro = O.switch_run(p, th, mo, x0, v0, x0, box)
+    x, v = T(x0), T(v0)
+    wf = torch.zeros(1, dtype=torch.float64, device=DEV)
+    wb = torch.zeros(1, dtype=torch.float64, device=DEV)
+    ne.ne_switch_run(ctx, mg, x, v, T(x0), box, wf, wb)
+    bg = ne.ne_ctx_boxes(ctx, 1)[0]
+    assert ro["box"][0] < box[0] - 0.02
+    assert np.allclose(bg, ro["box"], rtol=tb, atol=0)
+    assert np.abs(N(x) - ro["x"]).max() < tx
+    assert float(wf.item()) == pytest.approx(ro["W_f"], rel=tw, abs=tw)
+    assert float(wb.item()) == pytest.approx(ro["W_b"], rel=tw, abs=tw)
+
+
+def test_rs_barostat_segments_continue_the_run(ctx):
+    """Two segments, the second started from the box the first reached
+    (ne_ctx_boxes), give the single run's state (the list is rebuilt from
+    positions at a segment start, so to summation order)."""
+    x0, box = O.create_crystal(O.BCC, 2.90, 5, 5, 5)
+    mo, mg = md_pair(**NPT)
+    v0 = O.init_velocities(mo, len(x0))
+    S = 2 * NPT["t_eq"] + 2 * NPT["t_s"]
+    res = []
+    for cut in (S, 47):
+        x, v = T(x0), T(v0)
+        W2 = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
+        ne.ne_switch_run_segment(ctx, [mg], [0, len(x0)], x, v, T(x0), [box], W2, 0, cut)
+        if cut < S:
+            b1 = ne.ne_ctx_boxes(ctx, 1)[0]
+            ne.ne_switch_run_segment(ctx, [mg], [0, len(x0)], x, v, T(x0), [b1], W2, cut, S - cut)
+        res.append((N(x), ne.ne_ctx_boxes(ctx, 1)[0], N(W2)))
+    assert np.abs(res[0][0] - res[1][0]).max() < 1e-9
+    assert np.allclose(res[0][1], res[1][1], rtol=1e-12, atol=0)
+    assert np.allclose(res[0][2], res[1][2], rtol=1e-10, atol=1e-10)
+
+
+def test_barostat_is_rejected_outside_the_rs_runs(ctx):
+    x0, box = O.create_crystal(O.BCC, 2.87, 6, 6, 6)
+    _, mg = md_pair(**dict(NPT, path=O.PATH_FL))
+    W2 = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
+    with pytest.raises(ne.NeError, match="NE_EINVAL"):
+        ne.ne_switch_run_segment(ctx, [mg], [0, len(x0)], T(x0), T(x0 * 0), T(x0), [box], W2, 0, 10)
+    _, mg = md_pair(prec=ne.NE_MIXED, **NPT)
+    with pytest.raises(ne.NeError, match="NE_EINVAL"):
+        ne.ne_crystal_run_segment(ctx, [mg], [(O.BCC, 2.87, 6, 6, 6)], T(x0), T(x0 * 0), W2, 0, 10)
+
+
 def test_switch_run_with_graph_chunks(ctx, pot):
     """A run long enough to be replayed from captured CUDA graphs (t_eq and
     t_s not multiples of the chunk), at the 4x4x4 bcc size of the smallest
