@@ -154,3 +154,40 @@ def size_scaling(ctx, lattice, a, sizes, T, mass, k, seeds, t_eq, t_s, **kw):
     Fs = np.array([r["F"] for r in rows])
     slope, F_inf = np.polyfit(inv, Fs, 1)
     return rows, (F_inf, slope)
+
+
+def rs_works(ctx, lattice, a, n, T0, mass, lambda_f, t_eq, t_s, seeds, prec=ne.NE_MIXED, skin=1.0, npt=False,
+             beta_T=1.2, tau_p=0.5, device="cuda"):
+    """Reversible scaling (Sec. III.C): per seed, t_eq steps at lambda = 1,
+    a forward switch to lambda_f over t_s steps, t_eq steps there and the
+    switch back, at T0, in the box of lattice parameter a or, with npt, at
+    zero pressure under the isotropic barostat (beta_T, tau_p: its coupling).
+    Returns the cumulative works [seeds][t_s + 1] (forward, backward) and,
+    with npt, the final lattice parameters (box edge / cells)."""
+    import torch
+    x0_np, box = crystal_sites(lattice, a, n)
+    x0 = torch.tensor(x0_np, dtype=torch.float64, device=device)
+    cf, cb, a_end = [], [], []
+    for seed in seeds:
+        md = ne.md_params(T=T0, mass=mass, skin=skin, prec=prec, path=ne.NE_PATH_RS, lambda_f=lambda_f,
+                          t_eq=t_eq, t_s=t_s, seed=seed, replica=0, fix_cm=1, npt=int(npt), P0=0.0,
+                          beta_T=beta_T, tau_p=tau_p)
+        x, v = x0.clone(), torch.zeros_like(x0)
+        ne.ne_init_velocities(ctx, md, v)
+        wf = torch.zeros(t_s + 1, dtype=torch.float64, device=device)
+        wb = torch.zeros(t_s + 1, dtype=torch.float64, device=device)
+        ne.ne_rs_run(ctx, md, lambda_f, x, v, x0, box, wf, wb)
+        cf.append(wf.cpu().numpy())
+        cb.append(wb.cpu().numpy())
+        if npt:
+            a_end.append(ne.ne_ctx_boxes(ctx, 1)[0][0] / n)
+    return np.array(cf), np.array(cb), np.array(a_end)
+
+
+def rs_free_energy(lattice, a, n, T0, F0_T0_per_atom, lambda_f, t_s, Wcum_f, Wcum_b, T_grid):
+    """Eq. rs: free energy per atom on T_grid (T0 .. T0/lambda_f) from the
+    cumulative works and the free energy at T0 (with the barostat at P = 0,
+    the Gibbs free energy)."""
+    x0, _ = crystal_sites(lattice, a, n)
+    nat = len(x0)
+    return ne.ne_rs_free_energy(nat, T0, F0_T0_per_atom * nat, lambda_f, t_s, Wcum_f, Wcum_b, T_grid)
