@@ -226,6 +226,14 @@ ne_status ne_eam_backward(ne_ctx* ctx, ne_precision prec, const double* x_dev, i
                           const double box[3], double gE, double* gx_dev,
                           double* gtheta_dev, void* stream);
 
+/* Same, adding gE dU/dtheta into gtheta_acc_dev [3][n_knots][2] instead of
+ * overwriting it, for averages of dU/dtheta over configurations of a run:
+ * the free energy's parameter gradient is dF/dtheta = <dU/dtheta> in the
+ * EAM ensemble (lambda = 0 of the FL path), and sum_k dlambda_k dU/dtheta(x_k)
+ * is the derivative of a switching work at fixed trajectory. */
+ne_status ne_eam_backward_acc(ne_ctx* ctx, ne_precision prec, const double* x_dev, int n,
+                              const double box[3], double gE, double* gtheta_acc_dev, void* stream);
+
 /* ------------------------------------------------------------- dynamics */
 /* The Langevin noise of the path: for atoms 0..n-1 the three normals of one
  * Philox4x32-10 block with key = seed and counter = (atom, step_lo, step_hi,

@@ -770,8 +770,8 @@ ne_status ne_spring_forces(const double* x_dev, const double* x0_dev, int n, dou
     return cudaGetLastError() == cudaSuccess ? NE_OK : NE_ECUDA;
 }
 
-ne_status ne_eam_backward(ne_ctx* ctx, ne_precision prec, const double* x_dev, int n, const double box[3],
-                          double gE, double* gx_dev, double* gtheta_dev, void* stream)
+static ne_status backward_impl(ne_ctx* ctx, ne_precision prec, const double* x_dev, int n, const double box[3],
+                               double gE, double* gx_dev, double* gtheta_dev, bool accumulate, void* stream)
 {
     if (!ctx || !x_dev || !box || n < 2 || !gtheta_dev) return NE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
@@ -802,9 +802,21 @@ ne_status ne_eam_backward(ne_ctx* ctx, ne_precision prec, const double* x_dev, i
         NE_CU(cudaMalloc((void**)&ctx->bins, sizeof(float) * (size_t)nbb * 6 * ctx->eam.n_knots));
         ctx->bins_blocks = nbb;
     }
-    ne::launch_backward(B, mixed, gE, gx_dev, gtheta_dev, ctx->bins, nbb, st);
+    ne::launch_backward(B, mixed, gE, gx_dev, gtheta_dev, ctx->bins, nbb, accumulate, st);
     if (gx_dev) ne::launch_scale(gx_dev, 3 * n, -gE, st);  // dU/dx = -F times gE
     return finish(ctx, st);
+}
+
+ne_status ne_eam_backward(ne_ctx* ctx, ne_precision prec, const double* x_dev, int n, const double box[3],
+                          double gE, double* gx_dev, double* gtheta_dev, void* stream)
+{
+    return backward_impl(ctx, prec, x_dev, n, box, gE, gx_dev, gtheta_dev, false, stream);
+}
+
+ne_status ne_eam_backward_acc(ne_ctx* ctx, ne_precision prec, const double* x_dev, int n, const double box[3],
+                              double gE, double* gtheta_acc_dev, void* stream)
+{
+    return backward_impl(ctx, prec, x_dev, n, box, gE, nullptr, gtheta_acc_dev, true, stream);
 }
 
 ne_status ne_noise(unsigned long long seed, unsigned replica, int noise_stream, long long step, int n,

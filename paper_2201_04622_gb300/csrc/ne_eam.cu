@@ -421,13 +421,13 @@ __global__ void __launch_bounds__(NE_TILE* TPA) k_backward_mixed(DevBatch B, flo
 }
 
 __global__ void k_bins_reduce(const float* __restrict__ bins, int n_blocks, int nb, double gE,
-                              double* __restrict__ gtheta)
+                              double* __restrict__ gtheta, int accumulate)
 {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nb) return;
     double acc = 0.0;
     for (int b = 0; b < n_blocks; ++b) acc += (double)bins[(size_t)b * nb + q];
-    gtheta[q] = gE * acc;
+    gtheta[q] = (accumulate ? gtheta[q] : 0.0) + gE * acc;
 }
 
 // FP64 path: FP64 basis weights added straight into gtheta (pre-zeroed) with
@@ -598,7 +598,7 @@ void launch_virial(const DevBatch& B, double* out, cudaStream_t st)
 }
 
 void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, double* gtheta,
-                     float* bins, int n_bin_blocks, cudaStream_t st)
+                     float* bins, int n_bin_blocks, bool accumulate, cudaStream_t st)
 {
     (void)gx;
     const int nk = B.tab.nk;
@@ -623,9 +623,9 @@ void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, doubl
             k_backward_mixed<8><<<n_bin_blocks, NE_TILE * 8, smem, st>>>(B, bins);
             break;
         }
-        k_bins_reduce<<<(nb + 255) / 256, 256, 0, st>>>(bins, n_bin_blocks, nb, gE, gtheta);
+        k_bins_reduce<<<(nb + 255) / 256, 256, 0, st>>>(bins, n_bin_blocks, nb, gE, gtheta, accumulate ? 1 : 0);
     } else {
-        cudaMemsetAsync(gtheta, 0, sizeof(double) * nb, st);
+        if (!accumulate) cudaMemsetAsync(gtheta, 0, sizeof(double) * nb, st);
         dim3 g(B.n_tiles);
         switch (B.tpa) {
         case 1: k_backward_fp64<1><<<g, NE_TILE * 1, 0, st>>>(B, gE, gtheta); break;

@@ -277,7 +277,7 @@ void launch_spring(const double* x, const double* x0, int n, double k, double* f
 void launch_export(const DevBatch& B, bool mixed, double* f_out, double* e_out, cudaStream_t st);
 void launch_msd_sample(const DevBatch& B, double* acc, cudaStream_t st);
 void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, double* gtheta,
-                     float* bins, int n_bin_blocks, cudaStream_t st);
+                     float* bins, int n_bin_blocks, bool accumulate, cudaStream_t st);
 int backward_bin_blocks(const DevBatch& B);
 void launch_virial(const DevBatch& B, double* out, cudaStream_t st);
 void launch_npt_box(const DevBatch& B, const Sched& S, const long long* step_base, int j, cudaStream_t st);

@@ -27,7 +27,7 @@ SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_set_theta", "ne_ctx_get_th
            "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_boxes", "ne_ctx_counters", "ne_last_error",
            "ne_create_crystal", "ne_create_crystal_ca", "ne_eam_energy_forces", "ne_eam_virial", "ne_eam_energy_forces_noalloc",
            "ne_spring_forces",
-           "ne_eam_backward", "ne_noise", "ne_init_velocities", "ne_langevin_step",
+           "ne_eam_backward", "ne_eam_backward_acc", "ne_noise", "ne_init_velocities", "ne_langevin_step",
            "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment",
            "ne_profile_segment", "ne_crystal_run_segment",
            "ne_msd_fit", "ne_free_energy", "ne_jarzynski",
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
                 "ne_eam_energy_forces_noalloc": [p, i, p, i, p, p, p, p],
                 "ne_spring_forces": [p, p, i, d, p, p, p],
                 "ne_eam_backward": [p, i, p, i, p, d, p, p, p],
+                "ne_eam_backward_acc": [p, i, p, i, p, d, p, p],
                 "ne_noise": [C.c_ulonglong, C.c_uint, i, ll, i, i, p, p],
                 "ne_init_velocities": [p, p, i, p, p],
                 "ne_langevin_step": [p, p, p, p, p, i, p, ll, d, d, p, p],
@@ -281,6 +282,13 @@ def ne_eam_backward(ctx, prec, x, box, gE, gx, gtheta, stream=None):
     _err(ctx, load().ne_eam_backward(ctx, int(prec), _dev(x, 3 * n), n, _box(box), float(gE),
                                      _dev(gx, 3 * n), _dev(gtheta), _stream(stream)),
          "ne_eam_backward")
+
+
+def ne_eam_backward_acc(ctx, prec, x, box, gE, gtheta_acc, stream=None):
+    """gtheta_acc += gE dU/dtheta at configuration x (device tensors)."""
+    n = x.shape[0]
+    _err(ctx, load().ne_eam_backward_acc(ctx, int(prec), _dev(x, 3 * n), n, _box(box), float(gE),
+                                         _dev(gtheta_acc), _stream(stream)), "ne_eam_backward_acc")
 
 
 def ne_noise(seed, replica, noise_stream, step, z, prec=NE_FP64, stream=None):

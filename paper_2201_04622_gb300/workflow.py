@@ -191,3 +191,50 @@ def rs_free_energy(lattice, a, n, T0, F0_T0_per_atom, lambda_f, t_s, Wcum_f, Wcu
     x0, _ = crystal_sites(lattice, a, n)
     nat = len(x0)
     return ne.ne_rs_free_energy(nat, T0, F0_T0_per_atom * nat, lambda_f, t_s, Wcum_f, Wcum_b, T_grid)
+
+
+
+def lambda_fl2(tau):
+    """Frenkel-Ladd switching function of Sec. III.B (function 2):
+    tau^5 (70 tau^4 - 315 tau^3 + 540 tau^2 - 420 tau + 126)."""
+    t = min(max(tau, 0.0), 1.0)
+    return t ** 5 * (70 * t ** 4 - 315 * t ** 3 + 540 * t ** 2 - 420 * t + 126)
+
+
+def theta_gradient(ctx, lattice, a, n, T, mass, k, t_eq, t_s, n_knots, seed=1, stride=10, prec=ne.NE_MIXED,
+                   skin=1.0, device="cuda"):
+    """Gradients with respect to the spline knots theta along one FL run
+    (equilibration at lambda = 0, then the forward switch of Sec. III.B),
+    with dU/dtheta from the backward pass (rho recomputed) every `stride`
+    steps:
+      dF_dtheta  -- <dU/dtheta> over the equilibration at lambda = 0, the
+                    free energy's parameter gradient dF_0/dtheta;
+      dWf_dtheta -- sum over the forward switch of dlambda dU/dtheta(x), the
+                    derivative of W_f at fixed trajectory (lambda increments
+                    over `stride` steps).
+    Returns (dF_dtheta, dWf_dtheta, samples at lambda = 0), the gradients as
+    numpy [3][n_knots][2] (phi, f, F; value and slope per knot)."""
+    import torch
+    x0_np, box = crystal_sites(lattice, a, n)
+    nat = len(x0_np)
+    md = ne.md_params(T=T, mass=mass, k_spring=k, skin=skin, prec=prec, t_eq=t_eq, t_s=t_s, seed=seed,
+                      replica=0, fix_cm=1)
+    x0 = torch.tensor(x0_np, dtype=torch.float64, device=device)
+    x, v = x0.clone(), torch.zeros_like(x0)
+    ne.ne_init_velocities(ctx, md, v)
+    Wd = torch.zeros((1, 2), dtype=torch.float64, device=device)
+    g_eq = torch.zeros(6 * n_knots, dtype=torch.float64, device=device)
+    g_sw = torch.zeros(6 * n_knots, dtype=torch.float64, device=device)
+    n_eq, s = 0, 0
+    while s < t_eq + t_s:
+        step = min(stride, t_eq + t_s - s)
+        ne.ne_switch_run_segment(ctx, [md], [0, nat], x, v, x0, [box], Wd, s, step)
+        s0, s = s, s + step
+        if s <= t_eq:
+            ne.ne_eam_backward_acc(ctx, prec, x, box, 1.0, g_eq)
+            n_eq += 1
+        else:
+            dl = lambda_fl2((s - t_eq) / t_s) - lambda_fl2(max(s0 - t_eq, 0) / t_s)
+            ne.ne_eam_backward_acc(ctx, prec, x, box, dl, g_sw)
+    shape = (3, n_knots, 2)
+    return (g_eq.cpu().numpy() / max(n_eq, 1)).reshape(shape), g_sw.cpu().numpy().reshape(shape), n_eq

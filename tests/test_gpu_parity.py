@@ -598,3 +598,51 @@ def test_zero_pressure_lattice_parameter(ctx):
                                    stride=20)
     assert pts[0][1] > 0 > pts[-1][1]
     assert 2.95 < a1 < 3.02
+
+
+def test_backward_accumulates_and_satisfies_the_euler_identity(ctx, pot):
+    """ne_eam_backward_acc adds gE dU/dtheta into its buffer; and since U is
+    linear in the phi and F knot parameters (U_pair and U_emb are linear
+    combinations of them through the Hermite basis), theta_phi . dU/dtheta_phi
+    + theta_F . dU/dtheta_F = U exactly (the f knots enter through rho)."""
+    p, th = pot
+    nk = W.EAM_FE_LIKE["n_knots"]
+    x0, box = crystal(O.BCC, 6)
+    x1, x2 = W.displaced(x0, 0.12, 21), W.displaced(x0, 0.15, 22)
+    theta = torch.zeros(6 * nk, dtype=torch.float64, device=DEV)
+    ne.ne_ctx_get_theta(ctx, theta)
+    th_np = N(theta).reshape(3, nk, 2)
+    g = []
+    for x in (x1, x2):
+        gt = torch.zeros(6 * nk, dtype=torch.float64, device=DEV)
+        ne.ne_eam_backward(ctx, ne.NE_FP64, T(x), box, 1.0, None, gt)
+        g.append(N(gt).reshape(3, nk, 2))
+        E, _, _ = gpu_eam(ctx, ne.NE_FP64, x, box)
+        euler = (th_np[0] * g[-1][0]).sum() + (th_np[2] * g[-1][2]).sum()
+        assert euler == pytest.approx(E, rel=1e-10)
+    acc = torch.zeros(6 * nk, dtype=torch.float64, device=DEV)
+    ne.ne_eam_backward_acc(ctx, ne.NE_FP64, T(x1), box, 0.3, acc)
+    ne.ne_eam_backward_acc(ctx, ne.NE_FP64, T(x2), box, 0.7, acc)
+    want = 0.3 * g[0] + 0.7 * g[1]
+    assert np.allclose(N(acc).reshape(3, nk, 2), want, rtol=1e-10, atol=1e-12 * np.abs(want).max())
+    accm = torch.zeros(6 * nk, dtype=torch.float64, device=DEV)
+    ne.ne_eam_backward_acc(ctx, ne.NE_MIXED, T(x1), box, 0.3, accm)
+    ne.ne_eam_backward_acc(ctx, ne.NE_MIXED, T(x2), box, 0.7, accm)
+    assert rel(N(accm), want.ravel()) < 1e-3
+
+
+def test_theta_gradient_workflow(ctx):
+    """<dU/dtheta> at lambda = 0 along an FL run: its Euler sum is the mean
+    EAM energy of the sampled configurations, a cohesive energy per atom near
+    -4.2 eV; the switch term is finite."""
+    from paper_2201_04622_gb300 import workflow as WF
+    nk = W.EAM_FE_LIKE["n_knots"]
+    dF, dW, m = WF.theta_gradient(ctx, O.BCC, W.A_BCC, 6, 300.0, MASS, 4.0, 200, 100, nk, stride=20,
+                                  prec=ne.NE_FP64)
+    assert m == 10
+    theta = torch.zeros(6 * nk, dtype=torch.float64, device=DEV)
+    ne.ne_ctx_get_theta(ctx, theta)
+    th_np = N(theta).reshape(3, nk, 2)
+    u = ((th_np[0] * dF[0]).sum() + (th_np[2] * dF[2]).sum()) / 432
+    assert -4.35 < u < -4.1
+    assert np.all(np.isfinite(dW)) and np.abs(dW).max() > 0
