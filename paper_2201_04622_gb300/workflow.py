@@ -36,10 +36,21 @@ def fl_batch(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec=ne.NE_MIXED, run
     """Forward and backward FL works of a batch of crystal replicas.
 
     crystals: list of (lattice, a, n) per replica; ks, seeds: per replica.
-    runner: "crystal" (persistent cluster runner, mixed precision) or
-    "general" (multi-kernel path, FP64 or mixed).  Returns (W_f, W_b) numpy
-    arrays and the final positions."""
+    runner: "crystal" (persistent cluster runner, mixed precision),
+    "general" (multi-kernel path, FP64 or mixed), or "auto": the crystal
+    runner, and the general mixed path from the same start if an atom strays
+    beyond the runner's stencil range (NE_ERANGE; soft springs at high T).
+    Returns (W_f, W_b) numpy arrays and the final positions."""
     import torch
+    if runner == "auto":
+        try:
+            return fl_batch(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec, "crystal", skin, device, chunk)
+        except ne.NeError as e:
+            if "NE_ERANGE" not in str(e):
+                raise
+            import warnings
+            warnings.warn("crystal runner out of its stencil range; rerunning on the multi-kernel path")
+            return fl_batch(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec, "general", skin, device, chunk)
     x0s, offs, boxes, mds, crs = [], [0], [], [], []
     for r, ((lat, a, n), k, seed) in enumerate(zip(crystals, ks, seeds)):
         x0, box = crystal_sites(lat, a, n)
