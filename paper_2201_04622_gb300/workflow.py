@@ -35,7 +35,8 @@ def fl_batch(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec=ne.NE_MIXED, run
              skin=2.6, device="cuda", chunk=None):
     """Forward and backward FL works of a batch of crystal replicas.
 
-    crystals: list of (lattice, a, n) per replica; ks, seeds: per replica.
+    crystals: list of (lattice, a, n) per replica; ks, seeds: per replica;
+    T: one temperature or one per replica.
     runner: "crystal" (persistent cluster runner, mixed precision),
     "general" (multi-kernel path, FP64 or mixed), or "auto": the crystal
     runner, and the general mixed path from the same start if an atom strays
@@ -52,13 +53,14 @@ def fl_batch(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec=ne.NE_MIXED, run
             warnings.warn("crystal runner out of its stencil range; rerunning on the multi-kernel path")
             return fl_batch(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec, "general", skin, device, chunk)
     x0s, offs, boxes, mds, crs = [], [0], [], [], []
-    for r, ((lat, a, n), k, seed) in enumerate(zip(crystals, ks, seeds)):
+    Ts = list(T) if np.ndim(T) else [T] * len(crystals)
+    for r, ((lat, a, n), k, seed, Tr) in enumerate(zip(crystals, ks, seeds, Ts)):
         x0, box = crystal_sites(lat, a, n)
         x0s.append(x0)
         offs.append(offs[-1] + len(x0))
         boxes.append(box)
         crs.append((lat, a, n, n, n))
-        mds.append(ne.md_params(T=T, mass=mass, k_spring=k, skin=skin, prec=prec, t_eq=t_eq, t_s=t_s,
+        mds.append(ne.md_params(T=Tr, mass=mass, k_spring=k, skin=skin, prec=prec, t_eq=t_eq, t_s=t_s,
                                 seed=seed, replica=r, fix_cm=1))
     x0 = torch.tensor(np.concatenate(x0s), dtype=torch.float64, device=device)
     x, v = x0.clone(), torch.zeros_like(x0)

@@ -216,3 +216,18 @@ def test_size_scaling_workflow(ctx):
                                            runner="crystal")
     assert [r["atoms"] for r in rows] == [250, 432]
     assert all(np.isfinite([r["F"] for r in rows])) and np.isfinite(F_inf)
+
+
+def test_fl_batch_auto_falls_back_when_atoms_leave_the_stencil(ctx):
+    """Soft springs at high T in a small box (stencil range D = 0.94 A;
+    Einstein amplitude sqrt(kT/k) = 0.28 A per component, so some atom
+    leaves the range while pairs stay far from overlap): the crystal runner
+    reports NE_ERANGE; runner='auto' reruns the batch on the multi-kernel
+    path and returns finite works."""
+    from paper_2201_04622_gb300 import workflow as WF
+    args = (ctx, [(O.BCC, W.A_BCC, 5)] * 2, 1400.0, [1.5, 1.5], [1, 2], 200, 400, MASS)
+    with pytest.raises(ne.NeError, match="NE_ERANGE"):
+        WF.fl_batch(*args, runner="crystal", skin=1.0)
+    with pytest.warns(UserWarning):
+        Wf, Wb, _ = WF.fl_batch(*args, runner="auto", skin=1.0)
+    assert np.all(np.isfinite(Wf)) and np.all(np.isfinite(Wb))
