@@ -311,7 +311,8 @@ def run_ours(args):
            "config": {"workload": WORKLOADS[args.workload], "replicas": n_rep, "atoms": n_atoms,
                       "T_K": T_K if args.workload == "fl2" else "300-1600",
                       "t_eq": T_EQ, "t_s": T_S, "dt_fs": 1.0, "skin_A": SKIN,
-                      "precision": args.prec, "path": path, "threads_per_atom": args.tpa,
+                      "precision": args.prec, "path": path,
+                      "threads_per_atom": 2 if path == "crystal" else args.tpa,
                       "autotune": tuned,
                       "list_builds_per_replica_step": list_builds / (K * n_rep),
                       "parallelism": "replicas only" if world > 1 else "1 GPU",

@@ -63,10 +63,13 @@ constexpr int NKT = 256;
 constexpr int NWARP = THREADS / 32;
 
 // partial sums broadcast at the end of step s for step s+1: the energies
-// (double-float within a CTA), then sum u and sum xi for the mean removal (FP32
-// within a CTA); all in FP64 across the cluster
+// (double-float), then sum u and sum xi for the mean removal (FP32)
 enum { P_U0 = 0, P_UE, P_UX, P_UY, P_UZ, P_XX, P_XY, P_XZ, NP_ };
 constexpr int ND_ = 2, NF_ = NP_ - ND_;
+// floats per CTA partial (and in the replica totals): (hi, lo) of each energy,
+// then the FP32 sums; T_UX, T_XX: where sum u and sum xi start
+constexpr int NSV = 2 * ND_ + NF_;
+constexpr int T_UX = 2 * ND_ + (P_UX - ND_), T_XX = 2 * ND_ + (P_XX - ND_);
 // values per warp in the reduction scratch: the larger of the two reductions
 constexpr int NRED = (int)NP_ + 1;  // sums and one maximum
 
@@ -99,16 +102,18 @@ __device__ __forceinline__ void warp_df_sum(dfl (&v)[NV])
 
 // CTA sums of ND double-float and NF FP32 values and the maximum of mx,
 // written into slot `rank` of the slot arrays of every CTA of the cluster:
-// sums to dst[rank * (ND + NF) + q] (FP64), the maximum to mslot[rank]
-// (FP32).  The warps' partials are combined in fixed order, the double-float
-// ones in double-float (FP32 arithmetic), and converted to FP64 once.  One
-// __syncthreads; the caller separates two uses of s_red by a cluster barrier.
+// dst[rank * NSV + ...] gets (hi, lo) of each double-float sum, then the FP32
+// sums; mslot[rank] the maximum.  Each warp reduces its lanes; then warp q
+// combines quantity q over the warps with a shuffle tree (a fixed order) and
+// its lanes r < C store it into CTA r.  One __syncthreads; the caller
+// separates two uses of s_red by a cluster barrier.
 template <int ND, int NF>
 __device__ __forceinline__ void cta_sum_bcast(cg::cluster_group& cluster, dfl (&vd)[ND], float (&vf)[NF], float mx,
-                                              float* s_red, double* dst, float* mslot, int rank, int C, int nwarp)
+                                              float* s_red, float* dst, float* mslot, int rank, int C, int nwarp)
 {
     constexpr int NV = ND + NF;
-    static_assert(NV + 1 <= NRED, "reduction scratch too small");
+    static_assert(NV + 1 <= NRED && NV + 1 <= NWARP, "reduction scratch too small");
+    static_assert(2 * ND + NF == NSV, "slot layout");
     // only the first nwarp warps hold values (the threads that own atoms)
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (w < nwarp) {
@@ -129,27 +134,29 @@ __device__ __forceinline__ void cta_sum_bcast(cg::cluster_group& cluster, dfl (&
         }
     }
     __syncthreads();
-    if (threadIdx.x <= NV) {
-        const int q = threadIdx.x;
-        if (q < NV) {
-            double d;
-            if (q < ND) {
-                dfl acc = {0.f, 0.f};
-                for (int ww = 0; ww < nwarp; ++ww)
-                    acc = df_add(acc, {s_red[(ww * NRED + q) * 2], s_red[(ww * NRED + q) * 2 + 1]});
-                d = (double)acc.hi + (double)acc.lo;
-            } else {
-                float acc = 0.f;
-                for (int ww = 0; ww < nwarp; ++ww) acc += s_red[(ww * NRED + q) * 2];
-                d = (double)acc;
+    if (w <= NV) {  // warp-uniform: warp q handles quantity q, lane l holds warp l's partial
+        const int q = w;
+        const bool has = l < nwarp;
+        if (q < ND) {
+            dfl v = has ? dfl{s_red[(l * NRED + q) * 2], s_red[(l * NRED + q) * 2 + 1]} : dfl{0.f, 0.f};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                v = df_add(v, {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+            if (l < C) {
+                float* d = cluster.map_shared_rank(dst, l) + rank * NSV + 2 * q;
+                d[0] = v.hi;
+                d[1] = v.lo;
             }
-            dst[rank * NV + q] = d;
-            for (int r = 1; r < C; ++r) cluster.map_shared_rank(dst, (rank + r) % C)[rank * NV + q] = d;
+        } else if (q < NV) {
+            float v = has ? s_red[(l * NRED + q) * 2] : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (l < C) cluster.map_shared_rank(dst, l)[rank * NSV + ND + q] = v;
         } else {
-            float m = 0.f;
-            for (int ww = 0; ww < nwarp; ++ww) m = fmaxf(m, s_red[(ww * NRED + q) * 2]);
-            mslot[rank] = m;
-            for (int r = 1; r < C; ++r) cluster.map_shared_rank(mslot, (rank + r) % C)[rank] = m;
+            float m = has ? s_red[(l * NRED + NV) * 2] : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (l < C) cluster.map_shared_rank(mslot, l)[rank] = m;
         }
     }
 }
@@ -200,6 +207,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int C = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
     const int rep = blockIdx.x / C;
+    auto peer = [&](int r) { return rank + r < C ? rank + r : rank + r - C; };  // (rank + r) mod C, 0 < r < C
     const int n = reps[rep].n, nb = reps[rep].nb, nx = reps[rep].nx, ny = reps[rep].ny, nz = reps[rep].nz;
     const int nst = reps[rep].st_cnt, M = reps[rep].st_margin;
     const int A_c = atoms_per_cta(n, C, nb);
@@ -218,11 +226,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     // short list: entry q of thread (slot, lane) at [q][lane][slot], holding
     // k / TPA of its stencil entry k (k = TPA * entry + lane)
     unsigned char* s_sl = (unsigned char*)(s_K + 4 * NKT);      // [SLQ][TPA][SLOTS]
-    double* s_slotP = (double*)(((size_t)(s_sl + SLOTS * SLMAX) + 15) & ~(size_t)15);  // [2][16][NP_]
-    double* s_tot = s_slotP + 2 * 16 * NP_;                       // [NP_ + 1]
+    float* s_slotP = (float*)(((size_t)(s_sl + SLOTS * SLMAX) + 15) & ~(size_t)15);  // [2][16][NSV]
+    float* s_tot = s_slotP + 2 * 16 * NSV;                        // [NSV] replica totals
     // partial force, pair energy and rho of the second pair lane of each slot
     // (the first lane is the owning thread and keeps its part in registers)
-    float4* s_f = (float4*)(((size_t)(s_tot + NP_ + 1) + 15) & ~(size_t)15);  // [SLOTS]
+    float4* s_f = (float4*)(((size_t)(s_tot + NSV) + 15) & ~(size_t)15);  // [SLOTS]
     float2* s_rho = (float2*)(s_f + SLOTS);                       // [SLOTS] double-float
     float* s_slotM = (float*)(s_rho + SLOTS);                     // [2][16] max |u| per CTA
     float* s_red = s_slotM + 32;                                  // [NWARP][NRED][2]
@@ -320,7 +328,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
             s_u[tsu] = uv;
-            for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, (rank + r) % C)[tsu] = uv;
+            for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, peer(r))[tsu] = uv;
             ne_normals32(ne_philox_block(reps[rep].seed, reps[rep].replica, (unsigned)S.stream, (unsigned)ta,
                                          (unsigned long long)s_begin),
                          xi);
@@ -332,7 +340,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             um = sqrtf(u2);
         }
-        cta_sum_bcast<ND_, NF_>(cluster, pd, pf, um, s_red, s_slotP + (s_begin & 1) * 16 * NP_,
+        cta_sum_bcast<ND_, NF_>(cluster, pd, pf, um, s_red, s_slotP + (s_begin & 1) * 16 * NSV,
                                 s_slotM + (s_begin & 1) * 16, rank, C, own_warps);
     }
 
@@ -342,7 +350,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const float dt = (float)S.dt;
     const float rho_maxf = (float)tab.rho_max;
     const float ihr_hi = (float)tab.inv_h_rho, ihr_lo = (float)(tab.inv_h_rho - (double)ihr_hi);
-    double UE_prev = 0.0;  // rank 0, thread 0: U_E at the positions of the previous step
+    double UE_prev = 0.0;  // rank 0, thread SLOTS: U_E at the positions of the previous step
 
 #pragma unroll 1
     for (long long it = 0; it <= n_steps; ++it) {
@@ -350,37 +358,36 @@ __global__ void __launch_bounds__(THREADS, 1)
         const bool fin = it == n_steps;
         cluster.sync();  // u of step s and the partial sums for step s visible everywhere
 
-        // ---------------- replica sums for step s (fixed order over the CTAs)
-        if (threadIdx.x <= NP_) {
-            const int q = threadIdx.x;
-            if (q < NP_) {
-                const double* sp = s_slotP + (s & 1) * 16 * NP_;
-                double acc = 0.0;
-                for (int r = 0; r < C; ++r) acc += sp[r * NP_ + q];
-                s_tot[q] = acc;
-            } else {
-                const float* sm = s_slotM + (s & 1) * 16;
-                float um = 0.f;
-                for (int r = 0; r < C; ++r) um = fmaxf(um, sm[r]);
-                s_misc[0] = um;
-                if (um > reps[rep].D) ne_set_status(status, ST_ERANGE);
+        // ---------------- replica sums for step s: warp q < NP_ sums quantity q
+        // over the CTAs (lane r holds CTA r; a fixed shuffle tree, C <= 16),
+        // the energies in double-float, the sums for the mean removal in FP32.
+        // They are read after the next __syncthreads.  max |u| is needed at
+        // once, so every warp forms it itself.
+        float umax;
+        {
+            const int q = threadIdx.x >> 5, r = threadIdx.x & 31;
+            const float* sp = s_slotP + (s & 1) * 16 * NSV;
+            if (q < ND_) {
+                dfl acc = r < C ? dfl{sp[r * NSV + 2 * q], sp[r * NSV + 2 * q + 1]} : dfl{0.f, 0.f};
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1)
+                    acc = df_add(acc, {__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)});
+                if (r == 0) {
+                    s_tot[2 * q] = acc.hi;
+                    s_tot[2 * q + 1] = acc.lo;
+                }
+            } else if (q < NP_) {
+                float acc = r < C ? sp[r * NSV + ND_ + q] : 0.f;
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (r == 0) s_tot[ND_ + q] = acc;
             }
+            float um = r < C ? s_slotM[(s & 1) * 16 + r] : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
+            umax = um;
+            if (threadIdx.x == 0 && um > reps[rep].D) ne_set_status(status, ST_ERANGE);
         }
-        __syncthreads();
-        if (rank == 0 && threadIdx.x == 0) {
-            // work increment of step s - 1: (lambda_s - lambda_{s-1}) dH/dlambda(x_{s-1})
-            if (it > 0) {
-                const long long sp = s - 1;
-                const double U0 = s_tot[P_U0];
-                const double g = S.path == 0 ? U0 - UE_prev : U0;
-                int wslot = -1;
-                if (sp >= S.t_eq && sp < S.t_eq + S.t_s) wslot = 0;
-                else if (sp >= 2 * S.t_eq + S.t_s && sp < 2 * S.t_eq + 2 * S.t_s) wslot = 1;
-                if (wslot >= 0) Wg[2 * reps[rep].widx + wslot] += (lam_tab[it] - lam_tab[it - 1]) * g;
-            }
-            UE_prev = s_tot[P_UE];
-        }
-        const float umax = s_misc[0];
 
         // ---------------- pass 1: density, pair forces and energy, short list
         // (pair threads); the F'(rho) terms of the forces follow in pass 2
@@ -410,13 +417,21 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const float t = r2 * ir * inv_h;  // r / h >= 0
                     const int kk = min((int)t, nk - 2);
                     const float w = t - (float)kk;
+                    // intervals below the shared-memory window (r < ~1 A at
+                    // these sizes) come from global memory; the warp votes, so
+                    // the common case is a plain shared-memory gather
                     float4 c, g;
-                    if (kk >= k_lo) {
+                    if (__any_sync(__activemask(), kk < k_lo)) {
+                        if (kk >= k_lo) {
+                            c = s_tabP[kk - k_lo];
+                            g = s_tabF[kk - k_lo];
+                        } else {
+                            c = __ldg(&tab.pf32[2 * kk]);
+                            g = __ldg(&tab.pf32[2 * kk + 1]);
+                        }
+                    } else {
                         c = s_tabP[kk - k_lo];
                         g = s_tabF[kk - k_lo];
-                    } else {
-                        c = __ldg(&tab.pf32[2 * kk]);
-                        g = __ldg(&tab.pf32[2 * kk + 1]);
                     }
                     rho = df_add(rho, {g.x + w * (g.y + w * (g.z + w * g.w)), 0.f});
                     // phi and dphi/dw together (Horner with derivative)
@@ -458,7 +473,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             emb = c.x + w * (c.y + w * (c.z + w * c.w));
             const float dF = (c.y + w * (2.f * c.z + 3.f * w * c.w)) * tab.inv_h_rhof;
             s_u[tsu].w = dF;
-            for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, (rank + r) % C)[tsu].w = dF;
+            for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, peer(r))[tsu].w = dF;
             if (!isfinite(emb)) bad |= ST_ENAN;
         }
         cluster.sync();  // F' visible everywhere
@@ -497,6 +512,21 @@ __global__ void __launch_bounds__(THREADS, 1)
         // step s + 1 into the other CTAs, which by then have all finished
         // reading step s too (the integration hides the barrier's latency).
         asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        if (rank == 0 && threadIdx.x == SLOTS) {
+            // work increment of step s - 1, (lambda_s - lambda_{s-1}) dH/dlambda(x_{s-1}),
+            // by a thread that owns no atom (s_tot holds the sums of step s
+            // until the next cluster barrier)
+            const double U0 = (double)s_tot[2 * P_U0] + (double)s_tot[2 * P_U0 + 1];
+            if (it > 0) {
+                const long long sp = s - 1;
+                const double g = S.path == 0 ? U0 - UE_prev : U0;
+                int wslot = -1;
+                if (sp >= S.t_eq && sp < S.t_eq + S.t_s) wslot = 0;
+                else if (sp >= 2 * S.t_eq + S.t_s && sp < 2 * S.t_eq + 2 * S.t_s) wslot = 1;
+                if (wslot >= 0) Wg[2 * reps[rep].widx + wslot] += (lam_tab[it] - lam_tab[it - 1]) * g;
+            }
+            UE_prev = (double)s_tot[2 * P_UE] + (double)s_tot[2 * P_UE + 1];
+        }
         {
             dfl pd[ND_] = {};
             float pf[NF_] = {};
@@ -509,8 +539,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const float invN = 1.f / (float)n;
                 float mFE[3], mxi[3];
                 for (int c = 0; c < 3; ++c) {
-                    mFE[c] = S.fix_cm ? -kf * (float)s_tot[P_UX + c] * invN : 0.f;
-                    mxi[c] = S.fix_cm ? (float)s_tot[P_XX + c] * invN : 0.f;
+                    mFE[c] = S.fix_cm ? -kf * s_tot[T_UX + c] * invN : 0.f;
+                    mxi[c] = S.fix_cm ? s_tot[T_XX + c] * invN : 0.f;
                 }
                 const float ls = (float)lam_tab[it], ln = (float)lam_tab[it + 1];
                 if (it > 0)
@@ -537,7 +567,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (!fin) {
                     const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
                     s_u[tsu] = uv;
-                    for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, (rank + r) % C)[tsu] = uv;
+                    for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, peer(r))[tsu] = uv;
                 }
                 const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
                 pd[P_UE] = {0.5f * kf * u2, 0.f};
@@ -550,7 +580,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (!isfinite(v[c])) bad |= ST_ENAN;
             }
             if (!fin)
-                cta_sum_bcast<ND_, NF_>(cluster, pd, pf, un, s_red, s_slotP + ((s + 1) & 1) * 16 * NP_,
+                cta_sum_bcast<ND_, NF_>(cluster, pd, pf, un, s_red, s_slotP + ((s + 1) & 1) * 16 * NSV,
                                         s_slotM + ((s + 1) & 1) * 16, rank, C, own_warps);
         }
     }
@@ -583,7 +613,7 @@ size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
     size_t b = sizeof(float4) * (size_t)n_max + (sizeof(float4) + sizeof(float)) * (size_t)nb_nst_max +
                sizeof(int) * (size_t)lut_max + sizeof(unsigned short) * 4 * NKT + sizeof(unsigned char) * SLOTS * SLMAX;
     b = (b + 15) & ~(size_t)15;
-    b += sizeof(double) * (2 * 16 * NP_ + NP_ + 1);
+    b += sizeof(float) * (2 * 16 * NSV + NSV);
     b += 16;  // alignment of s_f
     b += sizeof(float4) * SLOTS + sizeof(float2) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2 + 8);
     return ((b + 15) & ~(size_t)15) + 16;  // + alignment of the tables
@@ -604,8 +634,10 @@ int cluster_atoms_for(int n, int C, int nb) { return atoms_per_cta(n, C, nb); }
 int cluster_max_active(int C, size_t smem)
 {
     if (cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        (C > 8 && cudaFuncSetAttribute(k_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess))
+        (C > 8 && cudaFuncSetAttribute(k_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+        (void)cudaGetLastError();  // not a launch error: clear it, the caller reports 0 clusters
         return 0;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
     cfg.blockDim = dim3(THREADS, 1, 1);

@@ -44,7 +44,7 @@ enum { PB_UE = 0, PB_UX, PB_UY, PB_UZ, PB_U2, PB_KE, NPB };
 // per-replica totals
 enum { TOT_UEMB = 0, TOT_UPAIR, TOT_F0X, TOT_F0Y, TOT_F0Z, TOT_XIX, TOT_XIY, TOT_XIZ, TOT_VIR,
        TOT_UE, TOT_UX, TOT_UY, TOT_UZ, TOT_U2, TOT_KE, NTOT };
-static_assert(TOT_VIR == PA_VIR && TOT_UE == NPA, "totals: pass-2 partials first, then the step's");
+static_assert((int)TOT_VIR == (int)PA_VIR && (int)TOT_UE == (int)NPA, "totals: pass-2 partials first, then the step's");
 
 struct RepDev {
     double L[3], invL[3];
