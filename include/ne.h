@@ -141,10 +141,12 @@ ne_status ne_ctx_boxes(ne_ctx* ctx, int n_rep, double* boxes_host);
  * (one at the start of every run or segment, plus one each time an atom
  * strays more than skin/2 from its list-build position); stencil_visits and
  * pairs -- lattice-stencil entries examined and pairs found inside r_c by
- * ne_crystal_run_segment (pass 1), for algorithmic operation counts.
+ * ne_crystal_run_segment (pass 1), for algorithmic operation counts;
+ * crystal_launches -- kernels launched by ne_crystal_run_segment (one lambda
+ * table and one cluster kernel per replica size class a call).
  * Synchronises the device. */
 ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds, long long* stencil_visits,
-                          long long* pairs);
+                          long long* pairs, long long* crystal_launches);
 
 /* Status bits recorded by the last call, and its message (msg may be NULL). */
 ne_status ne_last_error(ne_ctx* ctx, int* device_status, char* msg, int msg_len);
@@ -324,12 +326,21 @@ typedef struct {
  * advanced in place; W_dev [n_rep][2] accumulates (forward, backward) work.
  * md[r].prec must be NE_MIXED; at most 4096 atoms per replica, at least 3
  * cells per axis and box edges > 2 r_c + 1.2 A.  Neighbours come from a
- * lattice stencil covering displacements up to D = min(2 A, (L/2 - r_c)/2)
- * from the sites; a replica whose atoms stray further is reported as
- * NE_ERANGE.  Noise, work and schedule are those of ne_switch_run_segment. */
+ * lattice stencil covering displacements up to D = 2 A from the sites (in a
+ * small box it holds two periodic images of some sites, at most one of them
+ * within r_c); a replica whose atoms stray further is reported as NE_ERANGE.  Noise, work and schedule are those of ne_switch_run_segment. */
 ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep,
                                  double* x_dev, double* v_dev, double* W_dev, long long step_begin,
                                  long long n_steps, void* stream);
+
+/* Outcome per replica of the last ne_crystal_run_segment call that launched
+ * (bookkeeping; the paper has no counterpart): out_host[r] (host, n_rep ints)
+ * = NE_OK or the error replica r raised (NE_ENAN, NE_ERANGE, ...).  A replica
+ * that left the runner's range (a hop or melting at high T) can then be rerun
+ * alone on the multi-kernel path while the others keep their results: each
+ * replica's trajectory depends only on its own inputs and noise stream.
+ * NE_EINVAL if n_rep differs from that call's.  Synchronises the device. */
+ne_status ne_ctx_replica_status(ne_ctx* ctx, int n_rep, int* out_host);
 
 /* Timing hook (autotuning and roofline reports): the steps of
  * ne_switch_run_segment launched one by one, with CUDA events on the

@@ -33,6 +33,7 @@ struct ne_ctx {
     int max_atoms = 0, max_rep = 0, tiles_cap = 0, cells_cap = 0, tpa = 4;
     int cluster_c = 0;  // crystal runner: CTAs per cluster (0: chosen per batch)
     int last_nrep = 0;  // replicas of the last multi-kernel run (ne_ctx_boxes)
+    int last_nrep_cr = 0;  // replicas of the last crystal-runner call (ne_ctx_replica_status)
     double* theta = nullptr;
     float4* pf32 = nullptr;
     ned4* pf64 = nullptr;
@@ -46,6 +47,7 @@ struct ne_ctx {
     double *partA = nullptr, *partB = nullptr, *tot = nullptr, *W = nullptr, *scratch = nullptr;
     unsigned* tile_done = nullptr;
     int *flags = nullptr, *building = nullptr, *status = nullptr, *tile_rep = nullptr;
+    int* rep_status = nullptr;  // crystal runner: status bits per replica of the last call
     RepDev* rep = nullptr;
     long long* step_ctr = nullptr;
     unsigned long long* rebuilds = nullptr;
@@ -62,6 +64,7 @@ struct ne_ctx {
     std::vector<RepDev> rep_h;
     std::vector<int> tile_rep_h;
     int last_bits = 0;
+    long long cr_launches = 0;  // kernels launched by ne_crystal_run_segment
     std::string msg;
     Tables tab{};
 };
@@ -526,6 +529,7 @@ ne_status ne_ctx_create(const ne_eam_params* eam, int max_atoms, int max_replica
     A(dalloc(&ctx->flags, R));
     A(dalloc(&ctx->building, R));
     A(dalloc(&ctx->status, 1));
+    A(dalloc(&ctx->rep_status, R));
     A(dalloc(&ctx->tile_rep, (size_t)ctx->tiles_cap));
     A(dalloc(&ctx->rep, R));
     A(dalloc(&ctx->step_ctr, 1));
@@ -564,7 +568,7 @@ ne_status ne_ctx_destroy(ne_ctx* ctx)
                     ctx->pbuild, ctx->f32, ctx->f64, ctx->dF64, ctx->rho, ctx->xi64, ctx->xi32,
                     ctx->nbr, ctx->ncnt, ctx->sl, ctx->scnt, ctx->cellof, ctx->sorted, ctx->cstart,
                     ctx->cfill, ctx->partA, ctx->partB, ctx->tot, ctx->W, ctx->scratch,
-                    ctx->tile_done, ctx->flags, ctx->building, ctx->status, ctx->tile_rep, ctx->rep, ctx->step_ctr, ctx->rebuilds, ctx->xrep, ctx->work, ctx->st_vec, ctx->st_dist, ctx->lam_tab,
+                    ctx->tile_done, ctx->flags, ctx->building, ctx->status, ctx->rep_status, ctx->tile_rep, ctx->rep, ctx->step_ctr, ctx->rebuilds, ctx->xrep, ctx->work, ctx->st_vec, ctx->st_dist, ctx->lam_tab,
                     ctx->bins};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -624,7 +628,23 @@ ne_status ne_ctx_boxes(ne_ctx* ctx, int n_rep, double* boxes_host)
     return NE_OK;
 }
 
-ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds, long long* stencil_visits, long long* pairs)
+ne_status ne_ctx_replica_status(ne_ctx* ctx, int n_rep, int* out_host)
+{
+    if (!ctx || !out_host || n_rep < 1) return NE_EINVAL;
+    if (n_rep != ctx->last_nrep_cr) return fail(ctx, NE_EINVAL, "replica count differs from the last crystal-runner call");
+    std::vector<int> bits(n_rep);
+    if (cudaMemcpy(bits.data(), ctx->rep_status, sizeof(int) * n_rep, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(ctx, NE_ECUDA, "reading the replica status failed");
+    for (int r = 0; r < n_rep; ++r) {
+        const int b = bits[r];
+        out_host[r] = (b & ST_ENAN) ? NE_ENAN : (b & ST_ERANGE) ? NE_ERANGE : (b & ST_ENEIGH) ? NE_ENEIGH
+                    : (b & ST_ETIMEOUT) ? NE_ETIMEOUT : NE_OK;
+    }
+    return NE_OK;
+}
+
+ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds, long long* stencil_visits, long long* pairs,
+                          long long* crystal_launches)
 {
     if (!ctx) return NE_EINVAL;
     unsigned long long v[3] = {0, 0, 0};
@@ -634,6 +654,7 @@ ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds, long long* stenci
     if (list_builds) *list_builds = (long long)v[0];
     if (stencil_visits) *stencil_visits = (long long)v[1];
     if (pairs) *pairs = (long long)v[2];
+    if (crystal_launches) *crystal_launches = ctx->cr_launches;
     return NE_OK;
 }
 
@@ -1075,10 +1096,14 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         X.seed = m.seed;
         X.replica = m.replica;
         if (m.replica >= (1u << 28)) return fail(ctx, NE_EINVAL, "replica id must be < 2^28");
-        // stencil: sites within r_c + 2D of each basis site, sorted by distance
+        // stencil: sites within r_c + 2D of each basis site, sorted by distance,
+        // D = 2 A.  In a small box r_c + 2D can pass L/2 and the stencil then
+        // holds two periodic images of some sites; two images are L > 2 r_c
+        // apart, so at most one of them lies within r_c and every pair inside
+        // the cutoff is still counted exactly once.
         const double Lmin = std::min(X.cell[0] * X.nx, std::min(X.cell[1] * X.ny, X.cell[2] * X.nz));
-        const double D = std::min(2.0, 0.5 * (0.5 * Lmin - rc) - 1e-3);
-        if (D < 0.3) return fail(ctx, NE_EINVAL, "box too small for the crystal runner (needs L/2 > r_c + 0.6 A)");
+        if (0.5 * Lmin - rc < 0.6) return fail(ctx, NE_EINVAL, "box too small for the crystal runner (needs L/2 > r_c + 0.6 A)");
+        const double D = 2.0;
         X.D = (float)D;
         const double Rst = rc + 2.0 * D;
         const int M = (int)std::ceil(Rst / std::min(X.cell[0], std::min(X.cell[1], X.cell[2]))) + 1;
@@ -1209,6 +1234,8 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
     NE_CU(cudaMemcpyAsync(ctx->st_vec, sv.data(), sizeof(float4) * sv.size(), cudaMemcpyHostToDevice, st));
     NE_CU(cudaMemcpyAsync(ctx->st_dist, sd.data(), sizeof(float) * sd.size(), cudaMemcpyHostToDevice, st));
     NE_CU(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
+    NE_CU(cudaMemsetAsync(ctx->rep_status, 0, sizeof(int) * n_rep, st));
+    ctx->last_nrep_cr = n_rep;
     Sched S = make_sched(md[0]);
     if (n_steps + 2 > ctx->lam_cap) {
         if (ctx->lam_tab) {
@@ -1221,6 +1248,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         ctx->lam_cap = n_steps + 2;
     }
     NE_CU(ne::launch_lambda_table(S, step_begin, n_steps + 2, ctx->lam_tab, st));
+    ++ctx->cr_launches;
     // groups
     std::vector<std::pair<int, int>> groups;  // [begin, end) in xs
     for (int q = 0; q < n_rep;) {
@@ -1248,8 +1276,10 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         cudaStream_t gs = multi ? ctx->gst[g] : st;
         if (multi) NE_CU(cudaStreamWaitEvent(gs, ctx->gev[16], 0));
         NE_CU(ne::launch_cluster(ctx->xrep + b, e - b, csize(order[b]), smem, ctx->st_vec, ctx->st_dist, x_dev, v_dev,
-                                 W_dev, ctx->status, S, step_begin, n_steps, ctx->tab, ctx->work, k_lo, ctx->lam_tab,
+                                 W_dev, ctx->status, ctx->rep_status, S, step_begin, n_steps, ctx->tab, ctx->work, k_lo,
+                                 ctx->lam_tab,
                                  gs));
+        ++ctx->cr_launches;
         if (multi) {
             NE_CU(cudaEventRecord(ctx->gev[g], gs));
             NE_CU(cudaStreamWaitEvent(st, ctx->gev[g], 0));

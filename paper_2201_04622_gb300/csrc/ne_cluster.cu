@@ -10,7 +10,7 @@
 // atom i, the sites j with |r0_j - r0_i| < r_c + 2D sorted by that distance,
 // so r_ij = (r0_j - r0_i) + u_j - u_i needs no minimum image and no list, and
 // a pair can lie inside r_c only if |r0_j - r0_i| < r_c + |u_i| + max_j |u_j|
-// -- the loop over the stencil stops there.  D (<= 2 A) is the largest
+// -- the loop over the stencil stops there.  D (2 A) is the largest
 // displacement from a site the stencil covers; a replica whose atoms stray
 // further is reported (NE_ERANGE) -- the crystal has melted.
 //
@@ -198,7 +198,7 @@ __host__ __device__ inline int atoms_per_cta(int n, int C, int nb)
 
 __global__ void __launch_bounds__(THREADS, 1)
     k_cluster(const XRep* __restrict__ reps, const float4* __restrict__ st_vec, const float* __restrict__ st_dist,
-              double* __restrict__ xg, double* __restrict__ vg, double* __restrict__ Wg, int* status, Sched S,
+              double* __restrict__ xg, double* __restrict__ vg, double* __restrict__ Wg, int* status, int* rep_status, Sched S,
               long long s_begin, long long n_steps, Tables tab, unsigned long long* work, int k_lo,
               const double* __restrict__ lam_tab)
 {
@@ -386,7 +386,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
             umax = um;
-            if (threadIdx.x == 0 && um > reps[rep].D) ne_set_status(status, ST_ERANGE);
+            if (threadIdx.x == 0 && um > reps[rep].D) {
+                ne_set_status(status, ST_ERANGE);
+                ne_set_status(rep_status + reps[rep].widx, ST_ERANGE);
+            }
         }
 
         // ---------------- pass 1: density, pair forces and energy, short list
@@ -589,7 +592,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             xg[gi + c] = (double)(xr[c] + site_fix(c)) / XSCALE;
             vg[gi + c] = (double)v[c];
         }
-    if (bad) ne_set_status(status, bad);
+    if (bad) {
+        ne_set_status(status, bad);
+        ne_set_status(rep_status + reps[rep].widx, bad);
+    }
     if (work) {
         for (int o = 16; o > 0; o >>= 1) {
             n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
@@ -664,7 +670,8 @@ cudaError_t launch_lambda_table(const Sched& S, long long s_begin, long long cou
 }
 
 cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, const float4* st_vec,
-                           const float* st_dist, double* x, double* v, double* W, int* status, const Sched& S,
+                           const float* st_dist, double* x, double* v, double* W, int* status, int* rep_status,
+                           const Sched& S,
                            long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
                            int k_lo, double* lam_tab, cudaStream_t st)
 {
@@ -686,7 +693,7 @@ cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, cons
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_cluster, reps, st_vec, st_dist, x, v, W, status, S, s_begin, n_steps, tab,
+    return cudaLaunchKernelEx(&cfg, k_cluster, reps, st_vec, st_dist, x, v, W, status, rep_status, S, s_begin, n_steps, tab,
                               work, k_lo, (const double*)lam_tab);
 }
 

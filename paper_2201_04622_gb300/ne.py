@@ -24,7 +24,7 @@ NE_PATH_FL, NE_PATH_RS = 0, 1
 
 # every symbol include/ne.h declares
 SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_set_theta", "ne_ctx_get_theta",
-           "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_boxes", "ne_ctx_counters", "ne_last_error",
+           "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_boxes", "ne_ctx_replica_status", "ne_ctx_counters", "ne_last_error",
            "ne_create_crystal", "ne_create_crystal_ca", "ne_eam_energy_forces", "ne_eam_virial", "ne_eam_energy_forces_noalloc",
            "ne_spring_forces",
            "ne_eam_backward", "ne_eam_backward_acc", "ne_noise", "ne_init_velocities", "ne_langevin_step",
@@ -85,7 +85,8 @@ def load(build_if_missing: bool = True):
                 "ne_ctx_set_tuning": [p, i],
                 "ne_ctx_set_cluster_size": [p, i],
                 "ne_ctx_boxes": [p, i, p],
-                "ne_ctx_counters": [p, p, p, p],
+                "ne_ctx_replica_status": [p, i, p],
+                "ne_ctx_counters": [p, p, p, p, p],
                 "ne_last_error": [p, p, p, i],
                 "ne_create_crystal": [i, d, i, i, i, p, p, p],
                 "ne_create_crystal_ca": [i, d, d, i, i, i, p, p, p],
@@ -205,16 +206,25 @@ def ne_ctx_boxes(ctx, n_rep):
     return out
 
 
+def ne_ctx_replica_status(ctx, n_rep):
+    """Per-replica status codes (NE_OK, NE_ERANGE, ...) of the last crystal-runner call."""
+    import numpy as np
+    out = np.zeros(int(n_rep), dtype=np.int32)
+    _err(ctx, load().ne_ctx_replica_status(ctx, int(n_rep), out.ctypes.data_as(C.c_void_p)), "ne_ctx_replica_status")
+    return out
+
+
 def ne_ctx_set_cluster_size(ctx, ctas):
     """CTAs per cluster of the crystal runner (0: chosen per batch)."""
     _err(ctx, load().ne_ctx_set_cluster_size(ctx, int(ctas)), "ne_ctx_set_cluster_size")
 
 
 def ne_ctx_counters(ctx):
-    """(list builds, stencil entries visited, pairs inside r_c) so far."""
-    a, b, c = C.c_longlong(), C.c_longlong(), C.c_longlong()
-    _err(ctx, load().ne_ctx_counters(ctx, C.byref(a), C.byref(b), C.byref(c)), "ne_ctx_counters")
-    return a.value, b.value, c.value
+    """(list builds, stencil entries visited, pairs inside r_c, crystal-runner
+    kernel launches) so far."""
+    a, b, c, d = C.c_longlong(), C.c_longlong(), C.c_longlong(), C.c_longlong()
+    _err(ctx, load().ne_ctx_counters(ctx, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), "ne_ctx_counters")
+    return a.value, b.value, c.value, d.value
 
 
 def ne_last_error(ctx):

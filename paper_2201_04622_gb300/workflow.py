@@ -32,26 +32,22 @@ def fit_spring_constant(ctx, lattice, a, n, T, mass, prec=ne.NE_MIXED, seed=1, n
 
 
 def fl_batch(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec=ne.NE_MIXED, runner="crystal",
-             skin=2.6, device="cuda", chunk=None):
+             skin=2.6, device="cuda", chunk=None, replica_ids=None):
     """Forward and backward FL works of a batch of crystal replicas.
 
     crystals: list of (lattice, a, n) per replica; ks, seeds: per replica;
-    T: one temperature or one per replica.
+    T: one temperature or one per replica; replica_ids: the Philox replica
+    index of each replica (default 0 .. n-1).
     runner: "crystal" (persistent cluster runner, mixed precision),
     "general" (multi-kernel path, FP64 or mixed), or "auto": the crystal
-    runner, and the general mixed path from the same start if an atom strays
-    beyond the runner's stencil range (NE_ERANGE; soft springs at high T).
+    runner, and every replica that leaves the runner's stencil range
+    (NE_ERANGE: a hop or melting at high T) rerun from the same start on the
+    general mixed path; the other replicas keep their crystal-runner results.
     Returns (W_f, W_b) numpy arrays and the final positions."""
     import torch
+    ids = list(range(len(crystals))) if replica_ids is None else list(replica_ids)
     if runner == "auto":
-        try:
-            return fl_batch(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec, "crystal", skin, device, chunk)
-        except ne.NeError as e:
-            if "NE_ERANGE" not in str(e):
-                raise
-            import warnings
-            warnings.warn("crystal runner out of its stencil range; rerunning on the multi-kernel path")
-            return fl_batch(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec, "general", skin, device, chunk)
+        return _fl_batch_auto(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec, skin, device, chunk, ids)
     x0s, offs, boxes, mds, crs = [], [0], [], [], []
     Ts = list(T) if np.ndim(T) else [T] * len(crystals)
     for r, ((lat, a, n), k, seed, Tr) in enumerate(zip(crystals, ks, seeds, Ts)):
@@ -61,7 +57,7 @@ def fl_batch(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec=ne.NE_MIXED, run
         boxes.append(box)
         crs.append((lat, a, n, n, n))
         mds.append(ne.md_params(T=Tr, mass=mass, k_spring=k, skin=skin, prec=prec, t_eq=t_eq, t_s=t_s,
-                                seed=seed, replica=r, fix_cm=1))
+                                seed=seed, replica=ids[r], fix_cm=1))
     x0 = torch.tensor(np.concatenate(x0s), dtype=torch.float64, device=device)
     x, v = x0.clone(), torch.zeros_like(x0)
     for r, m in enumerate(mds):
@@ -77,6 +73,55 @@ def fl_batch(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec=ne.NE_MIXED, run
             ne.ne_switch_run_segment(ctx, mds, offs, x, v, x0, boxes, W, s0, ns)
     Wn = W.cpu().numpy()
     return Wn[:, 0], Wn[:, 1], x
+
+
+def _fl_batch_auto(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec, skin, device, chunk, ids):
+    """fl_batch(runner="auto"): crystal runner, replicas that leave its range
+    moved to the general path one call at a time (ne_ctx_replica_status)."""
+    import torch
+    import warnings
+    n = len(crystals)
+    Ts = list(T) if np.ndim(T) else [T] * n
+    on_crystal, on_general = list(range(n)), []
+    res = {}
+    while on_crystal:
+        pick = lambda L: [L[q] for q in on_crystal]  # noqa: E731
+        try:
+            Wf, Wb, x = fl_batch(ctx, pick(crystals), pick(Ts), pick(ks), pick(seeds), t_eq, t_s, mass, prec,
+                                 "crystal", skin, device, chunk, pick(ids))
+        except ne.NeError as e:
+            if "NE_ERANGE" not in str(e):
+                raise
+            st = ne.ne_ctx_replica_status(ctx, len(on_crystal))
+            bad = [on_crystal[q] for q in range(len(on_crystal)) if st[q] == ne.NE_ERANGE]
+            if not bad:
+                raise
+            warnings.warn("replicas %s left the crystal runner's stencil range; rerunning them on the "
+                          "multi-kernel path" % bad)
+            on_general += bad
+            on_crystal = [q for q in on_crystal if q not in bad]
+            continue
+        res.update(_split(on_crystal, crystals, Wf, Wb, x))
+        break
+    if on_general:
+        on_general.sort()
+        pick = lambda L: [L[q] for q in on_general]  # noqa: E731
+        Wf, Wb, x = fl_batch(ctx, pick(crystals), pick(Ts), pick(ks), pick(seeds), t_eq, t_s, mass, prec,
+                             "general", skin, device, chunk, pick(ids))
+        res.update(_split(on_general, crystals, Wf, Wb, x))
+    Wf = np.array([res[q][0] for q in range(n)])
+    Wb = np.array([res[q][1] for q in range(n)])
+    return Wf, Wb, torch.cat([res[q][2] for q in range(n)])
+
+
+def _split(idx, crystals, Wf, Wb, x):
+    out, o = {}, 0
+    for j, q in enumerate(idx):
+        lat, a, n = crystals[q]
+        na = (2 if lat == ne.NE_BCC else 4) * n ** 3
+        out[q] = (Wf[j], Wb[j], x[o:o + na])
+        o += na
+    return out
 
 
 def free_energy(lattice, a, n, T, mass, k, W_f, W_b):

@@ -123,8 +123,8 @@ def test_crystal_runner_full_size_batch(ctx, pot):
         assert float(Wd[r, 0]) == pytest.approx(ro["W_f"], rel=1e-4, abs=1e-3)
         assert float(Wd[r, 1]) == pytest.approx(ro["W_b"], rel=1e-4, abs=1e-3)
     # work counters advanced: every atom examined stencil entries and found pairs
-    builds, visits, pairs = ne.ne_ctx_counters(ctx)
-    assert pairs > 30 * offs[-1] * 40
+    builds, visits, pairs, launches = ne.ne_ctx_counters(ctx)
+    assert pairs > 30 * offs[-1] * 40 and launches >= 2
 
 
 def test_crystal_runner_resume_is_bitwise(ctx):
@@ -218,19 +218,79 @@ def test_size_scaling_workflow(ctx):
     assert all(np.isfinite([r["F"] for r in rows])) and np.isfinite(F_inf)
 
 
-def test_fl_batch_auto_falls_back_when_atoms_leave_the_stencil(ctx):
-    """Soft springs at high T in a small box (stencil range D = 0.94 A;
-    Einstein amplitude sqrt(kT/k) = 0.28 A per component, so some atom
-    leaves the range while pairs stay far from overlap): the crystal runner
-    reports NE_ERANGE; runner='auto' reruns the batch on the multi-kernel
-    path and returns finite works."""
+def test_crystal_runner_reports_atoms_beyond_the_stencil_range(ctx):
+    """Three bcc 6^3 replicas; the middle one starts with an atom 2.2 A from
+    its site (D = 2 A; along [110], 1.45 A from its nearest neighbours, far
+    from overlap): NE_ERANGE, and ne_ctx_replica_status names that replica
+    alone.  The same start 1.8 A out runs."""
+    mo, mg = md_pair(T=300.0)
+    x0, box = O.create_crystal(O.BCC, W.A_BCC, 6, 6, 6)
+    mgs = [md_pair(T=300.0, replica=r)[1] for r in range(3)]
+    crs = [(O.BCC, W.A_BCC, 6, 6, 6)] * 3
+    for shift, ok in ((2.2, False), (1.8, True)):
+        x = np.concatenate([x0] * 3)
+        x[len(x0), :2] += shift / np.sqrt(2.0)
+        xt, vt = T(x), T(np.zeros_like(x))
+        Wd = torch.zeros((3, 2), dtype=torch.float64, device=DEV)
+        if ok:
+            ne.ne_crystal_run_segment(ctx, mgs, crs, xt, vt, Wd, 0, 10)
+            assert list(ne.ne_ctx_replica_status(ctx, 3)) == [ne.NE_OK] * 3
+        else:
+            with pytest.raises(ne.NeError, match="NE_ERANGE"):
+                ne.ne_crystal_run_segment(ctx, mgs, crs, xt, vt, Wd, 0, 10)
+            assert list(ne.ne_ctx_replica_status(ctx, 3)) == [ne.NE_OK, ne.NE_ERANGE, ne.NE_OK]
+
+
+@pytest.mark.parametrize("lat,n", [(O.BCC, 5), (O.FCC, 4)])
+def test_crystal_runner_small_hot_boxes_track_oracle(ctx, pot, lat, n):
+    """bcc 5^3 and fcc 4^3 (L ~ 14.5 A < 2 (r_c + 2D)): the stencil holds two
+    periodic images of some sites.  At 1400 K over 100 steps the runner
+    follows the FP64 oracle as closely as on large boxes."""
+    p, th = pot
+    x, v, Wd, x0s, vs = run_crystals(ctx, [(lat, n, 1400.0, 7)], 0, 100, k_spring=2.5)
+    mo, _ = md_pair(T=1400.0, seed=7, replica=0, k_spring=2.5)
+    x0, box = O.create_crystal(lat, lat_a(lat), n, n, n)
+    ro = O.switch_run(p, th, mo, x0, vs[0], x0, box)
+    assert np.abs(x.cpu().numpy() - ro["x"]).max() < 2e-4
+    Wg = Wd.cpu().numpy()[0]
+    assert Wg[0] == pytest.approx(ro["W_f"], rel=1e-5, abs=1e-3)
+    assert Wg[1] == pytest.approx(ro["W_b"], rel=1e-5, abs=1e-3)
+
+
+def test_fl_batch_auto_reruns_only_the_replicas_out_of_range(ctx, monkeypatch):
+    """runner='auto': when the crystal runner reports NE_ERANGE for one
+    replica (a stand-in raises it and ne_ctx_replica_status names replica 1,
+    since a crystal that stays solid never leaves the range), that replica
+    alone is rerun on the multi-kernel mixed path with its own Philox index;
+    the others are rerun on the crystal runner without it.  Each result
+    equals the direct run of its subset bit for bit."""
     from paper_2201_04622_gb300 import workflow as WF
-    args = (ctx, [(O.BCC, W.A_BCC, 5)] * 2, 1400.0, [1.5, 1.5], [1, 2], 200, 400, MASS)
-    with pytest.raises(ne.NeError, match="NE_ERANGE"):
-        WF.fl_batch(*args, runner="crystal", skin=1.0)
+    real = WF.fl_batch
+    crystals = [(O.BCC, W.A_BCC, 6)] * 3
+    args = (ctx, crystals, 1400.0, [2.38] * 3, [1, 2, 3], 20, 40, MASS)
+    calls = []
+
+    def fake(*a, **kw):
+        runner, ids = a[9], list(a[13])
+        calls.append((runner, ids))
+        if runner == "crystal" and 1 in ids:
+            raise ne.NeError(ne.NE_ERANGE, "ne_crystal_run_segment", "stand-in")
+        return real(*a, **kw)
+
+    monkeypatch.setattr(WF, "fl_batch", fake)
+    monkeypatch.setattr(ne, "ne_ctx_replica_status",
+                        lambda c, n: np.array([ne.NE_OK, ne.NE_ERANGE, ne.NE_OK][:n], dtype=np.int32))
     with pytest.warns(UserWarning):
-        Wf, Wb, _ = WF.fl_batch(*args, runner="auto", skin=1.0)
-    assert np.all(np.isfinite(Wf)) and np.all(np.isfinite(Wb))
+        Wf, Wb, x = real(*args, runner="auto", skin=1.0)
+    assert calls == [("crystal", [0, 1, 2]), ("crystal", [0, 2]), ("general", [1])]
+    monkeypatch.undo()
+    Wc, Wbc, xc = WF.fl_batch(ctx, [crystals[0], crystals[2]], 1400.0, [2.38] * 2, [1, 3], 20, 40, MASS,
+                              runner="crystal", replica_ids=[0, 2])
+    Wg, Wbg, xg = WF.fl_batch(ctx, [crystals[1]], 1400.0, [2.38], [2], 20, 40, MASS,
+                              runner="general", skin=1.0, replica_ids=[1])
+    assert np.array_equal(Wf, [Wc[0], Wg[0], Wc[1]]) and np.array_equal(Wb, [Wbc[0], Wbg[0], Wbc[1]])
+    na = len(xg)
+    assert torch.equal(x, torch.cat([xc[:na], xg, xc[na:]]))
 
 
 def test_fl1400_full_length_works_vs_oracle(ctx):
