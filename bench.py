@@ -12,7 +12,10 @@ pass 1, pass 2, fused blend/spring/work/BAOAB step).  Inputs are synthetic
                     [--prec mixed|fp64] [--no-cpu-baseline]
 
 Prints one JSON line.  --impl reference times the CPU FP64 oracle (the
-baseline this build is checked against) on the host cores.
+baseline the library is checked against) on the host cores.  Under torchrun
+(N > 1) every rank runs its own copy of the workload (replicas only: distinct
+Philox replica indices, no data exchange); the time is the maximum over the
+ranks and the value the whole job's atom-steps over that time.
 """
 from __future__ import annotations
 
@@ -139,6 +142,25 @@ def flush_l2(torch, buf):
     buf.add_(1.0)
 
 
+def rank_replica_ids(n_rep, rank):
+    """Philox replica indices of one rank's replicas: every rank runs its own
+    copy of the workload, so the indices are shifted by n_rep per rank."""
+    return [rank * n_rep + r for r in range(n_rep)]
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (all_reduce MAX); the same value on every rank."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units per second of the whole job: all ranks' units over the slowest time."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -156,9 +178,9 @@ def run_ours(args):
     ne.load()
     prec = ne.NE_MIXED if args.prec == "mixed" else ne.NE_FP64
     x0_np, offs, boxes, mds = build_batch(ne, np)
-    for m in mds:
+    for m, rid in zip(mds, rank_replica_ids(len(mds), rank)):
         m.prec = prec
-        m.replica += 20 * rank   # replicas only: each rank runs its own 20
+        m.replica = rid
     n_rep, n_atoms = len(mds), int(offs[-1])
     ctx = ne.ne_ctx_create(ne.eam_params(**W.EAM_FE_LIKE), n_atoms, n_rep)
     ne.ne_ctx_set_tuning(ctx, args.tpa)
@@ -237,11 +259,9 @@ def run_ours(args):
     list_builds = c1[0] - c0[0]
     visits, pairs = c1[1] - c0[1], c1[2] - c0[2]
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         dist.barrier()
-    value = K * n_atoms * world / (ms * 1e-3)
+    value = whole_job_rate(K * n_atoms, world, ms)
 
     # end to end: the same K steps again from the state after warm-up, through
     # the C ABI from pinned host buffers (copies in, K steps, state and work out)
@@ -266,9 +286,11 @@ def run_ours(args):
         Wh.copy_(Wd2, non_blocking=True)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
+        if world > 1:
+            t_e2e = max_over_ranks(t_e2e * 1e3, dist, dev) * 1e-3
         h2d = (xh.numel() + vh.numel() + x0h.numel() + Wh.numel()) * 8
         d2h = (xh.numel() + vh.numel() + Wh.numel()) * 8
-        e2e = {"value": K2 * n_atoms * world / t_e2e, "unit": UNIT,
+        e2e = {"value": whole_job_rate(K2 * n_atoms, world, t_e2e * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": h2d / K2, "d2h_bytes_per_step": d2h / K2,
                "steps": K2, "note": "the timed K steps replayed through one ABI call from pinned host state: "
                                     "copies in, K steps, state and work out"}
@@ -330,7 +352,9 @@ def run_ours(args):
         f1.record(stream)
         torch.cuda.synchronize()
         ms64 = f0.elapsed_time(f1)
-        v64val = K64 * n_atoms * world / (ms64 * 1e-3)
+        if world > 1:
+            ms64 = max_over_ranks(ms64, dist, dev)
+        v64val = whole_job_rate(K64 * n_atoms, world, ms64)
         fp64 = {"value": v64val, "unit": UNIT, "ms_per_step": ms64 / K64, "steps": K64,
                 "path": "multi-kernel, FP64 throughout", "speedup_of_mixed": value / v64val}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
