@@ -300,6 +300,7 @@ ne_status finish(ne_ctx* ctx, cudaStream_t st)
     if (bits & ST_ERANGE) return fail(ctx, NE_ERANGE, "pair distance below 0.2 A, density >= rho_max, or an atom beyond the crystal runner's stencil range");
     if (bits & ST_ENEIGH) return fail(ctx, NE_ENEIGH, "neighbour-list capacity exceeded");
     if (bits & ST_ETIMEOUT) return fail(ctx, NE_ETIMEOUT, "bounded device wait gave up");
+    if (bits & ST_EINVAL) return fail(ctx, NE_EINVAL, "crystal runner: shared-memory layout larger than the launch's allocation");
     ctx->msg = "ok";
     return NE_OK;
 }
@@ -1069,8 +1070,6 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
     std::vector<XRep> xr(n_rep);
     std::vector<float4> sv;  // (lattice vector, neighbour code as float bits)
     std::vector<float> sd;   // |lattice vector|
-    int n_max = 0, nbst_max = 0, lut_max = 0;
-    (void)n_max;
     for (int r = 0; r < n_rep; ++r) {
         const ne_md_params& m = md[r];
         XRep& X = xr[r];
@@ -1107,12 +1106,13 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         X.D = (float)D;
         const double Rst = rc + 2.0 * D;
         const int M = (int)std::ceil(Rst / std::min(X.cell[0], std::min(X.cell[1], X.cell[2]))) + 1;
-        // neighbour code of a stencil entry (dx, dy, dz, b2): bits 0-9 the
+        // neighbour code of a stencil entry (dx, dy, dz, b2): bits 0-15 the
         // offset (dx + M) * (ny + 2M) + dy + M into the xy table of wrapped
-        // cells, bits 10-14 dz + M, bits 15-31 b2 * (cells per replica), the
-        // start of basis site b2 in the basis-major copy of the replica
-        const int LY = X.ny + 2 * M, ncell = X.nx * X.ny * X.nz;
-        if (2 * M * LY + 2 * M >= 1024 || 2 * M >= 32 || (X.nb - 1) * ncell >= (1 << 16))
+        // cells, bits 16-31 b2 * (nz + 2M) + dz + M into the z table, whose
+        // entries also carry the start of basis site b2 in the basis-major
+        // copy of the replica
+        const int LY = X.ny + 2 * M, LZ = X.nz + 2 * M;
+        if ((X.nx + 2 * M) * LY >= (1 << 16) || X.nb * LZ >= (1 << 16))
             return fail(ctx, NE_EINVAL, "crystal runner: box shape outside the stencil code range");
         std::vector<std::vector<std::pair<double, std::pair<float4, int>>>> per(X.nb);
         for (int b = 0; b < X.nb; ++b) {
@@ -1126,7 +1126,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
                             const double ez = X.cell[2] * (dz + basis[b2][2] - basis[b][2]);
                             const double d = std::sqrt(ex * ex + ey * ey + ez * ez);
                             if (d >= Rst) continue;
-                            const int code = ((dx + M) * LY + dy + M) | ((dz + M) << 10) | ((b2 * ncell) << 15);
+                            const int code = ((dx + M) * LY + dy + M) | ((b2 * LZ + dz + M) << 16);
                             per[b].push_back({d, {make_float4((float)ex, (float)ey, (float)ez, code_bits(code)), code}});
                         }
             std::stable_sort(per[b].begin(), per[b].end(), [](const auto& p, const auto& q) {
@@ -1138,7 +1138,6 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         if (cnt > NE_STENCIL_MAX) return fail(ctx, NE_EINVAL, "stencil too large");
         X.st_cnt = (int)cnt;
         X.st_margin = M;
-        lut_max = std::max(lut_max, (X.nx + 2 * M) * LY + X.nz + 2 * M);
         X.st_off = (int)sv.size();
         for (int b = 0; b < X.nb; ++b)
             for (size_t q = 0; q < cnt; ++q) {
@@ -1146,12 +1145,10 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
                     sv.push_back(per[b][q].second.first);
                     sd.push_back((float)per[b][q].first);
                 } else {  // padding: beyond any cutoff
-                    sv.push_back(make_float4(0.f, 0.f, 0.f, code_bits((M * LY + M) | (M << 10))));
+                    sv.push_back(make_float4(0.f, 0.f, 0.f, code_bits((M * LY + M) | (M << 16))));
                     sd.push_back(1e30f);
                 }
             }
-        n_max = std::max(n_max, X.n);
-        nbst_max = std::max(nbst_max, X.nb * X.st_cnt);
     }
     if (sv.size() > (size_t)ctx->max_rep * 4 * NE_STENCIL_MAX) return fail(ctx, NE_ENOMEM, "stencil capacity exceeded");
     int dev = 0, smem_max = 0;
@@ -1167,7 +1164,8 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
             gn = std::max(gn, xr[r].n);
             gnb = std::max(gnb, xr[r].nb * xr[r].st_cnt);
             const int Mr = xr[r].st_margin;
-            glut = std::max(glut, (xr[r].nx + 2 * Mr) * (xr[r].ny + 2 * Mr) + xr[r].nz + 2 * Mr);
+            // the kernel's wrapped-cell tables: (x, y) and, per basis site, z
+            glut = std::max(glut, (xr[r].nx + 2 * Mr) * (xr[r].ny + 2 * Mr) + xr[r].nb * (xr[r].nz + 2 * Mr));
         }
         const size_t base = (ne::cluster_smem_bytes(gn, gnb, glut) + 15) & ~(size_t)15;
         if (base > (size_t)smem_max) return false;

@@ -218,11 +218,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     float4* s_sv = s_u + n;                                       // [nb * nst] (r0_j - r0_i, code bits)
     float* s_sd = (float*)(s_sv + nb * nst);                      // [nb * nst] |r0_j - r0_i|
     // wrapped cell offsets: s_lxy[X * LY + Y] = ((X - M) mod nx * ny + (Y - M) mod ny) * nz,
-    // s_lz[Z] = (Z - M) mod nz, for X, Y, Z = cell index + stencil offset + M
+    // s_lz[b2 * (nz + 2M) + Z] = (Z - M) mod nz + b2 * ncell, for X, Y, Z =
+    // cell index + stencil offset + M and basis site b2 of the neighbour
     const int LY = ny + 2 * M;
     int* s_lxy = (int*)(s_sd + nb * nst);                         // [(nx + 2M) * LY]
-    int* s_lz = s_lxy + (nx + 2 * M) * LY;                        // [nz + 2M]
-    unsigned short* s_K = (unsigned short*)(s_lz + nz + 2 * M);  // [4][NKT] scan bounds
+    int* s_lz = s_lxy + (nx + 2 * M) * LY;                        // [nb][nz + 2M]
+    unsigned short* s_K = (unsigned short*)(s_lz + nb * (nz + 2 * M));  // [4][NKT] scan bounds
     // short list: entry q of thread (slot, lane) at [q][lane][slot], holding
     // k / TPA of its stencil entry k (k = TPA * entry + lane)
     unsigned char* s_sl = (unsigned char*)(s_K + 4 * NKT);      // [SLQ][TPA][SLOTS]
@@ -238,20 +239,37 @@ __global__ void __launch_bounds__(THREADS, 1)
     // spline intervals [k_lo, nk - 1) of phi, then of f: separate arrays, so
     // consecutive intervals fall in consecutive 16-byte bank groups
     float4* s_tabP = (float4*)(((size_t)(s_misc + 8) + 15) & ~(size_t)15);  // [nk-1-k_lo]
+    const int n_int = tab.nk - 1 - k_lo;  // intervals of the r grid held in shared memory
+    float4* s_tabF = s_tabP + n_int;                                           // [nk-1-k_lo]
+    {
+        // the layout must fit the launch's dynamic shared memory (sized on the
+        // host from the same counts); every CTA of a cluster takes the same
+        // decision before touching shared memory
+        unsigned dyn;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        if ((size_t)((unsigned char*)(s_tabF + n_int) - smem) > (size_t)dyn) {
+            if (threadIdx.x == 0) {
+                ne_set_status(status, ST_EINVAL);
+                ne_set_status(rep_status + reps[rep].widx, ST_EINVAL);
+            }
+            return;
+        }
+    }
 
     for (int q = threadIdx.x; q < nb * nst; q += THREADS) {
         s_sv[q] = st_vec[reps[rep].st_off + q];
         s_sd[q] = st_dist[reps[rep].st_off + q];
     }
-    const int n_int = tab.nk - 1 - k_lo;  // intervals of the r grid held in shared memory
-    float4* s_tabF = s_tabP + n_int;                                           // [nk-1-k_lo]
     for (int q = threadIdx.x; q < 2 * n_int; q += THREADS)
         ((q & 1) ? s_tabF : s_tabP)[q >> 1] = tab.pf32[2 * k_lo + q];
     // shared-memory copy of the replica is basis-major: entry b * ncell + cell
     const int ncell = n / nb;
     for (int q = threadIdx.x; q < (nx + 2 * M) * LY; q += THREADS)
         s_lxy[q] = ((((q / LY - M) % nx + nx) % nx) * ny + ((q % LY - M) % ny + ny) % ny) * nz;
-    for (int q = threadIdx.x; q < nz + 2 * M; q += THREADS) s_lz[q] = ((q - M) % nz + nz) % nz;
+    for (int q = threadIdx.x; q < nb * (nz + 2 * M); q += THREADS) {
+        const int Z = q % (nz + 2 * M);
+        s_lz[q] = ((Z - M) % nz + nz) % nz + (q / (nz + 2 * M)) * ncell;
+    }
 
     // slots are basis-major inside a CTA: the atoms of a warp share a stencil
     // and their neighbours for one stencil entry lie close together
@@ -409,8 +427,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int k = lane; k < K; k += 2) {
                 const float4 e = s_sv[stb + k];
                 const int code = __float_as_int(e.w);
-                const int j = s_lxy[sxy + (code & 1023)] + s_lz[sz + ((code >> 10) & 31)] +
-                              (int)((unsigned)code >> 15);
+                const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
                 const float4 uj = s_u[j];
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
@@ -490,8 +507,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int k = TPA * s_sl[(q * TPA + lane) * SLOTS + slot] + lane;
                 const float4 e = s_sv[stb + k];
                 const int code = __float_as_int(e.w);
-                const int j = s_lxy[sxy + (code & 1023)] + s_lz[sz + ((code >> 10) & 31)] +
-                              (int)((unsigned)code >> 15);
+                const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
                 const float4 uj = s_u[j];
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
