@@ -220,15 +220,28 @@ def run_ours(args):
         bad = [r for r, c in enumerate(ne.ne_ctx_replica_status(ctx, len(mds))) if c == ne.NE_ERANGE]
         if not bad:
             raise RuntimeError("crystal runner: NE_ERANGE without a replica")
-        idx = torch.cat([torch.arange(offs[r], offs[r + 1], device=dev) for r in bad])
+        # contiguous per-replica slices (plain copies; no gather kernels)
         so = [0]
         for r in bad:
             so.append(so[-1] + offs[r + 1] - offs[r])
-        xs, vs, Ws = snap[0][idx].contiguous(), snap[1][idx].contiguous(), snap[2][bad].contiguous()
-        ne.ne_switch_run_segment(ctx, [mds[r] for r in bad], so, xs, vs, x00[idx].contiguous(),
-                                 [boxes[r] for r in bad], Ws, s0, ns)
-        xx[idx], vv[idx], WW[bad] = xs, vs, Ws
-        moved.append({"replicas": bad, "steps": [s0, s0 + ns]})
+        xs = torch.empty((so[-1], 3), dtype=xx.dtype, device=dev)
+        vs, x0s = torch.empty_like(xs), torch.empty_like(xs)
+        Ws = torch.empty((len(bad), 2), dtype=WW.dtype, device=dev)
+        for i, r in enumerate(bad):
+            xs[so[i]:so[i + 1]].copy_(snap[0][offs[r]:offs[r + 1]])
+            vs[so[i]:so[i + 1]].copy_(snap[1][offs[r]:offs[r + 1]])
+            x0s[so[i]:so[i + 1]].copy_(x00[offs[r]:offs[r + 1]])
+            Ws[i].copy_(snap[2][r])
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        ne.ne_switch_run_segment(ctx, [mds[r] for r in bad], so, xs, vs, x0s, [boxes[r] for r in bad], Ws, s0, ns)
+        r1.record(stream)
+        for i, r in enumerate(bad):
+            xx[offs[r]:offs[r + 1]].copy_(xs[so[i]:so[i + 1]])
+            vv[offs[r]:offs[r + 1]].copy_(vs[so[i]:so[i + 1]])
+            WW[r].copy_(Ws[i])
+        torch.cuda.synchronize()
+        moved.append({"replicas": bad, "steps": [s0, s0 + ns], "rerun_ms": r0.elapsed_time(r1)})
 
     tuned = None
     if path == "general" and args.autotune:

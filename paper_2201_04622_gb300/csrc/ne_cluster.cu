@@ -404,10 +404,18 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
             umax = um;
-            if (threadIdx.x == 0 && um > reps[rep].D) {
-                ne_set_status(status, ST_ERANGE);
-                ne_set_status(rep_status + reps[rep].widx, ST_ERANGE);
+        }
+        // an atom beyond the stencil range (or a non-finite displacement): the
+        // replica's result is void, so its cluster stops here instead of
+        // scanning the whole stencil for the rest of the range.  Every CTA of
+        // the cluster holds the same slot values and leaves at the same step.
+        if (!(umax <= reps[rep].D)) {
+            if (threadIdx.x == 0) {
+                const int e = isnan(umax) ? ST_ENAN : ST_ERANGE;
+                ne_set_status(status, e);
+                ne_set_status(rep_status + reps[rep].widx, e);
             }
+            break;
         }
 
         // ---------------- pass 1: density, pair forces and energy, short list
