@@ -47,7 +47,7 @@ struct ne_ctx {
     double *partA = nullptr, *partB = nullptr, *tot = nullptr, *W = nullptr, *scratch = nullptr;
     unsigned* tile_done = nullptr;
     int *flags = nullptr, *building = nullptr, *status = nullptr, *tile_rep = nullptr;
-    int* rep_status = nullptr;  // crystal runner: status bits per replica of the last call
+    int* rep_status = nullptr;  // crystal runner: status bits per replica of the last call (= status + 1)
     RepDev* rep = nullptr;
     long long* step_ctr = nullptr;
     unsigned long long* rebuilds = nullptr;
@@ -529,8 +529,8 @@ ne_status ne_ctx_create(const ne_eam_params* eam, int max_atoms, int max_replica
     A(dalloc(&ctx->tile_done, R));
     A(dalloc(&ctx->flags, R));
     A(dalloc(&ctx->building, R));
-    A(dalloc(&ctx->status, 1));
-    A(dalloc(&ctx->rep_status, R));
+    A(dalloc(&ctx->status, 1 + R));  // the status word, then one per replica (crystal runner)
+    if (ok) ctx->rep_status = ctx->status + 1;
     A(dalloc(&ctx->tile_rep, (size_t)ctx->tiles_cap));
     A(dalloc(&ctx->rep, R));
     A(dalloc(&ctx->step_ctr, 1));
@@ -569,7 +569,7 @@ ne_status ne_ctx_destroy(ne_ctx* ctx)
                     ctx->pbuild, ctx->f32, ctx->f64, ctx->dF64, ctx->rho, ctx->xi64, ctx->xi32,
                     ctx->nbr, ctx->ncnt, ctx->sl, ctx->scnt, ctx->cellof, ctx->sorted, ctx->cstart,
                     ctx->cfill, ctx->partA, ctx->partB, ctx->tot, ctx->W, ctx->scratch,
-                    ctx->tile_done, ctx->flags, ctx->building, ctx->status, ctx->rep_status, ctx->tile_rep, ctx->rep, ctx->step_ctr, ctx->rebuilds, ctx->xrep, ctx->work, ctx->st_vec, ctx->st_dist, ctx->lam_tab,
+                    ctx->tile_done, ctx->flags, ctx->building, ctx->status, ctx->tile_rep, ctx->rep, ctx->step_ctr, ctx->rebuilds, ctx->xrep, ctx->work, ctx->st_vec, ctx->st_dist, ctx->lam_tab,
                     ctx->bins};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1274,8 +1274,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         cudaStream_t gs = multi ? ctx->gst[g] : st;
         if (multi) NE_CU(cudaStreamWaitEvent(gs, ctx->gev[16], 0));
         NE_CU(ne::launch_cluster(ctx->xrep + b, e - b, csize(order[b]), smem, ctx->st_vec, ctx->st_dist, x_dev, v_dev,
-                                 W_dev, ctx->status, ctx->rep_status, S, step_begin, n_steps, ctx->tab, ctx->work, k_lo,
-                                 ctx->lam_tab,
+                                 W_dev, ctx->status, S, step_begin, n_steps, ctx->tab, ctx->work, k_lo, ctx->lam_tab,
                                  gs));
         ++ctx->cr_launches;
         if (multi) {

@@ -198,7 +198,7 @@ __host__ __device__ inline int atoms_per_cta(int n, int C, int nb)
 
 __global__ void __launch_bounds__(THREADS, 1)
     k_cluster(const XRep* __restrict__ reps, const float4* __restrict__ st_vec, const float* __restrict__ st_dist,
-              double* __restrict__ xg, double* __restrict__ vg, double* __restrict__ Wg, int* status, int* rep_status, Sched S,
+              double* __restrict__ xg, double* __restrict__ vg, double* __restrict__ Wg, int* status, Sched S,
               long long s_begin, long long n_steps, Tables tab, unsigned long long* work, int k_lo,
               const double* __restrict__ lam_tab)
 {
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if ((size_t)((unsigned char*)(s_tabF + n_int) - smem) > (size_t)dyn) {
             if (threadIdx.x == 0) {
                 ne_set_status(status, ST_EINVAL);
-                ne_set_status(rep_status + reps[rep].widx, ST_EINVAL);
+                ne_set_status(status + 1 + reps[rep].widx, ST_EINVAL);
             }
             return;
         }
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (threadIdx.x == 0) {
                 const int e = isnan(umax) ? ST_ENAN : ST_ERANGE;
                 ne_set_status(status, e);
-                ne_set_status(rep_status + reps[rep].widx, e);
+                ne_set_status(status + 1 + reps[rep].widx, e);
             }
             break;
         }
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     if (bad) {
         ne_set_status(status, bad);
-        ne_set_status(rep_status + reps[rep].widx, bad);
+        ne_set_status(status + 1 + reps[rep].widx, bad);
     }
     if (work) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -694,8 +694,7 @@ cudaError_t launch_lambda_table(const Sched& S, long long s_begin, long long cou
 }
 
 cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, const float4* st_vec,
-                           const float* st_dist, double* x, double* v, double* W, int* status, int* rep_status,
-                           const Sched& S,
+                           const float* st_dist, double* x, double* v, double* W, int* status, const Sched& S,
                            long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
                            int k_lo, double* lam_tab, cudaStream_t st)
 {
@@ -717,7 +716,7 @@ cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, cons
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_cluster, reps, st_vec, st_dist, x, v, W, status, rep_status, S, s_begin, n_steps, tab,
+    return cudaLaunchKernelEx(&cfg, k_cluster, reps, st_vec, st_dist, x, v, W, status, S, s_begin, n_steps, tab,
                               work, k_lo, (const double*)lam_tab);
 }
 

@@ -29,8 +29,7 @@ int cluster_atoms_for(int n, int C, int nb);    // atoms per CTA of an n-atom re
 int cluster_max_active(int C, size_t smem);     // co-resident clusters of C CTAs (0 if none or on error)
 cudaError_t launch_lambda_table(const Sched& S, long long s_begin, long long count, double* out, cudaStream_t st);
 cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, const float4* st_vec,
-                           const float* st_dist, double* x, double* v, double* W, int* status, int* rep_status,
-                           const Sched& S,
+                           const float* st_dist, double* x, double* v, double* W, int* status, const Sched& S,
                            long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
                            int k_lo, double* lam_tab, cudaStream_t st);
 }  // namespace ne

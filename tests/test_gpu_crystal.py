@@ -323,3 +323,39 @@ def test_fl1400_full_length_works_vs_oracle(ctx):
         assert abs(Wb[q] - row["W_b"]) < tol, (q, Wb[q], row["W_b"])
         dF = 0.5 * ((Wf[q] - row["W_f"]) - (Wb[q] - row["W_b"])) / row["natoms"]
         assert abs(dF) < 1e-6
+
+
+@pytest.mark.parametrize("set_name", ["rs_bcc6", "fl_hcp6"])
+def test_runner_rs_and_hcp_full_length_works_vs_oracle(ctx, set_name):
+    """The crystal runner's other paths at lengths where the trajectories have
+    long decorrelated from their start (22,000 steps): reversible scaling on
+    bcc 6^3 from 300 to 1200 K, and Frenkel-Ladd on ideal hcp 6^3 at 1000 K.
+    Forward and backward works equal the stored FP64 oracle works
+    (tests/golden/runner_paths_works.json, same seeds and replica indices) to
+    the FP32 pair-energy rounding bound of the 1400 K test, 1e-6 eV per atom."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "runner_paths_works.json")) as f:
+        doc = json.load(f)
+    rows = [r for r in doc["rows"] if r["set"] == set_name]
+    assert len(rows) == 2
+    mgs, crs, x0s, vs = [], [], [], []
+    for r in rows:
+        m = ne.md_params(dt=1e-3, T=r["T"], damp=0.1, mass=MASS, k_spring=r["k"], skin=1.0, lambda_fn=2,
+                         path=r["path"], t_eq=doc["t_eq"], t_s=doc["t_s"], lambda_f=r["lambda_f"],
+                         seed=r["seed"], replica=r["replica"], fix_cm=1, prec=ne.NE_MIXED)
+        x0, box = O.create_crystal(r["lattice"], r["a"], r["n"], r["n"], r["n"])
+        v = torch.zeros((len(x0), 3), dtype=torch.float64, device=DEV)
+        ne.ne_init_velocities(ctx, m, v)
+        mgs.append(m)
+        crs.append((r["lattice"], r["a"], r["n"], r["n"], r["n"]))
+        x0s.append(x0)
+        vs.append(v)
+    x, v = T(np.concatenate(x0s)), torch.cat(vs)
+    Wd = torch.zeros((len(rows), 2), dtype=torch.float64, device=DEV)
+    ne.ne_crystal_run_segment(ctx, mgs, crs, x, v, Wd, 0, 2 * doc["t_eq"] + 2 * doc["t_s"])
+    Wg = Wd.cpu().numpy()
+    for q, r in enumerate(rows):
+        tol = 1e-6 * r["natoms"]
+        assert abs(Wg[q, 0] - r["W_f"]) < tol, (set_name, q, Wg[q, 0], r["W_f"])
+        assert abs(Wg[q, 1] - r["W_b"]) < tol, (set_name, q, Wg[q, 1], r["W_b"])
