@@ -201,47 +201,21 @@ def run_ours(args):
         path = "crystal" if prec == ne.NE_MIXED else "general"
     crystals = [(lat, a, n, n, n) for (lat, n, a, seed, Tk) in systems()]
 
-    moved = []  # replicas rerun on the multi-kernel path: out of the crystal runner's range
+    # the crystal path runs through the library's BatchAdvancer: a replica that
+    # leaves the crystal runner's range (a hop or melting at high T) continues
+    # on the multi-kernel mixed path from its state before that chunk, next to
+    # the crystal runner for the others; all of it inside the timed region
+    adv = None
+    if path == "crystal":
+        from paper_2201_04622_gb300.workflow import BatchAdvancer
+        adv = BatchAdvancer(ctx, mds, crystals, offs, boxes, x0,
+                            chunk=5000 if args.workload == "batched256" else None)
 
     def segment(xx, vv, x00, WW, s0, ns):
         if path != "crystal":
             ne.ne_switch_run_segment(ctx, mds, offs, xx, vv, x00, boxes, WW, s0, ns)
-            return
-        # a replica that leaves the runner's stencil range (a hop or melting
-        # at high T) is rerun alone on the multi-kernel mixed path over the
-        # same steps from its state before the call; the time counts
-        snap = (xx.clone(), vv.clone(), WW.clone())
-        try:
-            ne.ne_crystal_run_segment(ctx, mds, crystals, xx, vv, WW, s0, ns)
-            return
-        except ne.NeError as e:
-            if "NE_ERANGE" not in str(e):
-                raise
-        bad = [r for r, c in enumerate(ne.ne_ctx_replica_status(ctx, len(mds))) if c == ne.NE_ERANGE]
-        if not bad:
-            raise RuntimeError("crystal runner: NE_ERANGE without a replica")
-        # contiguous per-replica slices (plain copies; no gather kernels)
-        so = [0]
-        for r in bad:
-            so.append(so[-1] + offs[r + 1] - offs[r])
-        xs = torch.empty((so[-1], 3), dtype=xx.dtype, device=dev)
-        vs, x0s = torch.empty_like(xs), torch.empty_like(xs)
-        Ws = torch.empty((len(bad), 2), dtype=WW.dtype, device=dev)
-        for i, r in enumerate(bad):
-            xs[so[i]:so[i + 1]].copy_(snap[0][offs[r]:offs[r + 1]])
-            vs[so[i]:so[i + 1]].copy_(snap[1][offs[r]:offs[r + 1]])
-            x0s[so[i]:so[i + 1]].copy_(x00[offs[r]:offs[r + 1]])
-            Ws[i].copy_(snap[2][r])
-        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        r0.record(stream)
-        ne.ne_switch_run_segment(ctx, [mds[r] for r in bad], so, xs, vs, x0s, [boxes[r] for r in bad], Ws, s0, ns)
-        r1.record(stream)
-        for i, r in enumerate(bad):
-            xx[offs[r]:offs[r + 1]].copy_(xs[so[i]:so[i + 1]])
-            vv[offs[r]:offs[r + 1]].copy_(vs[so[i]:so[i + 1]])
-            WW[r].copy_(Ws[i])
-        torch.cuda.synchronize()
-        moved.append({"replicas": bad, "steps": [s0, s0 + ns], "rerun_ms": r0.elapsed_time(r1)})
+        else:
+            adv.advance(xx, vv, WW, s0, ns)
 
     tuned = None
     if path == "general" and args.autotune:
@@ -253,6 +227,7 @@ def run_ours(args):
     segment(x, v, x0, Wd, 0, Wm)
     torch.cuda.synchronize()
     x_w, v_w, W_w = x.clone(), v.clone(), Wd.clone()  # state after warm-up, for the e2e replay
+    moved_w = list(adv.moved) if adv else []
     flush_l2(torch, l2)
     if world > 1:
         dist.barrier()
@@ -260,7 +235,9 @@ def run_ours(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     c0 = ne.ne_ctx_counters(ctx)
-    n_moved0 = len(moved)
+    if adv:
+        adv.moved = list(moved_w)
+    n_log0 = len(adv.log) if adv else 0
     with Clocks() as clk:
         e0.record(stream)
         segment(x, v, x0, Wd, Wm, K)
@@ -268,7 +245,8 @@ def run_ours(args):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     c1 = ne.ne_ctx_counters(ctx)
-    n_moved1 = len(moved)
+    timed_log = list(adv.log[n_log0:]) if adv else []
+    moved_timed = list(adv.moved) if adv else []
     list_builds = c1[0] - c0[0]
     visits, pairs = c1[1] - c0[1], c1[2] - c0[2]
     if world > 1:
@@ -293,6 +271,8 @@ def run_ours(args):
         vd = vh.to(dev, non_blocking=True)
         x0d = x0h.to(dev, non_blocking=True)
         Wd2 = Wh.to(dev, non_blocking=True)
+        if adv:
+            adv.moved = list(moved_w)
         segment(xd, vd, x0d, Wd2, Wm, K2)
         xh.copy_(xd, non_blocking=True)
         vh.copy_(vd, non_blocking=True)
@@ -348,7 +328,8 @@ def run_ours(args):
     steps_per_graph = 32
     general_launches = 5 * K + (K - 1) // steps_per_graph + 10
     if path == "crystal":
-        launches = (c1[3] - c0[3]) + general_launches * (n_moved1 - n_moved0)
+        launches = (c1[3] - c0[3]) + sum(5 * e[3] + e[3] // steps_per_graph + 10
+                                         for e in timed_log if e[0] == "general")
     else:
         launches = general_launches
     # the plain FP64 GPU path on the same batch (the comparison the metric names)
@@ -386,7 +367,9 @@ def run_ours(args):
                       "threads_per_atom": 2 if path == "crystal" else args.tpa,
                       "autotune": tuned,
                       "list_builds_per_replica_step": list_builds / (K * n_rep),
-                      "moved_to_multikernel": moved[n_moved0:n_moved1],
+                      "moved_to_multikernel": {"replicas": moved_timed,
+                                               "calls": [[e[1], e[2], e[3]] for e in timed_log
+                                                         if e[0] == "general"]},
                       "parallelism": "replicas only" if world > 1 else "1 GPU",
                       "l2": "flushed before the timed segment; the 40k-atom state stays L2-resident "
                             "across MD steps by design"},
@@ -397,6 +380,8 @@ def run_ours(args):
     ne.ne_ctx_destroy(ctx)
     if rank == 0:
         print(json.dumps(out))
+    if adv:
+        adv.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -110,6 +110,14 @@ typedef struct {
 ne_status ne_ctx_create(const ne_eam_params* eam, int max_atoms, int max_replicas,
                         ne_ctx** out);
 ne_status ne_ctx_destroy(ne_ctx* ctx);
+/* A second context with the same potential, knot parameters theta and
+ * tuning as src and its own buffers for up to max_atoms atoms in up to
+ * max_replicas replicas (bookkeeping; the paper has no counterpart).  Calls
+ * on different contexts may run at once from different host threads on
+ * different streams -- e.g. the crystal runner on one and the multi-kernel
+ * path on the other; calls on one context must not overlap.  Synchronises
+ * the device.  *out is NULL on failure. */
+ne_status ne_ctx_clone(ne_ctx* src, int max_atoms, int max_replicas, ne_ctx** out);
 
 /* Replace the knot parameters theta (device, double [3][n_knots][2]: phi, f,
  * F; (value, slope) per knot) and rebuild the interpolation tables. */

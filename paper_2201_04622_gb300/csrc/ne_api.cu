@@ -581,6 +581,25 @@ ne_status ne_ctx_destroy(ne_ctx* ctx)
     return NE_OK;
 }
 
+ne_status ne_ctx_clone(ne_ctx* src, int max_atoms, int max_replicas, ne_ctx** out)
+{
+    if (out) *out = nullptr;
+    if (!src || !out) return NE_EINVAL;
+    ne_ctx* c = nullptr;
+    ne_status s = ne_ctx_create(&src->eam, max_atoms, max_replicas, &c);
+    if (s) return s;
+    c->tpa = src->tpa;
+    c->cluster_c = src->cluster_c;
+    s = ne_ctx_set_theta(c, src->theta, nullptr);
+    if (!s && cudaDeviceSynchronize() != cudaSuccess) s = NE_ECUDA;
+    if (s) {
+        ne_ctx_destroy(c);
+        return s;
+    }
+    *out = c;
+    return NE_OK;
+}
+
 ne_status ne_ctx_set_theta(ne_ctx* ctx, const double* theta_dev, void* stream)
 {
     if (!ctx || !theta_dev) return NE_EINVAL;

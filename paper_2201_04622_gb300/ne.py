@@ -23,7 +23,7 @@ NE_BCC, NE_FCC, NE_HCP = 0, 1, 2
 NE_PATH_FL, NE_PATH_RS = 0, 1
 
 # every symbol include/ne.h declares
-SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_set_theta", "ne_ctx_get_theta",
+SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_clone", "ne_ctx_set_theta", "ne_ctx_get_theta",
            "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_boxes", "ne_ctx_replica_status", "ne_ctx_counters", "ne_last_error",
            "ne_create_crystal", "ne_create_crystal_ca", "ne_eam_energy_forces", "ne_eam_virial", "ne_eam_energy_forces_noalloc",
            "ne_spring_forces",
@@ -80,6 +80,7 @@ def load(build_if_missing: bool = True):
             sigs = {
                 "ne_ctx_create": [p, i, i, p],
                 "ne_ctx_destroy": [p],
+                "ne_ctx_clone": [p, i, i, p],
                 "ne_ctx_set_theta": [p, p, p],
                 "ne_ctx_get_theta": [p, p, p],
                 "ne_ctx_set_tuning": [p, i],
@@ -184,6 +185,13 @@ def ne_ctx_create(eam: EamParams, max_atoms: int, max_replicas: int = 1):
 
 def ne_ctx_destroy(ctx):
     _err(None, load().ne_ctx_destroy(ctx), "ne_ctx_destroy")
+
+
+def ne_ctx_clone(src, max_atoms: int, max_replicas: int = 1):
+    """A second context with src's potential, theta and tuning."""
+    h = C.c_void_p()
+    _err(src, load().ne_ctx_clone(src, int(max_atoms), int(max_replicas), C.byref(h)), "ne_ctx_clone")
+    return h
 
 
 def ne_ctx_set_theta(ctx, theta, stream=None):

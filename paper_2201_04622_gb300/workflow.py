@@ -40,9 +40,10 @@ def fl_batch(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec=ne.NE_MIXED, run
     index of each replica (default 0 .. n-1).
     runner: "crystal" (persistent cluster runner, mixed precision),
     "general" (multi-kernel path, FP64 or mixed), or "auto": the crystal
-    runner, and every replica that leaves the runner's stencil range
-    (NE_ERANGE: a hop or melting at high T) rerun from the same start on the
-    general mixed path; the other replicas keep their crystal-runner results.
+    runner in chunks (`chunk` steps, default 5000) on a BatchAdvancer; a
+    replica that leaves the runner's stencil range (NE_ERANGE: a hop or
+    melting at high T) continues on the general mixed path from its state
+    before that chunk, alongside the crystal runner for the others.
     Returns (W_f, W_b) numpy arrays and the final positions."""
     import torch
     ids = list(range(len(crystals))) if replica_ids is None else list(replica_ids)
@@ -75,53 +76,175 @@ def fl_batch(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec=ne.NE_MIXED, run
     return Wn[:, 0], Wn[:, 1], x
 
 
-def _fl_batch_auto(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec, skin, device, chunk, ids):
-    """fl_batch(runner="auto"): crystal runner, replicas that leave its range
-    moved to the general path one call at a time (ne_ctx_replica_status)."""
-    import torch
-    import warnings
-    n = len(crystals)
-    Ts = list(T) if np.ndim(T) else [T] * n
-    on_crystal, on_general = list(range(n)), []
-    res = {}
-    while on_crystal:
-        pick = lambda L: [L[q] for q in on_crystal]  # noqa: E731
+class BatchAdvancer:
+    """Advances a batch of crystal replicas over step ranges of the schedule:
+    the crystal runner for the replicas inside its stencil range and the
+    multi-kernel mixed path for the others, the two at once (a second
+    context from ne_ctx_clone, its own stream and host thread).  A replica
+    that leaves the range inside a chunk (NE_ERANGE: a hop or melting at high
+    T) is rerun for that chunk from its state before it on the multi-kernel
+    path and stays there.  Each replica's trajectory depends only on its own
+    inputs and noise stream, so a move changes rounding only.
+
+    mds, crystals, offsets, boxes, x0: as for ne_crystal_run_segment and
+    ne_switch_run_segment (x0: the sites, device [N][3]); chunk: steps per
+    crystal-runner call (None: the whole range in one call).  `moved` lists
+    the replicas on the multi-kernel path, `log` each call:
+    (path, replicas, first step, steps)."""
+
+    def __init__(self, ctx, mds, crystals, offsets, boxes, x0, chunk=None):
+        import torch
+        self.ctx, self.mds, self.crystals = ctx, list(mds), list(crystals)
+        self.offs, self.boxes, self.x0 = list(offsets), list(boxes), x0
+        self.chunk = chunk
+        self.moved, self.log = [], []
+        self._ctx_g = None
+        self._sc, self._sg = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def close(self):
+        if self._ctx_g is not None:
+            ne.ne_ctx_destroy(self._ctx_g)
+            self._ctx_g = None
+
+    def _general_ctx(self):
+        if self._ctx_g is None:
+            self._ctx_g = ne.ne_ctx_clone(self.ctx, self.offs[-1], len(self.mds))
+        return self._ctx_g
+
+    def _gather(self, idx, x, v, W):
+        """Compact copies of the replicas idx (views if idx is the batch)."""
+        import torch
+        if idx == list(range(len(self.mds))):
+            return x, v, W, self.x0, self.offs
+        so = [0]
+        for r in idx:
+            so.append(so[-1] + self.offs[r + 1] - self.offs[r])
+        xs = torch.empty((so[-1], 3), dtype=x.dtype, device=x.device)
+        vs, x0s = torch.empty_like(xs), torch.empty_like(xs)
+        Ws = torch.empty((len(idx), 2), dtype=W.dtype, device=W.device)
+        for q, r in enumerate(idx):
+            a, b = self.offs[r], self.offs[r + 1]
+            xs[so[q]:so[q + 1]].copy_(x[a:b])
+            vs[so[q]:so[q + 1]].copy_(v[a:b])
+            x0s[so[q]:so[q + 1]].copy_(self.x0[a:b])
+            Ws[q].copy_(W[r])
+        return xs, vs, Ws, x0s, so
+
+    def _scatter(self, idx, so, xs, vs, Ws, x, v, W):
+        if xs is x:
+            return
+        for q, r in enumerate(idx):
+            a, b = self.offs[r], self.offs[r + 1]
+            x[a:b].copy_(xs[so[q]:so[q + 1]])
+            v[a:b].copy_(vs[so[q]:so[q + 1]])
+            W[r].copy_(Ws[q])
+
+    def _general(self, idx, xs, vs, x0s, so, Ws, s0, ns):
+        ne.ne_switch_run_segment(self._general_ctx(), [self.mds[r] for r in idx], so, xs, vs, x0s,
+                                 [self.boxes[r] for r in idx], Ws, s0, ns, stream=self._sg.cuda_stream)
+        self.log.append(("general", list(idx), s0, ns))
+
+    def advance(self, x, v, W, s0, ns):
+        step = self.chunk or ns
+        for c0 in range(s0, s0 + ns, step):
+            self._advance_chunk(x, v, W, c0, min(step, s0 + ns - c0))
+
+    def _advance_chunk(self, x, v, W, c0, cn):
+        import threading
+        import torch
+        on_c = [r for r in range(len(self.mds)) if r not in self.moved]
+        gen = list(self.moved)
+        xc, vc, Wc, _, sc = self._gather(on_c, x, v, W) if on_c else (None,) * 5
+        xg, vg, Wg, x0g, sg = self._gather(gen, x, v, W) if gen else (None,) * 5
+        snap = (xc.clone(), vc.clone(), Wc.clone()) if on_c else None
+        torch.cuda.synchronize()
+        errs, th = [], None
+        if gen:
+            if not on_c:
+                self._general(gen, xg, vg, x0g, sg, Wg, c0, cn)
+            else:
+                def work():
+                    try:
+                        self._general(gen, xg, vg, x0g, sg, Wg, c0, cn)
+                    except Exception as e:  # noqa: BLE001 -- re-raised below
+                        errs.append(e)
+                th = threading.Thread(target=work)
+                th.start()
+        bad = []
         try:
-            Wf, Wb, x = fl_batch(ctx, pick(crystals), pick(Ts), pick(ks), pick(seeds), t_eq, t_s, mass, prec,
-                                 "crystal", skin, device, chunk, pick(ids))
-        except ne.NeError as e:
-            if "NE_ERANGE" not in str(e):
-                raise
-            st = ne.ne_ctx_replica_status(ctx, len(on_crystal))
-            bad = [on_crystal[q] for q in range(len(on_crystal)) if st[q] == ne.NE_ERANGE]
-            if not bad:
-                raise
-            warnings.warn("replicas %s left the crystal runner's stencil range; rerunning them on the "
-                          "multi-kernel path" % bad)
-            on_general += bad
-            on_crystal = [q for q in on_crystal if q not in bad]
-            continue
-        res.update(_split(on_crystal, crystals, Wf, Wb, x))
-        break
-    if on_general:
-        on_general.sort()
-        pick = lambda L: [L[q] for q in on_general]  # noqa: E731
-        Wf, Wb, x = fl_batch(ctx, pick(crystals), pick(Ts), pick(ks), pick(seeds), t_eq, t_s, mass, prec,
-                             "general", skin, device, chunk, pick(ids))
-        res.update(_split(on_general, crystals, Wf, Wb, x))
-    Wf = np.array([res[q][0] for q in range(n)])
-    Wb = np.array([res[q][1] for q in range(n)])
-    return Wf, Wb, torch.cat([res[q][2] for q in range(n)])
+            if on_c:
+                try:
+                    ne.ne_crystal_run_segment(self.ctx, [self.mds[r] for r in on_c], [self.crystals[r] for r in on_c],
+                                              xc, vc, Wc, c0, cn, stream=self._sc.cuda_stream)
+                    self.log.append(("crystal", on_c, c0, cn))
+                except ne.NeError as e:
+                    if "NE_ERANGE" not in str(e):
+                        raise
+                    st = ne.ne_ctx_replica_status(self.ctx, len(on_c))
+                    bad = [on_c[q] for q in range(len(on_c)) if st[q] == ne.NE_ERANGE]
+                    if not bad:
+                        raise
+                    self.log.append(("crystal", on_c, c0, cn))
+        finally:
+            if th is not None:
+                th.join()
+        if errs:
+            raise errs[0]
+        torch.cuda.synchronize()
+        if on_c:
+            self._scatter(on_c, sc, xc, vc, Wc, x, v, W)
+        if gen:
+            self._scatter(gen, sg, xg, vg, Wg, x, v, W)
+        if bad:
+            import warnings
+            warnings.warn("replicas %s left the crystal runner's stencil range at steps %d-%d; they continue "
+                          "on the multi-kernel path" % (bad, c0, c0 + cn))
+            # their state before the chunk, then the chunk on the multi-kernel path
+            for r in bad:
+                q = on_c.index(r)
+                a, b = self.offs[r], self.offs[r + 1]
+                if xc is x:
+                    x[a:b].copy_(snap[0][a:b])
+                    v[a:b].copy_(snap[1][a:b])
+                    W[r].copy_(snap[2][r])
+                else:
+                    x[a:b].copy_(snap[0][sc[q]:sc[q + 1]])
+                    v[a:b].copy_(snap[1][sc[q]:sc[q + 1]])
+                    W[r].copy_(snap[2][q])
+            xb, vb, Wb, x0b, sb = self._gather(bad, x, v, W)
+            torch.cuda.synchronize()
+            self._general(bad, xb, vb, x0b, sb, Wb, c0, cn)
+            torch.cuda.synchronize()
+            self._scatter(bad, sb, xb, vb, Wb, x, v, W)
+            self.moved = sorted(self.moved + bad)
+        torch.cuda.synchronize()
 
 
-def _split(idx, crystals, Wf, Wb, x):
-    out, o = {}, 0
-    for j, q in enumerate(idx):
-        lat, a, n = crystals[q]
-        na = (2 if lat == ne.NE_BCC else 4) * n ** 3
-        out[q] = (Wf[j], Wb[j], x[o:o + na])
-        o += na
-    return out
+def _fl_batch_auto(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec, skin, device, chunk, ids):
+    """fl_batch(runner="auto") on a BatchAdvancer (chunks of 5000 steps unless given)."""
+    import torch
+    x0s, offs, boxes, mds, crs = [], [0], [], [], []
+    Ts = list(T) if np.ndim(T) else [T] * len(crystals)
+    for r, ((lat, a, n), k, seed, Tr) in enumerate(zip(crystals, ks, seeds, Ts)):
+        x0, box = crystal_sites(lat, a, n)
+        x0s.append(x0)
+        offs.append(offs[-1] + len(x0))
+        boxes.append(box)
+        crs.append((lat, a, n, n, n))
+        mds.append(ne.md_params(T=Tr, mass=mass, k_spring=k, skin=skin, prec=ne.NE_MIXED, t_eq=t_eq, t_s=t_s,
+                                seed=seed, replica=ids[r], fix_cm=1))
+    x0 = torch.tensor(np.concatenate(x0s), dtype=torch.float64, device=device)
+    x, v = x0.clone(), torch.zeros_like(x0)
+    for r, m in enumerate(mds):
+        ne.ne_init_velocities(ctx, m, v[offs[r]:offs[r + 1]])
+    W = torch.zeros((len(mds), 2), dtype=torch.float64, device=device)
+    adv = BatchAdvancer(ctx, mds, crs, offs, boxes, x0, chunk=chunk or 5000)
+    try:
+        adv.advance(x, v, W, 0, 2 * t_eq + 2 * t_s)
+    finally:
+        adv.close()
+    Wn = W.cpu().numpy()
+    return Wn[:, 0], Wn[:, 1], x
 
 
 def free_energy(lattice, a, n, T, mass, k, W_f, W_b):

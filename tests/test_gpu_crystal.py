@@ -257,40 +257,68 @@ def test_crystal_runner_small_hot_boxes_track_oracle(ctx, pot, lat, n):
     assert Wg[1] == pytest.approx(ro["W_b"], rel=1e-5, abs=1e-3)
 
 
-def test_fl_batch_auto_reruns_only_the_replicas_out_of_range(ctx, monkeypatch):
-    """runner='auto': when the crystal runner reports NE_ERANGE for one
-    replica (a stand-in raises it and ne_ctx_replica_status names replica 1,
-    since a crystal that stays solid never leaves the range), that replica
-    alone is rerun on the multi-kernel mixed path with its own Philox index;
-    the others are rerun on the crystal runner without it.  Each result
-    equals the direct run of its subset bit for bit."""
+def test_auto_runner_moves_out_of_range_replicas_to_the_multikernel_path(ctx, monkeypatch):
+    """fl_batch(runner='auto') on the BatchAdvancer, chunks of 40 steps: when
+    the crystal runner reports NE_ERANGE for replica 1 in the second chunk (a
+    stand-in raises it after the real call and ne_ctx_replica_status names
+    replica 1, since a crystal that stays solid never leaves the range),
+    replica 1 goes back to its state before that chunk and continues on the
+    multi-kernel mixed path (second context, concurrent with the crystal
+    runner for the others).  With the cluster size fixed, replicas 0 and 2
+    equal a plain crystal-runner run bit for bit, and replica 1 equals 40
+    crystal-runner steps followed by the multi-kernel path to rounding."""
     from paper_2201_04622_gb300 import workflow as WF
-    real = WF.fl_batch
-    crystals = [(O.BCC, W.A_BCC, 6)] * 3
-    args = (ctx, crystals, 1400.0, [2.38] * 3, [1, 2, 3], 20, 40, MASS)
+    real = ne.ne_crystal_run_segment
     calls = []
 
-    def fake(*a, **kw):
-        runner, ids = a[9], list(a[13])
-        calls.append((runner, ids))
-        if runner == "crystal" and 1 in ids:
+    def fake(c, mds, crs, x, v, W, s0, ns, stream=None):
+        real(c, mds, crs, x, v, W, s0, ns, stream=stream)
+        calls.append((s0, len(mds)))
+        if s0 == 40 and len(mds) == 3:
             raise ne.NeError(ne.NE_ERANGE, "ne_crystal_run_segment", "stand-in")
-        return real(*a, **kw)
 
-    monkeypatch.setattr(WF, "fl_batch", fake)
-    monkeypatch.setattr(ne, "ne_ctx_replica_status",
-                        lambda c, n: np.array([ne.NE_OK, ne.NE_ERANGE, ne.NE_OK][:n], dtype=np.int32))
-    with pytest.warns(UserWarning):
-        Wf, Wb, x = real(*args, runner="auto", skin=1.0)
-    assert calls == [("crystal", [0, 1, 2]), ("crystal", [0, 2]), ("general", [1])]
-    monkeypatch.undo()
-    Wc, Wbc, xc = WF.fl_batch(ctx, [crystals[0], crystals[2]], 1400.0, [2.38] * 2, [1, 3], 20, 40, MASS,
-                              runner="crystal", replica_ids=[0, 2])
-    Wg, Wbg, xg = WF.fl_batch(ctx, [crystals[1]], 1400.0, [2.38], [2], 20, 40, MASS,
-                              runner="general", skin=1.0, replica_ids=[1])
-    assert np.array_equal(Wf, [Wc[0], Wg[0], Wc[1]]) and np.array_equal(Wb, [Wbc[0], Wbg[0], Wbc[1]])
-    na = len(xg)
-    assert torch.equal(x, torch.cat([xc[:na], xg, xc[na:]]))
+    crystals = [(O.BCC, W.A_BCC, 6)] * 3
+    args = (ctx, crystals, 1400.0, [2.38] * 3, [1, 2, 3], 20, 40, MASS)
+    ne.ne_ctx_set_cluster_size(ctx, 2)
+    try:
+        monkeypatch.setattr(ne, "ne_crystal_run_segment", fake)
+        monkeypatch.setattr(ne, "ne_ctx_replica_status",
+                            lambda c, n: np.array([ne.NE_OK, ne.NE_ERANGE, ne.NE_OK][:n], dtype=np.int32))
+        with pytest.warns(UserWarning):
+            Wf, Wb, x = WF.fl_batch(*args, runner="auto", skin=1.0, chunk=40)
+        monkeypatch.undo()
+        assert calls == [(0, 3), (40, 3), (80, 2)]
+        # reference: the crystal runner for all three, in one call
+        Wc, Wbc, xc = WF.fl_batch(*args, runner="crystal")
+        # reference for replica 1: 40 crystal-runner steps, then the multi-kernel path
+        mass = MASS
+        mds, crs, x0s, offs = [], [], [], [0]
+        for r, (lat, a, n) in enumerate(crystals):
+            mds.append(ne.md_params(T=1400.0, mass=mass, k_spring=2.38, skin=1.0, prec=ne.NE_MIXED, t_eq=20,
+                                    t_s=40, seed=r + 1, replica=r, fix_cm=1))
+            x0, box = WF.crystal_sites(lat, a, n)
+            x0s.append(x0)
+            crs.append((lat, a, n, n, n))
+            offs.append(offs[-1] + len(x0))
+        X0 = T(np.concatenate(x0s))
+        xr, vr = X0.clone(), torch.zeros_like(X0)
+        for r, m in enumerate(mds):
+            ne.ne_init_velocities(ctx, m, vr[offs[r]:offs[r + 1]])
+        Wr = torch.zeros((3, 2), dtype=torch.float64, device=DEV)
+        ne.ne_crystal_run_segment(ctx, mds, crs, xr, vr, Wr, 0, 40)
+        a1, b1 = offs[1], offs[2]
+        x1, v1, W1 = xr[a1:b1].clone(), vr[a1:b1].clone(), Wr[1:2].clone()
+        ne.ne_switch_run_segment(ctx, [mds[1]], [0, b1 - a1], x1, v1, X0[a1:b1].contiguous(),
+                                 [WF.crystal_sites(*crystals[1])[1]], W1, 40, 80)
+    finally:
+        ne.ne_ctx_set_cluster_size(ctx, 0)
+    assert Wf[0] == Wc[0] and Wf[2] == Wc[2] and Wb[0] == Wbc[0] and Wb[2] == Wbc[2]
+    assert torch.equal(x[:a1], xc[:a1]) and torch.equal(x[b1:], xc[b1:])
+    # the multi-kernel path resumes bit for bit only while no atom has strayed
+    # skin/2 from its site (its list is rebuilt from positions after that), so
+    # replica 1 (split at step 80 there, not in the reference) agrees to rounding
+    assert abs(Wf[1] - float(W1[0, 0])) < 1e-6 * (b1 - a1) and abs(Wb[1] - float(W1[0, 1])) < 1e-6 * (b1 - a1)
+    assert float((x[a1:b1] - x1).abs().max()) < 1e-5
 
 
 def test_fl1400_full_length_works_vs_oracle(ctx):
