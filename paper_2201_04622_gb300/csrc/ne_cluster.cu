@@ -235,10 +235,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     float2* s_rho = (float2*)(s_f + SLOTS);                       // [SLOTS] double-float
     float* s_slotM = (float*)(s_rho + SLOTS);                     // [2][16] max |u| per CTA
     float* s_red = s_slotM + 32;                                  // [NWARP][NRED][2]
-    float* s_misc = s_red + NWARP * NRED * 2;                     // [8]
     // spline intervals [k_lo, nk - 1) of phi, then of f: separate arrays, so
     // consecutive intervals fall in consecutive 16-byte bank groups
-    float4* s_tabP = (float4*)(((size_t)(s_misc + 8) + 15) & ~(size_t)15);  // [nk-1-k_lo]
+    float4* s_tabP = (float4*)(((size_t)(s_red + NWARP * NRED * 2) + 15) & ~(size_t)15);  // [nk-1-k_lo]
     const int n_int = tab.nk - 1 - k_lo;  // intervals of the r grid held in shared memory
     float4* s_tabF = s_tabP + n_int;                                           // [nk-1-k_lo]
     {
@@ -645,7 +644,7 @@ size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
     b = (b + 15) & ~(size_t)15;
     b += sizeof(float) * (2 * 16 * NSV + NSV);
     b += 16;  // alignment of s_f
-    b += sizeof(float4) * SLOTS + sizeof(float2) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2 + 8);
+    b += sizeof(float4) * SLOTS + sizeof(float2) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2);
     return ((b + 15) & ~(size_t)15) + 16;  // + alignment of the tables
 }
 
