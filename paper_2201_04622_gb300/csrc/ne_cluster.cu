@@ -38,8 +38,8 @@
 // Precision: pair distances, splines, forces, velocities and the OU update
 // in FP32; rho as a double-float; positions in fixed point (2^-32 A,
 // registers); the work W in FP64; the replica energies as double-float pairs
-// within a CTA and FP64 across the cluster, the sums for the mean removal in
-// FP32 within a CTA and FP64 across it.
+// (within a CTA and across the cluster), the sums for the mean removal in
+// FP32.
 #include <algorithm>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
