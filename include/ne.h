@@ -316,6 +316,24 @@ ne_status ne_switch_run_segment(ne_ctx* ctx, const ne_md_params* md, int n_rep,
                                 const double* x0_dev, const double* boxes_host, double* W_dev,
                                 long long step_begin, long long n_steps, void* stream);
 
+/* ne_switch_run_segment that also accumulates the parameter gradient along
+ * the run (the backward pass of Sec. III.B's switching runs; the paper has no
+ * gradient): after the force evaluation at each x_k, k = step_begin ..
+ * step_begin + n_steps, gtheta_dev += w_dev[k - step_begin] * dU/dtheta(x_k),
+ * summed over the replicas, with the step's own neighbour list and rho (no
+ * recomputation; a zero weight skips the step's backward).  w_dev: device,
+ * double [n_steps + 1]; gtheta_dev: device, double [3][n_knots][2] (phi, f,
+ * F; value and slope per knot), accumulated.  E.g. w = 1 every `stride`
+ * steps at lambda = 0 gives sum dU/dtheta for <dU/dtheta> = dF_0/dtheta, and
+ * w_k = lambda_k - lambda_(k-stride) over a switch the derivative of W at
+ * fixed trajectory.  Mixed precision bins in FP32 per block and sums them in
+ * FP64; FP64 adds with FP64 atomics.  Errors as ne_switch_run_segment. */
+ne_status ne_switch_run_segment_grad(ne_ctx* ctx, const ne_md_params* md, int n_rep,
+                                     const int* offsets_host, double* x_dev, double* v_dev,
+                                     const double* x0_dev, const double* boxes_host, double* W_dev,
+                                     long long step_begin, long long n_steps, const double* w_dev,
+                                     double* gtheta_dev, void* stream);
+
 /* A crystal replica: nx*ny*nz cells of a bcc or fcc lattice with parameter a;
  * its sites r0 and atom order are those of ne_create_crystal. */
 typedef struct {

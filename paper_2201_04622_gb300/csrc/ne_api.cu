@@ -316,10 +316,27 @@ void force_eval(const DevBatch& B, const Sched& S, bool mixed, const long long* 
 }
 
 // One fused step of the schedule (device step = *ctr + j).
+// Optional parameter gradient along a run: after the force evaluation at
+// x_k, gtheta += w[k - s_off] dU/dtheta(x_k) (the step's own list and rho).
+struct GradAcc {
+    double* gtheta;
+    const double* w;
+    float* bins;
+    int nbb;
+    long long s_off;
+};
+
+void grad_at(const DevBatch& B, bool mixed, const GradAcc* ga, const long long* ctr, int j, cudaStream_t st)
+{
+    if (ga) ne::launch_backward(B, mixed, 0.0, nullptr, ga->gtheta, ga->bins, ga->nbb, true, st, ga->w, ctr, j,
+                                ga->s_off, false);
+}
+
 void one_step(const DevBatch& B, const Sched& S, bool mixed, const long long* ctr, int j, int first,
-              cudaStream_t st)
+              cudaStream_t st, const GradAcc* ga = nullptr)
 {
     force_eval(B, S, mixed, ctr, j, 1, 0, st);
+    grad_at(B, mixed, ga, ctr, j, st);
     ne::launch_step(B, S, mixed, ctr, j, first ? 0 : 1, 1, st);
     if (B.npt_any) ne::launch_npt_box(B, S, ctr, j, st);
 }
@@ -330,7 +347,7 @@ void one_step(const DevBatch& B, const Sched& S, bool mixed, const long long* ct
 // every chunk.
 ne_status run_steps(ne_ctx* ctx, const DevBatch& B, const Sched& S, bool mixed, long long s_begin,
                     long long n_steps, cudaStream_t st, double* msd_acc = nullptr,
-                    long long msd_from = 0, int msd_stride = 0)
+                    long long msd_from = 0, int msd_stride = 0, const GradAcc* ga = nullptr)
 {
     long long* ctr = ctx->step_ctr;
     NE_CU(cudaMemcpyAsync(ctr, &s_begin, sizeof(long long), cudaMemcpyHostToDevice, st));
@@ -342,7 +359,7 @@ ne_status run_steps(ne_ctx* ctx, const DevBatch& B, const Sched& S, bool mixed, 
     long long s = 0;
     // first step: no closing kick
     if (n_steps > 0) {
-        one_step(B, S, mixed, ctr, 0, 1, st);
+        one_step(B, S, mixed, ctr, 0, 1, st, ga);
         ne::launch_advance(ctr, 1, st);
         s = 1;
         if (msd_acc && msd_stride > 0 && s > msd_from && (s - msd_from) % msd_stride == 0)
@@ -360,7 +377,7 @@ ne_status run_steps(ne_ctx* ctx, const DevBatch& B, const Sched& S, bool mixed, 
         NE_CU(cudaEventRecord(ev, st));
         NE_CU(cudaStreamWaitEvent(cs, ev, 0));
         NE_CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        for (int j = 0; j < G; ++j) one_step(B, S, mixed, ctr, j, 0, cs);
+        for (int j = 0; j < G; ++j) one_step(B, S, mixed, ctr, j, 0, cs, ga);
         ne::launch_advance(ctr, G, cs);
         cudaError_t ce = cudaStreamEndCapture(cs, &graph);
         if (ce != cudaSuccess) {
@@ -387,13 +404,14 @@ ne_status run_steps(ne_ctx* ctx, const DevBatch& B, const Sched& S, bool mixed, 
         if (ce != cudaSuccess) return fail(ctx, NE_ECUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
     }
     for (; s < n_steps; ++s) {
-        one_step(B, S, mixed, ctr, 0, 0, st);
+        one_step(B, S, mixed, ctr, 0, 0, st, ga);
         ne::launch_advance(ctr, 1, st);
         if (msd_acc && msd_stride > 0 && s + 1 > msd_from && (s + 1 - msd_from) % msd_stride == 0)
             ne::launch_msd_sample(B, msd_acc, st);
     }
     // closing half kick of the last step
     force_eval(B, S, mixed, ctr, 0, 0, 0, st);
+    grad_at(B, mixed, ga, ctr, 0, st);
     ne::launch_step(B, S, mixed, ctr, 0, 1, 0, st);
     NE_CU(cudaGetLastError());
     return NE_OK;
@@ -941,7 +959,7 @@ static ne_status check_batch(ne_ctx* ctx, const ne_md_params* md, int n_rep, con
 static ne_status segment_impl(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* off, double* x,
                               double* v, const double* x0, const double* boxes, double* W, double* wcum,
                               double* trace, int trace_stride, long long s_begin, long long n_steps,
-                              cudaStream_t st)
+                              cudaStream_t st, const double* gw = nullptr, double* gtheta = nullptr)
 {
     const long long S_total = 2 * md[0].t_eq + 2 * md[0].t_s;
     if (s_begin < 0 || n_steps < 0 || s_begin + n_steps > S_total)
@@ -955,12 +973,28 @@ static ne_status segment_impl(ne_ctx* ctx, const ne_md_params* md, int n_rep, co
     a.trace = trace;
     a.trace_stride = trace_stride;
     a.trace_rows = trace ? (int)((S_total - 1) / (trace_stride > 0 ? trace_stride : 1) + 1) : 0;
+    a.rho = gtheta ? ctx->rho : nullptr;  // the backward pass reads rho (FP64) of each step
     DevBatch B;
     ne_status s = setup_batch(ctx, n_rep, off, boxes, md, 1, -1.0, B, a, st);
     if (s) return s;
     Sched S = make_sched(md[0]);
     if (n_steps == 0) return finish(ctx, st);
-    s = run_steps(ctx, B, S, md[0].prec == NE_MIXED, s_begin, n_steps, st);
+    const bool mixed = md[0].prec == NE_MIXED;
+    GradAcc ga{gtheta, gw, nullptr, 0, s_begin};
+    if (gtheta) {
+        ga.nbb = ne::backward_bin_blocks(B);
+        if (mixed && ga.nbb > ctx->bins_blocks) {
+            if (ctx->bins) cudaFree(ctx->bins);
+            ctx->bins = nullptr;
+            ctx->bins_blocks = 0;
+            NE_CU(cudaMalloc((void**)&ctx->bins, sizeof(float) * (size_t)ga.nbb * 6 * ctx->eam.n_knots));
+            ctx->bins_blocks = ga.nbb;
+        }
+        ga.bins = ctx->bins;
+        // the backward kernel's shared-memory attribute, once, outside any capture
+        if (mixed) NE_CU(ne::prepare_backward(B));
+    }
+    s = run_steps(ctx, B, S, mixed, s_begin, n_steps, st, nullptr, 0, 0, gtheta ? &ga : nullptr);
     if (s) return s;
     return finish(ctx, st);
 }
@@ -999,6 +1033,21 @@ static ne_status switch_run_impl(ne_ctx* ctx, const ne_md_params* md, int n_rep,
         cudaFree(wcum);
     }
     return s;
+}
+
+ne_status ne_switch_run_segment_grad(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* offsets_host,
+                                     double* x_dev, double* v_dev, const double* x0_dev, const double* boxes_host,
+                                     double* W_dev, long long step_begin, long long n_steps, const double* w_dev,
+                                     double* gtheta_dev, void* stream)
+{
+    if (!ctx || !md || !offsets_host || !x_dev || !v_dev || !x0_dev || !boxes_host || !W_dev || n_rep < 1 ||
+        !w_dev || !gtheta_dev)
+        return NE_EINVAL;
+    if (n_rep > ctx->max_rep) return fail(ctx, NE_ENOMEM, "replica count exceeds the context");
+    ne_status s = check_batch(ctx, md, n_rep, offsets_host);
+    if (s) return s;
+    return segment_impl(ctx, md, n_rep, offsets_host, x_dev, v_dev, x0_dev, boxes_host, W_dev, nullptr, nullptr,
+                        0, step_begin, n_steps, (cudaStream_t)stream, w_dev, gtheta_dev);
 }
 
 ne_status ne_switch_run_segment(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* offsets_host,

@@ -363,12 +363,29 @@ __device__ __forceinline__ void hermite_wf(float u, float h, float w[4])
     w[3] = (u3 - u2) * h;
 }
 
+// The weight gE of a backward launch: the host's value, or, inside a run,
+// gw[step - s_off] read on the device for step = *ctr + j, so a captured
+// graph replays the per-step weights.  A zero weight skips the launch's work.
+struct BwdWeight {
+    double gE;
+    const double* gw;
+    const long long* ctr;
+    int j;
+    long long s_off;
+};
+
+__device__ __forceinline__ double bwd_weight(const BwdWeight& W)
+{
+    return W.gw ? W.gw[*W.ctr + W.j - W.s_off] : W.gE;
+}
+
 // Mixed precision: FP32 basis weights accumulated in shared-memory FP32 bins
 // per block, flushed to bins[block][3*nk*2]; k_bins_reduce then sums the
 // blocks in FP64 in fixed order.
 template <int TPA>
-__global__ void __launch_bounds__(NE_TILE* TPA) k_backward_mixed(DevBatch B, float* __restrict__ bins)
+__global__ void __launch_bounds__(NE_TILE* TPA) k_backward_mixed(DevBatch B, float* __restrict__ bins, BwdWeight W)
 {
+    if (bwd_weight(W) == 0.0) return;
     extern __shared__ float sb[];
     const int nk = B.tab.nk;
     const int nb = 3 * nk * 2;
@@ -420,11 +437,12 @@ __global__ void __launch_bounds__(NE_TILE* TPA) k_backward_mixed(DevBatch B, flo
     for (int q = threadIdx.x; q < nb; q += blockDim.x) out[q] = sb[q];
 }
 
-__global__ void k_bins_reduce(const float* __restrict__ bins, int n_blocks, int nb, double gE,
+__global__ void k_bins_reduce(const float* __restrict__ bins, int n_blocks, int nb, BwdWeight W,
                               double* __restrict__ gtheta, int accumulate)
 {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nb) return;
+    const double gE = bwd_weight(W);
+    if (q >= nb || gE == 0.0) return;
     double acc = 0.0;
     for (int b = 0; b < n_blocks; ++b) acc += (double)bins[(size_t)b * nb + q];
     gtheta[q] = (accumulate ? gtheta[q] : 0.0) + gE * acc;
@@ -433,8 +451,10 @@ __global__ void k_bins_reduce(const float* __restrict__ bins, int n_blocks, int 
 // FP64 path: FP64 basis weights added straight into gtheta (pre-zeroed) with
 // FP64 atomics, scaled by gE.
 template <int TPA>
-__global__ void __launch_bounds__(NE_TILE* TPA) k_backward_fp64(DevBatch B, double gE, double* gtheta)
+__global__ void __launch_bounds__(NE_TILE* TPA) k_backward_fp64(DevBatch B, BwdWeight W, double* gtheta)
 {
+    const double gE = bwd_weight(W);
+    if (gE == 0.0) return;
     const int nk = B.tab.nk;
     const int tile = blockIdx.x;
     const int rep = B.tile_rep[tile];
@@ -579,6 +599,18 @@ void launch_force(const DevBatch& B, const Sched& S, bool mixed, const long long
         force_tpa<false>(B, S, step_base, j, want_noise, st);
 }
 
+cudaError_t prepare_backward(const DevBatch& B)
+{
+    const int smem = (int)(sizeof(float) * 6 * (size_t)B.tab.nk);
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    switch (B.tpa) {
+    case 1: return cudaFuncSetAttribute(k_backward_mixed<1>, a, smem);
+    case 2: return cudaFuncSetAttribute(k_backward_mixed<2>, a, smem);
+    case 4: return cudaFuncSetAttribute(k_backward_mixed<4>, a, smem);
+    default: return cudaFuncSetAttribute(k_backward_mixed<8>, a, smem);
+    }
+}
+
 int backward_bin_blocks(const DevBatch& B)
 {
     int nb = B.n_tiles < 296 ? B.n_tiles : 296;
@@ -598,40 +630,34 @@ void launch_virial(const DevBatch& B, double* out, cudaStream_t st)
 }
 
 void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, double* gtheta,
-                     float* bins, int n_bin_blocks, bool accumulate, cudaStream_t st)
+                     float* bins, int n_bin_blocks, bool accumulate, cudaStream_t st, const double* gw,
+                     const long long* ctr, int j, long long s_off, bool set_attr)
 {
     (void)gx;
     const int nk = B.tab.nk;
     const int nb = 3 * nk * 2;
+    const BwdWeight W{gE, gw, ctr, j, s_off};
     if (mixed) {
         size_t smem = (size_t)nb * sizeof(float);
+#define NE_BWD(T)                                                                                        \
+    if (set_attr) cudaFuncSetAttribute(k_backward_mixed<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    k_backward_mixed<T><<<n_bin_blocks, NE_TILE * T, smem, st>>>(B, bins, W)
         switch (B.tpa) {
-        case 1:
-            cudaFuncSetAttribute(k_backward_mixed<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_backward_mixed<1><<<n_bin_blocks, NE_TILE * 1, smem, st>>>(B, bins);
-            break;
-        case 2:
-            cudaFuncSetAttribute(k_backward_mixed<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_backward_mixed<2><<<n_bin_blocks, NE_TILE * 2, smem, st>>>(B, bins);
-            break;
-        case 4:
-            cudaFuncSetAttribute(k_backward_mixed<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_backward_mixed<4><<<n_bin_blocks, NE_TILE * 4, smem, st>>>(B, bins);
-            break;
-        default:
-            cudaFuncSetAttribute(k_backward_mixed<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_backward_mixed<8><<<n_bin_blocks, NE_TILE * 8, smem, st>>>(B, bins);
-            break;
+        case 1: NE_BWD(1); break;
+        case 2: NE_BWD(2); break;
+        case 4: NE_BWD(4); break;
+        default: NE_BWD(8); break;
         }
-        k_bins_reduce<<<(nb + 255) / 256, 256, 0, st>>>(bins, n_bin_blocks, nb, gE, gtheta, accumulate ? 1 : 0);
+#undef NE_BWD
+        k_bins_reduce<<<(nb + 255) / 256, 256, 0, st>>>(bins, n_bin_blocks, nb, W, gtheta, accumulate ? 1 : 0);
     } else {
         if (!accumulate) cudaMemsetAsync(gtheta, 0, sizeof(double) * nb, st);
         dim3 g(B.n_tiles);
         switch (B.tpa) {
-        case 1: k_backward_fp64<1><<<g, NE_TILE * 1, 0, st>>>(B, gE, gtheta); break;
-        case 2: k_backward_fp64<2><<<g, NE_TILE * 2, 0, st>>>(B, gE, gtheta); break;
-        case 4: k_backward_fp64<4><<<g, NE_TILE * 4, 0, st>>>(B, gE, gtheta); break;
-        default: k_backward_fp64<8><<<g, NE_TILE * 8, 0, st>>>(B, gE, gtheta); break;
+        case 1: k_backward_fp64<1><<<g, NE_TILE * 1, 0, st>>>(B, W, gtheta); break;
+        case 2: k_backward_fp64<2><<<g, NE_TILE * 2, 0, st>>>(B, W, gtheta); break;
+        case 4: k_backward_fp64<4><<<g, NE_TILE * 4, 0, st>>>(B, W, gtheta); break;
+        default: k_backward_fp64<8><<<g, NE_TILE * 8, 0, st>>>(B, W, gtheta); break;
         }
     }
 }

@@ -276,9 +276,15 @@ void launch_spring(const double* x, const double* x0, int n, double k, double* f
                    double* scratch, cudaStream_t st);
 void launch_export(const DevBatch& B, bool mixed, double* f_out, double* e_out, cudaStream_t st);
 void launch_msd_sample(const DevBatch& B, double* acc, cudaStream_t st);
+// gE, or with gw != nullptr the per-step weight gw[*ctr + j - s_off] read on
+// the device (runs replayed from graphs); set_attr: set the kernel's shared-
+// memory attribute (not inside a stream capture)
 void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, double* gtheta,
-                     float* bins, int n_bin_blocks, bool accumulate, cudaStream_t st);
+                     float* bins, int n_bin_blocks, bool accumulate, cudaStream_t st,
+                     const double* gw = nullptr, const long long* ctr = nullptr, int j = 0,
+                     long long s_off = 0, bool set_attr = true);
 int backward_bin_blocks(const DevBatch& B);
+cudaError_t prepare_backward(const DevBatch& B);  // the mixed backward kernel's shared-memory attribute
 void launch_virial(const DevBatch& B, double* out, cudaStream_t st);
 void launch_npt_box(const DevBatch& B, const Sched& S, const long long* step_base, int j, cudaStream_t st);
 }  // namespace ne

@@ -28,7 +28,7 @@ SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_clone", "ne_ctx_set_theta"
            "ne_create_crystal", "ne_create_crystal_ca", "ne_eam_energy_forces", "ne_eam_virial", "ne_eam_energy_forces_noalloc",
            "ne_spring_forces",
            "ne_eam_backward", "ne_eam_backward_acc", "ne_noise", "ne_init_velocities", "ne_langevin_step",
-           "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment",
+           "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment", "ne_switch_run_segment_grad",
            "ne_profile_segment", "ne_crystal_run_segment",
            "ne_msd_fit", "ne_free_energy", "ne_jarzynski",
            "ne_rs_free_energy"]
@@ -104,6 +104,7 @@ def load(build_if_missing: bool = True):
                 "ne_rs_run": [p, p, d, p, p, p, i, p, p, p, p],
                 "ne_switch_run_batched": [p, p, i, p, p, p, p, p, p, p, p],
                 "ne_switch_run_segment": [p, p, i, p, p, p, p, p, p, ll, ll, p],
+                "ne_switch_run_segment_grad": [p, p, i, p, p, p, p, p, p, ll, ll, p, p, p],
                 "ne_profile_segment": [p, p, i, p, p, p, p, p, p, ll, ll, p, p, p],
                 "ne_crystal_run_segment": [p, p, p, i, p, p, p, ll, ll, p],
                 "ne_msd_fit": [p, p, p, p, p, i, p, ll, ll, i, p, p, p],
@@ -370,6 +371,16 @@ def ne_switch_run_segment(ctx, mds, offsets, x, v, x0, boxes, W, step_begin, n_s
     _err(ctx, load().ne_switch_run_segment(ctx, arr, n_rep, off, _dev(x), _dev(v), _dev(x0), bx,
                                            _dev(W, 2 * n_rep), int(step_begin), int(n_steps),
                                            _stream(stream)), "ne_switch_run_segment")
+
+
+def ne_switch_run_segment_grad(ctx, mds, offsets, x, v, x0, boxes, W, step_begin, n_steps, w, gtheta, stream=None):
+    """ne_switch_run_segment plus gtheta += sum_k w[k - step_begin] dU/dtheta(x_k)
+    (w: device float64 [n_steps + 1]; gtheta: device float64 [3 * n_knots * 2])."""
+    n_rep, arr, off, bx = _batch_args(mds, offsets, boxes)
+    _err(ctx, load().ne_switch_run_segment_grad(ctx, arr, n_rep, off, _dev(x), _dev(v), _dev(x0), bx,
+                                                _dev(W, 2 * n_rep), int(step_begin), int(n_steps),
+                                                _dev(w, int(n_steps) + 1), _dev(gtheta), _stream(stream)),
+         "ne_switch_run_segment_grad")
 
 
 def ne_profile_segment(ctx, mds, offsets, x, v, x0, boxes, W, step_begin, n_steps, stream=None):

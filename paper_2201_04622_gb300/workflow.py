@@ -386,8 +386,8 @@ def theta_gradient(ctx, lattice, a, n, T, mass, k, t_eq, t_s, n_knots, seed=1, s
                    skin=1.0, device="cuda"):
     """Gradients with respect to the spline knots theta along one FL run
     (equilibration at lambda = 0, then the forward switch of Sec. III.B),
-    with dU/dtheta from the backward pass (rho recomputed) every `stride`
-    steps:
+    with dU/dtheta from the backward pass every `stride` steps, fused into
+    the run (ne_switch_run_segment_grad: the step's own list and rho):
       dF_dtheta  -- <dU/dtheta> over the equilibration at lambda = 0, the
                     free energy's parameter gradient dF_0/dtheta;
       dWf_dtheta -- sum over the forward switch of dlambda dU/dtheta(x), the
@@ -406,16 +406,24 @@ def theta_gradient(ctx, lattice, a, n, T, mass, k, t_eq, t_s, n_knots, seed=1, s
     Wd = torch.zeros((1, 2), dtype=torch.float64, device=device)
     g_eq = torch.zeros(6 * n_knots, dtype=torch.float64, device=device)
     g_sw = torch.zeros(6 * n_knots, dtype=torch.float64, device=device)
-    n_eq, s = 0, 0
-    while s < t_eq + t_s:
-        step = min(stride, t_eq + t_s - s)
-        ne.ne_switch_run_segment(ctx, [md], [0, nat], x, v, x0, [box], Wd, s, step)
-        s0, s = s, s + step
+    # sample points s = stride, 2 stride, ... (and the end of the switch):
+    # weight 1 at lambda = 0, the lambda increment since the previous sample
+    # during the switch; one fused run per phase (ne_switch_run_segment_grad)
+    S = t_eq + t_s
+    samples = list(range(stride, S, stride)) + [S]
+    w_eq = np.zeros(t_eq + 1)
+    w_sw = np.zeros(t_s + 1)
+    n_eq, prev = 0, 0
+    for s in samples:
         if s <= t_eq:
-            ne.ne_eam_backward_acc(ctx, prec, x, box, 1.0, g_eq)
+            w_eq[s] = 1.0
             n_eq += 1
         else:
-            dl = lambda_fl2((s - t_eq) / t_s) - lambda_fl2(max(s0 - t_eq, 0) / t_s)
-            ne.ne_eam_backward_acc(ctx, prec, x, box, dl, g_sw)
+            w_sw[s - t_eq] = lambda_fl2((s - t_eq) / t_s) - lambda_fl2(max(prev - t_eq, 0) / t_s)
+        prev = s
+    for s0, ns, w, g in ((0, t_eq, w_eq, g_eq), (t_eq, t_s, w_sw, g_sw)):
+        if ns > 0:
+            wd = torch.tensor(w, dtype=torch.float64, device=device)
+            ne.ne_switch_run_segment_grad(ctx, [md], [0, nat], x, v, x0, [box], Wd, s0, ns, wd, g)
     shape = (3, n_knots, 2)
     return (g_eq.cpu().numpy() / max(n_eq, 1)).reshape(shape), g_sw.cpu().numpy().reshape(shape), n_eq

@@ -646,3 +646,41 @@ def test_theta_gradient_workflow(ctx):
     u = ((th_np[0] * dF[0]).sum() + (th_np[2] * dF[2]).sum()) / 432
     assert -4.35 < u < -4.1
     assert np.all(np.isfinite(dW)) and np.abs(dW).max() > 0
+
+
+@pytest.mark.parametrize("prec", [ne.NE_FP64, ne.NE_MIXED])
+def test_fused_run_gradient_equals_separate_backward_calls(ctx, prec):
+    """ne_switch_run_segment_grad accumulates w_k dU/dtheta(x_k) inside the run
+    from the step's own list and rho.  Against the same run cut into 10-step
+    segments with ne_eam_backward_acc (fresh list, rho recomputed) at each cut:
+    the same trajectory (bitwise while atoms stay near their sites) and the
+    same gradients up to the order of the atomic additions (FP64 1e-12,
+    mixed FP32 bins 1e-5 of the largest entry)."""
+    nk = W.EAM_FE_LIKE["n_knots"]
+    x0_np, box = crystal(O.BCC, 6)
+    nat = len(x0_np)
+    md = ne.md_params(T=300.0, mass=MASS, k_spring=4.0, skin=1.0, prec=prec, t_eq=60, t_s=90, seed=3,
+                      replica=0, fix_cm=1)
+    X0 = T(x0_np)
+    v0 = torch.zeros_like(X0)
+    ne.ne_init_velocities(ctx, md, v0)
+    S, stride = 150, 10
+    w = np.zeros(S + 1)
+    w[stride::stride] = np.linspace(0.5, 2.0, S // stride)  # arbitrary nonzero weights every stride steps
+    # fused
+    x, v = X0.clone(), v0.clone()
+    Wd = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
+    g1 = torch.zeros(6 * nk, dtype=torch.float64, device=DEV)
+    ne.ne_switch_run_segment_grad(ctx, [md], [0, nat], x, v, X0, [box], Wd, 0, S, T(w), g1)
+    # separate calls
+    x2, v2 = X0.clone(), v0.clone()
+    Wd2 = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
+    g2 = torch.zeros(6 * nk, dtype=torch.float64, device=DEV)
+    for s in range(0, S, stride):
+        ne.ne_switch_run_segment(ctx, [md], [0, nat], x2, v2, X0, [box], Wd2, s, stride)
+        ne.ne_eam_backward_acc(ctx, prec, x2, box, float(w[s + stride]), g2)
+    assert torch.equal(x, x2) and torch.equal(Wd, Wd2)
+    a, b = N(g1), N(g2)
+    tol = (1e-12 if prec == ne.NE_FP64 else 1e-5) * np.abs(b).max()
+    assert np.abs(a - b).max() < tol
+    assert np.abs(b).max() > 0
