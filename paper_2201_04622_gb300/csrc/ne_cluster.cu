@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int K = valid ? (int)s_K[skb + min(NKT - 1, (int)(c * inv_dK) + 2)] : 0;
             // rho accumulated as a double-float (FP64-class precision from
             // FP32 arithmetic)
-#pragma unroll 4
+#pragma unroll 8
             for (int k = lane; k < K; k += 2) {
                 const float4 e = s_sv[stb + k];
                 const int code = __float_as_int(e.w);
