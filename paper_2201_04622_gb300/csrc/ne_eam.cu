@@ -182,7 +182,8 @@ __global__ void __launch_bounds__(NE_TILE* TPA) k_density(DevBatch B)
 }
 
 // ------------------------------------------------------------ pass 2
-template <bool MIXED, int TPA>
+// VIR: also the configurational virial (only runs with a barostat need it)
+template <bool MIXED, int TPA, bool VIR>
 __global__ void __launch_bounds__(NE_TILE* TPA)
     k_force(DevBatch B, Sched S, const long long* __restrict__ step_base, int j, int want_noise)
 {
@@ -256,14 +257,14 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
             fy += s * dy;
             fz += s * dz;
             ep += (R)0.5 * phi;
-            vir -= (R)0.5 * s * r2;
+            if constexpr (VIR) vir -= (R)0.5 * s * r2;
         }
     }
     fx = lane_sum(fx, TPA);
     fy = lane_sum(fy, TPA);
     fz = lane_sum(fz, TPA);
     double epd = lane_sum((double)ep, TPA);
-    double vird = lane_sum((double)vir, TPA);
+    const double vird = VIR ? lane_sum((double)vir, TPA) : 0.0;
     double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (valid && lane == 0) {
         if constexpr (MIXED) {
@@ -303,11 +304,12 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
             }
         }
     }
-    for (int q = 0; q < 8; ++q) red[q][threadIdx.x] = v[q];
+    constexpr int NQ = VIR ? 8 : 7;
+    for (int q = 0; q < NQ; ++q) red[q][threadIdx.x] = v[q];
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w)
-            for (int q = 0; q < 8; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+            for (int q = 0; q < NQ; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
         pa[PA_XIX] = red[4][0];
         pa[PA_XIY] = red[5][0];
         pa[PA_XIZ] = red[6][0];
-        pa[PA_VIR] = red[7][0];
+        pa[PA_VIR] = VIR ? red[7][0] : 0.0;
         __threadfence();
         unsigned prev = atomicAdd(&B.tile_done[rep], 1u);
         s_last = (prev == (unsigned)P.ntile - 1u);
@@ -563,11 +565,20 @@ void force_tpa(const DevBatch& B, const Sched& S, const long long* sb, int j, in
                cudaStream_t st)
 {
     dim3 g(B.n_tiles);
+    if (B.npt_any) {
+        switch (B.tpa) {
+        case 1: k_force<MIXED, 1, true><<<g, NE_TILE * 1, 0, st>>>(B, S, sb, j, wn); break;
+        case 2: k_force<MIXED, 2, true><<<g, NE_TILE * 2, 0, st>>>(B, S, sb, j, wn); break;
+        case 4: k_force<MIXED, 4, true><<<g, NE_TILE * 4, 0, st>>>(B, S, sb, j, wn); break;
+        default: k_force<MIXED, 8, true><<<g, NE_TILE * 8, 0, st>>>(B, S, sb, j, wn); break;
+        }
+        return;
+    }
     switch (B.tpa) {
-    case 1: k_force<MIXED, 1><<<g, NE_TILE * 1, 0, st>>>(B, S, sb, j, wn); break;
-    case 2: k_force<MIXED, 2><<<g, NE_TILE * 2, 0, st>>>(B, S, sb, j, wn); break;
-    case 4: k_force<MIXED, 4><<<g, NE_TILE * 4, 0, st>>>(B, S, sb, j, wn); break;
-    default: k_force<MIXED, 8><<<g, NE_TILE * 8, 0, st>>>(B, S, sb, j, wn); break;
+    case 1: k_force<MIXED, 1, false><<<g, NE_TILE * 1, 0, st>>>(B, S, sb, j, wn); break;
+    case 2: k_force<MIXED, 2, false><<<g, NE_TILE * 2, 0, st>>>(B, S, sb, j, wn); break;
+    case 4: k_force<MIXED, 4, false><<<g, NE_TILE * 4, 0, st>>>(B, S, sb, j, wn); break;
+    default: k_force<MIXED, 8, false><<<g, NE_TILE * 8, 0, st>>>(B, S, sb, j, wn); break;
     }
 }
 
