@@ -99,7 +99,18 @@ class BatchAdvancer:
         self.chunk = chunk
         self.moved, self.log = [], []
         self._ctx_g = None
-        self._sc, self._sg = torch.cuda.Stream(), torch.cuda.Stream()
+        self._cuda = bool(getattr(x0, "is_cuda", False))
+        self._sc = torch.cuda.Stream() if self._cuda else None
+        self._sg = torch.cuda.Stream() if self._cuda else None
+
+    @staticmethod
+    def _handle(st):
+        return st.cuda_stream if st is not None else None
+
+    def _sync(self):
+        if self._cuda:
+            import torch
+            torch.cuda.synchronize()
 
     def close(self):
         if self._ctx_g is not None:
@@ -141,7 +152,7 @@ class BatchAdvancer:
 
     def _general(self, idx, xs, vs, x0s, so, Ws, s0, ns):
         ne.ne_switch_run_segment(self._general_ctx(), [self.mds[r] for r in idx], so, xs, vs, x0s,
-                                 [self.boxes[r] for r in idx], Ws, s0, ns, stream=self._sg.cuda_stream)
+                                 [self.boxes[r] for r in idx], Ws, s0, ns, stream=self._handle(self._sg))
         self.log.append(("general", list(idx), s0, ns))
 
     def advance(self, x, v, W, s0, ns):
@@ -157,7 +168,7 @@ class BatchAdvancer:
         xc, vc, Wc, _, sc = self._gather(on_c, x, v, W) if on_c else (None,) * 5
         xg, vg, Wg, x0g, sg = self._gather(gen, x, v, W) if gen else (None,) * 5
         snap = (xc.clone(), vc.clone(), Wc.clone()) if on_c else None
-        torch.cuda.synchronize()
+        self._sync()
         errs, th = [], None
         if gen:
             if not on_c:
@@ -175,7 +186,7 @@ class BatchAdvancer:
             if on_c:
                 try:
                     ne.ne_crystal_run_segment(self.ctx, [self.mds[r] for r in on_c], [self.crystals[r] for r in on_c],
-                                              xc, vc, Wc, c0, cn, stream=self._sc.cuda_stream)
+                                              xc, vc, Wc, c0, cn, stream=self._handle(self._sc))
                     self.log.append(("crystal", on_c, c0, cn))
                 except ne.NeError as e:
                     if "NE_ERANGE" not in str(e):
@@ -190,7 +201,7 @@ class BatchAdvancer:
                 th.join()
         if errs:
             raise errs[0]
-        torch.cuda.synchronize()
+        self._sync()
         if on_c:
             self._scatter(on_c, sc, xc, vc, Wc, x, v, W)
         if gen:
@@ -212,12 +223,12 @@ class BatchAdvancer:
                     v[a:b].copy_(snap[1][sc[q]:sc[q + 1]])
                     W[r].copy_(snap[2][q])
             xb, vb, Wb, x0b, sb = self._gather(bad, x, v, W)
-            torch.cuda.synchronize()
+            self._sync()
             self._general(bad, xb, vb, x0b, sb, Wb, c0, cn)
-            torch.cuda.synchronize()
+            self._sync()
             self._scatter(bad, sb, xb, vb, Wb, x, v, W)
             self.moved = sorted(self.moved + bad)
-        torch.cuda.synchronize()
+        self._sync()
 
 
 def _fl_batch_auto(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec, skin, device, chunk, ids):
