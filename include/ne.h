@@ -359,6 +359,16 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
                                  double* x_dev, double* v_dev, double* W_dev, long long step_begin,
                                  long long n_steps, void* stream);
 
+/* ne_crystal_run_segment that also records the cumulative works of the two
+ * switches, as ne_rs_run does for eq. rs (Sec. III.C): Wcum_dev (device,
+ * double [n_rep][2][t_s + 1]; [r][0] forward, [r][1] backward) gets, for
+ * every switching step k of the range, [k + 1] = the replica's W after that
+ * step, and [0] = 0 at the switch's first step.  Errors as
+ * ne_crystal_run_segment; NE_EINVAL if Wcum_dev is NULL. */
+ne_status ne_crystal_run_segment_cum(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep,
+                                     double* x_dev, double* v_dev, double* W_dev, double* Wcum_dev,
+                                     long long step_begin, long long n_steps, void* stream);
+
 /* Outcome per replica of the last ne_crystal_run_segment call that launched
  * (bookkeeping; the paper has no counterpart): out_host[r] (host, n_rep ints)
  * = NE_OK or the error replica r raised (NE_ENAN, NE_ERANGE, ...).  A replica

@@ -1105,9 +1105,28 @@ static float code_bits(int code)
     return f;
 }
 
+static ne_status crystal_segment_impl(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep,
+                                      double* x_dev, double* v_dev, double* W_dev, double* Wcum_dev,
+                                      long long step_begin, long long n_steps, void* stream);
+
 ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep,
                                  double* x_dev, double* v_dev, double* W_dev, long long step_begin,
                                  long long n_steps, void* stream)
+{
+    return crystal_segment_impl(ctx, md, cr, n_rep, x_dev, v_dev, W_dev, nullptr, step_begin, n_steps, stream);
+}
+
+ne_status ne_crystal_run_segment_cum(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep,
+                                     double* x_dev, double* v_dev, double* W_dev, double* Wcum_dev,
+                                     long long step_begin, long long n_steps, void* stream)
+{
+    if (!Wcum_dev) return NE_EINVAL;
+    return crystal_segment_impl(ctx, md, cr, n_rep, x_dev, v_dev, W_dev, Wcum_dev, step_begin, n_steps, stream);
+}
+
+static ne_status crystal_segment_impl(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep,
+                                      double* x_dev, double* v_dev, double* W_dev, double* Wcum_dev,
+                                      long long step_begin, long long n_steps, void* stream)
 {
     if (!ctx || !md || !cr || !x_dev || !v_dev || !W_dev || n_rep < 1) return NE_EINVAL;
     if (n_rep > ctx->max_rep) return fail(ctx, NE_ENOMEM, "replica count exceeds the context");
@@ -1343,7 +1362,7 @@ ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_c
         if (multi) NE_CU(cudaStreamWaitEvent(gs, ctx->gev[16], 0));
         NE_CU(ne::launch_cluster(ctx->xrep + b, e - b, csize(order[b]), smem, ctx->st_vec, ctx->st_dist, x_dev, v_dev,
                                  W_dev, ctx->status, S, step_begin, n_steps, ctx->tab, ctx->work, k_lo, ctx->lam_tab,
-                                 gs));
+                                 Wcum_dev, gs));
         ++ctx->cr_launches;
         if (multi) {
             NE_CU(cudaEventRecord(ctx->gev[g], gs));

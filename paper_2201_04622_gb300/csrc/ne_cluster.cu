@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_cluster(const XRep* __restrict__ reps, const float4* __restrict__ st_vec, const float* __restrict__ st_dist,
               double* __restrict__ xg, double* __restrict__ vg, double* __restrict__ Wg, int* status, Sched S,
               long long s_begin, long long n_steps, Tables tab, unsigned long long* work, int k_lo,
-              const double* __restrict__ lam_tab)
+              const double* __restrict__ lam_tab, double* __restrict__ wcum)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -549,7 +549,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                 int wslot = -1;
                 if (sp >= S.t_eq && sp < S.t_eq + S.t_s) wslot = 0;
                 else if (sp >= 2 * S.t_eq + S.t_s && sp < 2 * S.t_eq + 2 * S.t_s) wslot = 1;
-                if (wslot >= 0) Wg[2 * reps[rep].widx + wslot] += (lam_tab[it] - lam_tab[it - 1]) * g;
+                if (wslot >= 0) {
+                    double* Wr = Wg + 2 * reps[rep].widx + wslot;
+                    *Wr += (lam_tab[it] - lam_tab[it - 1]) * g;
+                    if (wcum) {  // cumulative work of the switch: [0] = 0, [k + 1] after its step k
+                        const long long k = wslot == 0 ? sp - S.t_eq : sp - (2 * S.t_eq + S.t_s);
+                        double* wc = wcum + (size_t)(2 * reps[rep].widx + wslot) * (size_t)(S.t_s + 1);
+                        if (k == 0) wc[0] = 0.0;
+                        wc[k + 1] = *Wr;
+                    }
+                }
             }
             UE_prev = (double)s_tot[2 * P_UE] + (double)s_tot[2 * P_UE + 1];
         }
@@ -695,7 +704,7 @@ cudaError_t launch_lambda_table(const Sched& S, long long s_begin, long long cou
 cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, const float4* st_vec,
                            const float* st_dist, double* x, double* v, double* W, int* status, const Sched& S,
                            long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
-                           int k_lo, double* lam_tab, cudaStream_t st)
+                           int k_lo, double* lam_tab, double* wcum, cudaStream_t st)
 {
     cudaError_t e = cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -716,7 +725,7 @@ cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, cons
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_cluster, reps, st_vec, st_dist, x, v, W, status, S, s_begin, n_steps, tab,
-                              work, k_lo, (const double*)lam_tab);
+                              work, k_lo, (const double*)lam_tab, wcum);
 }
 
 }  // namespace ne

@@ -31,5 +31,5 @@ cudaError_t launch_lambda_table(const Sched& S, long long s_begin, long long cou
 cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, const float4* st_vec,
                            const float* st_dist, double* x, double* v, double* W, int* status, const Sched& S,
                            long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
-                           int k_lo, double* lam_tab, cudaStream_t st);
+                           int k_lo, double* lam_tab, double* wcum, cudaStream_t st);
 }  // namespace ne

@@ -29,7 +29,7 @@ SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_clone", "ne_ctx_set_theta"
            "ne_spring_forces",
            "ne_eam_backward", "ne_eam_backward_acc", "ne_noise", "ne_init_velocities", "ne_langevin_step",
            "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment", "ne_switch_run_segment_grad",
-           "ne_profile_segment", "ne_crystal_run_segment",
+           "ne_profile_segment", "ne_crystal_run_segment", "ne_crystal_run_segment_cum",
            "ne_msd_fit", "ne_free_energy", "ne_jarzynski",
            "ne_rs_free_energy"]
 
@@ -107,6 +107,7 @@ def load(build_if_missing: bool = True):
                 "ne_switch_run_segment_grad": [p, p, i, p, p, p, p, p, p, ll, ll, p, p, p],
                 "ne_profile_segment": [p, p, i, p, p, p, p, p, p, ll, ll, p, p, p],
                 "ne_crystal_run_segment": [p, p, p, i, p, p, p, ll, ll, p],
+                "ne_crystal_run_segment_cum": [p, p, p, i, p, p, p, p, ll, ll, p],
                 "ne_msd_fit": [p, p, p, p, p, i, p, ll, ll, i, p, p, p],
                 "ne_free_energy": [i, d, d, d, d, p, p, i, p, p, p],
                 "ne_jarzynski": [d, p, i, p],
@@ -404,6 +405,18 @@ def ne_crystal_run_segment(ctx, mds, crystals, x, v, W, step_begin, n_steps, str
     _err(ctx, load().ne_crystal_run_segment(ctx, arr, cr, n_rep, _dev(x), _dev(v), _dev(W, 2 * n_rep),
                                             int(step_begin), int(n_steps), _stream(stream)),
          "ne_crystal_run_segment")
+
+
+def ne_crystal_run_segment_cum(ctx, mds, crystals, x, v, W, Wcum, step_begin, n_steps, stream=None):
+    """ne_crystal_run_segment plus the cumulative works Wcum [n_rep][2][t_s + 1]."""
+    n_rep = len(mds)
+    arr = (MdParams * n_rep)(*mds)
+    cr = (Crystal * n_rep)(*[Crystal(int(c[0]), float(c[1]), int(c[2]), int(c[3]), int(c[4]),
+                                     float(c[5]) if len(c) > 5 else 0.0) for c in crystals])
+    _err(ctx, load().ne_crystal_run_segment_cum(ctx, arr, cr, n_rep, _dev(x), _dev(v), _dev(W, 2 * n_rep),
+                                                _dev(Wcum, n_rep * 2 * (int(mds[0].t_s) + 1)),
+                                                int(step_begin), int(n_steps), _stream(stream)),
+         "ne_crystal_run_segment_cum")
 
 
 def ne_msd_fit(ctx, md: MdParams, x, v, x0, box, n_eq, n_samples, stride, stream=None):

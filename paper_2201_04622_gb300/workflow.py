@@ -376,6 +376,38 @@ def rs_works(ctx, lattice, a, n, T0, mass, lambda_f, t_eq, t_s, seeds, prec=ne.N
     return np.array(cf), np.array(cb), np.array(a_end)
 
 
+def rs_batch(ctx, crystals, T0, seeds, lambda_f, t_eq, t_s, mass, replica_ids=None, chunk=20000,
+             device="cuda"):
+    """Reversible scaling (Sec. III.C) for a batch of crystal replicas on the
+    crystal runner at fixed volume: per replica, t_eq steps at lambda = 1, the
+    switch to lambda_f over t_s steps, t_eq steps there and the switch back, at
+    T0 (one value or one per replica).  Returns the cumulative works
+    [n_rep][t_s + 1] (forward, backward) for eq. rs (rs_free_energy)."""
+    import torch
+    n = len(crystals)
+    ids = list(range(n)) if replica_ids is None else list(replica_ids)
+    Ts = list(T0) if np.ndim(T0) else [T0] * n
+    x0s, offs, mds, crs = [], [0], [], []
+    for r, ((lat, a, nc), seed, Tr) in enumerate(zip(crystals, seeds, Ts)):
+        x0, _ = crystal_sites(lat, a, nc)
+        x0s.append(x0)
+        offs.append(offs[-1] + len(x0))
+        crs.append((lat, a, nc, nc, nc))
+        mds.append(ne.md_params(T=Tr, mass=mass, k_spring=1.0, prec=ne.NE_MIXED, path=ne.NE_PATH_RS,
+                                lambda_f=lambda_f, t_eq=t_eq, t_s=t_s, seed=seed, replica=ids[r], fix_cm=1))
+    x = torch.tensor(np.concatenate(x0s), dtype=torch.float64, device=device)
+    v = torch.zeros_like(x)
+    for r, m in enumerate(mds):
+        ne.ne_init_velocities(ctx, m, v[offs[r]:offs[r + 1]])
+    W = torch.zeros((n, 2), dtype=torch.float64, device=device)
+    Wc = torch.zeros(n * 2 * (t_s + 1), dtype=torch.float64, device=device)
+    S = 2 * t_eq + 2 * t_s
+    for s0 in range(0, S, chunk or S):
+        ne.ne_crystal_run_segment_cum(ctx, mds, crs, x, v, W, Wc, s0, min(chunk or S, S - s0))
+    wc = Wc.cpu().numpy().reshape(n, 2, t_s + 1)
+    return wc[:, 0], wc[:, 1]
+
+
 def rs_free_energy(lattice, a, n, T0, F0_T0_per_atom, lambda_f, t_s, Wcum_f, Wcum_b, T_grid):
     """Eq. rs: free energy per atom on T_grid (T0 .. T0/lambda_f) from the
     cumulative works and the free energy at T0 (with the barostat at P = 0,
