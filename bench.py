@@ -300,7 +300,7 @@ def run_ours(args):
                 # and state are read once per launch and the replica stays on chip, so the
                 # figure does not grow with the steps (a 301-step launch of this batch;
                 # the kernel's final x, v writes stay in L2); null for any other workload
-                "traffic": 2.50e6 if args.workload == "fl2" else None,
+                "traffic": 2.61e6 if args.workload == "fl2" else None,
                 "per_atom_step": {"stencil_visits": visits / (K * n_atoms), "pairs": pairs / (K * n_atoms)},
                 "note": "lane-ops = FP32 + INT32 lane instructions counted from the source per stencil "
                         "visit (%d), pair (%d) and atom-step (%d); peak = 152 SMs x 128 lanes x 2.07 GHz"
