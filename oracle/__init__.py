@@ -22,6 +22,12 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   switch_run (RS)       harmonic F(T) = 3NkT ln(hbar w/kT) at every T
   free_energy           F_E and dF_CM closed forms; low-T quasi-harmonic limit
   msd_fit               equipartition on a harmonic crystal
+  species tables        one species in a two-entry table reproduces the
+                        single-species run; Einstein F additive over species;
+                        eq. cm's centre-of-mass variance against sampling;
+                        per-species equipartition and msd under the
+                        mass-weighted constraint against Gaussian closed
+                        forms; harmonic -> per-species Einstein switch exact
 """
 from __future__ import annotations
 
@@ -63,7 +69,9 @@ class MD(C.Structure):
                 ("t_eq", C.c_long), ("t_s", C.c_long), ("lambda_f", C.c_double),
                 ("seed", C.c_uint64), ("replica", C.c_uint32),
                 ("fix_cm", C.c_int), ("h0", C.c_int), ("k_h0", C.c_double),
-                ("npt", C.c_int), ("P0", C.c_double), ("beta_T", C.c_double), ("tau_p", C.c_double)]
+                ("npt", C.c_int), ("P0", C.c_double), ("beta_T", C.c_double), ("tau_p", C.c_double),
+                ("n_species", C.c_int), ("species", C.c_void_p), ("mass_s", C.c_void_p),
+                ("k_s", C.c_void_p)]
 
 
 def build(force: bool = False) -> str:
@@ -111,6 +119,12 @@ def lib():
             L.ora_switch_run.argtypes = [p, p, p, p, p, p, i, p, p, p, p, p, p, i, i]
             L.ora_langevin_steps.argtypes = [p, p, p, d, p, p, p, i, p, C.c_long, C.c_long]
             L.ora_msd_fit.argtypes = [p, p, p, p, p, p, i, p, C.c_long, C.c_long, i, p, p]
+            L.ora_msd_fit_species.argtypes = [p, p, p, p, p, p, i, p, C.c_long, C.c_long, i, p, p]
+            L.ora_einstein_F_species.restype = d
+            L.ora_einstein_F_species.argtypes = [i, p, p, p, d]
+            L.ora_cm_correction_species.restype = d
+            L.ora_cm_correction_species.argtypes = [i, p, p, p, d, d]
+            L.ora_free_energy_species.argtypes = [i, p, i, p, p, d, d, p, p, i, p, p, p]
             L.ora_free_energy.argtypes = [i, d, d, d, d, p, p, i, p, p, p]
             L.ora_rs_free_energy.argtypes = [i, d, d, d, C.c_long, p, p, i, p, i, p]
             L.ora_philox4x32_10.argtypes = [p, p, p]
@@ -155,13 +169,27 @@ def eam(A, alpha, beta, B, r_e, r_s, r_c, rho_max, n_knots) -> EAM:
 
 def md(dt=1e-3, T=100.0, damp=0.1, mass=None, k_spring=5.0, lambda_fn=2, path=PATH_FL,
        t_eq=0, t_s=1, lambda_f=0.5, seed=1, replica=0, fix_cm=1, h0=H0_EAM,
-       k_h0=0.0, npt=0, P0=0.0, beta_T=0.0, tau_p=0.0) -> MD:
+       k_h0=0.0, npt=0, P0=0.0, beta_T=0.0, tau_p=0.0, species=None, mass_s=None,
+       k_s=None) -> MD:
     """npt = 1: isotropic barostat at pressure P0 (eV/A^3) with coupling
-    compressibility beta_T (A^3/eV) and time tau_p (ps); RS path only."""
+    compressibility beta_T (A^3/eV) and time tau_p (ps); RS path only.
+
+    species ([n] ints), mass_s and k_s ([n_species]): one mass and one Einstein
+    spring per species (Sec. V); mass and k_spring are then unused.  The
+    returned struct keeps the three arrays alive."""
     if mass is None:
         mass = 55.845 * amu()
-    return MD(dt, T, damp, mass, k_spring, lambda_fn, path, t_eq, t_s, lambda_f,
-              seed, replica, fix_cm, h0, k_h0, npt, P0, beta_T, tau_p)
+    m = MD(dt, T, damp, mass, k_spring, lambda_fn, path, t_eq, t_s, lambda_f,
+           seed, replica, fix_cm, h0, k_h0, npt, P0, beta_T, tau_p)
+    if species is not None:
+        sp = np.ascontiguousarray(species, dtype=np.int32)
+        ms, ks = _f64(mass_s).ravel().copy(), _f64(k_s).ravel().copy()
+        if ms.size != ks.size:
+            raise ValueError("mass_s and k_s need one entry per species")
+        m._keep = (sp, ms, ks)
+        m.n_species = ms.size
+        m.species, m.mass_s, m.k_s = sp.ctypes.data, ms.ctypes.data, ks.ctypes.data
+    return m
 
 
 def create_crystal(lattice, a, nx, ny, nz, c_over_a=None):
@@ -332,6 +360,43 @@ def msd_fit(p: EAM, theta, m: MD, x, v, x0, box, n_eq, n_samples, stride):
                              _ptr(x0), x.shape[0], _ptr(box), n_eq, n_samples, stride,
                              C.byref(msd), C.byref(k)), "msd_fit")
     return msd.value, k.value
+
+
+def msd_fit_species(p: EAM, theta, m: MD, x, v, x0, box, n_eq, n_samples, stride):
+    """Eq. msd per species (Sec. V): (msd_s, k_s) arrays over the species of m."""
+    theta, x0, box = _f64(theta), _f64(x0), _f64(box)
+    x, v = _f64(x).copy(), _f64(v).copy()
+    msd = np.zeros(m.n_species)
+    k = np.zeros(m.n_species)
+    _check(lib().ora_msd_fit_species(_pref(p), _ptr(theta), C.byref(m), _ptr(x), _ptr(v),
+                                     _ptr(x0), x.shape[0], _ptr(box), n_eq, n_samples, stride,
+                                     _ptr(msd), _ptr(k)), "msd_fit_species")
+    return msd, k
+
+
+def _species_args(species, mass_s, k_s):
+    sp = np.ascontiguousarray(species, dtype=np.int32)
+    return sp, _f64(mass_s).ravel(), _f64(k_s).ravel()
+
+
+def einstein_F_species(species, mass_s, k_s, T):
+    sp, ms, ks = _species_args(species, mass_s, k_s)
+    return lib().ora_einstein_F_species(sp.size, _ptr(sp), _ptr(ms), _ptr(ks), T)
+
+
+def cm_correction_species(species, mass_s, k_s, V, T):
+    sp, ms, ks = _species_args(species, mass_s, k_s)
+    return lib().ora_cm_correction_species(sp.size, _ptr(sp), _ptr(ms), _ptr(ks), V, T)
+
+
+def free_energy_species(species, mass_s, k_s, V, T, W_f, W_b):
+    sp, ms, ks = _species_args(species, mass_s, k_s)
+    W_f, W_b = _f64(W_f).ravel(), _f64(W_b).ravel()
+    F, se, ed = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().ora_free_energy_species(sp.size, _ptr(sp), ms.size, _ptr(ms), _ptr(ks), V, T,
+                                         _ptr(W_f), _ptr(W_b), W_f.size, C.byref(F),
+                                         C.byref(se), C.byref(ed)), "free_energy_species")
+    return F.value, se.value, ed.value
 
 
 def einstein_F(n, T, mass, k):

@@ -542,33 +542,109 @@ void ora_normals(uint64_t seed, uint32_t replica, uint32_t stream, uint32_t atom
 /* ------------------------------------------------------------ dynamics */
 static int dof(const ora_md* md, int n) { return md->fix_cm ? 3 * n - 3 : 3 * n; }
 
-static double kinetic(const double* v, int n, double m)
+/* Mass of atom i: its species' mass with a species table, md->mass without. */
+static double mass_of(const ora_md* md, int i)
+{
+    return md->species ? md->mass_s[md->species[i]] : md->mass;
+}
+
+/* A species table is usable when every index is in range, every mass
+ * positive and every spring non-negative; no table is always usable. */
+static int species_valid(const ora_md* md, int n)
+{
+    if (!md->species) return 1;
+    if (md->n_species < 1 || !md->mass_s || !md->k_s) return 0;
+    for (int s = 0; s < md->n_species; s++)
+        if (!(md->mass_s[s] > 0) || !(md->k_s[s] >= 0)) return 0;
+    for (int i = 0; i < n; i++)
+        if (md->species[i] < 0 || md->species[i] >= md->n_species) return 0;
+    return 1;
+}
+
+static double kinetic(const ora_md* md, const double* v, int n)
 {
     double ke = 0.0;
-    for (int i = 0; i < 3 * n; i++) ke += 0.5 * m * v[i] * v[i];
+    for (int i = 0; i < 3 * n; i++) ke += 0.5 * mass_of(md, i / 3) * v[i] * v[i];
     return ke;
 }
 
-/* Maxwell-Boltzmann start: normals times sqrt(kT/m), zero total momentum when
- * the centre of mass is fixed (Sec. III.A), rescaled to exactly T. */
+/* Fixed centre of mass (Sec. III.A), imposed as a projection in the mass
+ * metric.  A velocity-like array loses its centre-of-mass velocity,
+ * u_i -= sum_j m_j u_j / M; for one species that is the plain mean. */
+static void remove_cm_velocity(const ora_md* md, int n, double* u)
+{
+    for (int c = 0; c < 3; c++) {
+        if (!md->species) {
+            double mean = 0.0;
+            for (int i = 0; i < n; i++) mean += u[3 * i + c];
+            mean /= n;
+            for (int i = 0; i < n; i++) u[3 * i + c] -= mean;
+        } else {
+            double P = 0.0, M = 0.0;
+            for (int i = 0; i < n; i++) {
+                P += mass_of(md, i) * u[3 * i + c];
+                M += mass_of(md, i);
+            }
+            for (int i = 0; i < n; i++) u[3 * i + c] -= P / M;
+        }
+    }
+}
+
+/* A force array loses the part that would accelerate the centre of mass:
+ * F_i -= m_i sum_j F_j / M, the constraint force that holds sum_j m_j r_j
+ * fixed; for one species that is the plain mean. */
+static void remove_cm_force(const ora_md* md, int n, double* F)
+{
+    for (int c = 0; c < 3; c++) {
+        if (!md->species) {
+            double mean = 0.0;
+            for (int i = 0; i < n; i++) mean += F[3 * i + c];
+            mean /= n;
+            for (int i = 0; i < n; i++) F[3 * i + c] -= mean;
+        } else {
+            double S = 0.0, M = 0.0;
+            for (int i = 0; i < n; i++) {
+                S += F[3 * i + c];
+                M += mass_of(md, i);
+            }
+            for (int i = 0; i < n; i++) F[3 * i + c] -= mass_of(md, i) * S / M;
+        }
+    }
+}
+
+/* Einstein springs of eq. einstein; with a species table atom i has the
+ * spring k_s of its species (Sec. V). */
+static void spring_md(const ora_md* md, const double* x, const double* x0, int n,
+                      double* f, double* E)
+{
+    if (!md->species) {
+        ora_spring(x, x0, n, md->k_spring, f, E);
+        return;
+    }
+    double e = 0.0;
+    for (int i = 0; i < 3 * n; i++) {
+        double k = md->k_s[md->species[i / 3]];
+        double u = x[i] - x0[i];
+        e += 0.5 * k * u * u;
+        f[i] = -k * u;
+    }
+    *E = e;
+}
+
+/* Maxwell-Boltzmann start: normals times sqrt(kT/m_i), zero total momentum
+ * when the centre of mass is fixed (Sec. III.A), rescaled to exactly T. */
 int ora_init_velocities(const ora_md* md, int n, double* v)
 {
-    if (n < 2 || !(md->mass > 0) || !(md->T > 0)) return ORA_EINVAL;
-    double sd = sqrt(KB_EV_PER_K * md->T / md->mass);
+    if (n < 2 || !(md->T > 0) || !species_valid(md, n) || (!md->species && !(md->mass > 0)))
+        return ORA_EINVAL;
     for (int i = 0; i < n; i++) {
+        double sd = sqrt(KB_EV_PER_K * md->T / mass_of(md, i));
         double z[3];
         ora_normals(md->seed, md->replica, ORA_STREAM_INITV, (uint32_t)i, 0, z);
         for (int c = 0; c < 3; c++) v[3 * i + c] = sd * z[c];
     }
-    if (md->fix_cm) {
-        for (int c = 0; c < 3; c++) {
-            double mean = 0.0;
-            for (int i = 0; i < n; i++) mean += v[3 * i + c];
-            mean /= n;
-            for (int i = 0; i < n; i++) v[3 * i + c] -= mean;
-        }
-    }
-    double t_now = 2.0 * kinetic(v, n, md->mass) / (dof(md, n) * KB_EV_PER_K);
+    if (md->fix_cm) remove_cm_velocity(md, n, v);
+    double t_now = 2.0 * kinetic(md, v, n) / (dof(md, n) * KB_EV_PER_K);
     double s = sqrt(md->T / t_now);
     for (int i = 0; i < 3 * n; i++) v[i] *= s;
     return ORA_OK;
@@ -596,26 +672,19 @@ static int eval_terms(const ora_eam* p, const double* theta, const ora_md* md,
             if (st) return st;
         }
     }
-    ora_spring(x, x0, n, md->k_spring, t->FE, &t->UE);
+    spring_md(md, x, x0, n, t->FE, &t->UE);
     return ORA_OK;
 }
 
 /* Total force of H(lambda): (1-lambda) F0 + lambda F_E on the Frenkel-Ladd
  * path (eq. interp), lambda F0 on the reversible-scaling path (eq. H_rs).
- * With the centre of mass fixed, the mean force is removed. */
+ * With the centre of mass fixed, its constraint force is added. */
 static void blend_force(const ora_md* md, const terms* t, int n, double lam, double* F)
 {
     for (int i = 0; i < 3 * n; i++)
         F[i] = md->path == ORA_PATH_FL ? (1.0 - lam) * t->F0[i] + lam * t->FE[i]
                                        : lam * t->F0[i];
-    if (md->fix_cm) {
-        for (int c = 0; c < 3; c++) {
-            double mean = 0.0;
-            for (int i = 0; i < n; i++) mean += F[3 * i + c];
-            mean /= n;
-            for (int i = 0; i < n; i++) F[3 * i + c] -= mean;
-        }
-    }
+    if (md->fix_cm) remove_cm_force(md, n, F);
 }
 
 /* dH/dlambda along the path, in the sign convention that makes eq. fl hold as
@@ -630,7 +699,8 @@ static double dH_dlambda(const ora_md* md, const terms* t)
  *      sum of Sec. II.A, left point), i.e. the Hamiltonian jumps at fixed x;
  *   2. half kick with F(x_s; lambda_b);  3. half drift;
  *   4. Ornstein-Uhlenbeck velocity update (Langevin thermostat, damping
- *      1/gamma), noise mean removed when the centre of mass is fixed;
+ *      1/gamma), the centre-of-mass velocity of the noise removed when the
+ *      centre of mass is fixed;
  *   5. half drift;  5b. with the barostat, the volume update below;
  *   6. forces at x_{s+1};  7. half kick with F(x_{s+1}; lambda_b).
  * t holds the terms at x_s on entry and at x_{s+1} on return.
@@ -651,28 +721,30 @@ static int md_step(const ora_eam* p, const double* theta, const ora_md* md,
                    double* v, const double* x0, int n, double box[3], terms* t,
                    double* F, double* xi, double* dW)
 {
-    double m = md->mass, dt = md->dt;
+    double dt = md->dt;
     *dW = (lam_b - lam_a) * dH_dlambda(md, t);
     blend_force(md, t, n, lam_b, F);
-    for (int i = 0; i < 3 * n; i++) v[i] += 0.5 * dt / m * F[i];
+    for (int i = 0; i < 3 * n; i++) v[i] += 0.5 * dt / mass_of(md, i / 3) * F[i];
     for (int i = 0; i < 3 * n; i++) x[i] += 0.5 * dt * v[i];
     double gamma = md->damp > 0 ? 1.0 / md->damp : 0.0;
     double c1 = exp(-gamma * dt);
-    double c2 = sqrt((1.0 - c1 * c1) * KB_EV_PER_K * md->T / m);
     for (int i = 0; i < n; i++) {
         double z[3];
         ora_normals(md->seed, md->replica, stream, (uint32_t)i, (uint64_t)s, z);
         for (int c = 0; c < 3; c++) xi[3 * i + c] = z[c];
     }
-    if (md->fix_cm) {
-        for (int c = 0; c < 3; c++) {
-            double mean = 0.0;
-            for (int i = 0; i < n; i++) mean += xi[3 * i + c];
-            mean /= n;
-            for (int i = 0; i < n; i++) xi[3 * i + c] -= mean;
-        }
+    if (!md->species) {
+        double c2 = sqrt((1.0 - c1 * c1) * KB_EV_PER_K * md->T / md->mass);
+        if (md->fix_cm) remove_cm_velocity(md, n, xi);
+        for (int i = 0; i < 3 * n; i++) v[i] = c1 * v[i] + c2 * xi[i];
+    } else {
+        /* velocity increments sqrt((1 - c1^2) kT / m_i) xi_i, their
+         * centre-of-mass velocity removed */
+        for (int i = 0; i < 3 * n; i++)
+            xi[i] *= sqrt((1.0 - c1 * c1) * KB_EV_PER_K * md->T / mass_of(md, i / 3));
+        if (md->fix_cm) remove_cm_velocity(md, n, xi);
+        for (int i = 0; i < 3 * n; i++) v[i] = c1 * v[i] + xi[i];
     }
-    for (int i = 0; i < 3 * n; i++) v[i] = c1 * v[i] + c2 * xi[i];
     for (int i = 0; i < 3 * n; i++) x[i] += 0.5 * dt * v[i];
     if (md->npt) {
         double kT = KB_EV_PER_K * md->T, V = box[0] * box[1] * box[2];
@@ -687,7 +759,7 @@ static int md_step(const ora_eam* p, const double* theta, const ora_md* md,
     int st = eval_terms(p, theta, md, x, x0, n, box, t);
     if (st) return st;
     blend_force(md, t, n, lam_b, F);
-    for (int i = 0; i < 3 * n; i++) v[i] += 0.5 * dt / m * F[i];
+    for (int i = 0; i < 3 * n; i++) v[i] += 0.5 * dt / mass_of(md, i / 3) * F[i];
     for (int i = 0; i < 3 * n; i++)
         if (!isfinite(x[i]) || !isfinite(v[i])) return ORA_ENAN;
     return ORA_OK;
@@ -723,7 +795,7 @@ int ora_switch_run(const ora_eam* p, const double* theta, const ora_md* md,
                    double* Wcum_f, double* Wcum_b, double* trace,
                    int trace_stride, int n_trace_max)
 {
-    if (n < 2 || md->t_s < 1 || md->t_eq < 0) return ORA_EINVAL;
+    if (n < 2 || md->t_s < 1 || md->t_eq < 0 || !species_valid(md, n)) return ORA_EINVAL;
     if (md->path == ORA_PATH_RS && !(md->lambda_f > 0 && md->lambda_f < 1)) return ORA_EINVAL;
     if (md->npt && (md->path != ORA_PATH_RS || !(md->beta_T > 0) || !(md->tau_p > 0) || md->P0 < 0 ||
                     (md->h0 == ORA_H0_HARMONIC && md->k_h0 != 0.0)))
@@ -746,7 +818,7 @@ int ora_switch_run(const ora_eam* p, const double* theta, const ora_md* md,
             r[2] = dH_dlambda(md, &w.t);
             r[3] = w.t.U0;
             r[4] = w.t.UE;
-            r[5] = 2.0 * kinetic(v, n, md->mass) / (dof(md, n) * KB_EV_PER_K);
+            r[5] = 2.0 * kinetic(md, v, n) / (dof(md, n) * KB_EV_PER_K);
             r[6] = wf;
             r[7] = wb;
         }
@@ -770,7 +842,7 @@ int ora_langevin_steps(const ora_eam* p, const double* theta, const ora_md* md,
                        double lambda, double* x, double* v, const double* x0,
                        int n, const double box[3], long step0, long n_steps)
 {
-    if (n < 2 || md->npt) return ORA_EINVAL;  /* fixed box */
+    if (n < 2 || md->npt || !species_valid(md, n)) return ORA_EINVAL;  /* fixed box */
     double bx[3] = {box[0], box[1], box[2]};
     workspace w;
     ws_alloc(&w, n);
@@ -785,20 +857,29 @@ int ora_langevin_steps(const ora_eam* p, const double* theta, const ora_md* md,
 }
 
 /* Eq. msd (Sec. III.A): k = 3 k_B T / <|dr|^2>, with dr the displacement from
- * the initial site corrected for the centre-of-mass motion (compute msd com). */
-int ora_msd_fit(const ora_eam* p, const double* theta, const ora_md* md, double* x,
-                double* v, const double* x0, int n, const double box[3],
-                long n_eq, long n_samples, int stride, double* msd_out, double* k_out)
+ * the initial site corrected for the centre-of-mass motion (compute msd com).
+ * The average runs per class of atoms: the species with a species table (the
+ * centre of mass then mass-weighted, the one the dynamics holds fixed), one
+ * class of all atoms without.  acc[c] sums, over the samples, the class mean
+ * of |dr|^2. */
+static int msd_run(const ora_eam* p, const double* theta, const ora_md* md, double* x,
+                   double* v, const double* x0, int n, const double box[3], long n_eq,
+                   long n_samples, int stride, int n_class, double* acc)
 {
-    if (n < 2 || n_samples < 1 || stride < 1) return ORA_EINVAL;
     ora_md m0 = *md;
     m0.path = ORA_PATH_FL;
     m0.npt = 0;
     double bx[3] = {box[0], box[1], box[2]};
+    int* count = calloc(n_class, sizeof(int));
+    double* msd = calloc(n_class, sizeof(double));
+    for (int i = 0; i < n; i++) count[md->species ? md->species[i] : 0]++;
+    for (int c = 0; c < n_class; c++) acc[c] = 0.0;
+    int st = ORA_OK;
+    for (int c = 0; c < n_class; c++)
+        if (count[c] == 0) st = ORA_EINVAL;
     workspace w;
     ws_alloc(&w, n);
-    int st = eval_terms(p, theta, &m0, x, x0, n, box, &w.t);
-    double acc = 0.0;
+    if (!st) st = eval_terms(p, theta, &m0, x, x0, n, box, &w.t);
     long s = 0;
     for (; s < n_eq && !st; s++) {
         double dW;
@@ -812,25 +893,67 @@ int ora_msd_fit(const ora_eam* p, const double* theta, const ora_md* md, double*
                          &w.t, w.F, w.xi, &dW);
         }
         double R[3] = {0, 0, 0}, R0[3] = {0, 0, 0};
-        for (int i = 0; i < n; i++)
-            for (int c = 0; c < 3; c++) {
-                R[c] += x[3 * i + c] / n;
-                R0[c] += x0[3 * i + c] / n;
-            }
-        double msd = 0.0;
+        if (!md->species) {
+            for (int i = 0; i < n; i++)
+                for (int c = 0; c < 3; c++) {
+                    R[c] += x[3 * i + c] / n;
+                    R0[c] += x0[3 * i + c] / n;
+                }
+        } else {
+            double M = 0.0;
+            for (int i = 0; i < n; i++) M += mass_of(md, i);
+            for (int i = 0; i < n; i++)
+                for (int c = 0; c < 3; c++) {
+                    R[c] += mass_of(md, i) * x[3 * i + c] / M;
+                    R0[c] += mass_of(md, i) * x0[3 * i + c] / M;
+                }
+        }
+        for (int c = 0; c < n_class; c++) msd[c] = 0.0;
         for (int i = 0; i < n; i++)
             for (int c = 0; c < 3; c++) {
                 double d = (x[3 * i + c] - x0[3 * i + c]) - (R[c] - R0[c]);
-                msd += d * d;
+                msd[md->species ? md->species[i] : 0] += d * d;
             }
-        acc += msd / n;
+        for (int c = 0; c < n_class; c++) acc[c] += msd[c] / count[c];
     }
     ws_free(&w);
+    free(count);
+    free(msd);
+    return st;
+}
+
+int ora_msd_fit(const ora_eam* p, const double* theta, const ora_md* md, double* x,
+                double* v, const double* x0, int n, const double box[3],
+                long n_eq, long n_samples, int stride, double* msd_out, double* k_out)
+{
+    if (n < 2 || n_samples < 1 || stride < 1 || md->species) return ORA_EINVAL;
+    double acc;
+    int st = msd_run(p, theta, md, x, v, x0, n, box, n_eq, n_samples, stride, 1, &acc);
     if (st) return st;
     double mean = acc / n_samples;
     if (msd_out) *msd_out = mean;
     if (k_out) *k_out = 3.0 * KB_EV_PER_K * md->T / mean;
     return ORA_OK;
+}
+
+/* Sec. V: one spring per species, each from the msd of its own atoms. */
+int ora_msd_fit_species(const ora_eam* p, const double* theta, const ora_md* md,
+                        double* x, double* v, const double* x0, int n,
+                        const double box[3], long n_eq, long n_samples, int stride,
+                        double* msd_s, double* k_out)
+{
+    if (n < 2 || n_samples < 1 || stride < 1 || !md->species || !species_valid(md, n))
+        return ORA_EINVAL;
+    double* acc = calloc(md->n_species, sizeof(double));
+    int st = msd_run(p, theta, md, x, v, x0, n, box, n_eq, n_samples, stride,
+                     md->n_species, acc);
+    for (int c = 0; c < md->n_species && !st; c++) {
+        double mean = acc[c] / n_samples;
+        if (msd_s) msd_s[c] = mean;
+        if (k_out) k_out[c] = 3.0 * KB_EV_PER_K * md->T / mean;
+    }
+    free(acc);
+    return st;
 }
 
 /* --------------------------------------------------------------- assembly */
@@ -866,19 +989,16 @@ double ora_jarzynski(double T, const double* W, int n)
     return -kT * (xmax + log(sum) - log((double)n));
 }
 
-int ora_free_energy(int n, double V, double T, double mass, double k,
-                    const double* W_f, const double* W_b, int n_seeds,
-                    double* F_per_atom, double* stderr_per_atom,
-                    double* Ediss_per_atom)
+/* Seed statistics of eq. fl: the seed means of W_f and W_b, the standard
+ * error over seeds of (W_f - W_b)/(2n) and the dissipation -(mean W_f + mean
+ * W_b)/(2n) of eq. Ediss. */
+static void work_stats(int n, const double* W_f, const double* W_b, int n_seeds,
+                       double* mf_out, double* mb_out, double* se_out, double* ed_out)
 {
-    if (n < 1 || n_seeds < 1 || !(V > 0) || !(T > 0) || !(k > 0) || !(mass > 0))
-        return ORA_EINVAL;
     double mf = 0.0, mb = 0.0;
     for (int q = 0; q < n_seeds; q++) { mf += W_f[q]; mb += W_b[q]; }
     mf /= n_seeds;
     mb /= n_seeds;
-    double F = ora_einstein_F(n, T, mass, k) + 0.5 * (mf - mb) +
-               ora_cm_correction(n, V, T, mass, k);
     double se = 0.0;
     if (n_seeds > 1) {
         double mean = 0.5 * (mf - mb) / n, var = 0.0;
@@ -889,9 +1009,82 @@ int ora_free_energy(int n, double V, double T, double mass, double k,
         var /= (n_seeds - 1);
         se = sqrt(var / n_seeds);
     }
+    *mf_out = mf;
+    *mb_out = mb;
+    *se_out = se;
+    *ed_out = -0.5 * (mf + mb) / n;
+}
+
+int ora_free_energy(int n, double V, double T, double mass, double k,
+                    const double* W_f, const double* W_b, int n_seeds,
+                    double* F_per_atom, double* stderr_per_atom,
+                    double* Ediss_per_atom)
+{
+    if (n < 1 || n_seeds < 1 || !(V > 0) || !(T > 0) || !(k > 0) || !(mass > 0))
+        return ORA_EINVAL;
+    double mf, mb, se, ed;
+    work_stats(n, W_f, W_b, n_seeds, &mf, &mb, &se, &ed);
+    double F = ora_einstein_F(n, T, mass, k) + 0.5 * (mf - mb) +
+               ora_cm_correction(n, V, T, mass, k);
     if (F_per_atom) *F_per_atom = F / n;
     if (stderr_per_atom) *stderr_per_atom = se;
-    if (Ediss_per_atom) *Ediss_per_atom = -0.5 * (mf + mb) / n;
+    if (Ediss_per_atom) *Ediss_per_atom = ed;
+    return ORA_OK;
+}
+
+/* Eq. einstein for independent oscillators with one frequency per species
+ * (Sec. V): F_E = sum_i 3 k_B T ln(hbar omega_i / k_B T), omega_i^2 = k_i/m_i. */
+double ora_einstein_F_species(int n, const int* species, const double* mass_s,
+                              const double* k_s, double T)
+{
+    double F = 0.0;
+    for (int i = 0; i < n; i++) {
+        double omega = sqrt(k_s[species[i]] / mass_s[species[i]]);
+        F += 3.0 * KB_EV_PER_K * T * log(HBAR_EV_PS * omega / (KB_EV_PER_K * T));
+    }
+    return F;
+}
+
+/* Eq. cm with several species.  The factor 2 pi k_B T / (N m omega^2) of
+ * eq. cm is 2 pi sigma^2, sigma^2 the variance per axis of the centre of mass
+ * of the Einstein crystal about its site; the centre the dynamics holds fixed
+ * is R = sum_i m_i r_i / M, whose variance with independent springs k_i is
+ * sigma^2 = k_B T sum_i (m_i / M)^2 / k_i.  The leading N / V stays as
+ * printed. */
+double ora_cm_correction_species(int n, const int* species, const double* mass_s,
+                                 const double* k_s, double V, double T)
+{
+    double kT = KB_EV_PER_K * T, M = 0.0, s2 = 0.0;
+    const double pi = 3.14159265358979323846264338327950;
+    for (int i = 0; i < n; i++) M += mass_s[species[i]];
+    for (int i = 0; i < n; i++) {
+        double w = mass_s[species[i]] / M;
+        s2 += w * w * kT / k_s[species[i]];
+    }
+    return kT * log((n / V) * pow(2.0 * pi * s2, 1.5));
+}
+
+/* Eq. fl plus eq. cm with one spring per species (Sec. V). */
+int ora_free_energy_species(int n, const int* species, int n_species,
+                            const double* mass_s, const double* k_s, double V,
+                            double T, const double* W_f, const double* W_b,
+                            int n_seeds, double* F_per_atom,
+                            double* stderr_per_atom, double* Ediss_per_atom)
+{
+    if (n < 1 || n_seeds < 1 || !(V > 0) || !(T > 0) || n_species < 1 || !species ||
+        !mass_s || !k_s)
+        return ORA_EINVAL;
+    for (int s = 0; s < n_species; s++)
+        if (!(mass_s[s] > 0) || !(k_s[s] > 0)) return ORA_EINVAL;
+    for (int i = 0; i < n; i++)
+        if (species[i] < 0 || species[i] >= n_species) return ORA_EINVAL;
+    double mf, mb, se, ed;
+    work_stats(n, W_f, W_b, n_seeds, &mf, &mb, &se, &ed);
+    double F = ora_einstein_F_species(n, species, mass_s, k_s, T) + 0.5 * (mf - mb) +
+               ora_cm_correction_species(n, species, mass_s, k_s, V, T);
+    if (F_per_atom) *F_per_atom = F / n;
+    if (stderr_per_atom) *stderr_per_atom = se;
+    if (Ediss_per_atom) *Ediss_per_atom = ed;
     return ORA_OK;
 }
 

@@ -57,6 +57,16 @@ typedef struct {
     double P0;        /* target pressure, eV/A^3 */
     double beta_T;    /* compressibility of the coupling, A^3/eV */
     double tau_p;     /* relaxation time of the coupling, ps */
+    /* Several species (Sec. V: an A-B solid with one Einstein spring per
+     * species).  species == NULL: every atom has mass and k_spring.  Else atom
+     * i has mass mass_s[species[i]] and spring k_s[species[i]] (mass and
+     * k_spring unused), and the fixed centre of mass is the mass-weighted one:
+     * forces and noise are projected in the mass metric.  The springs of
+     * ORA_H0_HARMONIC stay k_h0 for every atom. */
+    int n_species;
+    const int* species;     /* [n], 0 <= species[i] < n_species */
+    const double* mass_s;   /* [n_species], eV ps^2 / A^2 */
+    const double* k_s;      /* [n_species], eV/A^2 */
 } ora_md;
 
 /* constants */
@@ -128,11 +138,20 @@ int ora_langevin_steps(const ora_eam* p, const double* theta, const ora_md* md,
                        double lambda, double* x, double* v, const double* x0,
                        int n, const double box[3], long step0, long n_steps);
 
-/* Spring-constant fit from the mean-squared displacement. */
+/* Spring-constant fit from the mean-squared displacement (one species:
+ * md->species must be NULL). */
 int ora_msd_fit(const ora_eam* p, const double* theta, const ora_md* md, double* x,
                 double* v, const double* x0, int n, const double box[3],
                 long n_eq, long n_samples, int stride, double* msd_out,
                 double* k_out);
+/* The same per species (Sec. V): msd_s[s] averages over the atoms of species
+ * s, displacements taken relative to the mass-weighted centre of mass, and
+ * k_out[s] = 3 k_B T / msd_s[s].  md->species must be set and every species
+ * must have atoms. */
+int ora_msd_fit_species(const ora_eam* p, const double* theta, const ora_md* md,
+                        double* x, double* v, const double* x0, int n,
+                        const double box[3], long n_eq, long n_samples, int stride,
+                        double* msd_s, double* k_out);
 
 /* Free-energy assembly (host, FP64). */
 double ora_einstein_F(int n, double T, double mass, double k);
@@ -144,6 +163,19 @@ int ora_free_energy(int n, double V, double T, double mass, double k,
                     const double* W_f, const double* W_b, int n_seeds,
                     double* F_per_atom, double* stderr_per_atom,
                     double* Ediss_per_atom);
+/* Several species (Sec. V): eq. einstein summed over the atoms with
+ * omega_i^2 = k_i / m_i, and eq. cm with the variance of the mass-weighted
+ * centre of the Einstein crystal, sigma^2 = k_B T sum_i (m_i/M)^2 / k_i, in
+ * place of k_B T / (N m omega^2).  species[i] indexes mass_s and k_s. */
+double ora_einstein_F_species(int n, const int* species, const double* mass_s,
+                              const double* k_s, double T);
+double ora_cm_correction_species(int n, const int* species, const double* mass_s,
+                                 const double* k_s, double V, double T);
+int ora_free_energy_species(int n, const int* species, int n_species,
+                            const double* mass_s, const double* k_s, double V,
+                            double T, const double* W_f, const double* W_b,
+                            int n_seeds, double* F_per_atom,
+                            double* stderr_per_atom, double* Ediss_per_atom);
 int ora_rs_free_energy(int n, double T0, double F0_T0, double lambda_f, long t_s,
                        const double* Wcum_f, const double* Wcum_b, int n_seeds,
                        const double* T_grid, int n_T, double* F_per_atom);
