@@ -39,6 +39,18 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert L.ne_noise(1, 0, 99, 0, 10, 0, None, None) == ne.NE_EINVAL
 
 
+def test_every_entry_point_rejects_null_arguments_without_a_gpu():
+    """Null context, null buffers, unit sizes: every entry point returns
+    NE_EINVAL before touching the device (the crystal builder's outputs are
+    all optional, so there a null call only counts sites)."""
+    L = ne.load()
+    for name in ne.SYMBOLS:
+        f = getattr(L, name)
+        args = [None if t is C.c_void_p else (1.0 if t is C.c_double else 1) for t in f.argtypes]
+        want = ne.NE_OK if name.startswith("ne_create_crystal") else ne.NE_EINVAL
+        assert f(*args) == want, name
+
+
 @pytest.mark.parametrize("lat,a,n,ca", [(ne.NE_BCC, 2.87, (4, 4, 4), None), (ne.NE_FCC, 3.65, (3, 4, 5), None),
                                        (ne.NE_HCP, 2.58, (4, 3, 3), None), (ne.NE_HCP, 2.58, (3, 3, 4), 1.6)])
 def test_crystal_matches_oracle(lat, a, n, ca):
