@@ -22,6 +22,10 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   switch_run (RS)       harmonic F(T) = 3NkT ln(hbar w/kT) at every T
   free_energy           F_E and dF_CM closed forms; low-T quasi-harmonic limit
   msd_fit               equipartition on a harmonic crystal
+  eam_virial_axes       sums to the virial; -dU/d eps_a by central differences;
+                        equal in-plane components on perfect hcp
+  barostat (aniso)      ideal-gas volume distribution; relaxes hcp to the
+                        static zero-stress a and c found from eam_virial_axes
   species tables        one species in a two-entry table reproduces the
                         single-species run; Einstein F additive over species;
                         eq. cm's centre-of-mass variance against sampling;
@@ -48,6 +52,7 @@ _lib = None
 BCC, FCC, HCP = 0, 1, 2
 PATH_FL, PATH_RS = 0, 1
 H0_EAM, H0_HARMONIC = 0, 1
+NPT_OFF, NPT_ISO, NPT_ANISO = 0, 1, 2
 STREAM_FL, STREAM_INITV, STREAM_RS, STREAM_MSD, STREAM_STEP = 0, 1, 2, 3, 4
 ERRORS = {0: "ok", -1: "EINVAL", -4: "ERANGE", -6: "ENAN"}
 
@@ -114,6 +119,7 @@ def lib():
             L.ora_pairs_cells.argtypes = [p, i, p, d, p, p, i, p]
             L.ora_eam_energy_forces.argtypes = [p, p, p, i, p, p, p, p]
             L.ora_eam_grad_theta.argtypes = [p, p, p, i, p, p]
+            L.ora_eam_virial_axes.argtypes = [p, p, p, i, p, p]
             L.ora_spring.argtypes = [p, p, i, d, p, p]
             L.ora_init_velocities.argtypes = [p, i, p]
             L.ora_switch_run.argtypes = [p, p, p, p, p, p, i, p, p, p, p, p, p, i, i]
@@ -171,8 +177,9 @@ def md(dt=1e-3, T=100.0, damp=0.1, mass=None, k_spring=5.0, lambda_fn=2, path=PA
        t_eq=0, t_s=1, lambda_f=0.5, seed=1, replica=0, fix_cm=1, h0=H0_EAM,
        k_h0=0.0, npt=0, P0=0.0, beta_T=0.0, tau_p=0.0, species=None, mass_s=None,
        k_s=None) -> MD:
-    """npt = 1: isotropic barostat at pressure P0 (eV/A^3) with coupling
-    compressibility beta_T (A^3/eV) and time tau_p (ps); RS path only.
+    """npt = NPT_ISO: isotropic barostat at pressure P0 (eV/A^3) with coupling
+    compressibility beta_T (A^3/eV) and time tau_p (ps); NPT_ANISO: the same
+    on each box edge separately (non-cubic cells); RS path only.
 
     species ([n] ints), mass_s and k_s ([n_species]): one mass and one Einstein
     spring per species (Sec. V); mass and k_spring are then unused.  The
@@ -269,6 +276,15 @@ def eam_virial(p: EAM, theta, x, box):
     _check(lib().ora_eam_virial(C.byref(p), _ptr(theta), _ptr(x), x.shape[0], _ptr(box), C.byref(W)),
            "eam_virial")
     return W.value
+
+
+def eam_virial_axes(p: EAM, theta, x, box):
+    """Diagonal of the virial tensor, W_a = -dU/d eps_a (axis a scaled alone)."""
+    theta, x, box = _f64(theta), _f64(x), _f64(box)
+    W = np.zeros(3)
+    _check(lib().ora_eam_virial_axes(C.byref(p), _ptr(theta), _ptr(x), x.shape[0], _ptr(box), _ptr(W)),
+           "eam_virial_axes")
+    return W
 
 
 def eam_grad_theta(p: EAM, theta, x, box):

@@ -390,6 +390,46 @@ int ora_eam_virial(const ora_eam* p, const double* theta, const double* x, int n
     return ORA_OK;
 }
 
+/* Diagonal of the configurational virial tensor, W_a = sum_{i<j} r_ij,a F_ij,a
+ * = -sum_{i<j} (r_ij,a^2 / r) dU/dr, the axis-by-axis form of the zero-stress
+ * condition of the anisotropic barostat (Sec. III.A, fix nph aniso):
+ * W_a = -dU/d eps_a when axis a and its coordinates scale by e^eps_a.  The
+ * three sum to the virial above. */
+int ora_eam_virial_axes(const ora_eam* p, const double* theta, const double* x, int n,
+                        const double box[3], double W[3])
+{
+    int nk = p->n_knots;
+    const double* th_phi = theta;
+    const double* th_f = theta + 2 * nk;
+    const double* th_F = theta + 4 * nk;
+    double* rho = calloc(n > 0 ? n : 1, sizeof(double));
+    double E;
+    int st = ora_eam_energy_forces(p, theta, x, n, box, NULL, &E, rho);
+    if (st) { free(rho); return st; }
+    int *pi, *pj, np;
+    st = pair_list(x, n, box, p->r_c, &pi, &pj, &np);
+    if (st) { free(rho); return st; }
+    double w[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < np; q++) {
+        int i = pi[q], j = pj[q];
+        double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
+        min_image(box, d);
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double fr, dfr, ph, dph, Fi, dFi, Fj, dFj;
+        ora_hermite(th_f, nk, p->r_c, r, &fr, &dfr);
+        ora_hermite(th_phi, nk, p->r_c, r, &ph, &dph);
+        ora_hermite(th_F, nk, p->rho_max, rho[i], &Fi, &dFi);
+        ora_hermite(th_F, nk, p->rho_max, rho[j], &Fj, &dFj);
+        double dU_dr = dph + (dFi + dFj) * dfr;
+        for (int a = 0; a < 3; a++) w[a] -= d[a] * d[a] / r * dU_dr;
+    }
+    free(pi);
+    free(pj);
+    free(rho);
+    for (int a = 0; a < 3; a++) W[a] = w[a];
+    return ORA_OK;
+}
+
 int ora_eam_grad_theta(const ora_eam* p, const double* theta, const double* x,
                        int n, const double box[3], double* grad)
 {
@@ -653,6 +693,7 @@ int ora_init_velocities(const ora_md* md, int n, double* v)
 /* Potential terms at one configuration (Wv: virial of U0, with the barostat). */
 typedef struct {
     double U0, UE, Wv;
+    double Wa[3];  /* diagonal of the virial tensor (anisotropic barostat) */
     double* F0;
     double* FE;
 } terms;
@@ -662,13 +703,17 @@ static int eval_terms(const ora_eam* p, const double* theta, const ora_md* md,
                       terms* t)
 {
     t->Wv = 0.0;
+    t->Wa[0] = t->Wa[1] = t->Wa[2] = 0.0;
     if (md->h0 == ORA_H0_HARMONIC) {
         ora_spring(x, x0, n, md->k_h0, t->F0, &t->U0);  /* with the barostat: k_h0 = 0, an ideal gas */
     } else {
         int st = ora_eam_energy_forces(p, theta, x, n, box, t->F0, &t->U0, NULL);
         if (st) return st;
-        if (md->npt) {
+        if (md->npt == ORA_NPT_ISO) {
             st = ora_eam_virial(p, theta, x, n, box, &t->Wv);
+            if (st) return st;
+        } else if (md->npt == ORA_NPT_ANISO) {
+            st = ora_eam_virial_axes(p, theta, x, n, box, t->Wa);
             if (st) return st;
         }
     }
@@ -715,7 +760,11 @@ static double dH_dlambda(const ora_md* md, const terms* t)
  *   d eps = m_p [(dof kT + lambda W)/(3V) - P0] dt + sqrt(2 kT m_p dt / V) eta,
  * W the virial of U at x_s (the Jacobian's kT/V cancels against dD/d eps);
  * positions and box are scaled by e^(d eps / 3) about the origin, eta
- * drawn from the barostat stream. */
+ * drawn from the barostat stream.  Per axis (ORA_NPT_ANISO), eps_a = ln L_a
+ * of each edge has p ~ V^(N'+1) exp(-(lambda U + P0 V)/kT) too (measure
+ * dL_x dL_y dL_z), and the same steps give the drive (N' kT + lambda W_a)/V
+ * - P0 per axis, W_a = -dU/d eps_a; coordinate a and edge a scale by
+ * e^(d eps_a), eta_a the a-th normal of the barostat stream. */
 static int md_step(const ora_eam* p, const double* theta, const ora_md* md,
                    uint32_t stream, long s, double lam_a, double lam_b, double* x,
                    double* v, const double* x0, int n, double box[3], terms* t,
@@ -746,7 +795,7 @@ static int md_step(const ora_eam* p, const double* theta, const ora_md* md,
         for (int i = 0; i < 3 * n; i++) v[i] = c1 * v[i] + xi[i];
     }
     for (int i = 0; i < 3 * n; i++) x[i] += 0.5 * dt * v[i];
-    if (md->npt) {
+    if (md->npt == ORA_NPT_ISO) {
         double kT = KB_EV_PER_K * md->T, V = box[0] * box[1] * box[2];
         double mp = md->beta_T / md->tau_p, z[3];
         ora_normals(md->seed, md->replica, ORA_STREAM_BARO, 0, (uint64_t)s, z);
@@ -755,6 +804,20 @@ static int md_step(const ora_eam* p, const double* theta, const ora_md* md,
         double mu = exp(deps / 3.0);
         for (int i = 0; i < 3 * n; i++) x[i] *= mu;
         for (int c = 0; c < 3; c++) box[c] *= mu;
+    } else if (md->npt == ORA_NPT_ANISO) {
+        /* one such equation per axis, eps_a = ln L_a, with the same mobility:
+         * d eps_a = m_p [(N' kT + lambda W_a)/V - P0] dt + sqrt(2 kT m_p dt / V) eta_a */
+        double kT = KB_EV_PER_K * md->T, V = box[0] * box[1] * box[2];
+        double mp = md->beta_T / md->tau_p, z[3], mu[3];
+        ora_normals(md->seed, md->replica, ORA_STREAM_BARO, 0, (uint64_t)s, z);
+        for (int c = 0; c < 3; c++) {
+            double drive = (dof(md, n) / 3.0 * kT + lam_b * t->Wa[c]) / V - md->P0;
+            double deps = mp * drive * dt + sqrt(2.0 * kT * mp * dt / V) * z[c];
+            mu[c] = exp(deps);
+        }
+        for (int i = 0; i < n; i++)
+            for (int c = 0; c < 3; c++) x[3 * i + c] *= mu[c];
+        for (int c = 0; c < 3; c++) box[c] *= mu[c];
     }
     int st = eval_terms(p, theta, md, x, x0, n, box, t);
     if (st) return st;
@@ -797,6 +860,7 @@ int ora_switch_run(const ora_eam* p, const double* theta, const ora_md* md,
 {
     if (n < 2 || md->t_s < 1 || md->t_eq < 0 || !species_valid(md, n)) return ORA_EINVAL;
     if (md->path == ORA_PATH_RS && !(md->lambda_f > 0 && md->lambda_f < 1)) return ORA_EINVAL;
+    if (md->npt < 0 || md->npt > ORA_NPT_ANISO) return ORA_EINVAL;
     if (md->npt && (md->path != ORA_PATH_RS || !(md->beta_T > 0) || !(md->tau_p > 0) || md->P0 < 0 ||
                     (md->h0 == ORA_H0_HARMONIC && md->k_h0 != 0.0)))
         return ORA_EINVAL;  /* the Einstein crystal has no pressure (Sec. III.A) */

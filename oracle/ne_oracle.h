@@ -25,6 +25,8 @@ enum { ORA_OK = 0, ORA_EINVAL = -1, ORA_ERANGE = -4, ORA_ENAN = -6 };
 enum { ORA_BCC = 0, ORA_FCC = 1, ORA_HCP = 2 };
 enum { ORA_PATH_FL = 0, ORA_PATH_RS = 1 };
 enum { ORA_H0_EAM = 0, ORA_H0_HARMONIC = 1 };
+/* barostat (ora_md.npt): off, isotropic, or one box edge at a time */
+enum { ORA_NPT_OFF = 0, ORA_NPT_ISO = 1, ORA_NPT_ANISO = 2 };
 /* Philox stream ids (4th counter word, low bits). */
 enum { ORA_STREAM_FL = 0, ORA_STREAM_INITV = 1, ORA_STREAM_RS = 2,
        ORA_STREAM_MSD = 3, ORA_STREAM_STEP = 4, ORA_STREAM_BARO = 5 };
@@ -52,7 +54,9 @@ typedef struct {
     int fix_cm;       /* 1: centre of mass held fixed (noise and force means removed) */
     int h0;           /* ORA_H0_EAM, or ORA_H0_HARMONIC (springs k_h0 to the sites) */
     double k_h0;
-    /* isotropic barostat (reversible-scaling path only, Sec. III.C): 0 off */
+    /* barostat (reversible-scaling path only, Sec. III.C): ORA_NPT_OFF,
+     * ORA_NPT_ISO (the volume) or ORA_NPT_ANISO (each box edge on its own,
+     * fix nph aniso of Sec. III.A, for non-cubic cells such as hcp) */
     int npt;
     double P0;        /* target pressure, eV/A^3 */
     double beta_T;    /* compressibility of the coupling, A^3/eV */
@@ -104,6 +108,10 @@ int ora_eam_energy_forces(const ora_eam* p, const double* theta, const double* x
  * (Sec. III.A zero-pressure condition; P = (N_dof k_B T + W) / (3V)). */
 int ora_eam_virial(const ora_eam* p, const double* theta, const double* x, int n,
                    const double box[3], double* W);
+/* Diagonal of the virial tensor, W_a = -dU/d eps_a for a scaling of axis a
+ * alone; W[0] + W[1] + W[2] is the virial above. */
+int ora_eam_virial_axes(const ora_eam* p, const double* theta, const double* x, int n,
+                        const double box[3], double W[3]);
 int ora_eam_grad_theta(const ora_eam* p, const double* theta, const double* x,
                        int n, const double box[3], double* grad);
 
@@ -124,8 +132,8 @@ int ora_init_velocities(const ora_md* md, int n, double* v);
  * Wcum_f / Wcum_b (nullable): cumulative work after each switch step, t_s+1.
  * trace (nullable): every trace_stride steps, 8 doubles
  *   (step, lambda, dH/dlambda, U0, U_E, T_internal, W_f, W_b).
- * With md->npt (RS path only) the box follows the isotropic barostat and
- * box[] returns the final box. */
+ * With md->npt (RS path only) the box follows the barostat, isotropic or
+ * per axis, and box[] returns the final box. */
 int ora_switch_run(const ora_eam* p, const double* theta, const ora_md* md,
                    double* x, double* v, const double* x0, int n,
                    double box[3], double* W_f, double* W_b,

@@ -647,3 +647,118 @@ def test_barostat_relaxes_a_cold_crystal_to_zero_pressure(pot):
     r = O.switch_run(p, th, m, x0, v, x0, box)
     assert r["box"][0] / 4 == pytest.approx(2.8705, abs=2.5e-3)
     assert np.allclose(r["box"], r["box"][0])
+
+
+# ------------------------------------------- per-axis virial and barostat
+@pytest.mark.parametrize("lat,a,dims,ca,amp,seed", [(O.BCC, 2.87, (5, 5, 5), None, 0.1, 12),
+                                                   (O.HCP, 2.60, (5, 3, 3), 1.58, 0.12, 13)])
+def test_virial_axes_are_single_axis_scaling_derivatives(pot, lat, a, dims, ca, amp, seed):
+    """W_a = -dU/d eps_a with axis a (coordinates and edge) scaled by e^eps_a
+    alone, by central differences; the three sum to the scalar virial."""
+    p, th = pot
+    x0, box = O.create_crystal(lat, a, *dims, c_over_a=ca)
+    x = x0 + np.random.default_rng(seed).uniform(-amp, amp, x0.shape)
+    Wa = O.eam_virial_axes(p, th, x, box)
+    assert Wa.sum() == pytest.approx(O.eam_virial(p, th, x, box), rel=1e-12)
+    h = 1e-5
+    for ax in range(3):
+        s = np.ones(3)
+        s[ax] = math.exp(h)
+        Up = O.eam_energy_forces(p, th, x * s, box * s)[0]
+        s[ax] = math.exp(-h)
+        Um = O.eam_energy_forces(p, th, x * s, box * s)[0]
+        assert Wa[ax] == pytest.approx(-(Up - Um) / (2 * h), rel=2e-6, abs=1e-6)
+
+
+def test_virial_axes_on_perfect_hcp_are_equal_in_the_basal_plane(pot):
+    """Hexagonal symmetry: the two in-plane components of the stress of a
+    perfect hcp cell are equal; off the zero-stress c/a the axial one is not."""
+    p, th = pot
+    x0, box = O.create_crystal(O.HCP, W.A_HCP, 5, 3, 3)
+    Wa = O.eam_virial_axes(p, th, x0, box)
+    assert Wa[0] == pytest.approx(Wa[1], rel=1e-12)
+    assert abs(Wa[2] - Wa[0]) > 0.1 * abs(Wa).max()
+
+
+def test_anisotropic_barostat_samples_the_ideal_gas_volume_distribution():
+    """Per-axis barostat, ideal gas: the box shape is free but the volume of
+    the N - 1 free positions must follow the same Gamma distribution as with
+    the isotropic barostat (mean N kT / P0, variance N (kT / P0)^2); a
+    kinetic drive of dof kT instead of N' kT per axis would triple it."""
+    n, T = 8, 300.0
+    kT = O.kB() * T
+    P0 = 2.585e-5
+    V0 = n * kT / P0
+    L = V0 ** (1 / 3)
+    x0 = np.random.default_rng(18).uniform(0, L, (n, 3))
+    box = np.array([L, L, L])
+    p = O.eam(**W.EAM_FE_LIKE)
+    th = np.zeros(3 * 2 * W.EAM_FE_LIKE["n_knots"])
+
+    def one(seed):
+        m = O.md(T=T, mass=mass(), path=O.PATH_RS, lambda_f=0.5, t_eq=1500, t_s=1, seed=seed,
+                 h0=O.H0_HARMONIC, k_h0=0.0, npt=O.NPT_ANISO, P0=P0, beta_T=1.0 / P0, tau_p=0.5)
+        r = O.switch_run(p, th, m, x0, O.init_velocities(m, n), x0, box)
+        return float(np.prod(r["box"])), r["box"]
+
+    with ThreadPoolExecutor(8) as ex:
+        out = list(ex.map(one, range(1, 801)))
+    Vs = np.array([o[0] for o in out])
+    se = Vs.std(ddof=1) / np.sqrt(len(Vs))
+    assert abs(Vs.mean() - V0) < max(4 * se, 0.02 * V0)
+    assert abs(Vs.mean() - V0) < 0.06 * V0
+    assert Vs.var(ddof=1) == pytest.approx(n * (kT / P0) ** 2, rel=0.3)
+    shapes = np.array([o[1][2] / o[1][0] for o in out])
+    assert shapes.std() > 0.05  # the edges did move independently
+
+
+def test_anisotropic_barostat_relaxes_hcp_to_the_static_zero_stress_cell(pot):
+    """fix nph aniso (Sec. III.A): hcp started at the ideal c/a under 4 GPa
+    of axial tension relaxes at 5 K, P0 = 0, to the cell whose static stress
+    vanishes on every axis (a, c from eam_virial_axes by root finding; the
+    kinetic pressure at 5 K moves them by ~1e-4 A).  The isotropic barostat
+    cannot change c/a."""
+    import scipy.optimize
+    p, th = pot
+
+    def stress(v):
+        x0, box = O.create_crystal(O.HCP, v[0], 5, 3, 3, c_over_a=v[1] / v[0])
+        Wa = O.eam_virial_axes(p, th, x0, box)
+        return [Wa[0] / np.prod(box), Wa[2] / np.prod(box)]
+
+    a_s, c_s = scipy.optimize.fsolve(stress, [W.A_HCP, W.A_HCP * math.sqrt(8 / 3)], xtol=1e-12)
+    x0, box = O.create_crystal(O.HCP, W.A_HCP, 5, 3, 3)
+    n, cells = len(x0), np.array([5.0, 3.0 * math.sqrt(3.0), 3.0])
+
+    def one(args):
+        seed, npt = args
+        m = O.md(T=5.0, mass=mass(), path=O.PATH_RS, lambda_f=0.9, t_eq=1000, t_s=1, seed=seed,
+                 npt=npt, P0=0.0, beta_T=1.2, tau_p=0.2)
+        return O.switch_run(p, th, m, x0, O.init_velocities(m, n), x0, box)["box"] / cells
+
+    with ThreadPoolExecutor(8) as ex:
+        got = np.array(list(ex.map(one, [(s, O.NPT_ANISO) for s in range(1, 9)])))
+    mean = got.mean(0)
+    assert mean[0] == pytest.approx(a_s, abs=3e-3)
+    assert mean[1] == pytest.approx(a_s, abs=3e-3)
+    assert mean[2] == pytest.approx(c_s, abs=3e-3)
+    assert abs(W.A_HCP - a_s) > 0.03 and abs(W.A_HCP * math.sqrt(8 / 3) - c_s) > 0.1
+    iso = one((1, O.NPT_ISO))
+    assert iso[2] / iso[0] == pytest.approx(math.sqrt(8 / 3), rel=1e-12)
+
+
+def test_anisotropic_barostat_moves_the_lattice_with_the_box(pot):
+    """Each barostat move scales coordinate a with edge a (fixed scaled
+    coordinates): a perfect bcc lattice at rest, without thermostat, stays
+    the perfect lattice of the new box, whose edges changed by different
+    factors (every site of a Bravais lattice is an inversion centre, so the
+    forces vanish under any homogeneous strain and only the barostat moves
+    the atoms)."""
+    p, th = pot
+    x0, box = O.create_crystal(O.BCC, 2.87, 5, 5, 5)
+    m = O.md(T=300.0, damp=0.0, mass=mass(), path=O.PATH_RS, lambda_f=0.9, t_eq=0, t_s=1, seed=21,
+             npt=O.NPT_ANISO, P0=0.0, beta_T=1.2, tau_p=0.2)
+    r = O.switch_run(p, th, m, x0, np.zeros_like(x0), x0, box)
+    ratio = r["box"] / box
+    assert np.ptp(ratio) > 1e-4
+    assert np.abs(r["x"] / r["box"] - x0 / box).max() < 1e-12
