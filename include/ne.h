@@ -421,6 +421,26 @@ ne_status ne_free_energy(int n, double V, double T, double mass, double k,
                          double* F_per_atom, double* stderr_per_atom,
                          double* Ediss_per_atom);
 
+/* Host only, FP64.  Eq. fl + eq. cm for a solid of several species with one
+ * Einstein spring per species (Sec. V: k_A, k_B for an A-B compound).
+ * species_host [n] gives each atom's species, 0 <= species[i] < n_species;
+ * mass_s_host and k_s_host [n_species] its mass (eV ps^2/A^2) and spring
+ * (eV/A^2).  F_E = sum_i 3 k_B T ln(hbar w_i / k_B T), w_i^2 = k_i/m_i.  The
+ * fixed centre of mass is the mass-weighted one, so the factor
+ * 2 pi k_B T/(N k) of eq. cm becomes 2 pi sigma^2, sigma^2 = k_B T
+ * sum_i (m_i/M)^2 / k_i (the per-axis variance of that centre in the
+ * Einstein crystal), with eq. cm's leading N/V kept.  With one species this
+ * is ne_free_energy.  W_*_host [n_seeds]; outputs per atom as in
+ * ne_free_energy (each nullable).  NE_EINVAL for a species index out of
+ * range or a non-positive mass or spring.  The switching runs themselves
+ * are single-species in this library. */
+ne_status ne_free_energy_species(int n, const int* species_host, int n_species,
+                                 const double* mass_s_host, const double* k_s_host,
+                                 double V, double T, const double* W_fwd_host,
+                                 const double* W_bwd_host, int n_seeds,
+                                 double* F_per_atom, double* stderr_per_atom,
+                                 double* Ediss_per_atom);
+
 /* Host only, FP64.  Eq. rs on a temperature grid: F_0(T) = F_0(T0)/l +
  * (3/2) N k_B T0 ln(l)/l + [W_{1->l} - W_{l->1}]/(2 l), l = T0/T, from the
  * seed-averaged cumulative works Wcum_*_host [n_seeds][t_s+1].  F0_T0 is the

@@ -1474,6 +1474,58 @@ ne_status ne_free_energy(int n, double V, double T, double mass, double k, const
     return NE_OK;
 }
 
+ne_status ne_free_energy_species(int n, const int* species, int n_species, const double* mass_s,
+                                 const double* k_s, double V, double T, const double* W_fwd,
+                                 const double* W_bwd, int n_seeds, double* F_per_atom,
+                                 double* stderr_per_atom, double* Ediss_per_atom)
+{
+    if (n < 1 || n_seeds < 1 || n_species < 1 || !species || !mass_s || !k_s || !W_fwd || !W_bwd ||
+        !(V > 0) || !(T > 0))
+        return NE_EINVAL;
+    for (int s = 0; s < n_species; ++s)
+        if (!(mass_s[s] > 0) || !(k_s[s] > 0)) return NE_EINVAL;
+    std::vector<long long> count(n_species, 0);
+    for (int i = 0; i < n; ++i) {
+        if (species[i] < 0 || species[i] >= n_species) return NE_EINVAL;
+        ++count[species[i]];
+    }
+    const double kT = kB * T;
+    // F_E: one oscillator frequency per species; the fixed centre is the
+    // mass-weighted one, with per-axis variance kT sum_s N_s m_s^2 / k_s / M^2.
+    double FE = 0.0, M = 0.0, m2k = 0.0;
+    for (int s = 0; s < n_species; ++s) {
+        if (!count[s]) continue;
+        const double Ns = (double)count[s], w = std::sqrt(k_s[s] / mass_s[s]);
+        FE += 3.0 * Ns * kT * std::log(HBAR * w / kT);
+        M += Ns * mass_s[s];
+        m2k += Ns * mass_s[s] * mass_s[s] / k_s[s];
+    }
+    const double sigma2 = kT * m2k / (M * M);
+    const double dcm = kT * std::log(n / V * std::pow(2.0 * PI * sigma2, 1.5));
+    double wf = 0, wb = 0;
+    for (int q = 0; q < n_seeds; ++q) {
+        wf += W_fwd[q];
+        wb += W_bwd[q];
+    }
+    wf /= n_seeds;
+    wb /= n_seeds;
+    if (F_per_atom) *F_per_atom = (FE + 0.5 * (wf - wb) + dcm) / n;
+    if (stderr_per_atom) {
+        double se = 0.0;
+        if (n_seeds > 1) {
+            double m = 0.5 * (wf - wb) / n, ss = 0.0;
+            for (int q = 0; q < n_seeds; ++q) {
+                double d = 0.5 * (W_fwd[q] - W_bwd[q]) / n - m;
+                ss += d * d;
+            }
+            se = std::sqrt(ss / (n_seeds - 1) / n_seeds);
+        }
+        *stderr_per_atom = se;
+    }
+    if (Ediss_per_atom) *Ediss_per_atom = -0.5 * (wf + wb) / n;
+    return NE_OK;
+}
+
 ne_status ne_jarzynski(double T, const double* W_host, int n_seeds, double* dF_out)
 {
     if (!W_host || n_seeds < 1 || !(T > 0) || !dF_out) return NE_EINVAL;

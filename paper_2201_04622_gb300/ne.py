@@ -30,7 +30,7 @@ SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_clone", "ne_ctx_set_theta"
            "ne_eam_backward", "ne_eam_backward_acc", "ne_noise", "ne_init_velocities", "ne_langevin_step",
            "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment", "ne_switch_run_segment_grad",
            "ne_profile_segment", "ne_crystal_run_segment", "ne_crystal_run_segment_cum",
-           "ne_msd_fit", "ne_free_energy", "ne_jarzynski",
+           "ne_msd_fit", "ne_free_energy", "ne_free_energy_species", "ne_jarzynski",
            "ne_rs_free_energy"]
 
 
@@ -110,6 +110,7 @@ def load(build_if_missing: bool = True):
                 "ne_crystal_run_segment_cum": [p, p, p, i, p, p, p, p, ll, ll, p],
                 "ne_msd_fit": [p, p, p, p, p, i, p, ll, ll, i, p, p, p],
                 "ne_free_energy": [i, d, d, d, d, p, p, i, p, p, p],
+                "ne_free_energy_species": [i, p, i, p, p, d, d, p, p, i, p, p, p],
                 "ne_jarzynski": [d, p, i, p],
                 "ne_rs_free_energy": [i, d, d, d, ll, p, p, i, p, i, p],
             }
@@ -438,6 +439,27 @@ def ne_free_energy(n, V, T, mass, k, W_fwd, W_bwd):
                                      wf.ctypes.data_as(C.c_void_p), wb.ctypes.data_as(C.c_void_p),
                                      wf.size, C.byref(F), C.byref(se), C.byref(ed)),
          "ne_free_energy")
+    return F.value, se.value, ed.value
+
+
+def ne_free_energy_species(species, mass_s, k_s, V, T, W_fwd, W_bwd):
+    """Eq. fl + eq. cm with one mass and one spring per species (Sec. V);
+    species [n] ints, mass_s and k_s [n_species]."""
+    import numpy as np
+    sp = np.ascontiguousarray(species, np.int32).ravel()
+    ms = np.ascontiguousarray(mass_s, np.float64).ravel()
+    ks = np.ascontiguousarray(k_s, np.float64).ravel()
+    if ms.size != ks.size:
+        raise ValueError("mass_s and k_s need one entry per species")
+    wf = np.ascontiguousarray(W_fwd, np.float64).ravel()
+    wb = np.ascontiguousarray(W_bwd, np.float64).ravel()
+    if wf.size != wb.size:
+        raise ValueError("W_fwd and W_bwd need one entry per seed")
+    F, se, ed = C.c_double(), C.c_double(), C.c_double()
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)
+    _err(None, load().ne_free_energy_species(sp.size, ptr(sp), ms.size, ptr(ms), ptr(ks), float(V), float(T),
+                                             ptr(wf), ptr(wb), wf.size, C.byref(F), C.byref(se),
+                                             C.byref(ed)), "ne_free_energy_species")
     return F.value, se.value, ed.value
 
 

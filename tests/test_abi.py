@@ -71,6 +71,33 @@ def test_free_energy_assembly_matches_oracle():
         assert np.allclose(a, b, rtol=1e-13, atol=1e-15)
 
 
+def test_species_free_energy_assembly_matches_oracle():
+    """Several species (Sec. V): the library's per-species sums against the
+    oracle's per-atom loops, and the one-species assembly when the table has
+    one entry."""
+    g = np.random.default_rng(7)
+    amu = O.amu()
+    for n, T, nsp in [(16, 300.0, 2), (432, 900.0, 3), (2000, 1400.0, 2)]:
+        sp = g.integers(0, nsp, n)
+        sp[:nsp] = np.arange(nsp)
+        ms = g.uniform(20.0, 200.0, nsp) * amu
+        ks = g.uniform(1.0, 9.0, nsp)
+        V = n * 11.82
+        wf = g.normal(-4.0 * n, 0.01 * n, 7)
+        wb = g.normal(4.0 * n, 0.01 * n, 7)
+        a = ne.ne_free_energy_species(sp, ms, ks, V, T, wf, wb)
+        b = O.free_energy_species(sp, ms, ks, V, T, wf, wb)
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-15)
+    m = W.MASS_FE_AMU * amu
+    one = ne.ne_free_energy_species(np.zeros(128, int), [m], [5.787], 128 * 11.82, 100.0, wf[:3], wb[:3])
+    assert np.allclose(one, ne.ne_free_energy(128, 128 * 11.82, 100.0, m, 5.787, wf[:3], wb[:3]),
+                       rtol=1e-13, atol=1e-15)
+    with pytest.raises(ne.NeError):
+        ne.ne_free_energy_species([0, 2], [m, m], [1.0, 1.0], 100.0, 300.0, [1.0], [1.0])
+    with pytest.raises(ne.NeError):
+        ne.ne_free_energy_species([0, 1], [m, m], [1.0, 0.0], 100.0, 300.0, [1.0], [1.0])
+
+
 def test_rs_assembly_matches_oracle():
     g = np.random.default_rng(5)
     n, T0, lf, ts = 128, 100.0, 0.0625, 400
