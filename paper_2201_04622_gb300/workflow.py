@@ -417,6 +417,29 @@ def rs_free_energy(lattice, a, n, T0, F0_T0_per_atom, lambda_f, t_s, Wcum_f, Wcu
     return ne.ne_rs_free_energy(nat, T0, F0_T0_per_atom * nat, lambda_f, t_s, Wcum_f, Wcum_b, T_grid)
 
 
+def transition_temperatures(T_grid, F_a, F_b):
+    """Temperatures where two phases exchange stability (Sec. IV): the sign
+    changes of dF(T) = F_a(T) - F_b(T) on an ascending T_grid.  Between two
+    consecutive grid points with nonzero dF of opposite sign the crossing is
+    located by linear interpolation; when grid points with dF exactly zero
+    separate them, it is the mean temperature of those points.  Returns a
+    list of (T, phase stable above: 0 for a, 1 for b)."""
+    T = np.asarray(T_grid, dtype=np.float64).ravel()
+    d = np.asarray(F_a, dtype=np.float64).ravel() - np.asarray(F_b, dtype=np.float64).ravel()
+    if T.size != d.size or T.size < 2 or np.any(np.diff(T) <= 0):
+        raise ValueError("T_grid must be ascending with one F_a and F_b value per point")
+    nz = np.flatnonzero(d != 0.0)
+    out = []
+    for q0, q1 in zip(nz[:-1], nz[1:]):
+        if np.sign(d[q0]) == np.sign(d[q1]):
+            continue
+        if q1 == q0 + 1:
+            Tc = T[q0] + (T[q1] - T[q0]) * d[q0] / (d[q0] - d[q1])
+        else:
+            Tc = T[q0 + 1:q1].mean()
+        out.append((float(Tc), 0 if d[q1] < 0 else 1))
+    return out
+
 
 def lambda_fl2(tau):
     """Frenkel-Ladd switching function of Sec. III.B (function 2):

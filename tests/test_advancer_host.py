@@ -70,3 +70,23 @@ def test_advancer_moves_a_failing_replica_and_keeps_the_others(monkeypatch):
         want = x0[offs[r]:offs[r + 1]] + nc * 1e-3 * (r + 1) + ng * 2e-3 * (r + 1)
         assert torch.allclose(x[offs[r]:offs[r + 1]], want, rtol=0, atol=1e-12)
         assert float(W[r, 0]) == nc * (r + 1) and float(W[r, 1]) == ng * (r + 1)
+
+
+def test_transition_temperatures_locate_every_crossing():
+    """Sec. IV: the temperature where G_a(T) = G_b(T), and which phase wins above it."""
+    from paper_2201_04622_gb300.workflow import transition_temperatures as tt
+    T = np.arange(100.0, 1001.0, 10.0)
+    # straight lines crossing at 487 K, b stable below and a above: found to rounding
+    got = tt(T, -1e-4 * T, -1e-4 * T + 2e-7 * (T - 487.0))
+    assert len(got) == 1 and abs(got[0][0] - 487.0) < 1e-9 and got[0][1] == 0
+    # three crossings of a sine, alternating winners, each within the grid's interpolation error
+    got = tt(T, 0 * T, 1e-3 * np.sin(T / 100.0))
+    want = [100 * np.pi, 200 * np.pi, 300 * np.pi]
+    assert [g[1] for g in got] == [1, 0, 1]
+    assert np.allclose([g[0] for g in got], want, atol=0.1)
+    # exact zeros on the grid count once; a touch without a sign change counts not at all
+    assert tt([1.0, 2.0, 3.0, 4.0], [1, 0, 0, -1], [0, 0, 0, 0]) == [(2.5, 0)]
+    assert tt([1.0, 2.0, 3.0], [1, 0, 1], [0, 0, 0]) == []
+    assert tt([1.0, 2.0], [0, 0], [0, 0]) == []
+    with pytest.raises(ValueError):
+        tt([2.0, 1.0], [0, 1], [1, 0])
