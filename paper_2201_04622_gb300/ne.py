@@ -129,16 +129,54 @@ def _torch():
 
 
 def _dev(t, n=None):
-    """Pointer of a contiguous float64 CUDA tensor (or None)."""
+    """Pointer of a contiguous float64 CUDA tensor (or None) holding at least
+    n elements; the size is checked first, so a host tensor of the right size
+    fails only on its device."""
     if t is None:
         return None
     torch = _torch()
-    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
-            and t.is_contiguous()):
+    if not isinstance(t, torch.Tensor):
         raise NeError(NE_EINVAL, "argument", "expected a contiguous float64 CUDA tensor")
     if n is not None and t.numel() < n:
-        raise NeError(NE_EINVAL, "argument", "tensor too small")
+        raise NeError(NE_EINVAL, "argument", "tensor too small: %d < %d elements" % (t.numel(), n))
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise NeError(NE_EINVAL, "argument", "expected a contiguous float64 CUDA tensor")
     return C.c_void_p(t.data_ptr())
+
+
+_BASIS = {NE_BCC: 2, NE_FCC: 4, NE_HCP: 4}
+_CTX_KNOTS = {}  # context handle -> n_knots, for the size of theta buffers
+
+
+def _knots6(ctx):
+    """Elements of a theta buffer [3][n_knots][2] of ctx (None when unknown)."""
+    nk = _CTX_KNOTS.get(getattr(ctx, "value", None))
+    return None if nk is None else 6 * nk
+
+
+def _batch_atoms(offsets, n_rep):
+    """Atoms of a batch from its offsets (n_rep + 1 entries, ascending from 0)."""
+    off = [int(o) for o in offsets]
+    if len(off) != n_rep + 1 or off[0] != 0 or any(b <= a for a, b in zip(off[:-1], off[1:])):
+        raise NeError(NE_EINVAL, "argument", "offsets must be n_rep + 1 ascending entries from 0")
+    return off[-1]
+
+
+def _crystal_atoms(crystals):
+    """Atoms of the crystal-runner replicas (lattice, a, nx, ny, nz[, c_over_a])."""
+    tot = 0
+    for c in crystals:
+        if int(c[0]) not in _BASIS:
+            raise NeError(NE_EINVAL, "argument", "unknown lattice")
+        tot += _BASIS[int(c[0])] * int(c[2]) * int(c[3]) * int(c[4])
+    return tot
+
+
+def _trace_rows(md, trace_stride):
+    """Rows ne_switch_run writes to its trace: every trace_stride steps of the
+    2 t_eq + 2 t_s steps of the run."""
+    stride = int(trace_stride) if int(trace_stride) > 0 else 1
+    return (2 * int(md.t_eq) + 2 * int(md.t_s) - 1) // stride + 1
 
 
 def _stream(stream):
@@ -183,26 +221,30 @@ def ne_ctx_create(eam: EamParams, max_atoms: int, max_replicas: int = 1):
     h = C.c_void_p()
     _err(None, load().ne_ctx_create(C.byref(eam), int(max_atoms), int(max_replicas), C.byref(h)),
          "ne_ctx_create")
+    _CTX_KNOTS[h.value] = int(eam.n_knots)
     return h
 
 
 def ne_ctx_destroy(ctx):
     _err(None, load().ne_ctx_destroy(ctx), "ne_ctx_destroy")
+    _CTX_KNOTS.pop(getattr(ctx, "value", None), None)
 
 
 def ne_ctx_clone(src, max_atoms: int, max_replicas: int = 1):
     """A second context with src's potential, theta and tuning."""
     h = C.c_void_p()
     _err(src, load().ne_ctx_clone(src, int(max_atoms), int(max_replicas), C.byref(h)), "ne_ctx_clone")
+    if getattr(src, "value", None) in _CTX_KNOTS:
+        _CTX_KNOTS[h.value] = _CTX_KNOTS[src.value]
     return h
 
 
 def ne_ctx_set_theta(ctx, theta, stream=None):
-    _err(ctx, load().ne_ctx_set_theta(ctx, _dev(theta), _stream(stream)), "ne_ctx_set_theta")
+    _err(ctx, load().ne_ctx_set_theta(ctx, _dev(theta, _knots6(ctx)), _stream(stream)), "ne_ctx_set_theta")
 
 
 def ne_ctx_get_theta(ctx, theta, stream=None):
-    _err(ctx, load().ne_ctx_get_theta(ctx, _dev(theta), _stream(stream)), "ne_ctx_get_theta")
+    _err(ctx, load().ne_ctx_get_theta(ctx, _dev(theta, _knots6(ctx)), _stream(stream)), "ne_ctx_get_theta")
 
 
 def ne_ctx_set_tuning(ctx, threads_per_atom):
@@ -301,7 +343,7 @@ def ne_spring_forces(x, x0, k, f=None, e=None, stream=None):
 def ne_eam_backward(ctx, prec, x, box, gE, gx, gtheta, stream=None):
     n = x.shape[0]
     _err(ctx, load().ne_eam_backward(ctx, int(prec), _dev(x, 3 * n), n, _box(box), float(gE),
-                                     _dev(gx, 3 * n), _dev(gtheta), _stream(stream)),
+                                     _dev(gx, 3 * n), _dev(gtheta, _knots6(ctx)), _stream(stream)),
          "ne_eam_backward")
 
 
@@ -309,7 +351,7 @@ def ne_eam_backward_acc(ctx, prec, x, box, gE, gtheta_acc, stream=None):
     """gtheta_acc += gE dU/dtheta at configuration x (device tensors)."""
     n = x.shape[0]
     _err(ctx, load().ne_eam_backward_acc(ctx, int(prec), _dev(x, 3 * n), n, _box(box), float(gE),
-                                         _dev(gtheta_acc), _stream(stream)), "ne_eam_backward_acc")
+                                         _dev(gtheta_acc, _knots6(ctx)), _stream(stream)), "ne_eam_backward_acc")
 
 
 def ne_noise(seed, replica, noise_stream, step, z, prec=NE_FP64, stream=None):
@@ -336,41 +378,43 @@ def ne_langevin_step(ctx, md: MdParams, x, v, x0, box, step, lambda_k, lambda_k1
 def ne_switch_run(ctx, md: MdParams, x, v, x0, box, W_fwd, W_bwd, Wcum_fwd=None, Wcum_bwd=None,
                   trace=None, trace_stride=0, stream=None):
     n = x.shape[0]
+    ncum = int(md.t_s) + 1
     _err(ctx, load().ne_switch_run(ctx, C.byref(md), _dev(x, 3 * n), _dev(v, 3 * n),
                                    _dev(x0, 3 * n), n, _box(box), _dev(W_fwd, 1), _dev(W_bwd, 1),
-                                   _dev(Wcum_fwd), _dev(Wcum_bwd), _dev(trace), int(trace_stride),
+                                   _dev(Wcum_fwd, ncum), _dev(Wcum_bwd, ncum),
+                                   _dev(trace, 8 * _trace_rows(md, trace_stride)), int(trace_stride),
                                    _stream(stream)), "ne_switch_run")
 
 
 def ne_rs_run(ctx, md: MdParams, lambda_f, x, v, x0, box, Wcum_fwd, Wcum_bwd, stream=None):
     n = x.shape[0]
     _err(ctx, load().ne_rs_run(ctx, C.byref(md), float(lambda_f), _dev(x, 3 * n), _dev(v, 3 * n),
-                               _dev(x0, 3 * n), n, _box(box), _dev(Wcum_fwd), _dev(Wcum_bwd),
-                               _stream(stream)), "ne_rs_run")
+                               _dev(x0, 3 * n), n, _box(box), _dev(Wcum_fwd, int(md.t_s) + 1),
+                               _dev(Wcum_bwd, int(md.t_s) + 1), _stream(stream)), "ne_rs_run")
 
 
-def ne_switch_run_batched(ctx, mds, offsets, x, v, x0, boxes, W_fwd, W_bwd, stream=None):
+def _batch_args(mds, offsets, boxes):
+    """(n_rep, md array, offsets array, boxes array, 3 * atoms) of a batch."""
     n_rep = len(mds)
+    n_atoms = _batch_atoms(offsets, n_rep)
+    if len(boxes) != n_rep or any(len(b) != 3 for b in boxes):
+        raise NeError(NE_EINVAL, "argument", "one box of 3 edges per replica")
     arr = (MdParams * n_rep)(*mds)
     off = (C.c_int * (n_rep + 1))(*[int(o) for o in offsets])
     flat = [float(b) for bx in boxes for b in bx]
-    bx = (C.c_double * len(flat))(*flat)
-    _err(ctx, load().ne_switch_run_batched(ctx, arr, n_rep, off, _dev(x), _dev(v), _dev(x0), bx,
+    return n_rep, arr, off, (C.c_double * len(flat))(*flat), 3 * n_atoms
+
+
+def ne_switch_run_batched(ctx, mds, offsets, x, v, x0, boxes, W_fwd, W_bwd, stream=None):
+    n_rep, arr, off, bx, n3 = _batch_args(mds, offsets, boxes)
+    _err(ctx, load().ne_switch_run_batched(ctx, arr, n_rep, off, _dev(x, n3), _dev(v, n3), _dev(x0, n3), bx,
                                            _dev(W_fwd, n_rep), _dev(W_bwd, n_rep),
                                            _stream(stream)), "ne_switch_run_batched")
 
 
-def _batch_args(mds, offsets, boxes):
-    n_rep = len(mds)
-    arr = (MdParams * n_rep)(*mds)
-    off = (C.c_int * (n_rep + 1))(*[int(o) for o in offsets])
-    flat = [float(b) for bx in boxes for b in bx]
-    return n_rep, arr, off, (C.c_double * len(flat))(*flat)
-
-
 def ne_switch_run_segment(ctx, mds, offsets, x, v, x0, boxes, W, step_begin, n_steps, stream=None):
-    n_rep, arr, off, bx = _batch_args(mds, offsets, boxes)
-    _err(ctx, load().ne_switch_run_segment(ctx, arr, n_rep, off, _dev(x), _dev(v), _dev(x0), bx,
+    n_rep, arr, off, bx, n3 = _batch_args(mds, offsets, boxes)
+    _err(ctx, load().ne_switch_run_segment(ctx, arr, n_rep, off, _dev(x, n3), _dev(v, n3), _dev(x0, n3), bx,
                                            _dev(W, 2 * n_rep), int(step_begin), int(n_steps),
                                            _stream(stream)), "ne_switch_run_segment")
 
@@ -378,20 +422,21 @@ def ne_switch_run_segment(ctx, mds, offsets, x, v, x0, boxes, W, step_begin, n_s
 def ne_switch_run_segment_grad(ctx, mds, offsets, x, v, x0, boxes, W, step_begin, n_steps, w, gtheta, stream=None):
     """ne_switch_run_segment plus gtheta += sum_k w[k - step_begin] dU/dtheta(x_k)
     (w: device float64 [n_steps + 1]; gtheta: device float64 [3 * n_knots * 2])."""
-    n_rep, arr, off, bx = _batch_args(mds, offsets, boxes)
-    _err(ctx, load().ne_switch_run_segment_grad(ctx, arr, n_rep, off, _dev(x), _dev(v), _dev(x0), bx,
+    n_rep, arr, off, bx, n3 = _batch_args(mds, offsets, boxes)
+    _err(ctx, load().ne_switch_run_segment_grad(ctx, arr, n_rep, off, _dev(x, n3), _dev(v, n3), _dev(x0, n3), bx,
                                                 _dev(W, 2 * n_rep), int(step_begin), int(n_steps),
-                                                _dev(w, int(n_steps) + 1), _dev(gtheta), _stream(stream)),
+                                                _dev(w, int(n_steps) + 1), _dev(gtheta, _knots6(ctx)),
+                                                _stream(stream)),
          "ne_switch_run_segment_grad")
 
 
 def ne_profile_segment(ctx, mds, offsets, x, v, x0, boxes, W, step_begin, n_steps, stream=None):
     """Returns (mean ms per launch [4], launches [4]) for list build, pass 1,
     pass 2 and the fused step."""
-    n_rep, arr, off, bx = _batch_args(mds, offsets, boxes)
+    n_rep, arr, off, bx, n3 = _batch_args(mds, offsets, boxes)
     ms = (C.c_double * 4)()
     cnt = (C.c_longlong * 4)()
-    _err(ctx, load().ne_profile_segment(ctx, arr, n_rep, off, _dev(x), _dev(v), _dev(x0), bx,
+    _err(ctx, load().ne_profile_segment(ctx, arr, n_rep, off, _dev(x, n3), _dev(v, n3), _dev(x0, n3), bx,
                                         _dev(W, 2 * n_rep), int(step_begin), int(n_steps), ms, cnt,
                                         _stream(stream)), "ne_profile_segment")
     return list(ms), list(cnt)
@@ -403,7 +448,8 @@ def ne_crystal_run_segment(ctx, mds, crystals, x, v, W, step_begin, n_steps, str
     arr = (MdParams * n_rep)(*mds)
     cr = (Crystal * n_rep)(*[Crystal(int(c[0]), float(c[1]), int(c[2]), int(c[3]), int(c[4]),
                                      float(c[5]) if len(c) > 5 else 0.0) for c in crystals])
-    _err(ctx, load().ne_crystal_run_segment(ctx, arr, cr, n_rep, _dev(x), _dev(v), _dev(W, 2 * n_rep),
+    n3 = 3 * _crystal_atoms(crystals)
+    _err(ctx, load().ne_crystal_run_segment(ctx, arr, cr, n_rep, _dev(x, n3), _dev(v, n3), _dev(W, 2 * n_rep),
                                             int(step_begin), int(n_steps), _stream(stream)),
          "ne_crystal_run_segment")
 
@@ -414,7 +460,8 @@ def ne_crystal_run_segment_cum(ctx, mds, crystals, x, v, W, Wcum, step_begin, n_
     arr = (MdParams * n_rep)(*mds)
     cr = (Crystal * n_rep)(*[Crystal(int(c[0]), float(c[1]), int(c[2]), int(c[3]), int(c[4]),
                                      float(c[5]) if len(c) > 5 else 0.0) for c in crystals])
-    _err(ctx, load().ne_crystal_run_segment_cum(ctx, arr, cr, n_rep, _dev(x), _dev(v), _dev(W, 2 * n_rep),
+    n3 = 3 * _crystal_atoms(crystals)
+    _err(ctx, load().ne_crystal_run_segment_cum(ctx, arr, cr, n_rep, _dev(x, n3), _dev(v, n3), _dev(W, 2 * n_rep),
                                                 _dev(Wcum, n_rep * 2 * (int(mds[0].t_s) + 1)),
                                                 int(step_begin), int(n_steps), _stream(stream)),
          "ne_crystal_run_segment_cum")
