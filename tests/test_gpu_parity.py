@@ -684,3 +684,46 @@ def test_fused_run_gradient_equals_separate_backward_calls(ctx, prec):
     tol = (1e-12 if prec == ne.NE_FP64 else 1e-5) * np.abs(b).max()
     assert np.abs(a - b).max() < tol
     assert np.abs(b).max() > 0
+
+
+def test_small_case_at_full_length_against_the_oracle(ctx):
+    """bcc 4x4x4 (128 atoms, a = 2.87 A) at 100 K at full length against the
+    oracle's stored results (tests/golden/c1_works.json, written by
+    make_c1_works.py from oracle/ alone): the spring from eq. msd (2000 + 2000
+    x 5 steps), then ten seeds of 2000 + 5000 + 2000 + 5000 steps as one
+    batch.  FP64: the fit and every work equal the oracle's to rounding;
+    mixed: F within 1 meV/atom of the oracle's, and within two combined
+    standard errors."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c1_works.json")))
+    x0, box = O.create_crystal(O.BCC, g["a"], g["cells"], g["cells"], g["cells"])
+    n, V, Tk, k = len(x0), float(np.prod(box)), g["T"], g["k"]
+    fit = g["fit"]
+    mo, mg = md_pair(T=Tk, k_spring=1.0, seed=fit["seed"], replica=fit["replica"])
+    x, v = T(x0), T(O.init_velocities(mo, n))
+    msd, kf = ne.ne_msd_fit(ctx, mg, x, v, T(x0), box, fit["n_eq"], fit["n_samples"], fit["stride"])
+    assert kf == pytest.approx(k, rel=1e-6) and msd == pytest.approx(g["msd"], rel=1e-6)
+    rows = g["rows"]
+    offs = [r * n for r in range(len(rows) + 1)]
+    F = {}
+    for name, prec in (("fp64", ne.NE_FP64), ("mixed", ne.NE_MIXED)):
+        mos, mgs, vs = [], [], []
+        for row in rows:
+            mo, mg = md_pair(T=Tk, k_spring=k, t_eq=g["t_eq"], t_s=g["t_s"], seed=row["seed"],
+                             replica=row["replica"], prec=prec)
+            mgs.append(mg)
+            vs.append(O.init_velocities(mo, n))
+        X0 = T(np.concatenate([x0] * len(rows)))
+        x, v = X0.clone(), T(np.concatenate(vs))
+        wf = torch.zeros(len(rows), dtype=torch.float64, device=DEV)
+        wb = torch.zeros_like(wf)
+        ne.ne_switch_run_batched(ctx, mgs, offs, x, v, X0, [box] * len(rows), wf, wb)
+        wf, wb = N(wf), N(wb)
+        if prec == ne.NE_FP64:
+            assert np.abs(wf - [r["W_f"] for r in rows]).max() < 1e-4
+            assert np.abs(wb - [r["W_b"] for r in rows]).max() < 1e-4
+        F[name] = ne.ne_free_energy(n, V, Tk, MASS, k, wf, wb)
+    assert F["fp64"][0] == pytest.approx(g["F_per_atom"], abs=1e-8)
+    assert abs(F["mixed"][0] - g["F_per_atom"]) < 1e-3
+    assert abs(F["mixed"][0] - g["F_per_atom"]) < 2 * math.hypot(F["mixed"][1], g["stderr_per_atom"]) + 1e-4
