@@ -13,15 +13,20 @@ def tune(ctx, mds, offsets, x, v, x0, boxes, W, step_begin=0, n_steps=100,
          threads_per_atom=(1, 2, 4, 8), skins=None):
     """Return (best, table): best = dict(tpa, skin, ms_per_step); table = all
     candidates.  The state (x, v, W) is restored after every trial."""
-    import torch
+    rc = ne.ctx_cutoff(ctx)
+    if rc is None:
+        raise ValueError("context not created through this binding: its cutoff is unknown")
     skins = skins or [m.skin for m in mds[:1]]
     L_min = min(min(b) for b in boxes)
+    fits = [(tpa, skin) for tpa, skin in itertools.product(threads_per_atom, skins)
+            if 2 * (rc + skin) < L_min]  # the list range must stay under half the box
+    if not fits:
+        raise ValueError("no candidate skin fits the smallest box (%.3f A) with r_c = %.3f A" % (L_min, rc))
+    import torch
     saved = (x.clone(), v.clone(), W.clone())
     old = [m.skin for m in mds]
     table = []
-    for tpa, skin in itertools.product(threads_per_atom, skins):
-        if 2 * (5.3 + skin) >= L_min:
-            continue
+    for tpa, skin in fits:
         for m in mds:
             m.skin = skin
         ne.ne_ctx_set_tuning(ctx, tpa)

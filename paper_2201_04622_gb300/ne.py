@@ -145,13 +145,19 @@ def _dev(t, n=None):
 
 
 _BASIS = {NE_BCC: 2, NE_FCC: 4, NE_HCP: 4}
-_CTX_KNOTS = {}  # context handle -> n_knots, for the size of theta buffers
+_CTX_EAM = {}  # context handle -> (n_knots, r_c) of its potential
 
 
 def _knots6(ctx):
     """Elements of a theta buffer [3][n_knots][2] of ctx (None when unknown)."""
-    nk = _CTX_KNOTS.get(getattr(ctx, "value", None))
-    return None if nk is None else 6 * nk
+    e = _CTX_EAM.get(getattr(ctx, "value", None))
+    return None if e is None else 6 * e[0]
+
+
+def ctx_cutoff(ctx):
+    """Cutoff r_c (A) of the potential of a context this binding created, else None."""
+    e = _CTX_EAM.get(getattr(ctx, "value", None))
+    return None if e is None else e[1]
 
 
 def _batch_atoms(offsets, n_rep):
@@ -221,21 +227,21 @@ def ne_ctx_create(eam: EamParams, max_atoms: int, max_replicas: int = 1):
     h = C.c_void_p()
     _err(None, load().ne_ctx_create(C.byref(eam), int(max_atoms), int(max_replicas), C.byref(h)),
          "ne_ctx_create")
-    _CTX_KNOTS[h.value] = int(eam.n_knots)
+    _CTX_EAM[h.value] = (int(eam.n_knots), float(eam.r_c))
     return h
 
 
 def ne_ctx_destroy(ctx):
     _err(None, load().ne_ctx_destroy(ctx), "ne_ctx_destroy")
-    _CTX_KNOTS.pop(getattr(ctx, "value", None), None)
+    _CTX_EAM.pop(getattr(ctx, "value", None), None)
 
 
 def ne_ctx_clone(src, max_atoms: int, max_replicas: int = 1):
     """A second context with src's potential, theta and tuning."""
     h = C.c_void_p()
     _err(src, load().ne_ctx_clone(src, int(max_atoms), int(max_replicas), C.byref(h)), "ne_ctx_clone")
-    if getattr(src, "value", None) in _CTX_KNOTS:
-        _CTX_KNOTS[h.value] = _CTX_KNOTS[src.value]
+    if getattr(src, "value", None) in _CTX_EAM:
+        _CTX_EAM[h.value] = _CTX_EAM[src.value]
     return h
 
 

@@ -85,13 +85,13 @@ def test_batched_runs_require_the_atoms_their_offsets_name(recorded):
     got = recorded(ne.ne_profile_segment, None, mds, offs, x, x, x, boxes, _z(2, 2), 0, 10)
     assert [r for _, r in got] == [120, 120, 120, 4]
     ctx = C.c_void_p(0x5150)
-    ne._CTX_KNOTS[ctx.value] = 7
+    ne._CTX_EAM[ctx.value] = (7, 5.3)
     try:
         got = recorded(ne.ne_switch_run_segment_grad, ctx, mds, offs, x, x, x, boxes, _z(2, 2), 0, 10, _z(11),
                        _z(42))
         assert [r for _, r in got] == [120, 120, 120, 4, 11, 42]
     finally:
-        ne._CTX_KNOTS.pop(ctx.value)
+        ne._CTX_EAM.pop(ctx.value)
     for bad_offs in ([0, 16], [1, 16, 40], [0, 16, 16], [0, 20, 16]):
         with pytest.raises(ne.NeError, match="offsets"):
             recorded(ne.ne_switch_run_segment, None, mds, bad_offs, x, x, x, boxes, _z(2, 2), 0, 10)
@@ -115,7 +115,7 @@ def test_crystal_runner_requires_the_atoms_of_its_cells(recorded):
 
 def test_theta_buffers_require_the_context_knots(recorded):
     ctx = C.c_void_p(0x6160)
-    ne._CTX_KNOTS[ctx.value] = 9
+    ne._CTX_EAM[ctx.value] = (9, 5.3)
     try:
         for fn in (ne.ne_ctx_set_theta, ne.ne_ctx_get_theta):
             assert recorded(fn, ctx, _z(54)) == [(54, 54)]
@@ -124,6 +124,33 @@ def test_theta_buffers_require_the_context_knots(recorded):
         got = recorded(ne.ne_eam_backward_acc, ctx, ne.NE_FP64, _z(4, 3), [9.0] * 3, 1.0, _z(54))
         assert [r for _, r in got] == [12, 54]
     finally:
-        ne._CTX_KNOTS.pop(ctx.value)
+        ne._CTX_EAM.pop(ctx.value)
     # a context the binding did not create: no knot count, no check
     assert recorded(ne.ne_ctx_set_theta, C.c_void_p(0x7170), _z(3)) == [(3, None)]
+
+
+def test_autotuner_refuses_a_box_no_candidate_fits(monkeypatch):
+    """Candidates whose list range 2 (r_c + skin) reaches the box are skipped
+    (r_c of the context's own potential); with none left the tuner says so
+    before any device work, and the caller's skins are left as they were."""
+    from paper_2201_04622_gb300 import autotune
+
+    def no_device_work(*a, **k):
+        raise AssertionError("the tuner reached the library")
+
+    monkeypatch.setattr(ne, "ne_ctx_set_tuning", no_device_work)
+    monkeypatch.setattr(ne, "ne_profile_segment", no_device_work)
+    ctx = C.c_void_p(0x8180)
+    ne._CTX_EAM[ctx.value] = (5000, 5.3)
+    try:
+        mds = [ne.md_params(skin=0.7)]
+        x = _z(128, 3)
+        # bcc 4^3 is 11.48 A wide: 2 (5.3 + 0.5) = 11.6 and 2 (5.3 + 0.7) = 12 do not fit
+        with pytest.raises(ValueError, match="no candidate"):
+            autotune.tune(ctx, mds, [0, 128], x, x.clone(), x.clone(), [[11.48] * 3], _z(1, 2),
+                          skins=[0.5, 0.7])
+        assert mds[0].skin == 0.7
+    finally:
+        ne._CTX_EAM.pop(ctx.value)
+    with pytest.raises(ValueError, match="not created"):
+        autotune.tune(C.c_void_p(0x9190), [ne.md_params()], [0, 128], x, x, x, [[20.0] * 3], _z(1, 2))
