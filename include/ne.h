@@ -334,8 +334,9 @@ ne_status ne_switch_run_segment_grad(ne_ctx* ctx, const ne_md_params* md, int n_
                                      long long step_begin, long long n_steps, const double* w_dev,
                                      double* gtheta_dev, void* stream);
 
-/* A crystal replica: nx*ny*nz cells of a bcc or fcc lattice with parameter a;
- * its sites r0 and atom order are those of ne_create_crystal. */
+/* A crystal replica: nx*ny*nz cells of a bcc, fcc or hcp lattice with
+ * parameter a (hcp: the orthohexagonal cell of ne_create_crystal_ca); its
+ * sites r0 and atom order are those of ne_create_crystal_ca. */
 typedef struct {
     ne_lattice lattice;
     double a;
