@@ -560,8 +560,8 @@ def eam_energy_function():
             x, theta = fctx.saved_tensors
             ctx, box, prec = fctx.ne
             ne_ctx_set_theta(ctx, theta.detach().contiguous())
-            gx = torch.empty_like(x)
-            gth = torch.empty_like(theta)
+            gx = torch.empty_like(x, memory_format=torch.contiguous_format)
+            gth = torch.empty_like(theta, memory_format=torch.contiguous_format)
             ne_eam_backward(ctx, prec, x.detach().contiguous(), box, float(gE), gx, gth)
             return gx, gth, None, None, None
 
