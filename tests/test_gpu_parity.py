@@ -727,3 +727,39 @@ def test_small_case_at_full_length_against_the_oracle(ctx):
     assert F["fp64"][0] == pytest.approx(g["F_per_atom"], abs=1e-8)
     assert abs(F["mixed"][0] - g["F_per_atom"]) < 1e-3
     assert abs(F["mixed"][0] - g["F_per_atom"]) < 2 * math.hypot(F["mixed"][1], g["stderr_per_atom"]) + 1e-4
+
+
+def test_uneven_256_replica_set_at_full_length_against_the_oracle():
+    """The 256-replica uneven set (bcc 6-12^3 / fcc 5-10^3, 300-1600 K, t_eq =
+    10 ps, t_s = 20 ps) through workflow.fl_batch(runner="auto") -- the
+    crystal runner in 20,000-step chunks, a replica that leaves its range
+    continuing on the multi-kernel path -- against the oracle's works for a
+    stated subset (the 16 smallest replicas and 8 drawn by PCG64(3);
+    tests/golden/config3_subset_works.json from make_config3_subset_works.py):
+    each replica's F within 1 meV/atom of the oracle's."""
+    import json
+    import os
+    import warnings
+    from paper_2201_04622_gb300 import workflow as WF
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "config3_subset_works.json")))
+    reps = W.batched_replicas(256, seed=1)
+    a = {W.BCC: W.A_BCC, W.FCC: W.A_FCC}
+    k = {W.BCC: W.K_BCC_1400, W.FCC: W.K_FCC_1400}
+    crystals = [(r["lattice"], a[r["lattice"]], r["n"]) for r in reps]
+    big = ne.ne_ctx_create(ne.eam_params(**W.EAM_FE_LIKE), 500000, 256)
+    try:
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore")  # a hop at high T moves its replica to the multi-kernel path
+            Wf, Wb, _ = WF.fl_batch(big, crystals, [r["T"] for r in reps], [k[r["lattice"]] for r in reps],
+                                    [r["seed"] for r in reps], g["t_eq"], g["t_s"], MASS, runner="auto",
+                                    chunk=20000)
+    finally:
+        ne.ne_ctx_destroy(big)
+    dF = []
+    for row in g["rows"]:
+        q = row["replica"]
+        assert reps[q]["lattice"] == row["lattice"] and reps[q]["n"] == row["n"]
+        x0, box = O.create_crystal(row["lattice"], row["a"], row["n"], row["n"], row["n"])
+        F = ne.ne_free_energy(len(x0), float(np.prod(box)), row["T"], MASS, row["k"], [Wf[q]], [Wb[q]])[0]
+        dF.append(F - row["F_per_atom"])
+    assert len(dF) == 24 and np.abs(dF).max() < 1e-3, np.abs(dF).max()
