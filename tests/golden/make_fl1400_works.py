@@ -10,6 +10,11 @@ Philox noise is keyed by (seed, replica).
 Calls only the oracle.  About half an hour on eight host cores:
 
     python tests/golden/make_fl1400_works.py
+
+With --all it writes fl1400_all_works.json for all twenty replicas of the
+batch (seeds 1-10 of each lattice), taking the eight rows of
+fl1400_works.json as they are (the oracle is deterministic) and running the
+other twelve: about an hour on eight host cores.
 """
 import json
 import os
@@ -26,6 +31,8 @@ T_EQ, T_S = 10000, 50000
 # (lattice, a, n, k, seed, replica index in the 20-replica batch)
 JOBS = [(0, 2.87, 10, 2.38, s, s - 1) for s in (1, 2, 3, 4)] + \
        [(1, 3.65, 8, 2.68, s, 10 + s - 1) for s in (1, 2, 3, 4)]
+JOBS_ALL = [(0, 2.87, 10, 2.38, s, s - 1) for s in range(1, 11)] + \
+           [(1, 3.65, 8, 2.68, s, 10 + s - 1) for s in range(1, 11)]
 
 
 def run(job):
@@ -47,15 +54,22 @@ def main():
     import oracle as O
     O.build()
     t0 = time.time()
+    everything = "--all" in sys.argv
+    jobs, done = (JOBS_ALL, []) if everything else (JOBS, [])
+    if everything:
+        with open(os.path.join(HERE, "fl1400_works.json")) as f:
+            done = json.load(f)["rows"]
+        have = {(r["lattice"], r["seed"]) for r in done}
+        jobs = [j for j in JOBS_ALL if (j[0], j[4]) not in have]
     with ProcessPoolExecutor(max_workers=min(8, os.cpu_count() or 1),
                              mp_context=mp.get_context("spawn")) as ex:
-        rows = list(ex.map(run, JOBS))
+        rows = sorted(done + list(ex.map(run, jobs)), key=lambda r: r["replica"])
     doc = {"_source": "CPU FP64 oracle (oracle/), written by tests/golden/make_fl1400_works.py",
            "cite": "Sec. III.A-B: Frenkel-Ladd switching, forward and backward works (eq. fl)",
            "T": T, "t_eq": T_EQ, "t_s": T_S, "dt_ps": 1e-3, "damping_ps": 0.1, "lambda_fn": 2,
            "batch": "10 x bcc 10^3 (a 2.87, k 2.38, seeds 1-10) then 10 x fcc 8^3 (a 3.65, k 2.68, seeds 1-10)",
            "rows": rows}
-    with open(os.path.join(HERE, "fl1400_works.json"), "w") as f:
+    with open(os.path.join(HERE, "fl1400_all_works.json" if everything else "fl1400_works.json"), "w") as f:
         json.dump(doc, f, indent=1)
     print("wrote %d rows in %.0f s" % (len(rows), time.time() - t0))
 
