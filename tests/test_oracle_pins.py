@@ -792,3 +792,45 @@ def test_two_sided_estimate_removes_the_dissipation_bias_of_short_switches(pot):
     assert abs(F2 - ref) < 4 * math.hypot(se, se_ref)
     assert F_fwd - ref < -1e-3 and F_bwd - ref > 1e-3
     assert ed > 1e-3
+
+
+@pytest.mark.slow
+def test_rs_of_the_eam_crystal_matches_an_independent_fl_point(pot):
+    """The check of Sec. III.C (fig. bcc) on the anharmonic crystal: eq. rs
+    from the 100 K Frenkel-Ladd reference of the 4x4x4 bcc cell
+    (tests/golden/c1_works.json) up to 400 K (lambda_f = 0.25, 20,000-step
+    switches, 8 seeds) equals a separate Frenkel-Ladd calculation at 400 K
+    (spring from eq. msd at 400 K, 8 seeds), both at the cell's fixed
+    volume, within 4 combined standard errors (~1 meV/atom).  Dropping the
+    kinetic term of eq. rs would move F by 72 meV/atom; a wrong sign or
+    mapping of the works, by eV."""
+    p, th = pot
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c1_works.json")))
+    x0, box = O.create_crystal(O.BCC, g["a"], g["cells"], g["cells"], g["cells"])
+    n, V = len(x0), float(np.prod(box))
+    T0, T1, lf, ts = g["T"], 400.0, 0.25, 20000
+
+    def rs(seed):
+        m = O.md(T=T0, mass=mass(), path=O.PATH_RS, lambda_f=lf, t_eq=2000, t_s=ts, seed=seed, replica=seed)
+        r = O.switch_run(p, th, m, x0, O.init_velocities(m, n), x0, box, cumulative=True)
+        return r["Wcum_f"], r["Wcum_b"]
+
+    mf = O.md(T=T1, mass=mass(), k_spring=1.0, seed=1, replica=0)
+    _, k = O.msd_fit(p, th, mf, x0, O.init_velocities(mf, n), x0, box, 2000, 2000, 5)
+
+    def fl(seed):
+        m = O.md(T=T1, mass=mass(), k_spring=k, t_eq=2000, t_s=5000, seed=seed, replica=seed)
+        r = O.switch_run(p, th, m, x0, O.init_velocities(m, n), x0, box)
+        return r["W_f"], r["W_b"]
+
+    with ThreadPoolExecutor(8) as ex:
+        res = list(ex.map(rs, range(1, 9)))
+        w = np.array(list(ex.map(fl, range(1, 9))))
+    cf, cb = np.array([r[0] for r in res]), np.array([r[1] for r in res])
+    F0 = g["F_per_atom"] * n
+    per = [O.rs_free_energy(n, T0, F0, lf, ts, cf[i], cb[i], [T1])[0] for i in range(len(res))]
+    F_rs = O.rs_free_energy(n, T0, F0, lf, ts, cf, cb, [T1])[0]
+    se_rs = math.hypot(np.std(per, ddof=1) / math.sqrt(len(per)), g["stderr_per_atom"] * T1 / T0)
+    F_fl, se_fl, _ = O.free_energy(n, V, T1, mass(), k, w[:, 0], w[:, 1])
+    assert abs(F_rs - F_fl) < 4 * math.hypot(se_rs, se_fl)
+    assert math.hypot(se_rs, se_fl) < 5e-4  # a dropped or wrong term of eq. rs is far larger
