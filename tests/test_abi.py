@@ -118,3 +118,24 @@ def test_jarzynski_matches_oracle():
         assert ne.ne_jarzynski(T, w) == pytest.approx(O.jarzynski(T, w), rel=1e-13, abs=1e-10)
     with pytest.raises(ne.NeError):
         ne.ne_jarzynski(-1.0, [1.0])
+
+
+def test_batched_entry_points_reject_an_empty_batch_without_a_gpu():
+    """n_rep = 0 is NE_EINVAL at every batched entry point, decided from the
+    arguments alone (the non-null pointers here are never followed)."""
+    L = ne.load()
+    dummy = C.c_void_p(16)
+    for name in ("ne_switch_run_batched", "ne_switch_run_segment", "ne_switch_run_segment_grad",
+                 "ne_profile_segment", "ne_crystal_run_segment", "ne_crystal_run_segment_cum"):
+        f = getattr(L, name)
+        args = []
+        for q, t in enumerate(f.argtypes):
+            if t is C.c_void_p:
+                args.append(dummy)
+            elif t is C.c_double:
+                args.append(1.0)
+            else:
+                args.append(1)
+        # the replica count: argument 2 of the md-array entry points, 3 of the crystal runner's
+        args[3 if name.startswith("ne_crystal") else 2] = 0
+        assert f(*args) == ne.NE_EINVAL, name
