@@ -834,3 +834,21 @@ def test_rs_of_the_eam_crystal_matches_an_independent_fl_point(pot):
     F_fl, se_fl, _ = O.free_energy(n, V, T1, mass(), k, w[:, 0], w[:, 1])
     assert abs(F_rs - F_fl) < 4 * math.hypot(se_rs, se_fl)
     assert math.hypot(se_rs, se_fl) < 5e-4  # a dropped or wrong term of eq. rs is far larger
+
+
+def test_one_step_switch_takes_the_work_at_the_start_of_the_step(pot):
+    """Sec. II.A's discrete work sum with the Hamiltonian jumping at fixed x:
+    a one-step switch (t_eq = 0, t_s = 1) from the lattice sites does work
+    (lambda_1 - lambda_0) dH/dlambda(x_0) = U_EAM(x_0) - U_E(x_0) = U_EAM(x_0)
+    on the Frenkel-Ladd path (function 2 reaches 1 in one step) and
+    (lambda_f - 1) U_EAM(x_0) on the reversible-scaling path -- exactly, since
+    the state after the step plays no part."""
+    p, th = pot
+    x0, box = O.create_crystal(O.BCC, W.A_BCC, 4, 4, 4)
+    U0 = O.eam_energy_forces(p, th, x0, box)[0]
+    for path, want in ((O.PATH_FL, U0), (O.PATH_RS, (0.3 - 1.0) * U0)):
+        m = O.md(T=300.0, mass=mass(), k_spring=4.0, path=path, lambda_f=0.3, t_eq=0, t_s=1, seed=2)
+        r = O.switch_run(p, th, m, x0, O.init_velocities(m, len(x0)), x0, box, cumulative=True)
+        assert r["W_f"] == want
+        assert r["Wcum_f"][0] == 0.0 and r["Wcum_f"][1] == want
+        assert r["W_b"] != 0.0 and abs(r["W_b"] + want) < 0.05 * abs(want)  # back from x_1, near x_0
