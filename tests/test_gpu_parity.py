@@ -763,3 +763,29 @@ def test_uneven_256_replica_set_at_full_length_against_the_oracle():
         F = ne.ne_free_energy(len(x0), float(np.prod(box)), row["T"], MASS, row["k"], [Wf[q]], [Wb[q]])[0]
         dF.append(F - row["F_per_atom"])
     assert len(dF) == 24 and np.abs(dF).max() < 1e-3, np.abs(dF).max()
+
+
+def test_one_step_schedule_edge_case(ctx, pot):
+    """Degenerate schedule: no equilibration and a one-step switch (t_eq = 0,
+    t_s = 1) from the lattice sites.  The forward work is then
+    U_EAM(x_0) - U_E(x_0) = U_EAM(x_0), taken before the step (Sec. II.A):
+    the oracle's exactly, the multi-kernel path's to 1e-9 (FP64) and 1e-6
+    (mixed) relative, and the crystal runner's to 1e-6 relative."""
+    p, th = pot
+    x0, box = O.create_crystal(O.BCC, W.A_BCC, 5, 5, 5)
+    U0 = O.eam_energy_forces(p, th, x0, box)[0]
+    for prec, tol in ((ne.NE_FP64, 1e-9), (ne.NE_MIXED, 1e-6)):
+        mo, mg = md_pair(T=300.0, k_spring=4.0, t_eq=0, t_s=1, seed=2, replica=0, prec=prec)
+        v0 = O.init_velocities(mo, len(x0))
+        ro = O.switch_run(p, th, mo, x0, v0, x0, box)
+        assert ro["W_f"] == U0
+        x, v = T(x0), T(v0)
+        wf = torch.zeros(1, dtype=torch.float64, device=DEV)
+        wb = torch.zeros(1, dtype=torch.float64, device=DEV)
+        ne.ne_switch_run(ctx, mg, x, v, T(x0), box, wf, wb)
+        assert float(wf.item()) == pytest.approx(U0, rel=tol)
+        if prec == ne.NE_MIXED:
+            x, v = T(x0), T(v0)
+            Wd = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
+            ne.ne_crystal_run_segment(ctx, [mg], [(O.BCC, W.A_BCC, 5, 5, 5)], x, v, Wd, 0, 2)
+            assert float(Wd[0, 0].item()) == pytest.approx(U0, rel=1e-6)
