@@ -124,6 +124,7 @@ def lib():
             L.ora_init_velocities.argtypes = [p, i, p]
             L.ora_switch_run.argtypes = [p, p, p, p, p, p, i, p, p, p, p, p, p, i, i]
             L.ora_langevin_steps.argtypes = [p, p, p, d, p, p, p, i, p, C.c_long, C.c_long]
+            L.ora_switch_run_prefix.argtypes = [p, p, p, p, p, p, i, p, C.c_long, p, p, p, p]
             L.ora_msd_fit.argtypes = [p, p, p, p, p, p, i, p, C.c_long, C.c_long, i, p, p]
             L.ora_msd_fit_species.argtypes = [p, p, p, p, p, p, i, p, C.c_long, C.c_long, i, p, p]
             L.ora_einstein_F_species.restype = d
@@ -356,6 +357,25 @@ def switch_run(p: EAM, theta, m: MD, x, v, x0, box, cumulative=False, trace_stri
         out.update(Wcum_f=cf, Wcum_b=cb)
     if tr is not None:
         out["trace"] = tr
+    return out
+
+
+def switch_run_prefix(p: EAM, theta, m: MD, x, v, x0, box, n_steps, cumulative=False):
+    """The first n_steps steps of switch_run's schedule on copies of x, v:
+    dict with W_f, W_b (works so far), x, v, box and optionally the
+    cumulative works (zero beyond the last switching step reached)."""
+    theta, x0 = _f64(theta), _f64(x0)
+    box = _f64(box).copy()
+    x, v = _f64(x).copy(), _f64(v).copy()
+    wf, wb = C.c_double(), C.c_double()
+    cf = np.zeros(m.t_s + 1) if cumulative else None
+    cb = np.zeros(m.t_s + 1) if cumulative else None
+    _check(lib().ora_switch_run_prefix(_pref(p), _ptr(theta), C.byref(m), _ptr(x), _ptr(v), _ptr(x0),
+                                       x.shape[0], _ptr(box), int(n_steps), C.byref(wf), C.byref(wb),
+                                       _ptr(cf), _ptr(cb)), "switch_run_prefix")
+    out = dict(W_f=wf.value, W_b=wb.value, x=x, v=v, box=box)
+    if cumulative:
+        out.update(Wcum_f=cf, Wcum_b=cb)
     return out
 
 

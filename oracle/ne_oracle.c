@@ -851,12 +851,14 @@ static void ws_free(workspace* w)
 
 /* Schedule of Sec. III.B (fix ti/spring) and Sec. III.C: equilibrate at the
  * initial lambda, switch forward over t_s steps, equilibrate at the final
- * lambda, switch back.  W_f and W_b are the two irreversible works. */
-int ora_switch_run(const ora_eam* p, const double* theta, const ora_md* md,
-                   double* x, double* v, const double* x0, int n,
-                   double box[3], double* W_f, double* W_b,
-                   double* Wcum_f, double* Wcum_b, double* trace,
-                   int trace_stride, int n_trace_max)
+ * lambda, switch back.  W_f and W_b are the two irreversible works.  The
+ * run stops after s_end steps of the schedule (all of it when s_end is
+ * 2 t_eq + 2 t_s). */
+static int switch_run_steps(const ora_eam* p, const double* theta, const ora_md* md,
+                            double* x, double* v, const double* x0, int n,
+                            double box[3], double* W_f, double* W_b,
+                            double* Wcum_f, double* Wcum_b, double* trace,
+                            int trace_stride, int n_trace_max, long s_end)
 {
     if (n < 2 || md->t_s < 1 || md->t_eq < 0 || !species_valid(md, n)) return ORA_EINVAL;
     if (md->path == ORA_PATH_RS && !(md->lambda_f > 0 && md->lambda_f < 1)) return ORA_EINVAL;
@@ -874,6 +876,7 @@ int ora_switch_run(const ora_eam* p, const double* theta, const ora_md* md,
     int nt = 0;
     if (Wcum_f) Wcum_f[0] = 0.0;
     if (Wcum_b) Wcum_b[0] = 0.0;
+    if (s_end < S) S = s_end;
     for (long s = 0; s < S && !st; s++) {
         if (trace && trace_stride > 0 && s % trace_stride == 0 && nt < n_trace_max) {
             double* r = trace + 8 * nt++;
@@ -900,6 +903,26 @@ int ora_switch_run(const ora_eam* p, const double* theta, const ora_md* md,
     if (W_f) *W_f = wf;
     if (W_b) *W_b = wb;
     return st;
+}
+
+int ora_switch_run(const ora_eam* p, const double* theta, const ora_md* md,
+                   double* x, double* v, const double* x0, int n,
+                   double box[3], double* W_f, double* W_b,
+                   double* Wcum_f, double* Wcum_b, double* trace,
+                   int trace_stride, int n_trace_max)
+{
+    return switch_run_steps(p, theta, md, x, v, x0, n, box, W_f, W_b, Wcum_f, Wcum_b, trace,
+                            trace_stride, n_trace_max, 2 * md->t_eq + 2 * md->t_s);
+}
+
+int ora_switch_run_prefix(const ora_eam* p, const double* theta, const ora_md* md,
+                          double* x, double* v, const double* x0, int n, double box[3],
+                          long n_steps, double* W_f, double* W_b, double* Wcum_f,
+                          double* Wcum_b)
+{
+    if (n_steps < 0) return ORA_EINVAL;
+    return switch_run_steps(p, theta, md, x, v, x0, n, box, W_f, W_b, Wcum_f, Wcum_b, NULL, 0, 0,
+                            n_steps);
 }
 
 int ora_langevin_steps(const ora_eam* p, const double* theta, const ora_md* md,

@@ -140,6 +140,15 @@ int ora_switch_run(const ora_eam* p, const double* theta, const ora_md* md,
                    double* Wcum_f, double* Wcum_b, double* trace,
                    int trace_stride, int n_trace_max);
 
+/* The first n_steps steps of that schedule (all of it when n_steps >= 2 t_eq
+ * + 2 t_s), the same steps, noise and works as ora_switch_run up to there:
+ * W_f, W_b the works done so far, Wcum_* filled up to the last switching
+ * step reached (entries beyond it untouched). */
+int ora_switch_run_prefix(const ora_eam* p, const double* theta, const ora_md* md,
+                          double* x, double* v, const double* x0, int n, double box[3],
+                          long n_steps, double* W_f, double* W_b, double* Wcum_f,
+                          double* Wcum_b);
+
 /* Plain Langevin steps at fixed lambda (FL blend), n_steps, noise stream STEP,
  * starting at global step step0. */
 int ora_langevin_steps(const ora_eam* p, const double* theta, const ora_md* md,

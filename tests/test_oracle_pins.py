@@ -852,3 +852,27 @@ def test_one_step_switch_takes_the_work_at_the_start_of_the_step(pot):
         assert r["W_f"] == want
         assert r["Wcum_f"][0] == 0.0 and r["Wcum_f"][1] == want
         assert r["W_b"] != 0.0 and abs(r["W_b"] + want) < 0.05 * abs(want)  # back from x_1, near x_0
+
+
+def test_prefix_runs_are_the_full_run_cut_short(pot):
+    """The first n steps of the schedule are the full run's first n steps:
+    positions, velocities and cumulative works equal bit for bit, the works
+    so far equal the cumulative work at that point, and a prefix covering
+    the whole schedule is the full run."""
+    p, th = pot
+    x0, box = O.create_crystal(O.BCC, W.A_BCC, 4, 4, 4)
+    for path in (O.PATH_FL, O.PATH_RS):
+        m = O.md(T=600.0, mass=mass(), k_spring=4.0, path=path, lambda_f=0.5, t_eq=15, t_s=40, seed=7)
+        v0 = O.init_velocities(m, len(x0))
+        full = O.switch_run(p, th, m, x0, v0, x0, box, cumulative=True)
+        cut = 15 + 23  # inside the forward switch
+        pre = O.switch_run_prefix(p, th, m, x0, v0, x0, box, cut, cumulative=True)
+        assert pre["W_f"] == full["Wcum_f"][23] and pre["W_b"] == 0.0
+        assert np.array_equal(pre["Wcum_f"][:24], full["Wcum_f"][:24]) and not pre["Wcum_f"][24:].any()
+        whole = O.switch_run_prefix(p, th, m, x0, v0, x0, box, 10 ** 6, cumulative=True)
+        for key in ("W_f", "W_b"):
+            assert whole[key] == full[key]
+        assert np.array_equal(whole["x"], full["x"]) and np.array_equal(whole["Wcum_b"], full["Wcum_b"])
+        # the state after the prefix is the state after that many steps of the full schedule
+        pre2 = O.switch_run_prefix(p, th, m, x0, v0, x0, box, cut + 1)
+        assert not np.array_equal(pre2["x"], pre["x"])
