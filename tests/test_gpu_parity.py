@@ -789,3 +789,26 @@ def test_one_step_schedule_edge_case(ctx, pot):
             Wd = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
             ne.ne_crystal_run_segment(ctx, [mg], [(O.BCC, W.A_BCC, 5, 5, 5)], x, v, Wd, 0, 2)
             assert float(Wd[0, 0].item()) == pytest.approx(U0, rel=1e-6)
+
+
+def test_reversible_scaling_workload_prefix_against_the_oracle(ctx):
+    """The reversible-scaling workload (bcc 16^3, 8192 atoms, T0 = 100 K,
+    lambda 1 -> 0.0625 over 100 ps after 10 ps at lambda = 1) on a stated
+    prefix -- its first 12,000 steps, the equilibration and 2000 switching
+    steps -- against the oracle's works (tests/golden/config4_prefix_works.json,
+    written by make_config4_prefix_works.py from oracle/ alone): the work
+    after the prefix to 1e-8 (FP64) and 1e-6 (mixed) relative."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "config4_prefix_works.json")))
+    x0, box = O.create_crystal(O.BCC, g["a"], g["cells"], g["cells"], g["cells"])
+    n = len(x0)
+    for row in g["rows"]:
+        for prec, tol in ((ne.NE_FP64, 1e-8), (ne.NE_MIXED, 1e-6)):
+            mo, mg = md_pair(T=g["T0"], k_spring=1.0, path=O.PATH_RS, lambda_f=g["lambda_f"], t_eq=g["t_eq"],
+                             t_s=g["t_s"], seed=row["seed"], replica=row["replica"], prec=prec)
+            x, v = T(x0), T(O.init_velocities(mo, n))
+            Wd = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
+            ne.ne_switch_run_segment(ctx, [mg], [0, n], x, v, T(x0), [box], Wd, 0, g["prefix_steps"])
+            assert float(Wd[0, 0].item()) == pytest.approx(row["W_f"], rel=tol)
+            assert float(Wd[0, 1].item()) == 0.0
