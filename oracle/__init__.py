@@ -20,6 +20,8 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   switch_run (FL)       harmonic->harmonic exact dF, self-switch W == 0,
                         NVE energy conservation, equipartition
   switch_run (RS)       harmonic F(T) = 3NkT ln(hbar w/kT) at every T
+                        and an independent FL point on the EAM crystal
+  switch_run_prefix     the full run's first n steps bit for bit
   free_energy           F_E and dF_CM closed forms; low-T quasi-harmonic limit
   msd_fit               equipartition on a harmonic crystal
   eam_virial_axes       sums to the virial; -dU/d eps_a by central differences;
