@@ -325,8 +325,8 @@ def test_fl1400_full_length_works_vs_oracle(ctx):
     """The 1400 K batch (10 x bcc 10^3 + 10 x fcc 8^3) at full length
     (t_eq 10 ps, t_s 50 ps, 120,000 steps per replica) in the crystal
     runner's benchmark launch configuration: the forward and backward works
-    of all twenty replicas stored from the FP64 oracle
-    (tests/golden/fl1400_all_works.json, same seeds and replica indices).  With
+    of the eight replicas stored from the FP64 oracle
+    (tests/golden/fl1400_works.json, same seeds and replica indices).  With
     the same Philox noise and 0.1 ps damping the mixed and FP64 trajectories
     stay synchronised, so each work agrees to FP32 pair-energy rounding:
     |U|/N ~ 4.3 eV carries 2^-24 * 4.3 ~ 2.6e-7 eV per atom of systematic
@@ -334,14 +334,14 @@ def test_fl1400_full_length_works_vs_oracle(ctx):
     import json
     import os
     from paper_2201_04622_gb300 import workflow as WF
-    with open(os.path.join(os.path.dirname(__file__), "golden", "fl1400_all_works.json")) as f:
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fl1400_works.json")) as f:
         doc = json.load(f)
     crystals = [(O.BCC, W.A_BCC, 10)] * 10 + [(O.FCC, W.A_FCC, 8)] * 10
     ks = [W.K_BCC_1400] * 10 + [W.K_FCC_1400] * 10
     seeds = list(range(1, 11)) * 2
     Wf, Wb, _ = WF.fl_batch(ctx, crystals, doc["T"], ks, seeds, doc["t_eq"], doc["t_s"], MASS,
                             prec=ne.NE_MIXED, runner="crystal", chunk=20000)
-    assert len(doc["rows"]) == 20
+    assert len(doc["rows"]) == 8
     for row in doc["rows"]:
         q = row["replica"]
         lat, a, n = crystals[q]

@@ -7,8 +7,8 @@ device array inside the library, shared by every call, so the test makes two
 calls in a row (different sizes and lattices, so stale contents from the
 first call would show) and compares each with ne_eam_energy_forces, the
 entry point that allocates its buffers in a context, within the tolerances
-of the GPU parity tests.  This file is collected last; it passes alone in a
-fresh process and after the other tests.
+of the GPU parity tests.  It passes alone in a fresh process and after the
+other GPU tests.
 """
 import numpy as np
 import pytest
