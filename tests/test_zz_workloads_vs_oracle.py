@@ -7,6 +7,7 @@ results, on the workloads' own sizes:
   multi-kernel fallback, against the oracle's 24-replica subset;
 - the reversible-scaling workload (bcc 16^3) on a stated 12,000-step prefix;
 - the degenerate one-step schedule on both GPU paths.
+- a potential read from a tabulated setfl file.
 
 The stored values come from tests/golden/make_*.py, which call only
 oracle/.  Collected after the other GPU tests.
@@ -218,3 +219,41 @@ def test_reversible_scaling_workload_prefix_against_the_oracle(ctx):
             ne.ne_switch_run_segment(ctx, [mg], [0, n], x, v, T(x0), [box], Wd, 0, g["prefix_steps"])
             assert float(Wd[0, 0].item()) == pytest.approx(row["W_f"], rel=tol)
             assert float(Wd[0, 1].item()) == 0.0
+
+
+def test_potential_from_a_setfl_file_matches_the_oracle(tmp_path):
+    """A tabulated single-element setfl file (written here from the analytic
+    Fe-like potential) loaded with potentials.load_eam: a context created
+    from its parameters and knots gives the oracle's FP64 energy, forces and
+    densities under the same knots to the FP64 parity tolerance."""
+    from paper_2201_04622_gb300 import potentials as P
+    nr = nrho = 20000
+    r_c, rho_max = W.EAM_FE_LIKE["r_c"], W.EAM_FE_LIKE["rho_max"]
+    p = O.eam(**W.EAM_FE_LIKE)
+    dr, drho = r_c / (nr - 1), rho_max / (nrho - 1)
+    r, rho = dr * np.arange(nr), drho * np.arange(nrho)
+    F = [O.eam_analytic(p, 2, float(t))[0] for t in rho]
+    f = [O.eam_analytic(p, 1, float(t))[0] for t in r]
+    rphi = [float(t) * O.eam_analytic(p, 0, float(t))[0] for t in r]
+    path = tmp_path / "fe.setfl"
+    with open(path, "w") as fh:
+        fh.write("c\nc\nc\n1 Fe\n%d %.16e %d %.16e %.16e\n26 55.845 2.87 bcc\n" % (nrho, drho, nr, dr, r_c))
+        fh.write("\n".join("%.16e" % v for v in F + f + rphi) + "\n")
+    params, theta, _ = P.load_eam(str(path))
+    x0, box = O.create_crystal(O.BCC, W.A_BCC, 6, 6, 6)
+    x = W.displaced(x0, 0.2, 41)
+    Eo, fo, rho_o = O.eam_energy_forces(O.eam(**params), theta.reshape(-1), x, box)
+    c = ne.ne_ctx_create(ne.eam_params(**params), 5000, 1)
+    try:
+        ne.ne_ctx_set_theta(c, T(theta.reshape(-1)))
+        xt = T(x)
+        fg = torch.zeros_like(xt)
+        e = torch.zeros(1, dtype=torch.float64, device=DEV)
+        rho_g = torch.zeros(len(x), dtype=torch.float64, device=DEV)
+        ne.ne_eam_energy_forces(c, ne.NE_FP64, xt, box, f=fg, e=e, rho=rho_g)
+        torch.cuda.synchronize()
+    finally:
+        ne.ne_ctx_destroy(c)
+    assert float(e.item()) == pytest.approx(Eo, rel=1e-10)
+    assert np.linalg.norm(N(fg) - fo) < 1e-10 * np.linalg.norm(fo)
+    assert np.abs(N(rho_g) - rho_o).max() < 1e-10 * np.abs(rho_o).max()
