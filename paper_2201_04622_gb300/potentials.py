@@ -23,7 +23,8 @@ value there with zero slope (the library rejects pairs closer than 0.2 A).
 load_eam(path) returns the parameter block for ne_ctx_create (r_c, rho_max
 and n_knots set; the analytic fields are placeholders, replaced as soon as
 the knots are loaded) and theta [3][n_knots][2] for ne_ctx_set_theta and the
-oracle.
+oracle.  ne_eam_energy_forces_noalloc builds its tables from the analytic
+parameters on every call and cannot take loaded knots.
 """
 from __future__ import annotations
 
