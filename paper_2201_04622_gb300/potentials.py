@@ -12,6 +12,8 @@ Two plain-text formats are read, both single-element:
 - setfl with one element: three comment lines; "1 <element>"; Nrho, drho,
   Nr, dr, cutoff; atomic number, mass, lattice constant, lattice type;
   F(rho) (Nrho values), f(r) (Nr values), then r * phi(r) (Nr values).
+  A single-element Finnis-Sinclair file (one density function per element
+  pair, so one in all) has the same layout and is read the same way.
 
 Numbers may be spread over lines in any way.  The tables are interpolated
 with not-a-knot cubic splines (scipy) and resampled onto the library's
