@@ -41,9 +41,17 @@ T_K = 1400.0
 K_SPRING = {W.BCC: W.K_BCC_1400, W.FCC: W.K_FCC_1400}  # eV/A^2, msd fits at 1400 K
 SKIN = float(os.environ.get("NE_BENCH_SKIN", "2.6"))  # A
 T_EQ, T_S = 10000, 50000
-FP32_LANES_PER_SM, N_SM = 128, 152
+FP32_LANES_PER_SM = 128
+# Algorithmic work of one atom-step of the mixed path (bcc at ~58 neighbours
+# inside r_c + skin): ~2,700 FP32 lane instructions (pass 1 ~16 and pass 2
+# ~30 per neighbour, plus the embedding and the integration), and ~200 bytes
+# of state stream (x, v read and written, the site, the FP32 position copy):
+# the figures the roofline is stated in.
+ALG_LANE_OPS_PER_ATOM_STEP = 2700
+ALG_BYTES_PER_ATOM_STEP = 200
 FLOPS_PER_PAIR_PASS2 = 44    # FP32 lane operations per neighbour pair in pass 2 (multi-kernel path)
-# crystal runner, lane operations (FP32 + INT32) counted from the source:
+# crystal runner, lane operations (FP32 + INT32) the source issues, for the
+# ratio of issued to algorithmic work:
 OPS_VISIT = 24    # one lattice-stencil entry examined in pass 1
 OPS_PAIR = 62     # one pair inside r_c: spline of f in pass 1 + forces in pass 2
 OPS_ATOM = 120    # per atom-step: F(rho), broadcasts, sums, Philox + Box-Muller, BAOAB
@@ -85,19 +93,35 @@ def build_batch(ne, np):
     return np.concatenate(x0s), offs, boxes, mds
 
 
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def clock_query():
+    """One read-only nvidia-smi reading of this rank's GPU (a csv line or None)."""
+    try:
+        r = subprocess.run(["nvidia-smi", "--query-gpu=" + CLOCK_QUERY, "--format=csv,noheader,nounits",
+                            "-i", str(os.environ.get("LOCAL_RANK", 0))],
+                           capture_output=True, text=True, timeout=20)
+        return r.stdout.strip().splitlines()[0] if r.returncode == 0 and r.stdout.strip() else None
+    except (OSError, subprocess.TimeoutExpired):
+        return None
+
+
 class Clocks:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples (200 ms) during the timed region, plus one reading
+    taken just before it starts and one just after it ends (a region of a
+    few milliseconds sees no periodic sample)."""
 
     def __init__(self):
         self.proc = None
         self.lines = []
+        self.edges = []
 
     def __enter__(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + CLOCK_QUERY, "--format=csv,noheader,nounits",
                                           "-lms", "200", "-i", str(os.environ.get("LOCAL_RANK", 0))],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
@@ -105,6 +129,11 @@ class Clocks:
         except OSError:
             self.proc = None
         return self
+
+    def edge(self):
+        ln = clock_query()
+        if ln:
+            self.edges.append(ln)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -118,10 +147,11 @@ class Clocks:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
-        sm, mx, reasons = [], [], set()
+    @staticmethod
+    def _parse(lines, reasons):
+        sm, mx = [], []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -133,9 +163,32 @@ class Clocks:
             for nm, val in zip(names, f[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
+        return sm, mx
+
+    def summary(self):
+        """Median SM clock of the periodic samples, or of the two edge
+        readings when the region was too short for any; throttle reasons
+        seen in either."""
+        reasons = set()
+        sm_p, mx_p = self._parse(self.lines, reasons)
+        sm_e, mx_e = self._parse(self.edges, reasons)
+        sm = sm_p or sm_e
+        mx = mx_p + mx_e
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm_p) + len(sm_e),
+                "from": "periodic samples" if sm_p else ("readings just before and after the timed region"
+                                                         if sm_e else None),
+                "edge_sm_mhz": sm_e}
+
+
+def measured_peak(key):
+    """A peak from MEASURED_PEAKS.json at the repository root (None if absent)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, KeyError, ValueError, TypeError):
+        return None
 
 
 def flush_l2(torch, buf):
@@ -239,11 +292,16 @@ def run_ours(args):
         adv.moved = list(moved_w)
     n_log0 = len(adv.log) if adv else 0
     with Clocks() as clk:
+        clk.edge()
         e0.record(stream)
         segment(x, v, x0, Wd, Wm, K)
         e1.record(stream)
         torch.cuda.synchronize()
+        clk.edge()
     ms = e0.elapsed_time(e1)
+    # device time of the crystal runner's own launches in the timed call
+    # (events the library records on the launching stream)
+    kern_ms = ne.ne_ctx_last_run_ms(ctx) if path == "crystal" and not (adv and adv.moved) else None
     c1 = ne.ne_ctx_counters(ctx)
     timed_log = list(adv.log[n_log0:]) if adv else []
     moved_timed = list(adv.moved) if adv else []
@@ -289,22 +347,40 @@ def run_ours(args):
                                     "copies in, K steps, state and work out"}
 
     roof = None
-    if path == "crystal":
-        # one persistent launch per segment: its duration is the timed region
-        ops = OPS_VISIT * visits + OPS_PAIR * pairs + OPS_ATOM * K * n_atoms
-        peak = N_SM * FP32_LANES_PER_SM * 2.07e9
+    clk_sum = clk.summary()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    if path == "crystal" and kern_ms:
+        # the timed call is one persistent launch per size class; its device
+        # time is kern_ms.  Algorithmic work: 2,700 FP32 lane instructions and
+        # 200 bytes per atom-step; peak lane rate = SMs x 128 FP32 lanes x the
+        # median SM clock sampled around the timed region
+        atom_steps = K * n_atoms
+        sm_hz = (clk_sum["sm_mhz"] or clk_sum["sm_max_mhz"] or 2070.0) * 1e6
+        peak = n_sm * FP32_LANES_PER_SM * sm_hz
+        alg = ALG_LANE_OPS_PER_ATOM_STEP * atom_steps / (kern_ms * 1e-3)
+        issued = (OPS_VISIT * visits + OPS_PAIR * pairs + OPS_ATOM * atom_steps) / (kern_ms * 1e-3)
+        hbm_peak = measured_peak("hbm_gbs")
+        hbm = ALG_BYTES_PER_ATOM_STEP * atom_steps / (kern_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "kernel": "k_cluster (persistent crystal runner)",
-                "achieved": ops / (ms * 1e-3) / 1e12, "peak": peak / 1e12, "unit": "T lane-ops/s",
-                "frac": ops / (ms * 1e-3) / peak,
-                # DRAM bytes (read + write) of one k_cluster launch from ncu: stencil, tables
-                # and state are read once per launch and the replica stays on chip, so the
-                # figure does not grow with the steps (a 301-step launch of this batch;
-                # the kernel's final x, v writes stay in L2); null for any other workload
-                "traffic": 2.61e6 if args.workload == "fl2" else None,
-                "per_atom_step": {"stencil_visits": visits / (K * n_atoms), "pairs": pairs / (K * n_atoms)},
-                "note": "lane-ops = FP32 + INT32 lane instructions counted from the source per stencil "
-                        "visit (%d), pair (%d) and atom-step (%d); peak = 152 SMs x 128 lanes x 2.07 GHz"
-                        % (OPS_VISIT, OPS_PAIR, OPS_ATOM)}
+                "achieved": alg / 1e12, "peak": peak / 1e12, "unit": "T lane-ops/s",
+                "frac": alg / peak,
+                # ncu DRAM read + write of one k_cluster launch; null until the
+                # current kernel has been captured (the replica lives on chip,
+                # so the figure does not grow with the steps)
+                "traffic": None,
+                "kernel_ms": kern_ms, "us_per_step": kern_ms * 1e3 / K,
+                "peak_note": "%d SMs x %d FP32 lanes x %.0f MHz (median SM clock sampled around the "
+                             "timed region)" % (n_sm, FP32_LANES_PER_SM, sm_hz / 1e6),
+                "algorithmic": "%d FP32 lane instructions per atom-step x %d atom-steps over the "
+                               "launch's CUDA-event duration" % (ALG_LANE_OPS_PER_ATOM_STEP, atom_steps),
+                "hbm": {"achieved_gbs": hbm, "peak_gbs": hbm_peak,
+                        "frac": hbm / hbm_peak if hbm_peak else None,
+                        "note": "%d B of state per atom-step; peak of measured copy bandwidth"
+                                % ALG_BYTES_PER_ATOM_STEP},
+                "issued": {"lane_ops_per_s": issued / 1e12, "ratio_to_algorithmic": issued / alg,
+                           "note": "lane-ops the source issues: %d per stencil visit, %d per pair, %d per "
+                                   "atom-step" % (OPS_VISIT, OPS_PAIR, OPS_ATOM)},
+                "per_atom_step": {"stencil_visits": visits / atom_steps, "pairs": pairs / atom_steps}}
     # per-kernel durations (events around each launch) for the roofline
     xp, vp = x.clone(), v.clone()
     Wp = Wd.clone()
@@ -318,8 +394,7 @@ def run_ours(args):
     if prof:
         t_force = prof[2] * 1e-3
         flops = FLOPS_PER_PAIR_PASS2 * pairs_per_atom * n_atoms
-        sm_mhz = None
-        peak = N_SM * FP32_LANES_PER_SM * 2.07e9
+        peak = n_sm * FP32_LANES_PER_SM * (clk_sum["sm_mhz"] or clk_sum["sm_max_mhz"] or 2070.0) * 1e6
         roof = {"bound": "alu", "kernel": "k_force (pass 2)", "achieved": flops / t_force / 1e12,
                 "peak": peak / 1e12, "unit": "TFLOP/s", "frac": flops / t_force / peak,
                 "traffic": None,
@@ -373,7 +448,7 @@ def run_ours(args):
                       "parallelism": "replicas only" if world > 1 else "1 GPU",
                       "l2": "flushed before the timed segment; the 40k-atom state stays L2-resident "
                             "across MD steps by design"},
-           "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e, "roofline": roof,
+           "gpu_launches": launches, "clocks": clk_sum, "e2e": e2e, "roofline": roof,
            "fp64_gpu": fp64}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_steps)

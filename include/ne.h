@@ -150,11 +150,19 @@ ne_status ne_ctx_boxes(ne_ctx* ctx, int n_rep, double* boxes_host);
  * strays more than skin/2 from its list-build position); stencil_visits and
  * pairs -- lattice-stencil entries examined and pairs found inside r_c by
  * ne_crystal_run_segment (pass 1), for algorithmic operation counts;
- * crystal_launches -- kernels launched by ne_crystal_run_segment (one lambda
- * table and one cluster kernel per replica size class a call).
- * Synchronises the device. */
+ * crystal_launches -- kernels launched by ne_crystal_run_segment (one cluster
+ * kernel per replica size class a call, plus one lambda-table kernel on the
+ * first call of each schedule).  Synchronises the device. */
 ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds, long long* stencil_visits,
                           long long* pairs, long long* crystal_launches);
+
+/* Device time (ms, host double) of the last ne_crystal_run_segment or
+ * ne_crystal_run_segment_cum call on this context: CUDA events recorded on
+ * the call's stream just before its first cluster launch and after the last
+ * size class has joined back, so the figure is the kernels' own duration,
+ * without the call's host work (bookkeeping for the roofline report; the
+ * paper has no counterpart).  NE_EINVAL if no such call has run. */
+ne_status ne_ctx_last_run_ms(ne_ctx* ctx, double* ms_host);
 
 /* Status bits recorded by the last call, and its message (msg may be NULL). */
 ne_status ne_last_error(ne_ctx* ctx, int* device_status, char* msg, int msg_len);
@@ -208,9 +216,13 @@ ne_status ne_eam_virial(ne_ctx* ctx, const double* x_dev, int n, const double bo
  *   Limits: n <= NE_NOALLOC_MAX_ATOMS and eam->n_knots <=
  *   NE_NOALLOC_MAX_KNOTS, else NE_ENOMEM; box edges > 2 r_c, else NE_EINVAL.
  *   Arguments and results as for ne_eam_energy_forces (no rho output).
- *   The first call on a device looks up the device address of the array
- *   (cudaGetSymbolAddress, with that device current); make that first call
- *   before any stream capture.
+ *   Each call looks up the device address of the array on the current
+ *   device (cudaGetSymbolAddress), so the address stays right after a
+ *   cudaDeviceReset; a call whose stream is capturing reuses the address of
+ *   that device's last lookup instead, so make the first call on a device
+ *   before any stream capture.  Analytic parameters that are not finite
+ *   (the NaN placeholders of a potential loaded from a file) are refused
+ *   with NE_EINVAL: this entry point tabulates the analytic form only.
  *   All calls on a device share the one array, which keeps the previous
  *   call's contents (the call clears what must start at zero): calls that
  *   overlap on the GPU -- on different streams or host threads -- race and
@@ -355,7 +367,16 @@ typedef struct {
  * cells per axis and box edges > 2 r_c + 1.2 A.  Neighbours come from a
  * lattice stencil covering displacements up to D = 2 A from the sites (in a
  * small box it holds two periodic images of some sites, at most one of them
- * within r_c); a replica whose atoms stray further is reported as NE_ERANGE.  Noise, work and schedule are those of ne_switch_run_segment. */
+ * within r_c); a replica whose atoms stray further is reported as NE_ERANGE.
+ * A replica that raises an error (NE_ERANGE, NE_ENAN, NE_ENEIGH) keeps its
+ * x, v and W of step_begin -- its run is void and can be repeated elsewhere
+ * (ne_ctx_replica_status names it) -- while the others are advanced.  Noise,
+ * work and schedule are those of ne_switch_run_segment.
+ * The launch plan (stencils, replica table, cluster size) is built on the
+ * first call for a batch and kept in the context; later calls with the same
+ * crystals and per-replica parameters only launch, so short segments
+ * (checkpoints, cumulative-work chunks) pay no set-up.  The table of lambda
+ * over the whole schedule is likewise computed once per schedule. */
 ne_status ne_crystal_run_segment(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep,
                                  double* x_dev, double* v_dev, double* W_dev, long long step_begin,
                                  long long n_steps, void* stream);
@@ -401,7 +422,39 @@ ne_status ne_msd_fit(ne_ctx* ctx, const ne_md_params* md, double* x_dev, double*
                      long long n_samples, int stride, double* msd_host, double* k_host,
                      void* stream);
 
+/* ne_msd_fit for a batch of replicas at once, each at its own size and
+ * temperature (Sec. III.A: the spring of a run comes from the msd at that
+ * run's N and T -- e.g. one spring per replica of an uneven batch drawn over
+ * 300-1600 K).  md[n_rep]: per-replica T, seed, replica, mass; dt, damp,
+ * fix_cm and prec shared.  offsets_host[n_rep+1], x_dev, v_dev, x0_dev and
+ * boxes_host as in ne_switch_run_batched.  msd_host, k_host: n_rep doubles
+ * each (either may be NULL), k_r = 3 k_B T_r / msd_r. */
+ne_status ne_msd_fit_batched(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* offsets_host,
+                             double* x_dev, double* v_dev, const double* x0_dev,
+                             const double* boxes_host, long long n_eq, long long n_samples, int stride,
+                             double* msd_host, double* k_host, void* stream);
+
 /* ------------------------------------------------------------ assembly */
+/* Host only, FP64.  Lambda in force at the start of step `step` of md's
+ * four-phase schedule (Sec. III.B, fix ti/spring; Sec. III.C for
+ * md->path = NE_PATH_RS), the value every run of this library uses: t_eq
+ * steps at lambda_i (FL 0, RS 1), the switch over t_s steps with tau =
+ * elapsed steps / t_s (FL: tau, or tau^5 (70 tau^4 - 315 tau^3 + 540 tau^2
+ * - 420 tau + 126) for lambda_fn 2; RS: 1 / (1 + tau (1/lambda_f - 1))),
+ * t_eq steps at lambda_f (FL 1), the switch back (FL: 1 - lambda(tau); RS:
+ * lambda(1 - tau)).  The work of step s is (lambda(s+1) - lambda(s))
+ * dH/dlambda(x_s).  0 <= step <= 2 t_eq + 2 t_s, else NE_EINVAL. */
+ne_status ne_lambda(const ne_md_params* md, long long step, double* lambda_host);
+
+/* Host only, FP64.  Pressure of an NVT state (Sec. III.A: the crystal is
+ * brought to zero pressure before switching) from n_samples configurational
+ * virials W_host (ne_eam_virial, eV):
+ *   P = (n_dof k_B T + <W>) / (3 V)   (eV/A^3; n_dof = 3N - 3 with the
+ *   centre of mass fixed), and its standard error s(W) / sqrt(n) / (3 V)
+ * (0 for one sample; stderr_host may be NULL). */
+ne_status ne_pressure(int n_dof, double T, double V, const double* W_host, int n_samples,
+                      double* P_host, double* stderr_host);
+
 /* Host only, FP64.  Jarzynski's equality (eq. jarz, Sec. II.A): the
  * free-energy difference from the exponential average of the work done on
  * the system over independent realisations started in equilibrium,

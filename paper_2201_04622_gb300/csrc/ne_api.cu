@@ -28,6 +28,24 @@ cudaError_t dalloc(T** p, size_t n)
 
 }  // namespace
 
+// Launch plan of a crystal-runner batch, cached in the context: built on the
+// first call for a batch and reused while the batch stays the same, so a call
+// is a memset, the launches and the status read.
+struct CrGroup {
+    int b, e;     // replicas [b, e) of the sorted table: one size class
+    int C;        // CTAs per cluster
+    size_t smem;  // dynamic shared memory per CTA
+    int k_lo;     // first spline interval held in shared memory
+};
+struct CrPlan {
+    bool valid = false;
+    std::vector<double> key;
+    std::vector<XRep> xs;  // replica table, sorted by size class (uploaded to ctx->xrep)
+    std::vector<CrGroup> groups;
+    std::vector<float4> sv;
+    std::vector<float> sd;
+};
+
 struct ne_ctx {
     ne_eam_params eam{};
     int max_atoms = 0, max_rep = 0, tiles_cap = 0, cells_cap = 0, tpa = 4;
@@ -53,8 +71,13 @@ struct ne_ctx {
     unsigned long long* rebuilds = nullptr;
     unsigned long long* work = nullptr;  // crystal runner: [0] stencil entries visited, [1] pairs < r_c
     XRep* xrep = nullptr;
-    double* lam_tab = nullptr;  // lambda of each step of a crystal-runner segment
+    double* lam_tab = nullptr;  // lambda of each step of the crystal runner's schedule
     long long lam_cap = 0;
+    Sched lam_sched{};          // the schedule lam_tab holds
+    bool lam_valid = false;
+    CrPlan plan;                // launch plan of the last crystal-runner batch
+    cudaEvent_t ev_run[2] = {}; // around the cluster launches of the last crystal-runner call
+    bool run_timed = false;
     cudaStream_t gst[16] = {};  // crystal runner: one stream per replica size class
     cudaEvent_t gev[17] = {};
     float4* st_vec = nullptr;
@@ -595,6 +618,8 @@ ne_status ne_ctx_destroy(ne_ctx* ctx)
         if (ctx->gst[g]) cudaStreamDestroy(ctx->gst[g]);
     for (int g = 0; g < 17; ++g)
         if (ctx->gev[g]) cudaEventDestroy(ctx->gev[g]);
+    for (int g = 0; g < 2; ++g)
+        if (ctx->ev_run[g]) cudaEventDestroy(ctx->ev_run[g]);
     delete ctx;
     return NE_OK;
 }
@@ -693,6 +718,18 @@ ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds, long long* stenci
     if (stencil_visits) *stencil_visits = (long long)v[1];
     if (pairs) *pairs = (long long)v[2];
     if (crystal_launches) *crystal_launches = ctx->cr_launches;
+    return NE_OK;
+}
+
+ne_status ne_ctx_last_run_ms(ne_ctx* ctx, double* ms_host)
+{
+    if (!ctx || !ms_host) return NE_EINVAL;
+    if (!ctx->run_timed) return fail(ctx, NE_EINVAL, "no crystal-runner call has run on this context");
+    float ms = 0.f;
+    if (cudaEventSynchronize(ctx->ev_run[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, ctx->ev_run[0], ctx->ev_run[1]) != cudaSuccess)
+        return fail(ctx, NE_ECUDA, "reading the run's events failed");
+    *ms_host = (double)ms;
     return NE_OK;
 }
 
@@ -1124,12 +1161,39 @@ ne_status ne_crystal_run_segment_cum(ne_ctx* ctx, const ne_md_params* md, const 
     return crystal_segment_impl(ctx, md, cr, n_rep, x_dev, v_dev, W_dev, Wcum_dev, step_begin, n_steps, stream);
 }
 
-static ne_status crystal_segment_impl(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep,
-                                      double* x_dev, double* v_dev, double* W_dev, double* Wcum_dev,
-                                      long long step_begin, long long n_steps, void* stream)
+// Key of a crystal-runner launch plan: everything the plan is built from
+// (crystals, the per-replica parameters that enter XRep, the fixed cluster
+// size), field by field so that struct padding never enters the comparison.
+static std::vector<double> plan_key(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep)
 {
-    if (!ctx || !md || !cr || !x_dev || !v_dev || !W_dev || n_rep < 1) return NE_EINVAL;
-    if (n_rep > ctx->max_rep) return fail(ctx, NE_ENOMEM, "replica count exceeds the context");
+    std::vector<double> k;
+    k.reserve(2 + 14 * (size_t)n_rep);
+    k.push_back((double)n_rep);
+    k.push_back((double)ctx->cluster_c);
+    for (int r = 0; r < n_rep; ++r) {
+        const double rec[] = {(double)cr[r].lattice, cr[r].a, cr[r].c_over_a, (double)cr[r].nx, (double)cr[r].ny,
+                              (double)cr[r].nz, md[r].k_spring, md[r].mass, md[r].dt, md[r].damp, md[r].T,
+                              (double)(md[r].seed & 0xffffffffull), (double)(md[r].seed >> 32), (double)md[r].replica};
+        k.insert(k.end(), rec, rec + sizeof rec / sizeof rec[0]);
+    }
+    return k;
+}
+
+static bool same_sched(const Sched& a, const Sched& b)
+{
+    return a.t_eq == b.t_eq && a.t_s == b.t_s && a.lambda_f == b.lambda_f && a.lam_a == b.lam_a &&
+           a.lam_b == b.lam_b && a.s0 == b.s0 && a.dt == b.dt && a.kind == b.kind && a.path == b.path &&
+           a.fn == b.fn && a.stream == b.stream && a.fix_cm == b.fix_cm;
+}
+
+// Build the launch plan of a batch (stencils, replica table, cluster size,
+// size classes and their shared memory) and upload its device part.  Runs
+// on a call whose key differs from the cached plan's; later calls with the
+// same batch launch at once.
+static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep, cudaStream_t st)
+{
+    CrPlan& P = ctx->plan;
+    P.valid = false;
     std::vector<int> off(n_rep + 1, 0);
     for (int r = 0; r < n_rep; ++r) {
         double cell[3];
@@ -1144,19 +1208,13 @@ static ne_status crystal_segment_impl(ne_ctx* ctx, const ne_md_params* md, const
             return fail(ctx, NE_EINVAL, "crystal runner: at most 4096 atoms per replica");
         off[r + 1] = off[r] + (int)nn;
     }
-    ne_status s = check_batch(ctx, md, n_rep, off.data());
-    if (s) return s;
-    if (md[0].prec != NE_MIXED) return fail(ctx, NE_EINVAL, "the crystal runner is mixed precision; use ne_switch_run_segment for FP64");
-    for (int r = 0; r < n_rep; ++r)
-        if (md[r].npt) return fail(ctx, NE_EINVAL, "the crystal runner keeps the box fixed; use ne_switch_run_segment for the barostat");
-    const long long S_total = 2 * md[0].t_eq + 2 * md[0].t_s;
-    if (step_begin < 0 || n_steps < 0 || step_begin + n_steps > S_total)
-        return fail(ctx, NE_EINVAL, "step range outside the schedule");
-    cudaStream_t st = (cudaStream_t)stream;
+    if (off[n_rep] > ctx->max_atoms) return fail(ctx, NE_ENOMEM, "atom count exceeds the context");
     const double rc = ctx->eam.r_c;
     std::vector<XRep> xr(n_rep);
-    std::vector<float4> sv;  // (lattice vector, neighbour code as float bits)
-    std::vector<float> sd;   // |lattice vector|
+    std::vector<float4>& sv = P.sv;  // (lattice vector, neighbour code as float bits)
+    std::vector<float>& sd = P.sd;   // |lattice vector|
+    sv.clear();
+    sd.clear();
     for (int r = 0; r < n_rep; ++r) {
         const ne_md_params& m = md[r];
         XRep& X = xr[r];
@@ -1201,6 +1259,19 @@ static ne_status crystal_segment_impl(ne_ctx* ctx, const ne_md_params* md, const
         const int LY = X.ny + 2 * M, LZ = X.nz + 2 * M;
         if ((X.nx + 2 * M) * LY >= (1 << 16) || X.nb * LZ >= (1 << 16))
             return fail(ctx, NE_EINVAL, "crystal runner: box shape outside the stencil code range");
+        // a replica with the same lattice, cell counts and margin as an
+        // earlier one of the batch shares its stencil
+        int same = -1;
+        for (int q = 0; q < r && same < 0; ++q)
+            if (cr[q].lattice == cr[r].lattice && cr[q].a == cr[r].a && cr[q].c_over_a == cr[r].c_over_a &&
+                cr[q].nx == cr[r].nx && cr[q].ny == cr[r].ny && cr[q].nz == cr[r].nz)
+                same = q;
+        if (same >= 0) {
+            X.st_cnt = xr[same].st_cnt;
+            X.st_margin = xr[same].st_margin;
+            X.st_off = xr[same].st_off;
+            continue;
+        }
         std::vector<std::vector<std::pair<double, std::pair<float4, int>>>> per(X.nb);
         for (int b = 0; b < X.nb; ++b) {
             for (int dx = -M; dx <= M; ++dx)
@@ -1310,66 +1381,118 @@ static ne_status crystal_segment_impl(ne_ctx* ctx, const ne_md_params* md, const
     std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
         return csize(p) > csize(q) || (csize(p) == csize(q) && xr[p].n > xr[q].n);
     });
-    std::vector<XRep> xs(n_rep);
+    P.xs.assign(n_rep, XRep{});
     for (int q = 0; q < n_rep; ++q) {
-        xs[q] = xr[order[q]];
-        xs[q].widx = order[q];
+        P.xs[q] = xr[order[q]];
+        P.xs[q].widx = order[q];
     }
-    NE_CU(cudaMemcpyAsync(ctx->xrep, xs.data(), sizeof(XRep) * n_rep, cudaMemcpyHostToDevice, st));
-    NE_CU(cudaMemcpyAsync(ctx->st_vec, sv.data(), sizeof(float4) * sv.size(), cudaMemcpyHostToDevice, st));
-    NE_CU(cudaMemcpyAsync(ctx->st_dist, sd.data(), sizeof(float) * sd.size(), cudaMemcpyHostToDevice, st));
-    NE_CU(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
-    NE_CU(cudaMemsetAsync(ctx->rep_status, 0, sizeof(int) * n_rep, st));
-    ctx->last_nrep_cr = n_rep;
-    Sched S = make_sched(md[0]);
-    if (n_steps + 2 > ctx->lam_cap) {
-        if (ctx->lam_tab) {
-            NE_CU(cudaStreamSynchronize(st));
-            cudaFree(ctx->lam_tab);
-            ctx->lam_tab = nullptr;
-            ctx->lam_cap = 0;
-        }
-        NE_CU(cudaMalloc((void**)&ctx->lam_tab, sizeof(double) * (size_t)(n_steps + 2)));
-        ctx->lam_cap = n_steps + 2;
-    }
-    NE_CU(ne::launch_lambda_table(S, step_begin, n_steps + 2, ctx->lam_tab, st));
-    ++ctx->cr_launches;
-    // groups
-    std::vector<std::pair<int, int>> groups;  // [begin, end) in xs
+    P.groups.clear();
     for (int q = 0; q < n_rep;) {
         int e = q;
         while (e < n_rep && csize(order[e]) == csize(order[q])) ++e;
-        groups.push_back({q, e});
+        CrGroup g{};
+        g.b = q;
+        g.e = e;
+        g.C = csize(order[q]);
+        std::vector<int> rs;
+        for (int t = q; t < e; ++t) rs.push_back(order[t]);
+        if (!launch_smem(rs, g.smem, g.k_lo)) return fail(ctx, NE_EINVAL, "replica too large for the crystal runner");
+        P.groups.push_back(g);
         q = e;
     }
-    if (groups.size() > 16) return fail(ctx, NE_EINVAL, "crystal runner: at most 16 size classes per call");
-    const bool multi = groups.size() > 1;
-    if (multi) {
-        if (!ctx->gev[0]) {
-            for (int g = 0; g < 17; ++g) NE_CU(cudaEventCreateWithFlags(&ctx->gev[g], cudaEventDisableTiming));
-            for (int g = 0; g < 16; ++g) NE_CU(cudaStreamCreateWithFlags(&ctx->gst[g], cudaStreamNonBlocking));
-        }
-        NE_CU(cudaEventRecord(ctx->gev[16], st));
+    if (P.groups.size() > 16) return fail(ctx, NE_EINVAL, "crystal runner: at most 16 size classes per call");
+    if (P.groups.size() > 1 && !ctx->gev[0]) {
+        for (int g = 0; g < 17; ++g) NE_CU(cudaEventCreateWithFlags(&ctx->gev[g], cudaEventDisableTiming));
+        for (int g = 0; g < 16; ++g) NE_CU(cudaStreamCreateWithFlags(&ctx->gst[g], cudaStreamNonBlocking));
     }
-    for (size_t g = 0; g < groups.size(); ++g) {
-        const int b = groups[g].first, e = groups[g].second;
-        std::vector<int> rs;
-        for (int q = b; q < e; ++q) rs.push_back(order[q]);
-        size_t smem = 0;
-        int k_lo = 0;
-        if (!launch_smem(rs, smem, k_lo)) return fail(ctx, NE_EINVAL, "replica too large for the crystal runner");
+    // the host vectors stay in the plan until the next rebuild, which comes
+    // after this call's closing synchronisation: the copies never outlive them
+    NE_CU(cudaMemcpyAsync(ctx->xrep, P.xs.data(), sizeof(XRep) * n_rep, cudaMemcpyHostToDevice, st));
+    NE_CU(cudaMemcpyAsync(ctx->st_vec, sv.data(), sizeof(float4) * sv.size(), cudaMemcpyHostToDevice, st));
+    NE_CU(cudaMemcpyAsync(ctx->st_dist, sd.data(), sizeof(float) * sd.size(), cudaMemcpyHostToDevice, st));
+    P.key = plan_key(ctx, md, cr, n_rep);
+    P.valid = true;
+    return NE_OK;
+}
+
+// lambda(s) of every step of the schedule, s = 0 .. 2 t_eq + 2 t_s + 1,
+// computed once per schedule (FP64) and read by the persistent kernel
+static ne_status lambda_table(ne_ctx* ctx, const Sched& S, cudaStream_t st)
+{
+    if (ctx->lam_valid && same_sched(ctx->lam_sched, S)) return NE_OK;
+    const long long need = 2 * S.t_eq + 2 * S.t_s + 2;
+    ctx->lam_valid = false;
+    if (need > ctx->lam_cap) {
+        // every earlier call ended with a synchronisation of its stream, so
+        // no kernel still reads the old table
+        if (ctx->lam_tab) cudaFree(ctx->lam_tab);
+        ctx->lam_tab = nullptr;
+        ctx->lam_cap = 0;
+        NE_CU(cudaMalloc((void**)&ctx->lam_tab, sizeof(double) * (size_t)need));
+        ctx->lam_cap = need;
+    }
+    NE_CU(ne::launch_lambda_table(S, 0, need, ctx->lam_tab, st));
+    ++ctx->cr_launches;
+    ctx->lam_sched = S;
+    ctx->lam_valid = true;
+    return NE_OK;
+}
+
+static ne_status crystal_segment_impl(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep,
+                                      double* x_dev, double* v_dev, double* W_dev, double* Wcum_dev,
+                                      long long step_begin, long long n_steps, void* stream)
+{
+    if (!ctx || !md || !cr || !x_dev || !v_dev || !W_dev || n_rep < 1) return NE_EINVAL;
+    if (n_rep > ctx->max_rep) return fail(ctx, NE_ENOMEM, "replica count exceeds the context");
+    std::vector<int> off(n_rep + 1, 0);
+    for (int r = 0; r < n_rep; ++r) {
+        const int nb = cr[r].lattice == NE_BCC ? 2 : 4;
+        if (cr[r].nx < 1 || cr[r].ny < 1 || cr[r].nz < 1 || cr[r].nx > 4096 || cr[r].ny > 4096 || cr[r].nz > 4096)
+            return fail(ctx, NE_EINVAL, "crystal: at least 3 cells per axis");
+        off[r + 1] = off[r] + (int)std::min<long long>((long long)nb * cr[r].nx * cr[r].ny * cr[r].nz, 1 << 20);
+    }
+    ne_status s = check_batch(ctx, md, n_rep, off.data());
+    if (s) return s;
+    if (md[0].prec != NE_MIXED) return fail(ctx, NE_EINVAL, "the crystal runner is mixed precision; use ne_switch_run_segment for FP64");
+    for (int r = 0; r < n_rep; ++r)
+        if (md[r].npt) return fail(ctx, NE_EINVAL, "the crystal runner keeps the box fixed; use ne_switch_run_segment for the barostat");
+    const long long S_total = 2 * md[0].t_eq + 2 * md[0].t_s;
+    if (step_begin < 0 || n_steps < 0 || step_begin + n_steps > S_total)
+        return fail(ctx, NE_EINVAL, "step range outside the schedule");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!ctx->plan.valid || ctx->plan.key != plan_key(ctx, md, cr, n_rep)) {
+        s = build_plan(ctx, md, cr, n_rep, st);
+        if (s) return s;
+    }
+    const CrPlan& P = ctx->plan;
+    // the status word and the per-replica words that follow it
+    NE_CU(cudaMemsetAsync(ctx->status, 0, sizeof(int) * (size_t)(1 + n_rep), st));
+    ctx->last_nrep_cr = n_rep;
+    Sched S = make_sched(md[0]);
+    s = lambda_table(ctx, S, st);
+    if (s) return s;
+    if (!ctx->ev_run[0]) {
+        NE_CU(cudaEventCreate(&ctx->ev_run[0]));
+        NE_CU(cudaEventCreate(&ctx->ev_run[1]));
+    }
+    NE_CU(cudaEventRecord(ctx->ev_run[0], st));
+    const bool multi = P.groups.size() > 1;
+    if (multi) NE_CU(cudaEventRecord(ctx->gev[16], st));
+    for (size_t g = 0; g < P.groups.size(); ++g) {
+        const CrGroup& G = P.groups[g];
         cudaStream_t gs = multi ? ctx->gst[g] : st;
         if (multi) NE_CU(cudaStreamWaitEvent(gs, ctx->gev[16], 0));
-        NE_CU(ne::launch_cluster(ctx->xrep + b, e - b, csize(order[b]), smem, ctx->st_vec, ctx->st_dist, x_dev, v_dev,
-                                 W_dev, ctx->status, S, step_begin, n_steps, ctx->tab, ctx->work, k_lo, ctx->lam_tab,
-                                 Wcum_dev, gs));
+        NE_CU(ne::launch_cluster(ctx->xrep + G.b, G.e - G.b, G.C, G.smem, ctx->st_vec, ctx->st_dist, x_dev, v_dev,
+                                 W_dev, ctx->status, S, step_begin, n_steps, ctx->tab, ctx->work, G.k_lo,
+                                 ctx->lam_tab + step_begin, Wcum_dev, gs));
         ++ctx->cr_launches;
         if (multi) {
             NE_CU(cudaEventRecord(ctx->gev[g], gs));
             NE_CU(cudaStreamWaitEvent(st, ctx->gev[g], 0));
         }
     }
-    NE_CU(cudaStreamSynchronize(st));  // host vectors above must outlive the copies
+    NE_CU(cudaEventRecord(ctx->ev_run[1], st));
+    ctx->run_timed = true;
     return finish(ctx, st);
 }
 
@@ -1401,43 +1524,64 @@ ne_status ne_profile_segment(ne_ctx* ctx, const ne_md_params* md, int n_rep, con
     return finish(ctx, st);
 }
 
-ne_status ne_msd_fit(ne_ctx* ctx, const ne_md_params* md, double* x_dev, double* v_dev, const double* x0_dev,
-                     int n, const double box[3], long long n_eq, long long n_samples, int stride,
-                     double* msd_host, double* k_host, void* stream)
+ne_status ne_msd_fit_batched(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* offsets_host,
+                             double* x_dev, double* v_dev, const double* x0_dev, const double* boxes_host,
+                             long long n_eq, long long n_samples, int stride, double* msd_host, double* k_host,
+                             void* stream)
 {
-    if (!ctx || !x_dev || !v_dev || !x0_dev || !box || n < 2 || n_eq < 0 || n_samples < 1 || stride < 1)
+    if (!ctx || !md || n_rep < 1 || !offsets_host || !x_dev || !v_dev || !x0_dev || !boxes_host || n_eq < 0 ||
+        n_samples < 1 || stride < 1)
         return NE_EINVAL;
-    ne_status s = check_md(ctx, md);
-    if (s) return s;
-    if (md->npt) return fail(ctx, NE_EINVAL, "the barostat runs in the switching runs (ne_switch_run_segment, ne_rs_run)");
+    if (n_rep > ctx->max_rep) return fail(ctx, NE_ENOMEM, "replica count exceeds the context");
+    for (int r = 0; r < n_rep; ++r) {
+        ne_status s = check_md(ctx, &md[r]);
+        if (s) return s;
+        if (md[r].npt) return fail(ctx, NE_EINVAL, "the barostat runs in the switching runs (ne_switch_run_segment, ne_rs_run)");
+        if (md[r].dt != md[0].dt || md[r].damp != md[0].damp || md[r].fix_cm != md[0].fix_cm ||
+            md[r].prec != md[0].prec)
+            return fail(ctx, NE_EINVAL, "replicas must share dt, damp, fix_cm and precision");
+        if (offsets_host[r + 1] - offsets_host[r] < 2) return fail(ctx, NE_EINVAL, "offsets must increase by at least 2");
+    }
+    if (offsets_host[0] != 0) return fail(ctx, NE_EINVAL, "offsets must start at 0");
     cudaStream_t st = (cudaStream_t)stream;
-    int off[2] = {0, n};
     RunArgs a{};
     a.x = x_dev;
     a.v = v_dev;
     a.x0 = x0_dev;
     a.W = ctx->W;
     DevBatch B;
-    s = setup_batch(ctx, 1, off, box, md, 0, -1.0, B, a, st);
+    ne_status s = setup_batch(ctx, n_rep, offsets_host, boxes_host, md, 0, -1.0, B, a, st);
     if (s) return s;
-    Sched S = make_sched(*md);
+    Sched S = make_sched(md[0]);
     S.kind = SCHED_FIXED;
     S.path = NE_PATH_FL;
     S.lam_a = S.lam_b = 0.0;
     S.s0 = -1;
     S.stream = STREAM_MSD;
-    double* acc = ctx->scratch;
-    NE_CU(cudaMemsetAsync(acc, 0, sizeof(double), st));
-    s = run_steps(ctx, B, S, md->prec == NE_MIXED, 0, n_eq + n_samples * stride, st, acc, n_eq, stride);
+    double* acc = ctx->scratch;  // one msd sum per replica
+    NE_CU(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)n_rep, st));
+    s = run_steps(ctx, B, S, md[0].prec == NE_MIXED, 0, n_eq + n_samples * stride, st, acc, n_eq, stride);
     if (s) return s;
-    double sum = 0.0;
-    NE_CU(cudaMemcpyAsync(&sum, acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+    std::vector<double> sum(n_rep, 0.0);
+    NE_CU(cudaMemcpyAsync(sum.data(), acc, sizeof(double) * (size_t)n_rep, cudaMemcpyDeviceToHost, st));
     s = finish(ctx, st);
     if (s) return s;
-    const double msd = sum / (double)n_samples;
-    if (msd_host) *msd_host = msd;
-    if (k_host) *k_host = 3.0 * kB * md->T / msd;
+    for (int r = 0; r < n_rep; ++r) {
+        const double msd = sum[r] / (double)n_samples;
+        if (msd_host) msd_host[r] = msd;
+        if (k_host) k_host[r] = 3.0 * kB * md[r].T / msd;
+    }
     return NE_OK;
+}
+
+ne_status ne_msd_fit(ne_ctx* ctx, const ne_md_params* md, double* x_dev, double* v_dev, const double* x0_dev,
+                     int n, const double box[3], long long n_eq, long long n_samples, int stride,
+                     double* msd_host, double* k_host, void* stream)
+{
+    if (!ctx || !md || !box || n < 2) return NE_EINVAL;
+    const int off[2] = {0, n};
+    return ne_msd_fit_batched(ctx, md, 1, off, x_dev, v_dev, x0_dev, box, n_eq, n_samples, stride, msd_host,
+                              k_host, stream);
 }
 
 // ------------------------------------------------------------ assembly
@@ -1523,6 +1667,32 @@ ne_status ne_free_energy_species(int n, const int* species, int n_species, const
         *stderr_per_atom = se;
     }
     if (Ediss_per_atom) *Ediss_per_atom = -0.5 * (wf + wb) / n;
+    return NE_OK;
+}
+
+ne_status ne_lambda(const ne_md_params* md, long long step, double* lambda_host)
+{
+    if (!md || !lambda_host) return NE_EINVAL;
+    if (md->path != NE_PATH_FL && md->path != NE_PATH_RS) return NE_EINVAL;
+    if (md->path == NE_PATH_FL && md->lambda_fn != 1 && md->lambda_fn != 2) return NE_EINVAL;
+    if (md->path == NE_PATH_RS && !(md->lambda_f > 0 && md->lambda_f < 1)) return NE_EINVAL;
+    if (md->t_s < 1 || md->t_eq < 0 || step < 0 || step > 2 * md->t_eq + 2 * md->t_s) return NE_EINVAL;
+    *lambda_host = ne_sched_lambda(make_sched(*md), step);
+    return NE_OK;
+}
+
+ne_status ne_pressure(int n_dof, double T, double V, const double* W_host, int n_samples, double* P_host,
+                      double* stderr_host)
+{
+    if (n_dof < 0 || !(T >= 0) || !(V > 0) || !W_host || n_samples < 1 || !P_host) return NE_EINVAL;
+    double mean = 0.0;
+    for (int q = 0; q < n_samples; ++q) mean += W_host[q];
+    mean /= n_samples;
+    double ss = 0.0;
+    for (int q = 0; q < n_samples; ++q) ss += (W_host[q] - mean) * (W_host[q] - mean);
+    *P_host = (n_dof * kB * T + mean) / (3.0 * V);
+    if (stderr_host)
+        *stderr_host = n_samples > 1 ? std::sqrt(ss / (n_samples - 1)) / std::sqrt((double)n_samples) / (3.0 * V) : 0.0;
     return NE_OK;
 }
 

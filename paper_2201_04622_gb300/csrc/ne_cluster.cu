@@ -367,7 +367,17 @@ __global__ void __launch_bounds__(THREADS, 1)
     const float dt = (float)S.dt;
     const float rho_maxf = (float)tab.rho_max;
     const float ihr_hi = (float)tab.inv_h_rho, ihr_lo = (float)(tab.inv_h_rho - (double)ihr_hi);
-    double UE_prev = 0.0;  // rank 0, thread SLOTS: U_E at the positions of the previous step
+    // rank 0, thread SLOTS (owns no atom) keeps the replica's two works in
+    // registers and writes them back at the end, only if the replica
+    // completed the range; likewise x and v below, so a replica that raised
+    // an error keeps its state of step s_begin and can be rerun from there
+    const bool wthread = rank == 0 && threadIdx.x == SLOTS;
+    double Wacc[2] = {0.0, 0.0};
+    if (wthread) {
+        Wacc[0] = Wg[2 * reps[rep].widx];
+        Wacc[1] = Wg[2 * reps[rep].widx + 1];
+    }
+    double UE_prev = 0.0;  // the work thread: U_E at the positions of the previous step
 
 #pragma unroll 1
     for (long long it = 0; it <= n_steps; ++it) {
@@ -538,7 +548,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         // step s + 1 into the other CTAs, which by then have all finished
         // reading step s too (the integration hides the barrier's latency).
         asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-        if (rank == 0 && threadIdx.x == SLOTS) {
+        if (wthread) {
             // work increment of step s - 1, (lambda_s - lambda_{s-1}) dH/dlambda(x_{s-1}),
             // by a thread that owns no atom (s_tot holds the sums of step s
             // until the next cluster barrier)
@@ -550,13 +560,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (sp >= S.t_eq && sp < S.t_eq + S.t_s) wslot = 0;
                 else if (sp >= 2 * S.t_eq + S.t_s && sp < 2 * S.t_eq + 2 * S.t_s) wslot = 1;
                 if (wslot >= 0) {
-                    double* Wr = Wg + 2 * reps[rep].widx + wslot;
-                    *Wr += (lam_tab[it] - lam_tab[it - 1]) * g;
+                    Wacc[wslot] += (lam_tab[it] - lam_tab[it - 1]) * g;
                     if (wcum) {  // cumulative work of the switch: [0] = 0, [k + 1] after its step k
                         const long long k = wslot == 0 ? sp - S.t_eq : sp - (2 * S.t_eq + S.t_s);
                         double* wc = wcum + (size_t)(2 * reps[rep].widx + wslot) * (size_t)(S.t_s + 1);
                         if (k == 0) wc[0] = 0.0;
-                        wc[k + 1] = *Wr;
+                        wc[k + 1] = Wacc[wslot];
                     }
                 }
             }
@@ -619,11 +628,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                                         s_slotM + ((s + 1) & 1) * 16, rank, C, own_warps);
         }
     }
-    if (own)
-        for (int c = 0; c < 3; ++c) {
-            xg[gi + c] = (double)(xr[c] + site_fix(c)) / XSCALE;
-            vg[gi + c] = (double)v[c];
-        }
     if (bad) {
         ne_set_status(status, bad);
         ne_set_status(status + 1 + reps[rep].widx, bad);
@@ -638,7 +642,25 @@ __global__ void __launch_bounds__(THREADS, 1)
             atomicAdd(&work[1], (unsigned long long)n_pair);
         }
     }
-    cluster.sync();  // no CTA leaves while others may still touch its shared memory
+    // every CTA's error bits for this replica are in its status word once the
+    // cluster has passed this barrier (the fence orders the atomics first);
+    // after it no CTA touches another's shared memory, so each may finish alone
+    __threadfence();
+    cluster.sync();
+    int* s_fail = (int*)s_slotM;  // no longer in use
+    if (threadIdx.x == 0) *s_fail = atomicOr(status + 1 + reps[rep].widx, 0);
+    __syncthreads();
+    if (*s_fail == 0) {
+        if (own)
+            for (int c = 0; c < 3; ++c) {
+                xg[gi + c] = (double)(xr[c] + site_fix(c)) / XSCALE;
+                vg[gi + c] = (double)v[c];
+            }
+        if (wthread) {
+            Wg[2 * reps[rep].widx] = Wacc[0];
+            Wg[2 * reps[rep].widx + 1] = Wacc[1];
+        }
+    }
 }
 
 }  // namespace

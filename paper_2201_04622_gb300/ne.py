@@ -24,13 +24,14 @@ NE_PATH_FL, NE_PATH_RS = 0, 1
 
 # every symbol include/ne.h declares
 SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_clone", "ne_ctx_set_theta", "ne_ctx_get_theta",
-           "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_boxes", "ne_ctx_replica_status", "ne_ctx_counters", "ne_last_error",
+           "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_boxes", "ne_ctx_replica_status", "ne_ctx_counters", "ne_ctx_last_run_ms",
+           "ne_last_error",
            "ne_create_crystal", "ne_create_crystal_ca", "ne_eam_energy_forces", "ne_eam_virial", "ne_eam_energy_forces_noalloc",
            "ne_spring_forces",
            "ne_eam_backward", "ne_eam_backward_acc", "ne_noise", "ne_init_velocities", "ne_langevin_step",
            "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment", "ne_switch_run_segment_grad",
            "ne_profile_segment", "ne_crystal_run_segment", "ne_crystal_run_segment_cum",
-           "ne_msd_fit", "ne_free_energy", "ne_free_energy_species", "ne_jarzynski",
+           "ne_msd_fit", "ne_msd_fit_batched", "ne_free_energy", "ne_free_energy_species", "ne_jarzynski", "ne_lambda", "ne_pressure",
            "ne_rs_free_energy"]
 
 
@@ -88,6 +89,7 @@ def load(build_if_missing: bool = True):
                 "ne_ctx_boxes": [p, i, p],
                 "ne_ctx_replica_status": [p, i, p],
                 "ne_ctx_counters": [p, p, p, p, p],
+                "ne_ctx_last_run_ms": [p, p],
                 "ne_last_error": [p, p, p, i],
                 "ne_create_crystal": [i, d, i, i, i, p, p, p],
                 "ne_create_crystal_ca": [i, d, d, i, i, i, p, p, p],
@@ -109,9 +111,12 @@ def load(build_if_missing: bool = True):
                 "ne_crystal_run_segment": [p, p, p, i, p, p, p, ll, ll, p],
                 "ne_crystal_run_segment_cum": [p, p, p, i, p, p, p, p, ll, ll, p],
                 "ne_msd_fit": [p, p, p, p, p, i, p, ll, ll, i, p, p, p],
+                "ne_msd_fit_batched": [p, p, i, p, p, p, p, p, ll, ll, i, p, p, p],
                 "ne_free_energy": [i, d, d, d, d, p, p, i, p, p, p],
                 "ne_free_energy_species": [i, p, i, p, p, d, d, p, p, i, p, p, p],
                 "ne_jarzynski": [d, p, i, p],
+                "ne_lambda": [p, ll, p],
+                "ne_pressure": [i, d, d, p, i, p, p],
                 "ne_rs_free_energy": [i, d, d, d, ll, p, p, i, p, i, p],
             }
             for name, args in sigs.items():
@@ -286,6 +291,13 @@ def ne_ctx_counters(ctx):
     return a.value, b.value, c.value, d.value
 
 
+def ne_ctx_last_run_ms(ctx):
+    """Device time (ms) of the cluster launches of the last crystal-runner call."""
+    ms = C.c_double()
+    _err(ctx, load().ne_ctx_last_run_ms(ctx, C.byref(ms)), "ne_ctx_last_run_ms")
+    return ms.value
+
+
 def ne_last_error(ctx):
     buf = C.create_string_buffer(256)
     st = C.c_int()
@@ -448,15 +460,25 @@ def ne_profile_segment(ctx, mds, offsets, x, v, x0, boxes, W, step_begin, n_step
     return list(ms), list(cnt)
 
 
+class CrystalBatch:
+    """The md and crystal arrays of a crystal-runner batch, packed once for
+    repeated ne_crystal_run_segment calls (pass it as `mds`, crystals=None)."""
+
+    def __init__(self, mds, crystals):
+        self.n_rep = len(mds)
+        self.md = (MdParams * self.n_rep)(*mds)
+        self.cr = (Crystal * self.n_rep)(*[Crystal(int(c[0]), float(c[1]), int(c[2]), int(c[3]), int(c[4]),
+                                                   float(c[5]) if len(c) > 5 else 0.0) for c in crystals])
+        self.n3 = 3 * _crystal_atoms(crystals)
+
+
 def ne_crystal_run_segment(ctx, mds, crystals, x, v, W, step_begin, n_steps, stream=None):
-    """crystals: list of (lattice, a, nx, ny, nz[, c_over_a])."""
-    n_rep = len(mds)
-    arr = (MdParams * n_rep)(*mds)
-    cr = (Crystal * n_rep)(*[Crystal(int(c[0]), float(c[1]), int(c[2]), int(c[3]), int(c[4]),
-                                     float(c[5]) if len(c) > 5 else 0.0) for c in crystals])
-    n3 = 3 * _crystal_atoms(crystals)
-    _err(ctx, load().ne_crystal_run_segment(ctx, arr, cr, n_rep, _dev(x, n3), _dev(v, n3), _dev(W, 2 * n_rep),
-                                            int(step_begin), int(n_steps), _stream(stream)),
+    """crystals: list of (lattice, a, nx, ny, nz[, c_over_a]); or mds a
+    CrystalBatch and crystals None."""
+    b = mds if isinstance(mds, CrystalBatch) else CrystalBatch(mds, crystals)
+    _err(ctx, load().ne_crystal_run_segment(ctx, b.md, b.cr, b.n_rep, _dev(x, b.n3), _dev(v, b.n3),
+                                            _dev(W, 2 * b.n_rep), int(step_begin), int(n_steps),
+                                            _stream(stream)),
          "ne_crystal_run_segment")
 
 
@@ -481,6 +503,23 @@ def ne_msd_fit(ctx, md: MdParams, x, v, x0, box, n_eq, n_samples, stride, stream
                                 int(stride), C.byref(msd), C.byref(k), _stream(stream)),
          "ne_msd_fit")
     return msd.value, k.value
+
+
+def ne_msd_fit_batched(ctx, mds, offsets, x, v, x0, boxes, n_eq, n_samples, stride, stream=None):
+    """Per-replica (msd, k) of a batch (numpy arrays of n_rep)."""
+    import numpy as np
+    n_rep = len(mds)
+    arr = (MdParams * n_rep)(*mds)
+    off = (C.c_int * (n_rep + 1))(*[int(o) for o in offsets])
+    n3 = 3 * _batch_atoms(offsets, n_rep)
+    bx = (C.c_double * (3 * n_rep))(*[float(b) for box in boxes for b in box])
+    msd = np.zeros(n_rep)
+    k = np.zeros(n_rep)
+    _err(ctx, load().ne_msd_fit_batched(ctx, arr, n_rep, off, _dev(x, n3), _dev(v, n3), _dev(x0, n3), bx,
+                                        int(n_eq), int(n_samples), int(stride), msd.ctypes.data_as(C.c_void_p),
+                                        k.ctypes.data_as(C.c_void_p), _stream(stream)),
+         "ne_msd_fit_batched")
+    return msd, k
 
 
 def ne_free_energy(n, V, T, mass, k, W_fwd, W_bwd):
@@ -514,6 +553,23 @@ def ne_free_energy_species(species, mass_s, k_s, V, T, W_fwd, W_bwd):
                                              ptr(wf), ptr(wb), wf.size, C.byref(F), C.byref(se),
                                              C.byref(ed)), "ne_free_energy_species")
     return F.value, se.value, ed.value
+
+
+def ne_lambda(md: MdParams, step):
+    """Lambda in force at the start of `step` of md's four-phase schedule."""
+    lam = C.c_double()
+    _err(None, load().ne_lambda(C.byref(md), int(step), C.byref(lam)), "ne_lambda")
+    return lam.value
+
+
+def ne_pressure(n_dof, T, V, W):
+    """(P, standard error) in eV/A^3 from virial samples W (eV)."""
+    import numpy as np
+    w = np.ascontiguousarray(np.atleast_1d(W), np.float64).ravel()
+    P, se = C.c_double(), C.c_double()
+    _err(None, load().ne_pressure(int(n_dof), float(T), float(V), w.ctypes.data_as(C.c_void_p), w.size,
+                                  C.byref(P), C.byref(se)), "ne_pressure")
+    return P.value, se.value
 
 
 def ne_jarzynski(T, W):

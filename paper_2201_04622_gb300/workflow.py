@@ -99,6 +99,7 @@ class BatchAdvancer:
         self.chunk = chunk
         self.moved, self.log = [], []
         self._ctx_g = None
+        self._packed = None
         self._cuda = bool(getattr(x0, "is_cuda", False))
         self._sc = torch.cuda.Stream() if self._cuda else None
         self._sg = torch.cuda.Stream() if self._cuda else None
@@ -160,17 +161,41 @@ class BatchAdvancer:
         for c0 in range(s0, s0 + ns, step):
             self._advance_chunk(x, v, W, c0, min(step, s0 + ns - c0))
 
+    def _crystal(self, on_c, x, v, W, c0, cn, stream):
+        """The crystal runner over replicas on_c (x, v, W compact for them);
+        returns the replicas (batch indices) that left its range.  A replica
+        that raised an error keeps its state of step c0 (the runner writes back
+        only replicas that completed the chunk)."""
+        key = tuple(on_c)
+        if self._packed is None or self._packed[0] != key:
+            self._packed = (key, ne.CrystalBatch([self.mds[r] for r in on_c], [self.crystals[r] for r in on_c]))
+        try:
+            ne.ne_crystal_run_segment(self.ctx, self._packed[1], None, x, v, W, c0, cn, stream=stream)
+        except ne.NeError as e:
+            if "NE_ERANGE" not in str(e):
+                raise
+            st = ne.ne_ctx_replica_status(self.ctx, len(on_c))
+            bad = [on_c[q] for q in range(len(on_c)) if st[q] == ne.NE_ERANGE]
+            if not bad:
+                raise
+            return bad
+        finally:
+            self.log.append(("crystal", list(on_c), c0, cn))
+        return []
+
     def _advance_chunk(self, x, v, W, c0, cn):
         import threading
-        import torch
         on_c = [r for r in range(len(self.mds)) if r not in self.moved]
         gen = list(self.moved)
-        xc, vc, Wc, _, sc = self._gather(on_c, x, v, W) if on_c else (None,) * 5
-        xg, vg, Wg, x0g, sg = self._gather(gen, x, v, W) if gen else (None,) * 5
-        snap = (xc.clone(), vc.clone(), Wc.clone()) if on_c else None
-        self._sync()
-        errs, th = [], None
-        if gen:
+        if not gen:
+            # every replica on the crystal runner: one call on the caller's
+            # stream, no copies and no extra synchronisation
+            bad = self._crystal(on_c, x, v, W, c0, cn, None)
+        else:
+            xc, vc, Wc, _, sc = self._gather(on_c, x, v, W) if on_c else (None,) * 5
+            xg, vg, Wg, x0g, sg = self._gather(gen, x, v, W)
+            self._sync()
+            errs, th = [], None
             if not on_c:
                 self._general(gen, xg, vg, x0g, sg, Wg, c0, cn)
             else:
@@ -181,54 +206,31 @@ class BatchAdvancer:
                         errs.append(e)
                 th = threading.Thread(target=work)
                 th.start()
-        bad = []
-        try:
+            bad = []
+            try:
+                if on_c:
+                    bad = self._crystal(on_c, xc, vc, Wc, c0, cn, self._handle(self._sc))
+            finally:
+                if th is not None:
+                    th.join()
+            if errs:
+                raise errs[0]
+            self._sync()
             if on_c:
-                try:
-                    ne.ne_crystal_run_segment(self.ctx, [self.mds[r] for r in on_c], [self.crystals[r] for r in on_c],
-                                              xc, vc, Wc, c0, cn, stream=self._handle(self._sc))
-                    self.log.append(("crystal", on_c, c0, cn))
-                except ne.NeError as e:
-                    if "NE_ERANGE" not in str(e):
-                        raise
-                    st = ne.ne_ctx_replica_status(self.ctx, len(on_c))
-                    bad = [on_c[q] for q in range(len(on_c)) if st[q] == ne.NE_ERANGE]
-                    if not bad:
-                        raise
-                    self.log.append(("crystal", on_c, c0, cn))
-        finally:
-            if th is not None:
-                th.join()
-        if errs:
-            raise errs[0]
-        self._sync()
-        if on_c:
-            self._scatter(on_c, sc, xc, vc, Wc, x, v, W)
-        if gen:
+                self._scatter(on_c, sc, xc, vc, Wc, x, v, W)
             self._scatter(gen, sg, xg, vg, Wg, x, v, W)
         if bad:
             import warnings
             warnings.warn("replicas %s left the crystal runner's stencil range at steps %d-%d; they continue "
                           "on the multi-kernel path" % (bad, c0, c0 + cn))
-            # their state before the chunk, then the chunk on the multi-kernel path
-            for r in bad:
-                q = on_c.index(r)
-                a, b = self.offs[r], self.offs[r + 1]
-                if xc is x:
-                    x[a:b].copy_(snap[0][a:b])
-                    v[a:b].copy_(snap[1][a:b])
-                    W[r].copy_(snap[2][r])
-                else:
-                    x[a:b].copy_(snap[0][sc[q]:sc[q + 1]])
-                    v[a:b].copy_(snap[1][sc[q]:sc[q + 1]])
-                    W[r].copy_(snap[2][q])
+            # their state of step c0 is in place: rerun the chunk on the multi-kernel path
             xb, vb, Wb, x0b, sb = self._gather(bad, x, v, W)
             self._sync()
             self._general(bad, xb, vb, x0b, sb, Wb, c0, cn)
             self._sync()
             self._scatter(bad, sb, xb, vb, Wb, x, v, W)
             self.moved = sorted(self.moved + bad)
-        self._sync()
+            self._sync()
 
 
 def _fl_batch_auto(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec, skin, device, chunk, ids):
@@ -287,11 +289,7 @@ def pressure(ctx, lattice, a, n, T, mass, n_eq=2000, n_samples=50, stride=20, pr
         s0 += stride
         ne.ne_eam_virial(ctx, x, box, w)
         ws.append(float(w.item()))
-    V = float(np.prod(box))
-    ws = np.asarray(ws)
-    P = ((3 * nat - 3) * KB * T + ws.mean()) / (3 * V)
-    err = ws.std(ddof=1) / np.sqrt(len(ws)) / (3 * V) if len(ws) > 1 else float("nan")
-    return P, err
+    return ne.ne_pressure(3 * nat - 3, T, float(np.prod(box)), ws)
 
 
 def lattice_parameter(ctx, lattice, n, T, mass, a_grid, **kw):
@@ -441,13 +439,6 @@ def transition_temperatures(T_grid, F_a, F_b):
     return out
 
 
-def lambda_fl2(tau):
-    """Frenkel-Ladd switching function of Sec. III.B (function 2):
-    tau^5 (70 tau^4 - 315 tau^3 + 540 tau^2 - 420 tau + 126)."""
-    t = min(max(tau, 0.0), 1.0)
-    return t ** 5 * (70 * t ** 4 - 315 * t ** 3 + 540 * t ** 2 - 420 * t + 126)
-
-
 def theta_gradient(ctx, lattice, a, n, T, mass, k, t_eq, t_s, n_knots, seed=1, stride=10, prec=ne.NE_MIXED,
                    skin=1.0, device="cuda"):
     """Gradients with respect to the spline knots theta along one FL run
@@ -485,7 +476,7 @@ def theta_gradient(ctx, lattice, a, n, T, mass, k, t_eq, t_s, n_knots, seed=1, s
             w_eq[s] = 1.0
             n_eq += 1
         else:
-            w_sw[s - t_eq] = lambda_fl2((s - t_eq) / t_s) - lambda_fl2(max(prev - t_eq, 0) / t_s)
+            w_sw[s - t_eq] = ne.ne_lambda(md, s) - ne.ne_lambda(md, max(prev, t_eq))
         prev = s
     for s0, ns, w, g in ((0, t_eq, w_eq, g_eq), (t_eq, t_s, w_sw, g_sw)):
         if ns > 0:

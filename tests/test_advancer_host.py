@@ -2,7 +2,9 @@
 GPU paths: chunking, the move of a replica that leaves the crystal runner's
 range (its state restored from before the chunk, the chunk rerun on the
 multi-kernel path, later chunks there, alongside the crystal runner for the
-others), and the gather/scatter of uneven replicas."""
+others), and the gather/scatter of uneven replicas.  The stand-in runner keeps
+the runner's contract: a replica that raises an error keeps its state of the
+chunk's first step."""
 import types
 
 import numpy as np
@@ -26,19 +28,22 @@ def test_advancer_moves_a_failing_replica_and_keeps_the_others(monkeypatch):
     def rows(o, q):
         return slice(o[q], o[q + 1])
 
-    def crystal(ctx, md, crs, xs, vs, Ws, s0, ns, stream=None):
+    def crystal(ctx, batch, crs, xs, vs, Ws, s0, ns, stream=None):
+        md = batch.mds
+        assert crs is None
         ids = [m.replica for m in md]
         calls.append(("crystal", ids, s0, ns))
         last["ids"] = ids
         o = [0]
         for m in md:
             o.append(o[-1] + offs[m.replica + 1] - offs[m.replica])
+        fail = s0 == 20 and 1 in ids       # replica 1 leaves the range in the third chunk
         for q, m in enumerate(md):
+            if fail and m.replica == 1:
+                continue                   # a replica that failed is not written back
             xs[rows(o, q)] += ns * 1e-3 * (m.replica + 1)
             Ws[q, 0] += ns * (m.replica + 1)
-        if s0 == 20 and 1 in ids:          # replica 1 leaves the range in the third chunk
-            q = ids.index(1)
-            xs[rows(o, q)] = float("nan")
+        if fail:
             raise ne.NeError(ne.NE_ERANGE, "ne_crystal_run_segment", "stand-in")
 
     def general(ctx, md, o, xs, vs, x0s, boxes, Ws, s0, ns, stream=None):
@@ -50,6 +55,7 @@ def test_advancer_moves_a_failing_replica_and_keeps_the_others(monkeypatch):
     def status(ctx, n):
         return np.array([ne.NE_ERANGE if r == 1 else ne.NE_OK for r in last["ids"]][:n], dtype=np.int32)
 
+    monkeypatch.setattr(ne, "CrystalBatch", lambda mds, crs: types.SimpleNamespace(mds=mds))
     monkeypatch.setattr(ne, "ne_crystal_run_segment", crystal)
     monkeypatch.setattr(ne, "ne_switch_run_segment", general)
     monkeypatch.setattr(ne, "ne_ctx_replica_status", status)

@@ -222,7 +222,8 @@ def test_crystal_runner_reports_atoms_beyond_the_stencil_range(ctx):
     """Three bcc 6^3 replicas; the middle one starts with an atom 2.2 A from
     its site (D = 2 A; along [110], 1.45 A from its nearest neighbours, far
     from overlap): NE_ERANGE, and ne_ctx_replica_status names that replica
-    alone.  The same start 1.8 A out runs."""
+    alone; it keeps its x, v and W of the first step while the other two are
+    advanced.  The same start 1.8 A out runs."""
     mo, mg = md_pair(T=300.0)
     x0, box = O.create_crystal(O.BCC, W.A_BCC, 6, 6, 6)
     mgs = [md_pair(T=300.0, replica=r)[1] for r in range(3)]
@@ -231,14 +232,19 @@ def test_crystal_runner_reports_atoms_beyond_the_stencil_range(ctx):
         x = np.concatenate([x0] * 3)
         x[len(x0), :2] += shift / np.sqrt(2.0)
         xt, vt = T(x), T(np.zeros_like(x))
-        Wd = torch.zeros((3, 2), dtype=torch.float64, device=DEV)
+        Wd = torch.full((3, 2), 1.5, dtype=torch.float64, device=DEV)
         if ok:
             ne.ne_crystal_run_segment(ctx, mgs, crs, xt, vt, Wd, 0, 10)
             assert list(ne.ne_ctx_replica_status(ctx, 3)) == [ne.NE_OK] * 3
         else:
+            xin, vin = xt.clone(), vt.clone()
             with pytest.raises(ne.NeError, match="NE_ERANGE"):
                 ne.ne_crystal_run_segment(ctx, mgs, crs, xt, vt, Wd, 0, 10)
             assert list(ne.ne_ctx_replica_status(ctx, 3)) == [ne.NE_OK, ne.NE_ERANGE, ne.NE_OK]
+            n1 = len(x0)
+            assert torch.equal(xt[n1:2 * n1], xin[n1:2 * n1]) and torch.equal(vt[n1:2 * n1], vin[n1:2 * n1])
+            assert Wd[1].tolist() == [1.5, 1.5]
+            assert not torch.equal(xt[:n1], xin[:n1]) and not torch.equal(xt[2 * n1:], xin[2 * n1:])
 
 
 @pytest.mark.parametrize("lat,n", [(O.BCC, 5), (O.FCC, 4)])
@@ -272,9 +278,14 @@ def test_auto_runner_moves_out_of_range_replicas_to_the_multikernel_path(ctx, mo
     calls = []
 
     def fake(c, mds, crs, x, v, W, s0, ns, stream=None):
+        n_rep = mds.n_rep if isinstance(mds, ne.CrystalBatch) else len(mds)
+        fail = s0 == 40 and n_rep == 3
+        if fail:  # the runner's contract: a replica that raised keeps its state of s0
+            keep = (x[432:864].clone(), v[432:864].clone(), W[1].clone())
         real(c, mds, crs, x, v, W, s0, ns, stream=stream)
-        calls.append((s0, len(mds)))
-        if s0 == 40 and len(mds) == 3:
+        calls.append((s0, n_rep))
+        if fail:
+            x[432:864], v[432:864], W[1] = keep
             raise ne.NeError(ne.NE_ERANGE, "ne_crystal_run_segment", "stand-in")
 
     crystals = [(O.BCC, W.A_BCC, 6)] * 3
