@@ -15,8 +15,15 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
                         analytic potential; Newton's third law
   eam_grad_theta        central differences in theta
   lambda_fl / lambda_rs end conditions, symmetry, printed values, T linear
-  philox4x32_10         normal moments and KS test (CPU); cuRAND's
-                        independent Philox on the GPU
+  sched_lambda          the four phases' end values, telescoping work weights,
+                        the backward switch mirrors the forward one
+  pressure              ideal-gas limit P V = (N - 1) k_B T with the centre
+                        fixed; at 0 K equals -dE/dV of the static lattice
+                        by central differences (zero at the fitted a)
+  philox4x32_10         normal moments, KS and avalanche tests (CPU); bit
+                        for bit against cuRAND's Philox4_32_10 (NVIDIA's
+                        implementation, run through its device API on the
+                        GPU) over >= 1e6 counters (tests/test_zz_philox_curand.py)
   switch_run (FL)       harmonic->harmonic exact dF, self-switch W == 0,
                         NVE energy conservation, equipartition
   switch_run (RS)       harmonic F(T) = 3NkT ln(hbar w/kT) at every T
@@ -137,6 +144,11 @@ def lib():
             L.ora_free_energy.argtypes = [i, d, d, d, d, p, p, i, p, p, p]
             L.ora_rs_free_energy.argtypes = [i, d, d, d, C.c_long, p, p, i, p, i, p]
             L.ora_philox4x32_10.argtypes = [p, p, p]
+            L.ora_philox_many.argtypes = [i, p, p, p]
+            L.ora_sched_lambda.restype = d
+            L.ora_sched_lambda.argtypes = [p, C.c_long]
+            L.ora_pressure.argtypes = [i, d, d, p, i, p, p]
+            L.ora_normals_many.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, i, p]
             _lib = L
     return _lib
 
@@ -314,12 +326,41 @@ def lambda_rs(lambda_f, tau):
     return lib().ora_lambda_rs(lambda_f, tau)
 
 
+def sched_lambda(m: MD, step):
+    """Lambda in force at the start of `step` of m's four-phase schedule."""
+    return lib().ora_sched_lambda(C.byref(m), step)
+
+
+def pressure(n_dof, T, V, W):
+    """(P, standard error) = ((N_dof k_B T + <W>) / (3V), s(W)/sqrt(n)/(3V))."""
+    w = _f64(np.atleast_1d(W))
+    P, e = C.c_double(), C.c_double()
+    lib().ora_pressure(n_dof, T, V, _ptr(w), w.size, C.byref(P), C.byref(e))
+    return P.value, e.value
+
+
 def philox(ctr, key):
     c = np.ascontiguousarray(ctr, dtype=np.uint32)
     k = np.ascontiguousarray(key, dtype=np.uint32)
     out = np.zeros(4, np.uint32)
     lib().ora_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
     return out
+
+
+def philox_many(ctr, key):
+    """Philox4x32-10 blocks of many counters ([n][4] uint32) under one key."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros_like(c)
+    lib().ora_philox_many(c.shape[0], _ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def normals_many(seed, replica, stream, step, n):
+    """normals() of atoms 0 .. n-1 at one (seed, replica, stream, step): [n][3]."""
+    z = np.zeros((n, 3))
+    lib().ora_normals_many(seed, replica, stream, step, n, _ptr(z))
+    return z
 
 
 def normals(seed, replica, stream, atom, step):

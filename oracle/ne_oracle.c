@@ -533,6 +533,23 @@ static double sched_lambda(const ora_md* md, long s)
     return li;
 }
 
+double ora_sched_lambda(const ora_md* md, long s) { return sched_lambda(md, s); }
+
+/* Sec. III.A: the pressure of an NVT state from the thermostat's degrees of
+ * freedom and the configurational virial W (ora_eam_virial) sampled along
+ * the run, P = (N_dof k_B T + <W>) / (3 V); its standard error from the
+ * scatter of the samples, s(W) / sqrt(n) / (3 V) (0 for one sample). */
+void ora_pressure(int n_dof, double T, double V, const double* W, int n, double* P, double* err)
+{
+    double mean = 0.0;
+    for (int i = 0; i < n; i++) mean += W[i];
+    mean /= n;
+    double ss = 0.0;
+    for (int i = 0; i < n; i++) ss += (W[i] - mean) * (W[i] - mean);
+    *P = (n_dof * ora_kB() * T + mean) / (3.0 * V);
+    *err = n > 1 ? sqrt(ss / (n - 1)) / sqrt((double)n) / (3.0 * V) : 0.0;
+}
+
 /* ------------------------------------------------------------------ Philox */
 /* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror & Shaw, SC'11):
  * ten rounds of two 32x32->64 multiplications with the round keys bumped by
@@ -577,6 +594,17 @@ void ora_normals(uint64_t seed, uint32_t replica, uint32_t stream, uint32_t atom
     z[0] = r0 * cos(two_pi * u[1]);
     z[1] = r0 * sin(two_pi * u[1]);
     z[2] = r1 * cos(two_pi * u[3]);
+}
+
+void ora_philox_many(int n, const uint32_t* ctr, const uint32_t key[2], uint32_t* out)
+{
+    for (int i = 0; i < n; i++) ora_philox4x32_10(ctr + 4 * (size_t)i, key, out + 4 * (size_t)i);
+}
+
+void ora_normals_many(uint64_t seed, uint32_t replica, uint32_t stream, uint64_t step, int n,
+                      double* z)
+{
+    for (int a = 0; a < n; a++) ora_normals(seed, replica, stream, (uint32_t)a, step, z + 3 * (size_t)a);
 }
 
 /* ------------------------------------------------------------ dynamics */

@@ -120,10 +120,19 @@ void ora_spring(const double* x, const double* x0, int n, double k, double* f,
 
 double ora_lambda_fl(int fn, double tau);
 double ora_lambda_rs(double lambda_f, double tau);
+/* lambda in force at the start of step s of md's four-phase schedule */
+double ora_sched_lambda(const ora_md* md, long s);
+/* P = (N_dof k_B T + <W>) / (3V) from n virial samples W, and its standard error */
+void ora_pressure(int n_dof, double T, double V, const double* W, int n, double* P, double* err);
 
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void ora_normals(uint64_t seed, uint32_t replica, uint32_t stream, uint32_t atom,
                  uint64_t step, double z[3]);
+/* The same, one call for many: out[4 i ..] = block of ctr[4 i ..] (one key);
+ * z[3 a ..] = normals of atoms a = 0 .. n-1 at one (seed, replica, stream, step). */
+void ora_philox_many(int n, const uint32_t* ctr, const uint32_t key[2], uint32_t* out);
+void ora_normals_many(uint64_t seed, uint32_t replica, uint32_t stream, uint64_t step, int n,
+                      double* z);
 
 int ora_init_velocities(const ora_md* md, int n, double* v);
 
