@@ -65,16 +65,23 @@ static __device__ __align__(256) unsigned char g_scratch[NE_NOALLOC_SCRATCH_BYTE
 std::mutex g_mu;
 unsigned char* g_addr[256] = {};
 
-// Device address of the scratch on the current device, looked up once per
-// device (with that device current).
-cudaError_t scratch_address(unsigned char** out)
+// Device address of the scratch on the current device (with that device
+// current).  Looked up again on every call made outside a stream capture --
+// a cudaDeviceReset reloads the module, and the array may then sit at another
+// address -- and kept per device for calls made while `st` is capturing,
+// where the last address looked up is used.
+cudaError_t scratch_address(cudaStream_t st, unsigned char** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    bool capturing = true;  // an error of the query counts as capturing
+    if (cudaStreamIsCapturing(st, &cap) == cudaSuccess) capturing = cap != cudaStreamCaptureStatusNone;
+    else (void)cudaGetLastError();
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    if (!capturing || !g_addr[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) return e;
@@ -132,13 +139,18 @@ extern "C" ne_status ne_eam_energy_forces_noalloc(const ne_eam_params* eam, ne_p
     if (!eam || !x_dev || !box || n < 2 || (!f_dev && !e_dev)) return NE_EINVAL;
     if (prec != NE_FP64 && prec != NE_MIXED) return NE_EINVAL;
     if (eam->n_knots < 4 || !(eam->r_c > 0) || !(eam->rho_max > 0) || !(eam->r_s < eam->r_c)) return NE_EINVAL;
+    // the potential is built from the analytic parameters alone: placeholders
+    // (NaN, as a file-loaded potential carries) are refused, not tabulated
+    if (!std::isfinite(eam->A) || !std::isfinite(eam->alpha) || !std::isfinite(eam->beta) ||
+        !std::isfinite(eam->B) || !(eam->r_e > 0) || !std::isfinite(eam->r_c) || !std::isfinite(eam->rho_max))
+        return NE_EINVAL;
     if (n > NE_NOALLOC_MAX_ATOMS || eam->n_knots > NE_NOALLOC_MAX_KNOTS) return NE_ENOMEM;
     const double rc = eam->r_c;
     for (int d = 0; d < 3; ++d)
         if (!(box[d] > 2.0 * rc)) return NE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char* base = nullptr;
-    if (scratch_address(&base) != cudaSuccess) return NE_ECUDA;
+    if (scratch_address(st, &base) != cudaSuccess) return NE_ECUDA;
 
     // ---- one replica: host-side description on the stack
     RepDev R{};

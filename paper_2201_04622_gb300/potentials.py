@@ -117,9 +117,34 @@ def theta_from_tables(tab, n_knots=5000):
 
 def load_eam(path, n_knots=5000):
     """(eam parameter dict for ne.eam_params / oracle.eam, theta, mass in u)
-    of a funcfl or single-element setfl file."""
+    of a funcfl or single-element setfl file.
+
+    The potential is theta; the dict carries the knot grid (r_c, rho_max,
+    n_knots) and NaN in place of the analytic parameters A, alpha, beta, B,
+    so a context made from it gives non-finite energies (NE_ENAN) until
+    ne_ctx_set_theta installs theta, and the allocation-free entry point,
+    which tabulates the analytic form only, refuses it (NE_EINVAL).
+    context_from_file does both steps at once."""
     tab = read_eam(path)
     r_c, rho_max, theta = theta_from_tables(tab, n_knots)
-    params = dict(A=0.0, alpha=0.0, beta=0.0, B=0.0, r_e=1.0, r_s=0.5 * r_c, r_c=r_c, rho_max=rho_max,
+    nan = float("nan")
+    params = dict(A=nan, alpha=nan, beta=nan, B=nan, r_e=1.0, r_s=0.5 * r_c, r_c=r_c, rho_max=rho_max,
                   n_knots=n_knots)
     return params, theta, tab["mass_amu"]
+
+
+def context_from_file(path, max_atoms, max_replicas=1, n_knots=5000, device="cuda"):
+    """A library context holding the potential of a funcfl or single-element
+    setfl file: ne_ctx_create on the file's knot grid, then ne_ctx_set_theta
+    with its knots.  Returns (ctx, mass in u)."""
+    import torch
+    from . import ne
+    params, theta, mass = load_eam(path, n_knots)
+    ctx = ne.ne_ctx_create(ne.eam_params(**params), max_atoms, max_replicas)
+    try:
+        ne.ne_ctx_set_theta(ctx, torch.tensor(theta.reshape(-1), dtype=torch.float64, device=device))
+        torch.cuda.synchronize()
+    except Exception:
+        ne.ne_ctx_destroy(ctx)
+        raise
+    return ctx, mass

@@ -139,3 +139,58 @@ def test_batched_entry_points_reject_an_empty_batch_without_a_gpu():
         # the replica count: argument 2 of the md-array entry points, 3 of the crystal runner's
         args[3 if name.startswith("ne_crystal") else 2] = 0
         assert f(*args) == ne.NE_EINVAL, name
+
+
+def test_noalloc_rejections_before_any_device_work():
+    """Every documented refusal of ne_eam_energy_forces_noalloc (limits
+    NE_NOALLOC_MAX_ATOMS = 2048, NE_NOALLOC_MAX_KNOTS = 5000) returns before
+    the call touches the device (the pointers below are never dereferenced):
+    sizes beyond the fixed scratch (NE_ENOMEM), boxes of edge <= 2 r_c, an
+    unknown precision, null buffers and non-finite analytic parameters (the
+    NaN placeholders of a file-loaded potential) (NE_EINVAL)."""
+    L = ne.load()
+    fake = C.c_void_p(256)  # stands for a device buffer; not dereferenced
+    box = (C.c_double * 3)(30.0, 30.0, 30.0)
+    small = (C.c_double * 3)(30.0, 30.0, 2.0 * W.EAM_FE_LIKE["r_c"])
+
+    def call(eam=None, prec=ne.NE_FP64, x=fake, n=128, bx=box, f=fake, e=fake):
+        e_ = ne.eam_params(**W.EAM_FE_LIKE) if eam is None else eam
+        return L.ne_eam_energy_forces_noalloc(C.byref(e_), prec, x, n, bx, f, e, None)
+
+    assert call(n=2048 + 1) == ne.NE_ENOMEM
+    big = dict(W.EAM_FE_LIKE, n_knots=5000 + 1)
+    assert call(eam=ne.eam_params(**big)) == ne.NE_ENOMEM
+    assert call(bx=small) == ne.NE_EINVAL
+    assert call(prec=7) == ne.NE_EINVAL
+    assert call(x=None) == ne.NE_EINVAL
+    assert call(f=None, e=None) == ne.NE_EINVAL
+    assert call(n=1) == ne.NE_EINVAL
+    for key in ("A", "alpha", "beta", "B"):
+        assert call(eam=ne.eam_params(**dict(W.EAM_FE_LIKE, **{key: float("nan")}))) == ne.NE_EINVAL, key
+
+
+
+@pytest.mark.parametrize("path,fn", [(ne.NE_PATH_FL, 2), (ne.NE_PATH_FL, 1), (ne.NE_PATH_RS, 2)])
+def test_lambda_schedule_matches_oracle(path, fn):
+    """ne_lambda (the schedule every run uses) against the oracle's schedule
+    at every step of a small four-phase run, and its range check."""
+    t_eq, t_s = 5, 13
+    kw = dict(path=path, lambda_fn=fn, t_eq=t_eq, t_s=t_s, lambda_f=0.0625)
+    md = ne.md_params(mass=1.0, **kw)
+    mo = O.md(mass=1.0, **kw)
+    for s in range(2 * t_eq + 2 * t_s + 1):
+        assert ne.ne_lambda(md, s) == pytest.approx(O.sched_lambda(mo, s), abs=1e-13), s
+    for bad in (-1, 2 * t_eq + 2 * t_s + 1):
+        with pytest.raises(ne.NeError, match="NE_EINVAL"):
+            ne.ne_lambda(md, bad)
+
+
+def test_pressure_matches_oracle():
+    """ne_pressure (P = (N_dof k_B T + <W>)/(3V) and its standard error)
+    against the oracle's, on virial samples of either sign."""
+    rng = np.random.default_rng(5)
+    for n_dof, T, V, w in [(381, 1400.0, 2364.5, rng.normal(-40.0, 5.0, 50)), (5997, 300.0, 23645.0, [12.5]),
+                           (0, 0.0, 10.0, [1.0, -3.0])]:
+        P, se = ne.ne_pressure(n_dof, T, V, w)
+        Po, seo = O.pressure(n_dof, T, V, w)
+        assert P == pytest.approx(Po, rel=1e-13, abs=1e-18) and se == pytest.approx(seo, rel=1e-12, abs=1e-18)

@@ -393,6 +393,36 @@ def test_msd_fit_matches_oracle(ctx, pot):
     assert k == pytest.approx(k_o, rel=1e-9)
 
 
+def test_msd_fit_batched_matches_oracle_per_replica(ctx, pot):
+    """Eq. msd for three replicas of different lattice, size and temperature
+    in one batched call (FP64): each replica's msd and k = 3 k_B T_r / msd_r
+    equal the oracle's fit of that replica alone; the mixed path agrees to
+    the FP32 force rounding."""
+    p, th = pot
+    reps = [(O.BCC, 4, 300.0, 3, 0), (O.FCC, 4, 800.0, 4, 1), (O.BCC, 5, 1200.0, 5, 2)]
+    x0s, v0s, offs, boxes, mos, mgs = [], [], [0], [], [], []
+    for lat, n, Tk, seed, rid in reps:
+        x0, box = crystal(lat, n)
+        mo, mg = md_pair(T=Tk, seed=seed, replica=rid)
+        x0s.append(x0)
+        v0s.append(O.init_velocities(mo, len(x0)))
+        offs.append(offs[-1] + len(x0))
+        boxes.append(box)
+        mos.append(mo)
+        mgs.append(mg)
+    want = [O.msd_fit(p, th, mo, x0, v0, x0, box, 20, 10, 5)
+            for mo, x0, v0, box in zip(mos, x0s, v0s, boxes)]
+    for prec, tol in [(ne.NE_FP64, 1e-9), (ne.NE_MIXED, 1e-4)]:
+        for m in mgs:
+            m.prec = prec
+        xs = T(np.concatenate(x0s))
+        msd, k = ne.ne_msd_fit_batched(ctx, mgs, offs, xs, T(np.concatenate(v0s)), T(np.concatenate(x0s)),
+                                       boxes, 20, 10, 5)
+        for r, (msd_o, k_o) in enumerate(want):
+            assert msd[r] == pytest.approx(msd_o, rel=tol), (prec, r)
+            assert k[r] == pytest.approx(k_o, rel=tol), (prec, r)
+
+
 # ---------------------------------------------------------------- backward
 # Mixed precision: the knot weights depend on u = r/h - k; an FP32 pair
 # distance carries ~2^-24 r ~ 3e-7 A of rounding against h = r_c/4999 ~

@@ -323,6 +323,64 @@ def test_rs_lambda_pins():
     assert np.allclose(np.diff(Ts), (g["T_end"] - g["T0"]) / 20, rtol=1e-12)
 
 
+def test_schedule_lambda_pins():
+    """The four phases of Sec. III.B / III.C: lambda_i for the first t_eq
+    steps, the switch over t_s steps (tau = elapsed steps / t_s), lambda_f for
+    t_eq steps, the switch back (FL: 1 - lambda(tau); RS: lambda(1 - tau)),
+    lambda_i at the end; the work weights of a switch telescope to
+    lambda_f - lambda_i."""
+    t_eq, t_s = 7, 10
+    fl = O.md(mass=mass(), path=O.PATH_FL, lambda_fn=2, t_eq=t_eq, t_s=t_s)
+    lam = [O.sched_lambda(fl, s) for s in range(2 * t_eq + 2 * t_s + 1)]
+    assert lam[:t_eq + 1] == [0.0] * (t_eq + 1)
+    assert lam[t_eq + t_s:2 * t_eq + t_s + 1] == [1.0] * (t_eq + 1)
+    assert lam[-1] == 0.0
+    assert lam[t_eq + 5] == pytest.approx(0.5, abs=1e-15)
+    for q in range(t_s + 1):
+        assert lam[t_eq + q] == pytest.approx(float(Fraction(q, t_s) ** 5 * sum(
+            c * Fraction(q, t_s) ** (4 - i) for i, c in enumerate(GOLDEN["fl_function2_coefficients"]["value"]))),
+            abs=1e-14)
+        assert lam[2 * t_eq + t_s + q] == pytest.approx(1.0 - lam[t_eq + q], abs=1e-14)
+    assert sum(lam[s + 1] - lam[s] for s in range(t_eq, t_eq + t_s)) == pytest.approx(1.0, abs=1e-15)
+    g = GOLDEN["rs_endpoints"]
+    rs = O.md(mass=mass(), path=O.PATH_RS, lambda_f=g["lambda_f"], t_eq=t_eq, t_s=t_s)
+    lam = [O.sched_lambda(rs, s) for s in range(2 * t_eq + 2 * t_s + 1)]
+    assert lam[:t_eq + 1] == [1.0] * (t_eq + 1) and lam[-1] == 1.0
+    assert lam[t_eq + t_s] == pytest.approx(g["lambda_f"], rel=1e-15)
+    Ts = [g["T0"] / lam[t_eq + q] for q in range(t_s + 1)]  # T = T0 / lambda, linear in time
+    assert np.allclose(np.diff(Ts), (g["T_end"] - g["T0"]) / t_s, rtol=1e-12)
+    for q in range(t_s + 1):
+        assert lam[2 * t_eq + t_s + q] == pytest.approx(lam[t_eq + t_s - q], rel=1e-15)
+
+
+def test_pressure_pins(pot):
+    """P = (N_dof k_B T + <W>) / (3V) (Sec. III.A's zero-pressure condition):
+    with W = 0 the ideal gas of the thermostat's 3N - 3 degrees of freedom,
+    P V = (N - 1) k_B T (k_B from CODATA); at 0 K the static lattice's
+    pressure equals -dE/dV by central differences in a, vanishing at the
+    fitted a = 2.87 A; the error is the standard error of the samples."""
+    p, th = pot
+    kB = sc.k / sc.e
+    P, err = O.pressure(3 * 128 - 3, 300.0, 1234.5, [0.0, 0.0, 0.0])
+    assert P * 1234.5 == pytest.approx(127 * kB * 300.0, rel=1e-9) and err == 0.0
+    n = 5
+    for a in (2.84, 2.87, 2.90):
+        x0, box = O.create_crystal(O.BCC, a, n, n, n)
+        P0, _ = O.pressure(3 * len(x0) - 3, 0.0, float(np.prod(box)), [O.eam_virial(p, th, x0, box)])
+        h = 1e-5
+        E = {}
+        for s in (-1, 1):
+            xs, bs = O.create_crystal(O.BCC, a + s * h, n, n, n)
+            E[s] = O.eam_energy_forces(p, th, xs, bs)[0]
+        dEdV = (E[1] - E[-1]) / ((n * (a + h)) ** 3 - (n * (a - h)) ** 3)
+        assert P0 == pytest.approx(-dEdV, rel=1e-6, abs=1e-9)
+        if a == 2.87:
+            assert abs(P0) < 1e-9
+    w = np.array([1.0, 2.0, 4.0, 7.0])
+    P, err = O.pressure(30, 100.0, 50.0, w)
+    assert err == pytest.approx(w.std(ddof=1) / 2.0 / 150.0, rel=1e-14)
+
+
 # ------------------------------------------------------------------ Philox
 def test_philox_normals_statistics():
     z = np.array([O.normals(7, 3, O.STREAM_FL, a, s) for a in range(200) for s in range(150)])

@@ -84,3 +84,20 @@ def test_malformed_and_multi_element_files_are_rejected(tmp_path):
     two.write_text("c1\nc2\nc3\n2 Fe Ni\n10 0.1 10 0.5 5.0\n" + "0 " * 100 + "\n")
     with pytest.raises(ValueError, match="single-element"):
         P.read_eam(str(two))
+
+
+def test_file_potential_placeholders_are_refused_by_the_analytic_entry_point(tmp_path):
+    """A potential loaded from a file carries NaN analytic parameters, so the
+    allocation-free entry point (it tabulates the analytic form only) refuses
+    it before touching the device (the pointers are never dereferenced)."""
+    import ctypes as C
+    from paper_2201_04622_gb300 import ne
+    path = tmp_path / "fe.eam"
+    write_funcfl(str(path), nr=2000, nrho=2000)
+    params, _, _ = P.load_eam(str(path))
+    assert all(np.isnan(params[k]) for k in ("A", "alpha", "beta", "B"))
+    L = ne.load()
+    box = (C.c_double * 3)(30.0, 30.0, 30.0)
+    e_ = ne.eam_params(**params)
+    assert L.ne_eam_energy_forces_noalloc(C.byref(e_), ne.NE_FP64, C.c_void_p(256), 128, box,
+                                          C.c_void_p(256), C.c_void_p(256), None) == ne.NE_EINVAL
