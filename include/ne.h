@@ -101,7 +101,27 @@ typedef struct {
     double P0;         /* eV / A^3, >= 0 */
     double beta_T;     /* coupling compressibility, A^3 / eV, > 0 */
     double tau_p;      /* coupling time, ps, > 0 */
+    /* Several species (Sec. V: one Einstein spring per species, k_A and k_B
+     * for an A-B solid).  n_species 0 or 1: every atom has `mass` and
+     * `k_spring` (the fields below are ignored).  2 .. NE_MAX_SPECIES: atom i
+     * of the replica has mass mass_s[species_dev[i]] and spring
+     * k_s[species_dev[i]] (mass > 0, spring >= 0); species_dev is device
+     * memory, one byte per atom of the replica, in its atom order, owned by
+     * the caller (an index out of range is reported as NE_EINVAL at the end
+     * of the call).  The EAM is the same for every species (an isotope-like
+     * mixture).  The fixed centre of mass is the mass-weighted one: the
+     * forces lose m_i sum_j F_j / M and the velocity increments of the
+     * thermostat, sqrt((1 - c1^2) k_B T / m_i) xi_i, their centre-of-mass
+     * velocity sum_j m_j dv_j / M.  With one species both reduce to the plain
+     * means.  Supported by the multi-kernel runs, ne_init_velocities,
+     * ne_msd_fit_species and the crystal runner. */
+    int n_species;
+    double mass_s[8];  /* eV ps^2 / A^2 */
+    double k_s[8];     /* eV / A^2 */
+    const unsigned char* species_dev;
 } ne_md_params;
+
+#define NE_MAX_SPECIES 8
 
 /* ------------------------------------------------------------- context */
 /* Create a context for up to max_atoms atoms in up to max_replicas replicas.
@@ -422,13 +442,26 @@ ne_status ne_msd_fit(ne_ctx* ctx, const ne_md_params* md, double* x_dev, double*
                      long long n_samples, int stride, double* msd_host, double* k_host,
                      void* stream);
 
+/* Eq. msd per species (Sec. V: one spring per species), for a replica with
+ * species tables (md->n_species >= 2): as ne_msd_fit, the samples taken
+ * about the mass-weighted centre, msd_s = mean over samples of
+ * (1/N_s) sum over the atoms of species s of |(r_i - r0_i) - (R - R0)|^2,
+ * R the mass-weighted centre, and k_s = 3 k_B T / msd_s.  msd_s_host and
+ * k_s_host: md->n_species doubles each (either may be NULL; a species with
+ * no atom gets 0). */
+ne_status ne_msd_fit_species(ne_ctx* ctx, const ne_md_params* md, double* x_dev, double* v_dev,
+                             const double* x0_dev, int n, const double box[3], long long n_eq,
+                             long long n_samples, int stride, double* msd_s_host, double* k_s_host,
+                             void* stream);
+
 /* ne_msd_fit for a batch of replicas at once, each at its own size and
  * temperature (Sec. III.A: the spring of a run comes from the msd at that
  * run's N and T -- e.g. one spring per replica of an uneven batch drawn over
  * 300-1600 K).  md[n_rep]: per-replica T, seed, replica, mass; dt, damp,
  * fix_cm and prec shared.  offsets_host[n_rep+1], x_dev, v_dev, x0_dev and
  * boxes_host as in ne_switch_run_batched.  msd_host, k_host: n_rep doubles
- * each (either may be NULL), k_r = 3 k_B T_r / msd_r. */
+ * each (either may be NULL), k_r = 3 k_B T_r / msd_r.  One species per replica
+ * (n_species >= 2: NE_EINVAL; see ne_msd_fit_species). */
 ne_status ne_msd_fit_batched(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* offsets_host,
                              double* x_dev, double* v_dev, const double* x0_dev,
                              const double* boxes_host, long long n_eq, long long n_samples, int stride,

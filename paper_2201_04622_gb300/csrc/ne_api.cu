@@ -14,6 +14,8 @@
 #include "ne_cluster.cuh"
 #include "ne_internal.cuh"
 
+static_assert(NE_MAX_SPECIES == NE_MAX_SPECIES_DEV, "species table size");
+
 namespace {
 
 const double kB = 8.617333262e-5;      // eV/K
@@ -192,6 +194,36 @@ struct RunArgs {
     double* rho;
 };
 
+// Species tables of one replica (Sec. V): per-species mass, spring, noise
+// amplitude and half-step factor, the atoms' species read back and checked
+// (every index in range) and the total mass formed on the host.
+ne_status species_tables(ne_ctx* ctx, const ne_md_params& m, int n, double c1, RepDev& R, cudaStream_t st)
+{
+    if (m.n_species < 2 || m.n_species > NE_MAX_SPECIES || !m.species_dev)
+        return fail(ctx, NE_EINVAL, "species: 2 .. NE_MAX_SPECIES species and a device species array");
+    for (int q = 0; q < m.n_species; ++q)
+        if (!(m.mass_s[q] > 0) || !(m.k_s[q] >= 0))
+            return fail(ctx, NE_EINVAL, "species: masses must be positive and springs non-negative");
+    std::vector<unsigned char> sp(n);
+    NE_CU(cudaMemcpyAsync(sp.data(), m.species_dev, (size_t)n, cudaMemcpyDeviceToHost, st));
+    NE_CU(cudaStreamSynchronize(st));
+    double M = 0.0;
+    for (int a = 0; a < n; ++a) {
+        if (sp[a] >= m.n_species) return fail(ctx, NE_EINVAL, "species index out of range");
+        M += m.mass_s[sp[a]];
+    }
+    R.nsp = m.n_species;
+    R.sp = m.species_dev;
+    R.M = M;
+    for (int q = 0; q < m.n_species; ++q) {
+        R.ms[q] = m.mass_s[q];
+        R.ks[q] = m.k_s[q];
+        R.c2s[q] = std::sqrt((1.0 - c1 * c1) * kB * m.T / m.mass_s[q]);
+        R.hdts[q] = 0.5 * m.dt / m.mass_s[q];
+    }
+    return NE_OK;
+}
+
 ne_status setup_batch(ne_ctx* ctx, int n_rep, const int* off, const double* boxes,
                       const ne_md_params* md, int md_stride, double skin_override, DevBatch& B,
                       const RunArgs& a, cudaStream_t st, bool geometry = true)
@@ -254,8 +286,16 @@ ne_status setup_batch(ne_ctx* ctx, int n_rep, const int* off, const double* boxe
         R.P0 = m.P0;
         R.mp = m.npt ? m.beta_T / m.tau_p : 0.0;
         npt_any |= m.npt;
+        if (m.n_species >= 2) {
+            ne_status sst = species_tables(ctx, m, n, R.c1, R, st);
+            if (sst) return sst;
+        } else if (m.n_species < 0 || m.n_species > NE_MAX_SPECIES) {
+            return fail(ctx, NE_EINVAL, "n_species must be 0 .. NE_MAX_SPECIES");
+        }
     }
     ctx->last_nrep = n_rep;
+    int species_all = 1;
+    for (int r = 0; r < n_rep; ++r) species_all &= ctx->rep_h[r].nsp >= 2;
     const int n_tiles = (int)ctx->tile_rep_h.size();
     if (n_tiles > ctx->tiles_cap) return fail(ctx, NE_ENOMEM, "tile capacity exceeded");
     if (cells > ctx->cells_cap) return fail(ctx, NE_ENOMEM, "cell capacity exceeded");
@@ -308,6 +348,7 @@ ne_status setup_batch(ne_ctx* ctx, int n_rep, const int* off, const double* boxe
     B.status = ctx->status;
     B.tab = ctx->tab;
     B.npt_any = npt_any;
+    B.species_any = species_all;
     return NE_OK;
 }
 
@@ -1240,6 +1281,24 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
         X.seed = m.seed;
         X.replica = m.replica;
         if (m.replica >= (1u << 28)) return fail(ctx, NE_EINVAL, "replica id must be < 2^28");
+        if (m.n_species >= 2) {
+            // one spring and mass per species (Sec. V): the tables of the
+            // multi-kernel path in FP32, the species checked on the host
+            RepDev R{};
+            ne_status sst = species_tables(ctx, m, X.n, c1, R, st);
+            if (sst) return sst;
+            X.nsp = R.nsp;
+            X.sp = R.sp;
+            X.invM = (float)(1.0 / R.M);
+            for (int q = 0; q < R.nsp; ++q) {
+                X.kfs[q] = (float)R.ks[q];
+                X.hdts[q] = (float)R.hdts[q];
+                X.c2fs[q] = (float)R.c2s[q];
+                X.mfs[q] = (float)R.ms[q];
+            }
+        } else if (m.n_species < 0 || m.n_species > NE_MAX_SPECIES) {
+            return fail(ctx, NE_EINVAL, "n_species must be 0 .. NE_MAX_SPECIES");
+        }
         // stencil: sites within r_c + 2D of each basis site, sorted by distance,
         // D = 2 A.  In a small box r_c + 2D can pass L/2 and the stencil then
         // holds two periodic images of some sites; two images are L > 2 r_c
@@ -1460,7 +1519,11 @@ static ne_status crystal_segment_impl(ne_ctx* ctx, const ne_md_params* md, const
     if (step_begin < 0 || n_steps < 0 || step_begin + n_steps > S_total)
         return fail(ctx, NE_EINVAL, "step range outside the schedule");
     cudaStream_t st = (cudaStream_t)stream;
-    if (!ctx->plan.valid || ctx->plan.key != plan_key(ctx, md, cr, n_rep)) {
+    // a batch with species tables is planned on every call: its species
+    // arrays are read back and checked each time
+    bool species = false;
+    for (int r = 0; r < n_rep; ++r) species = species || md[r].n_species >= 2;
+    if (species || !ctx->plan.valid || ctx->plan.key != plan_key(ctx, md, cr, n_rep)) {
         s = build_plan(ctx, md, cr, n_rep, st);
         if (s) return s;
     }
@@ -1537,6 +1600,7 @@ ne_status ne_msd_fit_batched(ne_ctx* ctx, const ne_md_params* md, int n_rep, con
         ne_status s = check_md(ctx, &md[r]);
         if (s) return s;
         if (md[r].npt) return fail(ctx, NE_EINVAL, "the barostat runs in the switching runs (ne_switch_run_segment, ne_rs_run)");
+        if (md[r].n_species >= 2) return fail(ctx, NE_EINVAL, "several species: use ne_msd_fit_species");
         if (md[r].dt != md[0].dt || md[r].damp != md[0].damp || md[r].fix_cm != md[0].fix_cm ||
             md[r].prec != md[0].prec)
             return fail(ctx, NE_EINVAL, "replicas must share dt, damp, fix_cm and precision");
@@ -1550,7 +1614,7 @@ ne_status ne_msd_fit_batched(ne_ctx* ctx, const ne_md_params* md, int n_rep, con
     a.x0 = x0_dev;
     a.W = ctx->W;
     DevBatch B;
-    ne_status s = setup_batch(ctx, n_rep, offsets_host, boxes_host, md, 0, -1.0, B, a, st);
+    ne_status s = setup_batch(ctx, n_rep, offsets_host, boxes_host, md, 1, -1.0, B, a, st);
     if (s) return s;
     Sched S = make_sched(md[0]);
     S.kind = SCHED_FIXED;
@@ -1570,6 +1634,55 @@ ne_status ne_msd_fit_batched(ne_ctx* ctx, const ne_md_params* md, int n_rep, con
         const double msd = sum[r] / (double)n_samples;
         if (msd_host) msd_host[r] = msd;
         if (k_host) k_host[r] = 3.0 * kB * md[r].T / msd;
+    }
+    return NE_OK;
+}
+
+ne_status ne_msd_fit_species(ne_ctx* ctx, const ne_md_params* md, double* x_dev, double* v_dev,
+                             const double* x0_dev, int n, const double box[3], long long n_eq,
+                             long long n_samples, int stride, double* msd_s_host, double* k_s_host, void* stream)
+{
+    if (!ctx || !md || !x_dev || !v_dev || !x0_dev || !box || n < 2 || n_eq < 0 || n_samples < 1 || stride < 1)
+        return NE_EINVAL;
+    ne_status s = check_md(ctx, md);
+    if (s) return s;
+    if (md->n_species < 2) return fail(ctx, NE_EINVAL, "ne_msd_fit_species needs species tables (n_species >= 2)");
+    if (md->npt) return fail(ctx, NE_EINVAL, "the barostat runs in the switching runs (ne_switch_run_segment, ne_rs_run)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int off[2] = {0, n};
+    RunArgs a{};
+    a.x = x_dev;
+    a.v = v_dev;
+    a.x0 = x0_dev;
+    a.W = ctx->W;
+    DevBatch B;
+    s = setup_batch(ctx, 1, off, box, md, 0, -1.0, B, a, st);
+    if (s) return s;
+    const RepDev& R = ctx->rep_h[0];
+    Sched S = make_sched(*md);
+    S.kind = SCHED_FIXED;
+    S.path = NE_PATH_FL;
+    S.lam_a = S.lam_b = 0.0;
+    S.s0 = -1;
+    S.stream = STREAM_MSD;
+    double* acc = ctx->scratch;  // one msd sum per species
+    NE_CU(cudaMemsetAsync(acc, 0, sizeof(double) * NE_MAX_SPECIES, st));
+    s = run_steps(ctx, B, S, md->prec == NE_MIXED, 0, n_eq + n_samples * stride, st, acc, n_eq, stride);
+    if (s) return s;
+    double sum[NE_MAX_SPECIES] = {};
+    NE_CU(cudaMemcpyAsync(sum, acc, sizeof(sum), cudaMemcpyDeviceToHost, st));
+    s = finish(ctx, st);
+    if (s) return s;
+    std::vector<int> cnt(NE_MAX_SPECIES, 0);
+    {
+        std::vector<unsigned char> sp(n);
+        NE_CU(cudaMemcpy(sp.data(), md->species_dev, (size_t)n, cudaMemcpyDeviceToHost));
+        for (int q = 0; q < n; ++q) ++cnt[sp[q]];
+    }
+    for (int q = 0; q < R.nsp; ++q) {
+        const double msd = cnt[q] ? sum[q] / (double)n_samples : 0.0;
+        if (msd_s_host) msd_s_host[q] = msd;
+        if (k_s_host) k_s_host[q] = msd > 0 ? 3.0 * kB * md->T / msd : 0.0;
     }
     return NE_OK;
 }

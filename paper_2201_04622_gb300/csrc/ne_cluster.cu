@@ -332,8 +332,19 @@ __global__ void __launch_bounds__(THREADS, 1)
     long long xr[3] = {0, 0, 0};
     float v[3] = {0, 0, 0}, u[3] = {0, 0, 0}, xi[3] = {0, 0, 0};
     int bad = 0;
-    const float kf = reps[rep].kf;
+    // the owned atom's spring, half-step factor and noise amplitude, and its
+    // weights in the centre-of-mass sums: with species tables the spring sum
+    // is sum_j k_j u_j and the noise sum sum_j m_j c2_j xi_j, and atom i takes
+    // m_i / M of the first and 1 / M of the second (the mass-weighted
+    // constraint); with one species the plain sums and means
+    // (read from the replica table where they are used, so that they hold
+    // no registers through the pair passes)
+    const bool spc = reps[rep].nsp >= 2;
+    const XRep& R_ = reps[rep];
+    auto spq = [&]() { return spc && own ? (int)R_.sp[ta] : 0; };
+    auto k_of = [&](int q) { return spc ? R_.kfs[q] : R_.kf; };
     {
+        const float kf = k_of(spq());
         dfl pd[ND_] = {};
         float pf[NF_] = {};
         float um = 0.f;
@@ -351,9 +362,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                          xi);
             const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
             pd[P_UE] = {0.5f * kf * u2, 0.f};
+            const float wxi = spc ? R_.mfs[spq()] * R_.c2fs[spq()] : 1.f;
             for (int c = 0; c < 3; ++c) {
-                pf[P_UX - ND_ + c] = u[c];
-                pf[P_XX - ND_ + c] = xi[c];
+                pf[P_UX - ND_ + c] = spc ? kf * u[c] : u[c];
+                pf[P_XX - ND_ + c] = spc ? wxi * xi[c] : xi[c];
             }
             um = sqrtf(u2);
         }
@@ -364,6 +376,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     unsigned n_cand = 0, n_pair = 0;  // work counters (stencil entries visited, pairs < r_c)
     const float rc2 = tab.rc2f, rmin2 = tab.rmin2f, inv_h = tab.inv_h_rf;
     const int nk = tab.nk;
+    // first interval above both the shared-memory window's start and r_min:
+    // pairs below it take the checked path of pass 1
+    const int kchk = max(k_lo, (int)(sqrtf(rmin2) * inv_h) + 2);
     const float dt = (float)S.dt;
     const float rho_maxf = (float)tab.rho_max;
     const float ihr_hi = (float)tab.inv_h_rho, ihr_lo = (float)(tab.inv_h_rho - (double)ihr_hi);
@@ -438,8 +453,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             // bins of margin against rounding of the bin index)
             const float c = sqrtf(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + umax;
             const int K = valid ? (int)s_K[skb + min(NKT - 1, (int)(c * inv_dK) + 2)] : 0;
-            // rho accumulated as a double-float (FP64-class precision from
-            // FP32 arithmetic)
+            // rho as an unnormalised double-float: the running FP32 sum rh and
+            // the exact rounding error of each addition (TwoSum) summed in rl
+            float rh = 0.f, rl = 0.f;
+            unsigned char* slp = s_sl + lane * SLOTS + slot;  // this thread's short list, stride TPA * SLOTS
 #pragma unroll 8
             for (int k = lane; k < K; k += 2) {
                 const float4 e = s_sv[stb + k];
@@ -449,16 +466,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 < rc2) {
-                    if (r2 < rmin2) bad |= ST_ERANGE;
-                    const float ir = rsqrtf(r2);
-                    const float t = r2 * ir * inv_h;  // r / h >= 0
+                    const float irh = rsqrtf(r2) * inv_h;  // 1 / (r h)
+                    const float t = r2 * irh;              // r / h >= 0
                     const int kk = min((int)t, nk - 2);
                     const float w = t - (float)kk;
-                    // intervals below the shared-memory window (r < ~1 A at
-                    // these sizes) come from global memory; the warp votes, so
-                    // the common case is a plain shared-memory gather
+                    // intervals below kchk (r < ~1 A: the shared-memory window
+                    // starts there, and r_min lies below it) are rare: their
+                    // own branch checks r_min and reads global memory
                     float4 c, g;
-                    if (__any_sync(__activemask(), kk < k_lo)) {
+                    if (kk < kchk) {
+                        if (r2 < rmin2) bad |= ST_ERANGE;
                         if (kk >= k_lo) {
                             c = s_tabP[kk - k_lo];
                             g = s_tabF[kk - k_lo];
@@ -470,24 +487,30 @@ __global__ void __launch_bounds__(THREADS, 1)
                         c = s_tabP[kk - k_lo];
                         g = s_tabF[kk - k_lo];
                     }
-                    rho = df_add(rho, {g.x + w * (g.y + w * (g.z + w * g.w)), 0.f});
+                    {
+                        const float fv = g.x + w * (g.y + w * (g.z + w * g.w));
+                        const float s_ = rh + fv, bp = s_ - rh;
+                        rl += (rh - (s_ - bp)) + (fv - bp);
+                        rh = s_;
+                    }
                     // phi and dphi/dw together (Horner with derivative)
                     float pv = fmaf(c.w, w, c.z), pd = c.w;
                     pd = fmaf(pd, w, pv);
                     pv = fmaf(pv, w, c.y);
                     pd = fmaf(pd, w, pv);
                     pv = fmaf(pv, w, c.x);
-                    const float sc = pd * (inv_h * ir);
+                    const float sc = pd * irh;
                     fx += sc * dx;
                     fy += sc * dy;
                     fz += sc * dz;
                     ep += pv;
                     // entries past the capacity overwrite the last one; the
                     // overflow is reported after the loop
-                    s_sl[(min(m, SLQ - 1) * TPA + lane) * SLOTS + slot] = (unsigned char)(k / TPA);
+                    slp[min(m, SLQ - 1) * (TPA * SLOTS)] = (unsigned char)(k / TPA);
                     ++m;
                 }
             }
+            rho = {rh, rl};
             n_cand += (K > lane) ? (unsigned)((K - lane + 1) / 2) : 0u;
             if (m > SLQ) bad |= ST_ENEIGH;
             m = min(m, SLQ);
@@ -528,12 +551,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const float4 uj = s_u[j];
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
-                const float ir = rsqrtf(r2);
-                const float t = r2 * ir * inv_h;
+                const float irh = rsqrtf(r2) * inv_h;
+                const float t = r2 * irh;
                 const int kk = min((int)t, nk - 2);
                 const float w = t - (float)kk;
                 const float4 g = kk >= k_lo ? s_tabF[kk - k_lo] : __ldg(&tab.pf32[2 * kk + 1]);
-                const float sc = (dFi + uj.w) * (g.y + w * (2.f * g.z + 3.f * w * g.w)) * (inv_h * ir);
+                const float sc = (dFi + uj.w) * (g.y + w * (2.f * g.z + 3.f * w * g.w)) * irh;
                 fx += sc * dx;
                 fy += sc * dy;
                 fz += sc * dz;
@@ -579,12 +602,20 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const float4 f1_ = s_f[threadIdx.x];
                 const float4 f = make_float4(fx + f1_.x, fy + f1_.y, fz + f1_.z, ep + f1_.w);
                 const float F0[3] = {f.x, f.y, f.z};
-                const float hdt = reps[rep].hdt_mf, c1 = reps[rep].c1f, c2 = reps[rep].c2f;
+                const int q = spq();
+                const float c1 = R_.c1f, kf = k_of(q);
+                const float hdt = spc ? R_.hdts[q] : R_.hdt_mf, c2 = spc ? R_.c2fs[q] : R_.c2f;
+                const float wcm = spc ? R_.mfs[q] * R_.invM : 0.f;
                 const float invN = 1.f / (float)n;
                 float mFE[3], mxi[3];
                 for (int c = 0; c < 3; ++c) {
-                    mFE[c] = S.fix_cm ? -kf * s_tot[T_UX + c] * invN : 0.f;
-                    mxi[c] = S.fix_cm ? s_tot[T_XX + c] * invN : 0.f;
+                    if (spc) {  // -m_i sum_j k_j u_j / M, and sum_j m_j c2_j xi_j / M
+                        mFE[c] = S.fix_cm ? -wcm * s_tot[T_UX + c] : 0.f;
+                        mxi[c] = S.fix_cm ? s_tot[T_XX + c] * reps[rep].invM : 0.f;
+                    } else {
+                        mFE[c] = S.fix_cm ? -kf * s_tot[T_UX + c] * invN : 0.f;
+                        mxi[c] = S.fix_cm ? s_tot[T_XX + c] * invN : 0.f;
+                    }
                 }
                 const float ls = (float)lam_tab[it], ln = (float)lam_tab[it + 1];
                 if (it > 0)
@@ -594,7 +625,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     for (int c = 0; c < 3; ++c) {
                         v[c] += hdt * blendf(S.path, ln, F0[c], -kf * u[c] - mFE[c]);
                         const float v1 = v[c];
-                        v[c] = c1 * v[c] + c2 * (xi[c] - mxi[c]);
+                        v[c] = spc ? c1 * v[c] + (c2 * xi[c] - mxi[c]) : c1 * v[c] + c2 * (xi[c] - mxi[c]);
                         const float dlt = 0.5f * dt * (v1 + v[c]);
                         if (!(fabsf(dlt) < 0.25f)) bad |= ST_ERANGE;  // > 250 A/ps at 1 fs, or NaN
                         xr[c] += (long long)__float2int_rn(dlt * 4294967296.f);
@@ -614,10 +645,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                     for (int r = 1; r < C; ++r) cluster.map_shared_rank(s_u, peer(r))[tsu] = uv;
                 }
                 const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+                const int q = spq();
+                const float kf = k_of(q), wxi = spc ? R_.mfs[q] * R_.c2fs[q] : 1.f;
                 pd[P_UE] = {0.5f * kf * u2, 0.f};
                 for (int c = 0; c < 3; ++c) {
-                    pf[P_UX - ND_ + c] = u[c];
-                    pf[P_XX - ND_ + c] = xi[c];
+                    pf[P_UX - ND_ + c] = spc ? kf * u[c] : u[c];
+                    pf[P_XX - ND_ + c] = spc ? wxi * xi[c] : xi[c];
                 }
                 un = sqrtf(u2);
                 for (int c = 0; c < 3; ++c)

@@ -19,6 +19,13 @@ struct XRep {
     unsigned long long seed;
     unsigned replica;
     int widx;             // index of the replica in the caller's arrays (work W)
+    // several species (Sec. V): nsp >= 2 -- atom a has species sp[a]
+    // (validated on the host) with spring kfs, half-step factor hdts, noise
+    // amplitude c2fs and mass mfs of its species; invM = 1 / total mass
+    int nsp;
+    const unsigned char* sp;
+    float invM;
+    float kfs[NE_MAX_SPECIES_DEV], hdts[NE_MAX_SPECIES_DEV], c2fs[NE_MAX_SPECIES_DEV], mfs[NE_MAX_SPECIES_DEV];
 };
 
 namespace ne {

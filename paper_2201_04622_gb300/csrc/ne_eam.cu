@@ -302,6 +302,13 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
                 v[5] = z[1];
                 v[6] = z[2];
             }
+            if (P.nsp) {  // the velocity increments' momentum: sum m_j c2_j xi_j
+                const int q = P.sp[a];
+                const double wq = P.ms[q] * P.c2s[q];
+                v[4] *= wq;
+                v[5] *= wq;
+                v[6] *= wq;
+            }
         }
     }
     constexpr int NQ = VIR ? 8 : 7;

@@ -27,6 +27,7 @@ struct __align__(32) ned4 {
 };
 
 #define NE_TILE 64
+#define NE_MAX_SPECIES_DEV 8  // species per replica (NE_MAX_SPECIES of the public header)
 #define NE_NMAX 256   // candidate neighbours per atom (r < r_c + skin)
 #define NE_SMAX 128   // neighbours per atom inside r_c
 #define NE_RMIN 0.2   // A: shorter pair distances are reported as NE_ERANGE (atoms may overlap at lambda -> 1)
@@ -63,6 +64,17 @@ struct RepDev {
     unsigned replica;
     int npt;         // isotropic barostat on (RS path)
     double P0, mp;   // target pressure, mobility beta_T / tau_p
+    // Several species (Sec. V): nsp = 0 -- every atom has m and k above;
+    // nsp >= 2 -- atom a has species sp[a] (validated on the host) with mass
+    // ms, spring ks, noise amplitude c2s and half-step factor hdts of its
+    // species; M is the replica's total mass.  With species tables the
+    // step kernel's sum PB_UX.. holds sum_j k_j u_j and pass 2's PA_XIX..
+    // holds sum_j m_j c2_j xi_j: the sums the mass-weighted centre-of-mass
+    // constraint needs.
+    int nsp;
+    const unsigned char* sp;
+    double M;
+    double ms[NE_MAX_SPECIES_DEV], ks[NE_MAX_SPECIES_DEV], c2s[NE_MAX_SPECIES_DEV], hdts[NE_MAX_SPECIES_DEV];
 };
 
 // Schedule of a run, shared by the replicas of one launch.
@@ -126,6 +138,7 @@ struct DevBatch {
     int* status;
     Tables tab;
     int npt_any;       // some replica has the barostat on
+    int species_any;   // every replica has species tables (msd sampling per species)
 };
 
 // ------------------------------------------------------------------ lambda

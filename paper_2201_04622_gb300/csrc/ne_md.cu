@@ -211,25 +211,38 @@ __global__ void __launch_bounds__(NE_TILE)
             F0[1] = B.f64[3 * i + 1];
             F0[2] = B.f64[3 * i + 2];
         }
+        // this atom's mass, spring, noise amplitude and half-step factor
+        // (one species, or its species' entries)
+        const int q = P.nsp ? (int)P.sp[a] : 0;
+        const double mi = P.nsp ? P.ms[q] : P.m, ki = P.nsp ? P.ks[q] : P.k;
+        const double c2i = P.nsp ? P.c2s[q] : P.c2, hdti = P.nsp ? P.hdts[q] : P.hdt_m;
         for (int c = 0; c < 3; ++c) {
-            mF0[c] = S.fix_cm ? T[TOT_F0X + c] * invN : 0.0;
-            mFE[c] = S.fix_cm ? -P.k * T[TOT_UX + c] * invN : 0.0;
+            if (P.nsp) {  // mass-weighted constraint: F_i -= m_i sum_j F_j / M
+                mF0[c] = S.fix_cm ? mi * T[TOT_F0X + c] / P.M : 0.0;
+                mFE[c] = S.fix_cm ? -mi * T[TOT_UX + c] / P.M : 0.0;  // TOT_UX: sum_j k_j u_j
+            } else {
+                mF0[c] = S.fix_cm ? T[TOT_F0X + c] * invN : 0.0;
+                mFE[c] = S.fix_cm ? -P.k * T[TOT_UX + c] * invN : 0.0;
+            }
         }
         if (do_close) {
             for (int c = 0; c < 3; ++c)
-                v[c] += P.hdt_m * blend(S.path, lam_s, F0[c] - mF0[c], -P.k * u[c] - mFE[c]);
+                v[c] += hdti * blend(S.path, lam_s, F0[c] - mF0[c], -ki * u[c] - mFE[c]);
         }
-        part[PB_KE] = 0.5 * P.m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        part[PB_KE] = 0.5 * mi * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         if (do_open) {
-            double xi[3];
+            // velocity increments of the thermostat: c2 (xi - mean xi) for one
+            // species; c2_i xi_i - sum_j m_j c2_j xi_j / M with species tables
+            double dv[3];
             for (int c = 0; c < 3; ++c) {
-                xi[c] = MIXED ? (double)B.xi32[3 * i + c] : B.xi64[3 * i + c];
-                if (S.fix_cm) xi[c] -= T[TOT_XIX + c] * invN;
+                const double xi = MIXED ? (double)B.xi32[3 * i + c] : B.xi64[3 * i + c];
+                if (P.nsp) dv[c] = c2i * xi - (S.fix_cm ? T[TOT_XIX + c] / P.M : 0.0);
+                else dv[c] = P.c2 * (S.fix_cm ? xi - T[TOT_XIX + c] * invN : xi);
             }
             for (int c = 0; c < 3; ++c) {
-                v[c] += P.hdt_m * blend(S.path, lam_n, F0[c] - mF0[c], -P.k * u[c] - mFE[c]);
+                v[c] += hdti * blend(S.path, lam_n, F0[c] - mF0[c], -ki * u[c] - mFE[c]);
                 x[c] += 0.5 * S.dt * v[c];
-                v[c] = P.c1 * v[c] + P.c2 * xi[c];
+                v[c] = P.c1 * v[c] + dv[c];
                 x[c] += 0.5 * S.dt * v[c];
             }
             if (P.npt) {
@@ -245,10 +258,10 @@ __global__ void __launch_bounds__(NE_TILE)
             if (!isfinite(x[c]) || !isfinite(v[c])) bad |= ST_ENAN;
             B.x[3 * i + c] = x[c];
             B.v[3 * i + c] = v[c];
-            part[PB_UX + c] = u[c];
+            part[PB_UX + c] = P.nsp ? ki * u[c] : u[c];
         }
         part[PB_U2] = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        part[PB_UE] = 0.5 * P.k * part[PB_U2];
+        part[PB_UE] = 0.5 * ki * part[PB_U2];
         // FP32 wrapped copy and displacement since the list build
         float w[3];
         for (int c = 0; c < 3; ++c) w[c] = (float)wrap(x[c], Lb[c], 1.0 / Lb[c]);
@@ -392,14 +405,18 @@ __global__ void __launch_bounds__(256) k_init_v(DevBatch B, int fix_cm)
     __shared__ double red[4][256];
     const int rep = blockIdx.x;
     const RepDev& P = B.rep[rep];
-    const double sd = sqrt(P.kT / P.m);
+    // with species tables atom a has sd = sqrt(kT / m_a), and the momentum
+    // sum_a m_a v_a / M is removed (the mass-weighted centre of mass)
+    auto mass = [&](int a) { return P.nsp ? P.ms[P.sp[a]] : P.m; };
     double sum[4] = {0, 0, 0, 0};
     for (int a = threadIdx.x; a < P.n; a += blockDim.x) {
+        const double sd = sqrt(P.kT / mass(a));
+        const double w = P.nsp ? mass(a) / P.M : 1.0;
         double z[3];
         ne_normals64(ne_philox_block(P.seed, P.replica, STREAM_INITV, (unsigned)a, 0ull), z);
         for (int c = 0; c < 3; ++c) {
             B.v[3 * (P.off + a) + c] = sd * z[c];
-            sum[c] += sd * z[c];
+            sum[c] += w * sd * z[c];
         }
     }
     for (int q = 0; q < 3; ++q) red[q][threadIdx.x] = sum[q];
@@ -410,14 +427,14 @@ __global__ void __launch_bounds__(256) k_init_v(DevBatch B, int fix_cm)
         __syncthreads();
     }
     double mean[3];
-    for (int c = 0; c < 3; ++c) mean[c] = fix_cm ? red[c][0] / P.n : 0.0;
+    for (int c = 0; c < 3; ++c) mean[c] = fix_cm ? (P.nsp ? red[c][0] : red[c][0] / P.n) : 0.0;
     __syncthreads();
     double ke = 0.0;
     for (int a = threadIdx.x; a < P.n; a += blockDim.x)
         for (int c = 0; c < 3; ++c) {
             double* vv = &B.v[3 * (P.off + a) + c];
             *vv -= mean[c];
-            ke += 0.5 * P.m * (*vv) * (*vv);
+            ke += 0.5 * mass(a) * (*vv) * (*vv);
         }
     red[3][threadIdx.x] = ke;
     __syncthreads();
@@ -495,6 +512,54 @@ __global__ void k_msd_sample(DevBatch B, double* acc)
     acc[rep] += s[3] * invN - (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]) * invN * invN;
 }
 
+// One msd sample per species of each replica with species tables (Sec. V):
+// displacements u_i = x_i - x0_i taken about the mass-weighted centre,
+// dR = sum_i m_i u_i / M; acc[rep * NE_MAX_SPECIES + s] += (1/N_s) sum over
+// the atoms of species s of |u_i - dR|^2.  One block per replica, FP64,
+// fixed-order block sums.
+__global__ void __launch_bounds__(256) k_msd_sample_species(DevBatch B, double* acc)
+{
+    __shared__ double red[3 + 2 * NE_MAX_SPECIES_DEV][256];
+    const int rep = blockIdx.x;
+    const RepDev& P = B.rep[rep];
+    double s[3] = {0, 0, 0};
+    for (int a = threadIdx.x; a < P.n; a += blockDim.x) {
+        const double w = P.ms[P.sp[a]] / P.M;
+        for (int c = 0; c < 3; ++c) s[c] += w * (B.x[3 * (P.off + a) + c] - B.x0[3 * (P.off + a) + c]);
+    }
+    for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = s[c];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    const double dR[3] = {red[0][0], red[1][0], red[2][0]};
+    __syncthreads();
+    double d2[NE_MAX_SPECIES_DEV] = {}, cnt[NE_MAX_SPECIES_DEV] = {};
+    for (int a = threadIdx.x; a < P.n; a += blockDim.x) {
+        const int q = P.sp[a];
+        for (int c = 0; c < 3; ++c) {
+            const double d = (B.x[3 * (P.off + a) + c] - B.x0[3 * (P.off + a) + c]) - dR[c];
+            d2[q] += d * d;
+        }
+        cnt[q] += 1.0;
+    }
+    for (int q = 0; q < NE_MAX_SPECIES_DEV; ++q) {
+        red[3 + q][threadIdx.x] = d2[q];
+        red[3 + NE_MAX_SPECIES_DEV + q][threadIdx.x] = cnt[q];
+    }
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 3; q < 3 + 2 * NE_MAX_SPECIES_DEV; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < P.nsp && red[3 + NE_MAX_SPECIES_DEV + threadIdx.x][0] > 0)
+        acc[rep * NE_MAX_SPECIES_DEV + threadIdx.x] +=
+            red[3 + threadIdx.x][0] / red[3 + NE_MAX_SPECIES_DEV + threadIdx.x][0];
+}
+
 }  // namespace
 
 namespace ne {
@@ -567,7 +632,10 @@ void launch_export(const DevBatch& B, bool mixed, double* f_out, double* e_out, 
 
 void launch_msd_sample(const DevBatch& B, double* acc, cudaStream_t st)
 {
-    k_msd_sample<<<B.n_rep, 32, 0, st>>>(B, acc);
+    if (B.species_any)
+        k_msd_sample_species<<<B.n_rep, 256, 0, st>>>(B, acc);
+    else
+        k_msd_sample<<<B.n_rep, 32, 0, st>>>(B, acc);
 }
 
 }  // namespace ne

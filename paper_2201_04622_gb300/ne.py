@@ -19,6 +19,8 @@ NE_OK, NE_EINVAL, NE_ENOMEM, NE_ECUDA, NE_ERANGE, NE_ENEIGH, NE_ENAN, NE_ETIMEOU
 STATUS = ["NE_OK", "NE_EINVAL", "NE_ENOMEM", "NE_ECUDA", "NE_ERANGE", "NE_ENEIGH", "NE_ENAN",
           "NE_ETIMEOUT", "NE_ENOTIMPL"]
 NE_FP64, NE_MIXED = 0, 1
+NE_MAX_SPECIES = 8
+CRYSTAL_RUNNER_MAX_ATOMS = 4096  # atoms per replica ne_crystal_run_segment holds
 NE_BCC, NE_FCC, NE_HCP = 0, 1, 2
 NE_PATH_FL, NE_PATH_RS = 0, 1
 
@@ -31,7 +33,7 @@ SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_clone", "ne_ctx_set_theta"
            "ne_eam_backward", "ne_eam_backward_acc", "ne_noise", "ne_init_velocities", "ne_langevin_step",
            "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment", "ne_switch_run_segment_grad",
            "ne_profile_segment", "ne_crystal_run_segment", "ne_crystal_run_segment_cum",
-           "ne_msd_fit", "ne_msd_fit_batched", "ne_free_energy", "ne_free_energy_species", "ne_jarzynski", "ne_lambda", "ne_pressure",
+           "ne_msd_fit", "ne_msd_fit_batched", "ne_msd_fit_species", "ne_free_energy", "ne_free_energy_species", "ne_jarzynski", "ne_lambda", "ne_pressure",
            "ne_rs_free_energy"]
 
 
@@ -59,7 +61,9 @@ class MdParams(C.Structure):
                 ("lambda_fn", C.c_int), ("path", C.c_int), ("t_eq", C.c_longlong),
                 ("t_s", C.c_longlong), ("lambda_f", C.c_double), ("seed", C.c_ulonglong),
                 ("replica", C.c_uint), ("fix_cm", C.c_int), ("prec", C.c_int),
-                ("npt", C.c_int), ("P0", C.c_double), ("beta_T", C.c_double), ("tau_p", C.c_double)]
+                ("npt", C.c_int), ("P0", C.c_double), ("beta_T", C.c_double), ("tau_p", C.c_double),
+                ("n_species", C.c_int), ("mass_s", C.c_double * 8), ("k_s", C.c_double * 8),
+                ("species_dev", C.c_void_p)]
 
 
 def lib_path() -> str:
@@ -112,6 +116,7 @@ def load(build_if_missing: bool = True):
                 "ne_crystal_run_segment_cum": [p, p, p, i, p, p, p, p, ll, ll, p],
                 "ne_msd_fit": [p, p, p, p, p, i, p, ll, ll, i, p, p, p],
                 "ne_msd_fit_batched": [p, p, i, p, p, p, p, p, ll, ll, i, p, p, p],
+                "ne_msd_fit_species": [p, p, p, p, p, i, p, ll, ll, i, p, p, p],
                 "ne_free_energy": [i, d, d, d, d, p, p, i, p, p, p],
                 "ne_free_energy_species": [i, p, i, p, p, d, d, p, p, i, p, p, p],
                 "ne_jarzynski": [d, p, i, p],
@@ -218,13 +223,34 @@ def eam_params(A, alpha, beta, B, r_e, r_s, r_c, rho_max, n_knots) -> EamParams:
 
 def md_params(dt=1e-3, T=100.0, damp=0.1, mass=None, k_spring=5.0, skin=0.5, lambda_fn=2,
               path=NE_PATH_FL, t_eq=0, t_s=1, lambda_f=0.5, seed=1, replica=0, fix_cm=1,
-              prec=NE_FP64, npt=0, P0=0.0, beta_T=0.0, tau_p=0.0) -> MdParams:
+              prec=NE_FP64, npt=0, P0=0.0, beta_T=0.0, tau_p=0.0, species=None, mass_s=None,
+              k_s=None) -> MdParams:
     """npt = 1: isotropic barostat at P0 (eV/A^3), coupling compressibility
-    beta_T (A^3/eV) and time tau_p (ps); reversible-scaling path only."""
+    beta_T (A^3/eV) and time tau_p (ps); reversible-scaling path only.
+
+    species (a uint8 CUDA tensor, one entry per atom of the replica), mass_s
+    and k_s (one value per species, 2 .. NE_MAX_SPECIES): one mass and one
+    Einstein spring per species (Sec. V); the returned block keeps a
+    reference to the tensor."""
     if mass is None:
         mass = 55.845 * 1.0364269656262175e-4
-    return MdParams(dt, T, damp, mass, k_spring, skin, lambda_fn, path, t_eq, t_s, lambda_f,
-                    seed, replica, fix_cm, prec, npt, P0, beta_T, tau_p)
+    m = MdParams(dt, T, damp, mass, k_spring, skin, lambda_fn, path, t_eq, t_s, lambda_f,
+                 seed, replica, fix_cm, prec, npt, P0, beta_T, tau_p)
+    if species is not None:
+        torch = _torch()
+        ms, ks = list(mass_s), list(k_s)
+        if not (2 <= len(ms) <= NE_MAX_SPECIES and len(ks) == len(ms)):
+            raise NeError(NE_EINVAL, "md_params", "2..%d species, one mass and one spring each" % NE_MAX_SPECIES)
+        if not (isinstance(species, torch.Tensor) and species.is_cuda and species.dtype == torch.uint8
+                and species.is_contiguous()):
+            raise NeError(NE_EINVAL, "md_params", "species must be a contiguous uint8 CUDA tensor")
+        m.n_species = len(ms)
+        for q in range(len(ms)):
+            m.mass_s[q] = float(ms[q])
+            m.k_s[q] = float(ks[q])
+        m.species_dev = species.data_ptr()
+        m._species_ref = species
+    return m
 
 
 # ------------------------------------------------------------------ entry points
@@ -503,6 +529,20 @@ def ne_msd_fit(ctx, md: MdParams, x, v, x0, box, n_eq, n_samples, stride, stream
                                 int(stride), C.byref(msd), C.byref(k), _stream(stream)),
          "ne_msd_fit")
     return msd.value, k.value
+
+
+def ne_msd_fit_species(ctx, md: MdParams, x, v, x0, box, n_eq, n_samples, stride, stream=None):
+    """Per-species (msd_s, k_s) numpy arrays of a replica with species tables."""
+    import numpy as np
+    n = x.shape[0]
+    msd = np.zeros(md.n_species)
+    k = np.zeros(md.n_species)
+    _err(ctx, load().ne_msd_fit_species(ctx, C.byref(md), _dev(x, 3 * n), _dev(v, 3 * n), _dev(x0, 3 * n), n,
+                                        _box(box), int(n_eq), int(n_samples), int(stride),
+                                        msd.ctypes.data_as(C.c_void_p), k.ctypes.data_as(C.c_void_p),
+                                        _stream(stream)),
+         "ne_msd_fit_species")
+    return msd, k
 
 
 def ne_msd_fit_batched(ctx, mds, offsets, x, v, x0, boxes, n_eq, n_samples, stride, stream=None):

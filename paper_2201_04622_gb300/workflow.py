@@ -89,15 +89,18 @@ class BatchAdvancer:
     mds, crystals, offsets, boxes, x0: as for ne_crystal_run_segment and
     ne_switch_run_segment (x0: the sites, device [N][3]); chunk: steps per
     crystal-runner call (None: the whole range in one call).  `moved` lists
-    the replicas on the multi-kernel path, `log` each call:
-    (path, replicas, first step, steps)."""
+    the replicas on the multi-kernel path -- from the start, those larger
+    than the crystal runner holds (ne.CRYSTAL_RUNNER_MAX_ATOMS) -- and `log`
+    each call: (path, replicas, first step, steps)."""
 
     def __init__(self, ctx, mds, crystals, offsets, boxes, x0, chunk=None):
         import torch
         self.ctx, self.mds, self.crystals = ctx, list(mds), list(crystals)
         self.offs, self.boxes, self.x0 = list(offsets), list(boxes), x0
         self.chunk = chunk
-        self.moved, self.log = [], []
+        self.moved = [r for r in range(len(self.mds))
+                      if self.offs[r + 1] - self.offs[r] > ne.CRYSTAL_RUNNER_MAX_ATOMS]
+        self.log = []
         self._ctx_g = None
         self._packed = None
         self._cuda = bool(getattr(x0, "is_cuda", False))
@@ -332,14 +335,21 @@ def fl_convergence(ctx, lattice, a, n, T, mass, k, t_s_list, seeds, t_eq, **kw):
 def size_scaling(ctx, lattice, a, sizes, T, mass, k, seeds, t_eq, t_s, **kw):
     """F(N) for n^3 cells (the finite-size study of Sec. IV.A), all sizes and
     seeds in one batch, and a straight-line fit in 1/N: returns the rows and
-    (F at 1/N -> 0, slope)."""
+    (F at 1/N -> 0, slope).  k: one spring for every size, or one per size.
+    With runner="auto" (fl_batch) cells larger than the crystal runner holds
+    run on the multi-kernel path alongside it, so the sizes can reach the
+    paper's ~1.1e4 atoms (bcc 18^3)."""
+    ks = list(k) if np.ndim(k) else [k] * len(sizes)
     crystals = [(lattice, a, m) for m in sizes for _ in seeds]
-    Wf, Wb, _ = fl_batch(ctx, crystals, T, [k] * len(crystals), list(seeds) * len(sizes), t_eq, t_s, mass, **kw)
+    kr = [kq for kq in ks for _ in seeds]
+    ids = kw.pop("replica_ids", None)
+    Wf, Wb, _ = fl_batch(ctx, crystals, T, kr, list(seeds) * len(sizes), t_eq, t_s, mass, replica_ids=ids, **kw)
     rows, ns = [], len(seeds)
     for q, m in enumerate(sizes):
         x0, _ = crystal_sites(lattice, a, m)
-        r = fl_free_energies(lattice, a, m, T, mass, k, Wf[q * ns:(q + 1) * ns], Wb[q * ns:(q + 1) * ns])
-        rows.append(dict(n=m, atoms=len(x0), **r))
+        r = fl_free_energies(lattice, a, m, T, mass, ks[q], Wf[q * ns:(q + 1) * ns], Wb[q * ns:(q + 1) * ns])
+        rows.append(dict(n=m, atoms=len(x0), k=ks[q], W_f=list(Wf[q * ns:(q + 1) * ns]),
+                         W_b=list(Wb[q * ns:(q + 1) * ns]), **r))
     inv = np.array([1.0 / r["atoms"] for r in rows])
     Fs = np.array([r["F"] for r in rows])
     slope, F_inf = np.polyfit(inv, Fs, 1)

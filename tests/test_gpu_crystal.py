@@ -210,12 +210,36 @@ def test_free_energy_estimators_and_convergence_workflow(ctx):
     assert abs(rows[1]["F"] - rows[0]["F"]) < 5 * (rows[0]["stderr"] + rows[1]["stderr"]) + 2 * rows[0]["Ediss"]
 
 
-def test_size_scaling_workflow(ctx):
+def test_size_scaling_workflow_against_the_oracle():
+    """The finite-size study of Sec. IV.A from 250 to 11,664 atoms (bcc 5^3
+    .. 18^3, the paper's size) in one batch, four seeds each at 1000 K:
+    cells the crystal runner holds run there, the larger ones (14^3, 18^3)
+    on the multi-kernel path alongside it.  The two smallest sizes equal the
+    oracle's stored runs (tests/golden/size_scaling_works.json, same seeds
+    and Philox replica indices): every work within 1e-6 eV per atom and F
+    within 1 meV/atom; the larger cells give finite F and the 1/N fit."""
+    import json
+    import os
     from paper_2201_04622_gb300 import workflow as WF
-    rows, (F_inf, slope) = WF.size_scaling(ctx, O.BCC, W.A_BCC, [5, 6], 800.0, MASS, 2.8, [1, 2], 200, 500,
-                                           runner="crystal")
-    assert [r["atoms"] for r in rows] == [250, 432]
-    assert all(np.isfinite([r["F"] for r in rows])) and np.isfinite(F_inf)
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "size_scaling_works.json")))
+    sizes = g["sizes"]
+    cells = [s["cells"] for s in sizes] + [10, 14, 18]
+    big = ne.ne_ctx_create(ne.eam_params(**W.EAM_FE_LIKE), 90000, 32)
+    try:
+        rows, (F_inf, slope) = WF.size_scaling(big, O.BCC, g["a"], cells, g["T"], MASS, g["k"], g["seeds"],
+                                               g["t_eq"], g["t_s"], runner="auto", chunk=3000)
+    finally:
+        ne.ne_ctx_destroy(big)
+    assert [r["atoms"] for r in rows] == [2 * c ** 3 for c in cells]
+    for q, ref in enumerate(sizes):
+        r = rows[q]
+        want = [w for w in g["rows"] if w["cells"] == ref["cells"]]
+        assert np.abs(np.array(r["W_f"]) - [w["W_f"] for w in want]).max() / r["atoms"] < 1e-6
+        assert np.abs(np.array(r["W_b"]) - [w["W_b"] for w in want]).max() / r["atoms"] < 1e-6
+        assert abs(r["F"] - ref["F_per_atom"]) < 1e-3
+    assert all(np.isfinite([r["F"] for r in rows])) and np.isfinite(F_inf) and np.isfinite(slope)
+    # F(N) flattens with size: the largest cells agree within their error bars
+    assert abs(rows[-1]["F"] - rows[-2]["F"]) < 4 * (rows[-1]["stderr"] + rows[-2]["stderr"]) + 1e-3
 
 
 def test_crystal_runner_reports_atoms_beyond_the_stencil_range(ctx):

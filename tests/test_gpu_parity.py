@@ -481,6 +481,70 @@ def test_autograd_function_against_finite_differences(ctx, pot):
     ne.ne_ctx_set_theta(ctx, T(th))
 
 
+def test_autograd_fd_on_perturbed_2000_atom_cell(ctx, pot):
+    """The differentiation check of the 65,536-atom gradient workload, at the
+    size it names: the EAM autograd.Function (FP64) on a bcc 10^3 cell
+    (2000 atoms) with 0.05 A random displacements, against central
+    differences of its own energy for 300 knot parameters (100 per table,
+    values and slopes, drawn among the knots the cell touches) and 90
+    position components, each within 1e-6 relative."""
+    p, th = pot
+    x0, box = crystal(O.BCC, 10)
+    x = W.displaced(x0, 0.05, 21)
+    EAM = ne.eam_energy_function()
+    theta = T(th).requires_grad_(True)
+    xt = T(x).requires_grad_(True)
+    EAM.apply(xt, theta, ctx, box, ne.NE_FP64).backward()
+    gth, gx = N(theta.grad), N(xt.grad)
+    rng = np.random.default_rng(10)
+    try:
+        for w in range(3):
+            active = np.flatnonzero(np.abs(gth[w]).sum(1) > 0)
+            for k in rng.choice(active, 50, replace=False):
+                for sl in (0, 1):
+                    h = 1e-6
+                    tp, tm = th.copy(), th.copy()
+                    tp[w, k, sl] += h
+                    tm[w, k, sl] -= h
+                    fd = (float(EAM.apply(T(x), T(tp), ctx, box, ne.NE_FP64)) -
+                          float(EAM.apply(T(x), T(tm), ctx, box, ne.NE_FP64))) / (2 * h)
+                    assert gth[w, k, sl] == pytest.approx(fd, rel=1e-6, abs=1e-6), (w, k, sl)
+        for i in rng.choice(len(x), 30, replace=False):
+            for c in range(3):
+                h = 1e-5
+                xp, xm = x.copy(), x.copy()
+                xp[i, c] += h
+                xm[i, c] -= h
+                fd = (float(EAM.apply(T(xp), T(th), ctx, box, ne.NE_FP64)) -
+                      float(EAM.apply(T(xm), T(th), ctx, box, ne.NE_FP64))) / (2 * h)
+                assert gx[i, c] == pytest.approx(fd, rel=1e-6, abs=1e-7), (i, c)
+    finally:
+        ne.ne_ctx_set_theta(ctx, T(th))
+
+
+def test_autograd_mixed_matches_oracle_gradient_on_2000_atoms(ctx, pot):
+    """The same Function in mixed precision (FP32 pair arithmetic, FP64
+    bins) on the perturbed 2000-atom cell: dU/dtheta against the oracle's
+    analytic gradient within the mixed tolerance of the backward pass (1e-3
+    norm-wise, from the FP32 offset u = r/h - k inside an interval), dU/dx =
+    -F against the oracle's forces within the mixed force tolerance, and U
+    within 1e-6 relative."""
+    p, th = pot
+    x0, box = crystal(O.BCC, 10)
+    x = W.displaced(x0, 0.05, 21)
+    Eo, fo, _ = O.eam_energy_forces(p, th, x, box)
+    go = O.eam_grad_theta(p, th, x, box)
+    EAM = ne.eam_energy_function()
+    theta = T(th).requires_grad_(True)
+    xt = T(x).requires_grad_(True)
+    U = EAM.apply(xt, theta, ctx, box, ne.NE_MIXED)
+    U.backward(torch.tensor(3.0, dtype=torch.float64, device=DEV))
+    assert float(U) == pytest.approx(Eo, rel=1e-6)
+    assert rel(N(theta.grad), 3.0 * go) < 1e-3
+    assert rel(N(xt.grad), -3.0 * fo) < 5e-5
+    ne.ne_ctx_set_theta(ctx, T(th))
+
+
 # ---------------------------------------------------------------- free energy
 def test_mixed_free_energy_within_1meV_of_fp64_and_oracle(ctx, pot):
     """Same seeds in FP64 and mixed precision, and the oracle, on the 4x4x4
