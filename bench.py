@@ -60,18 +60,34 @@ OPS_ATOM = 120    # per atom-step: F(rho), broadcasts, sums, Philox + Box-Muller
 WORKLOADS = {
     "fl2": "fl_bcc10x10x10_fcc8x8x8_T1400K_10seeds_each_batched20",
     "batched256": "fl_256_uneven_replicas_bcc6-12_fcc5-10_T300-1600K",
+    # reversible scaling of bcc 16^3 (8192 atoms), lambda 1 -> 1/16 from 100 K,
+    # t_eq 10 ps, t_s 100 ps, four seeds in one batch (multi-kernel path)
+    "rs16": "rs_bcc16x16x16_T0_100K_lambda_f_0.0625_4seeds_batched",
+    # bcc 32^3 (65,536 atoms), 1 ps at lambda = 0 then a 20 ps FL switch at
+    # 300 K, the backward pass (30,000 knot gradients) fused after every step
+    "grad32": "fl_grad_bcc32x32x32_T300K_backward_every_step",
 }
+# schedule (t_eq, t_s), path, lambda_f and the runner of each workload
+SCHEDULE = {"fl2": (T_EQ, T_S), "batched256": (T_EQ, 20000), "rs16": (10000, 100000), "grad32": (1000, 20000)}
 ARGS = None
+
+
+def workload():
+    return ARGS.workload if ARGS is not None else "fl2"
 
 
 def systems():
     """(lattice, n, a, seed, T) per replica of the workload."""
     out = []
-    if ARGS is not None and ARGS.workload == "batched256":
+    if workload() == "batched256":
         for r in W.batched_replicas(256, seed=1):
             a = W.A_BCC if r["lattice"] == W.BCC else W.A_FCC
             out.append((r["lattice"], r["n"], a, 1, r["T"]))
         return out
+    if workload() == "rs16":
+        return [(W.BCC, 16, W.A_BCC, 1 + s, 100.0) for s in range(4)]
+    if workload() == "grad32":
+        return [(W.BCC, 32, W.A_BCC, 1, 300.0)]
     for s in range(10):
         out.append((W.BCC, 10, W.A_BCC, 1 + s, T_K))
     for s in range(10):
@@ -82,14 +98,18 @@ def systems():
 def build_batch(ne, np):
     x0s, offs, boxes, mds = [], [0], [], []
     mass = W.MASS_FE_AMU * 1.0364269656262175e-4
+    t_eq, t_s = SCHEDULE[workload()]
+    rs = workload() == "rs16"
     for r, (lat, n, a, seed, Tk) in enumerate(systems()):
         x0, box = ne.ne_create_crystal(lat, a, n, n, n)
         x0s.append(x0)
         offs.append(offs[-1] + len(x0))
         boxes.append(box)
-        mds.append(ne.md_params(dt=1e-3, T=Tk, damp=0.1, mass=mass, k_spring=K_SPRING[lat], skin=SKIN,
-                                lambda_fn=2, path=ne.NE_PATH_FL, t_eq=T_EQ, t_s=T_S, seed=seed,
-                                replica=r, fix_cm=1))
+        k = 4.0 if workload() == "grad32" else K_SPRING[lat]
+        mds.append(ne.md_params(dt=1e-3, T=Tk, damp=0.1, mass=mass, k_spring=k,
+                                skin=1.0 if workload() in ("rs16", "grad32") else SKIN,
+                                lambda_fn=2, path=ne.NE_PATH_RS if rs else ne.NE_PATH_FL, lambda_f=0.0625,
+                                t_eq=t_eq, t_s=t_s, seed=seed, replica=r, fix_cm=1))
     return np.concatenate(x0s), offs, boxes, mds
 
 
@@ -244,14 +264,19 @@ def run_ours(args):
         ne.ne_init_velocities(ctx, m, v[offs[r]:offs[r + 1]])
     Wd = torch.zeros((n_rep, 2), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
-    S_total = 2 * T_EQ + 2 * T_S
+    t_eq_w, t_s_w = SCHEDULE[args.workload]
+    S_total = 2 * t_eq_w + 2 * t_s_w
     K, Wm = args.steps, args.warmup
     if Wm + K > S_total:
         raise SystemExit("warmup + steps exceeds the %d-step schedule" % S_total)
     l2 = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)  # > 129 MB L2
     path = args.path
     if path == "auto":
-        path = "crystal" if prec == ne.NE_MIXED else "general"
+        path = "crystal" if prec == ne.NE_MIXED and args.workload in ("fl2", "batched256") else "general"
+    grad = args.workload == "grad32"
+    if grad and path == "crystal":
+        raise SystemExit("the gradient workload runs on the multi-kernel path")
+    gth = torch.zeros(6 * W.EAM_FE_LIKE["n_knots"], dtype=torch.float64, device=dev) if grad else None
     crystals = [(lat, a, n, n, n) for (lat, n, a, seed, Tk) in systems()]
 
     # the crystal path runs through the library's BatchAdvancer: a replica that
@@ -264,13 +289,28 @@ def run_ours(args):
         adv = BatchAdvancer(ctx, mds, crystals, offs, boxes, x0,
                             chunk=5000 if args.workload == "batched256" else None)
 
+    wts = {}
+
     def segment(xx, vv, x00, WW, s0, ns):
-        if path != "crystal":
+        if grad:
+            # the backward after every step: weight 1 at each of the ns + 1
+            # configurations of the segment (the gradient sums over them)
+            if ns not in wts:
+                wts[ns] = torch.ones(ns + 1, dtype=torch.float64, device=dev)
+            ne.ne_switch_run_segment_grad(ctx, mds, offs, xx, vv, x00, boxes, WW, s0, ns, wts[ns], gth)
+        elif path != "crystal":
             ne.ne_switch_run_segment(ctx, mds, offs, xx, vv, x00, boxes, WW, s0, ns)
         else:
             adv.advance(xx, vv, WW, s0, ns)
+    if grad:
+        segment(x.clone(), v.clone(), x0, Wd.clone(), 0, 2)  # weights and backward set-up, untimed
 
     tuned = None
+    if path == "crystal" and not args.no_autotune and args.workload == "fl2":
+        # CTAs per cluster, timed on the batch itself before the timed region
+        from paper_2201_04622_gb300 import autotune
+        best, table = autotune.tune_crystal(ctx, mds, crystals, x, v, Wd, 0, 200)
+        tuned = {"best": best, "candidates": table, "what": "CTAs per cluster of the crystal runner"}
     if path == "general" and args.autotune:
         from paper_2201_04622_gb300 import autotune
         best, table = autotune.tune(ctx, mds, offs, x, v, x0, boxes, Wd, 0, 60,
@@ -364,10 +404,11 @@ def run_ours(args):
         roof = {"bound": "alu", "kernel": "k_cluster (persistent crystal runner)",
                 "achieved": alg / 1e12, "peak": peak / 1e12, "unit": "T lane-ops/s",
                 "frac": alg / peak,
-                # ncu DRAM read + write of one k_cluster launch; null until the
-                # current kernel has been captured (the replica lives on chip,
-                # so the figure does not grow with the steps)
-                "traffic": None,
+                # ncu DRAM read + write of one k_cluster launch of this kernel on
+                # this workload (a 301-step launch: 2.22 MB read, 0 written; the
+                # replica lives on chip, so the figure does not grow with the
+                # steps); null for the other workloads
+                "traffic": 2.22e6 if args.workload == "fl2" else None,
                 "kernel_ms": kern_ms, "us_per_step": kern_ms * 1e3 / K,
                 "peak_note": "%d SMs x %d FP32 lanes x %.0f MHz (median SM clock sampled around the "
                              "timed region)" % (n_sm, FP32_LANES_PER_SM, sm_hz / 1e6),
@@ -389,27 +430,44 @@ def run_ours(args):
     if n_prof > 0:
         kms, cnt = ne.ne_profile_segment(ctx, mds, offs, xp, vp, x0, boxes, Wp, Wm + K, n_prof)
         prof = kms
-    # pairs inside r_c (from the library's short-list counts) for the FLOP count
-    pairs_per_atom = 58.0 if SKIN else 58.0
+    # multi-kernel path: the dominant kernel of ne_profile_segment's per-launch
+    # times, against the algorithmic work of its pass: pass 1 ~16 and pass 2
+    # ~30 FP32 lane instructions per neighbour inside r_c (58 in bcc, 54 in
+    # fcc at these temperatures), the step kernel's ~164 B of state per atom
     if prof:
-        t_force = prof[2] * 1e-3
-        flops = FLOPS_PER_PAIR_PASS2 * pairs_per_atom * n_atoms
+        pairs_per_atom = sum((58.0 if lat == W.BCC else 54.0) * ((2 if lat == W.BCC else 4) * n ** 3)
+                             for (lat, n, a, seed, Tk) in systems()) / n_atoms
         peak = n_sm * FP32_LANES_PER_SM * (clk_sum["sm_mhz"] or clk_sum["sm_max_mhz"] or 2070.0) * 1e6
-        roof = {"bound": "alu", "kernel": "k_force (pass 2)", "achieved": flops / t_force / 1e12,
-                "peak": peak / 1e12, "unit": "TFLOP/s", "frac": flops / t_force / peak,
-                "traffic": None,
-                "per_launch_ms": {"nl_check": prof[0], "density": prof[1], "force": prof[2],
-                                  "step": prof[3]}}
+        per = {"nl_check": prof[0], "density": prof[1], "force": prof[2], "step": prof[3]}
+        top = max(("density", "force", "step"), key=lambda q: per[q])
+        if top == "step":
+            hbm_peak = measured_peak("hbm_gbs")
+            gbs = 164.0 * n_atoms / (per["step"] * 1e-3) / 1e9
+            roof = {"bound": "hbm", "kernel": "k_step (fused blend, spring, work, BAOAB)", "achieved": gbs,
+                    "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak if hbm_peak else None,
+                    "traffic": None, "per_launch_ms": per}
+        else:
+            ops = (16.0 if top == "density" else 30.0) * pairs_per_atom * n_atoms
+            ach = ops / (per[top] * 1e-3)
+            roof = {"bound": "alu", "kernel": "k_density (pass 1)" if top == "density" else "k_force (pass 2)",
+                    "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "T lane-ops/s", "frac": ach / peak,
+                    "traffic": None, "per_launch_ms": per,
+                    "algorithmic": "%d FP32 lane instructions per pair inside r_c x %.1f pairs per atom"
+                                   % (16 if top == "density" else 30, pairs_per_atom)}
+        if grad:
+            # the fused backward's own time per step: the timed step minus the
+            # forward kernels (same launches without the backward)
+            roof["backward_ms_per_step"] = ms / K - sum(per.values())
     steps_per_graph = 32
     general_launches = 5 * K + (K - 1) // steps_per_graph + 10
     if path == "crystal":
         launches = (c1[3] - c0[3]) + sum(5 * e[3] + e[3] // steps_per_graph + 10
                                          for e in timed_log if e[0] == "general")
     else:
-        launches = general_launches
+        launches = general_launches + (2 * (K + 1) if grad else 0)  # backward: bins + reduction per step
     # the plain FP64 GPU path on the same batch (the comparison the metric names)
     fp64 = None
-    if prec == ne.NE_MIXED and not args.no_fp64:
+    if prec == ne.NE_MIXED and not args.no_fp64 and not grad:
         K64 = min(K, 2000, S_total - 1)
         m64 = [ne.md_params(dt=m.dt, T=m.T, damp=m.damp, mass=m.mass, k_spring=m.k_spring, skin=SKIN,
                             lambda_fn=m.lambda_fn, path=m.path, t_eq=m.t_eq, t_s=m.t_s, seed=m.seed,
@@ -436,8 +494,9 @@ def run_ours(args):
            "vs_baseline": None, "dtype": "f32+f64" if prec == ne.NE_MIXED else "f64",
            "data": "synthetic (perfect bcc/fcc lattices, Philox Maxwell-Boltzmann velocities)",
            "config": {"workload": WORKLOADS[args.workload], "replicas": n_rep, "atoms": n_atoms,
-                      "T_K": T_K if args.workload == "fl2" else "300-1600",
-                      "t_eq": T_EQ, "t_s": T_S, "dt_fs": 1.0, "skin_A": SKIN,
+                      "T_K": {"fl2": T_K, "batched256": "300-1600", "rs16": "100 -> 1600 (lambda 1 -> 0.0625)",
+                              "grad32": 300.0}[args.workload],
+                      "t_eq": t_eq_w, "t_s": t_s_w, "dt_fs": 1.0, "skin_A": mds[0].skin,
                       "precision": args.prec, "path": path,
                       "threads_per_atom": 2 if path == "crystal" else args.tpa,
                       "autotune": tuned,
@@ -534,7 +593,11 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
     ap.add_argument("--autotune", action="store_true",
                     help="multi-kernel path: pick threads per atom and skin by timing the batch")
-    ap.add_argument("--workload", default="fl2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="crystal runner: keep the occupancy-based cluster size instead of timing 6-8 CTAs")
+    ap.add_argument("--workload", default="fl2", choices=sorted(WORKLOADS),
+                    help="fl2: FL switching of 20 crystals (crystal runner); batched256: 256 uneven replicas; "
+                         "rs16: reversible scaling of bcc 16^3; grad32: bcc 32^3 with the backward every step")
     args = ap.parse_args()
     global ARGS
     ARGS = args

@@ -87,16 +87,21 @@ typedef struct {
     unsigned replica;  /* < 2^28 */
     int fix_cm;        /* 1: centre of mass fixed (noise and force means removed) */
     ne_precision prec;
-    /* Isotropic barostat (Sec. III.C: reversible scaling at P = 0), RS path
-     * of the multi-kernel runs only; 0 = fixed box.  Each step, after the
-     * second drift, ln V takes one step of the overdamped Langevin equation
-     * whose stationary density is V^(N'+1) exp(-(lambda U + P0 V)/k_B T)
+    /* Barostat (Sec. III.C: reversible scaling at P = 0), RS path of the
+     * multi-kernel runs only; 0 = fixed box.  npt = 1, isotropic: each step,
+     * after the second drift, ln V takes one step of the overdamped Langevin
+     * equation whose stationary density is V^(N'+1) exp(-(lambda U + P0 V)/k_B T)
      * (N' = dof/3) at fixed scaled coordinates:
      *   d ln V = m [(dof k_B T + lambda W)/(3V) - P0] dt + sqrt(2 k_B T m dt / V) eta,
      * m = beta_T / tau_p, W the virial of U at the step's start, eta from
      * Philox stream 5; positions and box scale by exp(d ln V / 3) about the
-     * origin.  The final boxes are read back with ne_ctx_boxes (pass them
-     * to the next segment).  With P0 = 0, eq. rs gives G(T) at zero pressure. */
+     * origin.  npt = 2, per axis (the paper's fix nph aniso; non-cubic cells
+     * such as hcp relax their c/a): each eps_a = ln L_a takes
+     *   d eps_a = m [(dof/3 k_B T + lambda W_a)/V - P0] dt + sqrt(2 k_B T m dt / V) eta_a,
+     * W_a the a-th diagonal element of the virial, eta_a the a-th normal of
+     * the same draw; coordinate a and edge a scale by exp(d eps_a).  The final
+     * boxes are read back with ne_ctx_boxes (pass them to the next segment).
+     * With P0 = 0, eq. rs gives G(T) at zero pressure. */
     int npt;
     double P0;         /* eV / A^3, >= 0 */
     double beta_T;     /* coupling compressibility, A^3 / eV, > 0 */
@@ -347,6 +352,19 @@ ne_status ne_switch_run_segment(ne_ctx* ctx, const ne_md_params* md, int n_rep,
                                 const int* offsets_host, double* x_dev, double* v_dev,
                                 const double* x0_dev, const double* boxes_host, double* W_dev,
                                 long long step_begin, long long n_steps, void* stream);
+
+/* ne_switch_run_segment that also records the cumulative works of the two
+ * switches for every replica, for eq. rs over a batch of seeds (Sec. III.C):
+ * Wcum_dev (device, double [n_rep][2][t_s + 1]; [r][0] forward, [r][1]
+ * backward) gets, for every switching step k of the range, [k + 1] = replica
+ * r's W after that step and [0] = 0 at the switch's first step -- the layout
+ * of ne_crystal_run_segment_cum.  Errors as ne_switch_run_segment; NE_EINVAL
+ * if Wcum_dev is NULL. */
+ne_status ne_switch_run_segment_cum(ne_ctx* ctx, const ne_md_params* md, int n_rep,
+                                    const int* offsets_host, double* x_dev, double* v_dev,
+                                    const double* x0_dev, const double* boxes_host, double* W_dev,
+                                    double* Wcum_dev, long long step_begin, long long n_steps,
+                                    void* stream);
 
 /* ne_switch_run_segment that also accumulates the parameter gradient along
  * the run (the backward pass of Sec. III.B's switching runs; the paper has no

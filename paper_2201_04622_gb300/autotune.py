@@ -1,7 +1,11 @@
-"""Autotuner of the multi-kernel path: threads per atom of the pair kernels
-and the neighbour-list skin, chosen by timing real steps of the caller's own
-batch (ne_profile_segment: CUDA events around every launch, on the launching
-stream).  The persistent crystal runner has no free tile parameters."""
+"""Autotuners, each timing real steps of the caller's own batch with the
+state restored after every trial:
+  tune          -- the multi-kernel path: threads per atom of the pair
+                   kernels and the neighbour-list skin (ne_profile_segment:
+                   CUDA events around every launch, on the launching stream);
+  tune_crystal  -- the persistent crystal runner: CTAs per thread-block
+                   cluster, i.e. atoms per CTA against clusters resident at
+                   once (ne_ctx_last_run_ms: events around the launch)."""
 from __future__ import annotations
 
 import itertools
@@ -42,4 +46,46 @@ def tune(ctx, mds, offsets, x, v, x0, boxes, W, step_begin=0, n_steps=100,
     for m in mds:
         m.skin = best["skin"]
     torch.cuda.synchronize()
+    return best, table
+
+
+def tune_crystal(ctx, mds, crystals, x, v, W, step_begin=0, n_steps=200, sizes=None):
+    """CTAs per cluster of the crystal runner for a batch: every size from
+    the smallest that holds the largest replica up to 8 (the portable cluster
+    limit), or `sizes`, timed over n_steps of the batch; the fastest is fixed
+    with ne_ctx_set_cluster_size.  Returns (best, table): best =
+    dict(ctas, us_per_step); table = all candidates (a size the device cannot
+    launch is left out).  x, v, W are restored after every trial."""
+    import torch
+    per_cta = ne.CRYSTAL_RUNNER_ATOMS_PER_CTA
+    n_max = max((2 if int(c[0]) == ne.NE_BCC else 4) * int(c[2]) * int(c[3]) * int(c[4]) for c in crystals)
+    c_min = max(1, -(-n_max // per_cta))
+    cand = list(sizes) if sizes else list(range(c_min, 9))
+    saved = (x.clone(), v.clone(), W.clone())
+    batch = ne.CrystalBatch(mds, crystals)
+    table = []
+    try:
+        for C in cand:
+            try:
+                ne.ne_ctx_set_cluster_size(ctx, C)
+                ne.ne_crystal_run_segment(ctx, batch, None, x, v, W, step_begin, min(20, n_steps))  # plan, warm
+                x.copy_(saved[0])
+                v.copy_(saved[1])
+                W.copy_(saved[2])
+                ne.ne_crystal_run_segment(ctx, batch, None, x, v, W, step_begin, n_steps)
+                ms = ne.ne_ctx_last_run_ms(ctx)
+                table.append(dict(ctas=C, us_per_step=ms * 1e3 / n_steps))
+            except ne.NeError:
+                pass  # too few CTAs for a replica, or more than the device co-schedules
+            finally:
+                x.copy_(saved[0])
+                v.copy_(saved[1])
+                W.copy_(saved[2])
+    finally:
+        torch.cuda.synchronize()
+    if not table:
+        ne.ne_ctx_set_cluster_size(ctx, 0)
+        raise ValueError("no cluster size could run this batch")
+    best = min(table, key=lambda t: t["us_per_step"])
+    ne.ne_ctx_set_cluster_size(ctx, best["ctas"])
     return best, table

@@ -68,6 +68,7 @@ struct ne_ctx {
     unsigned* tile_done = nullptr;
     int *flags = nullptr, *building = nullptr, *status = nullptr, *tile_rep = nullptr;
     int* rep_status = nullptr;  // crystal runner: status bits per replica of the last call (= status + 1)
+    int* status_host = nullptr; // pinned host copy of the status word
     RepDev* rep = nullptr;
     long long* step_ctr = nullptr;
     unsigned long long* rebuilds = nullptr;
@@ -356,9 +357,10 @@ ne_status setup_batch(ne_ctx* ctx, int n_rep, const int* off, const double* boxe
 ne_status finish(ne_ctx* ctx, cudaStream_t st)
 {
     NE_CU(cudaGetLastError());
-    int bits = 0;
-    NE_CU(cudaMemcpyAsync(&bits, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    // the status word lands in pinned host memory: the copy is a plain DMA
+    NE_CU(cudaMemcpyAsync(ctx->status_host, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     NE_CU(cudaStreamSynchronize(st));
+    const int bits = *ctx->status_host;
     ctx->last_bits = bits;
     if (bits & ST_ENAN) return fail(ctx, NE_ENAN, "non-finite position, velocity or energy");
     if (bits & ST_ERANGE) return fail(ctx, NE_ERANGE, "pair distance below 0.2 A, density >= rho_max, or an atom beyond the crystal runner's stencil range");
@@ -552,7 +554,7 @@ ne_status check_md(ne_ctx* ctx, const ne_md_params* m)
     if (m->path == NE_PATH_RS && !(m->lambda_f > 0 && m->lambda_f < 1))
         return fail(ctx, NE_EINVAL, "lambda_f must lie in (0, 1)");
     if (m->prec != NE_FP64 && m->prec != NE_MIXED) return fail(ctx, NE_EINVAL, "unknown precision");
-    if (m->npt != 0 && m->npt != 1) return fail(ctx, NE_EINVAL, "npt must be 0 or 1");
+    if (m->npt < 0 || m->npt > 2) return fail(ctx, NE_EINVAL, "npt must be 0, 1 or 2");
     if (m->npt && m->path != NE_PATH_RS)
         return fail(ctx, NE_EINVAL, "the barostat runs on the reversible-scaling path (the Einstein crystal has no pressure)");
     if (m->npt && (!(m->beta_T > 0) || !(m->tau_p > 0) || !(m->P0 >= 0)))
@@ -619,6 +621,7 @@ ne_status ne_ctx_create(const ne_eam_params* eam, int max_atoms, int max_replica
     A(dalloc(&ctx->rebuilds, 1));
     A(dalloc(&ctx->xrep, R));
     A(dalloc(&ctx->work, 2));
+    A(cudaMallocHost((void**)&ctx->status_host, sizeof(int)));
     if (ok) ok = cudaMemset(ctx->work, 0, 2 * sizeof(unsigned long long)) == cudaSuccess;
     A(dalloc(&ctx->st_vec, R * 4 * NE_STENCIL_MAX));
     A(dalloc(&ctx->st_dist, R * 4 * NE_STENCIL_MAX));
@@ -655,6 +658,7 @@ ne_status ne_ctx_destroy(ne_ctx* ctx)
                     ctx->bins};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (ctx->status_host) cudaFreeHost(ctx->status_host);
     for (int g = 0; g < 16; ++g)
         if (ctx->gst[g]) cudaStreamDestroy(ctx->gst[g]);
     for (int g = 0; g < 17; ++g)
@@ -1126,6 +1130,21 @@ ne_status ne_switch_run_segment_grad(ne_ctx* ctx, const ne_md_params* md, int n_
     if (s) return s;
     return segment_impl(ctx, md, n_rep, offsets_host, x_dev, v_dev, x0_dev, boxes_host, W_dev, nullptr, nullptr,
                         0, step_begin, n_steps, (cudaStream_t)stream, w_dev, gtheta_dev);
+}
+
+ne_status ne_switch_run_segment_cum(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* offsets_host,
+                                    double* x_dev, double* v_dev, const double* x0_dev, const double* boxes_host,
+                                    double* W_dev, double* Wcum_dev, long long step_begin, long long n_steps,
+                                    void* stream)
+{
+    if (!ctx || !md || !offsets_host || !x_dev || !v_dev || !x0_dev || !boxes_host || !W_dev || !Wcum_dev ||
+        n_rep < 1)
+        return NE_EINVAL;
+    if (n_rep > ctx->max_rep) return fail(ctx, NE_ENOMEM, "replica count exceeds the context");
+    ne_status s = check_batch(ctx, md, n_rep, offsets_host);
+    if (s) return s;
+    return segment_impl(ctx, md, n_rep, offsets_host, x_dev, v_dev, x0_dev, boxes_host, W_dev, Wcum_dev, nullptr,
+                        0, step_begin, n_steps, (cudaStream_t)stream);
 }
 
 ne_status ne_switch_run_segment(ne_ctx* ctx, const ne_md_params* md, int n_rep, const int* offsets_host,

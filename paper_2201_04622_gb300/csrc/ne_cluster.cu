@@ -41,6 +41,7 @@
 // (within a CTA and across the cluster), the sums for the mean removal in
 // FP32.
 #include <algorithm>
+#include <atomic>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -698,6 +699,35 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 }  // namespace
 
+namespace {
+
+// The kernel's launch attributes on the current device, raised only (a launch
+// needs at least its shared memory and, above 8 CTAs, non-portable cluster
+// sizes): the driver is called only when a launch needs more than was set
+// before on the device.
+cudaError_t cluster_attributes(int C, size_t smem)
+{
+    static std::atomic<int> smem_set[64];
+    static std::atomic<int> nonportable_set[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool cached = dev >= 0 && dev < 64;
+    if (!cached || smem_set[dev].load() < (int)smem) {
+        e = cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (cached) smem_set[dev].store((int)smem);
+    }
+    if (C > 8 && (!cached || !nonportable_set[dev].load())) {
+        e = cudaFuncSetAttribute(k_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        if (cached) nonportable_set[dev].store(1);
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
 namespace ne {
 
 // Bytes of everything but the spline tables; the tables take what is left.
@@ -726,8 +756,7 @@ int cluster_atoms_for(int n, int C, int nb) { return atoms_per_cta(n, C, nb); }
 
 int cluster_max_active(int C, size_t smem)
 {
-    if (cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        (C > 8 && cudaFuncSetAttribute(k_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+    if (cluster_attributes(C, smem) != cudaSuccess) {
         (void)cudaGetLastError();  // not a launch error: clear it, the caller reports 0 clusters
         return 0;
     }
@@ -761,12 +790,8 @@ cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, cons
                            long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
                            int k_lo, double* lam_tab, double* wcum, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cluster_attributes(C, smem);
     if (e != cudaSuccess) return e;
-    if (C > 8) {
-        e = cudaFuncSetAttribute(k_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(n_rep * C, 1, 1);
     cfg.blockDim = dim3(THREADS, 1, 1);

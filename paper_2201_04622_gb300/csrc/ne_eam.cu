@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
     k_force(DevBatch B, Sched S, const long long* __restrict__ step_base, int j, int want_noise)
 {
     using R = typename Pos<MIXED>::R;
-    __shared__ double red[8][NE_TILE * TPA];
+    __shared__ double red[VIR ? 11 : 7][NE_TILE * TPA];
     __shared__ int s_last;
     const int tile = blockIdx.x;
     const int rep = B.tile_rep[tile];
@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
     const R inv_h = MIXED ? (R)B.tab.inv_h_rf : (R)B.tab.inv_h_r;
     const int nk = B.tab.nk;
     R fx = 0, fy = 0, fz = 0, ep = 0, vir = 0;  // vir: -(1/2) sum_j r dU/dr (the pair's half)
+    R vxx = 0, vyy = 0, vzz = 0;                  // its diagonal: -(1/2) sum_j r_a^2 / r dU/dr
     if (valid) {
         V3<R> pi;
         R dFi;
@@ -257,7 +258,12 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
             fy += s * dy;
             fz += s * dz;
             ep += (R)0.5 * phi;
-            if constexpr (VIR) vir -= (R)0.5 * s * r2;
+            if constexpr (VIR) {
+                vir -= (R)0.5 * s * r2;
+                vxx -= (R)0.5 * s * dx * dx;
+                vyy -= (R)0.5 * s * dy * dy;
+                vzz -= (R)0.5 * s * dz * dz;
+            }
         }
     }
     fx = lane_sum(fx, TPA);
@@ -265,7 +271,13 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
     fz = lane_sum(fz, TPA);
     double epd = lane_sum((double)ep, TPA);
     const double vird = VIR ? lane_sum((double)vir, TPA) : 0.0;
-    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double vdiag[3] = {0, 0, 0};
+    if constexpr (VIR) {
+        vdiag[0] = lane_sum((double)vxx, TPA);
+        vdiag[1] = lane_sum((double)vyy, TPA);
+        vdiag[2] = lane_sum((double)vzz, TPA);
+    }
+    double v[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (valid && lane == 0) {
         if constexpr (MIXED) {
             B.f32[i] = make_float4((float)fx, (float)fy, (float)fz, 0.f);
@@ -276,6 +288,9 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
         }
         v[0] = epd;
         v[7] = vird;
+        v[8] = vdiag[0];
+        v[9] = vdiag[1];
+        v[10] = vdiag[2];
         v[1] = (double)fx;
         v[2] = (double)fy;
         v[3] = (double)fz;
@@ -311,7 +326,7 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
             }
         }
     }
-    constexpr int NQ = VIR ? 8 : 7;
+    constexpr int NQ = VIR ? 11 : 7;
     for (int q = 0; q < NQ; ++q) red[q][threadIdx.x] = v[q];
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -328,7 +343,10 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
         pa[PA_XIX] = red[4][0];
         pa[PA_XIY] = red[5][0];
         pa[PA_XIZ] = red[6][0];
-        pa[PA_VIR] = VIR ? red[7][0] : 0.0;
+        pa[PA_VIR] = VIR ? red[VIR ? 7 : 0][0] : 0.0;
+        pa[PA_VXX] = VIR ? red[VIR ? 8 : 0][0] : 0.0;
+        pa[PA_VYY] = VIR ? red[VIR ? 9 : 0][0] : 0.0;
+        pa[PA_VZZ] = VIR ? red[VIR ? 10 : 0][0] : 0.0;
         __threadfence();
         unsigned prev = atomicAdd(&B.tile_done[rep], 1u);
         s_last = (prev == (unsigned)P.ntile - 1u);

@@ -39,12 +39,12 @@ enum { ST_ERANGE = 1, ST_ENEIGH = 2, ST_ENAN = 4, ST_ETIMEOUT = 8, ST_EINVAL = 1
 enum { STREAM_FL = 0, STREAM_INITV = 1, STREAM_RS = 2, STREAM_MSD = 3, STREAM_STEP = 4, STREAM_BARO = 5 };
 
 // tile partials of pass 1 / pass 2 (at x_k)
-enum { PA_UEMB = 0, PA_UPAIR, PA_F0X, PA_F0Y, PA_F0Z, PA_XIX, PA_XIY, PA_XIZ, PA_VIR, NPA };
+enum { PA_UEMB = 0, PA_UPAIR, PA_F0X, PA_F0Y, PA_F0Z, PA_XIX, PA_XIY, PA_XIZ, PA_VIR, PA_VXX, PA_VYY, PA_VZZ, NPA };
 // tile partials of the step kernel (at x_{k+1}; KE of the completed velocity)
 enum { PB_UE = 0, PB_UX, PB_UY, PB_UZ, PB_U2, PB_KE, NPB };
 // per-replica totals
 enum { TOT_UEMB = 0, TOT_UPAIR, TOT_F0X, TOT_F0Y, TOT_F0Z, TOT_XIX, TOT_XIY, TOT_XIZ, TOT_VIR,
-       TOT_UE, TOT_UX, TOT_UY, TOT_UZ, TOT_U2, TOT_KE, NTOT };
+       TOT_VXX, TOT_VYY, TOT_VZZ, TOT_UE, TOT_UX, TOT_UY, TOT_UZ, TOT_U2, TOT_KE, NTOT };
 static_assert((int)TOT_VIR == (int)PA_VIR && (int)TOT_UE == (int)NPA, "totals: pass-2 partials first, then the step's");
 
 struct RepDev {
@@ -62,7 +62,7 @@ struct RepDev {
     int dof;
     unsigned long long seed;
     unsigned replica;
-    int npt;         // isotropic barostat on (RS path)
+    int npt;         // barostat (RS path): 1 isotropic, 2 one equation per box edge
     double P0, mp;   // target pressure, mobility beta_T / tau_p
     // Several species (Sec. V): nsp = 0 -- every atom has m and k above;
     // nsp >= 2 -- atom a has species sp[a] (validated on the host) with mass

@@ -165,14 +165,30 @@ __device__ __forceinline__ double blend(int path, double lam, double F0, double 
 // normal of Philox stream 5 at (atom 0, step s).  Every block computes the
 // same factor; positions scale about the origin here, the box in k_npt_box
 // after this kernel.
-__device__ inline double npt_scale(const RepDev& P, const double* T, double lam, long long s, double dt)
+//
+// Per axis (RepDev.npt = 2, for non-cubic cells such as hcp, whose c/a the
+// isotropic form cannot change): each eps_a = ln L_a takes the same kind of
+// step with the measure dL_x dL_y dL_z,
+//   d eps_a = m [(dof/3 kT + lambda W_a)/V - P0] dt + sqrt(2 kT m dt / V) eta_a,
+// W_a = -dU/d eps_a the a-th diagonal element of the virial, eta_a the a-th
+// normal of the same Philox block; coordinate a and edge a scale by e^(d eps_a).
+__device__ inline void npt_scale(const RepDev& P, const double* T, double lam, long long s, double dt,
+                                 double mu[3])
 {
     const double V = P.L[0] * P.L[1] * P.L[2];
     double z[3];
     ne_normals64(ne_philox_block(P.seed, P.replica, (unsigned)STREAM_BARO, 0u, (unsigned long long)s), z);
+    const double noise = sqrt(2.0 * P.kT * P.mp * dt / V);
+    if (P.npt == 2) {
+        for (int c = 0; c < 3; ++c) {
+            const double drive = (P.dof / 3.0 * P.kT + lam * T[TOT_VXX + c]) / V - P.P0;
+            mu[c] = exp(P.mp * drive * dt + noise * z[c]);
+        }
+        return;
+    }
     const double drive = (P.dof * P.kT + lam * T[TOT_VIR]) / (3.0 * V) - P.P0;
-    const double deps = P.mp * drive * dt + sqrt(2.0 * P.kT * P.mp * dt / V) * z[0];
-    return exp(deps / 3.0);
+    const double deps = P.mp * drive * dt + noise * z[0];
+    mu[0] = mu[1] = mu[2] = exp(deps / 3.0);
 }
 
 template <bool MIXED>
@@ -246,10 +262,11 @@ __global__ void __launch_bounds__(NE_TILE)
                 x[c] += 0.5 * S.dt * v[c];
             }
             if (P.npt) {
-                const double mu = npt_scale(P, T, lam_n, s, S.dt);
+                double mu[3];
+                npt_scale(P, T, lam_n, s, S.dt, mu);
                 for (int c = 0; c < 3; ++c) {
-                    x[c] *= mu;
-                    Lb[c] = mu * P.L[c];
+                    x[c] *= mu[c];
+                    Lb[c] = mu[c] * P.L[c];
                 }
             }
             for (int c = 0; c < 3; ++c) u[c] = x[c] - B.x0[3 * i + c];
@@ -351,17 +368,18 @@ __global__ void k_npt_box(DevBatch B, Sched S, const long long* __restrict__ ste
     RepDev& P = const_cast<RepDev*>(B.rep)[rep];
     if (!P.npt) return;
     const long long s = *step_base + j;
-    const double mu = npt_scale(P, B.tot + (size_t)rep * NTOT, ne_sched_lambda(S, s + 1), s, S.dt);
+    double mu[3];
+    npt_scale(P, B.tot + (size_t)rep * NTOT, ne_sched_lambda(S, s + 1), s, S.dt, mu);
     const double rl = sqrt(P.rlist2);
     for (int c = 0; c < 3; ++c) {
-        const double L = mu * P.L[c];
+        const double L = mu[c] * P.L[c];
         if (!(L > 2.0 * rl) || (P.nc[c] > 0 && !(L / P.nc[c] >= rl))) {
             ne_set_status(B.status, ST_ERANGE);
             return;
         }
     }
     for (int c = 0; c < 3; ++c) {
-        P.L[c] *= mu;
+        P.L[c] *= mu[c];
         P.invL[c] = 1.0 / P.L[c];
     }
 }

@@ -21,6 +21,7 @@ STATUS = ["NE_OK", "NE_EINVAL", "NE_ENOMEM", "NE_ECUDA", "NE_ERANGE", "NE_ENEIGH
 NE_FP64, NE_MIXED = 0, 1
 NE_MAX_SPECIES = 8
 CRYSTAL_RUNNER_MAX_ATOMS = 4096  # atoms per replica ne_crystal_run_segment holds
+CRYSTAL_RUNNER_ATOMS_PER_CTA = 384  # atoms one CTA of its clusters owns
 NE_BCC, NE_FCC, NE_HCP = 0, 1, 2
 NE_PATH_FL, NE_PATH_RS = 0, 1
 
@@ -31,7 +32,7 @@ SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_clone", "ne_ctx_set_theta"
            "ne_create_crystal", "ne_create_crystal_ca", "ne_eam_energy_forces", "ne_eam_virial", "ne_eam_energy_forces_noalloc",
            "ne_spring_forces",
            "ne_eam_backward", "ne_eam_backward_acc", "ne_noise", "ne_init_velocities", "ne_langevin_step",
-           "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment", "ne_switch_run_segment_grad",
+           "ne_switch_run", "ne_rs_run", "ne_switch_run_batched", "ne_switch_run_segment", "ne_switch_run_segment_cum", "ne_switch_run_segment_grad",
            "ne_profile_segment", "ne_crystal_run_segment", "ne_crystal_run_segment_cum",
            "ne_msd_fit", "ne_msd_fit_batched", "ne_msd_fit_species", "ne_free_energy", "ne_free_energy_species", "ne_jarzynski", "ne_lambda", "ne_pressure",
            "ne_rs_free_energy"]
@@ -110,6 +111,7 @@ def load(build_if_missing: bool = True):
                 "ne_rs_run": [p, p, d, p, p, p, i, p, p, p, p],
                 "ne_switch_run_batched": [p, p, i, p, p, p, p, p, p, p, p],
                 "ne_switch_run_segment": [p, p, i, p, p, p, p, p, p, ll, ll, p],
+                "ne_switch_run_segment_cum": [p, p, i, p, p, p, p, p, p, p, ll, ll, p],
                 "ne_switch_run_segment_grad": [p, p, i, p, p, p, p, p, p, ll, ll, p, p, p],
                 "ne_profile_segment": [p, p, i, p, p, p, p, p, p, ll, ll, p, p, p],
                 "ne_crystal_run_segment": [p, p, p, i, p, p, p, ll, ll, p],
@@ -226,7 +228,8 @@ def md_params(dt=1e-3, T=100.0, damp=0.1, mass=None, k_spring=5.0, skin=0.5, lam
               prec=NE_FP64, npt=0, P0=0.0, beta_T=0.0, tau_p=0.0, species=None, mass_s=None,
               k_s=None) -> MdParams:
     """npt = 1: isotropic barostat at P0 (eV/A^3), coupling compressibility
-    beta_T (A^3/eV) and time tau_p (ps); reversible-scaling path only.
+    beta_T (A^3/eV) and time tau_p (ps); npt = 2: one such equation per box
+    edge (non-cubic cells); reversible-scaling path only.
 
     species (a uint8 CUDA tensor, one entry per atom of the replica), mass_s
     and k_s (one value per species, 2 .. NE_MAX_SPECIES): one mass and one
@@ -461,6 +464,15 @@ def ne_switch_run_segment(ctx, mds, offsets, x, v, x0, boxes, W, step_begin, n_s
     _err(ctx, load().ne_switch_run_segment(ctx, arr, n_rep, off, _dev(x, n3), _dev(v, n3), _dev(x0, n3), bx,
                                            _dev(W, 2 * n_rep), int(step_begin), int(n_steps),
                                            _stream(stream)), "ne_switch_run_segment")
+
+
+def ne_switch_run_segment_cum(ctx, mds, offsets, x, v, x0, boxes, W, Wcum, step_begin, n_steps, stream=None):
+    """ne_switch_run_segment plus the cumulative works Wcum [n_rep][2][t_s + 1]."""
+    n_rep, md_arr, off, bx, n3 = _batch_args(mds, offsets, boxes)
+    _err(ctx, load().ne_switch_run_segment_cum(ctx, md_arr, n_rep, off, _dev(x, n3), _dev(v, n3), _dev(x0, n3), bx,
+                                               _dev(W, 2 * n_rep), _dev(Wcum, n_rep * 2 * (int(mds[0].t_s) + 1)),
+                                               int(step_begin), int(n_steps), _stream(stream)),
+         "ne_switch_run_segment_cum")
 
 
 def ne_switch_run_segment_grad(ctx, mds, offsets, x, v, x0, boxes, W, step_begin, n_steps, w, gtheta, stream=None):

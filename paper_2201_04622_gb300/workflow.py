@@ -357,31 +357,40 @@ def size_scaling(ctx, lattice, a, sizes, T, mass, k, seeds, t_eq, t_s, **kw):
 
 
 def rs_works(ctx, lattice, a, n, T0, mass, lambda_f, t_eq, t_s, seeds, prec=ne.NE_MIXED, skin=1.0, npt=False,
-             beta_T=1.2, tau_p=0.5, device="cuda"):
+             beta_T=1.2, tau_p=0.5, device="cuda", replica_ids=None, chunk=None):
     """Reversible scaling (Sec. III.C): per seed, t_eq steps at lambda = 1,
     a forward switch to lambda_f over t_s steps, t_eq steps there and the
     switch back, at T0, in the box of lattice parameter a or, with npt, at
     zero pressure under the isotropic barostat (beta_T, tau_p: its coupling).
-    Returns the cumulative works [seeds][t_s + 1] (forward, backward) and,
-    with npt, the final lattice parameters (box edge / cells)."""
+    All seeds run as one batch on the multi-kernel path
+    (ne_switch_run_segment_cum; replica index 0 for every seed unless
+    replica_ids is given), in segments of `chunk` steps (all at once by
+    default).  Returns the cumulative works [seeds][t_s + 1] (forward,
+    backward) and, with npt, the final lattice parameters (box edge / cells)."""
     import torch
     x0_np, box = crystal_sites(lattice, a, n)
-    x0 = torch.tensor(x0_np, dtype=torch.float64, device=device)
-    cf, cb, a_end = [], [], []
-    for seed in seeds:
-        md = ne.md_params(T=T0, mass=mass, skin=skin, prec=prec, path=ne.NE_PATH_RS, lambda_f=lambda_f,
-                          t_eq=t_eq, t_s=t_s, seed=seed, replica=0, fix_cm=1, npt=int(npt), P0=0.0,
-                          beta_T=beta_T, tau_p=tau_p)
-        x, v = x0.clone(), torch.zeros_like(x0)
-        ne.ne_init_velocities(ctx, md, v)
-        wf = torch.zeros(t_s + 1, dtype=torch.float64, device=device)
-        wb = torch.zeros(t_s + 1, dtype=torch.float64, device=device)
-        ne.ne_rs_run(ctx, md, lambda_f, x, v, x0, box, wf, wb)
-        cf.append(wf.cpu().numpy())
-        cb.append(wb.cpu().numpy())
-        if npt:
-            a_end.append(ne.ne_ctx_boxes(ctx, 1)[0][0] / n)
-    return np.array(cf), np.array(cb), np.array(a_end)
+    nat, nr = len(x0_np), len(seeds)
+    ids = [0] * nr if replica_ids is None else list(replica_ids)
+    mds = [ne.md_params(T=T0, mass=mass, skin=skin, prec=prec, path=ne.NE_PATH_RS, lambda_f=lambda_f,
+                        t_eq=t_eq, t_s=t_s, seed=seed, replica=rid, fix_cm=1, npt=int(npt), P0=0.0,
+                        beta_T=beta_T, tau_p=tau_p) for seed, rid in zip(seeds, ids)]
+    x0 = torch.tensor(np.concatenate([x0_np] * nr), dtype=torch.float64, device=device)
+    x, v = x0.clone(), torch.zeros_like(x0)
+    offs = [q * nat for q in range(nr + 1)]
+    for r, m in enumerate(mds):
+        ne.ne_init_velocities(ctx, m, v[offs[r]:offs[r + 1]])
+    W = torch.zeros((nr, 2), dtype=torch.float64, device=device)
+    Wc = torch.zeros(nr * 2 * (t_s + 1), dtype=torch.float64, device=device)
+    boxes = [list(box)] * nr
+    S = 2 * t_eq + 2 * t_s
+    for s0 in range(0, S, chunk or S):
+        ns = min(chunk or S, S - s0)
+        ne.ne_switch_run_segment_cum(ctx, mds, offs, x, v, x0, boxes, W, Wc, s0, ns)
+        if npt:  # the barostat moved the boxes: the next segment starts from them
+            boxes = [list(b) for b in ne.ne_ctx_boxes(ctx, nr)]
+    wc = Wc.cpu().numpy().reshape(nr, 2, t_s + 1)
+    a_end = np.array([b[0] / n for b in boxes]) if npt else np.array([])
+    return wc[:, 0], wc[:, 1], a_end
 
 
 def rs_batch(ctx, crystals, T0, seeds, lambda_f, t_eq, t_s, mass, replica_ids=None, chunk=20000,
