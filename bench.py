@@ -272,7 +272,10 @@ def run_ours(args):
     l2 = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device=dev)  # > 129 MB L2
     path = args.path
     if path == "auto":
-        path = "crystal" if prec == ne.NE_MIXED and args.workload in ("fl2", "batched256") else "general"
+        # the crystal runners (cluster runner up to 4096 atoms a replica, brick
+        # runner above) for the mixed crystal workloads; the gradient workload
+        # needs the multi-kernel path's fused backward
+        path = "crystal" if prec == ne.NE_MIXED and args.workload != "grad32" else "general"
     grad = args.workload == "grad32"
     if grad and path == "crystal":
         raise SystemExit("the gradient workload runs on the multi-kernel path")
@@ -388,6 +391,10 @@ def run_ours(args):
 
     roof = None
     clk_sum = clk.summary()
+    runner_kind = None
+    if path == "crystal":
+        runner_kind = "brick" if max(offs[r + 1] - offs[r] for r in range(n_rep)) > ne.CRYSTAL_RUNNER_MAX_ATOMS \
+            else "cluster"
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     if path == "crystal" and kern_ms:
         # the timed call is one persistent launch per size class; its device
@@ -401,7 +408,8 @@ def run_ours(args):
         issued = (OPS_VISIT * visits + OPS_PAIR * pairs + OPS_ATOM * atom_steps) / (kern_ms * 1e-3)
         hbm_peak = measured_peak("hbm_gbs")
         hbm = ALG_BYTES_PER_ATOM_STEP * atom_steps / (kern_ms * 1e-3) / 1e9
-        roof = {"bound": "alu", "kernel": "k_cluster (persistent crystal runner)",
+        roof = {"bound": "alu", "kernel": "k_cluster (persistent cluster runner)" if runner_kind == "cluster"
+                else "k_brick (persistent brick runner, grid barriers)",
                 "achieved": alg / 1e12, "peak": peak / 1e12, "unit": "T lane-ops/s",
                 "frac": alg / peak,
                 # ncu DRAM read + write of one k_cluster launch of this kernel on
@@ -497,7 +505,7 @@ def run_ours(args):
                       "T_K": {"fl2": T_K, "batched256": "300-1600", "rs16": "100 -> 1600 (lambda 1 -> 0.0625)",
                               "grad32": 300.0}[args.workload],
                       "t_eq": t_eq_w, "t_s": t_s_w, "dt_fs": 1.0, "skin_A": mds[0].skin,
-                      "precision": args.prec, "path": path,
+                      "precision": args.prec, "path": path, "runner": runner_kind,
                       "threads_per_atom": 2 if path == "crystal" else args.tpa,
                       "autotune": tuned,
                       "list_builds_per_replica_step": list_builds / (K * n_rep),

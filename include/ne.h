@@ -163,6 +163,19 @@ ne_status ne_ctx_set_tuning(ne_ctx* ctx, int threads_per_atom);
  * C makes a replica's bits independent of the rest of its batch. */
 ne_status ne_ctx_set_cluster_size(ne_ctx* ctx, int ctas);
 
+/* Which persistent runner ne_crystal_run_segment uses (a scheduling choice;
+ * the paper has no counterpart).  0 (the default): the cluster runner --
+ * one thread-block cluster per replica, the whole replica in distributed
+ * shared memory -- when every replica of the batch has at most 4096 atoms,
+ * else the brick runner for the whole batch: one cooperative launch in which
+ * each CTA owns a block of cells of one replica and the CTAs exchange the
+ * displacements and F'(rho) through global memory (L2) between two grid
+ * barriers a step, so a replica may hold up to the device's CTAs x 384
+ * atoms.  1: the cluster runner only (a larger replica is NE_EINVAL).
+ * 2: the brick runner for every batch.  The two give the same trajectories
+ * to the rounding of the replica sums. */
+ne_status ne_ctx_set_runner(ne_ctx* ctx, int runner);
+
 /* Boxes [n_rep][3] (host) at the end of the last multi-kernel run or
  * segment of this context, in the order of its replicas: with the barostat
  * (ne_md_params.npt) the volumes it reached, else the boxes passed in.
@@ -401,8 +414,11 @@ typedef struct {
  * with x0 = the sites of cr[r]: x_dev, v_dev [N][3] (replicas concatenated in
  * order, each in crystal atom order) hold the state at step_begin and are
  * advanced in place; W_dev [n_rep][2] accumulates (forward, backward) work.
- * md[r].prec must be NE_MIXED; at most 4096 atoms per replica, at least 3
- * cells per axis and box edges > 2 r_c + 1.2 A.  Neighbours come from a
+ * md[r].prec must be NE_MIXED; at least 3 cells per axis and box edges
+ * > 2 r_c + 1.2 A; replicas above 4096 atoms run on the brick runner
+ * (ne_ctx_set_runner), which needs the batch's CTAs (one per 96-384 atoms)
+ * to fit the device at once (NE_ENOMEM otherwise); a grid barrier that
+ * waits longer than about a second gives NE_ETIMEOUT.  Neighbours come from a
  * lattice stencil covering displacements up to D = 2 A from the sites (in a
  * small box it holds two periodic images of some sites, at most one of them
  * within r_c); a replica whose atoms stray further is reported as NE_ERANGE.

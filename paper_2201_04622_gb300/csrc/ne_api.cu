@@ -46,6 +46,12 @@ struct CrPlan {
     std::vector<CrGroup> groups;
     std::vector<float4> sv;
     std::vector<float> sd;
+    // brick runner (replicas larger than a cluster holds): one cooperative
+    // launch of n_cta CTAs, tpa threads per atom, CTA -> replica table
+    bool brick = false;
+    int tpa = 0, n_cta = 0, k_lo = 0;
+    size_t smem = 0;
+    std::vector<int> cta_rep;
 };
 
 struct ne_ctx {
@@ -79,6 +85,10 @@ struct ne_ctx {
     Sched lam_sched{};          // the schedule lam_tab holds
     bool lam_valid = false;
     CrPlan plan;                // launch plan of the last crystal-runner batch
+    int runner = 0;             // 0 automatic, 1 cluster runner only, 2 brick runner for every batch
+    ne::BrickBufs bb{};         // brick runner's exchange buffers (allocated on first use)
+    int* cta_rep = nullptr;     // brick runner: replica of each CTA
+    int bb_ctas = 0;            // CTAs the partials buffer holds
     cudaEvent_t ev_run[2] = {}; // around the cluster launches of the last crystal-runner call
     bool run_timed = false;
     cudaStream_t gst[16] = {};  // crystal runner: one stream per replica size class
@@ -665,6 +675,9 @@ ne_status ne_ctx_destroy(ne_ctx* ctx)
         if (ctx->gev[g]) cudaEventDestroy(ctx->gev[g]);
     for (int g = 0; g < 2; ++g)
         if (ctx->ev_run[g]) cudaEventDestroy(ctx->ev_run[g]);
+    void* bptrs[] = {ctx->bb.u4, ctx->bb.fp, ctx->bb.part, ctx->bb.bar, ctx->bb.abortf, ctx->cta_rep};
+    for (void* p : bptrs)
+        if (p) cudaFree(p);
     delete ctx;
     return NE_OK;
 }
@@ -721,6 +734,14 @@ ne_status ne_ctx_set_cluster_size(ne_ctx* ctx, int ctas)
     if (!ctx) return NE_EINVAL;
     if (ctas < 0 || ctas > 16) return fail(ctx, NE_EINVAL, "cluster size must be 0 (automatic) or 1..16");
     ctx->cluster_c = ctas;
+    return NE_OK;
+}
+
+ne_status ne_ctx_set_runner(ne_ctx* ctx, int runner)
+{
+    if (!ctx) return NE_EINVAL;
+    if (runner < 0 || runner > 2) return fail(ctx, NE_EINVAL, "runner must be 0 (automatic), 1 (cluster) or 2 (brick)");
+    ctx->runner = runner;
     return NE_OK;
 }
 
@@ -1230,6 +1251,7 @@ static std::vector<double> plan_key(ne_ctx* ctx, const ne_md_params* md, const n
     k.reserve(2 + 14 * (size_t)n_rep);
     k.push_back((double)n_rep);
     k.push_back((double)ctx->cluster_c);
+    k.push_back((double)ctx->runner);
     for (int r = 0; r < n_rep; ++r) {
         const double rec[] = {(double)cr[r].lattice, cr[r].a, cr[r].c_over_a, (double)cr[r].nx, (double)cr[r].ny,
                               (double)cr[r].nz, md[r].k_spring, md[r].mass, md[r].dt, md[r].damp, md[r].T,
@@ -1264,11 +1286,16 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
             cr[r].ny < 3 || cr[r].nz < 3 || cr[r].c_over_a < 0)
             return fail(ctx, NE_EINVAL, "crystal: bcc/fcc/hcp, a > 0, c/a >= 0 and at least 3 cells per axis");
         const long long nn = (long long)nb * cr[r].nx * cr[r].ny * cr[r].nz;
-        if (nn > 4096)
-            return fail(ctx, NE_EINVAL, "crystal runner: at most 4096 atoms per replica");
+        if (nn > (1 << 24)) return fail(ctx, NE_EINVAL, "crystal: too many atoms");
         off[r + 1] = off[r] + (int)nn;
     }
     if (off[n_rep] > ctx->max_atoms) return fail(ctx, NE_ENOMEM, "atom count exceeds the context");
+    // the cluster runner holds up to 4096 atoms a replica; larger replicas,
+    // or every batch when the context says so, go to the brick runner
+    bool brick = ctx->runner == 2;
+    for (int r = 0; r < n_rep; ++r) brick = brick || off[r + 1] - off[r] > 4096;
+    if (brick && ctx->runner == 1)
+        return fail(ctx, NE_EINVAL, "cluster runner: at most 4096 atoms per replica (the runner setting excludes the brick runner)");
     const double rc = ctx->eam.r_c;
     std::vector<XRep> xr(n_rep);
     std::vector<float4>& sv = P.sv;  // (lattice vector, neighbour code as float bits)
@@ -1411,6 +1438,78 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
         smem = base + (size_t)n_int * 2 * sizeof(float4);
         return true;
     };
+    if (brick) {
+        // Brick runner: the largest threads-per-atom (8, 4, 2) at which every
+        // replica's blocks of cells, one CTA each, fit the device at once
+        int gnb = 0, glut = 0;
+        for (int r = 0; r < n_rep; ++r) {
+            gnb = std::max(gnb, xr[r].nb * xr[r].st_cnt);
+            const int Mr = xr[r].st_margin;
+            glut = std::max(glut, (xr[r].nx + 2 * Mr) * (xr[r].ny + 2 * Mr) + xr[r].nb * (xr[r].nz + 2 * Mr));
+        }
+        P.brick = false;
+        for (int tpa : {8, 4, 2}) {
+            const size_t base = (ne::brick_smem_bytes(tpa, gnb, glut) + 15) & ~(size_t)15;
+            if (base > (size_t)smem_max) continue;
+            const long long fit = ((long long)smem_max - (long long)base) / (2 * (long long)sizeof(float4));
+            const int n_int = (int)std::min<long long>(nk - 1, fit);
+            const size_t smem = base + (size_t)n_int * 2 * sizeof(float4);
+            const int per = ne::brick_atoms_per_cta(tpa);
+            std::vector<int> cr_(n_rep);
+            int total = 0;
+            for (int r = 0; r < n_rep; ++r) {
+                int C = (xr[r].n + per - 1) / per;
+                while ((((xr[r].n + C - 1) / C) + xr[r].nb - 1) / xr[r].nb * xr[r].nb > per) ++C;
+                cr_[r] = C;
+                total += C;
+            }
+            const int cap = ne::brick_max_ctas(tpa, smem);
+            if (total > cap) continue;
+            P.brick = true;
+            P.tpa = tpa;
+            P.n_cta = total;
+            P.smem = smem;
+            P.k_lo = nk - 1 - n_int;
+            P.cta_rep.clear();
+            for (int r = 0; r < n_rep; ++r) {
+                xr[r].cta0 = (int)P.cta_rep.size();
+                xr[r].ncta = cr_[r];
+                xr[r].widx = r;
+                for (int q = 0; q < cr_[r]; ++q) P.cta_rep.push_back(r);
+            }
+            break;
+        }
+        if (!P.brick)
+            return fail(ctx, NE_ENOMEM, "brick runner: the batch needs more CTAs than the device holds at once");
+        // exchange buffers, sized for the context (once)
+        if (!ctx->bb.u4) {
+            const size_t N = (size_t)ctx->max_atoms;
+            NE_CU(cudaMalloc((void**)&ctx->bb.u4, sizeof(float4) * 2 * N));
+            NE_CU(cudaMalloc((void**)&ctx->bb.fp, sizeof(float) * N));
+            NE_CU(cudaMalloc((void**)&ctx->bb.bar, sizeof(unsigned) * 2));
+            NE_CU(cudaMalloc((void**)&ctx->bb.abortf, sizeof(int)));
+        }
+        if (P.n_cta > ctx->bb_ctas) {
+            if (ctx->bb.part) cudaFree(ctx->bb.part);
+            if (ctx->cta_rep) cudaFree(ctx->cta_rep);
+            ctx->bb.part = nullptr;
+            ctx->cta_rep = nullptr;
+            ctx->bb_ctas = 0;
+            NE_CU(cudaMalloc((void**)&ctx->bb.part, sizeof(float) * 2 * 16 * (size_t)P.n_cta));
+            NE_CU(cudaMalloc((void**)&ctx->cta_rep, sizeof(int) * (size_t)P.n_cta));
+            ctx->bb_ctas = P.n_cta;
+        }
+        P.xs = xr;
+        P.groups.clear();
+        NE_CU(cudaMemcpyAsync(ctx->xrep, P.xs.data(), sizeof(XRep) * n_rep, cudaMemcpyHostToDevice, st));
+        NE_CU(cudaMemcpyAsync(ctx->cta_rep, P.cta_rep.data(), sizeof(int) * P.cta_rep.size(), cudaMemcpyHostToDevice, st));
+        NE_CU(cudaMemcpyAsync(ctx->st_vec, sv.data(), sizeof(float4) * sv.size(), cudaMemcpyHostToDevice, st));
+        NE_CU(cudaMemcpyAsync(ctx->st_dist, sd.data(), sizeof(float) * sd.size(), cudaMemcpyHostToDevice, st));
+        P.key = plan_key(ctx, md, cr, n_rep);
+        P.valid = true;
+        return NE_OK;
+    }
+    P.brick = false;
     // Cluster size per replica: the smallest C whose CTAs hold it, unless the
     // caller fixed C (ne_ctx_set_cluster_size).  When every replica needs the
     // same smallest C, a larger C is taken if the device then runs the batch
@@ -1558,6 +1657,20 @@ static ne_status crystal_segment_impl(ne_ctx* ctx, const ne_md_params* md, const
         NE_CU(cudaEventCreate(&ctx->ev_run[1]));
     }
     NE_CU(cudaEventRecord(ctx->ev_run[0], st));
+    if (P.brick) {
+        const long long n_tot = [&] {
+            long long t = 0;
+            for (const XRep& X : P.xs) t = std::max<long long>(t, (long long)X.off + X.n);
+            return t;
+        }();
+        NE_CU(ne::launch_brick(P.tpa, ctx->xrep, ctx->cta_rep, P.n_cta, P.smem, ctx->st_vec, ctx->st_dist, x_dev,
+                               v_dev, W_dev, ctx->status, S, step_begin, n_steps, ctx->tab, ctx->work, P.k_lo,
+                               ctx->lam_tab + step_begin, Wcum_dev, ctx->bb, n_tot, st));
+        ++ctx->cr_launches;
+        NE_CU(cudaEventRecord(ctx->ev_run[1], st));
+        ctx->run_timed = true;
+        return finish(ctx, st);
+    }
     const bool multi = P.groups.size() > 1;
     if (multi) NE_CU(cudaEventRecord(ctx->gev[16], st));
     for (size_t g = 0; g < P.groups.size(); ++g) {

@@ -26,6 +26,7 @@ struct XRep {
     const unsigned char* sp;
     float invM;
     float kfs[NE_MAX_SPECIES_DEV], hdts[NE_MAX_SPECIES_DEV], c2fs[NE_MAX_SPECIES_DEV], mfs[NE_MAX_SPECIES_DEV];
+    int cta0, ncta;       // brick runner: the replica's first CTA in the grid and its CTA count
 };
 
 namespace ne {
@@ -39,4 +40,22 @@ cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, cons
                            const float* st_dist, double* x, double* v, double* W, int* status, const Sched& S,
                            long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
                            int k_lo, double* lam_tab, double* wcum, cudaStream_t st);
+// Brick runner (ne_brick.cu): replicas larger than a cluster holds, one
+// cooperative launch over CTAs that own blocks of cells and exchange u and
+// F' through global memory between grid barriers.
+size_t brick_smem_bytes(int tpa, int nb_nst_max, int lut_max);
+int brick_atoms_per_cta(int tpa);
+int brick_max_ctas(int tpa, size_t smem);  // co-resident CTAs of the launch (0 on error)
+struct BrickBufs {
+    float4* u4;      // [2][N] (u, 0) of every atom, by step parity
+    float* fp;       // [N] F'(rho)
+    float* part;     // [2][n_cta][NPART] per-CTA partial sums, by step parity
+    unsigned* bar;   // [2] grid barrier: arrivals, generation
+    int* abortf;     // a bounded wait gave up: every CTA leaves
+};
+cudaError_t launch_brick(int tpa, const XRep* reps, const int* cta_rep, int n_cta, size_t smem, const float4* st_vec,
+                         const float* st_dist, double* x, double* v, double* W, int* status, const Sched& S,
+                         long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
+                         int k_lo, const double* lam_tab, double* wcum, const BrickBufs& bb, long long n_tot,
+                         cudaStream_t st);
 }  // namespace ne

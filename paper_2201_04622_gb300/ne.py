@@ -27,7 +27,7 @@ NE_PATH_FL, NE_PATH_RS = 0, 1
 
 # every symbol include/ne.h declares
 SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_clone", "ne_ctx_set_theta", "ne_ctx_get_theta",
-           "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_boxes", "ne_ctx_replica_status", "ne_ctx_counters", "ne_ctx_last_run_ms",
+           "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_set_runner", "ne_ctx_boxes", "ne_ctx_replica_status", "ne_ctx_counters", "ne_ctx_last_run_ms",
            "ne_last_error",
            "ne_create_crystal", "ne_create_crystal_ca", "ne_eam_energy_forces", "ne_eam_virial", "ne_eam_energy_forces_noalloc",
            "ne_spring_forces",
@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True):
                 "ne_ctx_get_theta": [p, p, p],
                 "ne_ctx_set_tuning": [p, i],
                 "ne_ctx_set_cluster_size": [p, i],
+                "ne_ctx_set_runner": [p, i],
                 "ne_ctx_boxes": [p, i, p],
                 "ne_ctx_replica_status": [p, i, p],
                 "ne_ctx_counters": [p, p, p, p, p],
@@ -310,6 +311,11 @@ def ne_ctx_replica_status(ctx, n_rep):
 def ne_ctx_set_cluster_size(ctx, ctas):
     """CTAs per cluster of the crystal runner (0: chosen per batch)."""
     _err(ctx, load().ne_ctx_set_cluster_size(ctx, int(ctas)), "ne_ctx_set_cluster_size")
+
+
+def ne_ctx_set_runner(ctx, runner):
+    """0 automatic, 1 cluster runner only, 2 brick runner for every batch."""
+    _err(ctx, load().ne_ctx_set_runner(ctx, int(runner)), "ne_ctx_set_runner")
 
 
 def ne_ctx_counters(ctx):

@@ -31,6 +31,53 @@ def fit_spring_constant(ctx, lattice, a, n, T, mass, prec=ne.NE_MIXED, seed=1, n
     return k, msd
 
 
+def fit_spring_constants(ctx, crystals, Ts, mass, prec=ne.NE_MIXED, seed=1, n_eq=2000, n_samples=500,
+                         stride=10, skin=1.0, device="cuda", replica_ids=None):
+    """One spring per replica of a batch (eq. msd at each replica's own N and
+    T, Sec. III.A: the fit must use the size and temperature of the switching
+    runs), all replicas in one batched run (ne_msd_fit_batched).  crystals:
+    (lattice, a, n) per replica; Ts: one temperature per replica.  Returns
+    numpy (k, msd) arrays."""
+    import torch
+    ids = list(range(len(crystals))) if replica_ids is None else list(replica_ids)
+    x0s, offs, boxes, mds = [], [0], [], []
+    for (lat, a, n), Tr, rid in zip(crystals, Ts, ids):
+        x0, box = crystal_sites(lat, a, n)
+        x0s.append(x0)
+        offs.append(offs[-1] + len(x0))
+        boxes.append(box)
+        mds.append(ne.md_params(T=Tr, mass=mass, skin=skin, prec=prec, seed=seed, replica=rid, fix_cm=1))
+    x0 = torch.tensor(np.concatenate(x0s), dtype=torch.float64, device=device)
+    x, v = x0.clone(), torch.zeros_like(x0)
+    for r, m in enumerate(mds):
+        ne.ne_init_velocities(ctx, m, v[offs[r]:offs[r + 1]])
+    msd, k = ne.ne_msd_fit_batched(ctx, mds, offs, x, v, x0, boxes, n_eq, n_samples, stride)
+    return k, msd
+
+
+def uneven_campaign(ctx, replicas, mass, t_eq, t_s, fit=dict(n_eq=2000, n_samples=500, stride=10), chunk=5000,
+                    device="cuda"):
+    """The uneven-batch workload of the batching pattern: replicas given as
+    dicts (lattice, n, T, seed, replica; workloads.batched_replicas), each
+    with its own spring from eq. msd at its own size and temperature (one
+    batched fit), then one forward and one backward FL switch per replica on
+    the batch advancer (crystal runner, and the multi-kernel path for any
+    replica that leaves its range).  Returns per replica (k, W_f, W_b, F per
+    atom) as a list of dicts."""
+    from . import workloads as WL
+    crystals = [(r["lattice"], WL.A_BCC if r["lattice"] == WL.BCC else WL.A_FCC, r["n"]) for r in replicas]
+    Ts = [r["T"] for r in replicas]
+    ids = [r["replica"] for r in replicas]
+    k, _ = fit_spring_constants(ctx, crystals, Ts, mass, replica_ids=ids, device=device, **fit)
+    Wf, Wb, _ = fl_batch(ctx, crystals, Ts, list(k), [r["seed"] for r in replicas], t_eq, t_s, mass,
+                         runner="auto", chunk=chunk, replica_ids=ids, device=device)
+    out = []
+    for q, ((lat, a, n), Tr) in enumerate(zip(crystals, Ts)):
+        F, se, ed = free_energy(lat, a, n, Tr, mass, k[q], [Wf[q]], [Wb[q]])
+        out.append(dict(k=float(k[q]), W_f=float(Wf[q]), W_b=float(Wb[q]), F=F))
+    return out
+
+
 def fl_batch(ctx, crystals, T, ks, seeds, t_eq, t_s, mass, prec=ne.NE_MIXED, runner="crystal",
              skin=2.6, device="cuda", chunk=None, replica_ids=None):
     """Forward and backward FL works of a batch of crystal replicas.
@@ -89,17 +136,18 @@ class BatchAdvancer:
     mds, crystals, offsets, boxes, x0: as for ne_crystal_run_segment and
     ne_switch_run_segment (x0: the sites, device [N][3]); chunk: steps per
     crystal-runner call (None: the whole range in one call).  `moved` lists
-    the replicas on the multi-kernel path -- from the start, those larger
-    than the crystal runner holds (ne.CRYSTAL_RUNNER_MAX_ATOMS) -- and `log`
-    each call: (path, replicas, first step, steps)."""
+    the replicas on the multi-kernel path, and `log` each call: (path,
+    replicas, first step, steps).  Replicas larger than a cluster holds
+    (ne.CRYSTAL_RUNNER_MAX_ATOMS) run on the library's brick runner with the
+    rest; if the device cannot hold the batch's CTAs at once (NE_ENOMEM), they
+    move to the multi-kernel path instead."""
 
     def __init__(self, ctx, mds, crystals, offsets, boxes, x0, chunk=None):
         import torch
         self.ctx, self.mds, self.crystals = ctx, list(mds), list(crystals)
         self.offs, self.boxes, self.x0 = list(offsets), list(boxes), x0
         self.chunk = chunk
-        self.moved = [r for r in range(len(self.mds))
-                      if self.offs[r + 1] - self.offs[r] > ne.CRYSTAL_RUNNER_MAX_ATOMS]
+        self.moved = []
         self.log = []
         self._ctx_g = None
         self._packed = None
@@ -193,7 +241,16 @@ class BatchAdvancer:
         if not gen:
             # every replica on the crystal runner: one call on the caller's
             # stream, no copies and no extra synchronisation
-            bad = self._crystal(on_c, x, v, W, c0, cn, None)
+            try:
+                bad = self._crystal(on_c, x, v, W, c0, cn, None)
+            except ne.NeError as e:
+                large = [r for r in on_c if self.offs[r + 1] - self.offs[r] > ne.CRYSTAL_RUNNER_MAX_ATOMS]
+                if "NE_ENOMEM" not in str(e) or not large:
+                    raise
+                # the batch's bricks do not fit the device at once: the large
+                # replicas go to the multi-kernel path (nothing has run yet)
+                self.moved = sorted(self.moved + large)
+                return self._advance_chunk(x, v, W, c0, cn)
         else:
             xc, vc, Wc, _, sc = self._gather(on_c, x, v, W) if on_c else (None,) * 5
             xg, vg, Wg, x0g, sg = self._gather(gen, x, v, W)

@@ -464,3 +464,35 @@ def test_rs_batch_on_the_crystal_runner_matches_the_multikernel_path(ctx):
     Fc = WF.rs_free_energy(O.BCC, W.A_BCC, 6, T0, -4.2, lam_f, t_s, cf, cb, grid)
     Fg = WF.rs_free_energy(O.BCC, W.A_BCC, 6, T0, -4.2, lam_f, t_s, gf, gb, grid)
     assert np.abs(np.asarray(Fc) - np.asarray(Fg)).max() < 1e-5
+
+
+def test_uneven_campaign_fits_one_spring_per_replica():
+    """The uneven-batch workload with one spring per replica at its own size
+    and temperature (eq. msd in one batched fit): each batched spring equals
+    the single-replica fit of the same replica (FP64 path, same noise), the
+    springs stiffen as T falls, and the campaign gives a finite F for every
+    replica."""
+    from paper_2201_04622_gb300 import workflow as WF
+    reps = [r for r in W.batched_replicas(64, seed=1) if r["n"] <= 7][:5]
+    big = ne.ne_ctx_create(ne.eam_params(**W.EAM_FE_LIKE), 20000, 8)
+    try:
+        crystals = [(r["lattice"], W.A_BCC if r["lattice"] == W.BCC else W.A_FCC, r["n"]) for r in reps]
+        Ts = [r["T"] for r in reps]
+        fit = dict(n_eq=200, n_samples=40, stride=5)
+        k, msd = WF.fit_spring_constants(big, crystals, Ts, MASS, prec=ne.NE_FP64,
+                                         replica_ids=[r["replica"] for r in reps], **fit)
+        for q, ((lat, a, n), Tr) in enumerate(zip(crystals, Ts)):
+            x0_np, box = WF.crystal_sites(lat, a, n)
+            md = ne.md_params(T=Tr, mass=MASS, skin=1.0, prec=ne.NE_FP64, seed=1, replica=reps[q]["replica"],
+                              fix_cm=1)
+            x0 = torch.tensor(x0_np, dtype=torch.float64, device=DEV)
+            x, v = x0.clone(), torch.zeros_like(x0)
+            ne.ne_init_velocities(big, md, v)
+            m1, k1 = ne.ne_msd_fit(big, md, x, v, x0, box, fit["n_eq"], fit["n_samples"], fit["stride"])
+            assert k[q] == pytest.approx(k1, rel=1e-9) and msd[q] == pytest.approx(m1, rel=1e-9)
+        order = np.argsort(Ts)
+        assert k[order[0]] > k[order[-1]]  # colder replicas are stiffer
+        rows = WF.uneven_campaign(big, reps, MASS, 100, 300, fit=fit, chunk=400)
+        assert len(rows) == len(reps) and all(np.isfinite(r["F"]) for r in rows)
+    finally:
+        ne.ne_ctx_destroy(big)

@@ -221,6 +221,33 @@ def test_reversible_scaling_workload_prefix_against_the_oracle(ctx):
             assert float(Wd[0, 1].item()) == 0.0
 
 
+def test_reversible_scaling_workload_prefix_on_the_brick_runner(ctx):
+    """The same prefix of the reversible-scaling workload on the brick runner
+    (bcc 16^3 is too large for one thread-block cluster, so the crystal
+    runner call takes it there), both seeds in one launch: each work after
+    the prefix within 1e-6 relative of the oracle's, as on the mixed
+    multi-kernel path."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "config4_prefix_works.json")))
+    x0, box = O.create_crystal(O.BCC, g["a"], g["cells"], g["cells"], g["cells"])
+    n = len(x0)
+    mgs, vs = [], []
+    for row in g["rows"]:
+        mo, mg = md_pair(T=g["T0"], k_spring=1.0, path=O.PATH_RS, lambda_f=g["lambda_f"], t_eq=g["t_eq"],
+                         t_s=g["t_s"], seed=row["seed"], replica=row["replica"], prec=ne.NE_MIXED, skin=1.0)
+        mgs.append(mg)
+        vs.append(O.init_velocities(mo, n))
+    nr = len(mgs)
+    x, v = T(np.concatenate([x0] * nr)), T(np.concatenate(vs))
+    Wd = torch.zeros((nr, 2), dtype=torch.float64, device=DEV)
+    crs = [(O.BCC, g["a"], g["cells"], g["cells"], g["cells"])] * nr
+    ne.ne_crystal_run_segment(ctx, mgs, crs, x, v, Wd, 0, g["prefix_steps"])
+    for q, row in enumerate(g["rows"]):
+        assert float(Wd[q, 0].item()) == pytest.approx(row["W_f"], rel=1e-6)
+        assert float(Wd[q, 1].item()) == 0.0
+
+
 def test_potential_from_a_setfl_file_matches_the_oracle(tmp_path):
     """A tabulated single-element setfl file (written here from the analytic
     Fe-like potential) loaded with potentials.load_eam: a context created
