@@ -313,7 +313,8 @@ def run_ours(args):
         # CTAs per cluster, timed on the batch itself before the timed region
         from paper_2201_04622_gb300 import autotune
         best, table = autotune.tune_crystal(ctx, mds, crystals, x, v, Wd, 0, 200)
-        tuned = {"best": best, "candidates": table, "what": "CTAs per cluster of the crystal runner"}
+        tuned = {"best": best, "candidates": table,
+                 "what": "crystal runner (cluster runner at 6-8 CTAs per cluster, or the brick runner)"}
     if path == "general" and args.autotune:
         from paper_2201_04622_gb300 import autotune
         best, table = autotune.tune(ctx, mds, offs, x, v, x0, boxes, Wd, 0, 60,
@@ -393,8 +394,8 @@ def run_ours(args):
     clk_sum = clk.summary()
     runner_kind = None
     if path == "crystal":
-        runner_kind = "brick" if max(offs[r + 1] - offs[r] for r in range(n_rep)) > ne.CRYSTAL_RUNNER_MAX_ATOMS \
-            else "cluster"
+        runner_kind = "brick" if (max(offs[r + 1] - offs[r] for r in range(n_rep)) > ne.CRYSTAL_RUNNER_MAX_ATOMS
+                                  or (tuned and tuned["best"]["runner"] == "brick")) else "cluster"
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     if path == "crystal" and kern_ms:
         # the timed call is one persistent launch per size class; its device

@@ -88,7 +88,7 @@ typedef struct {
     int fix_cm;        /* 1: centre of mass fixed (noise and force means removed) */
     ne_precision prec;
     /* Barostat (Sec. III.C: reversible scaling at P = 0), RS path of the
-     * multi-kernel runs only; 0 = fixed box.  npt = 1, isotropic: each step,
+     * multi-kernel runs and of the cluster runner; 0 = fixed box.  npt = 1, isotropic: each step,
      * after the second drift, ln V takes one step of the overdamped Langevin
      * equation whose stationary density is V^(N'+1) exp(-(lambda U + P0 V)/k_B T)
      * (N' = dof/3) at fixed scaled coordinates:
@@ -177,8 +177,9 @@ ne_status ne_ctx_set_cluster_size(ne_ctx* ctx, int ctas);
 ne_status ne_ctx_set_runner(ne_ctx* ctx, int runner);
 
 /* Boxes [n_rep][3] (host) at the end of the last multi-kernel run or
- * segment of this context, in the order of its replicas: with the barostat
- * (ne_md_params.npt) the volumes it reached, else the boxes passed in.
+ * segment of this context, or of its last crystal-runner call with the
+ * barostat, in the order of its replicas: with the barostat
+ * (ne_md_params.npt) the boxes it reached, else the boxes passed in.
  * NE_EINVAL if n_rep differs from that run's replica count. */
 ne_status ne_ctx_boxes(ne_ctx* ctx, int n_rep, double* boxes_host);
 
@@ -418,7 +419,11 @@ typedef struct {
  * > 2 r_c + 1.2 A; replicas above 4096 atoms run on the brick runner
  * (ne_ctx_set_runner), which needs the batch's CTAs (one per 96-384 atoms)
  * to fit the device at once (NE_ENOMEM otherwise); a grid barrier that
- * waits longer than about a second gives NE_ETIMEOUT.  Neighbours come from a
+ * waits longer than a few seconds gives NE_ETIMEOUT.  The barostat
+ * (md[r].npt, reversible-scaling path) runs on the cluster runner: the box
+ * and the lattice sites scale with it, ne_ctx_boxes reads the boxes the call
+ * reached, and the next segment takes cr[r].a = box edge / cells (and, per
+ * axis, c/a) of that box; the brick runner rejects it (NE_EINVAL).  Neighbours come from a
  * lattice stencil covering displacements up to D = 2 A from the sites (in a
  * small box it holds two periodic images of some sites, at most one of them
  * within r_c); a replica whose atoms stray further is reported as NE_ERANGE.

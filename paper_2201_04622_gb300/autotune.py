@@ -49,13 +49,15 @@ def tune(ctx, mds, offsets, x, v, x0, boxes, W, step_begin=0, n_steps=100,
     return best, table
 
 
-def tune_crystal(ctx, mds, crystals, x, v, W, step_begin=0, n_steps=200, sizes=None):
-    """CTAs per cluster of the crystal runner for a batch: every size from
-    the smallest that holds the largest replica up to 8 (the portable cluster
-    limit), or `sizes`, timed over n_steps of the batch; the fastest is fixed
-    with ne_ctx_set_cluster_size.  Returns (best, table): best =
-    dict(ctas, us_per_step); table = all candidates (a size the device cannot
-    launch is left out).  x, v, W are restored after every trial."""
+def tune_crystal(ctx, mds, crystals, x, v, W, step_begin=0, n_steps=200, sizes=None, brick=True):
+    """The crystal runner for a batch, by timing n_steps of it: the cluster
+    runner at every cluster size from the smallest that holds the largest
+    replica up to 8 (the portable cluster limit), or `sizes`, and (with
+    brick) the brick runner; the fastest is fixed with ne_ctx_set_runner and
+    ne_ctx_set_cluster_size.  Returns (best, table): best = dict(runner,
+    ctas, us_per_step) (ctas 0 for the brick runner); table = all candidates
+    (one the device cannot launch is left out).  x, v, W are restored after
+    every trial."""
     import torch
     per_cta = ne.CRYSTAL_RUNNER_ATOMS_PER_CTA
     n_max = max((2 if int(c[0]) == ne.NE_BCC else 4) * int(c[2]) * int(c[3]) * int(c[4]) for c in crystals)
@@ -64,9 +66,11 @@ def tune_crystal(ctx, mds, crystals, x, v, W, step_begin=0, n_steps=200, sizes=N
     saved = (x.clone(), v.clone(), W.clone())
     batch = ne.CrystalBatch(mds, crystals)
     table = []
+    trials = [("cluster", C) for C in cand] + ([("brick", 0)] if brick else [])
     try:
-        for C in cand:
+        for runner, C in trials:
             try:
+                ne.ne_ctx_set_runner(ctx, 1 if runner == "cluster" else 2)
                 ne.ne_ctx_set_cluster_size(ctx, C)
                 ne.ne_crystal_run_segment(ctx, batch, None, x, v, W, step_begin, min(20, n_steps))  # plan, warm
                 x.copy_(saved[0])
@@ -74,7 +78,7 @@ def tune_crystal(ctx, mds, crystals, x, v, W, step_begin=0, n_steps=200, sizes=N
                 W.copy_(saved[2])
                 ne.ne_crystal_run_segment(ctx, batch, None, x, v, W, step_begin, n_steps)
                 ms = ne.ne_ctx_last_run_ms(ctx)
-                table.append(dict(ctas=C, us_per_step=ms * 1e3 / n_steps))
+                table.append(dict(runner=runner, ctas=C, us_per_step=ms * 1e3 / n_steps))
             except ne.NeError:
                 pass  # too few CTAs for a replica, or more than the device co-schedules
             finally:
@@ -85,7 +89,9 @@ def tune_crystal(ctx, mds, crystals, x, v, W, step_begin=0, n_steps=200, sizes=N
         torch.cuda.synchronize()
     if not table:
         ne.ne_ctx_set_cluster_size(ctx, 0)
-        raise ValueError("no cluster size could run this batch")
+        ne.ne_ctx_set_runner(ctx, 0)
+        raise ValueError("no crystal runner could run this batch")
     best = min(table, key=lambda t: t["us_per_step"])
+    ne.ne_ctx_set_runner(ctx, 1 if best["runner"] == "cluster" else 2)
     ne.ne_ctx_set_cluster_size(ctx, best["ctas"])
     return best, table

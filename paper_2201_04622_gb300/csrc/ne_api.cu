@@ -49,6 +49,7 @@ struct CrPlan {
     // brick runner (replicas larger than a cluster holds): one cooperative
     // launch of n_cta CTAs, tpa threads per atom, CTA -> replica table
     bool brick = false;
+    bool npt = false;  // a replica has the barostat (cluster runner only)
     int tpa = 0, n_cta = 0, k_lo = 0;
     size_t smem = 0;
     std::vector<int> cta_rep;
@@ -89,6 +90,8 @@ struct ne_ctx {
     ne::BrickBufs bb{};         // brick runner's exchange buffers (allocated on first use)
     int* cta_rep = nullptr;     // brick runner: replica of each CTA
     int bb_ctas = 0;            // CTAs the partials buffer holds
+    double* cr_boxes = nullptr; // crystal runner with the barostat: each replica's box at the call's end
+    bool boxes_from_runner = false;
     cudaEvent_t ev_run[2] = {}; // around the cluster launches of the last crystal-runner call
     bool run_timed = false;
     cudaStream_t gst[16] = {};  // crystal runner: one stream per replica size class
@@ -305,6 +308,7 @@ ne_status setup_batch(ne_ctx* ctx, int n_rep, const int* off, const double* boxe
         }
     }
     ctx->last_nrep = n_rep;
+    ctx->boxes_from_runner = false;
     int species_all = 1;
     for (int r = 0; r < n_rep; ++r) species_all &= ctx->rep_h[r].nsp >= 2;
     const int n_tiles = (int)ctx->tile_rep_h.size();
@@ -631,6 +635,7 @@ ne_status ne_ctx_create(const ne_eam_params* eam, int max_atoms, int max_replica
     A(dalloc(&ctx->rebuilds, 1));
     A(dalloc(&ctx->xrep, R));
     A(dalloc(&ctx->work, 2));
+    A(dalloc(&ctx->cr_boxes, 3 * R));
     A(cudaMallocHost((void**)&ctx->status_host, sizeof(int)));
     if (ok) ok = cudaMemset(ctx->work, 0, 2 * sizeof(unsigned long long)) == cudaSuccess;
     A(dalloc(&ctx->st_vec, R * 4 * NE_STENCIL_MAX));
@@ -675,7 +680,7 @@ ne_status ne_ctx_destroy(ne_ctx* ctx)
         if (ctx->gev[g]) cudaEventDestroy(ctx->gev[g]);
     for (int g = 0; g < 2; ++g)
         if (ctx->ev_run[g]) cudaEventDestroy(ctx->ev_run[g]);
-    void* bptrs[] = {ctx->bb.u4, ctx->bb.fp, ctx->bb.part, ctx->bb.bar, ctx->bb.abortf, ctx->cta_rep};
+    void* bptrs[] = {ctx->bb.u4, ctx->bb.fp, ctx->bb.part, ctx->bb.bar, ctx->bb.abortf, ctx->cta_rep, ctx->cr_boxes};
     for (void* p : bptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -749,6 +754,12 @@ ne_status ne_ctx_boxes(ne_ctx* ctx, int n_rep, double* boxes_host)
 {
     if (!ctx || !boxes_host || n_rep < 1) return NE_EINVAL;
     if (n_rep != ctx->last_nrep) return fail(ctx, NE_EINVAL, "replica count differs from the last run");
+    if (ctx->boxes_from_runner) {
+        if (cudaMemcpy(boxes_host, ctx->cr_boxes, sizeof(double) * 3 * (size_t)n_rep, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return fail(ctx, NE_ECUDA, "reading the boxes failed");
+        return NE_OK;
+    }
     std::vector<RepDev> r(n_rep);
     if (cudaMemcpy(r.data(), ctx->rep, sizeof(RepDev) * n_rep, cudaMemcpyDeviceToHost) != cudaSuccess)
         return fail(ctx, NE_ECUDA, "reading the boxes failed");
@@ -1248,14 +1259,15 @@ ne_status ne_crystal_run_segment_cum(ne_ctx* ctx, const ne_md_params* md, const 
 static std::vector<double> plan_key(ne_ctx* ctx, const ne_md_params* md, const ne_crystal* cr, int n_rep)
 {
     std::vector<double> k;
-    k.reserve(2 + 14 * (size_t)n_rep);
+    k.reserve(3 + 19 * (size_t)n_rep);
     k.push_back((double)n_rep);
     k.push_back((double)ctx->cluster_c);
     k.push_back((double)ctx->runner);
     for (int r = 0; r < n_rep; ++r) {
         const double rec[] = {(double)cr[r].lattice, cr[r].a, cr[r].c_over_a, (double)cr[r].nx, (double)cr[r].ny,
                               (double)cr[r].nz, md[r].k_spring, md[r].mass, md[r].dt, md[r].damp, md[r].T,
-                              (double)(md[r].seed & 0xffffffffull), (double)(md[r].seed >> 32), (double)md[r].replica};
+                              (double)(md[r].seed & 0xffffffffull), (double)(md[r].seed >> 32), (double)md[r].replica,
+                              (double)md[r].npt, md[r].P0, md[r].beta_T, md[r].tau_p, (double)md[r].fix_cm};
         k.insert(k.end(), rec, rec + sizeof rec / sizeof rec[0]);
     }
     return k;
@@ -1327,6 +1339,14 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
         X.seed = m.seed;
         X.replica = m.replica;
         if (m.replica >= (1u << 28)) return fail(ctx, NE_EINVAL, "replica id must be < 2^28");
+        X.npt = m.npt;
+        X.dof = m.fix_cm ? 3 * X.n - 3 : 3 * X.n;
+        X.P0 = m.P0;
+        X.mp = m.npt ? m.beta_T / m.tau_p : 0.0;
+        X.kT = kB * m.T;
+        X.box0[0] = X.cell[0] * X.nx;
+        X.box0[1] = X.cell[1] * X.ny;
+        X.box0[2] = X.cell[2] * X.nz;
         if (m.n_species >= 2) {
             // one spring and mass per species (Sec. V): the tables of the
             // multi-kernel path in FP32, the species checked on the host
@@ -1430,7 +1450,7 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
             // the kernel's wrapped-cell tables: (x, y) and, per basis site, z
             glut = std::max(glut, (xr[r].nx + 2 * Mr) * (xr[r].ny + 2 * Mr) + xr[r].nb * (xr[r].nz + 2 * Mr));
         }
-        const size_t base = (ne::cluster_smem_bytes(gn, gnb, glut) + 15) & ~(size_t)15;
+        const size_t base = (ne::cluster_smem_bytes(gn, gnb, glut, P.npt) + 15) & ~(size_t)15;
         if (base > (size_t)smem_max) return false;
         const long long fit = ((long long)smem_max - (long long)base) / (2 * (long long)sizeof(float4));
         const int n_int = (int)std::min<long long>(nk - 1, fit);
@@ -1438,6 +1458,10 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
         smem = base + (size_t)n_int * 2 * sizeof(float4);
         return true;
     };
+    P.npt = false;
+    for (int r = 0; r < n_rep; ++r) P.npt = P.npt || xr[r].npt != 0;
+    if (brick && P.npt)
+        return fail(ctx, NE_EINVAL, "the brick runner keeps the box fixed; the barostat runs on the cluster runner and the multi-kernel path");
     if (brick) {
         // Brick runner: the largest threads-per-atom (8, 4, 2) at which every
         // replica's blocks of cells, one CTA each, fit the device at once
@@ -1631,8 +1655,7 @@ static ne_status crystal_segment_impl(ne_ctx* ctx, const ne_md_params* md, const
     ne_status s = check_batch(ctx, md, n_rep, off.data());
     if (s) return s;
     if (md[0].prec != NE_MIXED) return fail(ctx, NE_EINVAL, "the crystal runner is mixed precision; use ne_switch_run_segment for FP64");
-    for (int r = 0; r < n_rep; ++r)
-        if (md[r].npt) return fail(ctx, NE_EINVAL, "the crystal runner keeps the box fixed; use ne_switch_run_segment for the barostat");
+
     const long long S_total = 2 * md[0].t_eq + 2 * md[0].t_s;
     if (step_begin < 0 || n_steps < 0 || step_begin + n_steps > S_total)
         return fail(ctx, NE_EINVAL, "step range outside the schedule");
@@ -1679,7 +1702,7 @@ static ne_status crystal_segment_impl(ne_ctx* ctx, const ne_md_params* md, const
         if (multi) NE_CU(cudaStreamWaitEvent(gs, ctx->gev[16], 0));
         NE_CU(ne::launch_cluster(ctx->xrep + G.b, G.e - G.b, G.C, G.smem, ctx->st_vec, ctx->st_dist, x_dev, v_dev,
                                  W_dev, ctx->status, S, step_begin, n_steps, ctx->tab, ctx->work, G.k_lo,
-                                 ctx->lam_tab + step_begin, Wcum_dev, gs));
+                                 ctx->lam_tab + step_begin, Wcum_dev, gs, P.npt, ctx->cr_boxes));
         ++ctx->cr_launches;
         if (multi) {
             NE_CU(cudaEventRecord(ctx->gev[g], gs));
@@ -1688,6 +1711,10 @@ static ne_status crystal_segment_impl(ne_ctx* ctx, const ne_md_params* md, const
     }
     NE_CU(cudaEventRecord(ctx->ev_run[1], st));
     ctx->run_timed = true;
+    if (P.npt) {  // ne_ctx_boxes reads the boxes this call reached
+        ctx->boxes_from_runner = true;
+        ctx->last_nrep = n_rep;
+    }
     return finish(ctx, st);
 }
 

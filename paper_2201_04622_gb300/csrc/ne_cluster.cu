@@ -197,11 +197,14 @@ __host__ __device__ inline int atoms_per_cta(int n, int C, int nb)
     return (((n + C - 1) / C) + nb - 1) / nb * nb;
 }
 
+// NPT: the replicas have the barostat of the reversible-scaling path (a
+// separate instantiation, so the fixed-box kernel carries none of it)
+template <bool NPT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_cluster(const XRep* __restrict__ reps, const float4* __restrict__ st_vec, const float* __restrict__ st_dist,
               double* __restrict__ xg, double* __restrict__ vg, double* __restrict__ Wg, int* status, Sched S,
               long long s_begin, long long n_steps, Tables tab, unsigned long long* work, int k_lo,
-              const double* __restrict__ lam_tab, double* __restrict__ wcum)
+              const double* __restrict__ lam_tab, double* __restrict__ wcum, double* __restrict__ boxes_out)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -236,9 +239,16 @@ __global__ void __launch_bounds__(THREADS, 1)
     float2* s_rho = (float2*)(s_f + SLOTS);                       // [SLOTS] double-float
     float* s_slotM = (float*)(s_rho + SLOTS);                     // [2][16] max |u| per CTA
     float* s_red = s_slotM + 32;                                  // [NWARP][NRED][2]
+    // barostat: the diagonal virial of the second pair lane of each slot, the
+    // warps' double-float partials, every CTA's partial (written by the CTA
+    // into all CTAs of the cluster) and the step's scale factors
+    float4* s_vir = (float4*)(((size_t)(s_red + NWARP * NRED * 2) + 15) & ~(size_t)15);  // [SLOTS] (NPT)
+    float* s_vred = (float*)(s_vir + (NPT ? SLOTS : 0));          // [NWARP][6] (NPT)
+    float* s_vcta = s_vred + (NPT ? NWARP * 6 : 0);               // [16][6] (NPT)
+    double* s_mu = (double*)(((size_t)(s_vcta + (NPT ? 16 * 6 : 0)) + 7) & ~(size_t)7);  // [4] (NPT)
     // spline intervals [k_lo, nk - 1) of phi, then of f: separate arrays, so
     // consecutive intervals fall in consecutive 16-byte bank groups
-    float4* s_tabP = (float4*)(((size_t)(s_red + NWARP * NRED * 2) + 15) & ~(size_t)15);  // [nk-1-k_lo]
+    float4* s_tabP = (float4*)(((size_t)(s_mu + (NPT ? 4 : 0)) + 15) & ~(size_t)15);  // [nk-1-k_lo]
     const int n_int = tab.nk - 1 - k_lo;  // intervals of the r grid held in shared memory
     float4* s_tabF = s_tabP + n_int;                                           // [nk-1-k_lo]
     {
@@ -394,6 +404,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         Wacc[1] = Wg[2 * reps[rep].widx + 1];
     }
     double UE_prev = 0.0;  // the work thread: U_E at the positions of the previous step
+    // barostat: the box and the lattice sites scale by mu_tot per axis from
+    // the call's start (every thread holds the same values: they come from
+    // the same sums); stencil vectors are multiplied by it
+    double mu_tot[3] = {1.0, 1.0, 1.0};
+    float muf[3] = {1.f, 1.f, 1.f}, mu_min = 1.f;
 
 #pragma unroll 1
     for (long long it = 0; it <= n_steps; ++it) {
@@ -434,7 +449,16 @@ __global__ void __launch_bounds__(THREADS, 1)
         // replica's result is void, so its cluster stops here instead of
         // scanning the whole stencil for the rest of the range.  Every CTA of
         // the cluster holds the same slot values and leaves at the same step.
-        if (!(umax <= reps[rep].D)) {
+        bool out = !(umax <= reps[rep].D);
+        if constexpr (NPT) {
+            // the scaled stencil must still cover r_c + 2 max|u|, and the box
+            // must keep two periodic images more than 2 r_c apart
+            const float need = ((float)tab.r_c + 2.f * umax) / mu_min - (float)tab.r_c;
+            out = out || !(need <= 2.f * reps[rep].D);
+            for (int c = 0; c < 3; ++c)
+                out = out || !(mu_tot[c] * reps[rep].box0[c] > 2.0 * tab.r_c + 1.2);
+        }
+        if (out) {
             if (threadIdx.x == 0) {
                 const int e = isnan(umax) ? ST_ENAN : ST_ERANGE;
                 ne_set_status(status, e);
@@ -448,11 +472,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         const float4 ui = s_u[sui];
         int m = 0;
         float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
+        float vxx = 0.f, vyy = 0.f, vzz = 0.f;  // diagonal virial (barostat only)
         dfl rho = {0.f, 0.f};
         {
             // every entry with |r0_j - r0_i| < r_c + |u_i| + max |u| (two
             // bins of margin against rounding of the bin index)
-            const float c = sqrtf(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + umax;
+            float c = sqrtf(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + umax;
+            if constexpr (NPT) c = ((float)tab.r_c + c) / mu_min - (float)tab.r_c;  // in lattice units
             const int K = valid ? (int)s_K[skb + min(NKT - 1, (int)(c * inv_dK) + 2)] : 0;
             // rho as an unnormalised double-float: the running FP32 sum rh and
             // the exact rounding error of each addition (TwoSum) summed in rl
@@ -460,10 +486,15 @@ __global__ void __launch_bounds__(THREADS, 1)
             unsigned char* slp = s_sl + lane * SLOTS + slot;  // this thread's short list, stride TPA * SLOTS
 #pragma unroll 8
             for (int k = lane; k < K; k += 2) {
-                const float4 e = s_sv[stb + k];
+                float4 e = s_sv[stb + k];
                 const int code = __float_as_int(e.w);
                 const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
                 const float4 uj = s_u[j];
+                if constexpr (NPT) {
+                    e.x *= muf[0];
+                    e.y *= muf[1];
+                    e.z *= muf[2];
+                }
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 < rc2) {
@@ -505,6 +536,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                     fy += sc * dy;
                     fz += sc * dz;
                     ep += pv;
+                    if constexpr (NPT) {  // -(1/2) r_a^2 / r dU/dr of the pair's half
+                        vxx -= 0.5f * sc * dx * dx;
+                        vyy -= 0.5f * sc * dy * dy;
+                        vzz -= 0.5f * sc * dz * dz;
+                    }
                     // entries past the capacity overwrite the last one; the
                     // overflow is reported after the loop
                     slp[min(m, SLQ - 1) * (TPA * SLOTS)] = (unsigned char)(k / TPA);
@@ -546,10 +582,15 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll 2
             for (int q = 0; q < m; ++q) {
                 const int k = TPA * s_sl[(q * TPA + lane) * SLOTS + slot] + lane;
-                const float4 e = s_sv[stb + k];
+                float4 e = s_sv[stb + k];
                 const int code = __float_as_int(e.w);
                 const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
                 const float4 uj = s_u[j];
+                if constexpr (NPT) {
+                    e.x *= muf[0];
+                    e.y *= muf[1];
+                    e.z *= muf[2];
+                }
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 const float irh = rsqrtf(r2) * inv_h;
@@ -561,10 +602,52 @@ __global__ void __launch_bounds__(THREADS, 1)
                 fx += sc * dx;
                 fy += sc * dy;
                 fz += sc * dz;
+                if constexpr (NPT) {
+                    vxx -= 0.5f * sc * dx * dx;
+                    vyy -= 0.5f * sc * dy * dy;
+                    vzz -= 0.5f * sc * dz * dz;
+                }
             }
             if (valid && lane == 1) s_f[slot] = make_float4(fx, fy, fz, ep);
+            if constexpr (NPT)
+                if (valid && lane == 1) s_vir[slot] = make_float4(vxx, vyy, vzz, 0.f);
         }
         __syncthreads();
+        if constexpr (NPT) {
+            // the diagonal virial of this CTA's atoms at x_s (double-float per
+            // axis: a fixed warp tree, then warp 0 over the warps), written
+            // into every CTA of the cluster before the arrive below
+            const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+            dfl vd[3] = {};
+            if (own) {
+                const float4 v1 = s_vir[threadIdx.x];
+                vd[0] = df_add({vxx, 0.f}, {v1.x, 0.f});
+                vd[1] = df_add({vyy, 0.f}, {v1.y, 0.f});
+                vd[2] = df_add({vzz, 0.f}, {v1.z, 0.f});
+            }
+            if (w < own_warps) {
+                warp_df_sum<3>(vd);
+                if (l == 0)
+                    for (int a3 = 0; a3 < 3; ++a3) {
+                        s_vred[w * 6 + 2 * a3] = vd[a3].hi;
+                        s_vred[w * 6 + 2 * a3 + 1] = vd[a3].lo;
+                    }
+            }
+            __syncthreads();
+            if (w == 0) {
+                dfl t[3];
+                for (int a3 = 0; a3 < 3; ++a3)
+                    t[a3] = l < own_warps ? dfl{s_vred[l * 6 + 2 * a3], s_vred[l * 6 + 2 * a3 + 1]} : dfl{0.f, 0.f};
+                warp_df_sum<3>(t);
+                if (l < C) {
+                    float* d = cluster.map_shared_rank(s_vcta, l) + rank * 6;
+                    for (int a3 = 0; a3 < 3; ++a3) {
+                        d[2 * a3] = t[a3].hi;
+                        d[2 * a3 + 1] = t[a3].lo;
+                    }
+                }
+            }
+        }
 
         // ---------------- fused step of the owned atom
         // This CTA has finished reading u and F' of step s: arrive on the
@@ -639,6 +722,51 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
             }
             asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+            if constexpr (NPT) {
+                if (!fin) {
+                    // the barostat step after the second drift (reading A23): the
+                    // replica's diagonal virial at x_s from the C CTA partials
+                    // (fixed order), then one overdamped Langevin step of ln V
+                    // (isotropic) or of each ln L_a, with the first (or a-th)
+                    // normal of Philox stream 5 at (atom 0, step s)
+                    if (threadIdx.x == 0) {
+                        const XRep& Rb = reps[rep];
+                        double Wa[3];
+                        for (int a3 = 0; a3 < 3; ++a3) {
+                            dfl acc = {0.f, 0.f};
+                            for (int r = 0; r < C; ++r) acc = df_add(acc, {s_vcta[r * 6 + 2 * a3], s_vcta[r * 6 + 2 * a3 + 1]});
+                            Wa[a3] = (double)acc.hi + (double)acc.lo;
+                        }
+                        const double V = mu_tot[0] * Rb.box0[0] * mu_tot[1] * Rb.box0[1] * mu_tot[2] * Rb.box0[2];
+                        const double lam = lam_tab[it + 1], dtd = S.dt;
+                        double z[3];
+                        ne_normals64(ne_philox_block(Rb.seed, Rb.replica, (unsigned)STREAM_BARO, 0u,
+                                                     (unsigned long long)s),
+                                     z);
+                        const double noise = sqrt(2.0 * Rb.kT * Rb.mp * dtd / V);
+                        if (Rb.npt == 2) {
+                            for (int a3 = 0; a3 < 3; ++a3) {
+                                const double drive = (Rb.dof / 3.0 * Rb.kT + lam * Wa[a3]) / V - Rb.P0;
+                                s_mu[a3] = exp(Rb.mp * drive * dtd + noise * z[a3]);
+                            }
+                        } else {
+                            const double drive = (Rb.dof * Rb.kT + lam * (Wa[0] + Wa[1] + Wa[2])) / (3.0 * V) - Rb.P0;
+                            s_mu[0] = s_mu[1] = s_mu[2] = exp((Rb.mp * drive * dtd + noise * z[0]) / 3.0);
+                        }
+                    }
+                    __syncthreads();
+                    for (int a3 = 0; a3 < 3; ++a3) {
+                        const double mu = s_mu[a3];
+                        mu_tot[a3] *= mu;
+                        muf[a3] = (float)mu_tot[a3];
+                        if (own) {  // positions scale about the origin: the displacement from the scaled site by mu
+                            xr[a3] = __double2ll_rn(mu * (double)xr[a3]);
+                            u[a3] = fix_to_float(xr[a3]);
+                        }
+                    }
+                    mu_min = fminf(muf[0], fminf(muf[1], muf[2]));
+                }
+            }
             if (own) {
                 if (!fin) {
                     const float4 uv = make_float4(u[0], u[1], u[2], 0.f);
@@ -687,12 +815,16 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (*s_fail == 0) {
         if (own)
             for (int c = 0; c < 3; ++c) {
-                xg[gi + c] = (double)(xr[c] + site_fix(c)) / XSCALE;
+                // the site of the atom in the (scaled) box
+                const long long site = NPT ? __double2ll_rn(mu_tot[c] * (double)site_fix(c)) : site_fix(c);
+                xg[gi + c] = (double)(xr[c] + site) / XSCALE;
                 vg[gi + c] = (double)v[c];
             }
         if (wthread) {
             Wg[2 * reps[rep].widx] = Wacc[0];
             Wg[2 * reps[rep].widx + 1] = Wacc[1];
+            if (NPT && boxes_out)
+                for (int c = 0; c < 3; ++c) boxes_out[3 * reps[rep].widx + c] = mu_tot[c] * reps[rep].box0[c];
         }
     }
 }
@@ -705,6 +837,7 @@ namespace {
 // needs at least its shared memory and, above 8 CTAs, non-portable cluster
 // sizes): the driver is called only when a launch needs more than was set
 // before on the device.
+template <bool NPT>
 cudaError_t cluster_attributes(int C, size_t smem)
 {
     static std::atomic<int> smem_set[64];
@@ -714,12 +847,12 @@ cudaError_t cluster_attributes(int C, size_t smem)
     if (e != cudaSuccess) return e;
     const bool cached = dev >= 0 && dev < 64;
     if (!cached || smem_set[dev].load() < (int)smem) {
-        e = cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_cluster<NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         if (cached) smem_set[dev].store((int)smem);
     }
     if (C > 8 && (!cached || !nonportable_set[dev].load())) {
-        e = cudaFuncSetAttribute(k_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(k_cluster<NPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
         if (cached) nonportable_set[dev].store(1);
     }
@@ -731,7 +864,7 @@ cudaError_t cluster_attributes(int C, size_t smem)
 namespace ne {
 
 // Bytes of everything but the spline tables; the tables take what is left.
-size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
+size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max, bool npt)
 {
     size_t b = sizeof(float4) * (size_t)n_max + (sizeof(float4) + sizeof(float)) * (size_t)nb_nst_max +
                sizeof(int) * (size_t)lut_max + sizeof(unsigned short) * 4 * NKT + sizeof(unsigned char) * SLOTS * SLMAX;
@@ -739,6 +872,10 @@ size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max)
     b += sizeof(float) * (2 * 16 * NSV + NSV);
     b += 16;  // alignment of s_f
     b += sizeof(float4) * SLOTS + sizeof(float2) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2);
+    if (npt) {  // s_vir, s_vred, s_vcta, s_mu and their alignments
+        b = ((b + 15) & ~(size_t)15) + sizeof(float4) * SLOTS + sizeof(float) * (NWARP * 6 + 16 * 6);
+        b = ((b + 7) & ~(size_t)7) + sizeof(double) * 4;
+    }
     return ((b + 15) & ~(size_t)15) + 16;  // + alignment of the tables
 }
 
@@ -756,7 +893,9 @@ int cluster_atoms_for(int n, int C, int nb) { return atoms_per_cta(n, C, nb); }
 
 int cluster_max_active(int C, size_t smem)
 {
-    if (cluster_attributes(C, smem) != cudaSuccess) {
+    // the barostat instantiation has the same shape; the fixed-box kernel
+    // stands for both in this count
+    if (cluster_attributes<false>(C, smem) != cudaSuccess) {
         (void)cudaGetLastError();  // not a launch error: clear it, the caller reports 0 clusters
         return 0;
     }
@@ -772,7 +911,7 @@ int cluster_max_active(int C, size_t smem)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_cluster, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, k_cluster<false>, &cfg) != cudaSuccess) {
         (void)cudaGetLastError();
         return 0;
     }
@@ -788,9 +927,9 @@ cudaError_t launch_lambda_table(const Sched& S, long long s_begin, long long cou
 cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, const float4* st_vec,
                            const float* st_dist, double* x, double* v, double* W, int* status, const Sched& S,
                            long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
-                           int k_lo, double* lam_tab, double* wcum, cudaStream_t st)
+                           int k_lo, double* lam_tab, double* wcum, cudaStream_t st, bool npt, double* boxes_out)
 {
-    cudaError_t e = cluster_attributes(C, smem);
+    cudaError_t e = npt ? cluster_attributes<true>(C, smem) : cluster_attributes<false>(C, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(n_rep * C, 1, 1);
@@ -804,8 +943,11 @@ cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, cons
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_cluster, reps, st_vec, st_dist, x, v, W, status, S, s_begin, n_steps, tab,
-                              work, k_lo, (const double*)lam_tab, wcum);
+    if (npt)
+        return cudaLaunchKernelEx(&cfg, k_cluster<true>, reps, st_vec, st_dist, x, v, W, status, S, s_begin, n_steps,
+                                  tab, work, k_lo, (const double*)lam_tab, wcum, boxes_out);
+    return cudaLaunchKernelEx(&cfg, k_cluster<false>, reps, st_vec, st_dist, x, v, W, status, S, s_begin, n_steps,
+                              tab, work, k_lo, (const double*)lam_tab, wcum, boxes_out);
 }
 
 }  // namespace ne

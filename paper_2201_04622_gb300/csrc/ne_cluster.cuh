@@ -27,10 +27,16 @@ struct XRep {
     float invM;
     float kfs[NE_MAX_SPECIES_DEV], hdts[NE_MAX_SPECIES_DEV], c2fs[NE_MAX_SPECIES_DEV], mfs[NE_MAX_SPECIES_DEV];
     int cta0, ncta;       // brick runner: the replica's first CTA in the grid and its CTA count
+    // barostat (reversible-scaling path; reading A23): 0 none, 1 isotropic,
+    // 2 one equation per box edge; target pressure, mobility beta_T / tau_p,
+    // k_B T, degrees of freedom and the box at the call's start
+    int npt, dof;
+    double P0, mp, kT;
+    double box0[3];
 };
 
 namespace ne {
-size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max);
+size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max, bool npt = false);
 int cluster_atoms_per_cta();
 int cluster_size_for(int n, int nb);           // smallest CTAs per cluster for an n-atom replica
 int cluster_atoms_for(int n, int C, int nb);    // atoms per CTA of an n-atom replica on C CTAs
@@ -39,7 +45,8 @@ cudaError_t launch_lambda_table(const Sched& S, long long s_begin, long long cou
 cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, const float4* st_vec,
                            const float* st_dist, double* x, double* v, double* W, int* status, const Sched& S,
                            long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
-                           int k_lo, double* lam_tab, double* wcum, cudaStream_t st);
+                           int k_lo, double* lam_tab, double* wcum, cudaStream_t st, bool npt = false,
+                           double* boxes_out = nullptr);
 // Brick runner (ne_brick.cu): replicas larger than a cluster holds, one
 // cooperative launch over CTAs that own blocks of cells and exchange u and
 // F' through global memory between grid barriers.
