@@ -420,10 +420,10 @@ typedef struct {
  * (ne_ctx_set_runner), which needs the batch's CTAs (one per 96-384 atoms)
  * to fit the device at once (NE_ENOMEM otherwise); a grid barrier that
  * waits longer than a few seconds gives NE_ETIMEOUT.  The barostat
- * (md[r].npt, reversible-scaling path) runs on the cluster runner: the box
- * and the lattice sites scale with it, ne_ctx_boxes reads the boxes the call
+ * (md[r].npt, reversible-scaling path) runs on both runners: the box and
+ * the lattice sites scale with it, ne_ctx_boxes reads the boxes the call
  * reached, and the next segment takes cr[r].a = box edge / cells (and, per
- * axis, c/a) of that box; the brick runner rejects it (NE_EINVAL).  Neighbours come from a
+ * axis, c/a) of that box.  Neighbours come from a
  * lattice stencil covering displacements up to D = 2 A from the sites (in a
  * small box it holds two periodic images of some sites, at most one of them
  * within r_c); a replica whose atoms stray further is reported as NE_ERANGE.

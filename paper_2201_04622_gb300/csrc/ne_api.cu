@@ -49,7 +49,7 @@ struct CrPlan {
     // brick runner (replicas larger than a cluster holds): one cooperative
     // launch of n_cta CTAs, tpa threads per atom, CTA -> replica table
     bool brick = false;
-    bool npt = false;  // a replica has the barostat (cluster runner only)
+    bool npt = false;  // a replica has the barostat
     int tpa = 0, n_cta = 0, k_lo = 0;
     size_t smem = 0;
     std::vector<int> cta_rep;
@@ -680,7 +680,8 @@ ne_status ne_ctx_destroy(ne_ctx* ctx)
         if (ctx->gev[g]) cudaEventDestroy(ctx->gev[g]);
     for (int g = 0; g < 2; ++g)
         if (ctx->ev_run[g]) cudaEventDestroy(ctx->ev_run[g]);
-    void* bptrs[] = {ctx->bb.u4, ctx->bb.fp, ctx->bb.part, ctx->bb.bar, ctx->bb.abortf, ctx->cta_rep, ctx->cr_boxes};
+    void* bptrs[] = {ctx->bb.u4, ctx->bb.fp, ctx->bb.part, ctx->bb.vir, ctx->bb.bar, ctx->bb.abortf, ctx->cta_rep,
+                     ctx->cr_boxes};
     for (void* p : bptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -1460,8 +1461,6 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
     };
     P.npt = false;
     for (int r = 0; r < n_rep; ++r) P.npt = P.npt || xr[r].npt != 0;
-    if (brick && P.npt)
-        return fail(ctx, NE_EINVAL, "the brick runner keeps the box fixed; the barostat runs on the cluster runner and the multi-kernel path");
     if (brick) {
         // Brick runner: the largest threads-per-atom (8, 4, 2) at which every
         // replica's blocks of cells, one CTA each, fit the device at once
@@ -1473,7 +1472,7 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
         }
         P.brick = false;
         for (int tpa : {8, 4, 2}) {
-            const size_t base = (ne::brick_smem_bytes(tpa, gnb, glut) + 15) & ~(size_t)15;
+            const size_t base = (ne::brick_smem_bytes(tpa, gnb, glut, P.npt) + 15) & ~(size_t)15;
             if (base > (size_t)smem_max) continue;
             const long long fit = ((long long)smem_max - (long long)base) / (2 * (long long)sizeof(float4));
             const int n_int = (int)std::min<long long>(nk - 1, fit);
@@ -1487,7 +1486,7 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
                 cr_[r] = C;
                 total += C;
             }
-            const int cap = ne::brick_max_ctas(tpa, smem);
+            const int cap = ne::brick_max_ctas(tpa, smem, P.npt);
             if (total > cap) continue;
             P.brick = true;
             P.tpa = tpa;
@@ -1515,11 +1514,14 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
         }
         if (P.n_cta > ctx->bb_ctas) {
             if (ctx->bb.part) cudaFree(ctx->bb.part);
+            if (ctx->bb.vir) cudaFree(ctx->bb.vir);
             if (ctx->cta_rep) cudaFree(ctx->cta_rep);
             ctx->bb.part = nullptr;
+            ctx->bb.vir = nullptr;
             ctx->cta_rep = nullptr;
             ctx->bb_ctas = 0;
             NE_CU(cudaMalloc((void**)&ctx->bb.part, sizeof(float) * 2 * 16 * (size_t)P.n_cta));
+            NE_CU(cudaMalloc((void**)&ctx->bb.vir, sizeof(float) * 6 * (size_t)P.n_cta));
             NE_CU(cudaMalloc((void**)&ctx->cta_rep, sizeof(int) * (size_t)P.n_cta));
             ctx->bb_ctas = P.n_cta;
         }
@@ -1688,10 +1690,14 @@ static ne_status crystal_segment_impl(ne_ctx* ctx, const ne_md_params* md, const
         }();
         NE_CU(ne::launch_brick(P.tpa, ctx->xrep, ctx->cta_rep, P.n_cta, P.smem, ctx->st_vec, ctx->st_dist, x_dev,
                                v_dev, W_dev, ctx->status, S, step_begin, n_steps, ctx->tab, ctx->work, P.k_lo,
-                               ctx->lam_tab + step_begin, Wcum_dev, ctx->bb, n_tot, st));
+                               ctx->lam_tab + step_begin, Wcum_dev, ctx->bb, n_tot, st, P.npt, ctx->cr_boxes));
         ++ctx->cr_launches;
         NE_CU(cudaEventRecord(ctx->ev_run[1], st));
         ctx->run_timed = true;
+        if (P.npt) {  // ne_ctx_boxes reads the boxes this call reached
+            ctx->boxes_from_runner = true;
+            ctx->last_nrep = n_rep;
+        }
         return finish(ctx, st);
     }
     const bool multi = P.groups.size() > 1;

@@ -20,7 +20,11 @@
 //           CTA partials for step s+1
 //   [grid barrier]
 // Two grid barriers a step; u is double-buffered by step parity, so no CTA
-// overwrites a u another still reads.  The barrier is an arrival counter and
+// overwrites a u another still reads.  With the barostat (reading A23, the
+// cluster runner's arithmetic) pass 2 also sums the diagonal virial; the
+// CTA sums go to global memory behind a third grid barrier, after which
+// every CTA of the replica forms the same scale factors (the same sums in
+// the same order, the same Philox normal) before its integration.  The barrier is an arrival counter and
 // a generation word in global memory; every CTA of the launch is resident at
 // once (cooperative launch), and every wait is bounded: after BAR_SPIN_LIMIT
 // polls a CTA records NE_ETIMEOUT, raises the abort word and leaves, and the
@@ -126,13 +130,23 @@ __device__ bool grid_barrier(unsigned* bar, unsigned n_cta, unsigned& gen, int* 
     return *s_flag != 0;
 }
 
-template <int TPA>
+// Sum of three double-float values over the 32 lanes of a warp (fixed tree).
+__device__ __forceinline__ void warp_df3(dfl (&v)[3])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            v[q] = df_add(v[q], {__shfl_xor_sync(0xffffffffu, v[q].hi, o), __shfl_xor_sync(0xffffffffu, v[q].lo, o)});
+}
+
+template <int TPA, bool NPT>
 __global__ void __launch_bounds__(BTHREADS, 1)
     k_brick(const XRep* __restrict__ reps, const int* __restrict__ cta_rep, const float4* __restrict__ st_vec,
             const float* __restrict__ st_dist, double* __restrict__ xg, double* __restrict__ vg,
             double* __restrict__ Wg, int* status, Sched S, long long s_begin, long long n_steps, Tables tab,
             unsigned long long* work, int k_lo, const double* __restrict__ lam_tab, double* __restrict__ wcum,
-            ne::BrickBufs bb, long long n_tot)
+            ne::BrickBufs bb, long long n_tot, double* __restrict__ boxes_out)
 {
     constexpr int SLOTS = BTHREADS / TPA;
     constexpr int SLQ = SLMAX / TPA;
@@ -161,7 +175,17 @@ __global__ void __launch_bounds__(BTHREADS, 1)
     float2* s_rho = (float2*)(s_f + (TPA - 1) * SLOTS);           // [TPA - 1][SLOTS]
     float* s_red = (float*)(s_rho + (TPA - 1) * SLOTS);           // [NWARP][NRED][2]
     int* s_flag = (int*)(s_red + NWARP * NRED * 2);               // [4]
-    float4* s_tabP = (float4*)(((size_t)(s_flag + 4) + 15) & ~(size_t)15);  // [nk - 1 - k_lo]
+    unsigned char* s_end = (unsigned char*)(s_flag + 4);
+    float4* s_vir = nullptr;  // barostat: [TPA - 1][SLOTS] pair-lane virials
+    float* s_vred = nullptr;  // [NWARP][6] warp sums of the virial
+    double* s_mu = nullptr;   // [3] the step's scale factors
+    if constexpr (NPT) {
+        s_vir = (float4*)(((size_t)s_end + 15) & ~(size_t)15);
+        s_vred = (float*)(s_vir + (TPA - 1) * SLOTS);
+        s_mu = (double*)(((size_t)(s_vred + NWARP * 6) + 15) & ~(size_t)15);
+        s_end = (unsigned char*)(s_mu + 4);
+    }
+    float4* s_tabP = (float4*)(((size_t)s_end + 15) & ~(size_t)15);  // [nk - 1 - k_lo]
     const int n_int = tab.nk - 1 - k_lo;
     float4* s_tabF = s_tabP + n_int;
     {
@@ -345,6 +369,11 @@ __global__ void __launch_bounds__(BTHREADS, 1)
     }
     double UE_prev = 0.0;
     bool dead = false;  // the replica left the stencil range: its CTAs keep to the barriers only
+    // barostat: the box and the sites scale by mu_tot per axis from the
+    // call's start (the same values in every CTA of the replica); stencil
+    // vectors are multiplied by it
+    double mu_tot[3] = {1.0, 1.0, 1.0};
+    float muf[3] = {1.f, 1.f, 1.f}, mu_min = 1.f;
 
 #pragma unroll 1
     for (long long it = 0; it <= n_steps && alive; ++it) {
@@ -382,7 +411,15 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             for (int o = 16; o > 0; o >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
             umax = um;
         }
-        if (!dead && !(umax <= R_.D)) {
+        bool out_ = !(umax <= R_.D);
+        if constexpr (NPT) {
+            // the scaled stencil must still cover r_c + 2 max|u|, and the box
+            // must keep two periodic images more than 2 r_c apart
+            const float need = ((float)tab.r_c + 2.f * umax) / mu_min - (float)tab.r_c;
+            out_ = out_ || !(need <= 2.f * R_.D);
+            for (int c = 0; c < 3; ++c) out_ = out_ || !(mu_tot[c] * R_.box0[c] > 2.0 * tab.r_c + 1.2);
+        }
+        if (!dead && out_) {
             // an atom beyond the stencil range: the replica's result is void;
             // every CTA of the replica sees the same sums and stops working
             if (threadIdx.x == 0) {
@@ -397,18 +434,25 @@ __global__ void __launch_bounds__(BTHREADS, 1)
         const float4 ui = dead ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldcg(&u_cur[sui]);
         int m = 0;
         float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
+        float vxx = 0.f, vyy = 0.f, vzz = 0.f;  // diagonal virial (barostat only)
         dfl rho = {0.f, 0.f};
         if (!dead) {
-            const float c = sqrtf(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + umax;
+            float c = sqrtf(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + umax;
+            if constexpr (NPT) c = ((float)tab.r_c + c) / mu_min - (float)tab.r_c;  // in lattice units
             const int K = valid ? (int)s_K[skb + min(NKT - 1, (int)(c * inv_dK) + 2)] : 0;
             float rh = 0.f, rl = 0.f;
             unsigned char* slp = s_sl + lane * SLOTS + slot;
 #pragma unroll 4
             for (int k = lane; k < K; k += TPA) {
-                const float4 e = s_sv[stb + k];
+                float4 e = s_sv[stb + k];
                 const int code = __float_as_int(e.w);
                 const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
                 const float4 uj = __ldcg(&u_cur[j]);
+                if constexpr (NPT) {
+                    e.x *= muf[0];
+                    e.y *= muf[1];
+                    e.z *= muf[2];
+                }
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 < rc2) {
@@ -446,6 +490,11 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                     fy += sc * dy;
                     fz += sc * dz;
                     ep += pv;
+                    if constexpr (NPT) {  // -(1/2) r_a^2 / r dU/dr of the pair's half
+                        vxx -= 0.5f * sc * dx * dx;
+                        vyy -= 0.5f * sc * dy * dy;
+                        vzz -= 0.5f * sc * dz * dz;
+                    }
                     slp[min(m, SLQ - 1) * (TPA * SLOTS)] = (unsigned char)(k / TPA);
                     ++m;
                 }
@@ -485,11 +534,16 @@ __global__ void __launch_bounds__(BTHREADS, 1)
 #pragma unroll 2
             for (int q = 0; q < m; ++q) {
                 const int k = TPA * s_sl[(q * TPA + lane) * SLOTS + slot] + lane;
-                const float4 e = s_sv[stb + k];
+                float4 e = s_sv[stb + k];
                 const int code = __float_as_int(e.w);
                 const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
                 const float4 uj = __ldcg(&u_cur[j]);
                 const float dFj = __ldcg(&fp_r[j]);
+                if constexpr (NPT) {
+                    e.x *= muf[0];
+                    e.y *= muf[1];
+                    e.z *= muf[2];
+                }
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 const float irh = rsqrtf(r2) * inv_h;
@@ -501,10 +555,97 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                 fx += sc * dx;
                 fy += sc * dy;
                 fz += sc * dz;
+                if constexpr (NPT) {
+                    vxx -= 0.5f * sc * dx * dx;
+                    vyy -= 0.5f * sc * dy * dy;
+                    vzz -= 0.5f * sc * dz * dz;
+                }
             }
             if (valid && lane > 0) s_f[(lane - 1) * SLOTS + slot] = make_float4(fx, fy, fz, ep);
+            if constexpr (NPT)
+                if (valid && lane > 0) s_vir[(lane - 1) * SLOTS + slot] = make_float4(vxx, vyy, vzz, 0.f);
         }
         __syncthreads();
+        double mus[3] = {1.0, 1.0, 1.0};  // this step's scale factors (barostat)
+        if constexpr (NPT) {
+            if (!fin) {
+                // the diagonal virial of this CTA's atoms at x_s (double-float
+                // per axis: a fixed warp tree, then warp 0 over the warps) to
+                // global memory; after the barrier warp 0 of every CTA sums the
+                // replica's CTAs in a fixed order and thread 0 takes the
+                // barostat step of the cluster runner
+                const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+                dfl vd[3] = {};
+                if (own && !dead) {
+                    vd[0] = {vxx, 0.f};
+                    vd[1] = {vyy, 0.f};
+                    vd[2] = {vzz, 0.f};
+                    for (int l2 = 1; l2 < TPA; ++l2) {
+                        const float4 v1 = s_vir[(l2 - 1) * SLOTS + threadIdx.x];
+                        vd[0] = df_add(vd[0], {v1.x, 0.f});
+                        vd[1] = df_add(vd[1], {v1.y, 0.f});
+                        vd[2] = df_add(vd[2], {v1.z, 0.f});
+                    }
+                }
+                if (w < own_warps) {
+                    warp_df3(vd);
+                    if (l == 0)
+                        for (int a3 = 0; a3 < 3; ++a3) {
+                            s_vred[w * 6 + 2 * a3] = vd[a3].hi;
+                            s_vred[w * 6 + 2 * a3 + 1] = vd[a3].lo;
+                        }
+                }
+                __syncthreads();
+                if (w == 0) {
+                    dfl t[3];
+                    for (int a3 = 0; a3 < 3; ++a3)
+                        t[a3] = l < own_warps ? dfl{s_vred[l * 6 + 2 * a3], s_vred[l * 6 + 2 * a3 + 1]} : dfl{0.f, 0.f};
+                    warp_df3(t);
+                    if (l == 0)
+                        for (int a3 = 0; a3 < 3; ++a3) {
+                            bb.vir[(size_t)blockIdx.x * 6 + 2 * a3] = t[a3].hi;
+                            bb.vir[(size_t)blockIdx.x * 6 + 2 * a3 + 1] = t[a3].lo;
+                        }
+                }
+                alive = grid_barrier(bb.bar, n_cta, gen, status, bb.abortf, s_flag);  // virials visible
+                if (!alive) break;
+                if (w == 0) {
+                    dfl t[3] = {};
+                    const float* vp = bb.vir + (size_t)R_.cta0 * 6;
+                    for (int r = l; r < C; r += 32)
+                        for (int a3 = 0; a3 < 3; ++a3)
+                            t[a3] = df_add(t[a3], {__ldcg(&vp[r * 6 + 2 * a3]), __ldcg(&vp[r * 6 + 2 * a3 + 1])});
+                    warp_df3(t);
+                    if (l == 0) {
+                        double Wa[3];
+                        for (int a3 = 0; a3 < 3; ++a3) Wa[a3] = (double)t[a3].hi + (double)t[a3].lo;
+                        const double V = mu_tot[0] * R_.box0[0] * mu_tot[1] * R_.box0[1] * mu_tot[2] * R_.box0[2];
+                        const double lam = lam_tab[it + 1], dtd = S.dt;
+                        double z[3];
+                        ne_normals64(ne_philox_block(R_.seed, R_.replica, (unsigned)STREAM_BARO, 0u,
+                                                     (unsigned long long)s),
+                                     z);
+                        const double noise = sqrt(2.0 * R_.kT * R_.mp * dtd / V);
+                        if (R_.npt == 2) {
+                            for (int a3 = 0; a3 < 3; ++a3) {
+                                const double drive = (R_.dof / 3.0 * R_.kT + lam * Wa[a3]) / V - R_.P0;
+                                s_mu[a3] = exp(R_.mp * drive * dtd + noise * z[a3]);
+                            }
+                        } else {  // isotropic; a replica without the barostat has mp = 0: mu = 1
+                            const double drive = (R_.dof * R_.kT + lam * (Wa[0] + Wa[1] + Wa[2])) / (3.0 * V) - R_.P0;
+                            s_mu[0] = s_mu[1] = s_mu[2] = exp((R_.mp * drive * dtd + noise * z[0]) / 3.0);
+                        }
+                    }
+                }
+                __syncthreads();
+                for (int a3 = 0; a3 < 3; ++a3) {
+                    mus[a3] = s_mu[a3];
+                    mu_tot[a3] *= mus[a3];
+                    muf[a3] = (float)mu_tot[a3];
+                }
+                mu_min = fminf(muf[0], fminf(muf[1], muf[2]));
+            }
+        }
 
         // ---- fused step of the owned atom
         if (wthread && !dead) {
@@ -569,6 +710,9 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                         const float dlt = 0.5f * dt * (v1 + v[c]);
                         if (!(fabsf(dlt) < 0.25f)) bad |= ST_ERANGE;
                         xr[c] += (long long)__float2int_rn(dlt * 4294967296.f);
+                        // barostat: positions scale about the origin, so the
+                        // displacement from the scaled site scales by mu
+                        if constexpr (NPT) xr[c] = __double2ll_rn(mus[c] * (double)xr[c]);
                         u[c] = fix_to_float(xr[c]);
                     }
                     ne_normals32(ne_philox_block(R_.seed, R_.replica, (unsigned)S.stream, (unsigned)ta,
@@ -617,27 +761,53 @@ __global__ void __launch_bounds__(BTHREADS, 1)
     if (s_flag[1] == 0) {
         if (own)
             for (int c = 0; c < 3; ++c) {
-                xg[gi + c] = (double)(xr[c] + site_fix(c)) / XSCALE;
+                // the site of the atom in the (scaled) box
+                const long long site = NPT ? __double2ll_rn(mu_tot[c] * (double)site_fix(c)) : site_fix(c);
+                xg[gi + c] = (double)(xr[c] + site) / XSCALE;
                 vg[gi + c] = (double)v[c];
             }
         if (wthread) {
             Wg[2 * R_.widx] = Wacc[0];
             Wg[2 * R_.widx + 1] = Wacc[1];
+            if (NPT && boxes_out)
+                for (int c = 0; c < 3; ++c) boxes_out[3 * R_.widx + c] = mu_tot[c] * R_.box0[c];
         }
     }
 }
 
-template <int TPA>
+template <int TPA, bool NPT>
 cudaError_t brick_attributes(size_t smem)
 {
-    return cudaFuncSetAttribute(k_brick<TPA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(k_brick<TPA, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int TPA, bool NPT>
+cudaError_t brick_occupancy(size_t smem, int* per)
+{
+    cudaError_t e = brick_attributes<TPA, NPT>(smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_brick<TPA, NPT>, BTHREADS, smem);
+    return e;
+}
+
+template <int TPA, bool NPT>
+cudaError_t brick_launch(cudaLaunchConfig_t& cfg, const XRep* reps, const int* cta_rep, const float4* st_vec,
+                         const float* st_dist, double* x, double* v, double* W, int* status, const Sched& S,
+                         long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work, int k_lo,
+                         const double* lam_tab, double* wcum, const ne::BrickBufs& bb, long long n_tot,
+                         double* boxes_out)
+{
+    cudaError_t e = brick_attributes<TPA, NPT>(cfg.dynamicSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaLaunchKernelEx(&cfg, k_brick<TPA, NPT>, reps, cta_rep, st_vec, st_dist, x, v, W, status, S, s_begin,
+                               n_steps, tab, work, k_lo, lam_tab, wcum, bb, n_tot, boxes_out);
+    return e;
 }
 
 }  // namespace
 
 namespace ne {
 
-size_t brick_smem_bytes(int tpa, int nb_nst_max, int lut_max)
+size_t brick_smem_bytes(int tpa, int nb_nst_max, int lut_max, bool npt)
 {
     const size_t slots = (size_t)(BTHREADS / tpa);
     size_t b = (sizeof(float4) + sizeof(float)) * (size_t)nb_nst_max + sizeof(int) * (size_t)lut_max +
@@ -647,12 +817,18 @@ size_t brick_smem_bytes(int tpa, int nb_nst_max, int lut_max)
     b = (b + 15) & ~(size_t)15;
     b += (sizeof(float4) + sizeof(float2)) * (size_t)(tpa - 1) * slots + sizeof(float) * NWARP * NRED * 2 +
          sizeof(int) * 4;
+    if (npt) {  // pair-lane virials, warp sums, scale factors
+        b = (b + 15) & ~(size_t)15;
+        b += sizeof(float4) * (size_t)(tpa - 1) * slots + sizeof(float) * NWARP * 6;
+        b = (b + 15) & ~(size_t)15;
+        b += sizeof(double) * 4;
+    }
     return ((b + 15) & ~(size_t)15) + 16;  // + alignment of the tables
 }
 
 int brick_atoms_per_cta(int tpa) { return BTHREADS / tpa; }
 
-int brick_max_ctas(int tpa, size_t smem)
+int brick_max_ctas(int tpa, size_t smem, bool npt)
 {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -662,18 +838,9 @@ int brick_max_ctas(int tpa, size_t smem)
     }
     cudaError_t e;
     switch (tpa) {
-    case 2:
-        e = brick_attributes<2>(smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_brick<2>, BTHREADS, smem);
-        break;
-    case 4:
-        e = brick_attributes<4>(smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_brick<4>, BTHREADS, smem);
-        break;
-    default:
-        e = brick_attributes<8>(smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_brick<8>, BTHREADS, smem);
-        break;
+    case 2: e = npt ? brick_occupancy<2, true>(smem, &per) : brick_occupancy<2, false>(smem, &per); break;
+    case 4: e = npt ? brick_occupancy<4, true>(smem, &per) : brick_occupancy<4, false>(smem, &per); break;
+    default: e = npt ? brick_occupancy<8, true>(smem, &per) : brick_occupancy<8, false>(smem, &per); break;
     }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -686,8 +853,9 @@ cudaError_t launch_brick(int tpa, const XRep* reps, const int* cta_rep, int n_ct
                          const float* st_dist, double* x, double* v, double* W, int* status, const Sched& S,
                          long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
                          int k_lo, const double* lam_tab, double* wcum, const BrickBufs& bb, long long n_tot,
-                         cudaStream_t st)
+                         cudaStream_t st, bool npt, double* boxes_out)
 {
+    if (npt && !bb.vir) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(bb.bar, 0, 2 * sizeof(unsigned), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bb.abortf, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -701,29 +869,15 @@ cudaError_t launch_brick(int tpa, const XRep* reps, const int* cta_rep, int n_ct
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+#define NE_BRICK_ARGS cfg, reps, cta_rep, st_vec, st_dist, x, v, W, status, S, s_begin, n_steps, tab, work, k_lo, \
+                      lam_tab, wcum, bb, n_tot, boxes_out
     switch (tpa) {
-    case 2:
-        e = brick_attributes<2>(smem);
-        if (e == cudaSuccess)
-            e = cudaLaunchKernelEx(&cfg, k_brick<2>, reps, cta_rep, st_vec, st_dist, x, v, W, status, S, s_begin,
-                                   n_steps, tab, work, k_lo, lam_tab, wcum, bb, n_tot);
-        break;
-    case 4:
-        e = brick_attributes<4>(smem);
-        if (e == cudaSuccess)
-            e = cudaLaunchKernelEx(&cfg, k_brick<4>, reps, cta_rep, st_vec, st_dist, x, v, W, status, S, s_begin,
-                                   n_steps, tab, work, k_lo, lam_tab, wcum, bb, n_tot);
-        break;
-    case 8:
-        e = brick_attributes<8>(smem);
-        if (e == cudaSuccess)
-            e = cudaLaunchKernelEx(&cfg, k_brick<8>, reps, cta_rep, st_vec, st_dist, x, v, W, status, S, s_begin,
-                                   n_steps, tab, work, k_lo, lam_tab, wcum, bb, n_tot);
-        break;
-    default:
-        return cudaErrorInvalidValue;
+    case 2: return npt ? brick_launch<2, true>(NE_BRICK_ARGS) : brick_launch<2, false>(NE_BRICK_ARGS);
+    case 4: return npt ? brick_launch<4, true>(NE_BRICK_ARGS) : brick_launch<4, false>(NE_BRICK_ARGS);
+    case 8: return npt ? brick_launch<8, true>(NE_BRICK_ARGS) : brick_launch<8, false>(NE_BRICK_ARGS);
+    default: return cudaErrorInvalidValue;
     }
-    return e;
+#undef NE_BRICK_ARGS
 }
 
 }  // namespace ne

@@ -49,14 +49,16 @@ cudaError_t launch_cluster(const XRep* reps, int n_rep, int C, size_t smem, cons
                            double* boxes_out = nullptr);
 // Brick runner (ne_brick.cu): replicas larger than a cluster holds, one
 // cooperative launch over CTAs that own blocks of cells and exchange u and
-// F' through global memory between grid barriers.
-size_t brick_smem_bytes(int tpa, int nb_nst_max, int lut_max);
+// F' through global memory between grid barriers; with the barostat (npt)
+// a third grid barrier a step carries the CTAs' virial sums.
+size_t brick_smem_bytes(int tpa, int nb_nst_max, int lut_max, bool npt = false);
 int brick_atoms_per_cta(int tpa);
-int brick_max_ctas(int tpa, size_t smem);  // co-resident CTAs of the launch (0 on error)
+int brick_max_ctas(int tpa, size_t smem, bool npt = false);  // co-resident CTAs of the launch (0 on error)
 struct BrickBufs {
     float4* u4;      // [2][N] (u, 0) of every atom, by step parity
     float* fp;       // [N] F'(rho)
     float* part;     // [2][n_cta][NPART] per-CTA partial sums, by step parity
+    float* vir;      // [n_cta][6] per-CTA diagonal virial (hi, lo per axis; barostat only)
     unsigned* bar;   // [2] grid barrier: arrivals, generation
     int* abortf;     // a bounded wait gave up: every CTA leaves
 };
@@ -64,5 +66,5 @@ cudaError_t launch_brick(int tpa, const XRep* reps, const int* cta_rep, int n_ct
                          const float* st_dist, double* x, double* v, double* W, int* status, const Sched& S,
                          long long s_begin, long long n_steps, const Tables& tab, unsigned long long* work,
                          int k_lo, const double* lam_tab, double* wcum, const BrickBufs& bb, long long n_tot,
-                         cudaStream_t st);
+                         cudaStream_t st, bool npt = false, double* boxes_out = nullptr);
 }  // namespace ne

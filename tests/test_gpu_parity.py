@@ -366,23 +366,21 @@ def test_rs_barostat_segments_continue_the_run(ctx):
 
 def test_barostat_is_rejected_outside_the_rs_runs(ctx):
     """The Einstein crystal has no pressure: the barostat belongs to the
-    reversible-scaling path (NE_EINVAL on the FL path, on both GPU paths);
-    the brick runner keeps the box fixed (NE_EINVAL there too)."""
+    reversible-scaling path (NE_EINVAL on the FL path, on the multi-kernel
+    path and on both crystal runners)."""
     x0, box = O.create_crystal(O.BCC, 2.87, 6, 6, 6)
     _, mg = md_pair(**dict(NPT, path=O.PATH_FL))
     W2 = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
     with pytest.raises(ne.NeError, match="NE_EINVAL"):
         ne.ne_switch_run_segment(ctx, [mg], [0, len(x0)], T(x0), T(x0 * 0), T(x0), [box], W2, 0, 10)
     _, mg = md_pair(prec=ne.NE_MIXED, **dict(NPT, path=O.PATH_FL))
-    with pytest.raises(ne.NeError, match="NE_EINVAL"):
-        ne.ne_crystal_run_segment(ctx, [mg], [(O.BCC, 2.87, 6, 6, 6)], T(x0), T(x0 * 0), W2, 0, 10)
-    _, mg = md_pair(prec=ne.NE_MIXED, **NPT)
-    ne.ne_ctx_set_runner(ctx, 2)
-    try:
-        with pytest.raises(ne.NeError, match="NE_EINVAL"):
-            ne.ne_crystal_run_segment(ctx, [mg], [(O.BCC, 2.87, 6, 6, 6)], T(x0), T(x0 * 0), W2, 0, 10)
-    finally:
-        ne.ne_ctx_set_runner(ctx, 0)
+    for runner in (1, 2):
+        ne.ne_ctx_set_runner(ctx, runner)
+        try:
+            with pytest.raises(ne.NeError, match="NE_EINVAL"):
+                ne.ne_crystal_run_segment(ctx, [mg], [(O.BCC, 2.87, 6, 6, 6)], T(x0), T(x0 * 0), W2, 0, 10)
+        finally:
+            ne.ne_ctx_set_runner(ctx, 0)
 
 
 def test_switch_run_with_graph_chunks(ctx, pot):

@@ -1,5 +1,7 @@
 """The barostat of the reversible-scaling path (Sec. III.C at P = 0; reading
-A23) on the persistent cluster runner: the box and the lattice sites scale
+A23) on the persistent crystal runners (the cluster runner, and the brick
+runner whose CTAs exchange the virial through global memory behind a grid
+barrier): the box and the lattice sites scale
 with the overdamped Langevin step of ln V (isotropic) or of each ln L_a (per
 axis, the paper's fix nph aniso), positions stay in fixed point about the
 scaled sites.  Against the oracle's NPT_ISO and NPT_ANISO runs (same noise),
@@ -48,10 +50,18 @@ def pair(npt, **kw):
     return mo, mg
 
 
+@pytest.fixture(params=[1, 2], ids=["cluster", "brick"])
+def runner(request, ctx):
+    ne.ne_ctx_set_runner(ctx, request.param)
+    yield request.param
+    ne.ne_ctx_set_runner(ctx, 0)
+
+
 @pytest.mark.parametrize("npt,lat,a,cells", [(1, O.BCC, 2.90, (5, 5, 5)), (2, O.HCP, W.A_HCP, (5, 3, 3))])
-def test_runner_barostat_follows_the_oracle(ctx, pot, npt, lat, a, cells):
+def test_runner_barostat_follows_the_oracle(ctx, pot, runner, npt, lat, a, cells):
     """bcc under tension (isotropic) and hcp at the ideal c/a (per axis), 130
-    steps of the RS schedule: box, positions and works follow the oracle."""
+    steps of the RS schedule on either runner: box, positions and works
+    follow the oracle."""
     p, th = pot
     x0, box = O.create_crystal(lat, a, *cells)
     mo, mg = pair(npt)
@@ -71,8 +81,8 @@ def test_runner_barostat_follows_the_oracle(ctx, pot, npt, lat, a, cells):
         assert abs((bg[2] / bg[0]) / (box[2] / box[0]) - 1.0) > 1e-4
 
 
-def test_runner_barostat_matches_the_multikernel_path_and_resumes(ctx):
-    """Two bcc replicas with the isotropic barostat: the runner and the
+def test_runner_barostat_matches_the_multikernel_path_and_resumes(ctx, runner):
+    """Two bcc replicas with the isotropic barostat: either runner and the
     mixed multi-kernel path agree; a run split in two segments, the second
     started at the lattice parameter the first reached (box / cells), gives
     the single call's state to rounding."""
@@ -111,3 +121,42 @@ def test_runner_barostat_matches_the_multikernel_path_and_resumes(ctx):
     assert np.allclose(np.array(ne.ne_ctx_boxes(ctx, 2)), b_run, rtol=1e-6, atol=0)
     assert torch.abs(x3 - x).max().item() < 2e-5
     assert torch.allclose(W3, Wd, rtol=1e-6, atol=1e-5)
+
+
+def test_brick_barostat_on_a_cell_above_the_cluster_limit(ctx, pot):
+    """bcc 14^3 (5488 atoms, more than a cluster holds, so the brick runner
+    takes it with many CTAs whose virial sums meet in global memory) under
+    the isotropic barostat: box, positions and works follow the oracle."""
+    p, th = pot
+    x0, box = O.create_crystal(O.BCC, 2.90, 14, 14, 14)
+    mo, mg = pair(1, t_eq=10, t_s=20)
+    v0 = O.init_velocities(mo, len(x0))
+    ro = O.switch_run(p, th, mo, x0, v0, x0, box)
+    x, v = T(x0), T(v0)
+    Wd = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
+    ne.ne_crystal_run_segment(ctx, [mg], [(O.BCC, 2.90, 14, 14, 14)], x, v, Wd, 0, 60)
+    bg = ne.ne_ctx_boxes(ctx, 1)[0]
+    assert np.abs(np.asarray(bg) / box - 1.0).max() > 1e-4  # the box moved
+    assert np.allclose(bg, ro["box"], rtol=2e-6, atol=0)
+    assert np.abs(x.cpu().numpy() - ro["x"]).max() < 5e-5
+    assert float(Wd[0, 0]) == pytest.approx(ro["W_f"], rel=1e-5, abs=1e-3)
+    assert float(Wd[0, 1]) == pytest.approx(ro["W_b"], rel=1e-5, abs=1e-3)
+
+
+def test_rs_batch_at_zero_pressure_matches_rs_works(ctx):
+    """Reversible scaling at P = 0 (Sec. III.C with the isotropic barostat)
+    from workflow.rs_batch on the crystal runner, in chunks that restart from
+    the lattice parameter reached, against workflow.rs_works on the
+    multi-kernel path (the same seeds and noise streams): F(T) on a 300-600 K
+    grid and the final lattice parameters agree."""
+    from paper_2201_04622_gb300 import workflow as WF
+    lam_f, t_eq, t_s, T0 = 0.5, 200, 2000, 300.0
+    cf, cb, a_c = WF.rs_batch(ctx, [(O.BCC, W.A_BCC, 6)] * 2, T0, [1, 2], lam_f, t_eq, t_s, MASS,
+                              replica_ids=[0, 0], chunk=1500, npt=True)
+    gf, gb, a_g = WF.rs_works(ctx, O.BCC, W.A_BCC, 6, T0, MASS, lam_f, t_eq, t_s, [1, 2], npt=True)
+    assert np.abs(a_c / W.A_BCC - 1.0).max() > 1e-4  # the lattice moved
+    assert np.allclose(a_c, a_g, rtol=1e-4, atol=0)
+    grid = np.linspace(300.0, 600.0, 7)
+    Fc = WF.rs_free_energy(O.BCC, W.A_BCC, 6, T0, -4.2, lam_f, t_s, cf, cb, grid)
+    Fg = WF.rs_free_energy(O.BCC, W.A_BCC, 6, T0, -4.2, lam_f, t_s, gf, gb, grid)
+    assert np.abs(np.asarray(Fc) - np.asarray(Fg)).max() < 1e-4
