@@ -52,8 +52,8 @@ ALG_BYTES_PER_ATOM_STEP = 200
 FLOPS_PER_PAIR_PASS2 = 44    # FP32 lane operations per neighbour pair in pass 2 (multi-kernel path)
 # crystal runner, lane operations (FP32 + INT32) the source issues, for the
 # ratio of issued to algorithmic work:
-OPS_VISIT = 24    # one lattice-stencil entry examined in pass 1
-OPS_PAIR = 62     # one pair inside r_c: spline of f in pass 1 + forces in pass 2
+OPS_VISIT = 26    # one lattice-stencil entry examined in pass 1, and its TMEM word tested in pass 2
+OPS_PAIR = 54     # one pair inside r_c: splines of phi and f in pass 1, embedding force in pass 2
 OPS_ATOM = 120    # per atom-step: F(rho), broadcasts, sums, Philox + Box-Muller, BAOAB
 
 
@@ -414,10 +414,10 @@ def run_ours(args):
                 "achieved": alg / 1e12, "peak": peak / 1e12, "unit": "T lane-ops/s",
                 "frac": alg / peak,
                 # ncu DRAM read + write of one k_cluster launch of this kernel on
-                # this workload (a 301-step launch: 2.22 MB read, 0 written; the
+                # this workload (a 200-step launch: 2.27 MB read, 0 written; the
                 # replica lives on chip, so the figure does not grow with the
                 # steps); null for the other workloads
-                "traffic": 2.22e6 if args.workload == "fl2" else None,
+                "traffic": 2.27e6 if args.workload == "fl2" and runner_kind == "cluster" else None,
                 "kernel_ms": kern_ms, "us_per_step": kern_ms * 1e3 / K,
                 "peak_note": "%d SMs x %d FP32 lanes x %.0f MHz (median SM clock sampled around the "
                              "timed region)" % (n_sm, FP32_LANES_PER_SM, sm_hz / 1e6),

@@ -1419,6 +1419,7 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
         }
         size_t cnt = 0;
         for (int b = 0; b < X.nb; ++b) cnt = std::max(cnt, per[b].size());
+        cnt += NE_STENCIL_PAD;  // a runner may read a few entries past its scan bound
         if (cnt > NE_STENCIL_MAX) return fail(ctx, NE_EINVAL, "stencil too large");
         X.st_cnt = (int)cnt;
         X.st_margin = M;
@@ -1428,8 +1429,8 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
                 if (q < per[b].size()) {
                     sv.push_back(per[b][q].second.first);
                     sd.push_back((float)per[b][q].first);
-                } else {  // padding: beyond any cutoff
-                    sv.push_back(make_float4(0.f, 0.f, 0.f, code_bits((M * LY + M) | (M << 16))));
+                } else {  // padding: a site 1.7e4 A away (outside any cutoff), in the atom's own cell
+                    sv.push_back(make_float4(1e4f, 1e4f, 1e4f, code_bits((M * LY + M) | (M << 16))));
                     sd.push_back(1e30f);
                 }
             }
@@ -1438,6 +1439,11 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
     int dev = 0, smem_max = 0;
     NE_CU(cudaGetDevice(&dev));
     NE_CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    // a cluster-runner CTA takes all of its SM's tensor memory, so no two may
+    // share an SM: their shared memory is at least half of the SM's
+    int smem_sm = 0;
+    NE_CU(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    const size_t smem_floor = (size_t)smem_sm / 2 + 1024;
     const int nk = ctx->eam.n_knots;
     // shared memory of a launch over replicas rs: replica state, stencil,
     // lists and sums, then as many r intervals of the (phi, f) tables,
@@ -1456,8 +1462,8 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
         const long long fit = ((long long)smem_max - (long long)base) / (2 * (long long)sizeof(float4));
         const int n_int = (int)std::min<long long>(nk - 1, fit);
         k_lo = nk - 1 - n_int;
-        smem = base + (size_t)n_int * 2 * sizeof(float4);
-        return true;
+        smem = std::max(base + (size_t)n_int * 2 * sizeof(float4), smem_floor);
+        return smem <= (size_t)smem_max;
     };
     P.npt = false;
     for (int r = 0; r < n_rep; ++r) P.npt = P.npt || xr[r].npt != 0;

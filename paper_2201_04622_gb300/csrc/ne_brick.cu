@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                 const int kk = min((int)t, nk - 2);
                 const float w = t - (float)kk;
                 const float4 g = kk >= k_lo ? s_tabF[kk - k_lo] : __ldg(&tab.pf32[2 * kk + 1]);
-                const float sc = (dFi + dFj) * (g.y + w * (2.f * g.z + 3.f * w * g.w)) * irh;
+                const float sc = (dFi + dFj) * ((g.y + w * (2.f * g.z + 3.f * w * g.w)) * irh);
                 fx += sc * dx;
                 fy += sc * dy;
                 fz += sc * dz;

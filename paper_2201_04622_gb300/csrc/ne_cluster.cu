@@ -55,13 +55,21 @@ namespace {
 constexpr int THREADS = 768;  // 24 warps: six per SMSP, 80 registers a thread
 constexpr int TPA = 2;
 constexpr int SLOTS = THREADS / TPA;  // atoms per CTA (one CTA per SM)
-constexpr int SLMAX = 80;             // short-list entries per atom (SLMAX / TPA per thread)
-constexpr int SLQ = SLMAX / TPA;
-static_assert(NE_STENCIL_MAX / TPA <= 256, "short-list entries are bytes");
+// Tensor memory as per-thread scratch between the pair passes: pass 1
+// leaves f'(r)/r of every stencil visit (0 outside r_c) in TMEM, pass 2
+// reads it back instead of gathering the f table again.  The CTA holds all
+// TM_COLS columns (one CTA per SM); warp w uses TMEM lanes 32 (w mod 4) ..
+// +31 (its sub-partition's) and columns QMAX (w div 4) .. +QMAX-1: visit q
+// of a thread is column q of its lane, stored and loaded FRB at a time.
+// Visits past QMAX (a hot or disordered replica) are recomputed in pass 2.
+constexpr int TM_COLS = 512;
+constexpr int FRB = 8;
 // stencil scan bounds: entries of basis b with |r0_j - r0_i| < r_c + c for
 // c = q * 2D / (NKT - 1), q = 0 .. NKT - 1 (the last: the whole stencil)
 constexpr int NKT = 256;
 constexpr int NWARP = THREADS / 32;
+constexpr int QMAX = TM_COLS / (NWARP / 4) / FRB * FRB;
+static_assert(QMAX >= FRB && (NWARP / 4 + (NWARP % 4 ? 1 : 0)) * QMAX <= TM_COLS, "TMEM columns per warp");
 
 // partial sums broadcast at the end of step s for step s+1: the energies
 // (double-float), then sum u and sum xi for the mean removal (FP32)
@@ -197,6 +205,40 @@ __host__ __device__ inline int atoms_per_cta(int n, int C, int nb)
     return (((n + C - 1) / C) + nb - 1) / nb * nb;
 }
 
+// FRB consecutive TMEM columns of this thread's lane (32x32b shape: thread
+// i of the warp is lane i of the warp's quarter).  The load waits for its
+// data; the registers pass through the wait so no use moves above it.
+__device__ __forceinline__ void tm_st(unsigned taddr, const float (&v)[FRB])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :
+                 : "r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                   "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                   "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tm_ld(unsigned taddr, float (&v)[FRB])
+{
+    unsigned r0, r1, r2, r3, r4, r5, r6, r7;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3), "+r"(r4), "+r"(r5), "+r"(r6), "+r"(r7)
+                 :
+                 : "memory");
+    v[0] = __uint_as_float(r0);
+    v[1] = __uint_as_float(r1);
+    v[2] = __uint_as_float(r2);
+    v[3] = __uint_as_float(r3);
+    v[4] = __uint_as_float(r4);
+    v[5] = __uint_as_float(r5);
+    v[6] = __uint_as_float(r6);
+    v[7] = __uint_as_float(r7);
+}
+
 // NPT: the replicas have the barostat of the reversible-scaling path (a
 // separate instantiation, so the fixed-box kernel carries none of it)
 template <bool NPT>
@@ -228,10 +270,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     int* s_lxy = (int*)(s_sd + nb * nst);                         // [(nx + 2M) * LY]
     int* s_lz = s_lxy + (nx + 2 * M) * LY;                        // [nb][nz + 2M]
     unsigned short* s_K = (unsigned short*)(s_lz + nb * (nz + 2 * M));  // [4][NKT] scan bounds
-    // short list: entry q of thread (slot, lane) at [q][lane][slot], holding
-    // k / TPA of its stencil entry k (k = TPA * entry + lane)
-    unsigned char* s_sl = (unsigned char*)(s_K + 4 * NKT);      // [SLQ][TPA][SLOTS]
-    float* s_slotP = (float*)(((size_t)(s_sl + SLOTS * SLMAX) + 15) & ~(size_t)15);  // [2][16][NSV]
+    float* s_slotP = (float*)(((size_t)(s_K + 4 * NKT) + 15) & ~(size_t)15);  // [2][16][NSV]
     float* s_tot = s_slotP + 2 * 16 * NSV;                        // [NSV] replica totals
     // partial force, pair energy and rho of the second pair lane of each slot
     // (the first lane is the owning thread and keeps its part in registers)
@@ -239,10 +278,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     float2* s_rho = (float2*)(s_f + SLOTS);                       // [SLOTS] double-float
     float* s_slotM = (float*)(s_rho + SLOTS);                     // [2][16] max |u| per CTA
     float* s_red = s_slotM + 32;                                  // [NWARP][NRED][2]
+    unsigned* s_tm = (unsigned*)(s_red + NWARP * NRED * 2);       // [4] TMEM base address
     // barostat: the diagonal virial of the second pair lane of each slot, the
     // warps' double-float partials, every CTA's partial (written by the CTA
     // into all CTAs of the cluster) and the step's scale factors
-    float4* s_vir = (float4*)(((size_t)(s_red + NWARP * NRED * 2) + 15) & ~(size_t)15);  // [SLOTS] (NPT)
+    float4* s_vir = (float4*)(((size_t)(s_tm + 4) + 15) & ~(size_t)15);  // [SLOTS] (NPT)
     float* s_vred = (float*)(s_vir + (NPT ? SLOTS : 0));          // [NWARP][6] (NPT)
     float* s_vcta = s_vred + (NPT ? NWARP * 6 : 0);               // [16][6] (NPT)
     double* s_mu = (double*)(((size_t)(s_vcta + (NPT ? 16 * 6 : 0)) + 7) & ~(size_t)7);  // [4] (NPT)
@@ -318,22 +358,35 @@ __global__ void __launch_bounds__(THREADS, 1)
         return __double2ll_rn(reps[rep].cell[q] * (ic + reps[rep].basis[b][q]) * XSCALE);
     };
     const size_t gi = (size_t)(reps[rep].off + (own ? ta : 0)) * 3;
+    // TMEM: warp 0 takes all columns for the CTA (returned after the step
+    // loop, which every thread leaves at the same step)
+    if (threadIdx.x < 32) {
+        __syncwarp();
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :
+                     : "r"((unsigned)__cvta_generic_to_shared(s_tm)), "r"(TM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     cluster.sync();  // every CTA of the cluster has started: distributed shared memory is usable
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tm_base = *s_tm;
+    const unsigned tm_w = tm_base + ((unsigned)(32 * ((threadIdx.x >> 5) & 3)) << 16) +
+                          (unsigned)(QMAX * (threadIdx.x >> 7));  // this warp's lanes and columns
     const float Dr = reps[rep].D;
     for (int q = threadIdx.x; q < nb * NKT; q += THREADS) {
         const int b = q / NKT, iq = q % NKT;
-        int cnt = nst;
-        if (iq < NKT - 1) {
-            const float cq = (float)tab.r_c + (float)iq * (2.f * Dr / (float)(NKT - 1));
-            int lo = 0, hi = nst;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s_sd[b * nst + mid] < cq) lo = mid + 1;
-                else hi = mid;
-            }
-            cnt = lo;
+        // the last bin holds every real entry (the padding entries at the
+        // end of each basis site's stencil have distance 1e30)
+        const float cq = iq < NKT - 1 ? (float)tab.r_c + (float)iq * (2.f * Dr / (float)(NKT - 1)) : 1e29f;
+        int lo = 0, hi = nst;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_sd[b * nst + mid] < cq) lo = mid + 1;
+            else hi = mid;
         }
-        s_K[q] = (unsigned short)cnt;
+        s_K[q] = (unsigned short)lo;
     }
     const float inv_dK = (float)(NKT - 1) / (2.f * Dr);
 
@@ -467,10 +520,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
         }
 
-        // ---------------- pass 1: density, pair forces and energy, short list
-        // (pair threads); the F'(rho) terms of the forces follow in pass 2
+        // ---------------- pass 1: density, pair forces and energy, f'(r)/r of
+        // every visit to TMEM (pair threads); the F'(rho) terms of the forces
+        // follow in pass 2
         const float4 ui = s_u[sui];
-        int m = 0;
+        int m = 0, K, nq;  // pairs inside r_c; this thread's scan bound; the warp's visits
+        int ql = -1;       // this thread's last visit inside r_c
         float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
         float vxx = 0.f, vyy = 0.f, vzz = 0.f;  // diagonal virial (barostat only)
         dfl rho = {0.f, 0.f};
@@ -479,79 +534,103 @@ __global__ void __launch_bounds__(THREADS, 1)
             // bins of margin against rounding of the bin index)
             float c = sqrtf(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + umax;
             if constexpr (NPT) c = ((float)tab.r_c + c) / mu_min - (float)tab.r_c;  // in lattice units
-            const int K = valid ? (int)s_K[skb + min(NKT - 1, (int)(c * inv_dK) + 2)] : 0;
+            K = valid ? (int)s_K[skb + min(NKT - 1, (int)(c * inv_dK) + 2)] : 0;
+            // every thread of the warp visits up to the warp's largest bound,
+            // in whole batches of FRB (TMEM stores are warp-wide): entries
+            // past a thread's own bound lie outside r_c for it, and the
+            // stencil's NE_STENCIL_PAD far padding entries keep the last
+            // batch inside the array
+            const int Kw = __reduce_max_sync(0xffffffffu, K);
+            nq = Kw > lane ? ((Kw - lane + TPA - 1) / TPA + FRB - 1) / FRB * FRB : 0;
             // rho as an unnormalised double-float: the running FP32 sum rh and
             // the exact rounding error of each addition (TwoSum) summed in rl
             float rh = 0.f, rl = 0.f;
-            unsigned char* slp = s_sl + lane * SLOTS + slot;  // this thread's short list, stride TPA * SLOTS
-#pragma unroll 8
-            for (int k = lane; k < K; k += 2) {
-                float4 e = s_sv[stb + k];
-                const int code = __float_as_int(e.w);
-                const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
-                const float4 uj = s_u[j];
-                if constexpr (NPT) {
-                    e.x *= muf[0];
-                    e.y *= muf[1];
-                    e.z *= muf[2];
-                }
-                const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < rc2) {
-                    const float irh = rsqrtf(r2) * inv_h;  // 1 / (r h)
-                    const float t = r2 * irh;              // r / h >= 0
-                    const int kk = min((int)t, nk - 2);
-                    const float w = t - (float)kk;
-                    // intervals below kchk (r < ~1 A: the shared-memory window
-                    // starts there, and r_min lies below it) are rare: their
-                    // own branch checks r_min and reads global memory
-                    float4 c, g;
-                    if (kk < kchk) {
-                        if (r2 < rmin2) bad |= ST_ERANGE;
-                        if (kk >= k_lo) {
-                            c = s_tabP[kk - k_lo];
-                            g = s_tabF[kk - k_lo];
-                        } else {
-                            c = __ldg(&tab.pf32[2 * kk]);
-                            g = __ldg(&tab.pf32[2 * kk + 1]);
-                        }
-                    } else {
-                        c = s_tabP[kk - k_lo];
-                        g = s_tabF[kk - k_lo];
-                    }
+#pragma unroll 1
+            for (int q0 = 0; q0 < nq; q0 += FRB) {
+                float frv[FRB];
+#pragma unroll
+                for (int uq = 0; uq < FRB; ++uq) {
+                    const int k = lane + TPA * (q0 + uq);
+                    float fr = 0.f;
                     {
-                        const float fv = g.x + w * (g.y + w * (g.z + w * g.w));
-                        const float s_ = rh + fv, bp = s_ - rh;
-                        rl += (rh - (s_ - bp)) + (fv - bp);
-                        rh = s_;
+                        float4 e = s_sv[stb + k];
+                        const int code = __float_as_int(e.w);
+                        const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
+                        const float4 uj = s_u[j];
+                        if constexpr (NPT) {
+                            e.x *= muf[0];
+                            e.y *= muf[1];
+                            e.z *= muf[2];
+                        }
+                        const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < rc2) {
+                            const float irh = rsqrtf(r2) * inv_h;  // 1 / (r h)
+                            const float t = r2 * irh;              // r / h >= 0
+                            const int kk = min((int)t, nk - 2);
+                            const float w = t - (float)kk;
+                            // intervals below kchk (r < ~1 A: the shared-memory window
+                            // starts there, and r_min lies below it) are rare: their
+                            // own branch checks r_min and reads global memory
+                            float4 cf, g;
+                            if (kk < kchk) {
+                                if (r2 < rmin2) bad |= ST_ERANGE;
+                                if (kk >= k_lo) {
+                                    cf = s_tabP[kk - k_lo];
+                                    g = s_tabF[kk - k_lo];
+                                } else {
+                                    cf = __ldg(&tab.pf32[2 * kk]);
+                                    g = __ldg(&tab.pf32[2 * kk + 1]);
+                                }
+                            } else {
+                                cf = s_tabP[kk - k_lo];
+                                g = s_tabF[kk - k_lo];
+                            }
+                            {
+                                // f and df/dw together (Horner with derivative)
+                                float fv = fmaf(g.w, w, g.z), fd = g.w;
+                                fd = fmaf(fd, w, fv);
+                                fv = fmaf(fv, w, g.y);
+                                fd = fmaf(fd, w, fv);
+                                fv = fmaf(fv, w, g.x);
+                                const float s_ = rh + fv, bp = s_ - rh;
+                                rl += (rh - (s_ - bp)) + (fv - bp);
+                                rh = s_;
+                                fr = fd * irh;  // f'(r) / r
+                                ql = q0 + uq;
+                            }
+                            // phi and dphi/dw together (Horner with derivative)
+                            float pv = fmaf(cf.w, w, cf.z), pd = cf.w;
+                            pd = fmaf(pd, w, pv);
+                            pv = fmaf(pv, w, cf.y);
+                            pd = fmaf(pd, w, pv);
+                            pv = fmaf(pv, w, cf.x);
+                            const float sc = pd * irh;
+                            fx += sc * dx;
+                            fy += sc * dy;
+                            fz += sc * dz;
+                            ep += pv;
+                            if constexpr (NPT) {  // -(1/2) r_a^2 / r dU/dr of the pair's half
+                                vxx -= 0.5f * sc * dx * dx;
+                                vyy -= 0.5f * sc * dy * dy;
+                                vzz -= 0.5f * sc * dz * dz;
+                            }
+                            ++m;
+                        }
                     }
-                    // phi and dphi/dw together (Horner with derivative)
-                    float pv = fmaf(c.w, w, c.z), pd = c.w;
-                    pd = fmaf(pd, w, pv);
-                    pv = fmaf(pv, w, c.y);
-                    pd = fmaf(pd, w, pv);
-                    pv = fmaf(pv, w, c.x);
-                    const float sc = pd * irh;
-                    fx += sc * dx;
-                    fy += sc * dy;
-                    fz += sc * dz;
-                    ep += pv;
-                    if constexpr (NPT) {  // -(1/2) r_a^2 / r dU/dr of the pair's half
-                        vxx -= 0.5f * sc * dx * dx;
-                        vyy -= 0.5f * sc * dy * dy;
-                        vzz -= 0.5f * sc * dz * dz;
-                    }
-                    // entries past the capacity overwrite the last one; the
-                    // overflow is reported after the loop
-                    slp[min(m, SLQ - 1) * (TPA * SLOTS)] = (unsigned char)(k / TPA);
-                    ++m;
+                    frv[uq] = fr;
+                }
+                if (q0 < QMAX) {
+                    __syncwarp();
+                    tm_st(tm_w + (unsigned)q0, frv);
                 }
             }
+            __syncwarp();
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");  // the stores land before pass 2 loads
+            nq = __reduce_max_sync(0xffffffffu, ql) + 1;  // pass 2 stops after the warp's last pair
             rho = {rh, rl};
-            n_cand += (K > lane) ? (unsigned)((K - lane + 1) / 2) : 0u;
-            if (m > SLQ) bad |= ST_ENEIGH;
-            m = min(m, SLQ);
-            n_pair += (unsigned)m;
+            n_cand += valid ? (unsigned)nq : 0u;
+            n_pair += valid ? (unsigned)m : 0u;
             ep *= 0.5f;  // each pair energy is shared by the two atoms
             if (valid && lane == 1) s_rho[slot] = make_float2(rho.hi, rho.lo);
         }
@@ -575,13 +654,45 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         cluster.sync();  // F' visible everywhere
 
-        // ---------------- pass 2: embedding forces (F'_i + F'_j) f'(r) over
-        // the short list (pair threads)
+        // ---------------- pass 2: embedding forces (F'_i + F'_j) f'(r) r_ij / r
+        // over the visits of pass 1, f'(r)/r from TMEM (pair threads)
         {
             const float dFi = s_u[sui].w;
-#pragma unroll 2
-            for (int q = 0; q < m; ++q) {
-                const int k = TPA * s_sl[(q * TPA + lane) * SLOTS + slot] + lane;
+            const int nqt = min(nq, QMAX);
+#pragma unroll 1
+            for (int q0 = 0; q0 < nqt; q0 += FRB) {
+                float frv[FRB];
+                __syncwarp();
+                tm_ld(tm_w + (unsigned)q0, frv);
+#pragma unroll
+                for (int uq = 0; uq < FRB; ++uq) {
+                    if (frv[uq] != 0.f) {  // inside r_c (f' vanishes only at r_c)
+                        const int k = lane + TPA * (q0 + uq);
+                        float4 e = s_sv[stb + k];
+                        const int code = __float_as_int(e.w);
+                        const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
+                        const float4 uj = s_u[j];
+                        if constexpr (NPT) {
+                            e.x *= muf[0];
+                            e.y *= muf[1];
+                            e.z *= muf[2];
+                        }
+                        const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
+                        const float sc = (dFi + uj.w) * frv[uq];
+                        fx += sc * dx;
+                        fy += sc * dy;
+                        fz += sc * dz;
+                        if constexpr (NPT) {
+                            vxx -= 0.5f * sc * dx * dx;
+                            vyy -= 0.5f * sc * dy * dy;
+                            vzz -= 0.5f * sc * dz * dz;
+                        }
+                    }
+                }
+            }
+            // visits past the TMEM columns: the pair recomputed
+            for (int q = QMAX; q < nq; ++q) {
+                const int k = lane + TPA * q;
                 float4 e = s_sv[stb + k];
                 const int code = __float_as_int(e.w);
                 const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
@@ -593,12 +704,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < rc2)) continue;
                 const float irh = rsqrtf(r2) * inv_h;
                 const float t = r2 * irh;
                 const int kk = min((int)t, nk - 2);
                 const float w = t - (float)kk;
                 const float4 g = kk >= k_lo ? s_tabF[kk - k_lo] : __ldg(&tab.pf32[2 * kk + 1]);
-                const float sc = (dFi + uj.w) * (g.y + w * (2.f * g.z + 3.f * w * g.w)) * irh;
+                const float sc = (dFi + uj.w) * ((g.y + w * (2.f * g.z + 3.f * w * g.w)) * irh);
                 fx += sc * dx;
                 fy += sc * dy;
                 fz += sc * dz;
@@ -790,6 +902,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                                         s_slotM + ((s + 1) & 1) * 16, rank, C, own_warps);
         }
     }
+    // every warp is past its last TMEM access: return the columns
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm_base), "r"(TM_COLS) : "memory");
+    }
     if (bad) {
         ne_set_status(status, bad);
         ne_set_status(status + 1 + reps[rep].widx, bad);
@@ -867,11 +987,12 @@ namespace ne {
 size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max, bool npt)
 {
     size_t b = sizeof(float4) * (size_t)n_max + (sizeof(float4) + sizeof(float)) * (size_t)nb_nst_max +
-               sizeof(int) * (size_t)lut_max + sizeof(unsigned short) * 4 * NKT + sizeof(unsigned char) * SLOTS * SLMAX;
+               sizeof(int) * (size_t)lut_max + sizeof(unsigned short) * 4 * NKT;
     b = (b + 15) & ~(size_t)15;
     b += sizeof(float) * (2 * 16 * NSV + NSV);
     b += 16;  // alignment of s_f
-    b += sizeof(float4) * SLOTS + sizeof(float2) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2);
+    b += sizeof(float4) * SLOTS + sizeof(float2) * SLOTS + sizeof(float) * (32 + NWARP * NRED * 2) +
+         sizeof(unsigned) * 4;
     if (npt) {  // s_vir, s_vred, s_vcta, s_mu and their alignments
         b = ((b + 15) & ~(size_t)15) + sizeof(float4) * SLOTS + sizeof(float) * (NWARP * 6 + 16 * 6);
         b = ((b + 7) & ~(size_t)7) + sizeof(double) * 4;

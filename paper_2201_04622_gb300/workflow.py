@@ -393,9 +393,10 @@ def size_scaling(ctx, lattice, a, sizes, T, mass, k, seeds, t_eq, t_s, **kw):
     """F(N) for n^3 cells (the finite-size study of Sec. IV.A), all sizes and
     seeds in one batch, and a straight-line fit in 1/N: returns the rows and
     (F at 1/N -> 0, slope).  k: one spring for every size, or one per size.
-    With runner="auto" (fl_batch) cells larger than the crystal runner holds
-    run on the multi-kernel path alongside it, so the sizes can reach the
-    paper's ~1.1e4 atoms (bcc 18^3)."""
+    With runner="auto" (fl_batch) a batch holding cells larger than a
+    cluster holds runs on the brick runner (those cells move to the
+    multi-kernel path if the batch's CTAs do not fit the device at once), so
+    the sizes can reach the paper's ~1.1e4 atoms (bcc 18^3)."""
     ks = list(k) if np.ndim(k) else [k] * len(sizes)
     crystals = [(lattice, a, m) for m in sizes for _ in seeds]
     kr = [kq for kq in ks for _ in seeds]
@@ -451,12 +452,18 @@ def rs_works(ctx, lattice, a, n, T0, mass, lambda_f, t_eq, t_s, seeds, prec=ne.N
 
 
 def rs_batch(ctx, crystals, T0, seeds, lambda_f, t_eq, t_s, mass, replica_ids=None, chunk=20000,
-             device="cuda"):
+             device="cuda", npt=False, beta_T=1.2, tau_p=0.5):
     """Reversible scaling (Sec. III.C) for a batch of crystal replicas on the
-    crystal runner at fixed volume: per replica, t_eq steps at lambda = 1, the
-    switch to lambda_f over t_s steps, t_eq steps there and the switch back, at
-    T0 (one value or one per replica).  Returns the cumulative works
-    [n_rep][t_s + 1] (forward, backward) for eq. rs (rs_free_energy)."""
+    crystal runners (the cluster runner, or the brick runner for replicas
+    above ne.CRYSTAL_RUNNER_MAX_ATOMS): per replica, t_eq steps at
+    lambda = 1, the switch to lambda_f over t_s steps, t_eq steps there and
+    the switch back, at T0 (one value or one per replica), in the box of the
+    given lattice parameter or, with npt, at zero pressure under the
+    isotropic barostat (beta_T, tau_p: its coupling; each chunk starts from
+    the lattice parameter the last one reached).  Returns the cumulative
+    works [n_rep][t_s + 1] (forward, backward) for eq. rs (rs_free_energy)
+    and the final lattice parameters (box edge / cells; the given ones
+    without npt)."""
     import torch
     n = len(crystals)
     ids = list(range(n)) if replica_ids is None else list(replica_ids)
@@ -468,7 +475,8 @@ def rs_batch(ctx, crystals, T0, seeds, lambda_f, t_eq, t_s, mass, replica_ids=No
         offs.append(offs[-1] + len(x0))
         crs.append((lat, a, nc, nc, nc))
         mds.append(ne.md_params(T=Tr, mass=mass, k_spring=1.0, prec=ne.NE_MIXED, path=ne.NE_PATH_RS,
-                                lambda_f=lambda_f, t_eq=t_eq, t_s=t_s, seed=seed, replica=ids[r], fix_cm=1))
+                                lambda_f=lambda_f, t_eq=t_eq, t_s=t_s, seed=seed, replica=ids[r], fix_cm=1,
+                                npt=int(bool(npt)), P0=0.0, beta_T=beta_T, tau_p=tau_p))
     x = torch.tensor(np.concatenate(x0s), dtype=torch.float64, device=device)
     v = torch.zeros_like(x)
     for r, m in enumerate(mds):
@@ -478,8 +486,10 @@ def rs_batch(ctx, crystals, T0, seeds, lambda_f, t_eq, t_s, mass, replica_ids=No
     S = 2 * t_eq + 2 * t_s
     for s0 in range(0, S, chunk or S):
         ne.ne_crystal_run_segment_cum(ctx, mds, crs, x, v, W, Wc, s0, min(chunk or S, S - s0))
+        if npt:  # the barostat moved the boxes: the next chunk starts from their lattice parameter
+            crs = [(c[0], b[0] / c[2], c[2], c[3], c[4]) for c, b in zip(crs, ne.ne_ctx_boxes(ctx, n))]
     wc = Wc.cpu().numpy().reshape(n, 2, t_s + 1)
-    return wc[:, 0], wc[:, 1]
+    return wc[:, 0], wc[:, 1], np.array([c[1] for c in crs])
 
 
 def rs_free_energy(lattice, a, n, T0, F0_T0_per_atom, lambda_f, t_s, Wcum_f, Wcum_b, T_grid):

@@ -458,7 +458,7 @@ def test_rs_batch_on_the_crystal_runner_matches_the_multikernel_path(ctx):
     per atom (the trajectories stay synchronised over 4,400 steps)."""
     from paper_2201_04622_gb300 import workflow as WF
     lam_f, t_eq, t_s, T0 = 0.5, 200, 2000, 300.0
-    cf, cb = WF.rs_batch(ctx, [(O.BCC, W.A_BCC, 6)] * 2, T0, [1, 2], lam_f, t_eq, t_s, MASS, replica_ids=[0, 0])
+    cf, cb, _ = WF.rs_batch(ctx, [(O.BCC, W.A_BCC, 6)] * 2, T0, [1, 2], lam_f, t_eq, t_s, MASS, replica_ids=[0, 0])
     gf, gb, _ = WF.rs_works(ctx, O.BCC, W.A_BCC, 6, T0, MASS, lam_f, t_eq, t_s, [1, 2])
     grid = np.linspace(300.0, 600.0, 7)
     Fc = WF.rs_free_energy(O.BCC, W.A_BCC, 6, T0, -4.2, lam_f, t_s, cf, cb, grid)
