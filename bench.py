@@ -468,9 +468,9 @@ def run_ours(args):
             # forward kernels (same launches without the backward)
             roof["backward_ms_per_step"] = ms / K - sum(per.values())
     steps_per_graph = 32
-    general_launches = 5 * K + (K - 1) // steps_per_graph + 10
+    general_launches = 6 * K + (K - 1) // steps_per_graph + 10  # list prep, bin, list, pass 1, pass 2, step
     if path == "crystal":
-        launches = (c1[3] - c0[3]) + sum(5 * e[3] + e[3] // steps_per_graph + 10
+        launches = (c1[3] - c0[3]) + sum(6 * e[3] + e[3] // steps_per_graph + 10
                                          for e in timed_log if e[0] == "general")
     else:
         launches = general_launches + (2 * (K + 1) if grad else 0)  # backward: bins + reduction per step

@@ -353,14 +353,14 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
     }
     __syncthreads();
     if (s_last) {
-        // Last tile of this replica: fixed-order sums of every tile partial.
+        // Last tile of this replica: fixed-order sums of every tile partial,
+        // one warp per quantity (a replica of 65,536 atoms has 1,024 tiles)
         __threadfence();
-        for (int q = threadIdx.x; q < NTOT; q += blockDim.x) {
-            double acc = 0.0;
-            for (int t = P.tile0; t < P.tile0 + P.ntile; ++t)
-                acc += q < NPA ? __ldcg(&B.partA[(size_t)t * NPA + q])
-                               : __ldcg(&B.partB[(size_t)t * NPB + (q - NPA)]);
-            B.tot[(size_t)rep * NTOT + q] = acc;
+        const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int q = w; q < NTOT; q += nw) {
+            const double acc = q < NPA ? ne_warp_tile_sum(B.partA, NPA, q, P.tile0, P.ntile)
+                                       : ne_warp_tile_sum(B.partB, NPB, q - NPA, P.tile0, P.ntile);
+            if ((threadIdx.x & 31) == 0) B.tot[(size_t)rep * NTOT + q] = acc;
         }
         if (threadIdx.x == 0) B.tile_done[rep] = 0u;
     }
@@ -408,10 +408,22 @@ __device__ __forceinline__ double bwd_weight(const BwdWeight& W)
 
 // Mixed precision: FP32 basis weights accumulated in shared-memory FP32 bins
 // per block, flushed to bins[block][3*nk*2]; k_bins_reduce then sums the
-// blocks in FP64 in fixed order.
+// blocks in FP64 in fixed order.  Bins are function-major, then value/slope,
+// then knot (bin_index), so the lanes of a warp adding one basis weight at
+// random intervals spread over all 32 banks (knot-major pairs used 16).  The bins take 120 KB, so a block is the
+// SM's only one: it has BWD_THREADS threads and works on BWD_THREADS /
+// (NE_TILE * TPA) tiles at once, enough warps to hide the atomics' latency.
+constexpr int BWD_THREADS = 1024;
+
+// bin of knot parameter (function fn, knot k, c = 0 value / 1 slope); the
+// knot parameters theta themselves are [fn][k][c]
+__host__ __device__ __forceinline__ int bin_index(int fn, int k, int c, int nk) { return (2 * fn + c) * nk + k; }
+
 template <int TPA>
-__global__ void __launch_bounds__(NE_TILE* TPA) k_backward_mixed(DevBatch B, float* __restrict__ bins, BwdWeight W)
+__global__ void __launch_bounds__(BWD_THREADS, 1)
+    k_backward_mixed(DevBatch B, float* __restrict__ bins, BwdWeight W)
 {
+    constexpr int TPB = NE_TILE * TPA, TILES = BWD_THREADS / TPB;
     if (bwd_weight(W) == 0.0) return;
     extern __shared__ float sb[];
     const int nk = B.tab.nk;
@@ -420,10 +432,11 @@ __global__ void __launch_bounds__(NE_TILE* TPA) k_backward_mixed(DevBatch B, flo
     __syncthreads();
     const float h_r = (float)B.tab.h_r, inv_h = B.tab.inv_h_rf;
     const float h_rho = (float)B.tab.h_rho;
-    for (int tile = blockIdx.x; tile < B.n_tiles; tile += gridDim.x) {
+    const int sub = threadIdx.x / TPB, tt = threadIdx.x % TPB;
+    for (int tile = blockIdx.x * TILES + sub; tile < B.n_tiles; tile += gridDim.x * TILES) {
         const int rep = B.tile_rep[tile];
         const RepDev& P = B.rep[rep];
-        const int local = threadIdx.x / TPA, lane = threadIdx.x % TPA;
+        const int local = tt / TPA, lane = tt % TPA;
         const int a = (tile - P.tile0) * NE_TILE + local;
         if (a < P.n) {
             const int i = P.off + a;
@@ -432,7 +445,12 @@ __global__ void __launch_bounds__(NE_TILE* TPA) k_backward_mixed(DevBatch B, flo
             float4 pi = B.posF[i];
             const float dFi = pi.w;
             const int m = B.scnt[i * TPA + lane];
-            for (int q = 0; q < m; ++q) {
+            // each atom of a warp starts at another point of its list: lists
+            // run through the neighbour shells in the same order, so in step
+            // they would send the warp's weights to the same bins at once
+            const int rot = m > 0 ? (local * 7) % m : 0;
+            for (int qq = 0; qq < m; ++qq) {
+                const int q = qq + rot < m ? qq + rot : qq + rot - m;
                 const int jn = B.sl[(q * B.n_tot + i) * TPA + lane];
                 float4 pj = B.posF[jn];
                 float dx = mi(pj.x - pi.x, Lf0, iL0), dy = mi(pj.y - pi.y, Lf1, iL1),
@@ -442,11 +460,10 @@ __global__ void __launch_bounds__(NE_TILE* TPA) k_backward_mixed(DevBatch B, flo
                 int kk = min(max((int)t, 0), nk - 2);
                 float w[4];
                 hermite_wf(t - (float)kk, h_r, w);
-                float* bphi = sb + 2 * kk;
-                float* bf = sb + 2 * nk + 2 * kk;
+                // w = (y_kk, m_kk, y_kk+1, m_kk+1) weights
                 for (int c = 0; c < 4; ++c) {
-                    atomicAdd(bphi + c, 0.5f * w[c]);
-                    atomicAdd(bf + c, dFi * w[c]);
+                    atomicAdd(sb + bin_index(0, kk + (c >> 1), c & 1, nk), 0.5f * w[c]);
+                    atomicAdd(sb + bin_index(1, kk + (c >> 1), c & 1, nk), dFi * w[c]);
                 }
             }
             if (lane == 0) {
@@ -454,8 +471,7 @@ __global__ void __launch_bounds__(NE_TILE* TPA) k_backward_mixed(DevBatch B, flo
                 int kk = min(max((int)t, 0), nk - 2);
                 float w[4];
                 hermite_wf((float)(t - kk), h_rho, w);
-                float* bF = sb + 4 * nk + 2 * kk;
-                for (int c = 0; c < 4; ++c) atomicAdd(bF + c, w[c]);
+                for (int c = 0; c < 4; ++c) atomicAdd(sb + bin_index(2, kk + (c >> 1), c & 1, nk), w[c]);
             }
         }
     }
@@ -464,15 +480,34 @@ __global__ void __launch_bounds__(NE_TILE* TPA) k_backward_mixed(DevBatch B, flo
     for (int q = threadIdx.x; q < nb; q += blockDim.x) out[q] = sb[q];
 }
 
-__global__ void k_bins_reduce(const float* __restrict__ bins, int n_blocks, int nb, BwdWeight W,
-                              double* __restrict__ gtheta, int accumulate)
+// gtheta[q] (+)= gE * (sum over blocks of bin q's values): a block of
+// BR_COLS x BR_SEG threads takes BR_COLS knot parameters; segment g sums the
+// blocks b = g, g + BR_SEG, ... in FP64, then the segments are added in a
+// fixed order (the same every call).
+constexpr int BR_COLS = 32, BR_SEG = 8;
+
+__global__ void __launch_bounds__(BR_COLS* BR_SEG)
+    k_bins_reduce(const float* __restrict__ bins, int n_blocks, int nb, int nk, BwdWeight W,
+                  double* __restrict__ gtheta, int accumulate)
 {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double part[BR_SEG][BR_COLS];
+    const int col = threadIdx.x % BR_COLS, g = threadIdx.x / BR_COLS;
+    const int q = blockIdx.x * BR_COLS + col;  // knot parameter [fn][k][c]
     const double gE = bwd_weight(W);
-    if (q >= nb || gE == 0.0) return;
+    if (gE == 0.0) return;
     double acc = 0.0;
-    for (int b = 0; b < n_blocks; ++b) acc += (double)bins[(size_t)b * nb + q];
-    gtheta[q] = (accumulate ? gtheta[q] : 0.0) + gE * acc;
+    if (q < nb) {
+        const int fn = q / (2 * nk), k = (q % (2 * nk)) >> 1, c = q & 1;
+        const int bq = bin_index(fn, k, c, nk);
+        for (int b = g; b < n_blocks; b += BR_SEG) acc += (double)bins[(size_t)b * nb + bq];
+    }
+    part[g][col] = acc;
+    __syncthreads();
+    if (g == 0 && q < nb) {
+        double t = 0.0;
+        for (int h = 0; h < BR_SEG; ++h) t += part[h][col];
+        gtheta[q] = (accumulate ? gtheta[q] : 0.0) + gE * t;
+    }
 }
 
 // FP64 path: FP64 basis weights added straight into gtheta (pre-zeroed) with
@@ -649,7 +684,20 @@ cudaError_t prepare_backward(const DevBatch& B)
 
 int backward_bin_blocks(const DevBatch& B)
 {
-    int nb = B.n_tiles < 296 ? B.n_tiles : 296;
+    // one block per SM (the bins fill its shared memory), no more than the
+    // tiles need
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+            (void)cudaGetLastError();
+            sms = 148;
+        }
+    }
+    const int per = BWD_THREADS / (NE_TILE * (B.tpa < 1 ? 1 : B.tpa));
+    const int need = (B.n_tiles + per - 1) / per;
+    const int nb = need < sms ? need : sms;
     return nb < 1 ? 1 : nb;
 }
 
@@ -677,7 +725,7 @@ void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, doubl
         size_t smem = (size_t)nb * sizeof(float);
 #define NE_BWD(T)                                                                                        \
     if (set_attr) cudaFuncSetAttribute(k_backward_mixed<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    k_backward_mixed<T><<<n_bin_blocks, NE_TILE * T, smem, st>>>(B, bins, W)
+    k_backward_mixed<T><<<n_bin_blocks, BWD_THREADS, smem, st>>>(B, bins, W)
         switch (B.tpa) {
         case 1: NE_BWD(1); break;
         case 2: NE_BWD(2); break;
@@ -685,7 +733,8 @@ void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, doubl
         default: NE_BWD(8); break;
         }
 #undef NE_BWD
-        k_bins_reduce<<<(nb + 255) / 256, 256, 0, st>>>(bins, n_bin_blocks, nb, W, gtheta, accumulate ? 1 : 0);
+        k_bins_reduce<<<(nb + BR_COLS - 1) / BR_COLS, BR_COLS * BR_SEG, 0, st>>>(bins, n_bin_blocks, nb, nk, W, gtheta,
+                                                                                 accumulate ? 1 : 0);
     } else {
         if (!accumulate) cudaMemsetAsync(gtheta, 0, sizeof(double) * nb, st);
         dim3 g(B.n_tiles);

@@ -243,6 +243,20 @@ __device__ __forceinline__ int ne_nbr_index(int k, int i, int n_tot, int tpa)
     return ((k / tpa) * n_tot + i) * tpa + (k % tpa);
 }
 
+// Sum of quantity q over tiles [t0, t0 + nt) of a tile-partials array (nq
+// values a tile), by one warp: lane l adds tiles t0 + l, t0 + l + 32, ...
+// in order, then a fixed xor-shuffle tree; every lane returns the total, and
+// the order depends only on nt, never on scheduling.  Called by all 32 lanes.
+__device__ __forceinline__ double ne_warp_tile_sum(const double* part, int nq, int q, int t0, int nt)
+{
+    const int l = threadIdx.x & 31;
+    double acc = 0.0;
+    for (int t = l; t < nt; t += 32) acc += __ldcg(&part[(size_t)(t0 + t) * nq + q]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
 __device__ __forceinline__ void ne_set_status(int* status, int bits)
 {
     atomicOr(status, bits);

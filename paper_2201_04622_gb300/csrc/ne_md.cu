@@ -21,7 +21,31 @@ __device__ __forceinline__ double wrap(double x, double L, double invL) { return
 //              surrounding cells (all atoms when the box holds < 3 cells per
 //              axis) within r_c + skin, minimum image, FP32 distances with a
 //              1e-3 A margin so that rounding never drops a pair.
-// Both return at once for replicas that need no rebuild.
+// Both return at once for replicas that need no rebuild.  The per-atom part
+// of the binning (wrapped position, cell in FP64) runs first in k_nl_prep,
+// one block per tile, so a large replica's FP64 work spreads over the SMs.
+__global__ void __launch_bounds__(NE_TILE) k_nl_prep(DevBatch B, int force, int from_sites)
+{
+    const int tile = blockIdx.x;
+    const int rep = B.tile_rep[tile];
+    if (!(force || B.flags[rep] != 0)) return;
+    const RepDev& P = B.rep[rep];
+    const int a = (tile - P.tile0) * NE_TILE + threadIdx.x;
+    if (a >= P.n) return;
+    const int i = P.off + a;
+    const double* X = from_sites ? B.x0 : B.x;
+    double w[3];
+    for (int d = 0; d < 3; ++d) w[d] = wrap(X[3 * i + d], P.L[d], P.invL[d]);
+    B.pbuild[i] = make_float4((float)w[0], (float)w[1], (float)w[2], 0.f);
+    if (P.nc[0] == 0) return;
+    int c3[3];
+    for (int d = 0; d < 3; ++d) {
+        const int q = (int)(w[d] * P.invL[d] * P.nc[d]);
+        c3[d] = min(max(q, 0), P.nc[d] - 1);
+    }
+    B.cellof[i] = (c3[0] * P.nc[1] + c3[1]) * P.nc[2] + c3[2];
+}
+
 __global__ void __launch_bounds__(512) k_nl_bin(DevBatch B, int force, int from_sites)
 {
     const int rep = blockIdx.x;
@@ -35,14 +59,8 @@ __global__ void __launch_bounds__(512) k_nl_bin(DevBatch B, int force, int from_
         if (go) atomicAdd(B.rebuilds, 1ull);
     }
     if (!go) return;
+    (void)from_sites;  // positions were wrapped and binned by k_nl_prep
     const int n = P.n, off = P.off;
-    const double* X = from_sites ? B.x0 : B.x;
-    for (int a = tid; a < n; a += bs) {
-        const int i = off + a;
-        B.pbuild[i] = make_float4((float)wrap(X[3 * i], P.L[0], P.invL[0]),
-                                  (float)wrap(X[3 * i + 1], P.L[1], P.invL[1]),
-                                  (float)wrap(X[3 * i + 2], P.L[2], P.invL[2]), 0.f);
-    }
     if (P.nc[0] == 0) return;
     const int nc0 = P.nc[0], nc1 = P.nc[1], nc2 = P.nc[2];
     const int ncell = nc0 * nc1 * nc2;
@@ -51,21 +69,31 @@ __global__ void __launch_bounds__(512) k_nl_bin(DevBatch B, int force, int from_
     for (int c = tid; c <= ncell; c += bs) start[c] = 0;
     for (int c = tid; c < ncell; c += bs) fill[c] = 0;
     __syncthreads();
-    for (int a = tid; a < n; a += bs) {
-        const int i = off + a;
-        int c3[3];
-        for (int d = 0; d < 3; ++d) {
-            double s = wrap(X[3 * i + d], P.L[d], P.invL[d]);
-            int q = (int)(s * P.invL[d] * P.nc[d]);
-            c3[d] = min(max(q, 0), P.nc[d] - 1);
-        }
-        const int c = (c3[0] * nc1 + c3[1]) * nc2 + c3[2];
-        B.cellof[i] = c;
-        atomicAdd(&start[c + 1], 1);
-    }
+    for (int a = tid; a < n; a += bs) atomicAdd(&start[B.cellof[off + a] + 1], 1);
     __syncthreads();
-    if (tid == 0)
-        for (int c = 0; c < ncell; ++c) start[c + 1] += start[c];
+    // inclusive scan of start[1..ncell] by the whole block: each thread sums
+    // a contiguous chunk of cells, a shared-memory scan over the chunk
+    // totals gives each chunk's offset, then each thread writes its chunk
+    {
+        __shared__ int s_chunk[512];
+        const int per = (ncell + bs - 1) / bs;
+        const int c0 = 1 + tid * per, c1 = min(ncell + 1, c0 + per);
+        int tot = 0;
+        for (int c = c0; c < c1; ++c) tot += start[c];
+        s_chunk[tid] = tot;
+        __syncthreads();
+        for (int o = 1; o < bs; o <<= 1) {  // Hillis-Steele inclusive scan over the chunk totals
+            const int v = tid >= o ? s_chunk[tid - o] : 0;
+            __syncthreads();
+            s_chunk[tid] += v;
+            __syncthreads();
+        }
+        int run = tid > 0 ? s_chunk[tid - 1] : 0;
+        for (int c = c0; c < c1; ++c) {
+            run += start[c];
+            start[c] = run;
+        }
+    }
     __syncthreads();
     for (int a = tid; a < n; a += bs) {
         const int c = B.cellof[off + a];
@@ -73,16 +101,33 @@ __global__ void __launch_bounds__(512) k_nl_bin(DevBatch B, int force, int from_
         B.sorted[off + start[c] + pos] = a;
     }
     __syncthreads();
+    // sort each cell's atoms by index: in a thread-local copy when the cell
+    // holds at most NE_CELL_LOCAL atoms (the common case), else in place
+    constexpr int NE_CELL_LOCAL = 64;
     for (int c = tid; c < ncell; c += bs) {
         int* sl = B.sorted + off + start[c];
         const int len = start[c + 1] - start[c];
-        for (int p = 1; p < len; ++p) {
-            int key = sl[p], q = p - 1;
-            while (q >= 0 && sl[q] > key) {
-                sl[q + 1] = sl[q];
-                --q;
+        if (len <= NE_CELL_LOCAL) {
+            int loc[NE_CELL_LOCAL];
+            for (int p = 0; p < len; ++p) {
+                const int key = sl[p];
+                int q = p - 1;
+                while (q >= 0 && loc[q] > key) {
+                    loc[q + 1] = loc[q];
+                    --q;
+                }
+                loc[q + 1] = key;
             }
-            sl[q + 1] = key;
+            for (int p = 0; p < len; ++p) sl[p] = loc[p];
+        } else {
+            for (int p = 1; p < len; ++p) {
+                int key = sl[p], q = p - 1;
+                while (q >= 0 && sl[q] > key) {
+                    sl[q + 1] = sl[q];
+                    --q;
+                }
+                sl[q + 1] = key;
+            }
         }
     }
 }
@@ -349,10 +394,9 @@ __global__ void k_trace_T(DevBatch B, const long long* __restrict__ step_base, i
     const long long s = *step_base + j;
     if (!B.trace || s % B.trace_stride != 0 || s / B.trace_stride >= B.trace_rows) return;
     const RepDev& P = B.rep[0];
-    double ke = 0.0;
-    for (int t = P.tile0; t < P.tile0 + P.ntile; ++t) ke += B.partB[(size_t)t * NPB + PB_KE];
+    const double ke = ne_warp_tile_sum(B.partB, NPB, PB_KE, P.tile0, P.ntile);
     const double kB = 8.617333262e-5;
-    B.trace[8 * (s / B.trace_stride) + 5] = 2.0 * ke / (P.dof * kB);
+    if (threadIdx.x == 0) B.trace[8 * (s / B.trace_stride) + 5] = 2.0 * ke / (P.dof * kB);
 }
 
 __global__ void k_advance(long long* step_base, long long by) { *step_base += by; }
@@ -516,16 +560,13 @@ __global__ void k_export(DevBatch B, double* f, double* e)
 __global__ void k_msd_sample(DevBatch B, double* acc)
 {
     const int rep = blockIdx.x;
-    if (threadIdx.x != 0) return;
     const RepDev& P = B.rep[rep];
-    double s[4] = {0, 0, 0, 0};
-    for (int t = P.tile0; t < P.tile0 + P.ntile; ++t) {
-        const double* pb = B.partB + (size_t)t * NPB;
-        s[0] += pb[PB_UX];
-        s[1] += pb[PB_UY];
-        s[2] += pb[PB_UZ];
-        s[3] += pb[PB_U2];
-    }
+    double s[4];
+    s[0] = ne_warp_tile_sum(B.partB, NPB, PB_UX, P.tile0, P.ntile);
+    s[1] = ne_warp_tile_sum(B.partB, NPB, PB_UY, P.tile0, P.ntile);
+    s[2] = ne_warp_tile_sum(B.partB, NPB, PB_UZ, P.tile0, P.ntile);
+    s[3] = ne_warp_tile_sum(B.partB, NPB, PB_U2, P.tile0, P.ntile);
+    if (threadIdx.x != 0) return;
     const double invN = 1.0 / P.n;
     acc[rep] += s[3] * invN - (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]) * invN * invN;
 }
@@ -584,6 +625,7 @@ namespace ne {
 
 void launch_nl_build(const DevBatch& B, int force, int from_sites, cudaStream_t st)
 {
+    k_nl_prep<<<B.n_tiles, NE_TILE, 0, st>>>(B, force, from_sites);
     k_nl_bin<<<B.n_rep, 512, 0, st>>>(B, force, from_sites);
     k_nl_list<<<B.n_tiles, NE_TILE, 0, st>>>(B);
 }
@@ -595,7 +637,7 @@ void launch_step(const DevBatch& B, const Sched& S, bool mixed, const long long*
         k_step<true><<<B.n_tiles, NE_TILE, 0, st>>>(B, S, step_base, j, do_close, do_open);
     else
         k_step<false><<<B.n_tiles, NE_TILE, 0, st>>>(B, S, step_base, j, do_close, do_open);
-    if (B.trace) k_trace_T<<<1, 1, 0, st>>>(B, step_base, j);
+    if (B.trace) k_trace_T<<<1, 32, 0, st>>>(B, step_base, j);
 }
 
 void launch_prep(const DevBatch& B, const Sched& S, bool mixed, const long long* step_base,
