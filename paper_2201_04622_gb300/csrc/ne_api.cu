@@ -1439,7 +1439,7 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
     int dev = 0, smem_max = 0;
     NE_CU(cudaGetDevice(&dev));
     NE_CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    // a cluster-runner CTA takes all of its SM's tensor memory, so no two may
+    // a crystal-runner CTA takes all of its SM's tensor memory, so no two may
     // share an SM: their shared memory is at least half of the SM's
     int smem_sm = 0;
     NE_CU(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
@@ -1482,7 +1482,8 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
             if (base > (size_t)smem_max) continue;
             const long long fit = ((long long)smem_max - (long long)base) / (2 * (long long)sizeof(float4));
             const int n_int = (int)std::min<long long>(nk - 1, fit);
-            const size_t smem = base + (size_t)n_int * 2 * sizeof(float4);
+            const size_t smem = std::max(base + (size_t)n_int * 2 * sizeof(float4), smem_floor);
+            if (smem > (size_t)smem_max) continue;
             const int per = ne::brick_atoms_per_cta(tpa);
             std::vector<int> cr_(n_rep);
             int total = 0;

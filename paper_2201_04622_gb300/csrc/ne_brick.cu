@@ -45,7 +45,11 @@
 namespace {
 
 constexpr int BTHREADS = 768;
-constexpr int SLMAX = 80;   // short-list entries per atom
+// TMEM scratch between the pair passes (as in the cluster runner): warp w
+// holds f'(r)/r of its visits in lanes 32 (w mod 4) .. +31, columns
+// QMAX (w div 4) .. +QMAX-1; visits past QMAX are recomputed in pass 2
+constexpr int FRB = NE_TM_BATCH;
+constexpr int QMAX = NE_TM_COLS / (BTHREADS / 32 / 4) / FRB * FRB;
 constexpr int NKT = 256;    // scan-bound bins of the stencil distance
 constexpr int NWARP = BTHREADS / 32;
 enum { P_U0 = 0, P_UE, P_UX, P_UY, P_UZ, P_XX, P_XY, P_XZ, NP_ };
@@ -149,8 +153,6 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             ne::BrickBufs bb, long long n_tot, double* __restrict__ boxes_out)
 {
     constexpr int SLOTS = BTHREADS / TPA;
-    constexpr int SLQ = SLMAX / TPA;
-    static_assert(NE_STENCIL_MAX / TPA <= 256, "short-list entries are bytes");
     extern __shared__ __align__(16) unsigned char smem[];
     const int rep = cta_rep[blockIdx.x];
     const XRep& R_ = reps[rep];
@@ -169,13 +171,13 @@ __global__ void __launch_bounds__(BTHREADS, 1)
     int* s_lxy = (int*)(s_sd + nb * nst);                         // [(nx + 2M) * LY]
     int* s_lz = s_lxy + (nx + 2 * M) * LY;                        // [nb][nz + 2M]
     unsigned short* s_K = (unsigned short*)(s_lz + nb * (nz + 2 * M));  // [4][NKT]
-    unsigned char* s_sl = (unsigned char*)(s_K + 4 * NKT);      // [SLQ][TPA][SLOTS]
-    float* s_tot = (float*)(((size_t)(s_sl + SLOTS * SLMAX) + 15) & ~(size_t)15);  // [NSV]
+    float* s_tot = (float*)(((size_t)(s_K + 4 * NKT) + 15) & ~(size_t)15);  // [NSV]
     float4* s_f = (float4*)(((size_t)(s_tot + NSV) + 15) & ~(size_t)15);  // [TPA - 1][SLOTS]
     float2* s_rho = (float2*)(s_f + (TPA - 1) * SLOTS);           // [TPA - 1][SLOTS]
     float* s_red = (float*)(s_rho + (TPA - 1) * SLOTS);           // [NWARP][NRED][2]
     int* s_flag = (int*)(s_red + NWARP * NRED * 2);               // [4]
-    unsigned char* s_end = (unsigned char*)(s_flag + 4);
+    unsigned* s_tm = (unsigned*)(s_flag + 4);                     // [4] TMEM base address
+    unsigned char* s_end = (unsigned char*)(s_tm + 4);
     float4* s_vir = nullptr;  // barostat: [TPA - 1][SLOTS] pair-lane virials
     float* s_vred = nullptr;  // [NWARP][6] warp sums of the virial
     double* s_mu = nullptr;   // [3] the step's scale factors
@@ -213,22 +215,27 @@ __global__ void __launch_bounds__(BTHREADS, 1)
         const int Z = q % (nz + 2 * M);
         s_lz[q] = ((Z - M) % nz + nz) % nz + (q / (nz + 2 * M)) * ncell;
     }
+    // TMEM: all columns for this CTA (one per SM), returned after the step
+    // loop, which every thread of the CTA leaves at the same step
+    ne_tm_alloc(s_tm);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tm_base = *s_tm;
+    const unsigned tm_w = tm_base + ((unsigned)(32 * ((threadIdx.x >> 5) & 3)) << 16) +
+                          (unsigned)(QMAX * (threadIdx.x >> 7));  // this warp's lanes and columns
     const float Dr = R_.D;
     for (int q = threadIdx.x; q < nb * NKT; q += BTHREADS) {
         const int b = q / NKT, iq = q % NKT;
-        int cnt = nst;
-        if (iq < NKT - 1) {
-            const float cq = (float)tab.r_c + (float)iq * (2.f * Dr / (float)(NKT - 1));
-            int lo = 0, hi = nst;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s_sd[b * nst + mid] < cq) lo = mid + 1;
-                else hi = mid;
-            }
-            cnt = lo;
+        // the last bin holds every real entry (padding entries have distance 1e30)
+        const float cq = iq < NKT - 1 ? (float)tab.r_c + (float)iq * (2.f * Dr / (float)(NKT - 1)) : 1e29f;
+        int lo = 0, hi = nst;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_sd[b * nst + mid] < cq) lo = mid + 1;
+            else hi = mid;
         }
-        s_K[q] = (unsigned short)cnt;
+        s_K[q] = (unsigned short)lo;
     }
     const float inv_dK = (float)(NKT - 1) / (2.f * Dr);
 
@@ -430,9 +437,9 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             dead = true;
         }
 
-        // ---- pass 1
+        // ---- pass 1: density, pair forces and energy, f'(r)/r of every visit to TMEM
         const float4 ui = dead ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldcg(&u_cur[sui]);
-        int m = 0;
+        int m = 0, nq = 0;  // pairs inside r_c; the warp's visits
         float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
         float vxx = 0.f, vyy = 0.f, vzz = 0.f;  // diagonal virial (barostat only)
         dfl rho = {0.f, 0.f};
@@ -440,70 +447,94 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             float c = sqrtf(ui.x * ui.x + ui.y * ui.y + ui.z * ui.z) + umax;
             if constexpr (NPT) c = ((float)tab.r_c + c) / mu_min - (float)tab.r_c;  // in lattice units
             const int K = valid ? (int)s_K[skb + min(NKT - 1, (int)(c * inv_dK) + 2)] : 0;
+            // every thread of the warp visits up to the warp's largest bound in
+            // whole batches of FRB (TMEM stores are warp-wide); entries past a
+            // thread's own bound lie outside r_c for it, and visits past the
+            // stencil read its last entry, a far padding site
+            const int Kw = __reduce_max_sync(0xffffffffu, K);
+            nq = Kw > lane ? ((Kw - lane + TPA - 1) / TPA + FRB - 1) / FRB * FRB : 0;
+            int ql = -1;  // this thread's last visit inside r_c
             float rh = 0.f, rl = 0.f;
-            unsigned char* slp = s_sl + lane * SLOTS + slot;
-#pragma unroll 4
-            for (int k = lane; k < K; k += TPA) {
-                float4 e = s_sv[stb + k];
-                const int code = __float_as_int(e.w);
-                const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
-                const float4 uj = __ldcg(&u_cur[j]);
-                if constexpr (NPT) {
-                    e.x *= muf[0];
-                    e.y *= muf[1];
-                    e.z *= muf[2];
-                }
-                const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < rc2) {
-                    const float irh = rsqrtf(r2) * inv_h;
-                    const float t = r2 * irh;
-                    const int kk = min((int)t, nk - 2);
-                    const float w = t - (float)kk;
-                    float4 cf, g;
-                    if (kk < kchk) {
-                        if (r2 < rmin2) bad |= ST_ERANGE;
-                        if (kk >= k_lo) {
+#pragma unroll 1
+            for (int q0 = 0; q0 < nq; q0 += FRB) {
+                float frv[FRB];
+#pragma unroll
+                for (int uq = 0; uq < FRB; ++uq) {
+                    const int k = min(lane + TPA * (q0 + uq), nst - 1);
+                    float fr = 0.f;
+                    float4 e = s_sv[stb + k];
+                    const int code = __float_as_int(e.w);
+                    const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
+                    const float4 uj = __ldcg(&u_cur[j]);
+                    if constexpr (NPT) {
+                        e.x *= muf[0];
+                        e.y *= muf[1];
+                        e.z *= muf[2];
+                    }
+                    const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < rc2) {
+                        const float irh = rsqrtf(r2) * inv_h;
+                        const float t = r2 * irh;
+                        const int kk = min((int)t, nk - 2);
+                        const float w = t - (float)kk;
+                        float4 cf, g;
+                        if (kk < kchk) {
+                            if (r2 < rmin2) bad |= ST_ERANGE;
+                            if (kk >= k_lo) {
+                                cf = s_tabP[kk - k_lo];
+                                g = s_tabF[kk - k_lo];
+                            } else {
+                                cf = __ldg(&tab.pf32[2 * kk]);
+                                g = __ldg(&tab.pf32[2 * kk + 1]);
+                            }
+                        } else {
                             cf = s_tabP[kk - k_lo];
                             g = s_tabF[kk - k_lo];
-                        } else {
-                            cf = __ldg(&tab.pf32[2 * kk]);
-                            g = __ldg(&tab.pf32[2 * kk + 1]);
                         }
-                    } else {
-                        cf = s_tabP[kk - k_lo];
-                        g = s_tabF[kk - k_lo];
+                        {
+                            // f and df/dw together (Horner with derivative)
+                            float fv = fmaf(g.w, w, g.z), fd = g.w;
+                            fd = fmaf(fd, w, fv);
+                            fv = fmaf(fv, w, g.y);
+                            fd = fmaf(fd, w, fv);
+                            fv = fmaf(fv, w, g.x);
+                            const float s_ = rh + fv, bp = s_ - rh;
+                            rl += (rh - (s_ - bp)) + (fv - bp);
+                            rh = s_;
+                            fr = fd * irh;  // f'(r) / r
+                            ql = q0 + uq;
+                        }
+                        float pv = fmaf(cf.w, w, cf.z), pd = cf.w;
+                        pd = fmaf(pd, w, pv);
+                        pv = fmaf(pv, w, cf.y);
+                        pd = fmaf(pd, w, pv);
+                        pv = fmaf(pv, w, cf.x);
+                        const float sc = pd * irh;
+                        fx += sc * dx;
+                        fy += sc * dy;
+                        fz += sc * dz;
+                        ep += pv;
+                        if constexpr (NPT) {  // -(1/2) r_a^2 / r dU/dr of the pair's half
+                            vxx -= 0.5f * sc * dx * dx;
+                            vyy -= 0.5f * sc * dy * dy;
+                            vzz -= 0.5f * sc * dz * dz;
+                        }
+                        ++m;
                     }
-                    {
-                        const float fv = g.x + w * (g.y + w * (g.z + w * g.w));
-                        const float s_ = rh + fv, bp = s_ - rh;
-                        rl += (rh - (s_ - bp)) + (fv - bp);
-                        rh = s_;
-                    }
-                    float pv = fmaf(cf.w, w, cf.z), pd = cf.w;
-                    pd = fmaf(pd, w, pv);
-                    pv = fmaf(pv, w, cf.y);
-                    pd = fmaf(pd, w, pv);
-                    pv = fmaf(pv, w, cf.x);
-                    const float sc = pd * irh;
-                    fx += sc * dx;
-                    fy += sc * dy;
-                    fz += sc * dz;
-                    ep += pv;
-                    if constexpr (NPT) {  // -(1/2) r_a^2 / r dU/dr of the pair's half
-                        vxx -= 0.5f * sc * dx * dx;
-                        vyy -= 0.5f * sc * dy * dy;
-                        vzz -= 0.5f * sc * dz * dz;
-                    }
-                    slp[min(m, SLQ - 1) * (TPA * SLOTS)] = (unsigned char)(k / TPA);
-                    ++m;
+                    frv[uq] = fr;
+                }
+                if (q0 < QMAX) {
+                    __syncwarp();
+                    ne_tm_st(tm_w + (unsigned)q0, frv);
                 }
             }
+            __syncwarp();
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");  // the stores land before pass 2 loads
             rho = {rh, rl};
-            n_cand += (K > lane) ? (unsigned)((K - lane + TPA - 1) / TPA) : 0u;
-            if (m > SLQ) bad |= ST_ENEIGH;
-            m = min(m, SLQ);
-            n_pair += (unsigned)m;
+            n_cand += valid ? (unsigned)nq : 0u;
+            n_pair += valid ? (unsigned)m : 0u;
+            nq = __reduce_max_sync(0xffffffffu, ql) + 1;  // pass 2 stops after the warp's last pair
             ep *= 0.5f;
             if (valid && lane > 0) s_rho[(lane - 1) * SLOTS + slot] = make_float2(rho.hi, rho.lo);
         }
@@ -527,18 +558,50 @@ __global__ void __launch_bounds__(BTHREADS, 1)
         alive = grid_barrier(bb.bar, n_cta, gen, status, bb.abortf, s_flag);  // F' visible everywhere
         if (!alive) break;
 
-        // ---- pass 2
+        // ---- pass 2: embedding forces over the visits of pass 1, f'(r)/r from TMEM
         if (!dead) {
             const float dFi = __ldcg(&bb.fp[gofs + sui]);
             const float* fp_r = bb.fp + gofs;
-#pragma unroll 2
-            for (int q = 0; q < m; ++q) {
-                const int k = TPA * s_sl[(q * TPA + lane) * SLOTS + slot] + lane;
+            const int nqt = min(nq, QMAX);
+#pragma unroll 1
+            for (int q0 = 0; q0 < nqt; q0 += FRB) {
+                float frv[FRB];
+                __syncwarp();
+                ne_tm_ld(tm_w + (unsigned)q0, frv);
+#pragma unroll
+                for (int uq = 0; uq < FRB; ++uq) {
+                    if (frv[uq] != 0.f) {  // inside r_c (f' vanishes only at r_c)
+                        const int k = min(lane + TPA * (q0 + uq), nst - 1);
+                        float4 e = s_sv[stb + k];
+                        const int code = __float_as_int(e.w);
+                        const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
+                        const float4 uj = __ldcg(&u_cur[j]);
+                        const float dFj = __ldcg(&fp_r[j]);
+                        if constexpr (NPT) {
+                            e.x *= muf[0];
+                            e.y *= muf[1];
+                            e.z *= muf[2];
+                        }
+                        const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
+                        const float sc = (dFi + dFj) * frv[uq];
+                        fx += sc * dx;
+                        fy += sc * dy;
+                        fz += sc * dz;
+                        if constexpr (NPT) {
+                            vxx -= 0.5f * sc * dx * dx;
+                            vyy -= 0.5f * sc * dy * dy;
+                            vzz -= 0.5f * sc * dz * dz;
+                        }
+                    }
+                }
+            }
+            // visits past the TMEM columns: the pair recomputed
+            for (int q = QMAX; q < nq; ++q) {
+                const int k = min(lane + TPA * q, nst - 1);
                 float4 e = s_sv[stb + k];
                 const int code = __float_as_int(e.w);
                 const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
                 const float4 uj = __ldcg(&u_cur[j]);
-                const float dFj = __ldcg(&fp_r[j]);
                 if constexpr (NPT) {
                     e.x *= muf[0];
                     e.y *= muf[1];
@@ -546,6 +609,8 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                 }
                 const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < rc2)) continue;
+                const float dFj = __ldcg(&fp_r[j]);
                 const float irh = rsqrtf(r2) * inv_h;
                 const float t = r2 * irh;
                 const int kk = min((int)t, nk - 2);
@@ -737,6 +802,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             }
         }
     }
+    ne_tm_free(tm_base);  // every warp is past its last TMEM access
     if (bad) {
         ne_set_status(status, bad);
         ne_set_status(status + 1 + R_.widx, bad);
@@ -811,12 +877,12 @@ size_t brick_smem_bytes(int tpa, int nb_nst_max, int lut_max, bool npt)
 {
     const size_t slots = (size_t)(BTHREADS / tpa);
     size_t b = (sizeof(float4) + sizeof(float)) * (size_t)nb_nst_max + sizeof(int) * (size_t)lut_max +
-               sizeof(unsigned short) * 4 * NKT + slots * SLMAX;
+               sizeof(unsigned short) * 4 * NKT;
     b = (b + 15) & ~(size_t)15;
     b += sizeof(float) * NSV;
     b = (b + 15) & ~(size_t)15;
     b += (sizeof(float4) + sizeof(float2)) * (size_t)(tpa - 1) * slots + sizeof(float) * NWARP * NRED * 2 +
-         sizeof(int) * 4;
+         sizeof(int) * 4 + sizeof(unsigned) * 4;
     if (npt) {  // pair-lane virials, warp sums, scale factors
         b = (b + 15) & ~(size_t)15;
         b += sizeof(float4) * (size_t)(tpa - 1) * slots + sizeof(float) * NWARP * 6;

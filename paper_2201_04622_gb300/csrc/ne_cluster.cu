@@ -62,8 +62,8 @@ constexpr int SLOTS = THREADS / TPA;  // atoms per CTA (one CTA per SM)
 // +31 (its sub-partition's) and columns QMAX (w div 4) .. +QMAX-1: visit q
 // of a thread is column q of its lane, stored and loaded FRB at a time.
 // Visits past QMAX (a hot or disordered replica) are recomputed in pass 2.
-constexpr int TM_COLS = 512;
-constexpr int FRB = 8;
+constexpr int TM_COLS = NE_TM_COLS;
+constexpr int FRB = NE_TM_BATCH;
 // stencil scan bounds: entries of basis b with |r0_j - r0_i| < r_c + c for
 // c = q * 2D / (NKT - 1), q = 0 .. NKT - 1 (the last: the whole stencil)
 constexpr int NKT = 256;
@@ -205,40 +205,6 @@ __host__ __device__ inline int atoms_per_cta(int n, int C, int nb)
     return (((n + C - 1) / C) + nb - 1) / nb * nb;
 }
 
-// FRB consecutive TMEM columns of this thread's lane (32x32b shape: thread
-// i of the warp is lane i of the warp's quarter).  The load waits for its
-// data; the registers pass through the wait so no use moves above it.
-__device__ __forceinline__ void tm_st(unsigned taddr, const float (&v)[FRB])
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
-                 :
-                 : "r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-                   "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-                   "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tm_ld(unsigned taddr, float (&v)[FRB])
-{
-    unsigned r0, r1, r2, r3, r4, r5, r6, r7;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
-                 : "r"(taddr)
-                 : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3), "+r"(r4), "+r"(r5), "+r"(r6), "+r"(r7)
-                 :
-                 : "memory");
-    v[0] = __uint_as_float(r0);
-    v[1] = __uint_as_float(r1);
-    v[2] = __uint_as_float(r2);
-    v[3] = __uint_as_float(r3);
-    v[4] = __uint_as_float(r4);
-    v[5] = __uint_as_float(r5);
-    v[6] = __uint_as_float(r6);
-    v[7] = __uint_as_float(r7);
-}
-
 // NPT: the replicas have the barostat of the reversible-scaling path (a
 // separate instantiation, so the fixed-box kernel carries none of it)
 template <bool NPT>
@@ -360,14 +326,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const size_t gi = (size_t)(reps[rep].off + (own ? ta : 0)) * 3;
     // TMEM: warp 0 takes all columns for the CTA (returned after the step
     // loop, which every thread leaves at the same step)
-    if (threadIdx.x < 32) {
-        __syncwarp();
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :
-                     : "r"((unsigned)__cvta_generic_to_shared(s_tm)), "r"(TM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    ne_tm_alloc(s_tm);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     cluster.sync();  // every CTA of the cluster has started: distributed shared memory is usable
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -622,7 +581,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 if (q0 < QMAX) {
                     __syncwarp();
-                    tm_st(tm_w + (unsigned)q0, frv);
+                    ne_tm_st(tm_w + (unsigned)q0, frv);
                 }
             }
             __syncwarp();
@@ -663,7 +622,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int q0 = 0; q0 < nqt; q0 += FRB) {
                 float frv[FRB];
                 __syncwarp();
-                tm_ld(tm_w + (unsigned)q0, frv);
+                ne_tm_ld(tm_w + (unsigned)q0, frv);
 #pragma unroll
                 for (int uq = 0; uq < FRB; ++uq) {
                     if (frv[uq] != 0.f) {  // inside r_c (f' vanishes only at r_c)
@@ -902,14 +861,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                                         s_slotM + ((s + 1) & 1) * 16, rank, C, own_warps);
         }
     }
-    // every warp is past its last TMEM access: return the columns
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        __syncwarp();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm_base), "r"(TM_COLS) : "memory");
-    }
+    ne_tm_free(tm_base);  // every warp is past its last TMEM access
     if (bad) {
         ne_set_status(status, bad);
         ne_set_status(status + 1 + reps[rep].widx, bad);

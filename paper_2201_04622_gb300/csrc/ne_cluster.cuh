@@ -36,6 +36,75 @@ struct XRep {
     double box0[3];
 };
 
+// Tensor memory as per-thread scratch (both crystal runners): a CTA that is
+// alone on its SM takes all NE_TM_COLS columns; a warp reads and writes
+// NE_TM_BATCH columns of its own lanes at a time.
+#define NE_TM_COLS 512
+#define NE_TM_BATCH 8
+
+// NE_TM_BATCH consecutive TMEM columns of this thread's lane (32x32b shape: thread
+// i of the warp is lane i of the warp's quarter).  The load waits for its
+// data; the registers pass through the wait so no use moves above it.
+__device__ __forceinline__ void ne_tm_st(unsigned taddr, const float (&v)[NE_TM_BATCH])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :
+                 : "r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                   "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                   "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+
+__device__ __forceinline__ void ne_tm_ld(unsigned taddr, float (&v)[NE_TM_BATCH])
+{
+    unsigned r0, r1, r2, r3, r4, r5, r6, r7;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3), "+r"(r4), "+r"(r5), "+r"(r6), "+r"(r7)
+                 :
+                 : "memory");
+    v[0] = __uint_as_float(r0);
+    v[1] = __uint_as_float(r1);
+    v[2] = __uint_as_float(r2);
+    v[3] = __uint_as_float(r3);
+    v[4] = __uint_as_float(r4);
+    v[5] = __uint_as_float(r5);
+    v[6] = __uint_as_float(r6);
+    v[7] = __uint_as_float(r7);
+}
+
+// Warp 0 of the CTA takes all NE_TM_COLS columns (the base address goes to
+// *s_slot in shared memory); the caller then makes it visible with
+// tcgen05.fence::before_thread_sync, a CTA barrier and
+// tcgen05.fence::after_thread_sync.
+__device__ __forceinline__ void ne_tm_alloc(unsigned* s_slot)
+{
+    if (threadIdx.x < 32) {
+        __syncwarp();
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :
+                     : "r"((unsigned)__cvta_generic_to_shared(s_slot)), "r"(NE_TM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+}
+
+// Every thread of the CTA calls this once it is past its last TMEM access:
+// warp 0 returns the columns.
+__device__ __forceinline__ void ne_tm_free(unsigned base)
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(NE_TM_COLS) : "memory");
+    }
+}
+
 namespace ne {
 size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max, bool npt = false);
 int cluster_atoms_per_cta();
