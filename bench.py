@@ -413,11 +413,13 @@ def run_ours(args):
                 else "k_brick (persistent brick runner, grid barriers)",
                 "achieved": alg / 1e12, "peak": peak / 1e12, "unit": "T lane-ops/s",
                 "frac": alg / peak,
-                # ncu DRAM read + write of one k_cluster launch of this kernel on
-                # this workload (a 200-step launch: 2.27 MB read, 0 written; the
-                # replica lives on chip, so the figure does not grow with the
-                # steps); null for the other workloads
-                "traffic": 2.27e6 if args.workload == "fl2" and runner_kind == "cluster" else None,
+                # ncu DRAM read + write of one launch of this kernel on this
+                # workload (k_cluster on fl2, a 200-step launch: 2.27 MB read, 0
+                # written; k_brick on rs16, a 200-step launch: 1.86 MB read,
+                # 0.07 MB written); the replicas live on chip or in L2, so the
+                # figure does not grow with the steps; null elsewhere
+                "traffic": (2.27e6 if args.workload == "fl2" and runner_kind == "cluster" else
+                            1.93e6 if args.workload == "rs16" and runner_kind == "brick" else None),
                 "kernel_ms": kern_ms, "us_per_step": kern_ms * 1e3 / K,
                 "peak_note": "%d SMs x %d FP32 lanes x %.0f MHz (median SM clock sampled around the "
                              "timed region)" % (n_sm, FP32_LANES_PER_SM, sm_hz / 1e6),

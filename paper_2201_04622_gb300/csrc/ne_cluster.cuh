@@ -42,38 +42,53 @@ struct XRep {
 #define NE_TM_COLS 512
 #define NE_TM_BATCH 8
 
-// NE_TM_BATCH consecutive TMEM columns of this thread's lane (32x32b shape: thread
-// i of the warp is lane i of the warp's quarter).  The load waits for its
-// data; the registers pass through the wait so no use moves above it.
-__device__ __forceinline__ void ne_tm_st(unsigned taddr, const float (&v)[NE_TM_BATCH])
+// N (4 or 8) consecutive TMEM columns of this thread's lane (32x32b shape:
+// thread i of the warp is lane i of the warp's quarter).  The load waits for
+// its data; the registers pass through the wait so no use moves above it.
+template <int N>
+__device__ __forceinline__ void ne_tm_st(unsigned taddr, const float (&v)[N])
 {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
-                 :
-                 : "r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-                   "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-                   "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
-                 : "memory");
+    static_assert(N == 4 || N == 8, "TMEM batches of 4 or 8 columns");
+    if constexpr (N == 8)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                     :
+                     : "r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
+                       "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])),
+                       "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                     : "memory");
+    else
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};"
+                     :
+                     : "r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
+                       "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3]))
+                     : "memory");
 }
 
-__device__ __forceinline__ void ne_tm_ld(unsigned taddr, float (&v)[NE_TM_BATCH])
+template <int N>
+__device__ __forceinline__ void ne_tm_ld(unsigned taddr, float (&v)[N])
 {
-    unsigned r0, r1, r2, r3, r4, r5, r6, r7;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
-                 : "r"(taddr)
-                 : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3), "+r"(r4), "+r"(r5), "+r"(r6), "+r"(r7)
-                 :
-                 : "memory");
-    v[0] = __uint_as_float(r0);
-    v[1] = __uint_as_float(r1);
-    v[2] = __uint_as_float(r2);
-    v[3] = __uint_as_float(r3);
-    v[4] = __uint_as_float(r4);
-    v[5] = __uint_as_float(r5);
-    v[6] = __uint_as_float(r6);
-    v[7] = __uint_as_float(r7);
+    static_assert(N == 4 || N == 8, "TMEM batches of 4 or 8 columns");
+    unsigned r[8];
+    if constexpr (N == 8) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7])
+                     : "r"(taddr)
+                     : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                       "+r"(r[7])
+                     :
+                     : "memory");
+    } else {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                     : "r"(taddr)
+                     : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) : : "memory");
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) v[q] = __uint_as_float(r[q]);
 }
 
 // Warp 0 of the CTA takes all NE_TM_COLS columns (the base address goes to
