@@ -462,53 +462,90 @@ __global__ void k_wrap32(DevBatch B)
 // ------------------------------------------------------------ velocities
 // Philox normals (stream 1, step 0) times sqrt(kT/m); mean removed when the
 // centre of mass is fixed; rescaled to exactly T over the free dof.
-__global__ void __launch_bounds__(256) k_init_v(DevBatch B, int fix_cm)
+// Velocity start: Maxwell-Boltzmann from Philox normals, the centre-of-mass
+// momentum removed, then scaled to T exactly.  Three launches over the
+// tiles (draw, centre, scale); each block forms its replica's sums from the
+// tile partials in a fixed order (the partA slots of pass 1 and 2, which a
+// force evaluation rewrites before it reads them), so the FP64 Box-Muller of
+// a large replica spreads over the SMs instead of one block doing it all.
+__device__ __forceinline__ double tile_sum64(double v, double* red)
 {
-    __shared__ double red[4][256];
-    const int rep = blockIdx.x;
-    const RepDev& P = B.rep[rep];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = NE_TILE / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double t = red[0];
+    __syncthreads();
+    return t;
+}
+
+__device__ __forceinline__ double init_mass(const RepDev& P, int a) { return P.nsp ? P.ms[P.sp[a]] : P.m; }
+
+__global__ void __launch_bounds__(NE_TILE) k_init_v_draw(DevBatch B)
+{
+    __shared__ double red[NE_TILE];
+    const int tile = blockIdx.x;
+    const RepDev& P = B.rep[B.tile_rep[tile]];
+    const int a = (tile - P.tile0) * NE_TILE + threadIdx.x;
     // with species tables atom a has sd = sqrt(kT / m_a), and the momentum
     // sum_a m_a v_a / M is removed (the mass-weighted centre of mass)
-    auto mass = [&](int a) { return P.nsp ? P.ms[P.sp[a]] : P.m; };
-    double sum[4] = {0, 0, 0, 0};
-    for (int a = threadIdx.x; a < P.n; a += blockDim.x) {
-        const double sd = sqrt(P.kT / mass(a));
-        const double w = P.nsp ? mass(a) / P.M : 1.0;
+    double sum[3] = {0, 0, 0};
+    if (a < P.n) {
+        const double sd = sqrt(P.kT / init_mass(P, a));
+        const double w = P.nsp ? init_mass(P, a) / P.M : 1.0;
         double z[3];
         ne_normals64(ne_philox_block(P.seed, P.replica, STREAM_INITV, (unsigned)a, 0ull), z);
         for (int c = 0; c < 3; ++c) {
             B.v[3 * (P.off + a) + c] = sd * z[c];
-            sum[c] += w * sd * z[c];
+            sum[c] = w * sd * z[c];
         }
     }
-    for (int q = 0; q < 3; ++q) red[q][threadIdx.x] = sum[q];
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
-        __syncthreads();
+    for (int c = 0; c < 3; ++c) {
+        const double t = tile_sum64(sum[c], red);
+        if (threadIdx.x == 0) B.partA[(size_t)tile * NPA + c] = t;
     }
-    double mean[3];
-    for (int c = 0; c < 3; ++c) mean[c] = fix_cm ? (P.nsp ? red[c][0] : red[c][0] / P.n) : 0.0;
+}
+
+__global__ void __launch_bounds__(NE_TILE) k_init_v_center(DevBatch B, int fix_cm)
+{
+    __shared__ double red[NE_TILE];
+    __shared__ double s_mean[3];
+    const int tile = blockIdx.x;
+    const RepDev& P = B.rep[B.tile_rep[tile]];
+    if (threadIdx.x < 32)
+        for (int c = 0; c < 3; ++c) {
+            const double t = ne_warp_tile_sum(B.partA, NPA, c, P.tile0, P.ntile);
+            if (threadIdx.x == 0) s_mean[c] = fix_cm ? (P.nsp ? t : t / P.n) : 0.0;
+        }
     __syncthreads();
+    const int a = (tile - P.tile0) * NE_TILE + threadIdx.x;
     double ke = 0.0;
-    for (int a = threadIdx.x; a < P.n; a += blockDim.x)
+    if (a < P.n)
         for (int c = 0; c < 3; ++c) {
             double* vv = &B.v[3 * (P.off + a) + c];
-            *vv -= mean[c];
-            ke += 0.5 * mass(a) * (*vv) * (*vv);
+            *vv -= s_mean[c];
+            ke += 0.5 * init_mass(P, a) * (*vv) * (*vv);
         }
-    red[3][threadIdx.x] = ke;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[3][threadIdx.x] += red[3][threadIdx.x + w];
-        __syncthreads();
+    const double t = tile_sum64(ke, red);
+    if (threadIdx.x == 0) B.partA[(size_t)tile * NPA + 3] = t;
+}
+
+__global__ void __launch_bounds__(NE_TILE) k_init_v_scale(DevBatch B)
+{
+    __shared__ double s_sc;
+    const int tile = blockIdx.x;
+    const RepDev& P = B.rep[B.tile_rep[tile]];
+    if (threadIdx.x < 32) {
+        const double ke = ne_warp_tile_sum(B.partA, NPA, 3, P.tile0, P.ntile);
+        const double kB = 8.617333262e-5;
+        if (threadIdx.x == 0) s_sc = sqrt((P.kT / kB) / (2.0 * ke / (P.dof * kB)));
     }
-    const double kB = 8.617333262e-5;
-    const double t_now = 2.0 * red[3][0] / (P.dof * kB);
-    const double sc = sqrt((P.kT / kB) / t_now);
-    for (int a = threadIdx.x; a < P.n; a += blockDim.x)
-        for (int c = 0; c < 3; ++c) B.v[3 * (P.off + a) + c] *= sc;
+    __syncthreads();
+    const int a = (tile - P.tile0) * NE_TILE + threadIdx.x;
+    if (a < P.n)
+        for (int c = 0; c < 3; ++c) B.v[3 * (P.off + a) + c] *= s_sc;
 }
 
 // ------------------------------------------------------------ spring
@@ -673,7 +710,9 @@ void launch_advance(long long* step_base, long long by, cudaStream_t st)
 
 void launch_init_velocities(const DevBatch& B, int fix_cm, cudaStream_t st)
 {
-    k_init_v<<<B.n_rep, 256, 0, st>>>(B, fix_cm);
+    k_init_v_draw<<<B.n_tiles, NE_TILE, 0, st>>>(B);
+    k_init_v_center<<<B.n_tiles, NE_TILE, 0, st>>>(B, fix_cm);
+    k_init_v_scale<<<B.n_tiles, NE_TILE, 0, st>>>(B);
 }
 
 void launch_spring(const double* x, const double* x0, int n, double k, double* f, double* e,
