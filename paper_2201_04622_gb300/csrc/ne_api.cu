@@ -968,12 +968,15 @@ static ne_status backward_impl(ne_ctx* ctx, ne_precision prec, const double* x_d
     ne::launch_density(B, mixed, ctx->step_ctr, 0, st);
     ne::launch_force(B, S, mixed, ctx->step_ctr, 0, 0, st);
     if (gx_dev) ne::launch_export(B, mixed, gx_dev, nullptr, st);
+    if (mixed && !ne::backward_fits(ctx->eam.n_knots))
+        return fail(ctx, NE_EINVAL, "mixed backward: n_knots too large for one block's shared-memory bins");
     int nbb = ne::backward_bin_blocks(B);
     if (mixed && nbb > ctx->bins_blocks) {
         if (ctx->bins) cudaFree(ctx->bins);
         ctx->bins = nullptr;
         ctx->bins_blocks = 0;
-        NE_CU(cudaMalloc((void**)&ctx->bins, sizeof(float) * (size_t)nbb * 6 * ctx->eam.n_knots));
+        NE_CU(cudaMalloc((void**)&ctx->bins, ne::backward_bins_bytes(ctx->eam.n_knots, nbb)));
+        NE_CU(cudaMemset(ctx->bins, 0, ne::backward_bins_bytes(ctx->eam.n_knots, nbb)));  // F bins start at 0
         ctx->bins_blocks = nbb;
     }
     ne::launch_backward(B, mixed, gE, gx_dev, gtheta_dev, ctx->bins, nbb, accumulate, st);
@@ -1097,12 +1100,15 @@ static ne_status segment_impl(ne_ctx* ctx, const ne_md_params* md, int n_rep, co
     const bool mixed = md[0].prec == NE_MIXED;
     GradAcc ga{gtheta, gw, nullptr, 0, s_begin};
     if (gtheta) {
+        if (mixed && !ne::backward_fits(ctx->eam.n_knots))
+            return fail(ctx, NE_EINVAL, "mixed backward: n_knots too large for one block's shared-memory bins");
         ga.nbb = ne::backward_bin_blocks(B);
         if (mixed && ga.nbb > ctx->bins_blocks) {
             if (ctx->bins) cudaFree(ctx->bins);
             ctx->bins = nullptr;
             ctx->bins_blocks = 0;
-            NE_CU(cudaMalloc((void**)&ctx->bins, sizeof(float) * (size_t)ga.nbb * 6 * ctx->eam.n_knots));
+            NE_CU(cudaMalloc((void**)&ctx->bins, ne::backward_bins_bytes(ctx->eam.n_knots, ga.nbb)));
+        NE_CU(cudaMemset(ctx->bins, 0, ne::backward_bins_bytes(ctx->eam.n_knots, ga.nbb)));  // F bins start at 0
             ctx->bins_blocks = ga.nbb;
         }
         ga.bins = ctx->bins;

@@ -406,32 +406,47 @@ __device__ __forceinline__ double bwd_weight(const BwdWeight& W)
     return W.gw ? W.gw[*W.ctr + W.j - W.s_off] : W.gE;
 }
 
-// Mixed precision: FP32 basis weights accumulated in shared-memory FP32 bins
-// per block, flushed to bins[block][3*nk*2]; k_bins_reduce then sums the
-// blocks in FP64 in fixed order.  Bins are function-major, then value/slope,
-// then knot (bin_index), so the lanes of a warp adding one basis weight at
-// random intervals spread over all 32 banks (knot-major pairs used 16).  The bins take 120 KB, so a block is the
-// SM's only one: it has BWD_THREADS threads and works on BWD_THREADS /
-// (NE_TILE * TPA) tiles at once, enough warps to hide the atomics' latency.
+// Mixed precision.  phi and f (8 adds a pair): FP32 basis weights, the
+// slope weights without their factor h, into per-block FP32 bins in shared
+// memory (a block is the SM's only one, with BWD_THREADS threads working on
+// BWD_THREADS / (NE_TILE * TPA) tiles at once), flushed to global memory and
+// summed over the blocks in FP64 by k_bins_reduce.  F (4 adds an atom, on the
+// few intervals a crystal's densities fall in): one global array of 64-bit
+// fixed-point bins, 2^-32 per unit, the lanes of a warp on one interval
+// adding their weights before one integer atomic add each (exact, so the
+// order of the adds does not matter), read and cleared by k_bins_reduce.
+// (64-bit shared-memory bins for phi and f too made the whole gradient
+// bitwise reproducible but the kernel 1.7x slower: 64-bit shared atomics are
+// slower than FP32 ones on this SM.)  Bins are function-major, then
+// value/slope, then knot (bin_index), so a warp's adds at random intervals
+// spread over the shared-memory banks.
 constexpr int BWD_THREADS = 1024;
+constexpr double BWD_FIX = 4294967296.0;  // 2^32
 
 // bin of knot parameter (function fn, knot k, c = 0 value / 1 slope); the
 // knot parameters theta themselves are [fn][k][c]
 __host__ __device__ __forceinline__ int bin_index(int fn, int k, int c, int nk) { return (2 * fn + c) * nk + k; }
 
+// The global bins buffer: the 2 nk 64-bit F bins first (at a fixed place, so
+// a launch with another block count finds them cleared), then each block's
+// 4 nk FP32 phi/f bins
+__host__ __device__ __forceinline__ size_t bwd_block_bytes(int nk) { return sizeof(float) * 4 * (size_t)nk; }
+__host__ __device__ __forceinline__ size_t bwd_f_bytes(int nk) { return sizeof(unsigned long long) * 2 * (size_t)nk; }
+
 template <int TPA>
 __global__ void __launch_bounds__(BWD_THREADS, 1)
-    k_backward_mixed(DevBatch B, float* __restrict__ bins, BwdWeight W)
+    k_backward_mixed(DevBatch B, unsigned char* __restrict__ bins, BwdWeight W)
 {
     constexpr int TPB = NE_TILE * TPA, TILES = BWD_THREADS / TPB;
     if (bwd_weight(W) == 0.0) return;
-    extern __shared__ float sb[];
+    extern __shared__ __align__(16) unsigned char sbytes[];
     const int nk = B.tab.nk;
-    const int nb = 3 * nk * 2;
-    for (int q = threadIdx.x; q < nb; q += blockDim.x) sb[q] = 0.f;
+    float* const spf = (float*)sbytes;  // [4 nk] phi, f
+    unsigned long long* const gF = (unsigned long long*)bins;  // global F bins: F's bin_index - 4 nk
+    for (int q = threadIdx.x; q < 4 * nk; q += blockDim.x) spf[q] = 0.f;
     __syncthreads();
-    const float h_r = (float)B.tab.h_r, inv_h = B.tab.inv_h_rf;
-    const float h_rho = (float)B.tab.h_rho;
+    const float inv_h = B.tab.inv_h_rf;
+    const float fix = (float)BWD_FIX;
     const int sub = threadIdx.x / TPB, tt = threadIdx.x % TPB;
     for (int tile = blockIdx.x * TILES + sub; tile < B.n_tiles; tile += gridDim.x * TILES) {
         const int rep = B.tile_rep[tile];
@@ -445,12 +460,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
             float4 pi = B.posF[i];
             const float dFi = pi.w;
             const int m = B.scnt[i * TPA + lane];
-            // each atom of a warp starts at another point of its list: lists
-            // run through the neighbour shells in the same order, so in step
-            // they would send the warp's weights to the same bins at once
-            const int rot = m > 0 ? (local * 7) % m : 0;
-            for (int qq = 0; qq < m; ++qq) {
-                const int q = qq + rot < m ? qq + rot : qq + rot - m;
+            for (int q = 0; q < m; ++q) {
                 const int jn = B.sl[(q * B.n_tot + i) * TPA + lane];
                 float4 pj = B.posF[jn];
                 float dx = mi(pj.x - pi.x, Lf0, iL0), dy = mi(pj.y - pi.y, Lf1, iL1),
@@ -459,53 +469,81 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
                 float t = r * inv_h;
                 int kk = min(max((int)t, 0), nk - 2);
                 float w[4];
-                hermite_wf(t - (float)kk, h_r, w);
-                // w = (y_kk, m_kk, y_kk+1, m_kk+1) weights
+                hermite_wf(t - (float)kk, 1.f, w);  // slope weights without h
+                // w = (y_kk, m_kk / h, y_kk+1, m_kk+1 / h) weights
                 for (int c = 0; c < 4; ++c) {
-                    atomicAdd(sb + bin_index(0, kk + (c >> 1), c & 1, nk), 0.5f * w[c]);
-                    atomicAdd(sb + bin_index(1, kk + (c >> 1), c & 1, nk), dFi * w[c]);
+                    atomicAdd(spf + bin_index(0, kk + (c >> 1), c & 1, nk), 0.5f * w[c]);
+                    atomicAdd(spf + bin_index(1, kk + (c >> 1), c & 1, nk), dFi * w[c]);
                 }
             }
             if (lane == 0) {
                 double t = B.rho[i] * B.tab.inv_h_rho;
                 int kk = min(max((int)t, 0), nk - 2);
                 float w[4];
-                hermite_wf((float)(t - kk), h_rho, w);
-                for (int c = 0; c < 4; ++c) atomicAdd(sb + bin_index(2, kk + (c >> 1), c & 1, nk), w[c]);
+                hermite_wf((float)(t - kk), 1.f, w);  // slope weights without h
+                // the densities of a crystal fall in a few F intervals, so the
+                // atoms of a warp mostly share one: the lanes on an interval
+                // add their fixed-point weights and one of them does the
+                // atomic adds, instead of all of them contending for the bins
+                long long wq[4];
+                for (int c = 0; c < 4; ++c) wq[c] = __float2ll_rn(w[c] * fix);
+                const unsigned act = __activemask();
+                const unsigned grp = __match_any_sync(act, kk);
+                long long g[4] = {0, 0, 0, 0};
+                for (unsigned rest = act; rest; rest &= rest - 1) {
+                    const int src = __ffs(rest) - 1;
+                    for (int c = 0; c < 4; ++c) {
+                        const long long v = __shfl_sync(act, wq[c], src);
+                        if (grp & (1u << src)) g[c] += v;
+                    }
+                }
+                if ((int)(threadIdx.x & 31) == __ffs(grp) - 1)
+                    for (int c = 0; c < 4; ++c)
+                        atomicAdd(gF + (bin_index(2, kk + (c >> 1), c & 1, nk) - 4 * nk), (unsigned long long)g[c]);
             }
         }
     }
     __syncthreads();
-    float* out = bins + (size_t)blockIdx.x * nb;
-    for (int q = threadIdx.x; q < nb; q += blockDim.x) out[q] = sb[q];
+    float* opf = (float*)(bins + bwd_f_bytes(nk) + (size_t)blockIdx.x * bwd_block_bytes(nk));
+    for (int q = threadIdx.x; q < 4 * nk; q += blockDim.x) opf[q] = spf[q];
 }
 
-// gtheta[q] (+)= gE * (sum over blocks of bin q's values): a block of
-// BR_COLS x BR_SEG threads takes BR_COLS knot parameters; segment g sums the
-// blocks b = g, g + BR_SEG, ... in FP64, then the segments are added in a
-// fixed order (the same every call).
+// gtheta[q] (+)= gE * (the bin total of parameter q): a block of BR_COLS x
+// BR_SEG threads takes BR_COLS knot parameters.  phi and f: segment g adds
+// the blocks b = g, g + BR_SEG, ... in FP64, then the segments in a fixed
+// order; F: the global fixed-point bin (2^-32), read and cleared for the next
+// launch.  A slope total is scaled by h once.
 constexpr int BR_COLS = 32, BR_SEG = 8;
 
 __global__ void __launch_bounds__(BR_COLS* BR_SEG)
-    k_bins_reduce(const float* __restrict__ bins, int n_blocks, int nb, int nk, BwdWeight W,
+    k_bins_reduce(unsigned char* __restrict__ bins, int n_blocks, int nk, double h_r, double h_rho, BwdWeight W,
                   double* __restrict__ gtheta, int accumulate)
 {
     __shared__ double part[BR_SEG][BR_COLS];
+    const int nb = 6 * nk;
     const int col = threadIdx.x % BR_COLS, g = threadIdx.x / BR_COLS;
     const int q = blockIdx.x * BR_COLS + col;  // knot parameter [fn][k][c]
     const double gE = bwd_weight(W);
     if (gE == 0.0) return;
+    const size_t stride = bwd_block_bytes(nk);
+    const int fn = q / (2 * nk), k = (q % (2 * nk)) >> 1, c = q & 1;
+    const int bq = bin_index(fn, k, c, nk);
     double acc = 0.0;
-    if (q < nb) {
-        const int fn = q / (2 * nk), k = (q % (2 * nk)) >> 1, c = q & 1;
-        const int bq = bin_index(fn, k, c, nk);
-        for (int b = g; b < n_blocks; b += BR_SEG) acc += (double)bins[(size_t)b * nb + bq];
-    }
+    if (q < nb && fn < 2)
+        for (int b = g; b < n_blocks; b += BR_SEG)
+            acc += (double)((const float*)(bins + bwd_f_bytes(nk) + (size_t)b * stride))[bq];
     part[g][col] = acc;
     __syncthreads();
     if (g == 0 && q < nb) {
         double t = 0.0;
-        for (int h = 0; h < BR_SEG; ++h) t += part[h][col];
+        if (fn < 2) {
+            for (int h = 0; h < BR_SEG; ++h) t += part[h][col];
+        } else {
+            unsigned long long* gF = (unsigned long long*)bins + (bq - 4 * nk);
+            t = (double)(long long)*gF * (1.0 / BWD_FIX);
+            *gF = 0ull;
+        }
+        if (c) t *= fn < 2 ? h_r : h_rho;
         gtheta[q] = (accumulate ? gtheta[q] : 0.0) + gE * t;
     }
 }
@@ -672,7 +710,7 @@ void launch_force(const DevBatch& B, const Sched& S, bool mixed, const long long
 
 cudaError_t prepare_backward(const DevBatch& B)
 {
-    const int smem = (int)(sizeof(float) * 6 * (size_t)B.tab.nk);
+    const int smem = (int)bwd_block_bytes(B.tab.nk);
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
     switch (B.tpa) {
     case 1: return cudaFuncSetAttribute(k_backward_mixed<1>, a, smem);
@@ -680,6 +718,24 @@ cudaError_t prepare_backward(const DevBatch& B)
     case 4: return cudaFuncSetAttribute(k_backward_mixed<4>, a, smem);
     default: return cudaFuncSetAttribute(k_backward_mixed<8>, a, smem);
     }
+}
+
+size_t backward_block_bytes(int nk) { return bwd_block_bytes(nk); }
+
+size_t backward_bins_bytes(int nk, int n_blocks)
+{
+    return bwd_f_bytes(nk) + bwd_block_bytes(nk) * (size_t)n_blocks;
+}
+
+bool backward_fits(int nk)
+{
+    int dev = 0, smem_max = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return bwd_block_bytes(nk) <= (size_t)smem_max;
 }
 
 int backward_bin_blocks(const DevBatch& B)
@@ -722,10 +778,10 @@ void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, doubl
     const int nb = 3 * nk * 2;
     const BwdWeight W{gE, gw, ctr, j, s_off};
     if (mixed) {
-        size_t smem = (size_t)nb * sizeof(float);
+        size_t smem = bwd_block_bytes(nk);
 #define NE_BWD(T)                                                                                        \
     if (set_attr) cudaFuncSetAttribute(k_backward_mixed<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    k_backward_mixed<T><<<n_bin_blocks, BWD_THREADS, smem, st>>>(B, bins, W)
+    k_backward_mixed<T><<<n_bin_blocks, BWD_THREADS, smem, st>>>(B, (unsigned char*)bins, W)
         switch (B.tpa) {
         case 1: NE_BWD(1); break;
         case 2: NE_BWD(2); break;
@@ -733,8 +789,8 @@ void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, doubl
         default: NE_BWD(8); break;
         }
 #undef NE_BWD
-        k_bins_reduce<<<(nb + BR_COLS - 1) / BR_COLS, BR_COLS * BR_SEG, 0, st>>>(bins, n_bin_blocks, nb, nk, W, gtheta,
-                                                                                 accumulate ? 1 : 0);
+        k_bins_reduce<<<(nb + BR_COLS - 1) / BR_COLS, BR_COLS * BR_SEG, 0, st>>>(
+            (unsigned char*)bins, n_bin_blocks, nk, B.tab.h_r, B.tab.h_rho, W, gtheta, accumulate ? 1 : 0);
     } else {
         if (!accumulate) cudaMemsetAsync(gtheta, 0, sizeof(double) * nb, st);
         dim3 g(B.n_tiles);

@@ -306,6 +306,9 @@ void launch_msd_sample(const DevBatch& B, double* acc, cudaStream_t st);
 // gE, or with gw != nullptr the per-step weight gw[*ctr + j - s_off] read on
 // the device (runs replayed from graphs); set_attr: set the kernel's shared-
 // memory attribute (not inside a stream capture)
+size_t backward_block_bytes(int nk);  // one mixed backward block's bins (device and shared memory)
+size_t backward_bins_bytes(int nk, int n_blocks);  // the whole bins buffer: F's (zeroed once), then the blocks'
+bool backward_fits(int nk);           // those bins fit one block's shared memory
 void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, double* gtheta,
                      float* bins, int n_bin_blocks, bool accumulate, cudaStream_t st,
                      const double* gw = nullptr, const long long* ctr = nullptr, int j = 0,

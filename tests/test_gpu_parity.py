@@ -518,6 +518,32 @@ def test_backward_matches_oracle_gradient(ctx, pot, prec, tol):
     assert rel(N(gx), -2.0 * fo) < (1e-10 if prec == ne.NE_FP64 else 5e-5)
 
 
+def test_mixed_backward_repeats_and_keeps_its_f_bins_clean(ctx, pot):
+    """The mixed backward's F gradient is summed in 64-bit fixed point in a
+    global array that each call reads and clears: repeated calls, and a call
+    after a larger configuration (more blocks), give the same F gradient bit
+    for bit and the same phi and f gradients to FP32 rounding; and it
+    follows the oracle."""
+    p, th = pot
+    x0, box = crystal(O.BCC, 8)
+    x = W.displaced(x0, 0.08, 11)
+    go = O.eam_grad_theta(p, th, x, box)
+    shape = (3, W.EAM_FE_LIKE["n_knots"], 2)
+    runs = []
+    for q in range(3):
+        if q == 2:  # a larger configuration in between: more blocks, the F bins reused
+            xb, bb = crystal(O.BCC, 14)
+            ne.ne_eam_backward(ctx, ne.NE_MIXED, T(xb), bb, 1.0, None,
+                               torch.zeros(shape, dtype=torch.float64, device=DEV))
+        g = torch.zeros(shape, dtype=torch.float64, device=DEV)
+        ne.ne_eam_backward(ctx, ne.NE_MIXED, T(x), box, 1.0, None, g)
+        runs.append(g)
+    for g in runs[1:]:
+        assert torch.equal(runs[0][2], g[2])
+        assert rel(N(g), N(runs[0])) < 1e-6
+    assert rel(N(runs[0]), go) < 1e-3
+
+
 def test_autograd_function_against_finite_differences(ctx, pot):
     p, th = pot
     x0, box = crystal(O.BCC, 5)
