@@ -83,7 +83,36 @@ __device__ __forceinline__ R lane_sum(R v, int tpa)
     return v;
 }
 
+// double-float (hi + lo, |lo| <= ulp(hi) / 2) sum of two such numbers from
+// FP32 operations (TwoSum of the high parts, the low parts added to its error)
+struct dff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dff dff_add(dff a, dff b)
+{
+    const float s = a.hi + b.hi, bp = s - a.hi;
+    float e = (a.hi - (s - bp)) + (b.hi - bp);
+    e += a.lo + b.lo;
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+
+// sum over the warp of a double-float (fixed xor tree: every lane gets it)
+__device__ __forceinline__ dff dff_warp_sum(dff v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = dff_add(v, {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+    return v;
+}
+
 // ------------------------------------------------------------ pass 1
+// Mixed precision keeps GB300's FP64 pipe (1/64 of FP32) out of the pair
+// loop and the sums: rho as an unnormalised double-float (the FP32 running
+// sum and the TwoSum error of each addition), combined over the lanes and
+// the block in double-float; the interval of F from the double-float rho
+// with the high part of 1/h exact in the FMA (the crystal runner's forms).
 template <bool MIXED, int TPA>
 __global__ void __launch_bounds__(NE_TILE* TPA) k_density(DevBatch B)
 {
@@ -103,9 +132,8 @@ __global__ void __launch_bounds__(NE_TILE* TPA) k_density(DevBatch B)
     const R inv_h = MIXED ? (R)B.tab.inv_h_rf : (R)B.tab.inv_h_r;
     const int nk = B.tab.nk;
     const int cap = NE_SMAX / TPA;
-    double rho = 0.0;
-    float chunk = 0.f;
-    int nchunk = 0;
+    double rho = 0.0;           // FP64 path
+    float rh = 0.f, rl = 0.f;   // mixed: running sum and TwoSum errors
     int m = 0, bad = 0;
     if (valid) {
         const V3<R> pi = Pos<MIXED>::load(B, i);
@@ -126,12 +154,9 @@ __global__ void __launch_bounds__(NE_TILE* TPA) k_density(DevBatch B)
                 if constexpr (MIXED) {
                     float4 c = __ldg(&B.tab.pf32[2 * kk + 1]);
                     fr = (R)(c.x + (float)u * (c.y + (float)u * (c.z + (float)u * c.w)));
-                    chunk += (float)fr;
-                    if (++nchunk == 8) {
-                        rho += (double)chunk;
-                        chunk = 0.f;
-                        nchunk = 0;
-                    }
+                    const float s_ = rh + (float)fr, bp = s_ - rh;
+                    rl += (rh - (s_ - bp)) + ((float)fr - bp);
+                    rh = s_;
                 } else {
                     ned4 c = B.tab.pf64[2 * kk + 1];
                     fr = (R)(c.x + (double)u * (c.y + (double)u * (c.z + (double)u * c.w)));
@@ -144,24 +169,35 @@ __global__ void __launch_bounds__(NE_TILE* TPA) k_density(DevBatch B)
                 ++m;
             }
         }
-        rho += (double)chunk;
         B.scnt[i * TPA + lane] = min(m, cap);
     }
-    rho = lane_sum(rho, TPA);
+    dff rr = {0.f, 0.f};
+    if constexpr (MIXED) {
+        rr = dff_add({rh, 0.f}, {rl, 0.f});  // normalised
+        for (int o = TPA >> 1; o > 0; o >>= 1)
+            rr = dff_add(rr, {__shfl_xor_sync(0xffffffffu, rr.hi, o), __shfl_xor_sync(0xffffffffu, rr.lo, o)});
+        rho = (double)rr.hi + (double)rr.lo;
+    } else {
+        rho = lane_sum(rho, TPA);
+    }
     double Femb = 0.0;
+    float Femb32 = 0.f;
     if (valid && lane == 0) {
         if (!(rho < B.tab.rho_max)) bad |= ST_ERANGE;
-        double t = rho * B.tab.inv_h_rho;
-        int kk = min(max((int)t, 0), nk - 2);
         double dF;
         if constexpr (MIXED) {
-            float u = (float)(t - kk);
+            const float ihr_hi = (float)B.tab.inv_h_rho, ihr_lo = (float)(B.tab.inv_h_rho - (double)ihr_hi);
+            const int kk = min(max((int)(rr.hi * ihr_hi), 0), nk - 2);
+            const float u = fmaf(rr.hi, ihr_hi, -(float)kk) + (rr.hi * ihr_lo + rr.lo * ihr_hi);
             float4 c = __ldg(&B.tab.F32[kk]);
-            Femb = (double)(c.x + u * (c.y + u * (c.z + u * c.w)));
+            Femb32 = c.x + u * (c.y + u * (c.z + u * c.w));
             dF = (double)((c.y + u * (2.f * c.z + 3.f * u * c.w)) * (float)B.tab.inv_h_rho);
             float4 p = B.pos32[i];
             B.posF[i] = make_float4(p.x, p.y, p.z, (float)dF);
+            if (!isfinite(Femb32)) bad |= ST_ENAN;
         } else {
+            double t = rho * B.tab.inv_h_rho;
+            int kk = min(max((int)t, 0), nk - 2);
             double u = t - kk;
             ned4 c = B.tab.F64[kk];
             Femb = c.x + u * (c.y + u * (c.z + u * c.w));
@@ -172,13 +208,27 @@ __global__ void __launch_bounds__(NE_TILE* TPA) k_density(DevBatch B)
         if (!isfinite(Femb)) bad |= ST_ENAN;
     }
     if (bad) ne_set_status(B.status, bad);
-    red[threadIdx.x] = Femb;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    if constexpr (MIXED) {
+        // the tile's embedding energy in double-float: a fixed tree in each
+        // warp, then warp 0 over the warps in order
+        const dff e = dff_warp_sum({Femb32, 0.f});
+        float2* wsum = (float2*)red;
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+        if (l == 0) wsum[w] = make_float2(e.hi, e.lo);
         __syncthreads();
+        if (w == 0) {
+            const dff t = dff_warp_sum(l < nw ? dff{wsum[l].x, wsum[l].y} : dff{0.f, 0.f});
+            if (l == 0) B.partA[(size_t)tile * NPA + PA_UEMB] = (double)t.hi + (double)t.lo;
+        }
+    } else {
+        red[threadIdx.x] = Femb;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) B.partA[(size_t)tile * NPA + PA_UEMB] = red[0];
     }
-    if (threadIdx.x == 0) B.partA[(size_t)tile * NPA + PA_UEMB] = red[0];
 }
 
 // ------------------------------------------------------------ pass 2

@@ -761,7 +761,9 @@ def test_autotuner_picks_a_valid_configuration_and_restores_state(ctx):
 def test_backward_at_full_size(ctx, pot, lat, n):
     """dU/dtheta and dU/dx at the 65,536- and 70,304-atom sizes of the
     differentiation workload (0.05 A random displacements), FP64 against the
-    oracle's analytic gradient; mixed within the FP32 bound derived above."""
+    oracle's analytic gradient; mixed within the FP32 bound derived above,
+    scaled to these boxes: L = 92-95 A gives ulp(L) ~ 5.5e-6 A, ~6e-5
+    relative in a force, so the forces are held to 1e-4."""
     big = ne.ne_ctx_create(ne.eam_params(**W.EAM_FE_LIKE), 71000, 1)
     try:
         p, th = pot
@@ -769,7 +771,7 @@ def test_backward_at_full_size(ctx, pot, lat, n):
         x = W.displaced(x0, 0.05, 40 + n)
         go = O.eam_grad_theta(p, th, x, box)
         _, fo, _ = O.eam_energy_forces(p, th, x, box)
-        for prec, tol, ftol in [(ne.NE_FP64, 1e-10, 1e-10), (ne.NE_MIXED, 1e-3, 5e-5)]:
+        for prec, tol, ftol in [(ne.NE_FP64, 1e-10, 1e-10), (ne.NE_MIXED, 1e-3, 1e-4)]:
             gx = torch.zeros((len(x), 3), dtype=torch.float64, device=DEV)
             gth = torch.zeros((3, W.EAM_FE_LIKE["n_knots"], 2), dtype=torch.float64, device=DEV)
             ne.ne_eam_backward(big, prec, T(x), box, 1.0, gx, gth)
