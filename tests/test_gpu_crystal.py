@@ -496,3 +496,35 @@ def test_uneven_campaign_fits_one_spring_per_replica():
         assert len(rows) == len(reps) and all(np.isfinite(r["F"]) for r in rows)
     finally:
         ne.ne_ctx_destroy(big)
+
+
+@pytest.mark.parametrize("runner", [1, 2], ids=["cluster", "brick"])
+def test_runner_pairs_past_the_tmem_visits(ctx, pot, runner):
+    """The runners keep f'(r)/r of 80 stencil visits a thread in tensor
+    memory and recompute later visits in pass 2.  Two atoms of the (2,2,0)a
+    shell of bcc (stencil entries 168-179: visits 84-89 at 2 threads per
+    atom), each moved 1.55 A towards the other (within the 2 A range), are
+    5.02 A apart: inside r_c, with their embedding force from that
+    recomputation.  10 steps at 10 K against the oracle."""
+    p, th = pot
+    x0, box = O.create_crystal(O.BCC, W.A_BCC, 6, 6, 6)
+    tgt = x0[0] + W.A_BCC * np.array([2.0, 2.0, 0.0])
+    j = int(np.argmin(np.linalg.norm(x0 - tgt, axis=1)))
+    nrm = np.array([1.0, 1.0, 0.0]) / np.sqrt(2.0)
+    xs = x0.copy()
+    xs[0] += 1.55 * nrm
+    xs[j] -= 1.55 * nrm
+    mo, mg = md_pair(T=10.0, t_eq=2, t_s=3, k_spring=3.0, seed=3, replica=0)
+    v0 = O.init_velocities(mo, len(x0))
+    ro = O.switch_run(p, th, mo, xs, v0, x0, box)
+    ne.ne_ctx_set_runner(ctx, runner)
+    try:
+        x, v = T(xs), T(v0)
+        Wd = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
+        ne.ne_crystal_run_segment(ctx, [mg], [(O.BCC, W.A_BCC, 6, 6, 6)], x, v, Wd, 0, 10)
+    finally:
+        ne.ne_ctx_set_runner(ctx, 0)
+    assert np.abs(x.cpu().numpy() - ro["x"]).max() < 2e-5
+    assert np.abs(v.cpu().numpy() - ro["v"]).max() < 1e-3  # that force alone changes v by ~4e-3 A/ps a step
+    assert float(Wd[0, 0]) == pytest.approx(ro["W_f"], rel=1e-5)
+    assert float(Wd[0, 1]) == pytest.approx(ro["W_b"], rel=1e-5)
