@@ -12,10 +12,10 @@
 // rounding of its replica sums (which depend on how the atoms are split over
 // CTAs).  Per step:
 //   replica sums of step s from the CTA partials written at the end of s-1
-//   pass 1: rho, pair forces and energy, short list (u_j from L2);
+//   pass 1: rho, pair forces and energy, f'(r)/r of every visit to tensor memory (u_j from L2);
 //           F'(rho) of the owned atoms to global memory
 //   [grid barrier]
-//   pass 2: embedding forces over the short list (u_j, F'_j from L2)
+//   pass 2: embedding forces over the visits inside r_c (u_j, F'_j from L2)
 //   fused step of the owned atoms; u of step s+1 to the other parity buffer;
 //           CTA partials for step s+1
 //   [grid barrier]

@@ -19,9 +19,10 @@
 //                      CTA broadcast at the end of step s-1): noise mean,
 //                      spring mean, max |u|; the work increment of step s-1;
 //                      pass 1: rho, the pair forces phi'(r) and energy phi(r),
-//                      short list; F(rho), F'(rho), F' broadcast
-//   [cluster barrier]  pass 2: the embedding forces (F'_i + F'_j) f'(r) over
-//                      the short list
+//                      f'(r)/r of every visit into tensor memory; F(rho),
+//                      F'(rho), F' broadcast
+//   [cluster barrier]  pass 2: the embedding forces (F'_i + F'_j) f'(r) r_ij/r
+//                      over the visits inside r_c, f'(r)/r from tensor memory
 //   [arrive]           closing and opening half kicks, drift,
 //                      Ornstein-Uhlenbeck, drift; the normals of step s+1
 //                      (counter-based, so drawn one step ahead)

@@ -5,7 +5,7 @@
 
 #include "ne_internal.cuh"
 
-#define NE_STENCIL_MAX 512  // stencil entries per basis site (short lists store entry / 2 in a byte)
+#define NE_STENCIL_MAX 512  // stencil entries per basis site
 #define NE_STENCIL_PAD 16   // far entries ending each basis site's stencil (outside any cutoff)
 
 struct XRep {
