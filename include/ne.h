@@ -417,7 +417,7 @@ typedef struct {
  * advanced in place; W_dev [n_rep][2] accumulates (forward, backward) work.
  * md[r].prec must be NE_MIXED; at least 3 cells per axis and box edges
  * > 2 r_c + 1.2 A; replicas above 4096 atoms run on the brick runner
- * (ne_ctx_set_runner), which needs the batch's CTAs (one per 96-384 atoms)
+ * (ne_ctx_set_runner), which needs the batch's CTAs (one per 96-768 atoms)
  * to fit the device at once (NE_ENOMEM otherwise); a grid barrier that
  * waits longer than a few seconds gives NE_ETIMEOUT.  The barostat
  * (md[r].npt, reversible-scaling path) runs on both runners: the box and

@@ -1474,7 +1474,7 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
     P.npt = false;
     for (int r = 0; r < n_rep; ++r) P.npt = P.npt || xr[r].npt != 0;
     if (brick) {
-        // Brick runner: the largest threads-per-atom (8, 4, 2) at which every
+        // Brick runner: the largest threads-per-atom (8, 4, 2, 1) at which every
         // replica's blocks of cells, one CTA each, fit the device at once
         int gnb = 0, glut = 0;
         for (int r = 0; r < n_rep; ++r) {
@@ -1483,7 +1483,7 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
             glut = std::max(glut, (xr[r].nx + 2 * Mr) * (xr[r].ny + 2 * Mr) + xr[r].nb * (xr[r].nz + 2 * Mr));
         }
         P.brick = false;
-        for (int tpa : {8, 4, 2}) {
+        for (int tpa : {8, 4, 2, 1}) {
             const size_t base = (ne::brick_smem_bytes(tpa, gnb, glut, P.npt) + 15) & ~(size_t)15;
             if (base > (size_t)smem_max) continue;
             const long long fit = ((long long)smem_max - (long long)base) / (2 * (long long)sizeof(float4));

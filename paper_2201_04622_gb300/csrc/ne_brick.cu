@@ -31,7 +31,7 @@
 // others leave at their next barrier.  Loads of data other CTAs wrote use
 // ld.global.cg (L2, never a stale L1 line).
 //
-// Threads: TPA threads per atom (2, 4 or 8, chosen on the host so that the
+// Threads: TPA threads per atom (8, 4, 2 or 1, the largest at which the
 // batch's CTAs fit the device at one CTA per SM); thread t works on slot
 // t % SLOTS and takes the stencil entries k = lane + TPA q, lane = t / SLOTS,
 // so the 32 threads of a warp read one stencil entry.  One thread per atom
@@ -904,6 +904,7 @@ int brick_max_ctas(int tpa, size_t smem, bool npt)
     }
     cudaError_t e;
     switch (tpa) {
+    case 1: e = npt ? brick_occupancy<1, true>(smem, &per) : brick_occupancy<1, false>(smem, &per); break;
     case 2: e = npt ? brick_occupancy<2, true>(smem, &per) : brick_occupancy<2, false>(smem, &per); break;
     case 4: e = npt ? brick_occupancy<4, true>(smem, &per) : brick_occupancy<4, false>(smem, &per); break;
     default: e = npt ? brick_occupancy<8, true>(smem, &per) : brick_occupancy<8, false>(smem, &per); break;
@@ -938,6 +939,7 @@ cudaError_t launch_brick(int tpa, const XRep* reps, const int* cta_rep, int n_ct
 #define NE_BRICK_ARGS cfg, reps, cta_rep, st_vec, st_dist, x, v, W, status, S, s_begin, n_steps, tab, work, k_lo, \
                       lam_tab, wcum, bb, n_tot, boxes_out
     switch (tpa) {
+    case 1: return npt ? brick_launch<1, true>(NE_BRICK_ARGS) : brick_launch<1, false>(NE_BRICK_ARGS);
     case 2: return npt ? brick_launch<2, true>(NE_BRICK_ARGS) : brick_launch<2, false>(NE_BRICK_ARGS);
     case 4: return npt ? brick_launch<4, true>(NE_BRICK_ARGS) : brick_launch<4, false>(NE_BRICK_ARGS);
     case 8: return npt ? brick_launch<8, true>(NE_BRICK_ARGS) : brick_launch<8, false>(NE_BRICK_ARGS);
