@@ -976,7 +976,6 @@ static ne_status backward_impl(ne_ctx* ctx, ne_precision prec, const double* x_d
         ctx->bins = nullptr;
         ctx->bins_blocks = 0;
         NE_CU(cudaMalloc((void**)&ctx->bins, ne::backward_bins_bytes(ctx->eam.n_knots, nbb)));
-        NE_CU(cudaMemset(ctx->bins, 0, ne::backward_bins_bytes(ctx->eam.n_knots, nbb)));  // F bins start at 0
         ctx->bins_blocks = nbb;
     }
     ne::launch_backward(B, mixed, gE, gx_dev, gtheta_dev, ctx->bins, nbb, accumulate, st);
@@ -1108,7 +1107,6 @@ static ne_status segment_impl(ne_ctx* ctx, const ne_md_params* md, int n_rep, co
             ctx->bins = nullptr;
             ctx->bins_blocks = 0;
             NE_CU(cudaMalloc((void**)&ctx->bins, ne::backward_bins_bytes(ctx->eam.n_knots, ga.nbb)));
-        NE_CU(cudaMemset(ctx->bins, 0, ne::backward_bins_bytes(ctx->eam.n_knots, ga.nbb)));  // F bins start at 0
             ctx->bins_blocks = ga.nbb;
         }
         ga.bins = ctx->bins;

@@ -462,9 +462,9 @@ __device__ __forceinline__ double bwd_weight(const BwdWeight& W)
 // BWD_THREADS / (NE_TILE * TPA) tiles at once), flushed to global memory and
 // summed over the blocks in FP64 by k_bins_reduce.  F (4 adds an atom, on the
 // few intervals a crystal's densities fall in): one global array of 64-bit
-// fixed-point bins, 2^-32 per unit, the lanes of a warp on one interval
-// adding their weights before one integer atomic add each (exact, so the
-// order of the adds does not matter), read and cleared by k_bins_reduce.
+// fixed-point bins, 2^-32 per unit, cleared before the launch, the lanes of a
+// warp on one interval adding their weights before one integer atomic add
+// each (exact, so the order of the adds does not matter).
 // (64-bit shared-memory bins for phi and f too made the whole gradient
 // bitwise reproducible but the kernel 1.7x slower: 64-bit shared atomics are
 // slower than FP32 ones on this SM.)  Bins are function-major, then
@@ -477,9 +477,8 @@ constexpr double BWD_FIX = 4294967296.0;  // 2^32
 // knot parameters theta themselves are [fn][k][c]
 __host__ __device__ __forceinline__ int bin_index(int fn, int k, int c, int nk) { return (2 * fn + c) * nk + k; }
 
-// The global bins buffer: the 2 nk 64-bit F bins first (at a fixed place, so
-// a launch with another block count finds them cleared), then each block's
-// 4 nk FP32 phi/f bins
+// The global bins buffer: the 2 nk 64-bit F bins first (cleared by each
+// launch), then each block's 4 nk FP32 phi/f bins
 __host__ __device__ __forceinline__ size_t bwd_block_bytes(int nk) { return sizeof(float) * 4 * (size_t)nk; }
 __host__ __device__ __forceinline__ size_t bwd_f_bytes(int nk) { return sizeof(unsigned long long) * 2 * (size_t)nk; }
 
@@ -561,7 +560,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
 // gtheta[q] (+)= gE * (the bin total of parameter q): a block of BR_COLS x
 // BR_SEG threads takes BR_COLS knot parameters.  phi and f: segment g adds
 // the blocks b = g, g + BR_SEG, ... in FP64, then the segments in a fixed
-// order; F: the global fixed-point bin (2^-32), read and cleared for the next
+// order; F: the global fixed-point bin (2^-32), cleared before each backward
 // launch.  A slope total is scaled by h once.
 constexpr int BR_COLS = 32, BR_SEG = 8;
 
@@ -589,9 +588,7 @@ __global__ void __launch_bounds__(BR_COLS* BR_SEG)
         if (fn < 2) {
             for (int h = 0; h < BR_SEG; ++h) t += part[h][col];
         } else {
-            unsigned long long* gF = (unsigned long long*)bins + (bq - 4 * nk);
-            t = (double)(long long)*gF * (1.0 / BWD_FIX);
-            *gF = 0ull;
+            t = (double)(long long)((const unsigned long long*)bins)[bq - 4 * nk] * (1.0 / BWD_FIX);
         }
         if (c) t *= fn < 2 ? h_r : h_rho;
         gtheta[q] = (accumulate ? gtheta[q] : 0.0) + gE * t;
@@ -829,6 +826,7 @@ void launch_backward(const DevBatch& B, bool mixed, double gE, double* gx, doubl
     const BwdWeight W{gE, gw, ctr, j, s_off};
     if (mixed) {
         size_t smem = bwd_block_bytes(nk);
+        cudaMemsetAsync(bins, 0, bwd_f_bytes(nk), st);  // the global F bins
 #define NE_BWD(T)                                                                                        \
     if (set_attr) cudaFuncSetAttribute(k_backward_mixed<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     k_backward_mixed<T><<<n_bin_blocks, BWD_THREADS, smem, st>>>(B, (unsigned char*)bins, W)
