@@ -195,13 +195,27 @@ def test_cluster_size_changes_rounding_only(ctx):
         ne.ne_ctx_set_cluster_size(ctx, 17)
 
 
-def test_free_energy_estimators_and_convergence_workflow(ctx):
+def test_free_energy_estimators_and_convergence_workflow(ctx, pot):
     """Two-sided FL estimate and the one-sided Jarzynski estimates from the
     same works agree to within the dissipation; dissipation falls with the
-    switching time (Sec. III.B)."""
+    switching time (Sec. III.B); and every F(t_s) point, with its Jarzynski
+    estimates and dissipation, equals the one assembled from the oracle's
+    runs of the same seeds (Philox replica indices 0-3) to 1e-5 eV/atom."""
     from paper_2201_04622_gb300 import workflow as WF
-    rows = WF.fl_convergence(ctx, O.BCC, W.A_BCC, 5, 800.0, MASS, 2.8, [500, 2000], [1, 2, 3, 4], 300,
-                             runner="crystal")
+    seeds, t_s_list = [1, 2, 3, 4], [500, 2000]
+    rows = WF.fl_convergence(ctx, O.BCC, W.A_BCC, 5, 800.0, MASS, 2.8, t_s_list, seeds, 300, runner="crystal")
+    p, th = pot
+    x0, box = O.create_crystal(O.BCC, W.A_BCC, 5, 5, 5)
+    for r, ts in zip(rows, t_s_list):
+        wf, wb = [], []
+        for q, seed in enumerate(seeds):
+            mo = O.md(mass=MASS, T=800.0, k_spring=2.8, t_eq=300, t_s=ts, seed=seed, replica=q, fix_cm=1)
+            ro = O.switch_run(p, th, mo, x0, O.init_velocities(mo, len(x0)), x0, box)
+            wf.append(ro["W_f"])
+            wb.append(ro["W_b"])
+        fo = WF.fl_free_energies(O.BCC, W.A_BCC, 5, 800.0, MASS, 2.8, wf, wb)
+        for key in ("F", "F_jarzynski_fwd", "F_jarzynski_bwd", "Ediss"):
+            assert abs(r[key] - fo[key]) < 1e-5, (ts, key)
     for r in rows:
         tol = 3 * abs(r["Ediss"]) + 6 * r["stderr"] + 1e-4
         assert abs(r["F_jarzynski_fwd"] - r["F"]) < tol
@@ -212,9 +226,10 @@ def test_free_energy_estimators_and_convergence_workflow(ctx):
 
 def test_size_scaling_workflow_against_the_oracle():
     """The finite-size study of Sec. IV.A from 250 to 11,664 atoms (bcc 5^3
-    .. 18^3, the paper's size) in one batch, four seeds each at 1000 K:
-    cells the crystal runner holds run there, the larger ones (14^3, 18^3)
-    on the multi-kernel path alongside it.  The two smallest sizes equal the
+    .. 18^3, the paper's size) in one batch, four seeds each at 1000 K: a
+    batch with cells above 4096 atoms (14^3, 18^3) runs on the brick runner
+    (the multi-kernel path takes them only if the batch's CTAs do not fit
+    the device at once).  The two smallest sizes equal the
     oracle's stored runs (tests/golden/size_scaling_works.json, same seeds
     and Philox replica indices): every work within 1e-6 eV per atom and F
     within 1 meV/atom; the larger cells give finite F and the 1/N fit."""
