@@ -319,15 +319,17 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
     fx = lane_sum(fx, TPA);
     fy = lane_sum(fy, TPA);
     fz = lane_sum(fz, TPA);
-    double epd = lane_sum((double)ep, TPA);
-    const double vird = VIR ? lane_sum((double)vir, TPA) : 0.0;
-    double vdiag[3] = {0, 0, 0};
-    if constexpr (VIR) {
-        vdiag[0] = lane_sum((double)vxx, TPA);
-        vdiag[1] = lane_sum((double)vyy, TPA);
-        vdiag[2] = lane_sum((double)vzz, TPA);
-    }
+    // the tile's totals: pair energy and virials from every lane's partial,
+    // forces and noise from the atom's lane 0
+    constexpr int NQ = VIR ? 11 : 7;
     double v[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    v[0] = (double)ep;
+    if constexpr (VIR) {
+        v[7] = (double)vir;
+        v[8] = (double)vxx;
+        v[9] = (double)vyy;
+        v[10] = (double)vzz;
+    }
     if (valid && lane == 0) {
         if constexpr (MIXED) {
             B.f32[i] = make_float4((float)fx, (float)fy, (float)fz, 0.f);
@@ -336,11 +338,6 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
             B.f64[3 * i + 1] = (double)fy;
             B.f64[3 * i + 2] = (double)fz;
         }
-        v[0] = epd;
-        v[7] = vird;
-        v[8] = vdiag[0];
-        v[9] = vdiag[1];
-        v[10] = vdiag[2];
         v[1] = (double)fx;
         v[2] = (double)fy;
         v[3] = (double)fz;
@@ -376,27 +373,45 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
             }
         }
     }
-    constexpr int NQ = VIR ? 11 : 7;
-    for (int q = 0; q < NQ; ++q) red[q][threadIdx.x] = v[q];
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            for (int q = 0; q < NQ; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+    double tq[11];  // the totals, in thread 0
+    if constexpr (MIXED) {
+        // FP32 values summed as double-float (GB300's FP64 pipe kept out): a
+        // fixed tree in each warp, then warp 0 over the warps in order
+        float2* wsum = (float2*)&red[0][0];  // [NQ][warps]
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int q = 0; q < NQ; ++q) {
+            const dff t = dff_warp_sum({(float)v[q], 0.f});
+            if (l == 0) wsum[q * nw + w] = make_float2(t.hi, t.lo);
+        }
         __syncthreads();
+        if (w == 0)
+            for (int q = 0; q < NQ; ++q) {
+                const dff t = dff_warp_sum(l < nw ? dff{wsum[q * nw + l].x, wsum[q * nw + l].y} : dff{0.f, 0.f});
+                tq[q] = (double)t.hi + (double)t.lo;
+            }
+    } else {
+        for (int q = 0; q < NQ; ++q) red[q][threadIdx.x] = v[q];
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w)
+                for (int q = 0; q < NQ; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+            __syncthreads();
+        }
+        for (int q = 0; q < NQ; ++q) tq[q] = red[q][0];
     }
     if (threadIdx.x == 0) {
         double* pa = B.partA + (size_t)tile * NPA;
-        pa[PA_UPAIR] = red[0][0];
-        pa[PA_F0X] = red[1][0];
-        pa[PA_F0Y] = red[2][0];
-        pa[PA_F0Z] = red[3][0];
-        pa[PA_XIX] = red[4][0];
-        pa[PA_XIY] = red[5][0];
-        pa[PA_XIZ] = red[6][0];
-        pa[PA_VIR] = VIR ? red[VIR ? 7 : 0][0] : 0.0;
-        pa[PA_VXX] = VIR ? red[VIR ? 8 : 0][0] : 0.0;
-        pa[PA_VYY] = VIR ? red[VIR ? 9 : 0][0] : 0.0;
-        pa[PA_VZZ] = VIR ? red[VIR ? 10 : 0][0] : 0.0;
+        pa[PA_UPAIR] = tq[0];
+        pa[PA_F0X] = tq[1];
+        pa[PA_F0Y] = tq[2];
+        pa[PA_F0Z] = tq[3];
+        pa[PA_XIX] = tq[4];
+        pa[PA_XIY] = tq[5];
+        pa[PA_XIZ] = tq[6];
+        pa[PA_VIR] = VIR ? tq[VIR ? 7 : 0] : 0.0;
+        pa[PA_VXX] = VIR ? tq[VIR ? 8 : 0] : 0.0;
+        pa[PA_VYY] = VIR ? tq[VIR ? 9 : 0] : 0.0;
+        pa[PA_VZZ] = VIR ? tq[VIR ? 10 : 0] : 0.0;
         __threadfence();
         unsigned prev = atomicAdd(&B.tile_done[rep], 1u);
         s_last = (prev == (unsigned)P.ntile - 1u);
