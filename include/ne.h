@@ -226,7 +226,8 @@ ne_status ne_create_crystal_ca(ne_lattice lattice, double a, double c_over_a, in
 /* EAM energy U (Sec. II.B, eq. H) and forces at one configuration:
  * U = sum_{i<j} phi(r_ij) + sum_i F(rho_i), rho_i = sum_j f(r_ij).
  * x_dev [n][3]; f_dev [n][3] (may be NULL); e_dev: 1 double; rho_dev [n]
- * (may be NULL).  NE_MIXED evaluates pairs in FP32 with FP64 sums. */
+ * (may be NULL).  NE_MIXED evaluates pairs in FP32 with double-float sums
+ * (FP64-class precision from FP32 operations). */
 ne_status ne_eam_energy_forces(ne_ctx* ctx, ne_precision prec, const double* x_dev,
                                int n, const double box[3], double* f_dev,
                                double* e_dev, double* rho_dev, void* stream);
@@ -281,8 +282,9 @@ ne_status ne_spring_forces(const double* x_dev, const double* x0_dev, int n, dou
 /* Backward pass of the EAM energy for automatic differentiation: given the
  * upstream gradient gE = dL/dU, writes gx_dev [n][3] = gE dU/dx = -gE F and
  * gtheta_dev [3][n_knots][2] = gE dU/dtheta for every knot value and slope of
- * phi, f and F.  rho is recomputed, not stored.  FP32 pair arithmetic with
- * FP64 bins when prec = NE_MIXED, FP64 throughout when NE_FP64. */
+ * phi, f and F.  rho is recomputed, not stored.  NE_MIXED: FP32 pair
+ * arithmetic, FP32 per-block bins summed over the blocks in FP64, and the F
+ * bins in exact 64-bit fixed point; NE_FP64: FP64 throughout. */
 ne_status ne_eam_backward(ne_ctx* ctx, ne_precision prec, const double* x_dev, int n,
                           const double box[3], double gE, double* gx_dev,
                           double* gtheta_dev, void* stream);

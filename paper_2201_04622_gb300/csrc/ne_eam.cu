@@ -83,30 +83,6 @@ __device__ __forceinline__ R lane_sum(R v, int tpa)
     return v;
 }
 
-// double-float (hi + lo, |lo| <= ulp(hi) / 2) sum of two such numbers from
-// FP32 operations (TwoSum of the high parts, the low parts added to its error)
-struct dff {
-    float hi, lo;
-};
-
-__device__ __forceinline__ dff dff_add(dff a, dff b)
-{
-    const float s = a.hi + b.hi, bp = s - a.hi;
-    float e = (a.hi - (s - bp)) + (b.hi - bp);
-    e += a.lo + b.lo;
-    const float h = s + e;
-    return {h, e - (h - s)};
-}
-
-// sum over the warp of a double-float (fixed xor tree: every lane gets it)
-__device__ __forceinline__ dff dff_warp_sum(dff v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        v = dff_add(v, {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
-    return v;
-}
-
 // ------------------------------------------------------------ pass 1
 // Mixed precision keeps GB300's FP64 pipe (1/64 of FP32) out of the pair
 // loop and the sums: rho as an unnormalised double-float (the FP32 running

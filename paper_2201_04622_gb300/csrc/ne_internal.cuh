@@ -243,6 +243,30 @@ __device__ __forceinline__ int ne_nbr_index(int k, int i, int n_tot, int tpa)
     return ((k / tpa) * n_tot + i) * tpa + (k % tpa);
 }
 
+// double-float (hi + lo, |lo| <= ulp(hi) / 2) sum of two such numbers from
+// FP32 operations (TwoSum of the high parts, the low parts added to its error)
+struct dff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dff dff_add(dff a, dff b)
+{
+    const float s = a.hi + b.hi, bp = s - a.hi;
+    float e = (a.hi - (s - bp)) + (b.hi - bp);
+    e += a.lo + b.lo;
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+
+// sum over the warp of a double-float (fixed xor tree: every lane gets it)
+__device__ __forceinline__ dff dff_warp_sum(dff v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = dff_add(v, {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+    return v;
+}
+
 // Sum of quantity q over tiles [t0, t0 + nt) of a tile-partials array (nq
 // values a tile), by one warp: lane l adds tiles t0 + l, t0 + l + 32, ...
 // in order, then a fixed xor-shuffle tree; every lane returns the total, and

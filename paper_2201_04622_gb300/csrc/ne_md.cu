@@ -236,6 +236,48 @@ __device__ inline void npt_scale(const RepDev& P, const double* T, double lam, l
     mu[0] = mu[1] = mu[2] = exp(deps / 3.0);
 }
 
+// The work increment (lambda_{s+1} - lambda_s) dH/dlambda(x_s) of replica
+// rep into W (and its cumulative record and trace row), by one thread.
+__device__ void step_work(const DevBatch& B, const Sched& S, const double* T, int rep, long long s, double lam_s,
+                          double lam_n)
+{
+    const double U0 = T[TOT_UEMB] + T[TOT_UPAIR];
+    const double g = S.path == 0 ? U0 - T[TOT_UE] : U0;
+    const double dW = (lam_n - lam_s) * g;
+    int slot = -1;
+    long long k = 0;
+    if (S.kind == SCHED_FIXED) {
+        slot = 0;
+    } else if (s >= S.t_eq && s < S.t_eq + S.t_s) {
+        slot = 0;
+        k = s - S.t_eq;
+    } else if (s >= 2 * S.t_eq + S.t_s && s < 2 * S.t_eq + 2 * S.t_s) {
+        slot = 1;
+        k = s - (2 * S.t_eq + S.t_s);
+    }
+    if (slot >= 0) {
+        double* W = B.W + (S.kind == SCHED_FIXED ? rep : 2 * rep + slot);
+        *W += dW;
+        if (B.Wcum && S.kind == SCHED_SWITCH) {
+            double* wc = B.Wcum + ((size_t)(2 * rep + slot)) * (S.t_s + 1);
+            if (k == 0) wc[0] = 0.0;
+            wc[k + 1] = *W;
+        }
+    }
+    if (B.trace && s % B.trace_stride == 0 && s / B.trace_stride < B.trace_rows) {
+        double* row = B.trace + 8 * (s / B.trace_stride);
+        row[0] = (double)s;
+        row[1] = lam_s;
+        row[2] = g;
+        row[3] = U0;
+        row[4] = T[TOT_UE];
+        row[6] = B.W[2 * rep];
+        row[7] = B.W[2 * rep + 1];
+        if (slot == 0) row[6] -= dW;
+        if (slot == 1) row[7] -= dW;
+    }
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(NE_TILE)
     k_step(DevBatch B, Sched S, const long long* __restrict__ step_base, int j, int do_close, int do_open)
@@ -337,43 +379,7 @@ __global__ void __launch_bounds__(NE_TILE)
         if (d0 * d0 + d1 * d1 + d2 * d2 > P.half_skin2) B.flags[rep] = 1;
     }
     if (bad) ne_set_status(B.status, bad);
-    if (do_open && valid && a == 0) {
-        const double U0 = T[TOT_UEMB] + T[TOT_UPAIR];
-        const double g = S.path == 0 ? U0 - T[TOT_UE] : U0;
-        const double dW = (lam_n - lam_s) * g;
-        int slot = -1;
-        long long k = 0;
-        if (S.kind == SCHED_FIXED) {
-            slot = 0;
-        } else if (s >= S.t_eq && s < S.t_eq + S.t_s) {
-            slot = 0;
-            k = s - S.t_eq;
-        } else if (s >= 2 * S.t_eq + S.t_s && s < 2 * S.t_eq + 2 * S.t_s) {
-            slot = 1;
-            k = s - (2 * S.t_eq + S.t_s);
-        }
-        if (slot >= 0) {
-            double* W = B.W + (S.kind == SCHED_FIXED ? rep : 2 * rep + slot);
-            *W += dW;
-            if (B.Wcum && S.kind == SCHED_SWITCH) {
-                double* wc = B.Wcum + ((size_t)(2 * rep + slot)) * (S.t_s + 1);
-                if (k == 0) wc[0] = 0.0;
-                wc[k + 1] = *W;
-            }
-        }
-        if (B.trace && s % B.trace_stride == 0 && s / B.trace_stride < B.trace_rows) {
-            double* row = B.trace + 8 * (s / B.trace_stride);
-            row[0] = (double)s;
-            row[1] = lam_s;
-            row[2] = g;
-            row[3] = U0;
-            row[4] = T[TOT_UE];
-            row[6] = B.W[2 * rep];
-            row[7] = B.W[2 * rep + 1];
-            if (slot == 0) row[6] -= dW;
-            if (slot == 1) row[7] -= dW;
-        }
-    }
+    if (do_open && valid && a == 0) step_work(B, S, T, rep, s, lam_s, lam_n);
     for (int q = 0; q < NPB; ++q) red[q][threadIdx.x] = part[q];
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -384,6 +390,128 @@ __global__ void __launch_bounds__(NE_TILE)
     if (threadIdx.x == 0) {
         double* pb = B.partB + (size_t)tile * NPB;
         for (int q = 0; q < NPB; ++q) pb[q] = red[q][0];
+    }
+}
+
+// The mixed-precision step: the same steps as k_step, with the velocity
+// arithmetic (kicks, thermostat) in FP32, each drift added to the FP64
+// position once, and the tile sums in double-float -- the crystal runner's
+// precision, keeping GB300's FP64 pipe (1/64 of FP32) to ~12 operations an
+// atom.  Thread 0 forms the block's replica scalars (lambda at s and s + 1,
+// the centre-of-mass means, the barostat's factors) in FP64 once.
+__global__ void __launch_bounds__(NE_TILE)
+    k_step_mixed(DevBatch B, Sched S, const long long* __restrict__ step_base, int j, int do_close, int do_open)
+{
+    __shared__ double s_lam[2], s_mu[3];
+    __shared__ float s_mean[9];  // mean F0, spring and noise terms (see below)
+    __shared__ float2 s_w[NPB][NE_TILE / 32];
+    const int tile = blockIdx.x;
+    const int rep = B.tile_rep[tile];
+    const RepDev& P = B.rep[rep];
+    const int a = (tile - P.tile0) * NE_TILE + threadIdx.x;
+    const bool valid = a < P.n;
+    const int i = P.off + (valid ? a : 0);
+    const long long s = *step_base + j;
+    const double* T = B.tot + (size_t)rep * NTOT;
+    if (threadIdx.x == 0) {
+        s_lam[0] = ne_sched_lambda(S, s);
+        s_lam[1] = ne_sched_lambda(S, s + 1);
+        double mu[3] = {1.0, 1.0, 1.0};
+        if (do_open && P.npt) npt_scale(P, T, s_lam[1], s, S.dt, mu);
+        for (int c = 0; c < 3; ++c) s_mu[c] = mu[c];
+        // with the centre of mass fixed: mean F0, the spring's mean and the
+        // noise mean, per unit mass with species tables (mass-weighted)
+        const double den = P.nsp ? P.M : (double)P.n;
+        for (int c = 0; c < 3; ++c) {
+            s_mean[c] = S.fix_cm ? (float)(T[TOT_F0X + c] / den) : 0.f;
+            s_mean[3 + c] = S.fix_cm ? (float)(-(P.nsp ? 1.0 : P.k) * T[TOT_UX + c] / den) : 0.f;
+            s_mean[6 + c] = S.fix_cm ? (float)(T[TOT_XIX + c] / den) : 0.f;
+        }
+    }
+    __syncthreads();
+    const double lam_s = s_lam[0], lam_n = s_lam[1];
+    const float ls = (float)lam_s, ln = (float)lam_n;
+    float part[NPB] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int bad = 0;
+    if (valid) {
+        double x[3], Lb[3];
+        float v[3], u[3], F0[3], mF0[3], mFE[3];
+        const float4 f = B.f32[i];
+        F0[0] = f.x;
+        F0[1] = f.y;
+        F0[2] = f.z;
+        for (int c = 0; c < 3; ++c) {
+            x[c] = B.x[3 * i + c];
+            v[c] = (float)B.v[3 * i + c];
+            u[c] = (float)(x[c] - B.x0[3 * i + c]);
+            Lb[c] = P.L[c];
+        }
+        const int q = P.nsp ? (int)P.sp[a] : 0;
+        const float mi = (float)(P.nsp ? P.ms[q] : P.m), ki = (float)(P.nsp ? P.ks[q] : P.k);
+        const float c2i = (float)(P.nsp ? P.c2s[q] : P.c2), hdti = (float)(P.nsp ? P.hdts[q] : P.hdt_m);
+        const float wm = P.nsp ? mi : 1.f;  // F_i -= m_i sum_j F_j / M with species tables
+        for (int c = 0; c < 3; ++c) {
+            mF0[c] = wm * s_mean[c];
+            mFE[c] = wm * s_mean[3 + c];
+        }
+        auto blendf = [&](float lam, float a0, float ae) { return S.path == 0 ? (1.f - lam) * a0 + lam * ae : lam * a0; };
+        if (do_close)
+            for (int c = 0; c < 3; ++c) v[c] += hdti * blendf(ls, F0[c] - mF0[c], -ki * u[c] - mFE[c]);
+        part[PB_KE] = 0.5f * mi * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (do_open) {
+            for (int c = 0; c < 3; ++c) {
+                const float xi = B.xi32[3 * i + c];
+                const float dv = P.nsp ? c2i * xi - s_mean[6 + c] : c2i * (xi - s_mean[6 + c]);
+                v[c] += hdti * blendf(ln, F0[c] - mF0[c], -ki * u[c] - mFE[c]);
+                const float v1 = v[c];
+                v[c] = (float)P.c1 * v[c] + dv;
+                x[c] += (double)(0.5f * (float)S.dt * (v1 + v[c]));
+            }
+            if (P.npt)
+                for (int c = 0; c < 3; ++c) {
+                    x[c] *= s_mu[c];
+                    Lb[c] = s_mu[c] * P.L[c];
+                }
+            for (int c = 0; c < 3; ++c) u[c] = (float)(x[c] - B.x0[3 * i + c]);
+        }
+        for (int c = 0; c < 3; ++c) {
+            if (!isfinite(x[c]) || !isfinite(v[c])) bad |= ST_ENAN;
+            B.x[3 * i + c] = x[c];
+            B.v[3 * i + c] = (double)v[c];
+            part[PB_UX + c] = P.nsp ? ki * u[c] : u[c];
+        }
+        part[PB_U2] = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        part[PB_UE] = 0.5f * ki * part[PB_U2];
+        // FP32 wrapped copy (the image index in FP32, the shift in FP64) and
+        // displacement since the list build
+        float w[3];
+        for (int c = 0; c < 3; ++c) {
+            const float iL = (float)(P.npt ? P.invL[c] / s_mu[c] : P.invL[c]);
+            w[c] = (float)(x[c] - Lb[c] * (double)floorf((float)x[c] * iL));
+        }
+        B.pos32[i] = make_float4(w[0], w[1], w[2], 0.f);
+        float4 pb = B.pbuild[i];
+        float d0 = w[0] - pb.x, d1 = w[1] - pb.y, d2 = w[2] - pb.z;
+        const float L0 = (float)Lb[0], L1 = (float)Lb[1], L2 = (float)Lb[2];
+        d0 -= L0 * rintf(d0 / L0);
+        d1 -= L1 * rintf(d1 / L1);
+        d2 -= L2 * rintf(d2 / L2);
+        if (d0 * d0 + d1 * d1 + d2 * d2 > P.half_skin2) B.flags[rep] = 1;
+    }
+    if (bad) ne_set_status(B.status, bad);
+    if (do_open && valid && a == 0) step_work(B, S, T, rep, s, lam_s, lam_n);
+    // the tile's partials in double-float: a fixed tree in each warp, then
+    // the two warps in order
+    const int wp = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int q = 0; q < NPB; ++q) {
+        const dff t = dff_warp_sum({part[q], 0.f});
+        if (l == 0) s_w[q][wp] = make_float2(t.hi, t.lo);
+    }
+    __syncthreads();
+    if (threadIdx.x < NPB) {
+        dff t = {0.f, 0.f};
+        for (int w2 = 0; w2 < NE_TILE / 32; ++w2) t = dff_add(t, {s_w[threadIdx.x][w2].x, s_w[threadIdx.x][w2].y});
+        B.partB[(size_t)tile * NPB + threadIdx.x] = (double)t.hi + (double)t.lo;
     }
 }
 
@@ -671,7 +799,7 @@ void launch_step(const DevBatch& B, const Sched& S, bool mixed, const long long*
                  int do_close, int do_open, cudaStream_t st)
 {
     if (mixed)
-        k_step<true><<<B.n_tiles, NE_TILE, 0, st>>>(B, S, step_base, j, do_close, do_open);
+        k_step_mixed<<<B.n_tiles, NE_TILE, 0, st>>>(B, S, step_base, j, do_close, do_open);
     else
         k_step<false><<<B.n_tiles, NE_TILE, 0, st>>>(B, S, step_base, j, do_close, do_open);
     if (B.trace) k_trace_T<<<1, 32, 0, st>>>(B, step_base, j);
@@ -681,7 +809,7 @@ void launch_prep(const DevBatch& B, const Sched& S, bool mixed, const long long*
                  cudaStream_t st)
 {
     if (mixed)
-        k_step<true><<<B.n_tiles, NE_TILE, 0, st>>>(B, S, step_base, 0, 0, 0);
+        k_step_mixed<<<B.n_tiles, NE_TILE, 0, st>>>(B, S, step_base, 0, 0, 0);
     else
         k_step<false><<<B.n_tiles, NE_TILE, 0, st>>>(B, S, step_base, 0, 0, 0);
 }

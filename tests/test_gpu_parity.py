@@ -5,7 +5,8 @@ Tolerances
   FP64 path: energies and forces 1e-10 relative (norm-wise for forces, with
   a 1e-12 eV/A floor per component); trajectories with the same Philox
   stream 1e-8 A over the first 100 steps.
-  Mixed path (FP32 pair arithmetic, FP64 sums and integration): pair
+  Mixed path (FP32 pair arithmetic and velocities, double-float sums,
+  FP64 positions and works): pair
   distances come from FP32 positions wrapped into the box, whose rounding
   is ulp(L) ~ L 2^-24 (1e-6 A for L ~ 15 A); through phi' ~ 1-10 eV/A that
   is ~1e-5 relative in a force and, summed with random signs over ~7000
