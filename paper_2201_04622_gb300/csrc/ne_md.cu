@@ -396,14 +396,17 @@ __global__ void __launch_bounds__(NE_TILE)
 // The mixed-precision step: the same steps as k_step, with the velocity
 // arithmetic (kicks, thermostat) in FP32, each drift added to the FP64
 // position once, and the tile sums in double-float -- the crystal runner's
-// precision, keeping GB300's FP64 pipe (1/64 of FP32) to ~12 operations an
-// atom.  Thread 0 forms the block's replica scalars (lambda at s and s + 1,
-// the centre-of-mass means, the barostat's factors) in FP64 once.
+// precision, keeping GB300's FP64 pipe (1/64 of FP32) to a few conversions
+// an atom.  Thread 0 forms the block's replica scalars (lambda at s and s + 1,
+// the centre-of-mass means, the barostat's factors, the box after it) in FP64
+// once and the second warp the FP32 mass, spring and thermostat tables.
 __global__ void __launch_bounds__(NE_TILE)
     k_step_mixed(DevBatch B, Sched S, const long long* __restrict__ step_base, int j, int do_close, int do_open)
 {
     __shared__ double s_lam[2], s_mu[3];
     __shared__ float s_mean[9];  // mean F0, spring and noise terms (see below)
+    __shared__ float s_box[8];   // box and 1 / box after this step's scaling, c1, (skin / 2)^2
+    __shared__ float s_tab[4][NE_MAX_SPECIES_DEV + 1];  // m, k, c2, dt / 2m: species 0.., the replica's last
     __shared__ float2 s_w[NPB][NE_TILE / 32];
     const int tile = blockIdx.x;
     const int rep = B.tile_rep[tile];
@@ -426,6 +429,23 @@ __global__ void __launch_bounds__(NE_TILE)
             s_mean[c] = S.fix_cm ? (float)(T[TOT_F0X + c] / den) : 0.f;
             s_mean[3 + c] = S.fix_cm ? (float)(-(P.nsp ? 1.0 : P.k) * T[TOT_UX + c] / den) : 0.f;
             s_mean[6 + c] = S.fix_cm ? (float)(T[TOT_XIX + c] / den) : 0.f;
+            s_box[c] = (float)(mu[c] * P.L[c]);
+            s_box[3 + c] = (float)(P.invL[c] / mu[c]);
+        }
+        s_box[6] = (float)P.c1;
+        s_box[7] = (float)P.half_skin2;
+    } else if (threadIdx.x >= 32 && threadIdx.x < 33 + NE_MAX_SPECIES_DEV) {
+        const int t = threadIdx.x - 32;
+        if (t == NE_MAX_SPECIES_DEV) {
+            s_tab[0][t] = (float)P.m;
+            s_tab[1][t] = (float)P.k;
+            s_tab[2][t] = (float)P.c2;
+            s_tab[3][t] = (float)P.hdt_m;
+        } else if (t < P.nsp) {
+            s_tab[0][t] = (float)P.ms[t];
+            s_tab[1][t] = (float)P.ks[t];
+            s_tab[2][t] = (float)P.c2s[t];
+            s_tab[3][t] = (float)P.hdts[t];
         }
     }
     __syncthreads();
@@ -434,7 +454,7 @@ __global__ void __launch_bounds__(NE_TILE)
     float part[NPB] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int bad = 0;
     if (valid) {
-        double x[3], Lb[3];
+        double x[3];
         float v[3], u[3], F0[3], mF0[3], mFE[3];
         const float4 f = B.f32[i];
         F0[0] = f.x;
@@ -444,11 +464,9 @@ __global__ void __launch_bounds__(NE_TILE)
             x[c] = B.x[3 * i + c];
             v[c] = (float)B.v[3 * i + c];
             u[c] = (float)(x[c] - B.x0[3 * i + c]);
-            Lb[c] = P.L[c];
         }
-        const int q = P.nsp ? (int)P.sp[a] : 0;
-        const float mi = (float)(P.nsp ? P.ms[q] : P.m), ki = (float)(P.nsp ? P.ks[q] : P.k);
-        const float c2i = (float)(P.nsp ? P.c2s[q] : P.c2), hdti = (float)(P.nsp ? P.hdts[q] : P.hdt_m);
+        const int q = P.nsp ? (int)P.sp[a] : NE_MAX_SPECIES_DEV;
+        const float mi = s_tab[0][q], ki = s_tab[1][q], c2i = s_tab[2][q], hdti = s_tab[3][q];
         const float wm = P.nsp ? mi : 1.f;  // F_i -= m_i sum_j F_j / M with species tables
         for (int c = 0; c < 3; ++c) {
             mF0[c] = wm * s_mean[c];
@@ -464,39 +482,40 @@ __global__ void __launch_bounds__(NE_TILE)
                 const float dv = P.nsp ? c2i * xi - s_mean[6 + c] : c2i * (xi - s_mean[6 + c]);
                 v[c] += hdti * blendf(ln, F0[c] - mF0[c], -ki * u[c] - mFE[c]);
                 const float v1 = v[c];
-                v[c] = (float)P.c1 * v[c] + dv;
-                x[c] += (double)(0.5f * (float)S.dt * (v1 + v[c]));
+                v[c] = s_box[6] * v[c] + dv;
+                const float dx = 0.5f * (float)S.dt * (v1 + v[c]);
+                if (!isfinite(dx)) bad |= ST_ENAN;
+                x[c] += (double)dx;
             }
             if (P.npt)
-                for (int c = 0; c < 3; ++c) {
-                    x[c] *= s_mu[c];
-                    Lb[c] = s_mu[c] * P.L[c];
-                }
+                for (int c = 0; c < 3; ++c) x[c] *= s_mu[c];
+            // from x itself, so that a run resumed from (x, v) forms the same totals
             for (int c = 0; c < 3; ++c) u[c] = (float)(x[c] - B.x0[3 * i + c]);
         }
         for (int c = 0; c < 3; ++c) {
-            if (!isfinite(x[c]) || !isfinite(v[c])) bad |= ST_ENAN;
+            if (!isfinite(v[c])) bad |= ST_ENAN;
             B.x[3 * i + c] = x[c];
             B.v[3 * i + c] = (double)v[c];
             part[PB_UX + c] = P.nsp ? ki * u[c] : u[c];
         }
         part[PB_U2] = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         part[PB_UE] = 0.5f * ki * part[PB_U2];
-        // FP32 wrapped copy (the image index in FP32, the shift in FP64) and
-        // displacement since the list build
+        // FP32 wrapped copy and displacement since the list build: the image
+        // index in FP32, the shift (only for an atom outside the box) in FP64
         float w[3];
         for (int c = 0; c < 3; ++c) {
-            const float iL = (float)(P.npt ? P.invL[c] / s_mu[c] : P.invL[c]);
-            w[c] = (float)(x[c] - Lb[c] * (double)floorf((float)x[c] * iL));
+            w[c] = (float)x[c];
+            const float n = floorf(w[c] * s_box[3 + c]);
+            if (n != 0.f) w[c] = (float)(x[c] - s_mu[c] * P.L[c] * (double)n);
         }
         B.pos32[i] = make_float4(w[0], w[1], w[2], 0.f);
-        float4 pb = B.pbuild[i];
-        float d0 = w[0] - pb.x, d1 = w[1] - pb.y, d2 = w[2] - pb.z;
-        const float L0 = (float)Lb[0], L1 = (float)Lb[1], L2 = (float)Lb[2];
-        d0 -= L0 * rintf(d0 / L0);
-        d1 -= L1 * rintf(d1 / L1);
-        d2 -= L2 * rintf(d2 / L2);
-        if (d0 * d0 + d1 * d1 + d2 * d2 > P.half_skin2) B.flags[rep] = 1;
+        const float4 pb = B.pbuild[i];
+        float d[3] = {w[0] - pb.x, w[1] - pb.y, w[2] - pb.z}, d2 = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            d[c] = fmaf(-s_box[c], rintf(d[c] * s_box[3 + c]), d[c]);
+            d2 = fmaf(d[c], d[c], d2);
+        }
+        if (d2 > s_box[7]) B.flags[rep] = 1;
     }
     if (bad) ne_set_status(B.status, bad);
     if (do_open && valid && a == 0) step_work(B, S, T, rep, s, lam_s, lam_n);
