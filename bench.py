@@ -20,6 +20,7 @@ ranks and the value the whole job's atom-steps over that time.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -154,6 +155,18 @@ class Clocks:
         ln = clock_query()
         if ln:
             self.edges.append(ln)
+
+    def settle(self, timeout=5.0, quiet_s=0.05):
+        """The reading before the timed region, taken once the periodic
+        sampler is past its start-up (its first line is in): an nvidia-smi
+        that is starting up or has just exited holds driver calls of this
+        process back by tens of microseconds, so the region starts quiet_s
+        after both."""
+        t0 = time.time()
+        while self.proc and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.01)
+        self.edge()
+        time.sleep(quiet_s)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -320,29 +333,32 @@ def run_ours(args):
         best, table = autotune.tune(ctx, mds, offs, x, v, x0, boxes, Wd, 0, 60,
                                     skins=[1.0, 1.8, 2.6])
         tuned = {"best": {k: best[k] for k in ("tpa", "skin", "ms_per_step")}, "candidates": len(table)}
-    # warm-up steps (the start of the schedule)
-    segment(x, v, x0, Wd, 0, Wm)
-    torch.cuda.synchronize()
-    x_w, v_w, W_w = x.clone(), v.clone(), Wd.clone()  # state after warm-up, for the e2e replay
-    moved_w = list(adv.moved) if adv else []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    c0 = ne.ne_ctx_counters(ctx)
-    if adv:
-        adv.moved = list(moved_w)
-    n_log0 = len(adv.log) if adv else 0
+    # torch creates an event at its first record (~20 us of host time): for e1
+    # that would fall between the last kernel and the end stamp
+    e0.record(stream)
+    e1.record(stream)
     with Clocks() as clk:
-        # the reading just before comes ahead of the L2 flush: a synchronous
-        # nvidia-smi run right before the call delays its first launch by ~20 us
-        clk.edge()
+        clk.settle()
+        # warm-up steps (the start of the schedule) right before the timed
+        # ones: after the host has idled, a single call carries ~50 us more
+        # host latency than one that follows a call of the same path
+        segment(x, v, x0, Wd, 0, Wm)
+        x_w, v_w, W_w = x.clone(), v.clone(), Wd.clone()  # state after warm-up, for the e2e replay
+        moved_w = list(adv.moved) if adv else []
+        c0 = ne.ne_ctx_counters(ctx)
+        n_log0 = len(adv.log) if adv else 0
         flush_l2(torch, l2)
         if world > 1:
             dist.barrier()
+        gc.disable()  # no collection inside the timed call (as timeit does)
         torch.cuda.synchronize()
         e0.record(stream)
         segment(x, v, x0, Wd, Wm, K)
         e1.record(stream)
         torch.cuda.synchronize()
+        gc.enable()
         clk.edge()
     ms = e0.elapsed_time(e1)
     # device time of the crystal runner's own launches in the timed call
@@ -377,6 +393,7 @@ def run_ours(args):
         x0d = torch.empty_like(x0h, device=dev) if x0h is not None else x0
         Wd2 = torch.empty_like(Wh, device=dev)
         flush_l2(torch, l2)
+        gc.disable()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sd.copy_(sh, non_blocking=True)
@@ -390,6 +407,7 @@ def run_ours(args):
         Wh.copy_(Wd2, non_blocking=True)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
+        gc.enable()
         if world > 1:
             t_e2e = max_over_ranks(t_e2e * 1e3, dist, dev) * 1e-3
         h2d = (sh.numel() + (x0h.numel() if x0h is not None else 0) + Wh.numel()) * 8
@@ -499,6 +517,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        f1.record(stream)
+        torch.cuda.synchronize()
         f0.record(stream)
         ne.ne_switch_run_segment(ctx, m64, offs, x64, v64, x0, boxes, W64, 50, K64)
         f1.record(stream)
