@@ -56,21 +56,28 @@ namespace {
 constexpr int THREADS = 768;  // 24 warps: six per SMSP, 80 registers a thread
 constexpr int TPA = 2;
 constexpr int SLOTS = THREADS / TPA;  // atoms per CTA (one CTA per SM)
-// Tensor memory as per-thread scratch between the pair passes: pass 1
-// leaves f'(r)/r of every stencil visit (0 outside r_c) in TMEM, pass 2
-// reads it back instead of gathering the f table again.  The CTA holds all
-// TM_COLS columns (one CTA per SM); warp w uses TMEM lanes 32 (w mod 4) ..
-// +31 (its sub-partition's) and columns QMAX (w div 4) .. +QMAX-1: visit q
-// of a thread is column q of its lane, stored and loaded FRB at a time.
-// Visits past QMAX (a hot or disordered replica) are recomputed in pass 2.
+// Tensor memory as per-thread scratch: the shared-memory slot j of the
+// neighbour at each of a thread's first QMAX stencil visits (fixed for the
+// whole launch: the stencil is a lattice one, so atom i's k-th entry is
+// always the same atom), written once before the step loop, and f'(r)/r of
+// each of those visits (0 outside r_c), written by pass 1 and read by pass
+// 2 instead of gathering the f table again.  The CTA holds all TM_COLS
+// columns (one CTA per SM); warp w uses TMEM lanes 32 (w mod 4) .. +31 (its
+// sub-partition's) and the CW columns from CW (w div 4): visit q of a thread
+// is column q of its lane for f'(r)/r and half of column QMAX + q / 2 for j
+// (two 16-bit slots a column), loaded FRB visits at a time.  Visits past
+// QMAX (a hot or disordered replica) take j from the wrapped-cell tables
+// and are recomputed in pass 2.
 constexpr int TM_COLS = NE_TM_COLS;
 constexpr int FRB = NE_TM_BATCH;
 // stencil scan bounds: entries of basis b with |r0_j - r0_i| < r_c + c for
 // c = q * 2D / (NKT - 1), q = 0 .. NKT - 1 (the last: the whole stencil)
 constexpr int NKT = 256;
 constexpr int NWARP = THREADS / 32;
-constexpr int QMAX = TM_COLS / (NWARP / 4) / FRB * FRB;
-static_assert(QMAX >= FRB && (NWARP / 4 + (NWARP % 4 ? 1 : 0)) * QMAX <= TM_COLS, "TMEM columns per warp");
+constexpr int WQ = NWARP / 4;  // warps per TMEM lane quarter
+constexpr int QMAX = TM_COLS / WQ * 2 / 3 / FRB * FRB;
+constexpr int CW = QMAX + QMAX / 2;  // TMEM columns per warp
+static_assert(NWARP % 4 == 0 && QMAX >= FRB && QMAX % FRB == 0 && WQ * CW <= TM_COLS, "TMEM columns per warp");
 
 // partial sums broadcast at the end of step s for step s+1: the energies
 // (double-float), then sum u and sum xi for the mean removal (FP32)
@@ -333,7 +340,31 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tm_base = *s_tm;
     const unsigned tm_w = tm_base + ((unsigned)(32 * ((threadIdx.x >> 5) & 3)) << 16) +
-                          (unsigned)(QMAX * (threadIdx.x >> 7));  // this warp's lanes and columns
+                          (unsigned)(CW * (threadIdx.x >> 7));  // this warp's lanes and columns
+    const unsigned tm_j = tm_w + (unsigned)QMAX;                    // its neighbour-slot columns
+    // the neighbour slots of this thread's first QMAX visits (entries past
+    // the stencil, which no visit reaches, get slot 0); every atom of the
+    // replica has a 16-byte entry in shared memory, so slots are < 2^16
+#pragma unroll 1
+    for (int q0 = 0; q0 < QMAX; q0 += FRB) {
+        unsigned jw[FRB / 2];
+#pragma unroll
+        for (int h = 0; h < FRB / 2; ++h) {
+            unsigned w2 = 0u;
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const int k = lane + TPA * (q0 + 2 * h + o);
+                if (k < nst) {
+                    const int code = __float_as_int(s_sv[stb + k].w);
+                    w2 |= (unsigned)(s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)]) << (16 * o);
+                }
+            }
+            jw[h] = w2;
+        }
+        __syncwarp();
+        ne_tm_st_u4(tm_j + (unsigned)(q0 / 2), jw);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     const float Dr = reps[rep].D;
     for (int q = threadIdx.x; q < nb * NKT; q += THREADS) {
         const int b = q / NKT, iq = q % NKT;
@@ -505,85 +536,98 @@ __global__ void __launch_bounds__(THREADS, 1)
             // rho as an unnormalised double-float: the running FP32 sum rh and
             // the exact rounding error of each addition (TwoSum) summed in rl
             float rh = 0.f, rl = 0.f;
+            // one stencil visit (entry e, neighbour slot j, visit index qv):
+            // the pair's terms of rho, the forces and the energy; returns
+            // f'(r)/r inside r_c, else 0
+            auto visit = [&](float4 e, int j, int qv) -> float {
+                const float4 uj = s_u[j];
+                if constexpr (NPT) {
+                    e.x *= muf[0];
+                    e.y *= muf[1];
+                    e.z *= muf[2];
+                }
+                const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                float fr = 0.f;
+                if (r2 < rc2) {
+                    const float irh = rsqrtf(r2) * inv_h;  // 1 / (r h)
+                    const float t = r2 * irh;              // r / h >= 0
+                    const int kk = min((int)t, nk - 2);
+                    const float w = t - (float)kk;
+                    // intervals below kchk (r < ~1 A: the shared-memory window
+                    // starts there, and r_min lies below it) are rare: their
+                    // own branch checks r_min and reads global memory
+                    float4 cf, g;
+                    if (kk < kchk) {
+                        if (r2 < rmin2) bad |= ST_ERANGE;
+                        if (kk >= k_lo) {
+                            cf = s_tabP[kk - k_lo];
+                            g = s_tabF[kk - k_lo];
+                        } else {
+                            cf = __ldg(&tab.pf32[2 * kk]);
+                            g = __ldg(&tab.pf32[2 * kk + 1]);
+                        }
+                    } else {
+                        cf = s_tabP[kk - k_lo];
+                        g = s_tabF[kk - k_lo];
+                    }
+                    {
+                        // f and df/dw together (Horner with derivative)
+                        float fv = fmaf(g.w, w, g.z), fd = g.w;
+                        fd = fmaf(fd, w, fv);
+                        fv = fmaf(fv, w, g.y);
+                        fd = fmaf(fd, w, fv);
+                        fv = fmaf(fv, w, g.x);
+                        const float s_ = rh + fv, bp = s_ - rh;
+                        rl += (rh - (s_ - bp)) + (fv - bp);
+                        rh = s_;
+                        fr = fd * irh;  // f'(r) / r
+                        ql = qv;
+                    }
+                    // phi and dphi/dw together (Horner with derivative)
+                    float pv = fmaf(cf.w, w, cf.z), pd = cf.w;
+                    pd = fmaf(pd, w, pv);
+                    pv = fmaf(pv, w, cf.y);
+                    pd = fmaf(pd, w, pv);
+                    pv = fmaf(pv, w, cf.x);
+                    const float sc = pd * irh;
+                    fx += sc * dx;
+                    fy += sc * dy;
+                    fz += sc * dz;
+                    ep += pv;
+                    if constexpr (NPT) {  // -(1/2) r_a^2 / r dU/dr of the pair's half
+                        vxx -= 0.5f * sc * dx * dx;
+                        vyy -= 0.5f * sc * dy * dy;
+                        vzz -= 0.5f * sc * dz * dz;
+                    }
+                    ++m;
+                }
+                return fr;
+            };
+            // the first QMAX visits: neighbour slots from TMEM, f'(r)/r to TMEM
+            const int nqa = min(nq, QMAX);
 #pragma unroll 1
-            for (int q0 = 0; q0 < nq; q0 += FRB) {
+            for (int q0 = 0; q0 < nqa; q0 += FRB) {
+                unsigned jw[FRB / 2];
+                __syncwarp();
+                ne_tm_ld_u4(tm_j + (unsigned)(q0 / 2), jw);
                 float frv[FRB];
 #pragma unroll
                 for (int uq = 0; uq < FRB; ++uq) {
                     const int k = lane + TPA * (q0 + uq);
-                    float fr = 0.f;
-                    {
-                        float4 e = s_sv[stb + k];
-                        const int code = __float_as_int(e.w);
-                        const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
-                        const float4 uj = s_u[j];
-                        if constexpr (NPT) {
-                            e.x *= muf[0];
-                            e.y *= muf[1];
-                            e.z *= muf[2];
-                        }
-                        const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < rc2) {
-                            const float irh = rsqrtf(r2) * inv_h;  // 1 / (r h)
-                            const float t = r2 * irh;              // r / h >= 0
-                            const int kk = min((int)t, nk - 2);
-                            const float w = t - (float)kk;
-                            // intervals below kchk (r < ~1 A: the shared-memory window
-                            // starts there, and r_min lies below it) are rare: their
-                            // own branch checks r_min and reads global memory
-                            float4 cf, g;
-                            if (kk < kchk) {
-                                if (r2 < rmin2) bad |= ST_ERANGE;
-                                if (kk >= k_lo) {
-                                    cf = s_tabP[kk - k_lo];
-                                    g = s_tabF[kk - k_lo];
-                                } else {
-                                    cf = __ldg(&tab.pf32[2 * kk]);
-                                    g = __ldg(&tab.pf32[2 * kk + 1]);
-                                }
-                            } else {
-                                cf = s_tabP[kk - k_lo];
-                                g = s_tabF[kk - k_lo];
-                            }
-                            {
-                                // f and df/dw together (Horner with derivative)
-                                float fv = fmaf(g.w, w, g.z), fd = g.w;
-                                fd = fmaf(fd, w, fv);
-                                fv = fmaf(fv, w, g.y);
-                                fd = fmaf(fd, w, fv);
-                                fv = fmaf(fv, w, g.x);
-                                const float s_ = rh + fv, bp = s_ - rh;
-                                rl += (rh - (s_ - bp)) + (fv - bp);
-                                rh = s_;
-                                fr = fd * irh;  // f'(r) / r
-                                ql = q0 + uq;
-                            }
-                            // phi and dphi/dw together (Horner with derivative)
-                            float pv = fmaf(cf.w, w, cf.z), pd = cf.w;
-                            pd = fmaf(pd, w, pv);
-                            pv = fmaf(pv, w, cf.y);
-                            pd = fmaf(pd, w, pv);
-                            pv = fmaf(pv, w, cf.x);
-                            const float sc = pd * irh;
-                            fx += sc * dx;
-                            fy += sc * dy;
-                            fz += sc * dz;
-                            ep += pv;
-                            if constexpr (NPT) {  // -(1/2) r_a^2 / r dU/dr of the pair's half
-                                vxx -= 0.5f * sc * dx * dx;
-                                vyy -= 0.5f * sc * dy * dy;
-                                vzz -= 0.5f * sc * dz * dz;
-                            }
-                            ++m;
-                        }
-                    }
-                    frv[uq] = fr;
+                    frv[uq] = visit(s_sv[stb + k], (int)((jw[uq >> 1] >> (16 * (uq & 1))) & 0xffffu), q0 + uq);
                 }
-                if (q0 < QMAX) {
-                    __syncwarp();
-                    ne_tm_st(tm_w + (unsigned)q0, frv);
-                }
+                __syncwarp();
+                ne_tm_st(tm_w + (unsigned)q0, frv);
+            }
+            // visits past QMAX: slots from the wrapped-cell tables, f'(r)/r
+            // recomputed in pass 2
+#pragma unroll 1
+            for (int q = nqa; q < nq; ++q) {
+                const int k = lane + TPA * q;
+                const float4 e = s_sv[stb + k];
+                const int code = __float_as_int(e.w);
+                (void)visit(e, s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)], q);
             }
             __syncwarp();
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");  // the stores land before pass 2 loads
@@ -622,15 +666,15 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll 1
             for (int q0 = 0; q0 < nqt; q0 += FRB) {
                 float frv[FRB];
+                unsigned jw[FRB / 2];
                 __syncwarp();
-                ne_tm_ld(tm_w + (unsigned)q0, frv);
+                ne_tm_ld_f8u4(tm_w + (unsigned)q0, tm_j + (unsigned)(q0 / 2), frv, jw);
 #pragma unroll
                 for (int uq = 0; uq < FRB; ++uq) {
                     if (frv[uq] != 0.f) {  // inside r_c (f' vanishes only at r_c)
                         const int k = lane + TPA * (q0 + uq);
                         float4 e = s_sv[stb + k];
-                        const int code = __float_as_int(e.w);
-                        const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
+                        const int j = (int)((jw[uq >> 1] >> (16 * (uq & 1))) & 0xffffu);
                         const float4 uj = s_u[j];
                         if constexpr (NPT) {
                             e.x *= muf[0];

@@ -91,6 +91,46 @@ __device__ __forceinline__ void ne_tm_ld(unsigned taddr, float (&v)[N])
     for (int q = 0; q < N; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// Four columns of 32-bit words (packed integers) of this thread's lane.
+__device__ __forceinline__ void ne_tm_st_u4(unsigned taddr, const unsigned (&v)[4])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};"
+                 :
+                 : "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+                 : "memory");
+}
+
+__device__ __forceinline__ void ne_tm_ld_u4(unsigned taddr, unsigned (&v)[4])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]) : : "memory");
+}
+
+// Eight float columns at taddr_f and four word columns at taddr_w, both
+// loads in flight before the one wait.
+__device__ __forceinline__ void ne_tm_ld_f8u4(unsigned taddr_f, unsigned taddr_w, float (&f)[8], unsigned (&w)[4])
+{
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr_f)
+                 : "memory");
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+                 : "r"(taddr_w)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int q = 0; q < 8; ++q) f[q] = __uint_as_float(r[q]);
+}
+
 // Warp 0 of the CTA takes all NE_TM_COLS columns (the base address goes to
 // *s_slot in shared memory); the caller then makes it visible with
 // tcgen05.fence::before_thread_sync, a CTA barrier and
