@@ -416,36 +416,49 @@ __global__ void __launch_bounds__(NE_TILE)
     const int i = P.off + (valid ? a : 0);
     const long long s = *step_base + j;
     const double* T = B.tot + (size_t)rep * NTOT;
-    if (threadIdx.x == 0) {
-        s_lam[0] = ne_sched_lambda(S, s);
-        s_lam[1] = ne_sched_lambda(S, s + 1);
+    if (threadIdx.x < 32) {
+        // the replica scalars, one a lane, the lanes running the same
+        // instructions (GB300 issues an FP64 warp instruction at the same cost
+        // for one lane as for 32, so a serial chain on one thread held the
+        // whole block): lambda at s and s + 1 in lanes of each parity; the
+        // barostat's factors (lane 0); one division for the centre-of-mass
+        // means (lanes 0-8: mean F0, the spring's mean and the noise mean,
+        // per unit mass with species tables, mass-weighted) and 1 / box
+        // (lanes 9-11); the box (lanes 12-14), c1 and (skin / 2)^2
+        const int l = threadIdx.x, c = l % 3;
+        const double lam = ne_sched_lambda(S, s + (l & 1));
+        if (l < 2) s_lam[l] = lam;
         double mu[3] = {1.0, 1.0, 1.0};
-        if (do_open && P.npt) npt_scale(P, T, s_lam[1], s, S.dt, mu);
-        for (int c = 0; c < 3; ++c) s_mu[c] = mu[c];
-        // with the centre of mass fixed: mean F0, the spring's mean and the
-        // noise mean, per unit mass with species tables (mass-weighted)
-        const double den = P.nsp ? P.M : (double)P.n;
-        for (int c = 0; c < 3; ++c) {
-            s_mean[c] = S.fix_cm ? (float)(T[TOT_F0X + c] / den) : 0.f;
-            s_mean[3 + c] = S.fix_cm ? (float)(-(P.nsp ? 1.0 : P.k) * T[TOT_UX + c] / den) : 0.f;
-            s_mean[6 + c] = S.fix_cm ? (float)(T[TOT_XIX + c] / den) : 0.f;
-            s_box[c] = (float)(mu[c] * P.L[c]);
-            s_box[3 + c] = (float)(P.invL[c] / mu[c]);
+        if (do_open && P.npt) {
+            const double lam_n1 = __shfl_sync(0xffffffffu, lam, 1);
+            if (l == 0) npt_scale(P, T, lam_n1, s, S.dt, mu);
+            for (int q = 0; q < 3; ++q) mu[q] = __shfl_sync(0xffffffffu, mu[q], 0);
         }
-        s_box[6] = (float)P.c1;
-        s_box[7] = (float)P.half_skin2;
+        const double muc = c == 0 ? mu[0] : (c == 1 ? mu[1] : mu[2]);
+        double num, den = P.nsp ? P.M : (double)P.n;
+        if (l < 3) num = T[TOT_F0X + c];
+        else if (l < 6) num = -(P.nsp ? 1.0 : P.k) * T[TOT_UX + c];
+        else if (l < 9) num = T[TOT_XIX + c];
+        else {
+            num = P.invL[c];
+            den = muc;
+        }
+        const double quo = num / den;
+        if (l < 9) s_mean[l] = S.fix_cm ? (float)quo : 0.f;
+        else if (l < 12) s_box[3 + c] = (float)quo;
+        else if (l < 15) s_box[c] = (float)(muc * P.L[c]);
+        else if (l == 15) s_box[6] = (float)P.c1;
+        else if (l == 16) s_box[7] = (float)P.half_skin2;
+        if (l < 3) s_mu[l] = muc;
     } else if (threadIdx.x >= 32 && threadIdx.x < 33 + NE_MAX_SPECIES_DEV) {
         const int t = threadIdx.x - 32;
-        if (t == NE_MAX_SPECIES_DEV) {
-            s_tab[0][t] = (float)P.m;
-            s_tab[1][t] = (float)P.k;
-            s_tab[2][t] = (float)P.c2;
-            s_tab[3][t] = (float)P.hdt_m;
-        } else if (t < P.nsp) {
-            s_tab[0][t] = (float)P.ms[t];
-            s_tab[1][t] = (float)P.ks[t];
-            s_tab[2][t] = (float)P.c2s[t];
-            s_tab[3][t] = (float)P.hdts[t];
+        const bool r1 = t == NE_MAX_SPECIES_DEV;  // the replica's single-species values
+        const int ts = r1 ? 0 : t;
+        if (r1 || t < P.nsp) {
+            s_tab[0][t] = (float)(r1 ? P.m : P.ms[ts]);
+            s_tab[1][t] = (float)(r1 ? P.k : P.ks[ts]);
+            s_tab[2][t] = (float)(r1 ? P.c2 : P.c2s[ts]);
+            s_tab[3][t] = (float)(r1 ? P.hdt_m : P.hdts[ts]);
         }
     }
     __syncthreads();
