@@ -515,12 +515,14 @@ def test_uneven_campaign_fits_one_spring_per_replica():
 
 @pytest.mark.parametrize("runner", [1, 2], ids=["cluster", "brick"])
 def test_runner_pairs_past_the_tmem_visits(ctx, pot, runner):
-    """The runners keep f'(r)/r of 80 stencil visits a thread in tensor
-    memory and recompute later visits in pass 2.  Two atoms of the (2,2,0)a
-    shell of bcc (stencil entries 168-179: visits 84-89 at 2 threads per
-    atom), each moved 1.55 A towards the other (within the 2 A range), are
-    5.02 A apart: inside r_c, with their embedding force from that
-    recomputation.  10 steps at 10 K against the oracle."""
+    """The cluster runner keeps the neighbour slot and f'(r)/r of 56 stencil
+    visits a thread in tensor memory, the brick runner f'(r)/r of 80; later
+    visits take their neighbour from the wrapped-cell tables and are
+    recomputed in pass 2.  Two atoms of the (2,2,0)a shell of bcc (stencil
+    entries 168-179: visits 84-89 at 2 threads per atom), each moved 1.55 A
+    towards the other (within the 2 A range), are 5.02 A apart: inside r_c,
+    with their embedding force from that recomputation.  10 steps at 10 K
+    against the oracle."""
     p, th = pot
     x0, box = O.create_crystal(O.BCC, W.A_BCC, 6, 6, 6)
     tgt = x0[0] + W.A_BCC * np.array([2.0, 2.0, 0.0])
