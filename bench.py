@@ -419,10 +419,11 @@ def run_ours(args):
 
     roof = None
     clk_sum = clk.summary()
-    runner_kind = None
+    runner_kind, plan = None, None
     if path == "crystal":
-        runner_kind = "brick" if (max(offs[r + 1] - offs[r] for r in range(n_rep)) > ne.CRYSTAL_RUNNER_MAX_ATOMS
-                                  or (tuned and tuned["best"]["runner"] == "brick")) else "cluster"
+        # the launch plan of the timed call (runner, threads per atom, CTAs)
+        plan = ne.ne_ctx_crystal_plan(ctx)
+        runner_kind = plan["runner"]
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     if path == "crystal" and kern_ms:
         # the timed call is one persistent launch per size class; its device
@@ -539,7 +540,9 @@ def run_ours(args):
                               "grad32": 300.0}[args.workload],
                       "t_eq": t_eq_w, "t_s": t_s_w, "dt_fs": 1.0, "skin_A": mds[0].skin,
                       "precision": args.prec, "path": path, "runner": runner_kind,
-                      "threads_per_atom": 2 if path == "crystal" else args.tpa,
+                      "threads_per_atom": plan["threads_per_atom"] if plan else args.tpa,
+                      "ctas": plan["ctas"] if plan else None,
+                      "ctas_per_cluster": (plan["cluster_ctas"] or None) if plan else None,
                       "autotune": tuned,
                       "list_builds_per_replica_step": list_builds / (K * n_rep),
                       "moved_to_multikernel": {"replicas": moved_timed,

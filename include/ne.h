@@ -203,6 +203,15 @@ ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds, long long* stenci
  * paper has no counterpart).  NE_EINVAL if no such call has run. */
 ne_status ne_ctx_last_run_ms(ne_ctx* ctx, double* ms_host);
 
+/* Launch plan of the last ne_crystal_run_segment or
+ * ne_crystal_run_segment_cum call on this context (bookkeeping for reports;
+ * the paper has no counterpart): runner 1 the cluster runner, 2 the brick
+ * runner; threads_per_atom the threads on each atom in the pair passes;
+ * ctas the CTAs of the call's launches; cluster_ctas the CTAs per cluster of
+ * the cluster runner's largest (0 for the brick runner).  Each pointer may
+ * be NULL.  NE_EINVAL if no crystal-runner call has planned a launch. */
+ne_status ne_ctx_crystal_plan(ne_ctx* ctx, int* runner, int* threads_per_atom, int* ctas, int* cluster_ctas);
+
 /* Status bits recorded by the last call, and its message (msg may be NULL). */
 ne_status ne_last_error(ne_ctx* ctx, int* device_status, char* msg, int msg_len);
 

@@ -799,6 +799,28 @@ ne_status ne_ctx_counters(ne_ctx* ctx, long long* list_builds, long long* stenci
     return NE_OK;
 }
 
+ne_status ne_ctx_crystal_plan(ne_ctx* ctx, int* runner, int* threads_per_atom, int* ctas, int* cluster_ctas)
+{
+    if (!ctx) return NE_EINVAL;
+    const CrPlan& P = ctx->plan;
+    if (!P.valid) return fail(ctx, NE_EINVAL, "no crystal-runner launch has been planned on this context");
+    int r = 2, tpa = P.tpa, n = P.n_cta, cc = 0;
+    if (!P.brick) {
+        r = 1;
+        tpa = ne::cluster_threads_per_atom();
+        n = 0;
+        for (const CrGroup& G : P.groups) {
+            n += (G.e - G.b) * G.C;
+            cc = std::max(cc, G.C);
+        }
+    }
+    if (runner) *runner = r;
+    if (threads_per_atom) *threads_per_atom = tpa;
+    if (ctas) *ctas = n;
+    if (cluster_ctas) *cluster_ctas = cc;
+    return NE_OK;
+}
+
 ne_status ne_ctx_last_run_ms(ne_ctx* ctx, double* ms_host)
 {
     if (!ctx || !ms_host) return NE_EINVAL;
@@ -1472,8 +1494,9 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
     P.npt = false;
     for (int r = 0; r < n_rep; ++r) P.npt = P.npt || xr[r].npt != 0;
     if (brick) {
-        // Brick runner: the largest threads-per-atom (8, 4, 2, 1) at which every
-        // replica's blocks of cells, one CTA each, fit the device at once
+        // Brick runner: the largest threads-per-atom (8, 4, 3, 2, 1: each
+        // divides the 768 threads into whole warps of one pair lane) at which
+        // every replica's blocks of cells, one CTA each, fit the device at once
         int gnb = 0, glut = 0;
         for (int r = 0; r < n_rep; ++r) {
             gnb = std::max(gnb, xr[r].nb * xr[r].st_cnt);
@@ -1481,7 +1504,7 @@ static ne_status build_plan(ne_ctx* ctx, const ne_md_params* md, const ne_crysta
             glut = std::max(glut, (xr[r].nx + 2 * Mr) * (xr[r].ny + 2 * Mr) + xr[r].nb * (xr[r].nz + 2 * Mr));
         }
         P.brick = false;
-        for (int tpa : {8, 4, 2, 1}) {
+        for (int tpa : {8, 4, 3, 2, 1}) {
             const size_t base = (ne::brick_smem_bytes(tpa, gnb, glut, P.npt) + 15) & ~(size_t)15;
             if (base > (size_t)smem_max) continue;
             const long long fit = ((long long)smem_max - (long long)base) / (2 * (long long)sizeof(float4));

@@ -31,7 +31,7 @@
 // others leave at their next barrier.  Loads of data other CTAs wrote use
 // ld.global.cg (L2, never a stale L1 line).
 //
-// Threads: TPA threads per atom (8, 4, 2 or 1, the largest at which the
+// Threads: TPA threads per atom (8, 4, 3, 2 or 1, the largest at which the
 // batch's CTAs fit the device at one CTA per SM); thread t works on slot
 // t % SLOTS and takes the stencil entries k = lane + TPA q, lane = t / SLOTS,
 // so the 32 threads of a warp read one stencil entry.  One thread per atom
@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             ne::BrickBufs bb, long long n_tot, double* __restrict__ boxes_out)
 {
     constexpr int SLOTS = BTHREADS / TPA;
+    static_assert(BTHREADS % TPA == 0 && SLOTS % 32 == 0, "whole warps of one pair lane");
     extern __shared__ __align__(16) unsigned char smem[];
     const int rep = cta_rep[blockIdx.x];
     const XRep& R_ = reps[rep];
@@ -906,6 +907,7 @@ int brick_max_ctas(int tpa, size_t smem, bool npt)
     switch (tpa) {
     case 1: e = npt ? brick_occupancy<1, true>(smem, &per) : brick_occupancy<1, false>(smem, &per); break;
     case 2: e = npt ? brick_occupancy<2, true>(smem, &per) : brick_occupancy<2, false>(smem, &per); break;
+    case 3: e = npt ? brick_occupancy<3, true>(smem, &per) : brick_occupancy<3, false>(smem, &per); break;
     case 4: e = npt ? brick_occupancy<4, true>(smem, &per) : brick_occupancy<4, false>(smem, &per); break;
     default: e = npt ? brick_occupancy<8, true>(smem, &per) : brick_occupancy<8, false>(smem, &per); break;
     }
@@ -941,6 +943,7 @@ cudaError_t launch_brick(int tpa, const XRep* reps, const int* cta_rep, int n_ct
     switch (tpa) {
     case 1: return npt ? brick_launch<1, true>(NE_BRICK_ARGS) : brick_launch<1, false>(NE_BRICK_ARGS);
     case 2: return npt ? brick_launch<2, true>(NE_BRICK_ARGS) : brick_launch<2, false>(NE_BRICK_ARGS);
+    case 3: return npt ? brick_launch<3, true>(NE_BRICK_ARGS) : brick_launch<3, false>(NE_BRICK_ARGS);
     case 4: return npt ? brick_launch<4, true>(NE_BRICK_ARGS) : brick_launch<4, false>(NE_BRICK_ARGS);
     case 8: return npt ? brick_launch<8, true>(NE_BRICK_ARGS) : brick_launch<8, false>(NE_BRICK_ARGS);
     default: return cudaErrorInvalidValue;

@@ -1007,6 +1007,8 @@ int cluster_size_for(int n, int nb)
 
 int cluster_atoms_per_cta() { return SLOTS; }
 
+int cluster_threads_per_atom() { return TPA; }
+
 int cluster_atoms_for(int n, int C, int nb) { return atoms_per_cta(n, C, nb); }
 
 int cluster_max_active(int C, size_t smem)

@@ -163,6 +163,7 @@ __device__ __forceinline__ void ne_tm_free(unsigned base)
 namespace ne {
 size_t cluster_smem_bytes(int n_max, int nb_nst_max, int lut_max, bool npt = false);
 int cluster_atoms_per_cta();
+int cluster_threads_per_atom();
 int cluster_size_for(int n, int nb);           // smallest CTAs per cluster for an n-atom replica
 int cluster_atoms_for(int n, int C, int nb);    // atoms per CTA of an n-atom replica on C CTAs
 int cluster_max_active(int C, size_t smem);     // co-resident clusters of C CTAs (0 if none or on error)

@@ -27,7 +27,7 @@ NE_PATH_FL, NE_PATH_RS = 0, 1
 
 # every symbol include/ne.h declares
 SYMBOLS = ["ne_ctx_create", "ne_ctx_destroy", "ne_ctx_clone", "ne_ctx_set_theta", "ne_ctx_get_theta",
-           "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_set_runner", "ne_ctx_boxes", "ne_ctx_replica_status", "ne_ctx_counters", "ne_ctx_last_run_ms",
+           "ne_ctx_set_tuning", "ne_ctx_set_cluster_size", "ne_ctx_set_runner", "ne_ctx_boxes", "ne_ctx_replica_status", "ne_ctx_counters", "ne_ctx_last_run_ms", "ne_ctx_crystal_plan",
            "ne_last_error",
            "ne_create_crystal", "ne_create_crystal_ca", "ne_eam_energy_forces", "ne_eam_virial", "ne_eam_energy_forces_noalloc",
            "ne_spring_forces",
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
                 "ne_ctx_replica_status": [p, i, p],
                 "ne_ctx_counters": [p, p, p, p, p],
                 "ne_ctx_last_run_ms": [p, p],
+                "ne_ctx_crystal_plan": [p, p, p, p, p],
                 "ne_last_error": [p, p, p, i],
                 "ne_create_crystal": [i, d, i, i, i, p, p, p],
                 "ne_create_crystal_ca": [i, d, d, i, i, i, p, p, p],
@@ -331,6 +332,15 @@ def ne_ctx_last_run_ms(ctx):
     ms = C.c_double()
     _err(ctx, load().ne_ctx_last_run_ms(ctx, C.byref(ms)), "ne_ctx_last_run_ms")
     return ms.value
+
+
+def ne_ctx_crystal_plan(ctx):
+    """Launch plan of the last crystal-runner call: dict with runner
+    ("cluster" or "brick"), threads_per_atom, ctas and cluster_ctas."""
+    r, t, n, c = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _err(ctx, load().ne_ctx_crystal_plan(ctx, C.byref(r), C.byref(t), C.byref(n), C.byref(c)), "ne_ctx_crystal_plan")
+    return {"runner": "cluster" if r.value == 1 else "brick", "threads_per_atom": t.value, "ctas": n.value,
+            "cluster_ctas": c.value}
 
 
 def ne_last_error(ctx):

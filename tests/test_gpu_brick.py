@@ -3,7 +3,7 @@ above 4096 atoms): every CTA owns a block of cells of one replica and the
 CTAs exchange displacements and F'(rho) through global memory between grid
 barriers.  Against the oracle (FP64) on small cells at 1400 K and on a
 config-4-sized bcc 16^3 cell, against the cluster runner on the same batch,
-with one threads-per-atom choice per batch size (8, 4 or 2), species tables,
+with one threads-per-atom choice per batch size (8, 4, 3, 2 or 1), species tables,
 the cumulative works of eq. rs, a replica that leaves the stencil range, and
 segment resume.  The reversible-scaling prefix of bcc 16^3 against the stored
 oracle works is in test_zz_workloads_vs_oracle.py."""
@@ -148,6 +148,30 @@ def test_brick_runner_one_thread_per_atom_on_bcc32(ctx, pot):
     Wg = Wd.cpu().numpy()[0]
     assert Wg[0] == pytest.approx(ro["W_f"], rel=1e-6)
     assert Wg[1] == pytest.approx(ro["W_b"], rel=1e-6)
+
+
+def test_brick_runner_three_threads_per_atom_on_four_bcc16(ctx, pot):
+    """Four bcc 16^3 replicas (32,768 atoms, the reversible-scaling bench
+    batch): 4 threads per atom would need 172 CTAs, more than a 152-SM device
+    holds, so the brick runner takes 3 (128 CTAs of 256 atoms), as
+    ne_ctx_crystal_plan reports; the 60-step FL schedule at 1400 K,
+    replica 2 against the oracle atom by atom."""
+    p, th = pot
+    mgs, mos, crs, x0s, vs = batch([(O.BCC, 16, 1400.0, s) for s in (3, 5, 7, 9)], t_eq=10, t_s=20,
+                                   k_spring=2.4)
+    x, v, Wd = run(ctx, 0, mgs, crs, x0s, vs, 0, 60)
+    plan = ne.ne_ctx_crystal_plan(ctx)
+    assert plan["runner"] == "brick" and plan["cluster_ctas"] == 0
+    sms = torch.cuda.get_device_properties(DEV).multi_processor_count
+    if 128 <= sms < 172:
+        assert plan["threads_per_atom"] == 3 and plan["ctas"] == 128
+    q, n = 2, len(x0s[0])
+    box = O.create_crystal(O.BCC, W.A_BCC, 16, 16, 16)[1]
+    ro = O.switch_run(p, th, mos[q], x0s[q], vs[q], x0s[q], box)
+    assert np.abs(x.cpu().numpy()[q * n:(q + 1) * n] - ro["x"]).max() < 2e-4
+    Wg = Wd.cpu().numpy()[q]
+    assert Wg[0] == pytest.approx(ro["W_f"], rel=1e-5, abs=1e-2)
+    assert Wg[1] == pytest.approx(ro["W_b"], rel=1e-5, abs=1e-2)
 
 
 def test_brick_runner_cumulative_works_resume_and_species(ctx, pot):

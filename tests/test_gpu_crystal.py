@@ -539,8 +539,12 @@ def test_runner_pairs_past_the_tmem_visits(ctx, pot, runner):
         x, v = T(xs), T(v0)
         Wd = torch.zeros((1, 2), dtype=torch.float64, device=DEV)
         ne.ne_crystal_run_segment(ctx, [mg], [(O.BCC, W.A_BCC, 6, 6, 6)], x, v, Wd, 0, 10)
+        plan = ne.ne_ctx_crystal_plan(ctx)
     finally:
         ne.ne_ctx_set_runner(ctx, 0)
+    assert plan["runner"] == ("cluster" if runner == 1 else "brick")
+    if runner == 1:  # 432 atoms: two CTAs of 384 slots, two threads per atom
+        assert plan["threads_per_atom"] == 2 and plan["cluster_ctas"] >= 2 and plan["ctas"] == plan["cluster_ctas"]
     assert np.abs(x.cpu().numpy() - ro["x"]).max() < 2e-5
     assert np.abs(v.cpu().numpy() - ro["v"]).max() < 1e-3  # that force alone changes v by ~4e-3 A/ps a step
     assert float(Wd[0, 0]) == pytest.approx(ro["W_f"], rel=1e-5)
