@@ -447,7 +447,7 @@ def run_ours(args):
                 # 0.07 MB written); the replicas live on chip or in L2, so the
                 # figure does not grow with the steps; null elsewhere
                 "traffic": (2.27e6 if args.workload == "fl2" and runner_kind == "cluster" else
-                            1.93e6 if args.workload == "rs16" and runner_kind == "brick" else None),
+                            1.91e6 if args.workload == "rs16" and runner_kind == "brick" else None),
                 "kernel_ms": kern_ms, "us_per_step": kern_ms * 1e3 / K,
                 "peak_note": "%d SMs x %d FP32 lanes x %.0f MHz (median SM clock sampled around the "
                              "timed region)" % (n_sm, FP32_LANES_PER_SM, sm_hz / 1e6),
