@@ -409,9 +409,11 @@ __global__ void __launch_bounds__(NE_TILE* TPA)
 
 // ------------------------------------------------------------ backward
 // dU/dtheta: U is linear in the phi and F knot parameters; the f knots enter
-// through rho_i, weighted by F'(rho_i).  With the full list each pair is seen
-// from both atoms: phi takes 1/2 per direction, f takes F'(rho_i) from atom
-// i's side only.  Hermite basis on interval k with u in [0, 1) and spacing h:
+// through rho_i, weighted by F'(rho_i).  The FP64 kernel walks the full
+// list, each pair from both atoms: phi takes 1/2 per direction, f takes
+// F'(rho_i) from atom i's side only; the mixed kernel takes each pair once,
+// phi whole and f with F'(rho_i) + F'(rho_j) (half the bin atomics).
+// Hermite basis on interval k with u in [0, 1) and spacing h:
 // (h00, h h10, h01, h h11) multiply (y_k, m_k, y_{k+1}, m_{k+1}).
 __device__ __forceinline__ void hermite_w(double u, double h, double w[4])
 {
@@ -502,6 +504,12 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
             const int m = B.scnt[i * TPA + lane];
             for (int q = 0; q < m; ++q) {
                 const int jn = B.sl[(q * B.n_tot + i) * TPA + lane];
+                // each pair once, from its lower-index atom: the short lists
+                // are symmetric (the minimum-image difference of j and i is
+                // the exact negative of that of i and j, so both atoms see
+                // the same r), and the pair adds phi's basis weights whole
+                // and f's times F'_i + F'_j
+                if (jn < i) continue;
                 float4 pj = B.posF[jn];
                 float dx = mi(pj.x - pi.x, Lf0, iL0), dy = mi(pj.y - pi.y, Lf1, iL1),
                       dz = mi(pj.z - pi.z, Lf2, iL2);
@@ -511,9 +519,10 @@ __global__ void __launch_bounds__(BWD_THREADS, 1)
                 float w[4];
                 hermite_wf(t - (float)kk, 1.f, w);  // slope weights without h
                 // w = (y_kk, m_kk / h, y_kk+1, m_kk+1 / h) weights
+                const float dFij = dFi + pj.w;
                 for (int c = 0; c < 4; ++c) {
-                    atomicAdd(spf + bin_index(0, kk + (c >> 1), c & 1, nk), 0.5f * w[c]);
-                    atomicAdd(spf + bin_index(1, kk + (c >> 1), c & 1, nk), dFi * w[c]);
+                    atomicAdd(spf + bin_index(0, kk + (c >> 1), c & 1, nk), w[c]);
+                    atomicAdd(spf + bin_index(1, kk + (c >> 1), c & 1, nk), dFij * w[c]);
                 }
             }
             if (lane == 0) {
