@@ -45,9 +45,14 @@
 namespace {
 
 constexpr int BTHREADS = 768;
-// TMEM scratch between the pair passes (as in the cluster runner): warp w
-// holds f'(r)/r of its visits in lanes 32 (w mod 4) .. +31, columns
-// QMAX (w div 4) .. +QMAX-1; visits past QMAX are recomputed in pass 2
+// TMEM scratch (as in the cluster runner): warp w owns lanes 32 (w mod 4)
+// .. +31 and the QMAX columns from QMAX (w div 4): f'(r)/r of a thread's
+// first QF visits (written by pass 1, read by pass 2; later visits are
+// recomputed in pass 2), then the neighbour index of its first QJ visits
+// (32 bits a column, written once per launch and read by pass 1: a lattice
+// stencil sends atom i's k-th entry to the same atom for the whole launch).  QF and QJ depend
+// on the threads per atom: at 1 a thread visits up to ~112 entries and all
+// columns hold f'(r)/r
 constexpr int FRB = NE_TM_BATCH;
 constexpr int QMAX = NE_TM_COLS / (BTHREADS / 32 / 4) / FRB * FRB;
 constexpr int NKT = 256;    // scan-bound bins of the stencil distance
@@ -154,6 +159,9 @@ __global__ void __launch_bounds__(BTHREADS, 1)
 {
     constexpr int SLOTS = BTHREADS / TPA;
     static_assert(BTHREADS % TPA == 0 && SLOTS % 32 == 0, "whole warps of one pair lane");
+    constexpr int QF = TPA == 1 ? QMAX : (TPA == 2 ? 56 : 48);
+    constexpr int QJ = TPA == 1 ? 0 : QMAX - QF;
+    static_assert(QF % FRB == 0 && QJ % FRB == 0 && QF + QJ <= QMAX && QJ <= QF, "TMEM columns per warp");
     extern __shared__ __align__(16) unsigned char smem[];
     const int rep = cta_rep[blockIdx.x];
     const XRep& R_ = reps[rep];
@@ -258,6 +266,23 @@ __global__ void __launch_bounds__(BTHREADS, 1)
         sxy = (c / ny) * LY + c % ny;
         stb = b * nst;
         skb = b * NKT;
+    }
+    if constexpr (QJ > 0) {
+        // the neighbour indices of this thread's first QJ visits (visits past
+        // the stencil read its last entry, as in the passes)
+#pragma unroll 1
+        for (int q0 = 0; q0 < QJ; q0 += FRB) {
+            float jf[FRB];
+#pragma unroll
+            for (int uq = 0; uq < FRB; ++uq) {
+                const int k = min(lane + TPA * (q0 + uq), nst - 1);
+                const int code = __float_as_int(s_sv[stb + k].w);
+                jf[uq] = __int_as_float(s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)]);
+            }
+            __syncwarp();
+            ne_tm_st(tm_w + (unsigned)(QF + q0), jf);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     const int ta = slot_atom(threadIdx.x);
     const bool own = threadIdx.x < A_c && ta < n;
@@ -456,76 +481,97 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             nq = Kw > lane ? ((Kw - lane + TPA - 1) / TPA + FRB - 1) / FRB * FRB : 0;
             int ql = -1;  // this thread's last visit inside r_c
             float rh = 0.f, rl = 0.f;
+            // one stencil visit (entry e, neighbour index j, visit index qv):
+            // the pair's terms of rho, the forces and the energy; returns
+            // f'(r)/r inside r_c, else 0
+            auto visit = [&](float4 e, int j, int qv) -> float {
+                float fr = 0.f;
+                const float4 uj = __ldcg(&u_cur[j]);
+                if constexpr (NPT) {
+                    e.x *= muf[0];
+                    e.y *= muf[1];
+                    e.z *= muf[2];
+                }
+                const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < rc2) {
+                    const float irh = rsqrtf(r2) * inv_h;
+                    const float t = r2 * irh;
+                    const int kk = min((int)t, nk - 2);
+                    const float w = t - (float)kk;
+                    float4 cf, g;
+                    if (kk < kchk) {
+                        if (r2 < rmin2) bad |= ST_ERANGE;
+                        if (kk >= k_lo) {
+                            cf = s_tabP[kk - k_lo];
+                            g = s_tabF[kk - k_lo];
+                        } else {
+                            cf = __ldg(&tab.pf32[2 * kk]);
+                            g = __ldg(&tab.pf32[2 * kk + 1]);
+                        }
+                    } else {
+                        cf = s_tabP[kk - k_lo];
+                        g = s_tabF[kk - k_lo];
+                    }
+                    {
+                        // f and df/dw together (Horner with derivative)
+                        float fv = fmaf(g.w, w, g.z), fd = g.w;
+                        fd = fmaf(fd, w, fv);
+                        fv = fmaf(fv, w, g.y);
+                        fd = fmaf(fd, w, fv);
+                        fv = fmaf(fv, w, g.x);
+                        const float s_ = rh + fv, bp = s_ - rh;
+                        rl += (rh - (s_ - bp)) + (fv - bp);
+                        rh = s_;
+                        fr = fd * irh;  // f'(r) / r
+                        ql = qv;
+                    }
+                    float pv = fmaf(cf.w, w, cf.z), pd = cf.w;
+                    pd = fmaf(pd, w, pv);
+                    pv = fmaf(pv, w, cf.y);
+                    pd = fmaf(pd, w, pv);
+                    pv = fmaf(pv, w, cf.x);
+                    const float sc = pd * irh;
+                    fx += sc * dx;
+                    fy += sc * dy;
+                    fz += sc * dz;
+                    ep += pv;
+                    if constexpr (NPT) {  // -(1/2) r_a^2 / r dU/dr of the pair's half
+                        vxx -= 0.5f * sc * dx * dx;
+                        vyy -= 0.5f * sc * dy * dy;
+                        vzz -= 0.5f * sc * dz * dz;
+                    }
+                    ++m;
+                }
+                return fr;
+            };
+            // the first QJ visits: neighbour indices from TMEM
+            const int nqa = QJ > 0 ? min(nq, QJ) : 0;
 #pragma unroll 1
-            for (int q0 = 0; q0 < nq; q0 += FRB) {
+            for (int q0 = 0; q0 < nqa; q0 += FRB) {
+                float jf[FRB], frv[FRB];
+                __syncwarp();
+                ne_tm_ld(tm_w + (unsigned)(QF + q0), jf);
+#pragma unroll
+                for (int uq = 0; uq < FRB; ++uq) {
+                    const int k = min(lane + TPA * (q0 + uq), nst - 1);
+                    frv[uq] = visit(s_sv[stb + k], __float_as_int(jf[uq]), q0 + uq);
+                }
+                __syncwarp();
+                ne_tm_st(tm_w + (unsigned)q0, frv);
+            }
+            // the rest: indices from the wrapped-cell tables
+#pragma unroll 1
+            for (int q0 = nqa; q0 < nq; q0 += FRB) {
                 float frv[FRB];
 #pragma unroll
                 for (int uq = 0; uq < FRB; ++uq) {
                     const int k = min(lane + TPA * (q0 + uq), nst - 1);
-                    float fr = 0.f;
-                    float4 e = s_sv[stb + k];
+                    const float4 e = s_sv[stb + k];
                     const int code = __float_as_int(e.w);
-                    const int j = s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)];
-                    const float4 uj = __ldcg(&u_cur[j]);
-                    if constexpr (NPT) {
-                        e.x *= muf[0];
-                        e.y *= muf[1];
-                        e.z *= muf[2];
-                    }
-                    const float dx = e.x + uj.x - ui.x, dy = e.y + uj.y - ui.y, dz = e.z + uj.z - ui.z;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    if (r2 < rc2) {
-                        const float irh = rsqrtf(r2) * inv_h;
-                        const float t = r2 * irh;
-                        const int kk = min((int)t, nk - 2);
-                        const float w = t - (float)kk;
-                        float4 cf, g;
-                        if (kk < kchk) {
-                            if (r2 < rmin2) bad |= ST_ERANGE;
-                            if (kk >= k_lo) {
-                                cf = s_tabP[kk - k_lo];
-                                g = s_tabF[kk - k_lo];
-                            } else {
-                                cf = __ldg(&tab.pf32[2 * kk]);
-                                g = __ldg(&tab.pf32[2 * kk + 1]);
-                            }
-                        } else {
-                            cf = s_tabP[kk - k_lo];
-                            g = s_tabF[kk - k_lo];
-                        }
-                        {
-                            // f and df/dw together (Horner with derivative)
-                            float fv = fmaf(g.w, w, g.z), fd = g.w;
-                            fd = fmaf(fd, w, fv);
-                            fv = fmaf(fv, w, g.y);
-                            fd = fmaf(fd, w, fv);
-                            fv = fmaf(fv, w, g.x);
-                            const float s_ = rh + fv, bp = s_ - rh;
-                            rl += (rh - (s_ - bp)) + (fv - bp);
-                            rh = s_;
-                            fr = fd * irh;  // f'(r) / r
-                            ql = q0 + uq;
-                        }
-                        float pv = fmaf(cf.w, w, cf.z), pd = cf.w;
-                        pd = fmaf(pd, w, pv);
-                        pv = fmaf(pv, w, cf.y);
-                        pd = fmaf(pd, w, pv);
-                        pv = fmaf(pv, w, cf.x);
-                        const float sc = pd * irh;
-                        fx += sc * dx;
-                        fy += sc * dy;
-                        fz += sc * dz;
-                        ep += pv;
-                        if constexpr (NPT) {  // -(1/2) r_a^2 / r dU/dr of the pair's half
-                            vxx -= 0.5f * sc * dx * dx;
-                            vyy -= 0.5f * sc * dy * dy;
-                            vzz -= 0.5f * sc * dz * dz;
-                        }
-                        ++m;
-                    }
-                    frv[uq] = fr;
+                    frv[uq] = visit(e, s_lxy[sxy + (code & 0xffff)] + s_lz[sz + ((unsigned)code >> 16)], q0 + uq);
                 }
-                if (q0 < QMAX) {
+                if (q0 < QF) {
                     __syncwarp();
                     ne_tm_st(tm_w + (unsigned)q0, frv);
                 }
@@ -563,9 +609,12 @@ __global__ void __launch_bounds__(BTHREADS, 1)
         if (!dead) {
             const float dFi = __ldcg(&bb.fp[gofs + sui]);
             const float* fp_r = bb.fp + gofs;
-            const int nqt = min(nq, QMAX);
+            const int nqt = min(nq, QF);
 #pragma unroll 1
             for (int q0 = 0; q0 < nqt; q0 += FRB) {
+                // (the neighbour indices from the tables: also reading them
+                // from TMEM here, 16 live words a batch, spilled at the
+                // 80-register cap)
                 float frv[FRB];
                 __syncwarp();
                 ne_tm_ld(tm_w + (unsigned)q0, frv);
@@ -597,7 +646,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
                 }
             }
             // visits past the TMEM columns: the pair recomputed
-            for (int q = QMAX; q < nq; ++q) {
+            for (int q = QF; q < nq; ++q) {
                 const int k = min(lane + TPA * q, nst - 1);
                 float4 e = s_sv[stb + k];
                 const int code = __float_as_int(e.w);
