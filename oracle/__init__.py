@@ -23,7 +23,7 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   philox4x32_10         normal moments, KS and avalanche tests (CPU); bit
                         for bit against cuRAND's Philox4_32_10 (NVIDIA's
                         implementation, run through its device API on the
-                        GPU) over >= 1e6 counters (tests/test_zz_philox_curand.py)
+                        GPU) over >= 1e6 counters (tests/test_gpu_philox_curand.py)
   switch_run (FL)       harmonic->harmonic exact dF, self-switch W == 0,
                         NVE energy conservation, equipartition
   switch_run (RS)       harmonic F(T) = 3NkT ln(hbar w/kT) at every T
