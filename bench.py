@@ -632,7 +632,7 @@ def main():
     ap.add_argument("--tpa", type=int, default=4)
     ap.add_argument("--path", default="auto", choices=["auto", "crystal", "general"],
                     help="crystal: persistent cluster runner (mixed); general: multi-kernel path")
-    ap.add_argument("--cpu-steps", type=int, default=40)
+    ap.add_argument("--cpu-steps", type=int, default=80)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
     ap.add_argument("--autotune", action="store_true",
