@@ -153,7 +153,10 @@ class BatchAdvancer:
         self._packed = None
         self._cuda = bool(getattr(x0, "is_cuda", False))
         self._sc = torch.cuda.Stream() if self._cuda else None
-        self._sg = torch.cuda.Stream() if self._cuda else None
+        # the multi-kernel path's short kernels at high priority: the crystal
+        # runner's persistent clusters hold their SMs for a whole chunk, and a
+        # freed SM should go to the moved replicas' next kernel first
+        self._sg = torch.cuda.Stream(priority=-1) if self._cuda else None
 
     @staticmethod
     def _handle(st):
