@@ -154,3 +154,17 @@ def test_autotuner_refuses_a_box_no_candidate_fits(monkeypatch):
         ne._CTX_EAM.pop(ctx.value)
     with pytest.raises(ValueError, match="not created"):
         autotune.tune(C.c_void_p(0x9190), [ne.md_params()], [0, 128], x, x, x, [[20.0] * 3], _z(1, 2))
+
+
+def test_crystal_plan_wrapper_reads_the_four_integers(monkeypatch):
+    """ne_ctx_crystal_plan: runner 1 is the cluster runner, 2 the brick
+    runner; the four integers come back in the dict the bench reports."""
+    def plan(r, t, n, c):
+        def fake(ctx, pr, pt, pn, pc):
+            pr._obj.value, pt._obj.value, pn._obj.value, pc._obj.value = r, t, n, c
+            return 0
+        return fake
+    for args, want in (((1, 2, 120, 6), {"runner": "cluster", "threads_per_atom": 2, "ctas": 120, "cluster_ctas": 6}),
+                       ((2, 3, 128, 0), {"runner": "brick", "threads_per_atom": 3, "ctas": 128, "cluster_ctas": 0})):
+        monkeypatch.setattr(ne, "load", lambda *a, f=plan(*args), **k: types.SimpleNamespace(ne_ctx_crystal_plan=f))
+        assert ne.ne_ctx_crystal_plan(None) == want
