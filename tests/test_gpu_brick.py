@@ -113,6 +113,25 @@ def test_brick_runner_matches_the_cluster_runner(ctx):
     assert torch.allclose(Wb, Wc, rtol=1e-5, atol=1e-4)
 
 
+def test_brick_runner_two_threads_per_atom_matches_the_cluster_runner(ctx):
+    """The 20-replica benchmark batch (10 x bcc 10^3 + 10 x fcc 8^3 at
+    1400 K) forced onto the brick runner: 3 threads per atom would need 160
+    CTAs on a 152-SM device, so it takes 2 (120 CTAs; 24 neighbour indices a
+    thread in tensor memory beside 56 visits of f'(r)/r); the 100-step
+    schedule against the cluster runner on the same batch."""
+    systems = [(O.BCC, 10, 1400.0, s) for s in range(1, 11)] + [(O.FCC, 8, 1400.0, s) for s in range(11, 21)]
+    mgs, mos, crs, x0s, vs = batch(systems, k_spring=2.4)
+    xb, vb, Wb = run(ctx, 2, mgs, crs, x0s, vs, 0, 100)
+    plan = ne.ne_ctx_crystal_plan(ctx)
+    xc, vc, Wc = run(ctx, 1, mgs, crs, x0s, vs, 0, 100)
+    assert plan["runner"] == "brick"
+    sms = torch.cuda.get_device_properties(DEV).multi_processor_count
+    if 120 <= sms < 160:
+        assert plan["threads_per_atom"] == 2 and plan["ctas"] == 120
+    assert torch.abs(xb - xc).max().item() < 2e-5
+    assert torch.allclose(Wb, Wc, rtol=1e-5, atol=1e-4)
+
+
 def test_brick_runner_large_replica_against_oracle(ctx, pot):
     """bcc 16^3 (8192 atoms, the reversible-scaling cell): too large for a
     cluster, so the default setting runs it on the brick runner; 60 steps
